@@ -1,0 +1,963 @@
+/*
+ * FP64 CPU oracle for the multiple-shooting augmented-Lagrangian iLQR method
+ * over a scenario tree (branch MPC), arXiv 2506.13624.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the CUDA path computes.  Only tests, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * constant or helper with the CUDA path.
+ *
+ * Passages followed (paper section / equation / algorithm):
+ *   problem             Sec. II-B, Eq. (bmpc): node costs, x_i = f_p(i)(x_p(i), u_p(i)), g <= 0
+ *   tree LQR            Sec. III-A, Eq. (lqr_tree_approx), Eq. (tree_Riccati),
+ *                       Eq. (tree_feedback_laws); forward rollout as in Sec. II-A
+ *   augmented Lagr.     Sec. IV-A, Eq. (AL) (PHR penalty), Lagrangian with lambda,
+ *                       Gauss-Newton Hessian of the PHR term
+ *   linear rollout      Sec. IV-A "Search direction" (multiple shooting)
+ *   merit, line search  Eq. (merit), Eq. (sufficient_decrease), Algorithm 1
+ *   KKT residual        Sec. IV-A "Inner loop stopping criterion"
+ *   outer loop (BCL)    Sec. IV-B, Algorithm 1, constants of Sec. V-B
+ *
+ * Readings where the paper is silent or garbled (kept identical on the CUDA side):
+ *   - dynamics Jacobians A_n, B_n per parent node; defect c_m per child edge;
+ *   - multiplier update y <- max(0, y + rho g) (standard PHR, Algorithm 1 drops y);
+ *   - tolerance schedules omega <- omega rho^-b_omega, eta <- eta rho^-b_eta on success,
+ *     omega <- omega0 rho^-a_omega, eta <- eta0 rho^-a_eta on failure, both floored at eps_tol;
+ *   - the merit uses J = L_a and moves (x, u, lambda) jointly; lambda_QP = P dx + p;
+ *   - mu rule: phi'(0; mu) <= -1/2 dz'W dz, else mu <- max(mu, 2(phi'(0;0) + 1/2 dz'W dz)/|d|^2);
+ *   - alpha_i = 2^-i; Armijo with an absolute slack ls_rel_eps*|phi(0)| for finite precision;
+ *     no accepted alpha -> smallest alpha, three failures in a row -> LS_FAIL;
+ *   - the root carries no state constraints (x_0 is fixed), leaves no input constraints;
+ *   - cold start: x linearly interpolated from x0 to the node's final reference, u = 0,
+ *     lambda = 0, y = 0 (Sec. V-B initialisation).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXX 16
+#define MAXU 8
+#define MAXN (MAXX + MAXU)
+#define OBS_EPS 1e-6   /* smoothing of the normalised distance at the ellipse centre */
+
+typedef struct {
+    int n, nx, nu, model, n_obs, box_on, lane_on;
+    const int *parent;
+    double dt;
+    const double *params;   /* [10]: L, m, Iz, lf, lr, Cf, Cr, vmin, veps, n_sub */
+    const double *x0;       /* [nx] */
+    const double *xref;     /* [n][nx] */
+    const double *weight;   /* [n] */
+    const double *Qw, *QNw; /* [nx] */
+    const double *Rw;       /* [nu] */
+    const double *u_lo, *u_hi;
+    double lane_lo, lane_hi;
+    const double *obs;      /* [n][n_obs][5] cx, cy, heading, a, b */
+    const double *Alin, *Blin;
+} orc_problem;
+
+typedef struct {
+    int max_iters, max_outer, n_alpha;
+    double eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta;
+    double rho0, rho_max, mu0, beta, ls_rel_eps;
+} orc_opts;
+
+typedef struct {
+    int status, inner_iters, outer_iters, ls_fail_total;
+    double r_kkt, c, rho, mu, omega, eta;
+} orc_stats;
+
+enum { ORC_OK = 0, ORC_MAX_ITER = 1, ORC_LS_FAIL = 2, ORC_ERR_INVALID = -1, ORC_ERR_NUMERIC = -3 };
+
+/* ------------------------------------------------------------ small dense algebra */
+/* row-major: M[i*cols + j] */
+static void matmul(int r, int k, int c, const double *A, const double *B, double *C) {
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < c; ++j) {
+            double s = 0.0;
+            for (int t = 0; t < k; ++t) s += A[i * k + t] * B[t * c + j];
+            C[i * c + j] = s;
+        }
+}
+/* C = A^T B with A (k x r), B (k x c) */
+static void matTmul(int r, int k, int c, const double *A, const double *B, double *C) {
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < c; ++j) {
+            double s = 0.0;
+            for (int t = 0; t < k; ++t) s += A[t * r + i] * B[t * c + j];
+            C[i * c + j] = s;
+        }
+}
+/* y = A x, A (r x c) */
+static void matvec(int r, int c, const double *A, const double *x, double *y) {
+    for (int i = 0; i < r; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < c; ++j) s += A[i * c + j] * x[j];
+        y[i] = s;
+    }
+}
+/* y = A^T x, A (r x c) */
+static void matTvec(int r, int c, const double *A, const double *x, double *y) {
+    for (int j = 0; j < c; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < r; ++i) s += A[i * c + j] * x[i];
+        y[j] = s;
+    }
+}
+/* Cholesky H = L L^T (n x n), returns 0 if not positive definite. */
+static int cholesky(int n, const double *H, double *L) {
+    memset(L, 0, sizeof(double) * n * n);
+    for (int j = 0; j < n; ++j) {
+        double s = H[j * n + j];
+        for (int t = 0; t < j; ++t) s -= L[j * n + t] * L[j * n + t];
+        if (!(s > 0.0)) return 0;
+        L[j * n + j] = sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double v = H[i * n + j];
+            for (int t = 0; t < j; ++t) v -= L[i * n + t] * L[j * n + t];
+            L[i * n + j] = v / L[j * n + j];
+        }
+    }
+    return 1;
+}
+/* solve (L L^T) X = Bm for X (n x m) in place of Bm */
+static void chol_solve(int n, int m, const double *L, double *Bm) {
+    for (int col = 0; col < m; ++col) {
+        for (int i = 0; i < n; ++i) {
+            double v = Bm[i * m + col];
+            for (int t = 0; t < i; ++t) v -= L[i * n + t] * Bm[t * m + col];
+            Bm[i * m + col] = v / L[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double v = Bm[i * m + col];
+            for (int t = i + 1; t < n; ++t) v -= L[t * n + i] * Bm[t * m + col];
+            Bm[i * m + col] = v / L[i * n + i];
+        }
+    }
+}
+
+/* ------------------------------------------------------------ dynamics (Eq. bmpc, x_i = f_p(i)) */
+/* Continuous-time right-hand side fc(s, u) and its Jacobians Jx (nx x nx), Ju (nx x nu). */
+static void rhs(const orc_problem *P, const double *s, const double *u, double *f, double *Jx, double *Ju) {
+    const double *prm = P->params;
+    int nx = P->nx, nu = P->nu;
+    memset(Jx, 0, sizeof(double) * nx * nx);
+    memset(Ju, 0, sizeof(double) * nx * nu);
+    if (P->model == 0) {
+        /* kinematic bicycle: X' = v cos psi, Y' = v sin psi, psi' = v tan(delta)/L, v' = a */
+        double L = prm[0], psi = s[2], v = s[3], a = u[0], d = u[1];
+        double td = tan(d);
+        f[0] = v * cos(psi);
+        f[1] = v * sin(psi);
+        f[2] = v * td / L;
+        f[3] = a;
+        Jx[0 * 4 + 2] = -v * sin(psi);
+        Jx[0 * 4 + 3] = cos(psi);
+        Jx[1 * 4 + 2] = v * cos(psi);
+        Jx[1 * 4 + 3] = sin(psi);
+        Jx[2 * 4 + 3] = td / L;
+        Ju[2 * 2 + 1] = v * (1.0 + td * td) / L;
+        Ju[3 * 2 + 0] = 1.0;
+        return;
+    }
+    /* dynamic bicycle, linear tyres:
+     *   slip alpha_f = atan((vy + lf r)/vb) - delta, alpha_r = atan((vy - lr r)/vb),
+     *   vb = smooth max(vx, vmin), F_f = -Cf alpha_f, F_r = -Cr alpha_r,
+     *   X' = vx cos psi - vy sin psi, Y' = vx sin psi + vy cos psi, psi' = r,
+     *   vx' = a - F_f sin(delta)/m + r vy, vy' = (F_f cos(delta) + F_r)/m - r vx,
+     *   r' = (lf F_f cos(delta) - lr F_r)/Iz                                    */
+    double m = prm[1], Iz = prm[2], lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6];
+    double vmin = prm[7], veps = prm[8];
+    double psi = s[2], vx = s[3], vy = s[4], r = s[5], a = u[0], d = u[1];
+    double w = sqrt((vx - vmin) * (vx - vmin) + veps * veps);
+    double vb = 0.5 * (vx + vmin + w);
+    double dvb = 0.5 * (1.0 + (vx - vmin) / w);
+    double tf = (vy + lf * r) / vb, tr = (vy - lr * r) / vb;
+    double af = atan(tf) - d, ar = atan(tr);
+    double Ff = -Cf * af, Fr = -Cr * ar;
+    double cp = cos(psi), sp = sin(psi);
+    f[0] = vx * cp - vy * sp;
+    f[1] = vx * sp + vy * cp;
+    f[2] = r;
+    f[3] = a + r * vy;
+    f[4] = (Ff + Fr) / m - r * vx;
+    f[5] = (lf * Ff - lr * Fr) / Iz;
+    double gf = 1.0 / (1.0 + tf * tf), gr = 1.0 / (1.0 + tr * tr);
+    /* partials of the slip angles */
+    double daf_vx = gf * (-tf / vb) * dvb, daf_vy = gf / vb, daf_r = gf * lf / vb;
+    double dar_vx = gr * (-tr / vb) * dvb, dar_vy = gr / vb, dar_r = -gr * lr / vb;
+    double dFf_vx = -Cf * daf_vx, dFf_vy = -Cf * daf_vy, dFf_r = -Cf * daf_r, dFf_d = Cf;
+    double dFr_vx = -Cr * dar_vx, dFr_vy = -Cr * dar_vy, dFr_r = -Cr * dar_r;
+    /* row X */
+    Jx[0 * 6 + 2] = -vx * sp - vy * cp;
+    Jx[0 * 6 + 3] = cp;
+    Jx[0 * 6 + 4] = -sp;
+    /* row Y */
+    Jx[1 * 6 + 2] = vx * cp - vy * sp;
+    Jx[1 * 6 + 3] = sp;
+    Jx[1 * 6 + 4] = cp;
+    /* row psi */
+    Jx[2 * 6 + 5] = 1.0;
+    /* row vx */
+    Jx[3 * 6 + 4] = r;
+    Jx[3 * 6 + 5] = vy;
+    Ju[3 * 2 + 0] = 1.0;
+    /* row vy */
+    Jx[4 * 6 + 3] = (dFf_vx + dFr_vx) / m - r;
+    Jx[4 * 6 + 4] = (dFf_vy + dFr_vy) / m;
+    Jx[4 * 6 + 5] = (dFf_r + dFr_r) / m - vx;
+    Ju[4 * 2 + 1] = dFf_d / m;
+    /* row r */
+    Jx[5 * 6 + 3] = (lf * dFf_vx - lr * dFr_vx) / Iz;
+    Jx[5 * 6 + 4] = (lf * dFf_vy - lr * dFr_vy) / Iz;
+    Jx[5 * 6 + 5] = (lf * dFf_r - lr * dFr_r) / Iz;
+    Ju[5 * 2 + 1] = lf * dFf_d / Iz;
+}
+
+/* Discrete dynamics x+ = f(x, u) and, if A/B are given, A = df/dx, B = df/du.
+ * Models 0/1: n_sub classical RK4 steps of length dt/n_sub, Jacobians by the
+ * forward-mode chain rule through every RK4 stage.  Model 2: x+ = Alin x + Blin u. */
+int orc_dynamics(const orc_problem *P, const double *x, const double *u, double *xn, double *A, double *B) {
+    int nx = P->nx, nu = P->nu, nz = nx + nu;
+    if (P->model == 2) {
+        double t[MAXX];
+        matvec(nx, nx, P->Alin, x, xn);
+        matvec(nx, nu, P->Blin, u, t);
+        for (int i = 0; i < nx; ++i) xn[i] += t[i];
+        if (A) memcpy(A, P->Alin, sizeof(double) * nx * nx);
+        if (B) memcpy(B, P->Blin, sizeof(double) * nx * nu);
+        return 0;
+    }
+    int n_sub = (int)P->params[9];
+    if (n_sub < 1) n_sub = 1;
+    double h = P->dt / n_sub;
+    double S[MAXX * MAXN], Eu[MAXU * MAXN];          /* dz/d(x,u): state and input parts */
+    memset(S, 0, sizeof S);
+    memset(Eu, 0, sizeof Eu);
+    for (int i = 0; i < nx; ++i) S[i * nz + i] = 1.0;
+    for (int j = 0; j < nu; ++j) Eu[j * nz + nx + j] = 1.0;
+    double z[MAXX];
+    memcpy(z, x, sizeof(double) * nx);
+    static const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+    static const double wts[4] = {1.0, 2.0, 2.0, 1.0};
+    for (int sub = 0; sub < n_sub; ++sub) {
+        double kprev[MAXX] = {0}, Dprev[MAXX * MAXN];
+        memset(Dprev, 0, sizeof Dprev);
+        double ksum[MAXX] = {0}, Dsum[MAXX * MAXN];
+        memset(Dsum, 0, sizeof Dsum);
+        for (int st = 0; st < 4; ++st) {
+            double zs[MAXX], Ss[MAXX * MAXN], k[MAXX], D[MAXX * MAXN], Jx[MAXX * MAXX], Ju[MAXX * MAXU];
+            for (int i = 0; i < nx; ++i) zs[i] = z[i] + cst[st] * h * kprev[i];
+            for (int i = 0; i < nx * nz; ++i) Ss[i] = S[i] + cst[st] * h * Dprev[i];
+            rhs(P, zs, u, k, Jx, Ju);
+            for (int i = 0; i < nx; ++i) ksum[i] += wts[st] * k[i];
+            memcpy(kprev, k, sizeof(double) * nx);
+            if (!A && !B) continue;                    /* no Jacobian requested */
+            double t1[MAXX * MAXN], t2[MAXX * MAXN];
+            matmul(nx, nx, nz, Jx, Ss, t1);
+            matmul(nx, nu, nz, Ju, Eu, t2);
+            for (int i = 0; i < nx * nz; ++i) D[i] = t1[i] + t2[i];
+            for (int i = 0; i < nx * nz; ++i) Dsum[i] += wts[st] * D[i];
+            memcpy(Dprev, D, sizeof(double) * nx * nz);
+        }
+        for (int i = 0; i < nx; ++i) z[i] += h / 6.0 * ksum[i];
+        for (int i = 0; i < nx * nz; ++i) S[i] += h / 6.0 * Dsum[i];
+    }
+    memcpy(xn, z, sizeof(double) * nx);
+    if (A)
+        for (int i = 0; i < nx; ++i)
+            for (int j = 0; j < nx; ++j) A[i * nx + j] = S[i * nz + j];
+    if (B)
+        for (int i = 0; i < nx; ++i)
+            for (int j = 0; j < nu; ++j) B[i * nu + j] = S[i * nz + nx + j];
+    return 0;
+}
+
+/* ------------------------------------------------------------ tree helpers */
+typedef struct {
+    int n;
+    int *first_child, *n_child, *child; /* children of i: child[first_child[i] .. +n_child[i]) ascending */
+    int *stage;
+} tree_t;
+
+static int tree_build(const orc_problem *P, tree_t *T) {
+    int n = P->n;
+    T->n = n;
+    T->first_child = (int *)calloc(n, sizeof(int));
+    T->n_child = (int *)calloc(n, sizeof(int));
+    T->child = (int *)calloc(n > 1 ? n - 1 : 1, sizeof(int));
+    T->stage = (int *)calloc(n, sizeof(int));
+    if (P->parent[0] != -1) return 0;
+    for (int i = 1; i < n; ++i) {
+        int p = P->parent[i];
+        if (p < 0 || p >= i) return 0;
+        T->n_child[p]++;
+        T->stage[i] = T->stage[p] + 1;
+    }
+    int off = 0;
+    for (int i = 0; i < n; ++i) { T->first_child[i] = off; off += T->n_child[i]; }
+    int *fill = (int *)calloc(n, sizeof(int));
+    for (int i = 1; i < n; ++i) {
+        int p = P->parent[i];
+        T->child[T->first_child[p] + fill[p]++] = i;
+    }
+    free(fill);
+    return 1;
+}
+static void tree_free(tree_t *T) {
+    free(T->first_child); free(T->n_child); free(T->child); free(T->stage);
+}
+
+/* number of constraint rows per node (same layout at every node) */
+static int n_con(const orc_problem *P) { return 2 * P->nu * P->box_on + P->n_obs + 2 * P->lane_on; }
+
+/* Constraint rows g(x, u) <= 0 of Eq. (bmpc) at node i, their Jacobians and existence flags.
+ * Row layout: [u - u_hi (nu), u_lo - u (nu)] (box, non-leaf nodes), obstacle keep-out ellipses
+ * as a normalised distance g = 1 - sqrt((d_par/a)^2 + (d_perp/b)^2 + eps) (non-root nodes),
+ * lane [Y - hi, lo - Y] (non-root nodes). */
+int orc_constraints(const orc_problem *P, int node, int is_leaf, const double *x, const double *u,
+                    double *g, double *Jx, double *Ju, int *exists) {
+    int nx = P->nx, nu = P->nu, nc = n_con(P), row = 0;
+    memset(Jx, 0, sizeof(double) * nc * nx);
+    memset(Ju, 0, sizeof(double) * nc * nu);
+    for (int c = 0; c < nc; ++c) { g[c] = 0.0; exists[c] = 0; }
+    if (P->box_on) {
+        for (int j = 0; j < nu; ++j) {
+            exists[row] = !is_leaf;
+            g[row] = is_leaf ? 0.0 : u[j] - P->u_hi[j];
+            Ju[row * nu + j] = 1.0;
+            ++row;
+        }
+        for (int j = 0; j < nu; ++j) {
+            exists[row] = !is_leaf;
+            g[row] = is_leaf ? 0.0 : P->u_lo[j] - u[j];
+            Ju[row * nu + j] = -1.0;
+            ++row;
+        }
+    }
+    for (int o = 0; o < P->n_obs; ++o) {
+        const double *ob = P->obs + ((size_t)node * P->n_obs + o) * 5;
+        double dx = x[0] - ob[0], dy = x[1] - ob[1];
+        double ch = cos(ob[2]), sh = sin(ob[2]);
+        double dpar = ch * dx + sh * dy, dper = -sh * dx + ch * dy;
+        double a2 = ob[3] * ob[3], b2 = ob[4] * ob[4];
+        double rr = sqrt(dpar * dpar / a2 + dper * dper / b2 + OBS_EPS);
+        exists[row] = node != 0;
+        g[row] = 1.0 - rr;
+        Jx[row * nx + 0] = -(dpar / a2 * ch - dper / b2 * sh) / rr;
+        Jx[row * nx + 1] = -(dpar / a2 * sh + dper / b2 * ch) / rr;
+        ++row;
+    }
+    if (P->lane_on) {
+        exists[row] = node != 0;
+        g[row] = x[1] - P->lane_hi;
+        Jx[row * nx + 1] = 1.0;
+        ++row;
+        exists[row] = node != 0;
+        g[row] = P->lane_lo - x[1];
+        Jx[row * nx + 1] = -1.0;
+        ++row;
+    }
+    return row;
+}
+
+/* ------------------------------------------------------------ tree LQR (Sec. III-A) */
+/* Solves the tree LQR problem of Eq. (lqr_tree_approx):
+ *   min sum_i 1/2 dx'Q dx + du'M dx + 1/2 du'R du + q'dx + r'du   (leaves: Q, q only)
+ *   s.t. dx_m = A_i dx_i + B_i du_i + c_m for m in ch(i), dx_0 = 0.
+ * Backward: the modified Riccati recursion of Eq. (tree_Riccati) that sums the child value
+ * functions, with the feedback law of Eq. (tree_feedback_laws); forward: the affine rollout
+ * along every root-to-leaf path.  lam_m = P_m dx_m + p_m are the multipliers of the dynamics.
+ * Arrays are per node, row-major: Q[n][nx][nx], M[n][nu][nx], R[n][nu][nu], A[n][nx][nx],
+ * B[n][nx][nu], c[n][nx] (edge into node m; c[0] unused). */
+static int tree_lqr(const tree_t *T, int nx, int nu, const double *Q, const double *M, const double *R,
+                    const double *q, const double *r, const double *A, const double *B, const double *c,
+                    double *K, double *k, double *Pm, double *pv, double *dx, double *du, double *lam) {
+    int n = T->n;
+    for (int i = n - 1; i >= 0; --i) {       /* children always have larger index */
+        double *Pi = Pm + (size_t)i * nx * nx, *pi = pv + (size_t)i * nx;
+        if (T->n_child[i] == 0) {
+            memcpy(Pi, Q + (size_t)i * nx * nx, sizeof(double) * nx * nx);
+            memcpy(pi, q + (size_t)i * nx, sizeof(double) * nx);
+            continue;
+        }
+        /* child sums: Pbar = sum P_m, pbar = sum (p_m + P_m c_m) */
+        double Pbar[MAXX * MAXX] = {0}, pbar[MAXX] = {0};
+        for (int t = 0; t < T->n_child[i]; ++t) {
+            int m = T->child[T->first_child[i] + t];
+            const double *Pc = Pm + (size_t)m * nx * nx, *pc = pv + (size_t)m * nx;
+            double Pcc[MAXX];
+            matvec(nx, nx, Pc, c + (size_t)m * nx, Pcc);
+            for (int e = 0; e < nx * nx; ++e) Pbar[e] += Pc[e];
+            for (int e = 0; e < nx; ++e) pbar[e] += pc[e] + Pcc[e];
+        }
+        const double *Ai = A + (size_t)i * nx * nx, *Bi = B + (size_t)i * nx * nu;
+        double PA[MAXX * MAXX], PB[MAXX * MAXU];
+        double Qxx[MAXX * MAXX], Qux[MAXU * MAXX], Quu[MAXU * MAXU], qx[MAXX], qu[MAXU];
+        matmul(nx, nx, nx, Pbar, Ai, PA);
+        matmul(nx, nx, nu, Pbar, Bi, PB);
+        matTmul(nx, nx, nx, Ai, PA, Qxx);
+        matTmul(nu, nx, nx, Bi, PA, Qux);
+        matTmul(nu, nx, nu, Bi, PB, Quu);
+        matTvec(nx, nx, Ai, pbar, qx);
+        matTvec(nx, nu, Bi, pbar, qu);
+        for (int e = 0; e < nx * nx; ++e) Qxx[e] += Q[(size_t)i * nx * nx + e];
+        for (int e = 0; e < nu * nx; ++e) Qux[e] += M[(size_t)i * nu * nx + e];
+        for (int e = 0; e < nu * nu; ++e) Quu[e] += R[(size_t)i * nu * nu + e];
+        for (int e = 0; e < nx; ++e) qx[e] += q[(size_t)i * nx + e];
+        for (int e = 0; e < nu; ++e) qu[e] += r[(size_t)i * nu + e];
+        double L[MAXU * MAXU];
+        if (!cholesky(nu, Quu, L)) return ORC_ERR_NUMERIC;
+        double *Ki = K + (size_t)i * nu * nx, *ki = k + (size_t)i * nu;
+        for (int e = 0; e < nu * nx; ++e) Ki[e] = -Qux[e];
+        for (int e = 0; e < nu; ++e) ki[e] = -qu[e];
+        chol_solve(nu, nx, L, Ki);
+        chol_solve(nu, 1, L, ki);
+        /* P = Qxx + Qux' K (symmetric in exact arithmetic; stored symmetrised), p = qx + Qux' k */
+        double QK[MAXX * MAXX], Qk[MAXX];
+        matTmul(nx, nu, nx, Qux, Ki, QK);
+        matTvec(nu, nx, Qux, ki, Qk);
+        for (int a = 0; a < nx; ++a)
+            for (int b = 0; b < nx; ++b)
+                Pi[a * nx + b] = 0.5 * ((Qxx[a * nx + b] + QK[a * nx + b]) + (Qxx[b * nx + a] + QK[b * nx + a]));
+        for (int e = 0; e < nx; ++e) pi[e] = qx[e] + Qk[e];
+    }
+    /* forward sweep from the root (dx_0 = 0) */
+    memset(dx, 0, sizeof(double) * nx);
+    for (int i = 0; i < n; ++i) {
+        if (T->n_child[i] == 0) { memset(du + (size_t)i * nu, 0, sizeof(double) * nu); continue; }
+        const double *Ki = K + (size_t)i * nu * nx, *ki = k + (size_t)i * nu;
+        double *dui = du + (size_t)i * nu;
+        matvec(nu, nx, Ki, dx + (size_t)i * nx, dui);
+        for (int e = 0; e < nu; ++e) dui[e] += ki[e];
+        double Ax[MAXX], Bu[MAXX];
+        matvec(nx, nx, A + (size_t)i * nx * nx, dx + (size_t)i * nx, Ax);
+        matvec(nx, nu, B + (size_t)i * nx * nu, dui, Bu);
+        for (int t = 0; t < T->n_child[i]; ++t) {
+            int m = T->child[T->first_child[i] + t];
+            for (int e = 0; e < nx; ++e) dx[(size_t)m * nx + e] = Ax[e] + Bu[e] + c[(size_t)m * nx + e];
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double Pd[MAXX];
+        matvec(nx, nx, Pm + (size_t)i * nx * nx, dx + (size_t)i * nx, Pd);
+        for (int e = 0; e < nx; ++e) lam[(size_t)i * nx + e] = Pd[e] + pv[(size_t)i * nx + e];
+    }
+    return ORC_OK;
+}
+
+int orc_tree_lqr(int n, const int *parent, int nx, int nu, const double *Q, const double *M, const double *R,
+                 const double *q, const double *r, const double *A, const double *B, const double *c,
+                 double *K, double *k, double *Pm, double *pv, double *dx, double *du, double *lam) {
+    if (nx > MAXX || nu > MAXU || n < 1) return ORC_ERR_INVALID;
+    orc_problem P;
+    memset(&P, 0, sizeof P);
+    P.n = n;
+    P.parent = parent;
+    tree_t T;
+    if (!tree_build(&P, &T)) { tree_free(&T); return ORC_ERR_INVALID; }
+    int st = tree_lqr(&T, nx, nu, Q, M, R, q, r, A, B, c, K, k, Pm, pv, dx, du, lam);
+    tree_free(&T);
+    return st;
+}
+
+/* ------------------------------------------------------------ AL quadratisation (Sec. IV-A) */
+typedef struct {
+    tree_t T;
+    int nc;
+    double *A, *B, *f;              /* per node (non-leaf): Jacobians and f(x_i, u_i) */
+    double *d;                      /* defect d_m = f_p(m) - x_m per node (row 0 zero) */
+    double *Q, *M, *R, *q, *r;      /* GN quadratisation of L_a */
+    double *g;                      /* constraint values [n][nc] */
+    int *ex;                        /* existence flags [n][nc] */
+    double *K, *k, *P, *p, *dx, *du, *lqp;
+    double La;                      /* L_a value at the linearisation point */
+} work_t;
+
+static void work_alloc(work_t *W, const orc_problem *P) {
+    int n = P->n, nx = P->nx, nu = P->nu, nc = n_con(P);
+    W->nc = nc;
+    W->A = (double *)calloc((size_t)n * nx * nx, sizeof(double));
+    W->B = (double *)calloc((size_t)n * nx * nu, sizeof(double));
+    W->f = (double *)calloc((size_t)n * nx, sizeof(double));
+    W->d = (double *)calloc((size_t)n * nx, sizeof(double));
+    W->Q = (double *)calloc((size_t)n * nx * nx, sizeof(double));
+    W->M = (double *)calloc((size_t)n * nu * nx, sizeof(double));
+    W->R = (double *)calloc((size_t)n * nu * nu, sizeof(double));
+    W->q = (double *)calloc((size_t)n * nx, sizeof(double));
+    W->r = (double *)calloc((size_t)n * nu, sizeof(double));
+    W->g = (double *)calloc((size_t)n * (nc ? nc : 1), sizeof(double));
+    W->ex = (int *)calloc((size_t)n * (nc ? nc : 1), sizeof(int));
+    W->K = (double *)calloc((size_t)n * nu * nx, sizeof(double));
+    W->k = (double *)calloc((size_t)n * nu, sizeof(double));
+    W->P = (double *)calloc((size_t)n * nx * nx, sizeof(double));
+    W->p = (double *)calloc((size_t)n * nx, sizeof(double));
+    W->dx = (double *)calloc((size_t)n * nx, sizeof(double));
+    W->du = (double *)calloc((size_t)n * nu, sizeof(double));
+    W->lqp = (double *)calloc((size_t)n * nx, sizeof(double));
+}
+static void work_free(work_t *W) {
+    free(W->A); free(W->B); free(W->f); free(W->d); free(W->Q); free(W->M); free(W->R);
+    free(W->q); free(W->r); free(W->g); free(W->ex); free(W->K); free(W->k); free(W->P);
+    free(W->p); free(W->dx); free(W->du); free(W->lqp);
+    tree_free(&W->T);
+}
+
+/* Node cost l_i (stage) or l_f,i (leaf) of Eq. (bmpc): weighted quadratic tracking. */
+static double node_cost(const orc_problem *P, int i, int leaf, const double *x, const double *u,
+                        double *lx, double *lu) {
+    int nx = P->nx, nu = P->nu;
+    double w = P->weight ? P->weight[i] : 1.0, v = 0.0;
+    const double *Qd = leaf ? P->QNw : P->Qw;
+    for (int j = 0; j < nx; ++j) {
+        double e = x[j] - P->xref[(size_t)i * nx + j];
+        v += 0.5 * w * Qd[j] * e * e;
+        if (lx) lx[j] = w * Qd[j] * e;
+    }
+    if (!leaf)
+        for (int j = 0; j < nu; ++j) {
+            v += 0.5 * w * P->Rw[j] * u[j] * u[j];
+            if (lu) lu[j] = w * P->Rw[j] * u[j];
+        }
+    return v;
+}
+
+/* Evaluate everything the iteration needs at (x, u): dynamics, defects, the GN
+ * quadratisation of L_a (Eq. AL) with fixed (y, rho), and L_a itself. */
+static void linearise(const orc_problem *P, work_t *W, const double *x, const double *u, const double *y,
+                      double rho) {
+    int n = P->n, nx = P->nx, nu = P->nu, nc = W->nc;
+    const tree_t *T = &W->T;
+    double La = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int leaf = T->n_child[i] == 0;
+        const double *xi = x + (size_t)i * nx, *ui = u + (size_t)i * nu;
+        if (!leaf) orc_dynamics(P, xi, ui, W->f + (size_t)i * nx, W->A + (size_t)i * nx * nx, W->B + (size_t)i * nx * nu);
+        double lx[MAXX] = {0}, lu[MAXU] = {0};
+        La += node_cost(P, i, leaf, xi, ui, lx, lu);
+        double *Qi = W->Q + (size_t)i * nx * nx, *Mi = W->M + (size_t)i * nu * nx, *Ri = W->R + (size_t)i * nu * nu;
+        double *qi = W->q + (size_t)i * nx, *ri = W->r + (size_t)i * nu;
+        double w = P->weight ? P->weight[i] : 1.0;
+        memset(Qi, 0, sizeof(double) * nx * nx);
+        memset(Mi, 0, sizeof(double) * nu * nx);
+        memset(Ri, 0, sizeof(double) * nu * nu);
+        for (int j = 0; j < nx; ++j) { Qi[j * nx + j] = w * (leaf ? P->QNw[j] : P->Qw[j]); qi[j] = lx[j]; }
+        for (int j = 0; j < nu; ++j) { Ri[j * nu + j] = leaf ? 0.0 : w * P->Rw[j]; ri[j] = leaf ? 0.0 : lu[j]; }
+        if (nc) {
+            double Jx[64 * MAXX], Ju[64 * MAXU];
+            double *gi = W->g + (size_t)i * nc;
+            int *ei = W->ex + (size_t)i * nc;
+            orc_constraints(P, i, leaf, xi, ui, gi, Jx, Ju, ei);
+            for (int c = 0; c < nc; ++c) {
+                if (!ei[c]) continue;
+                double s = y[(size_t)i * nc + c] + rho * gi[c];
+                if (s > 0.0) {
+                    double pen = s / rho;     /* max(0, g + y/rho) */
+                    La += 0.5 * rho * pen * pen;
+                    for (int a = 0; a < nx; ++a) qi[a] += s * Jx[c * nx + a];
+                    for (int a = 0; a < nu; ++a) ri[a] += s * Ju[c * nu + a];
+                    for (int a = 0; a < nx; ++a)
+                        for (int b = 0; b < nx; ++b) Qi[a * nx + b] += rho * Jx[c * nx + a] * Jx[c * nx + b];
+                    for (int a = 0; a < nu; ++a)
+                        for (int b = 0; b < nx; ++b) Mi[a * nx + b] += rho * Ju[c * nu + a] * Jx[c * nx + b];
+                    for (int a = 0; a < nu; ++a)
+                        for (int b = 0; b < nu; ++b) Ri[a * nu + b] += rho * Ju[c * nu + a] * Ju[c * nu + b];
+                }
+            }
+        }
+    }
+    memset(W->d, 0, sizeof(double) * nx);
+    for (int m = 1; m < n; ++m) {
+        int pnt = P->parent[m];
+        for (int j = 0; j < nx; ++j) W->d[(size_t)m * nx + j] = W->f[(size_t)pnt * nx + j] - x[(size_t)m * nx + j];
+    }
+    W->La = La;
+}
+
+/* KKT residual of the relaxed problem Eq. (relax_bmpc) at the linearisation point:
+ * max(|grad_{x,u} Lagrangian|_inf, |d|_inf); the root state row is left out (x_0 fixed). */
+static double kkt_relaxed(const orc_problem *P, const work_t *W, const double *lam) {
+    int n = P->n, nx = P->nx, nu = P->nu;
+    const tree_t *T = &W->T;
+    double r = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double lsum[MAXX] = {0};
+        for (int t = 0; t < T->n_child[i]; ++t) {
+            int m = T->child[T->first_child[i] + t];
+            for (int e = 0; e < nx; ++e) lsum[e] += lam[(size_t)m * nx + e];
+        }
+        if (i != 0) {
+            double Al[MAXX] = {0};
+            if (T->n_child[i]) matTvec(nx, nx, W->A + (size_t)i * nx * nx, lsum, Al);
+            for (int e = 0; e < nx; ++e) {
+                double gx = W->q[(size_t)i * nx + e] + Al[e] - lam[(size_t)i * nx + e];
+                if (fabs(gx) > r) r = fabs(gx);
+            }
+            for (int e = 0; e < nx; ++e) if (fabs(W->d[(size_t)i * nx + e]) > r) r = fabs(W->d[(size_t)i * nx + e]);
+        }
+        if (T->n_child[i]) {
+            double Bl[MAXU];
+            matTvec(nx, nu, W->B + (size_t)i * nx * nu, lsum, Bl);
+            for (int e = 0; e < nu; ++e) {
+                double gu = W->r[(size_t)i * nu + e] + Bl[e];
+                if (fabs(gu) > r) r = fabs(gu);
+            }
+        }
+    }
+    return r;
+}
+
+/* L_a + lambda'd + mu/2 |d|^2 at (x, u, lam): the merit of Eq. (merit) with J = L_a. */
+static double merit_at(const orc_problem *P, const tree_t *T, int nc, const double *x, const double *u,
+                       const double *lam, const double *y, double rho, double mu) {
+    int n = P->n, nx = P->nx, nu = P->nu;
+    double La = 0.0, ld = 0.0, dd = 0.0;
+    for (int i = 0; i < n; ++i) {
+        int leaf = T->n_child[i] == 0;
+        const double *xi = x + (size_t)i * nx, *ui = u + (size_t)i * nu;
+        La += node_cost(P, i, leaf, xi, ui, NULL, NULL);
+        if (nc) {
+            double g[64], Jx[64 * MAXX], Ju[64 * MAXU];
+            int ex[64];
+            orc_constraints(P, i, leaf, xi, ui, g, Jx, Ju, ex);
+            for (int c = 0; c < nc; ++c) {
+                if (!ex[c]) continue;
+                double pen = g[c] + y[(size_t)i * nc + c] / rho;
+                if (pen > 0.0) La += 0.5 * rho * pen * pen;
+            }
+        }
+        if (!leaf) {
+            double fx[MAXX];
+            orc_dynamics(P, xi, ui, fx, NULL, NULL);
+            for (int t = 0; t < T->n_child[i]; ++t) {
+                int m = T->child[T->first_child[i] + t];
+                for (int e = 0; e < nx; ++e) {
+                    double dm = fx[e] - x[(size_t)m * nx + e];
+                    ld += lam[(size_t)m * nx + e] * dm;
+                    dd += dm * dm;
+                }
+            }
+        }
+    }
+    return La + ld + 0.5 * mu * dd;
+}
+
+static int check_problem(const orc_problem *P) {
+    if (!P || P->n < 1 || P->nx < 1 || P->nx > MAXX || P->nu < 1 || P->nu > MAXU) return 0;
+    if (P->model < 0 || P->model > 2) return 0;
+    if (P->model == 0 && (P->nx != 4 || P->nu != 2)) return 0;
+    if (P->model == 1 && (P->nx != 6 || P->nu != 2)) return 0;
+    if (P->model != 2 && (P->nx < 2)) return 0;
+    if (n_con(P) > 64) return 0;
+    return 1;
+}
+
+/* Cold start of Sec. V-B: states linearly interpolated between x0 and the final reference
+ * state of the node's first leaf descendant, u = 0, lambda = 0, y = 0. */
+void orc_cold_start(const orc_problem *P, double *x, double *u, double *lam, double *y) {
+    tree_t T;
+    int n = P->n, nx = P->nx, nu = P->nu, nc = n_con(P);
+    tree_build(P, &T);
+    for (int i = 0; i < n; ++i) {
+        int leaf = i;
+        while (T.n_child[leaf]) leaf = T.child[T.first_child[leaf]];
+        double s = T.stage[leaf] > 0 ? (double)T.stage[i] / T.stage[leaf] : 0.0;
+        for (int j = 0; j < nx; ++j)
+            x[(size_t)i * nx + j] = P->x0[j] + s * (P->xref[(size_t)leaf * nx + j] - P->x0[j]);
+    }
+    memset(u, 0, sizeof(double) * n * nu);
+    memset(lam, 0, sizeof(double) * n * nx);
+    if (nc) memset(y, 0, sizeof(double) * n * nc);
+    tree_free(&T);
+}
+
+void orc_default_opts(orc_opts *o) {
+    o->max_iters = 100;
+    o->max_outer = 60;
+    o->n_alpha = 10;
+    o->eps_tol = 1e-5;
+    o->tau = 100.0;
+    o->omega0 = 1.0;
+    o->eta0 = 0.1;
+    o->a_omega = 1.0;
+    o->b_omega = 1.0;
+    o->a_eta = 0.1;
+    o->b_eta = 0.9;
+    o->rho0 = 10.0;
+    o->rho_max = 1e6;
+    o->mu0 = 1.0;
+    o->beta = 1e-4;
+    o->ls_rel_eps = 1e-6;
+}
+
+/* Directional data of one inner iteration at (x, u, lam) for fixed (y, rho, mu), with W
+ * already linearised at (x, u): solves the tree LQR, and returns dx, du, dlam = lam_QP - lam,
+ * phi(0), phi'(0) of the merit along (dx, du, dlam), dz'W dz and |d|^2. */
+static int direction(const orc_problem *P, work_t *W, const double *x, const double *u, const double *lam,
+                     const double *y, double rho, double mu, double *dlam, double out[6]) {
+    int n = P->n, nx = P->nx, nu = P->nu;
+    int st = tree_lqr(&W->T, nx, nu, W->Q, W->M, W->R, W->q, W->r, W->A, W->B, W->d, W->K, W->k, W->P, W->p,
+                      W->dx, W->du, W->lqp);
+    if (st) return st;
+    double gd = 0.0, wq = 0.0, ld = 0.0, dd = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double *dxi = W->dx + (size_t)i * nx, *dui = W->du + (size_t)i * nu;
+        double Qd[MAXX], Md[MAXU], Rd[MAXU];
+        matvec(nx, nx, W->Q + (size_t)i * nx * nx, dxi, Qd);
+        matvec(nu, nx, W->M + (size_t)i * nu * nx, dxi, Md);
+        matvec(nu, nu, W->R + (size_t)i * nu * nu, dui, Rd);
+        for (int e = 0; e < nx; ++e) { gd += W->q[(size_t)i * nx + e] * dxi[e]; wq += dxi[e] * Qd[e]; }
+        for (int e = 0; e < nu; ++e) { gd += W->r[(size_t)i * nu + e] * dui[e]; wq += dui[e] * (2.0 * Md[e] + Rd[e]); }
+        for (int e = 0; e < nx; ++e) {
+            double dl = (i == 0) ? 0.0 : W->lqp[(size_t)i * nx + e] - lam[(size_t)i * nx + e];
+            dlam[(size_t)i * nx + e] = dl;
+            if (i) {
+                double de = W->d[(size_t)i * nx + e];
+                ld += (dl - lam[(size_t)i * nx + e]) * de;
+                dd += de * de;
+            }
+        }
+    }
+    double phi0 = merit_at(P, &W->T, W->nc, x, u, lam, y, rho, mu);
+    out[0] = phi0;
+    out[1] = gd + ld - mu * dd;    /* phi'(0; mu) */
+    out[2] = wq;
+    out[3] = dd;
+    out[4] = gd + ld;              /* phi'(0; 0) */
+    out[5] = W->La;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------ the AL method (Algorithm 1) */
+int orc_solve(const orc_problem *P, const orc_opts *O_in, const double *wx, const double *wu, const double *wlam,
+              const double *wy, double *x, double *u, double *lam, double *y, orc_stats *S) {
+    if (!check_problem(P)) return ORC_ERR_INVALID;
+    orc_opts O;
+    if (O_in) O = *O_in; else orc_default_opts(&O);
+    int n = P->n, nx = P->nx, nu = P->nu;
+    work_t W;
+    if (!tree_build(P, &W.T)) { tree_free(&W.T); return ORC_ERR_INVALID; }
+    work_alloc(&W, P);
+    int nc = W.nc;
+    if (wx) {
+        memcpy(x, wx, sizeof(double) * n * nx);
+        memcpy(u, wu, sizeof(double) * n * nu);
+        memcpy(lam, wlam, sizeof(double) * n * nx);
+        if (nc) memcpy(y, wy, sizeof(double) * n * nc);
+    } else {
+        orc_cold_start(P, x, u, lam, y);
+    }
+    memcpy(x, P->x0, sizeof(double) * nx);                        /* x_0 = x-bar */
+    for (int i = 0; i < n; ++i)
+        if (W.T.n_child[i] == 0) memset(u + (size_t)i * nu, 0, sizeof(double) * nu);
+    memset(lam, 0, sizeof(double) * nx);
+
+    double rho = O.rho0, mu = O.mu0, omega = O.omega0, eta = O.eta0;
+    double r_kkt = INFINITY, cviol = INFINITY;
+    int inner = 0, outer = 0, ls_fail = 0, ls_fail_total = 0, status = ORC_MAX_ITER;
+    double *dlam = (double *)calloc((size_t)n * nx, sizeof(double));
+    double *xt = (double *)calloc((size_t)n * nx, sizeof(double));
+    double *ut = (double *)calloc((size_t)n * nu, sizeof(double));
+    double *lt = (double *)calloc((size_t)n * nx, sizeof(double));
+
+    while (outer < O.max_outer) {
+        ++outer;
+        /* inner loop: iLQR steps on the relaxed problem until r_kkt <= omega */
+        for (;;) {
+            linearise(P, &W, x, u, y, rho);
+            r_kkt = kkt_relaxed(P, &W, lam);
+            if (r_kkt <= omega) break;
+            if (inner >= O.max_iters) goto done;
+            double info[6];
+            int st = direction(P, &W, x, u, lam, y, rho, mu, dlam, info);
+            if (st) { status = st; goto done; }
+            double wq = info[2], dd = info[3], dphi0 = info[4];
+            /* adaptive merit penalty (Gill et al. 1992 reading) */
+            if (dd > 0.0 && dphi0 - mu * dd > -0.5 * wq) {
+                double need = 2.0 * (dphi0 + 0.5 * wq) / dd;
+                if (need > mu) mu = need;
+            }
+            double phi0 = merit_at(P, &W.T, nc, x, u, lam, y, rho, mu);
+            double dphi = dphi0 - mu * dd;
+            /* all step sizes alpha_i = 2^-i, take the largest satisfying Eq. (sufficient_decrease) */
+            double alpha = ldexp(1.0, -(O.n_alpha - 1));
+            int accepted = 0;
+            for (int a = 0; a < O.n_alpha; ++a) {
+                double al = ldexp(1.0, -a);
+                for (int e = 0; e < n * nx; ++e) { xt[e] = x[e] + al * W.dx[e]; lt[e] = lam[e] + al * dlam[e]; }
+                for (int e = 0; e < n * nu; ++e) ut[e] = u[e] + al * W.du[e];
+                double phi = merit_at(P, &W.T, nc, xt, ut, lt, y, rho, mu);
+                if (phi <= phi0 + O.beta * al * dphi + O.ls_rel_eps * fabs(phi0)) { alpha = al; accepted = 1; break; }
+            }
+            if (accepted) ls_fail = 0; else { ++ls_fail; ++ls_fail_total; }
+            for (int e = 0; e < n * nx; ++e) { x[e] += alpha * W.dx[e]; lam[e] += alpha * dlam[e]; }
+            for (int e = 0; e < n * nu; ++e) u[e] += alpha * W.du[e];
+            ++inner;
+            if (ls_fail >= 3) { status = ORC_LS_FAIL; goto done; }
+        }
+        /* outer loop: BCL update of (y, rho) and the tolerance schedules */
+        cviol = 0.0;
+        for (int e = 0; e < n * nc; ++e) {
+            if (!W.ex[e]) continue;
+            double v = W.g[e] > -y[e] / rho ? W.g[e] : -y[e] / rho;
+            if (fabs(v) > cviol) cviol = fabs(v);
+        }
+        if (cviol <= eta) {
+            for (int e = 0; e < n * nc; ++e) {
+                if (!W.ex[e]) continue;
+                double v = y[e] + rho * W.g[e];
+                y[e] = v > 0.0 ? v : 0.0;
+            }
+            if ((r_kkt > cviol ? r_kkt : cviol) < O.eps_tol) { status = ORC_OK; goto done; }
+            omega = omega * pow(rho, -O.b_omega);
+            eta = eta * pow(rho, -O.b_eta);
+        } else {
+            rho = O.tau * rho;
+            if (rho > O.rho_max) rho = O.rho_max;
+            omega = O.omega0 * pow(rho, -O.a_omega);
+            eta = O.eta0 * pow(rho, -O.a_eta);
+        }
+        if (omega < O.eps_tol) omega = O.eps_tol;
+        if (eta < O.eps_tol) eta = O.eps_tol;
+    }
+done:
+    if (S) {
+        S->status = status;
+        S->inner_iters = inner;
+        S->outer_iters = outer;
+        S->ls_fail_total = ls_fail_total;
+        S->r_kkt = r_kkt;
+        S->c = cviol;
+        S->rho = rho;
+        S->mu = mu;
+        S->omega = omega;
+        S->eta = eta;
+    }
+    free(dlam); free(xt); free(ut); free(lt);
+    work_free(&W);
+    return status;
+}
+
+/* ------------------------------------------------------------ evaluation entry points for tests */
+
+/* KKT conditions of the original problem Eq. (bmpc) at (x, u, lam, y):
+ * out[0] = |grad_{x,u} (sum l + y'g + lam'd)|_inf (root state row left out),
+ * out[1] = |d|_inf, out[2] = |max(g, 0)|_inf, out[3] = |min(-g, y)|_inf, out[4] = |min(y, 0)|_inf. */
+int orc_kkt(const orc_problem *P, const double *x, const double *u, const double *lam, const double *y,
+            double *out) {
+    if (!check_problem(P)) return ORC_ERR_INVALID;
+    work_t W;
+    if (!tree_build(P, &W.T)) { tree_free(&W.T); return ORC_ERR_INVALID; }
+    work_alloc(&W, P);
+    int n = P->n, nx = P->nx, nu = P->nu, nc = W.nc;
+    /* y enters the stationarity directly: linearise with rho -> 0 penalty replaced by y'g */
+    double *zero = (double *)calloc((size_t)n * (nc ? nc : 1), sizeof(double));
+    linearise(P, &W, x, u, zero, 1.0);
+    /* remove the PHR contribution (y = 0, rho = 1 activates g > 0 rows) and add y'g instead */
+    for (int i = 0; i < n; ++i) {
+        int leaf = W.T.n_child[i] == 0;
+        double lx[MAXX] = {0}, lu[MAXU] = {0};
+        node_cost(P, i, leaf, x + (size_t)i * nx, u + (size_t)i * nu, lx, lu);
+        for (int e = 0; e < nx; ++e) W.q[(size_t)i * nx + e] = lx[e];
+        for (int e = 0; e < nu; ++e) W.r[(size_t)i * nu + e] = leaf ? 0.0 : lu[e];
+        if (nc) {
+            double g[64], Jx[64 * MAXX], Ju[64 * MAXU];
+            int ex[64];
+            orc_constraints(P, i, leaf, x + (size_t)i * nx, u + (size_t)i * nu, g, Jx, Ju, ex);
+            for (int c = 0; c < nc; ++c) {
+                if (!ex[c]) continue;
+                double yc = y[(size_t)i * nc + c];
+                for (int a = 0; a < nx; ++a) W.q[(size_t)i * nx + a] += yc * Jx[c * nx + a];
+                for (int a = 0; a < nu; ++a) W.r[(size_t)i * nu + a] += yc * Ju[c * nu + a];
+            }
+        }
+    }
+    double stat = 0.0, dmax = 0.0, inf = 0.0, comp = 0.0, neg = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double lsum[MAXX] = {0};
+        for (int t = 0; t < W.T.n_child[i]; ++t) {
+            int m = W.T.child[W.T.first_child[i] + t];
+            for (int e = 0; e < nx; ++e) lsum[e] += lam[(size_t)m * nx + e];
+        }
+        if (i) {
+            double Al[MAXX] = {0};
+            if (W.T.n_child[i]) matTvec(nx, nx, W.A + (size_t)i * nx * nx, lsum, Al);
+            for (int e = 0; e < nx; ++e) {
+                double gx = W.q[(size_t)i * nx + e] + Al[e] - lam[(size_t)i * nx + e];
+                if (fabs(gx) > stat) stat = fabs(gx);
+                if (fabs(W.d[(size_t)i * nx + e]) > dmax) dmax = fabs(W.d[(size_t)i * nx + e]);
+            }
+        }
+        if (W.T.n_child[i]) {
+            double Bl[MAXU];
+            matTvec(nx, nu, W.B + (size_t)i * nx * nu, lsum, Bl);
+            for (int e = 0; e < nu; ++e) {
+                double gu = W.r[(size_t)i * nu + e] + Bl[e];
+                if (fabs(gu) > stat) stat = fabs(gu);
+            }
+        }
+        for (int c = 0; c < nc; ++c) {
+            if (!W.ex[(size_t)i * nc + c]) continue;
+            double g = W.g[(size_t)i * nc + c], yc = y[(size_t)i * nc + c];
+            if (g > inf) inf = g;
+            double cm = fabs(-g < yc ? -g : yc);
+            if (cm > comp) comp = cm;
+            if (-yc > neg) neg = -yc;
+        }
+    }
+    out[0] = stat; out[1] = dmax; out[2] = inf; out[3] = comp; out[4] = neg;
+    free(zero);
+    work_free(&W);
+    return ORC_OK;
+}
+
+/* Merit phi = L_a + lam'd + mu/2 |d|^2 at a given point (Eq. merit with J = L_a). */
+double orc_merit(const orc_problem *P, const double *x, const double *u, const double *lam, const double *y,
+                 double rho, double mu) {
+    tree_t T;
+    if (!check_problem(P) || !tree_build(P, &T)) return NAN;
+    double v = merit_at(P, &T, n_con(P), x, u, lam, y, rho, mu);
+    tree_free(&T);
+    return v;
+}
+
+/* One search direction at a given point (for tests): dx, du, dlam and
+ * info = [phi(0), phi'(0; mu), dz'W dz, |d|^2, phi'(0; 0), L_a]. */
+int orc_direction(const orc_problem *P, const double *x, const double *u, const double *lam, const double *y,
+                  double rho, double mu, double *dx, double *du, double *dlam, double *info) {
+    if (!check_problem(P)) return ORC_ERR_INVALID;
+    work_t W;
+    if (!tree_build(P, &W.T)) { tree_free(&W.T); return ORC_ERR_INVALID; }
+    work_alloc(&W, P);
+    linearise(P, &W, x, u, y, rho);
+    int st = direction(P, &W, x, u, lam, y, rho, mu, dlam, info);
+    memcpy(dx, W.dx, sizeof(double) * P->n * P->nx);
+    memcpy(du, W.du, sizeof(double) * P->n * P->nu);
+    work_free(&W);
+    return st;
+}
+
+/* KKT residual of the relaxed problem (Sec. IV-A) at (x, u, lam) for (y, rho). */
+double orc_kkt_relaxed(const orc_problem *P, const double *x, const double *u, const double *lam,
+                       const double *y, double rho) {
+    if (!check_problem(P)) return NAN;
+    work_t W;
+    if (!tree_build(P, &W.T)) { tree_free(&W.T); return NAN; }
+    work_alloc(&W, P);
+    linearise(P, &W, x, u, y, rho);
+    double r = kkt_relaxed(P, &W, lam);
+    work_free(&W);
+    return r;
+}
+
+/* L_a (Eq. AL) at (x, u) for (y, rho). */
+double orc_aug_lagrangian(const orc_problem *P, const double *x, const double *u, const double *y, double rho) {
+    if (!check_problem(P)) return NAN;
+    work_t W;
+    if (!tree_build(P, &W.T)) { tree_free(&W.T); return NAN; }
+    work_alloc(&W, P);
+    linearise(P, &W, x, u, y, rho);
+    double v = W.La;
+    work_free(&W);
+    return v;
+}

@@ -1,0 +1,316 @@
+"""Seeded synthetic driving scenes for branch MPC (scenario-tree) problems.
+
+This module only *generates inputs*: scenario trees, initial states, reference
+trajectories, per-node obstacle predictions and model constants.  It contains
+none of the solver's arithmetic (no dynamics integration of the ego vehicle,
+no costs, no constraints) and is the one module shared by the FP64 oracle and
+the CUDA path.
+
+Every floating-point value is rounded to the nearest float32, so the FP64
+oracle and the FP32 GPU path receive bit-identical problem data.
+
+Problem layout (all arrays are numpy):
+  parent  int32  [n]            parent[0] = -1, parent[i] < i, level order
+                                (nodes sorted by stage, children of a node
+                                contiguous and in parent order)
+  stage   int32  [n]            stage of each node (root stage 0)
+  x0      f64    [nx]           measured state x-bar (the root state is fixed)
+  xref    f64    [n, nx]        tracking reference per node
+  weight  f64    [n]            node cost weight (branch probability)
+  Qw, QNw f64    [nx]           diagonal stage / final state weights
+  Rw      f64    [nu]           diagonal input weights
+  u_lo, u_hi f64 [nu]           input box
+  box_on, lane_on int           which constraint families exist
+  lane_lo, lane_hi float        lateral lane bounds on the Y coordinate
+  obs     f64    [n, n_obs, 5]  obstacle ellipse per node: cx, cy, heading, a, b
+  params  f64    [10]           model constants (see MODEL_PARAMS_*)
+  Alin, Blin                    discrete dynamics for the linear model (model 2)
+
+The tree sizes follow the convention "a branch at stage s with factor b gives
+every stage-(s-1) node b children at stage s"; leaves are at stage N.  Scene
+recipes stand in for the intersection / overtaking planning problems of the
+paper's Sec. II-B (Fig. 1a) and Sec. V-B; no dataset is used.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+MODEL_KINEMATIC = 0
+MODEL_DYNAMIC = 1
+MODEL_LINEAR = 2
+
+# params layout: [L, m, Iz, lf, lr, Cf, Cr, vmin, veps, n_sub]
+MODEL_PARAMS_KINEMATIC = (2.7, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+MODEL_PARAMS_DYNAMIC = (2.7, 1500.0, 2250.0, 1.2, 1.5, 8.0e4, 8.0e4, 2.0, 0.1, 4.0)
+MODEL_PARAMS_LINEAR = (0.0,) * 9 + (1.0,)
+
+V_REF = 8.0          # lane cruising speed [m/s]
+REF_ACCEL = 1.0      # speed ramp of the reference profile [m/s^2]
+ELLIPSE_A = 3.0      # keep-out semi-axis along the obstacle heading [m]
+ELLIPSE_B = 1.5      # keep-out semi-axis across the obstacle heading [m]
+LANE = (-5.25, 5.25)
+
+
+def f32(a):
+    """Round to the nearest float32 and return float64 (exactly representable)."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def tree_parents(N: int, splits: dict[int, int]):
+    """Level-ordered scenario tree: root at stage 0, leaves at stage N.
+
+    ``splits`` maps a stage s to the factor b: every stage-(s-1) node gets b
+    children at stage s; every other stage has fan-out 1.
+    """
+    parent = [-1]
+    stage = [0]
+    frontier = [0]
+    for k in range(1, N + 1):
+        b = int(splits.get(k, 1))
+        nxt = []
+        for p in frontier:
+            for _ in range(b):
+                parent.append(p)
+                stage.append(k)
+                nxt.append(len(parent) - 1)
+        frontier = nxt
+    return np.asarray(parent, np.int32), np.asarray(stage, np.int32)
+
+
+def branch_weights(parent: np.ndarray) -> np.ndarray:
+    """Uniform branch probabilities: a child of a b-way split gets 1/b of its parent."""
+    n = parent.shape[0]
+    nch = np.zeros(n, np.int64)
+    for i in range(1, n):
+        nch[parent[i]] += 1
+    w = np.ones(n)
+    for i in range(1, n):
+        w[i] = w[parent[i]] / nch[parent[i]]
+    return w
+
+
+def _reference(x0, stage, nx, dt, y_line=0.0):
+    """Straight reference line Y = y_line, heading 0, speed ramping to V_REF."""
+    N = int(stage.max())
+    v0 = float(x0[3])
+    v = np.array([v0 + np.clip(V_REF - v0, -REF_ACCEL * k * dt, REF_ACCEL * k * dt)
+                  for k in range(N + 1)])
+    X = np.empty(N + 1)
+    X[0] = x0[0]
+    for k in range(N):
+        X[k + 1] = X[k] + 0.5 * (v[k] + v[k + 1]) * dt
+    ref_stage = np.zeros((N + 1, nx))
+    ref_stage[:, 0] = X
+    ref_stage[:, 1] = y_line
+    ref_stage[:, 3] = v
+    return ref_stage[stage]
+
+
+# ---------------------------------------------------------------- obstacles
+def _sample_mode(rng, family, side):
+    """Behaviour of one obstacle on one branch segment: (speed or None, yaw_rate, decel)."""
+    if family == "line":            # straight-line car, speed per branch U[0, 10]
+        return (rng.uniform(0.0, 10.0), 0.0, 0.0)
+    r = rng.uniform()
+    if family == "adjacent":        # car in a neighbouring lane: keep, brake, or drift in
+        if r < 0.4:
+            return (None, 0.0, 0.0)
+        if r < 0.7:
+            return (None, 0.0, 2.0)
+        return (None, -side * 0.05, 0.0)
+    if r < 0.4:                     # crossing car: go (constant velocity)
+        return (None, 0.0, 0.0)
+    if r < 0.75:                    # yield: decelerate to a stop at 2 m/s^2
+        return (None, 0.0, 2.0)
+    return (None, rng.choice([-0.2, 0.2]), 0.0)   # turning branch
+
+
+def _obstacle_tree(rng, parent, stage, dt, init_states, families):
+    """Propagate each obstacle along the tree; branches resample the behaviour."""
+    if isinstance(families, str):
+        families = [families] * len(init_states)
+    n = parent.shape[0]
+    n_obs = len(init_states)
+    nch = np.zeros(n, np.int64)
+    for i in range(1, n):
+        nch[parent[i]] += 1
+    # state per node per obstacle: cx, cy, heading, speed, yaw_rate, decel
+    st = np.zeros((n, n_obs, 6))
+    for j, s0 in enumerate(init_states):
+        st[0, j] = s0
+    for i in range(1, n):
+        p = parent[i]
+        for j in range(n_obs):
+            cx, cy, hd, sp, yr, dc = st[p, j]
+            if nch[p] > 1:
+                m_sp, m_yr, m_dc = _sample_mode(rng, families[j], np.sign(st[0, j, 1]) or 1.0)
+                if m_sp is not None:
+                    sp = m_sp
+                yr, dc = m_yr, m_dc
+            sp_new = max(0.0, sp - dc * dt)
+            hd_new = hd + yr * dt
+            vmean = 0.5 * (sp + sp_new)
+            cx += vmean * math.cos(hd_new) * dt
+            cy += vmean * math.sin(hd_new) * dt
+            st[i, j] = (cx, cy, hd_new, sp_new, yr, dc)
+    obs = np.zeros((n, n_obs, 5))
+    obs[:, :, 0:3] = st[:, :, 0:3]
+    obs[:, :, 3] = ELLIPSE_A
+    obs[:, :, 4] = ELLIPSE_B
+    return obs
+
+
+def _inside_any(obs_root, X, Y):
+    for cx, cy, hd, a, b in obs_root:
+        dx, dy = X - cx, Y - cy
+        dpar = math.cos(hd) * dx + math.sin(hd) * dy
+        dper = -math.sin(hd) * dx + math.cos(hd) * dy
+        if (dpar / a) ** 2 + (dper / b) ** 2 < 1.5:
+            return True
+    return False
+
+
+# ---------------------------------------------------------------- problems
+def _base(model, N, splits, dt=0.1):
+    parent, stage = tree_parents(N, splits)
+    if model == MODEL_KINEMATIC:
+        nx, params = 4, MODEL_PARAMS_KINEMATIC
+        Qw, Rw = [1.0, 1.0, 0.1, 0.5], [0.1, 1.0]
+    elif model == MODEL_DYNAMIC:
+        nx, params = 6, MODEL_PARAMS_DYNAMIC
+        Qw, Rw = [1.0, 1.0, 0.1, 0.5, 0.1, 0.1], [0.1, 1.0]
+    else:
+        raise ValueError(model)
+    return dict(model=model, nx=nx, nu=2, dt=dt, parent=parent, stage=stage,
+                params=np.array(params, np.float64), Qw=np.array(Qw), QNw=np.array(Qw),
+                Rw=np.array(Rw), u_lo=np.array([-3.0, -0.5]), u_hi=np.array([3.0, 0.5]),
+                box_on=1, weight=branch_weights(parent))
+
+
+def _finish(p):
+    """Round every float array to float32 and fill derived entries."""
+    for k in ("x0", "xref", "weight", "Qw", "QNw", "Rw", "u_lo", "u_hi", "obs", "params"):
+        p[k] = f32(p[k])
+    p["lane_lo"] = float(np.float32(p.get("lane_lo", LANE[0])))
+    p["lane_hi"] = float(np.float32(p.get("lane_hi", LANE[1])))
+    p["dt"] = float(np.float32(p["dt"]))
+    p["n"] = int(p["parent"].shape[0])
+    p["n_obs"] = int(p["obs"].shape[1])
+    p.setdefault("Alin", np.zeros((p["nx"], p["nx"])))
+    p.setdefault("Blin", np.zeros((p["nx"], p["nu"])))
+    return p
+
+
+def _x0(rng, model, box_y, heading, vrange):
+    X = rng.uniform(-10.0, 10.0)
+    Y = rng.uniform(-box_y, box_y)
+    psi = rng.uniform(-heading, heading)
+    v = rng.uniform(*vrange)
+    return np.array([X, Y, psi, v] + ([0.0, 0.0] if model == MODEL_DYNAMIC else []))
+
+
+def _crossing_obstacle(rng, X0, dist=(30.0, 50.0)):
+    """Car approaching an intersection dist[0]-dist[1] m ahead from either side."""
+    side = rng.choice([-1.0, 1.0])
+    return (X0 + rng.uniform(*dist), side * rng.uniform(10.0, 18.0),
+            -side * math.pi / 2, rng.uniform(3.0, 8.0), 0.0, 0.0)
+
+
+def _adjacent_obstacle(rng, X0):
+    """Car in a neighbouring lane (centre +-3.5 m), 5-30 m ahead."""
+    side = rng.choice([-1.0, 1.0])
+    return (X0 + rng.uniform(5.0, 30.0), side * 3.5, 0.0, rng.uniform(4.0, 9.0), 0.0, 0.0)
+
+
+def config1(seed: int):
+    """Kinematic bicycle, N = 20, root splits into 3; one obstacle car driving ahead on the
+    ego's line (offset by up to 1 m), with a different speed U[0, 10] on each branch."""
+    rng = np.random.default_rng([1, seed])
+    p = _base(MODEL_KINEMATIC, 20, {1: 3})
+    x0 = _x0(rng, MODEL_KINEMATIC, 10.0, math.pi / 6, (0.0, 10.0))
+    p["x0"] = f32(x0)
+    p["xref"] = _reference(p["x0"], p["stage"], p["nx"], p["dt"], y_line=float(p["x0"][1]))
+    init = [(x0[0] + rng.uniform(15.0, 30.0), x0[1] + rng.uniform(-1.0, 1.0), 0.0, 0.0, 0.0, 0.0)]
+    p["obs"] = _obstacle_tree(rng, p["parent"], p["stage"], p["dt"], init, "line")
+    p["lane_on"] = 0
+    return _finish(p)
+
+
+def _multi_obstacle(rng, p, n_obs, n_cross, cross_dist=(30.0, 50.0)):
+    x0 = p["x0"]
+    init, fam = [], []
+    for j in range(n_obs):
+        if j < n_cross:
+            init.append(_crossing_obstacle(rng, x0[0], cross_dist))
+            fam.append("crossing")
+        else:
+            init.append(_adjacent_obstacle(rng, x0[0]))
+            fam.append("adjacent")
+    p["obs"] = _obstacle_tree(rng, p["parent"], p["stage"], p["dt"], init, fam)
+    p["lane_on"] = 1
+    return p
+
+
+def config2(seed: int):
+    """Kinematic bicycle, N = 40, binary splits at 1, 5, 10, 15, 20; 3 crossing cars."""
+    rng = np.random.default_rng([2, seed])
+    p = _base(MODEL_KINEMATIC, 40, {1: 2, 5: 2, 10: 2, 15: 2, 20: 2})
+    p["x0"] = f32(_x0(rng, MODEL_KINEMATIC, 1.5, math.pi / 12, (0.0, 10.0)))
+    p["xref"] = _reference(p["x0"], p["stage"], p["nx"], p["dt"])
+    return _finish(_multi_obstacle(rng, p, 3, 3))
+
+
+def config3(seed: int):
+    """Dynamic bicycle, N = 60, factor 4 at 1, 10, 20; 5 obstacles."""
+    rng = np.random.default_rng([3, seed])
+    p = _base(MODEL_DYNAMIC, 60, {1: 4, 10: 4, 20: 4})
+    p["x0"] = f32(_x0(rng, MODEL_DYNAMIC, 1.5, math.pi / 12, (2.0, 10.0)))
+    p["xref"] = _reference(p["x0"], p["stage"], p["nx"], p["dt"])
+    return _finish(_multi_obstacle(rng, p, 5, 2, cross_dist=(45.0, 70.0)))
+
+
+def config4_problem(seed: int, index: int):
+    """One problem of the mixed batch: S in {2..64}, N in [20, 60], 1-5 obstacles."""
+    rng = np.random.default_rng([4, seed, index])
+    S = int(rng.choice([2, 4, 8, 16, 32, 64]))
+    N = int(rng.integers(20, 61))
+    n_obs = int(rng.integers(1, 6))
+    model = MODEL_KINEMATIC if rng.uniform() < 0.5 else MODEL_DYNAMIC
+    levels = int(round(math.log2(S)))
+    gap = max(1, N // (2 * levels))
+    splits = {1 + j * gap: 2 for j in range(levels)}
+    p = _base(model, N, splits)
+    vr = (0.0, 10.0) if model == MODEL_KINEMATIC else (2.0, 10.0)
+    p["x0"] = f32(_x0(rng, model, 1.5, math.pi / 12, vr))
+    p["xref"] = _reference(p["x0"], p["stage"], p["nx"], p["dt"])
+    return _finish(_multi_obstacle(rng, p, n_obs, min(n_obs, 2)))
+
+
+def config4(seed: int = 4, count: int = 4096):
+    return [config4_problem(seed, i) for i in range(count)]
+
+
+def linear_problem(seed: int, N: int = 10, splits=None, nx: int = 4, nu: int = 2,
+                   constrained: bool = False):
+    """Linear dynamics x+ = A x + B u with quadratic cost (the LQ special case)."""
+    rng = np.random.default_rng([7, seed])
+    parent, stage = tree_parents(N, splits or {})
+    n = parent.shape[0]
+    A = np.eye(nx) + 0.1 * rng.standard_normal((nx, nx))
+    B = 0.1 * rng.standard_normal((nx, nu)) + 0.1 * np.eye(nx, nu)
+    p = dict(model=MODEL_LINEAR, nx=nx, nu=nu, dt=0.1, parent=parent, stage=stage,
+             params=np.array(MODEL_PARAMS_LINEAR), Qw=rng.uniform(0.5, 2.0, nx),
+             QNw=rng.uniform(0.5, 2.0, nx), Rw=rng.uniform(0.1, 1.0, nu),
+             u_lo=-np.ones(nu) * (0.5 if constrained else 1e3),
+             u_hi=np.ones(nu) * (0.5 if constrained else 1e3),
+             box_on=1 if constrained else 0, lane_on=0, weight=branch_weights(parent),
+             x0=rng.standard_normal(nx), xref=0.3 * rng.standard_normal((n, nx)),
+             obs=np.zeros((n, 0, 5)), Alin=f32(A), Blin=f32(B))
+    return _finish(p)
+
+
+def instances(config: int, count: int, seed0: int = 0):
+    """Seeded instances of a configuration (1-3), seeds seed0 .. seed0+count-1."""
+    gen = {1: config1, 2: config2, 3: config3}[config]
+    return [gen(seed0 + s) for s in range(count)]

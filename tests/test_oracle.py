@@ -1,0 +1,394 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed-form
+motion, a textbook steady-state gain, central finite differences, a dense KKT
+solve of the tree LQR QP (exactness of the recursion in Sec. III-A), the
+discrete algebraic Riccati equation (scipy), the one-step convergence of the
+Gauss-Newton/LQR step on a linear-quadratic problem, nonanticipativity and the
+value-function summation at branch points, and the KKT conditions of Eq. (bmpc)
+at the returned point.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+import scenes
+
+
+# ------------------------------------------------------------------ dynamics
+def test_kinematic_straight_line_closed_form():
+    """delta = 0, constant a: position is quadratic in time, RK4 is exact."""
+    p = scenes.config1(0)
+    x = np.array([1.0, -2.0, 0.3, 4.0])
+    a, dt = 1.5, p["dt"]
+    xn, _, _ = oracle.dynamics(p, x, np.array([a, 0.0]))
+    s = x[3] * dt + 0.5 * a * dt * dt
+    ref = np.array([x[0] + s * math.cos(x[2]), x[1] + s * math.sin(x[2]), x[2], x[3] + a * dt])
+    np.testing.assert_allclose(xn, ref, rtol=0, atol=1e-14)
+
+
+def test_kinematic_circle_closed_form():
+    """a = 0, constant steering: circular arc of radius L / tan(delta)."""
+    p = scenes.config1(0)
+    L, dt = p["params"][0], p["dt"]
+    x = np.array([0.0, 0.0, 0.2, 6.0])
+    d = 0.3
+    xn, _, _ = oracle.dynamics(p, x, np.array([0.0, d]))
+    w = x[3] * math.tan(d) / L
+    Rc = L / math.tan(d)
+    psi1 = x[2] + w * dt
+    ref = np.array([x[0] + Rc * (math.sin(psi1) - math.sin(x[2])),
+                    x[1] - Rc * (math.cos(psi1) - math.cos(x[2])), psi1, x[3]])
+    # classical RK4 local error is O((w dt)^5) * Rc
+    np.testing.assert_allclose(xn, ref, rtol=0, atol=1e-8)
+
+
+def test_dynamic_straight_line_closed_form():
+    p = scenes.config3(0)
+    x = np.array([3.0, 1.0, -0.4, 7.0, 0.0, 0.0])
+    a, dt = -2.0, p["dt"]
+    xn, _, _ = oracle.dynamics(p, x, np.array([a, 0.0]))
+    s = x[3] * dt + 0.5 * a * dt * dt
+    ref = np.array([x[0] + s * math.cos(x[2]), x[1] + s * math.sin(x[2]), x[2], x[3] + a * dt, 0.0, 0.0])
+    np.testing.assert_allclose(xn, ref, rtol=0, atol=1e-13)
+
+
+def test_dynamic_bicycle_steady_state_yaw_gain():
+    """Linear single-track model: r_ss = u delta / (L + K u^2), K = m (lr Cr - lf Cf) / (L Cf Cr)."""
+    p = scenes.config3(0)
+    L_, m, Iz, lf, lr, Cf, Cr = p["params"][:7]
+    u0, d = 8.0, 0.004
+    x = np.array([0.0, 0.0, 0.0, u0, 0.0, 0.0])
+    for _ in range(60):
+        x, _, _ = oracle.dynamics(p, x, np.array([0.0, d]))
+    L = lf + lr
+    K = m * (lr * Cr - lf * Cf) / (L * Cf * Cr)
+    r_ss = x[3] * d / (L + K * x[3] ** 2)
+    assert abs(x[5] - r_ss) < 2e-3 * abs(r_ss)
+
+
+@pytest.mark.parametrize("cfg", [1, 3])
+def test_jacobians_central_differences(cfg):
+    p = scenes.instances(cfg, 1)[0]
+    rng = np.random.default_rng(cfg)
+    nx = p["nx"]
+    for _ in range(5):
+        x = p["x0"] + 0.5 * rng.standard_normal(nx)
+        u = 0.3 * rng.standard_normal(2)
+        _, A, B = oracle.dynamics(p, x, u)
+        h = 1e-6
+        Afd = np.stack([(oracle.dynamics(p, x + h * e, u)[0] - oracle.dynamics(p, x - h * e, u)[0]) / (2 * h)
+                        for e in np.eye(nx)], 1)
+        Bfd = np.stack([(oracle.dynamics(p, x, u + h * e)[0] - oracle.dynamics(p, x, u - h * e)[0]) / (2 * h)
+                        for e in np.eye(2)], 1)
+        np.testing.assert_allclose(A, Afd, rtol=0, atol=1e-6 * max(1.0, np.abs(A).max()))
+        np.testing.assert_allclose(B, Bfd, rtol=0, atol=1e-6 * max(1.0, np.abs(B).max()))
+
+
+# ------------------------------------------------------------------ constraints
+def test_ellipse_constraint_boundary_and_jacobian():
+    p = scenes.config2(0)
+    i = 5
+    cx, cy, hd, a, b = p["obs"][i, 0]
+    rows = 4
+    for t in np.linspace(0, 2 * math.pi, 7):
+        X = cx + a * math.cos(t) * math.cos(hd) - b * math.sin(t) * math.sin(hd)
+        Y = cy + a * math.cos(t) * math.sin(hd) + b * math.sin(t) * math.cos(hd)
+        g, Jx, Ju, ex = oracle.constraints(p, i, False, np.array([X, Y, 0, 0]), np.zeros(2))
+        assert abs(g[rows]) < 1e-6          # on the ellipse: normalised distance 1
+        x = np.array([X + 0.3, Y - 0.2, 0.0, 0.0])
+        g0, Jx0, _, _ = oracle.constraints(p, i, False, x, np.zeros(2))
+        h = 1e-6
+        fd = [(oracle.constraints(p, i, False, x + h * e, np.zeros(2))[0][rows]
+               - oracle.constraints(p, i, False, x - h * e, np.zeros(2))[0][rows]) / (2 * h) for e in np.eye(4)]
+        np.testing.assert_allclose(Jx0[rows], fd, atol=1e-7)
+    g, _, _, ex = oracle.constraints(p, i, False, np.array([cx, cy, 0, 0]), np.zeros(2))
+    assert abs(g[rows] - 1.0) < 2e-3 and ex[rows]
+    g, _, _, ex = oracle.constraints(p, 0, False, np.array([cx, cy, 0, 0]), np.array([5.0, 0.0]))
+    assert not ex[rows] and ex[0] and abs(g[0] - 2.0) < 1e-12      # root: no state rows, box exists
+    g, _, _, ex = oracle.constraints(p, p["n"] - 1, True, np.array([cx, cy, 0, 0]), np.zeros(2))
+    assert not ex[:4].any() and ex[rows]                              # leaf: no input rows
+
+
+# ------------------------------------------------------------------ tree LQR
+def _random_tree(rng, n_max=30):
+    """Level-ordered tree with random fan-out 0..3 and leaves at ragged depths."""
+    parent = [-1]
+    frontier = [0]
+    while frontier and len(parent) < n_max:
+        nxt = []
+        for q in frontier:
+            for _ in range(int(rng.integers(1 if q == 0 else 0, 4))):
+                if len(parent) >= n_max:
+                    break
+                parent.append(q)
+                nxt.append(len(parent) - 1)
+        frontier = nxt
+    return np.array(parent, np.int32)
+
+
+def _random_lqr(rng, parent, nx, nu):
+    n = len(parent)
+    leaf = np.ones(n, bool)
+    leaf[parent[1:]] = False
+    Q, M, R = np.zeros((n, nx, nx)), np.zeros((n, nu, nx)), np.zeros((n, nu, nu))
+    for i in range(n):
+        F = rng.standard_normal((nx + nu, nx + nu))
+        W = F @ F.T + 0.2 * np.eye(nx + nu)
+        Q[i] = W[:nx, :nx]
+        if not leaf[i]:
+            M[i], R[i] = W[nx:, :nx], W[nx:, nx:]
+    q, r = rng.standard_normal((n, nx)), rng.standard_normal((n, nu)) * (~leaf)[:, None]
+    A = np.eye(nx) + 0.3 * rng.standard_normal((n, nx, nx))
+    B = rng.standard_normal((n, nx, nu))
+    c = rng.standard_normal((n, nx))
+    c[0] = 0
+    return leaf, Q, M, R, q, r, A, B, c
+
+
+def _dense_kkt(parent, leaf, Q, M, R, q, r, A, B, c):
+    """Dense KKT system of Eq. (lqr_tree_approx) with dx_0 = 0: returns dx, du, lam."""
+    n, nx, nu = len(parent), Q.shape[1], R.shape[1]
+    uidx = {}
+    off = n * nx
+    for i in range(n):
+        if not leaf[i]:
+            uidx[i] = off
+            off += nu
+    nz = off
+    H = np.zeros((nz, nz))
+    h = np.zeros(nz)
+    for i in range(n):
+        xi = slice(i * nx, (i + 1) * nx)
+        H[xi, xi] += Q[i]
+        h[xi] += q[i]
+        if not leaf[i]:
+            ui = slice(uidx[i], uidx[i] + nu)
+            H[ui, ui] += R[i]
+            H[ui, xi] += M[i]
+            H[xi, ui] += M[i].T
+            h[ui] += r[i]
+    ncon = n * nx
+    E = np.zeros((ncon, nz))
+    e = np.zeros(ncon)
+    E[0:nx, 0:nx] = np.eye(nx)                      # dx_0 = 0
+    for m in range(1, n):
+        pnt = parent[m]
+        rows = slice(m * nx, (m + 1) * nx)
+        E[rows, m * nx:(m + 1) * nx] = np.eye(nx)
+        E[rows, pnt * nx:(pnt + 1) * nx] -= A[pnt]
+        E[rows, uidx[pnt]:uidx[pnt] + nu] -= B[pnt]
+        e[rows] = c[m]
+    K = np.block([[H, E.T], [E, np.zeros((ncon, ncon))]])
+    sol = np.linalg.solve(K, np.concatenate([-h, e]))
+    z, nu_ = sol[:nz], sol[nz:]
+    dx = z[:n * nx].reshape(n, nx)
+    du = np.zeros((n, nu))
+    for i, o in uidx.items():
+        du[i] = z[o:o + nu]
+    lam = -nu_.reshape(n, nx)        # lambda multiplies (A dx + B du + c - dx_m)
+    return dx, du, lam
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tree_lqr_equals_dense_kkt(seed):
+    rng = np.random.default_rng(100 + seed)
+    nx, nu = (4, 2) if seed % 2 == 0 else (3, 1)
+    parent = _random_tree(rng)
+    leaf, Q, M, R, q, r, A, B, c = _random_lqr(rng, parent, nx, nu)
+    K, k, P, pv, dx, du, lam = oracle.tree_lqr(parent, Q, M, R, q, r, A, B, c)
+    dx2, du2, lam2 = _dense_kkt(parent, leaf, Q, M, R, q, r, A, B, c)
+    scale = max(1.0, np.abs(dx2).max(), np.abs(lam2).max())
+    np.testing.assert_allclose(dx, dx2, atol=1e-10 * scale)
+    np.testing.assert_allclose(du, du2, atol=1e-10 * scale)
+    np.testing.assert_allclose(lam[1:], lam2[1:], atol=1e-10 * scale)
+
+
+def test_single_path_riccati_reaches_dare():
+    rng = np.random.default_rng(7)
+    nx, nu, N = 4, 2, 400
+    A1 = np.eye(nx) + 0.1 * rng.standard_normal((nx, nx))
+    B1 = rng.standard_normal((nx, nu))
+    F = rng.standard_normal((nx, nx))
+    Q1 = F @ F.T + np.eye(nx)
+    R1 = np.diag([0.5, 2.0])
+    parent = np.arange(-1, N, dtype=np.int32)
+    n = N + 1
+    Q = np.repeat(Q1[None], n, 0)
+    R = np.repeat(R1[None], n, 0)
+    R[-1] = 0
+    M = np.zeros((n, nu, nx))
+    A = np.repeat(A1[None], n, 0)
+    B = np.repeat(B1[None], n, 0)
+    K, k, P, pv, dx, du, lam = oracle.tree_lqr(parent, Q, M, R, np.zeros((n, nx)), np.zeros((n, nu)),
+                                               A, B, np.zeros((n, nx)))
+    Pd = scipy.linalg.solve_discrete_are(A1, B1, Q1, R1)
+    np.testing.assert_allclose(P[0], Pd, rtol=1e-9, atol=1e-9 * np.abs(Pd).max())
+    Kd = -np.linalg.solve(R1 + B1.T @ Pd @ B1, B1.T @ Pd @ A1)
+    np.testing.assert_allclose(K[0], Kd, rtol=1e-8, atol=1e-9)
+
+
+# ------------------------------------------------------------------ iLQR step, merit
+def test_lq_problem_converges_in_one_iteration():
+    p = scenes.linear_problem(3, N=12, splits={2: 2, 6: 3})
+    r = oracle.solve(p)
+    assert r["status"] == oracle.OK
+    assert r["inner_iters"] == 1
+    k = oracle.kkt(p, r["x"], r["u"], r["lam"], r["y"])
+    assert k.max() < 1e-11
+
+
+def test_lq_full_step_merit_identity():
+    """For linear dynamics and quadratic cost phi(1) - phi(0) = phi'(0)/2 exactly."""
+    p = scenes.linear_problem(4, N=8, splits={3: 2})
+    x, u, lam, y = oracle.cold_start(p)
+    x[0] = p["x0"]
+    lam = 0.1 * np.random.default_rng(0).standard_normal(lam.shape)
+    lam[0] = 0
+    dx, du, dl, info = oracle.direction(p, x, u, lam, y, 10.0, 3.0)
+    phi1 = oracle.merit(p, x + dx, u + du, lam + dl, y, 10.0, 3.0)
+    assert abs((phi1 - info[0]) - 0.5 * info[1]) < 1e-9 * max(1.0, abs(info[1]))
+    # and the closed form phi'(0; 0) = -dz'W dz + 2 dlam'd of the exact QP step
+    nx = p["nx"]
+    d = np.zeros_like(x)
+    for m in range(1, p["n"]):
+        pn = p["parent"][m]
+        d[m] = oracle.dynamics(p, x[pn], u[pn])[0] - x[m]
+    assert abs(info[4] - (-info[2] + 2 * np.sum(dl[1:] * d[1:]))) < 1e-9 * max(1.0, abs(info[4]))
+    assert nx == 4
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_merit_directional_derivative_matches_central_difference(cfg):
+    p = scenes.instances(cfg, 1, seed0=5)[0]
+    x, u, lam, y = oracle.cold_start(p)
+    x[0] = p["x0"]
+    rng = np.random.default_rng(1)
+    lam = 0.05 * rng.standard_normal(lam.shape)
+    lam[0] = 0
+    y = np.abs(0.1 * rng.standard_normal(y.shape))
+    rho, mu = 10.0, 2.0
+    dx, du, dl, info = oracle.direction(p, x, u, lam, y, rho, mu)
+    h = 1e-6
+    fp = oracle.merit(p, x + h * dx, u + h * du, lam + h * dl, y, rho, mu)
+    fm = oracle.merit(p, x - h * dx, u - h * du, lam - h * dl, y, rho, mu)
+    fd = (fp - fm) / (2 * h)
+    assert abs(fd - info[1]) < 1e-6 * max(1.0, abs(info[1]))
+    assert info[0] == pytest.approx(oracle.merit(p, x, u, lam, y, rho, mu), rel=1e-14)
+
+
+# ------------------------------------------------------------------ tree structure
+def test_identical_branches_are_bitwise_equal():
+    """Nonanticipativity is exact: with stage-only data, all scenarios coincide bit for bit."""
+    p = scenes.linear_problem(5, N=10, splits={2: 3, 5: 2})
+    st = p["stage"]
+    xr = np.zeros((st.max() + 1, p["nx"]))
+    for i in range(p["n"]):
+        xr[st[i]] = p["xref"][i]
+    p["xref"] = xr[st]
+    r = oracle.solve(p)
+    for k in range(st.max() + 1):
+        rows = r["x"][st == k]
+        assert (rows == rows[0]).all()
+
+
+def test_branch_value_functions_sum():
+    """b identical children of weight w/b give the same plan as one child of weight w."""
+    base = scenes.linear_problem(6, N=9, splits={})
+    tree = scenes.linear_problem(6, N=9, splits={4: 3})
+    for q in (base, tree):
+        st = q["stage"]
+        q["xref"] = base["xref"][st]
+        q["weight"] = scenes.branch_weights(q["parent"])
+    rb, rt = oracle.solve(base), oracle.solve(tree)
+    st = tree["stage"]
+    first = {}
+    for i in range(tree["n"]):
+        first.setdefault(st[i], i)
+    for k, i in first.items():
+        np.testing.assert_allclose(rt["x"][i], rb["x"][k], atol=1e-10)
+        if k < st.max():
+            np.testing.assert_allclose(rt["u"][i], rb["u"][k], atol=1e-10)
+
+
+# ------------------------------------------------------------------ AL method, KKT
+@pytest.mark.parametrize("cfg,seed", [(1, 0), (1, 1), (1, 2), (2, 0), (2, 3)])
+def test_al_reaches_kkt_of_original_problem(cfg, seed):
+    p = scenes.instances(cfg, 1, seed0=seed)[0]
+    r = oracle.solve(p)
+    assert r["status"] == oracle.OK
+    k = oracle.kkt(p, r["x"], r["u"], r["lam"], r["y"])
+    assert k[:4].max() < 1e-5                  # stationarity, defects, feasibility, complementarity
+    assert (r["y"] >= 0).all() and k[4] == 0.0
+
+
+def _objective(p, x, u):
+    return oracle.aug_lagrangian(p, x, u, np.zeros((p["n"], oracle.n_con(p))), 1e-300)
+
+
+def test_stationarity_by_finite_differences():
+    """grad of sum(l) + y'g + lam'd vanishes at the returned point (FD, independent of the KKT code)."""
+    p = scenes.config1(3)
+    r = oracle.solve(p)
+    assert r["status"] == oracle.OK
+    x, u, lam, y = r["x"], r["u"], r["lam"], r["y"]
+    n, nx, nu = p["n"], p["nx"], p["nu"]
+    ch = [[] for _ in range(n)]
+    for i in range(1, n):
+        ch[p["parent"][i]].append(i)
+
+    def lagr(xx, uu):
+        v = _objective(p, xx, uu)
+        for i in range(n):
+            g, _, _, ex = oracle.constraints(p, i, not ch[i], xx[i], uu[i])
+            v += float(np.sum(y[i][ex] * g[ex]))
+            if ch[i]:
+                f = oracle.dynamics(p, xx[i], uu[i])[0]
+                for m in ch[i]:
+                    v += float(lam[m] @ (f - xx[m]))
+        return v
+
+    h = 1e-5
+    worst = 0.0
+    rng = np.random.default_rng(0)
+    for i in rng.choice(np.arange(1, n), 12, replace=False):
+        for j in range(nx):
+            xp, xm = x.copy(), x.copy()
+            xp[i, j] += h
+            xm[i, j] -= h
+            worst = max(worst, abs((lagr(xp, u) - lagr(xm, u)) / (2 * h)))
+        if ch[i]:
+            for j in range(nu):
+                up, um = u.copy(), u.copy()
+                up[i, j] += h
+                um[i, j] -= h
+                worst = max(worst, abs((lagr(x, up) - lagr(x, um)) / (2 * h)))
+    assert worst < 2e-5
+
+
+def test_inactive_constraints_give_zero_multipliers():
+    """Obstacles moved far away: same plan as without them and y = 0 on their rows."""
+    p = scenes.config1(4)
+    far = dict(p)
+    far["obs"] = p["obs"].copy()
+    far["obs"][:, :, 1] += 1000.0
+    none = dict(p)
+    none["obs"] = p["obs"][:, :0, :]
+    none["n_obs"] = 0
+    rf, rn = oracle.solve(far), oracle.solve(none)
+    assert rf["status"] == oracle.OK and rn["status"] == oracle.OK
+    np.testing.assert_allclose(rf["u"], rn["u"], atol=1e-7)
+    assert (rf["y"][:, 4] == 0).all()
+
+
+def test_invalid_tree_rejected():
+    p = scenes.config1(0)
+    bad = dict(p)
+    par = p["parent"].copy()
+    par[5] = 7                       # parent after child: not level ordered
+    bad["parent"] = par
+    r = oracle.solve(bad)
+    assert r["status"] == -1
