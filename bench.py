@@ -1,0 +1,330 @@
+"""Benchmark: branch-MPC solves per second to KKT <= 1e-5 (FP32) on one or more GPUs.
+
+One step = one batch of seeded synthetic scenario-tree problems solved to
+convergence by the whole hot path (RK4 linearisation, tree Riccati recursion,
+forward rollout, merit line search, BCL update) in one persistent kernel
+launch, replayed from a captured CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config2|config4] [--batch B]
+  python bench.py --impl reference ...   # the FP64 oracle on the host cores
+
+Under torchrun every rank solves its own shard of B problems (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "BMPC solves/sec at KKT<=1e-5 (FP32)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
+
+
+def workload(name: str, batch: int, rank: int = 0):
+    """Seeded problems of the named configuration; each rank gets its own seeds."""
+    if name == "config2":
+        return [scenes.config2(rank * batch + i) for i in range(batch)]
+    if name == "config4":
+        return [scenes.config4_problem(4 + rank, i) for i in range(batch)]
+    if name == "config3":
+        return [scenes.config3(rank * batch + i) for i in range(batch)]
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------- algorithmic flop model
+def flops_model(p) -> dict:
+    """Algorithmic FP32 flops per node of one inner iteration, by phase (FMA = 2 flops).
+
+    Counted from the arithmetic the method needs, not from instructions: RK4 with forward-mode
+    tangents, the tree Riccati step, the rollout, one line-search evaluation per step size.
+    """
+    nx, model, nsub = int(p["nx"]), int(p["model"]), max(1, int(p["params"][9]))
+    nz = nx + 2
+    ns = nx * (nx + 1) // 2
+    rhs = {0: 20, 1: 70, 2: 2 * nx * nz}[model]
+    nnz = {0: 7, 1: 18, 2: nx * nz}[model]
+    n_obs = int(p["n_obs"])
+    if model == 2:
+        lin_dyn = 2 * nx * nz
+        ls_dyn = 2 * nx * nz
+    else:
+        per_stage = rhs + 2 * nnz * nz + 2 * nx * nz + 4 * nx * nz
+        lin_dyn = nsub * (4 * per_stage + 2 * nx * nz + 2 * nx)
+        ls_dyn = nsub * 4 * (rhs + 6 * nx)
+    con = 8 * nx + 30 * n_obs + 20
+    return dict(
+        linearise=lin_dyn + con + 2 * nx * nx + 8 * nx,
+        riccati=(2 * nx ** 3 + 4 * nx * nx + 2 * ns * nx + 4 * nx * nx + 2 * nx * nx + ns * (2 * nx + 4)
+                 + 12 * nx + 60 + ns + 2 * nx * nx),
+        forward=4 * nx * nx + 8 * nx + 8 * nx,
+        ls_eval=ls_dyn + con + 6 * nx + 6 * nx,
+        update=6 * nx,
+        outer=con,
+    )
+
+
+def algorithmic_flops(problems, results) -> float:
+    tot = 0.0
+    for p, r in zip(problems, results):
+        m = flops_model(p)
+        n = int(p["n"])
+        it = r["inner_iters"]
+        checks = it + r["outer_iters"]            # linearisation + KKT check per inner step and per outer exit
+        tot += n * (checks * m["linearise"] + it * (m["riccati"] + m["forward"] + m["update"])
+                    + r["ls_evals"] * m["ls_eval"] + r["outer_iters"] * m["outer"])
+    return tot
+
+
+# ----------------------------------------------------------------- clocks sampling
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=smax, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+def oracle_rate(name: str, seconds: float, max_problems: int, rank: int = 0):
+    """The FP64 oracle as it stands, one thread, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    probs = workload(name, max_problems, rank)
+    t0 = time.perf_counter()
+    solved = done = 0
+    for p in probs:
+        r = oracle.solve(p)
+        done += 1
+        solved += int(r["status"] == oracle.OK)
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=solved / dt, attempted_per_s=done / dt, unit="solves/s", cores=1, kind="oracle",
+                sample=f"{done} {name} problems solved sequentially with the FP64 oracle ({dt:.1f} s)")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        probs = workload(args.workload, args.ref_sample, rank=1000 + s)
+        import oracle
+        oracle.build()
+        tsolve = time.perf_counter()
+        solved = sum(int(oracle.solve(p)["status"] == oracle.OK) for p in probs)
+        dt = time.perf_counter() - tsolve
+        if s >= args.warmup:
+            steps.append((solved, dt))
+        del t0
+    tot_s = sum(d for _, d in steps)
+    value = sum(n for n, _ in steps) / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / len(steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "batch": args.ref_sample},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.ref_sample} {args.workload} problems per step, FP64 oracle, one thread"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+
+    # CPU baseline first (rank 0, N = 1 only), before the GPU is busy
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_rate(args.workload, args.cpu_seconds, 256)
+
+    from paper_2506_13624_b300 import bmpc
+    problems = workload(args.workload, args.batch, rank)
+    stream = torch.cuda.Stream()
+    b = bmpc.Batch(problems, stream=stream)
+    b.set_problems()
+    opts = bmpc.default_opts(block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm,
+                             ls_chunk=args.ls_chunk)
+    for _ in range(args.warmup):
+        b.solve(opts, graph=True)
+    res = b.get_solutions(want_arrays=False)
+    conv = np.array([r["status"] == 0 for r in res])
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b.solve(opts, graph=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = sampler.stop() if rank == 0 else None
+    res = b.get_solutions(want_arrays=False)
+    n_conv = int(sum(r["status"] == 0 for r in res))
+
+    # end to end through the C ABI with host buffers: pack + H2D, solve, D2H + unpack
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        b.set_problems()
+        b.solve(opts, graph=True)
+        b.get_solutions(want_arrays=True)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    h2d = b.data_bytes  # upper bound: recs + inputs (the warm region is skipped for cold starts)
+    from paper_2506_13624_b300.bmpc import lib  # noqa: F401
+    import ctypes as C  # noqa: F401
+
+    ms_all = torch.tensor([ms], device="cuda")
+    e2e_all = torch.tensor([e2e_s], device="cuda")
+    nconv_all = torch.tensor([n_conv], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e2e_all, op=dist.ReduceOp.MAX)
+        dist.all_reduce(nconv_all, op=dist.ReduceOp.SUM)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    ms = float(ms_all.item())
+    total_conv = float(nconv_all.item())
+    value = total_conv / (ms / 1e3)
+    flops = algorithmic_flops(problems, res)
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (ms / 1e3) / 1e12
+    iters = np.array([r["inner_iters"] for r in res])
+    clk = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
+    bwd_us = np.array([r["cycles"]["backward"] for r in res]) / (clk * 1e6) * 1e6
+    ric_us_iter = float(np.sum(bwd_us) / max(1, iters.sum()))
+    tot_us = np.array([r["cycles"]["total"] for r in res]) / (clk * 1e6) * 1e6
+    out_bytes = int(sum(int(p["n"]) * (2 * int(p["nx"]) + 2 + bmpc.n_con(p)) * 4 for p in problems))
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "batch_per_gpu": args.batch,
+                   "nodes_per_gpu": int(sum(int(p["n"]) for p in problems)),
+                   "l2": f"working set {(b.data_bytes + b.scratch_bytes) / 1e9:.2f} GB > 126 MB L2, no flush",
+                   "launch": "one persistent kernel per step, CUDA graph replay"},
+        "converged_fraction": float(conv.mean()),
+        "tree_riccati_us_per_iter": ric_us_iter,
+        "solve_latency_us": {"mean": float(tot_us.mean()), "max": float(tot_us.max())},
+        "inner_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"},
+        "e2e": {"value": total_conv / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": out_bytes},
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="config2", choices=["config2", "config3", "config4"])
+    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--ls-chunk", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=16)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "b300":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * bmpc.h - C ABI of the B300 branch-MPC solver (multiple-shooting augmented-
+ * Lagrangian iLQR over a scenario tree, arXiv 2506.13624).
+ *
+ * One call of bmpc_solve / bmpc_solve_batch runs the whole method of
+ * Algorithm 1 on the GPU in one persistent kernel launch: per-node RK4
+ * linearisation and Gauss-Newton quadratisation of the augmented Lagrangian
+ * (Sec. IV-A, Eq. AL), the tree Riccati recursion that sums the children's
+ * value functions at branch points (Sec. III-A, Eq. tree_Riccati and
+ * Eq. tree_feedback_laws), the linear forward rollout along all root-to-leaf
+ * paths, the merit line search over all step sizes (Eq. merit,
+ * Eq. sufficient_decrease) and the BCL multiplier / penalty update (Sec. IV-B).
+ *
+ * Memory.  The library never allocates device memory.  The caller provides two
+ * device arenas (any allocator: PyTorch tensors, cudaMalloc, ...) whose sizes
+ * bmpc_batch_bytes reports: a data arena (problem tables, inputs, outputs,
+ * statistics) and a scratch arena (per-node Jacobians, Riccati factors and
+ * search directions).  Arenas must be 256-byte aligned and stay valid until
+ * bmpc_destroy_batch.  Host staging memory for uploads/downloads may be passed
+ * in (pinned memory gives asynchronous copies); with NULL the library uses
+ * malloc.
+ *
+ * Streams.  Every device operation of a handle is issued on the stream given
+ * at creation (a cudaStream_t passed as void*, NULL = legacy default stream).
+ * bmpc_get_solutions synchronises that stream.  Handles are not thread safe.
+ *
+ * Errors.  Every function returns a bmpc_status; negative values are errors.
+ * After BMPC_ERR_CUDA the handle should be destroyed.
+ */
+#ifndef BMPC_H
+#define BMPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BMPC_OK = 0,            /* converged: max(r_kkt, c) < eps_tol (Sec. IV-B)        */
+    BMPC_MAX_ITER = 1,      /* iteration cap reached; the last iterate is returned   */
+    BMPC_LS_FAIL = 2,       /* three consecutive line searches found no Armijo step  */
+    BMPC_ERR_INVALID = -1,  /* bad argument, tree or size                            */
+    BMPC_ERR_CUDA = -2,     /* a CUDA runtime call failed                            */
+    BMPC_ERR_NUMERIC = -3,  /* non-positive-definite H_n or non-finite value         */
+    BMPC_ERR_TIMEOUT = -4,  /* reserved: a bounded device wait expired               */
+    BMPC_ERR_SPACE = -5     /* an arena or staging buffer is too small               */
+} bmpc_status;
+
+#define BMPC_MAX_OBS 8
+#define BMPC_MAX_NX 6
+#define BMPC_NU 2
+
+/* Dynamics models (the ego vehicle's f_i of Eq. bmpc; discretised by RK4):
+ *   0 kinematic bicycle, x = (X, Y, psi, v),          u = (a, delta), nx = 4
+ *   1 dynamic bicycle (linear tyres, small steering), x = (X, Y, psi, vx, vy, r), nx = 6
+ *   2 linear x+ = Alin x + Blin u,                     nx = 4                       */
+typedef struct {
+    int32_t num_nodes;      /* >= 2 */
+    const int32_t *parent;  /* host [num_nodes]; parent[0] = -1; level order: nodes sorted by
+                               stage, parent[i] < i and non-decreasing for i >= 1 (so the children
+                               of a node are contiguous).  Copied at creation. */
+    int32_t nx, nu, model;  /* nu must be 2 */
+    int32_t n_obs;          /* obstacle ellipses per node, 0..BMPC_MAX_OBS */
+    int32_t box_on;         /* input box rows on non-leaf nodes */
+    int32_t lane_on;        /* lateral lane rows on non-root nodes */
+    float dt;               /* discretisation step */
+    float params[10];       /* L, m, Iz, lf, lr, Cf, Cr, vmin, veps, n_sub (RK4 substeps) */
+} bmpc_tree_desc;
+
+/* Problem data of one tree (host pointers, copied by bmpc_set_problems).
+ * Cost (Eq. bmpc):  l_i = w_i [1/2 (x-xref_i)' diag(Qw) (x-xref_i) + 1/2 u' diag(Rw) u],
+ *                   l_f,i = w_i 1/2 (x-xref_i)' diag(QNw) (x-xref_i) at leaves.
+ * Constraints g <= 0: u - u_hi, u_lo - u (non-leaf nodes); per obstacle the normalised
+ * ellipse distance 1 - sqrt((d_par/a)^2 + (d_perp/b)^2 + 1e-6); Y - lane_hi, lane_lo - Y.
+ * The root state is fixed to x0 and carries no state constraints. */
+typedef struct {
+    const float *x0;        /* [nx] measured state */
+    const float *xref;      /* [num_nodes][nx] */
+    const float *weight;    /* [num_nodes] node weights w_i, or NULL for all ones */
+    float Qw[BMPC_MAX_NX], QNw[BMPC_MAX_NX], Rw[BMPC_NU];
+    float u_lo[BMPC_NU], u_hi[BMPC_NU];
+    float lane_lo, lane_hi;
+    const float *obs;       /* [num_nodes][n_obs][5]: cx, cy, heading, a, b (may be NULL if n_obs = 0) */
+    const float *Alin;      /* [nx][nx] row-major, model 2 only */
+    const float *Blin;      /* [nx][nu] row-major, model 2 only */
+    /* optional warm start; all four NULL = cold start of Sec. V-B (x linearly interpolated
+       from x0 to the final reference of the node's first leaf, u = lam = y = 0) */
+    const float *warm_x;    /* [num_nodes][nx] */
+    const float *warm_u;    /* [num_nodes][nu] */
+    const float *warm_lam;  /* [num_nodes][nx] */
+    const float *warm_y;    /* [num_nodes][nc], nc = 2*nu*box_on + n_obs + 2*lane_on */
+} bmpc_problem;
+
+/* Algorithm 1 constants (defaults: the values of Sec. V-B plus the readings of the oracle). */
+typedef struct {
+    int32_t max_iters;      /* cap on inner iterations (tree-LQR solves), default 100 */
+    int32_t max_outer;      /* cap on outer iterations, default 60 */
+    int32_t n_alpha;        /* step sizes alpha_i = 2^-i, i < n_alpha (<= 16), default 10 */
+    float eps_tol;          /* 1e-5 */
+    float tau;              /* 100 */
+    float omega0, eta0;     /* 1, 0.1 */
+    float a_omega, b_omega; /* 1, 1 */
+    float a_eta, b_eta;     /* 0.1, 0.9 */
+    float rho0, rho_max;    /* 10, 1e6 */
+    float mu0;              /* 1 */
+    float beta;             /* Armijo constant, 1e-4 */
+    float ls_rel_eps;       /* Armijo slack relative to |phi(0)|, 1e-6 */
+    int32_t ls_chunk;       /* step sizes evaluated per parallel round (1..n_alpha); 0 = all */
+    int32_t block_threads;  /* threads per problem (32..1024, multiple of 32); 0 = automatic */
+    int32_t blocks_per_sm;  /* resident problems per SM; 0 = automatic */
+} bmpc_opts;
+
+typedef struct {
+    int32_t status;         /* bmpc_status of this problem */
+    int32_t inner_iters;    /* tree-LQR solves */
+    int32_t outer_iters;
+    int32_t ls_fail_total;
+    int32_t ls_evals;       /* step sizes evaluated by the line search, summed over iterations */
+    int32_t reserved;
+    float r_kkt, c, rho, mu;
+    int64_t cycles_linearise, cycles_backward, cycles_forward, cycles_linesearch, cycles_total;
+} bmpc_stats;
+
+typedef struct bmpc_batch bmpc_batch;   /* opaque handle */
+
+/* Fill *opts with the defaults listed above. */
+void bmpc_default_opts(bmpc_opts *opts);
+
+/* Bytes needed for n problems with the given tree descriptors: device data arena,
+ * device scratch arena and host staging buffer.  Returns BMPC_ERR_INVALID on a bad tree. */
+int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
+                     size_t *staging_bytes);
+
+/* Create a handle over caller-owned memory (see "Memory").  Validates every tree,
+ * computes the device layout and uploads the tree tables on `stream`. */
+int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, size_t data_bytes,
+                      void *dev_scratch, size_t scratch_bytes, void *host_staging, size_t staging_bytes,
+                      void *stream, bmpc_batch **out);
+
+/* Copy the problem data of all n problems (host pointers) to the device: one packing
+ * pass into the staging buffer and one host-to-device copy on the handle's stream. */
+int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *problems);
+
+/* Run Algorithm 1 on every problem of the batch from its warm (or cold) start in one
+ * persistent kernel launch on the handle's stream (asynchronous).  opts may be NULL. */
+int bmpc_solve_batch(bmpc_batch *b, const bmpc_opts *opts);
+
+/* Same work captured once into a CUDA graph (queue reset + persistent kernel) and
+ * replayed; the graph is rebuilt when opts change.  Asynchronous. */
+int bmpc_solve_batch_graph(bmpc_batch *b, const bmpc_opts *opts);
+
+/* Copy solutions back (synchronises the stream).  Host arrays, concatenated over problems
+ * in batch order, node-major: x [sum n_i][nx_i], u [sum n_i][nu] (zero rows at leaves),
+ * lam [sum n_i][nx_i] (row of each root zero), y [sum n_i][nc_i]; stats [n].
+ * Any pointer may be NULL. */
+int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats);
+
+/* Device pointers of the output arrays of problem i (component-major [comp][npad]) and its
+ * padded node count, for callers that keep results on the GPU. */
+int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float **u, float **lam, float **y,
+                                int32_t *npad);
+
+void bmpc_destroy_batch(bmpc_batch *b);
+
+/* ---- single-tree interface of the paper's problem statement (a batch of one) ---- */
+typedef bmpc_batch bmpc_tree;
+int bmpc_tree_bytes(const bmpc_tree_desc *desc, size_t *data_bytes, size_t *scratch_bytes, size_t *staging_bytes);
+int bmpc_create_tree(const bmpc_tree_desc *desc, void *dev_data, size_t data_bytes, void *dev_scratch,
+                     size_t scratch_bytes, void *host_staging, size_t staging_bytes, void *stream, bmpc_tree **out);
+int bmpc_set_problem(bmpc_tree *t, const bmpc_problem *problem);
+int bmpc_solve(bmpc_tree *t, const bmpc_opts *opts, bmpc_stats *stats /* nullable; synchronises if given */);
+int bmpc_get_solution(bmpc_tree *t, float *x, float *u, float *lam, float *y);
+void bmpc_destroy_tree(bmpc_tree *t);
+
+const char *bmpc_status_str(int status);
+/* Library build string (architecture and version). */
+const char *bmpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BMPC_H */

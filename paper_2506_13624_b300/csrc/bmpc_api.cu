@@ -1,0 +1,600 @@
+/*
+ * Host side of the bmpc C ABI (include/bmpc.h): tree validation, device layout,
+ * packing of problem data into one staging buffer, one host-to-device copy per
+ * upload, the persistent solver launch (optionally captured into a CUDA graph)
+ * and unpacking of the results.  The library allocates no device memory: all
+ * device regions are carved out of the two caller-owned arenas.
+ */
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/bmpc.h"
+#include "bmpc_layout.h"
+
+namespace bmpc {
+cudaError_t launch_solve(const KernelArgs &args, int grid, int block, cudaStream_t stream);
+int max_block_threads();
+cudaError_t occupancy(int block, int *blocks_per_sm);
+}  // namespace bmpc
+
+using namespace bmpc;
+
+static_assert(sizeof(Stats) == sizeof(bmpc_stats), "device statistics must match the public struct");
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int n_con(const bmpc_tree_desc &d) { return 2 * NU * (d.box_on ? 1 : 0) + d.n_obs + 2 * (d.lane_on ? 1 : 0); }
+
+/* Tree checks: level order, children contiguous, model/size consistency. */
+int validate(const bmpc_tree_desc &d, std::vector<int> *stage_out) {
+    if (d.num_nodes < 2 || !d.parent) return BMPC_ERR_INVALID;
+    if (d.nu != NU) return BMPC_ERR_INVALID;
+    if (d.model == 0 && d.nx != 4) return BMPC_ERR_INVALID;
+    if (d.model == 1 && d.nx != 6) return BMPC_ERR_INVALID;
+    if (d.model == 2 && d.nx != 4) return BMPC_ERR_INVALID;
+    if (d.model < 0 || d.model > 2) return BMPC_ERR_INVALID;
+    if (d.n_obs < 0 || d.n_obs > MAX_OBS) return BMPC_ERR_INVALID;
+    if (!(d.dt > 0.f) || !std::isfinite(d.dt)) return BMPC_ERR_INVALID;
+    if (d.model != 2 && !(d.params[9] >= 1.f && d.params[9] <= 64.f)) return BMPC_ERR_INVALID;
+    const int n = d.num_nodes;
+    std::vector<int> stage(n, 0);
+    if (d.parent[0] != -1) return BMPC_ERR_INVALID;
+    for (int i = 1; i < n; ++i) {
+        const int p = d.parent[i];
+        if (p < 0 || p >= i) return BMPC_ERR_INVALID;
+        if (i >= 2 && p < d.parent[i - 1]) return BMPC_ERR_INVALID;   /* children contiguous */
+        stage[i] = stage[p] + 1;
+        if (stage[i] < stage[i - 1]) return BMPC_ERR_INVALID;          /* level order */
+    }
+    if (stage_out) *stage_out = std::move(stage);
+    return BMPC_OK;
+}
+
+struct Layout {
+    size_t recs, order, queue, ints, in, warm, out, stats, data_total;   /* byte offsets in the data arena */
+    size_t ints_n, in_n, warm_n, out_n, scr_n;                           /* element counts */
+    size_t staging;
+};
+
+}  // namespace
+
+struct bmpc_batch {
+    int n = 0;
+    std::vector<ProbRec> recs;
+    std::vector<int32_t> order;
+    std::vector<int> nodes;
+    Layout L{};
+    char *data = nullptr;
+    float *scr = nullptr;
+    size_t data_bytes = 0, scr_bytes = 0;
+    char *stage = nullptr;
+    size_t stage_bytes = 0;
+    bool own_stage = false;
+    cudaStream_t stream = nullptr;
+    int sm_count = 148;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bmpc_opts gopts{};
+    bool have_graph = false;
+};
+
+namespace {
+
+void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &recs, std::vector<int> &nodes,
+                    Layout &L) {
+    recs.assign(n, ProbRec{});
+    nodes.resize(n);
+    size_t oi = 0, oin = 0, ow = 0, oo = 0, os = 0;
+    for (int k = 0; k < n; ++k) {
+        const bmpc_tree_desc &d = descs[k];
+        ProbRec &R = recs[k];
+        std::memset(&R, 0, sizeof R);
+        int max_stage = 0;
+        {
+            std::vector<int> stage;
+            validate(d, &stage);
+            max_stage = stage.back();
+        }
+        R.n = d.num_nodes;
+        R.npad = round_up(d.num_nodes, 32);
+        R.nx = d.nx;
+        R.nu = d.nu;
+        R.model = d.model;
+        R.n_obs = d.n_obs;
+        R.nc = n_con(d);
+        R.box_on = d.box_on ? 1 : 0;
+        R.lane_on = d.lane_on ? 1 : 0;
+        R.n_stage = max_stage + 1;
+        R.dt = d.dt;
+        std::memcpy(R.params, d.params, sizeof R.params);
+        R.off_int = (int64_t)oi;
+        R.off_in = (int64_t)oin;
+        R.off_warm = (int64_t)ow;
+        R.off_out = (int64_t)oo;
+        R.off_scr = (int64_t)os;
+        oi += (size_t)int_elems(R.npad, R.n_stage);
+        oin += (size_t)in_rows(R.nx, R.n_obs).total * R.npad;
+        ow += (size_t)warm_rows(R.nx, R.nc).total * R.npad;
+        oo += (size_t)out_rows(R.nx, R.nc).total * R.npad;
+        os += (size_t)scr_rows(R.nx).total * R.npad;
+        nodes[k] = d.num_nodes;
+    }
+    L.ints_n = oi;
+    L.in_n = oin;
+    L.warm_n = ow;
+    L.out_n = oo;
+    L.scr_n = os;
+    size_t off = 0;
+    L.recs = off;
+    off = align_up(off + sizeof(ProbRec) * n);
+    L.order = off;
+    off = align_up(off + sizeof(int32_t) * n);
+    L.queue = off;
+    off = align_up(off + sizeof(int32_t) * 4);
+    L.ints = off;
+    off = align_up(off + sizeof(int32_t) * oi);
+    L.in = off;
+    off = align_up(off + sizeof(float) * oin);
+    L.warm = off;
+    off = align_up(off + sizeof(float) * ow);
+    L.out = off;
+    off = align_up(off + sizeof(float) * oo);
+    L.stats = off;
+    off = align_up(off + sizeof(Stats) * n);
+    L.data_total = off;
+    /* staging mirrors [recs .. stats] of the data arena */
+    L.staging = L.data_total;
+}
+
+KOpts to_kopts(const bmpc_opts &o) {
+    KOpts k;
+    k.max_iters = o.max_iters;
+    k.max_outer = o.max_outer;
+    k.n_alpha = o.n_alpha;
+    k.ls_chunk = o.ls_chunk;
+    k.eps_tol = o.eps_tol;
+    k.tau = o.tau;
+    k.omega0 = o.omega0;
+    k.eta0 = o.eta0;
+    k.a_omega = o.a_omega;
+    k.b_omega = o.b_omega;
+    k.a_eta = o.a_eta;
+    k.b_eta = o.b_eta;
+    k.rho0 = o.rho0;
+    k.rho_max = o.rho_max;
+    k.mu0 = o.mu0;
+    k.beta = o.beta;
+    k.ls_rel_eps = o.ls_rel_eps;
+    return k;
+}
+
+int check_opts(const bmpc_opts &o) {
+    if (o.max_iters < 0 || o.max_outer < 1 || o.n_alpha < 1 || o.n_alpha > 16) return BMPC_ERR_INVALID;
+    if (o.ls_chunk < 0 || o.ls_chunk > 16) return BMPC_ERR_INVALID;
+    if (!(o.eps_tol > 0.f) || !(o.tau > 1.f) || !(o.rho0 > 0.f) || !(o.rho_max >= o.rho0)) return BMPC_ERR_INVALID;
+    if (!(o.beta > 0.f && o.beta < 0.5f) || !(o.mu0 >= 0.f) || !(o.ls_rel_eps >= 0.f)) return BMPC_ERR_INVALID;
+    if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > max_block_threads() || o.block_threads % 32))
+        return BMPC_ERR_INVALID;
+    if (o.blocks_per_sm < 0) return BMPC_ERR_INVALID;
+    return BMPC_OK;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? BMPC_OK : BMPC_ERR_CUDA; }
+
+template <typename T>
+T *at(char *base, size_t off) {
+    return reinterpret_cast<T *>(base + off);
+}
+
+/* Launch geometry: threads per problem and number of persistent blocks. */
+void geometry(const bmpc_batch *b, const bmpc_opts &o, int *grid, int *block) {
+    int bt = o.block_threads;
+    if (bt == 0) {
+        int maxn = 0;
+        for (int v : b->nodes) maxn = std::max(maxn, v);
+        bt = b->n == 1 ? (maxn > 1024 ? 256 : 128) : 64;
+    }
+    int per_sm = o.blocks_per_sm;
+    if (per_sm == 0) {
+        int occ = 1;
+        if (occupancy(bt, &occ) != cudaSuccess || occ < 1) occ = 1;
+        per_sm = occ;
+    }
+    *block = bt;
+    *grid = std::max(1, std::min(b->n, b->sm_count * per_sm));
+}
+
+int launch(bmpc_batch *b, const bmpc_opts &o) {
+    KernelArgs a;
+    a.recs = at<const ProbRec>(b->data, b->L.recs);
+    a.order = at<const int32_t>(b->data, b->L.order);
+    a.n_problems = b->n;
+    a.queue = at<int32_t>(b->data, b->L.queue);
+    a.ibase = at<const int32_t>(b->data, b->L.ints);
+    a.inbase = at<const float>(b->data, b->L.in);
+    a.warmbase = at<const float>(b->data, b->L.warm);
+    a.outbase = at<float>(b->data, b->L.out);
+    a.scr = b->scr;
+    a.stats = at<Stats>(b->data, b->L.stats);
+    a.opts = to_kopts(o);
+    int grid, block;
+    geometry(b, o, &grid, &block);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), b->stream);
+    if (e != cudaSuccess) return BMPC_ERR_CUDA;
+    return cuda_status(launch_solve(a, grid, block, b->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+void bmpc_default_opts(bmpc_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->max_iters = 100;
+    o->max_outer = 60;
+    o->n_alpha = 10;
+    o->eps_tol = 1e-5f;
+    o->tau = 100.f;
+    o->omega0 = 1.f;
+    o->eta0 = 0.1f;
+    o->a_omega = 1.f;
+    o->b_omega = 1.f;
+    o->a_eta = 0.1f;
+    o->b_eta = 0.9f;
+    o->rho0 = 10.f;
+    o->rho_max = 1e6f;
+    o->mu0 = 1.f;
+    o->beta = 1e-4f;
+    o->ls_rel_eps = 1e-6f;
+    o->ls_chunk = 0;
+    o->block_threads = 0;
+    o->blocks_per_sm = 0;
+}
+
+int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
+                     size_t *staging_bytes) {
+    if (!descs || n < 1) return BMPC_ERR_INVALID;
+    for (int k = 0; k < n; ++k)
+        if (validate(descs[k], nullptr) != BMPC_OK) return BMPC_ERR_INVALID;
+    std::vector<ProbRec> recs;
+    std::vector<int> nodes;
+    Layout L;
+    compute_layout(descs, n, recs, nodes, L);
+    if (data_bytes) *data_bytes = L.data_total;
+    if (scratch_bytes) *scratch_bytes = std::max<size_t>(kAlign, L.scr_n * sizeof(float));
+    if (staging_bytes) *staging_bytes = L.staging;
+    return BMPC_OK;
+}
+
+int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, size_t data_bytes, void *dev_scratch,
+                      size_t scratch_bytes, void *host_staging, size_t staging_bytes, void *stream,
+                      bmpc_batch **out) {
+    if (!out) return BMPC_ERR_INVALID;
+    *out = nullptr;
+    size_t need_d, need_s, need_h;
+    int st = bmpc_batch_bytes(descs, n, &need_d, &need_s, &need_h);
+    if (st != BMPC_OK) return st;
+    if (!dev_data || !dev_scratch) return BMPC_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(dev_data) % kAlign) || (reinterpret_cast<uintptr_t>(dev_scratch) % kAlign))
+        return BMPC_ERR_INVALID;
+    if (data_bytes < need_d || scratch_bytes < need_s) return BMPC_ERR_SPACE;
+    if (host_staging && staging_bytes < need_h) return BMPC_ERR_SPACE;
+    bmpc_batch *b = new (std::nothrow) bmpc_batch();
+    if (!b) return BMPC_ERR_SPACE;
+    b->n = n;
+    compute_layout(descs, n, b->recs, b->nodes, b->L);
+    b->data = static_cast<char *>(dev_data);
+    b->scr = static_cast<float *>(dev_scratch);
+    b->data_bytes = data_bytes;
+    b->scr_bytes = scratch_bytes;
+    b->stream = static_cast<cudaStream_t>(stream);
+    if (host_staging) {
+        b->stage = static_cast<char *>(host_staging);
+        b->stage_bytes = staging_bytes;
+    } else {
+        b->stage = static_cast<char *>(std::malloc(need_h));
+        if (!b->stage) {
+            delete b;
+            return BMPC_ERR_SPACE;
+        }
+        b->stage_bytes = need_h;
+        b->own_stage = true;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    /* visiting order: largest trees first (longest-processing-time-first on the work queue) */
+    b->order.resize(n);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return b->nodes[a] > b->nodes[c]; });
+    /* int tables of every tree, packed into the staging buffer and uploaded once */
+    int32_t *ib = at<int32_t>(b->stage, b->L.ints);
+    std::memset(ib, 0, sizeof(int32_t) * b->L.ints_n);
+    for (int k = 0; k < n; ++k) {
+        const bmpc_tree_desc &d = descs[k];
+        const ProbRec &R = b->recs[k];
+        int32_t *t = ib + R.off_int;
+        const int nn = R.n, np = R.npad;
+        int32_t *parent = t + IntRows::parent * np, *nch = t + IntRows::nchild * np, *fch = t + IntRows::fchild * np;
+        int32_t *stg = t + IntRows::stage * np, *leaf = t + IntRows::leaf * np, *ss = t + IntRows::stage_start * np;
+        for (int i = 0; i < nn; ++i) {
+            parent[i] = d.parent[i];
+            nch[i] = 0;
+            fch[i] = 0;
+        }
+        stg[0] = 0;
+        for (int i = 1; i < nn; ++i) {
+            const int p = d.parent[i];
+            if (nch[p] == 0) fch[p] = i;
+            nch[p]++;
+            stg[i] = stg[p] + 1;
+        }
+        for (int i = nn - 1; i >= 0; --i) leaf[i] = nch[i] ? leaf[fch[i]] : i;
+        for (int s = 0; s <= R.n_stage; ++s) ss[s] = 0;
+        for (int i = 0; i < nn; ++i) ss[stg[i] + 1]++;
+        for (int s = 0; s < R.n_stage; ++s) ss[s + 1] += ss[s];
+    }
+    std::memcpy(b->stage + b->L.order, b->order.data(), sizeof(int32_t) * n);
+    cudaError_t e = cudaMemcpyAsync(b->data + b->L.order, b->stage + b->L.order, sizeof(int32_t) * n,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->data + b->L.ints, b->stage + b->L.ints, sizeof(int32_t) * b->L.ints_n,
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        bmpc_destroy_batch(b);
+        return BMPC_ERR_CUDA;
+    }
+    *out = b;
+    return BMPC_OK;
+}
+
+int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
+    if (!b || !probs) return BMPC_ERR_INVALID;
+    const int n = b->n;
+    bool any_warm = false;
+    float *fin = at<float>(b->stage, b->L.in);
+    float *fw = at<float>(b->stage, b->L.warm);
+    for (int k = 0; k < n; ++k) {
+        const bmpc_problem &P = probs[k];
+        ProbRec &R = b->recs[k];
+        const int nn = R.n, np = R.npad, nx = R.nx, nc = R.nc;
+        if (!P.x0 || !P.xref || (R.n_obs > 0 && !P.obs)) return BMPC_ERR_INVALID;
+        if (R.model == 2 && (!P.Alin || !P.Blin)) return BMPC_ERR_INVALID;
+        const bool warm = P.warm_x || P.warm_u || P.warm_lam || P.warm_y;
+        if (warm && (!P.warm_x || !P.warm_u || !P.warm_lam || (nc > 0 && !P.warm_y))) return BMPC_ERR_INVALID;
+        for (int j = 0; j < nx; ++j) {
+            R.x0[j] = P.x0[j];
+            R.Qw[j] = P.Qw[j];
+            R.QNw[j] = P.QNw[j];
+            if (!std::isfinite(P.x0[j])) return BMPC_ERR_INVALID;
+        }
+        for (int j = 0; j < NU; ++j) {
+            R.Rw[j] = P.Rw[j];
+            R.u_lo[j] = P.u_lo[j];
+            R.u_hi[j] = P.u_hi[j];
+            if (!(P.Rw[j] > 0.f)) return BMPC_ERR_INVALID;
+        }
+        R.lane_lo = P.lane_lo;
+        R.lane_hi = P.lane_hi;
+        if (R.model == 2) {
+            std::memcpy(R.Alin, P.Alin, sizeof(float) * nx * nx);
+            std::memcpy(R.Blin, P.Blin, sizeof(float) * nx * NU);
+        }
+        R.has_warm = warm ? 1 : 0;
+        any_warm |= warm;
+        const InRows ir = in_rows(nx, R.n_obs);
+        float *base = fin + R.off_in;
+        std::memset(base, 0, sizeof(float) * (size_t)ir.total * np);
+        for (int i = 0; i < nn; ++i) {
+            for (int j = 0; j < nx; ++j) base[(size_t)(ir.xref + j) * np + i] = P.xref[(size_t)i * nx + j];
+            base[(size_t)ir.weight * np + i] = P.weight ? P.weight[i] : 1.f;
+            for (int o = 0; o < R.n_obs; ++o)
+                for (int c = 0; c < 5; ++c)
+                    base[(size_t)(ir.obs + 5 * o + c) * np + i] = P.obs[((size_t)i * R.n_obs + o) * 5 + c];
+        }
+        if (warm) {
+            const WarmRows wr = warm_rows(nx, nc);
+            float *wb = fw + R.off_warm;
+            std::memset(wb, 0, sizeof(float) * (size_t)wr.total * np);
+            for (int i = 0; i < nn; ++i) {
+                for (int j = 0; j < nx; ++j) {
+                    wb[(size_t)(wr.wx + j) * np + i] = P.warm_x[(size_t)i * nx + j];
+                    wb[(size_t)(wr.wl + j) * np + i] = P.warm_lam[(size_t)i * nx + j];
+                }
+                for (int j = 0; j < NU; ++j) wb[(size_t)(wr.wu + j) * np + i] = P.warm_u[(size_t)i * NU + j];
+                for (int c = 0; c < nc; ++c) wb[(size_t)(wr.wy + c) * np + i] = P.warm_y[(size_t)i * nc + c];
+            }
+        }
+    }
+    std::memcpy(b->stage + b->L.recs, b->recs.data(), sizeof(ProbRec) * n);
+    cudaError_t e = cudaMemcpyAsync(b->data + b->L.recs, b->stage + b->L.recs, sizeof(ProbRec) * n,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->data + b->L.in, b->stage + b->L.in, sizeof(float) * b->L.in_n, cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && any_warm)
+        e = cudaMemcpyAsync(b->data + b->L.warm, b->stage + b->L.warm, sizeof(float) * b->L.warm_n,
+                            cudaMemcpyHostToDevice, b->stream);
+    return cuda_status(e);
+}
+
+int bmpc_solve_batch(bmpc_batch *b, const bmpc_opts *opts) {
+    if (!b) return BMPC_ERR_INVALID;
+    bmpc_opts o;
+    if (opts) o = *opts;
+    else bmpc_default_opts(&o);
+    int st = check_opts(o);
+    if (st != BMPC_OK) return st;
+    return launch(b, o);
+}
+
+int bmpc_solve_batch_graph(bmpc_batch *b, const bmpc_opts *opts) {
+    if (!b) return BMPC_ERR_INVALID;
+    bmpc_opts o;
+    if (opts) o = *opts;
+    else bmpc_default_opts(&o);
+    int st = check_opts(o);
+    if (st != BMPC_OK) return st;
+    if (!b->have_graph || std::memcmp(&o, &b->gopts, sizeof o) != 0) {
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->gexec = nullptr;
+        b->graph = nullptr;
+        b->have_graph = false;
+        cudaStream_t cap;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return BMPC_ERR_CUDA;
+        cudaStream_t saved = b->stream;
+        b->stream = cap;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int ls = BMPC_OK;
+        if (e == cudaSuccess) ls = launch(b, o);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        b->stream = saved;
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess || e2 != cudaSuccess || ls != BMPC_OK || !g) {
+            if (g) cudaGraphDestroy(g);
+            return BMPC_ERR_CUDA;
+        }
+        if (cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return BMPC_ERR_CUDA;
+        }
+        b->graph = g;
+        b->gopts = o;
+        b->have_graph = true;
+    }
+    return cuda_status(cudaGraphLaunch(b->gexec, b->stream));
+}
+
+int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats) {
+    if (!b) return BMPC_ERR_INVALID;
+    cudaError_t e = cudaSuccess;
+    if (x || u || lam || y)
+        e = cudaMemcpyAsync(b->stage + b->L.out, b->data + b->L.out, sizeof(float) * b->L.out_n,
+                            cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->stage + b->L.stats, b->data + b->L.stats, sizeof(Stats) * b->n,
+                            cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return BMPC_ERR_CUDA;
+    const float *fo = at<const float>(b->stage, b->L.out);
+    size_t ox = 0, ou = 0, ol = 0, oy = 0;
+    for (int k = 0; k < b->n; ++k) {
+        const ProbRec &R = b->recs[k];
+        const OutRows orw = out_rows(R.nx, R.nc);
+        const float *base = fo + R.off_out;
+        const int nn = R.n, np = R.npad;
+        for (int i = 0; i < nn; ++i) {
+            for (int j = 0; j < R.nx; ++j) {
+                if (x) x[ox + (size_t)i * R.nx + j] = base[(size_t)(orw.x + j) * np + i];
+                if (lam) lam[ol + (size_t)i * R.nx + j] = base[(size_t)(orw.lam + j) * np + i];
+            }
+            for (int j = 0; j < NU; ++j)
+                if (u) u[ou + (size_t)i * NU + j] = base[(size_t)(orw.u + j) * np + i];
+            for (int c = 0; c < R.nc; ++c)
+                if (y) y[oy + (size_t)i * R.nc + c] = base[(size_t)(orw.y + c) * np + i];
+        }
+        ox += (size_t)nn * R.nx;
+        ol += (size_t)nn * R.nx;
+        ou += (size_t)nn * NU;
+        oy += (size_t)nn * R.nc;
+    }
+    if (stats) {
+        const Stats *s = at<const Stats>(b->stage, b->L.stats);
+        for (int k = 0; k < b->n; ++k) {
+            stats[k].status = s[k].status;
+            stats[k].inner_iters = s[k].inner_iters;
+            stats[k].outer_iters = s[k].outer_iters;
+            stats[k].ls_fail_total = s[k].ls_fail_total;
+            stats[k].ls_evals = s[k].ls_evals;
+            stats[k].reserved = 0;
+            stats[k].r_kkt = s[k].r_kkt;
+            stats[k].c = s[k].c;
+            stats[k].rho = s[k].rho;
+            stats[k].mu = s[k].mu;
+            stats[k].cycles_linearise = s[k].cyc_lin;
+            stats[k].cycles_backward = s[k].cyc_bwd;
+            stats[k].cycles_forward = s[k].cyc_fwd;
+            stats[k].cycles_linesearch = s[k].cyc_ls;
+            stats[k].cycles_total = s[k].cyc_total;
+        }
+    }
+    return BMPC_OK;
+}
+
+int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float **u, float **lam, float **y,
+                                int32_t *npad) {
+    if (!b || i < 0 || i >= b->n) return BMPC_ERR_INVALID;
+    const ProbRec &R = b->recs[i];
+    const OutRows orw = out_rows(R.nx, R.nc);
+    float *base = reinterpret_cast<float *>(b->data + b->L.out) + R.off_out;
+    if (x) *x = base + (size_t)orw.x * R.npad;
+    if (u) *u = base + (size_t)orw.u * R.npad;
+    if (lam) *lam = base + (size_t)orw.lam * R.npad;
+    if (y) *y = base + (size_t)orw.y * R.npad;
+    if (npad) *npad = R.npad;
+    return BMPC_OK;
+}
+
+void bmpc_destroy_batch(bmpc_batch *b) {
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->own_stage) std::free(b->stage);
+    delete b;
+}
+
+int bmpc_tree_bytes(const bmpc_tree_desc *desc, size_t *data_bytes, size_t *scratch_bytes, size_t *staging_bytes) {
+    return bmpc_batch_bytes(desc, 1, data_bytes, scratch_bytes, staging_bytes);
+}
+
+int bmpc_create_tree(const bmpc_tree_desc *desc, void *dev_data, size_t data_bytes, void *dev_scratch,
+                     size_t scratch_bytes, void *host_staging, size_t staging_bytes, void *stream, bmpc_tree **out) {
+    return bmpc_create_batch(desc, 1, dev_data, data_bytes, dev_scratch, scratch_bytes, host_staging, staging_bytes,
+                             stream, out);
+}
+
+int bmpc_set_problem(bmpc_tree *t, const bmpc_problem *problem) { return bmpc_set_problems(t, problem); }
+
+int bmpc_solve(bmpc_tree *t, const bmpc_opts *opts, bmpc_stats *stats) {
+    int st = bmpc_solve_batch(t, opts);
+    if (st != BMPC_OK || !stats) return st;
+    st = bmpc_get_solutions(t, nullptr, nullptr, nullptr, nullptr, stats);
+    return st != BMPC_OK ? st : stats->status;
+}
+
+int bmpc_get_solution(bmpc_tree *t, float *x, float *u, float *lam, float *y) {
+    return bmpc_get_solutions(t, x, u, lam, y, nullptr);
+}
+
+void bmpc_destroy_tree(bmpc_tree *t) { bmpc_destroy_batch(t); }
+
+const char *bmpc_status_str(int s) {
+    switch (s) {
+        case BMPC_OK: return "converged";
+        case BMPC_MAX_ITER: return "iteration cap reached";
+        case BMPC_LS_FAIL: return "line search failed three times in a row";
+        case BMPC_ERR_INVALID: return "invalid argument";
+        case BMPC_ERR_CUDA: return "CUDA error";
+        case BMPC_ERR_NUMERIC: return "numerical failure (H not positive definite or non-finite value)";
+        case BMPC_ERR_TIMEOUT: return "device wait timed out";
+        case BMPC_ERR_SPACE: return "arena or staging buffer too small";
+        default: return "unknown status";
+    }
+}
+
+const char *bmpc_version(void) { return "bmpc 0.1 sm_103a fp32"; }
+
+}  // extern "C"

@@ -1,0 +1,1118 @@
+/*
+ * Persistent FP32 solver kernel for branch MPC: the multiple-shooting
+ * augmented-Lagrangian iLQR method of arXiv 2506.13624 (Algorithm 1) over a
+ * scenario tree.  One thread block owns one problem at a time and takes the
+ * next problem from a device work queue when it finishes, so a single launch
+ * solves a whole batch of trees of uneven size.
+ *
+ * Per inner iteration the block runs, with a block barrier between phases:
+ *   linearise   every node in parallel: RK4 step with forward-mode Jacobians
+ *               A_n, B_n, cost gradient, PHR penalty gradient and its
+ *               Gauss-Newton Hessian (Sec. IV-A, Eq. AL);
+ *   kkt         defects d_m = f_p(m) - x_m, KKT residual of the relaxed problem
+ *               (Sec. IV-A stopping criterion) by a block max-reduction;
+ *   backward    the tree Riccati recursion, level by level from the leaves:
+ *               child value functions summed at branch points, then the
+ *               feedback law of Eq. (tree_feedback_laws) (Sec. III-A);
+ *   forward     the linear rollout, level by level from the root, and the
+ *               QP multipliers lam_m = P_m dx_m + p_m;
+ *   merit       phi(0), phi'(0) and the merit penalty mu (Eq. merit);
+ *   line search all step sizes alpha_i = 2^-i of a chunk evaluated in
+ *               parallel over (node, alpha), the largest one satisfying
+ *               Eq. (sufficient_decrease) is taken (Algorithm 1);
+ *   update      x, u, lam moved by alpha.
+ * After the inner loop the block evaluates the constraint violation c and
+ * applies the BCL update of (y_e, rho, omega, eta) (Sec. IV-B).
+ *
+ * Scalar control (rho, mu, omega, eta, counters) is replicated in every
+ * thread: block reductions return identical totals to all threads, so all
+ * threads take the same branches.  Reductions use a fixed order and are
+ * bitwise reproducible for a fixed block size.
+ */
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bmpc_layout.h"
+
+namespace bmpc {
+
+constexpr int MAX_BLOCK = 256;
+constexpr int MAX_WARPS = MAX_BLOCK / 32;
+constexpr int MAX_CHUNK = 16;
+
+struct Shared {
+    float red[MAX_WARPS][MAX_CHUNK + 1];
+    int flag;
+};
+
+/* ------------------------------------------------------------------ block reductions */
+template <int K>
+__device__ __forceinline__ void block_sum(float (&v)[K], Shared &sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh.red[warp][k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float s = 0.f;
+        for (int w = 0; w < nw; ++w) s += sh.red[w][k];
+        v[k] = s;
+    }
+}
+
+/* max of non-negative values; NaN is mapped to +inf so that it cannot vanish */
+__device__ __forceinline__ float block_max(float v, Shared &sh) {
+    if (!(v == v)) v = INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.red[warp][0] = v;
+    __syncthreads();
+    float m = 0.f;
+    for (int w = 0; w < nw; ++w) m = fmaxf(m, sh.red[w][0]);
+    return m;
+}
+
+/* ------------------------------------------------------------------ packed symmetric index */
+template <int NX>
+__host__ __device__ constexpr int sidx(int a, int b) {
+    return a <= b ? a * NX - a * (a - 1) / 2 + (b - a) : b * NX - b * (b - 1) / 2 + (a - b);
+}
+
+/* ------------------------------------------------------------------ dynamics */
+/* Continuous right-hand side and its Jacobians (dense arrays; compile-time zero
+ * entries are folded away after unrolling).  MODEL 0: kinematic bicycle, 1: dynamic
+ * bicycle with linear tyres and small steering angle. */
+template <int NX, int MODEL>
+__device__ __forceinline__ void rhs_jac(const float *prm, const float (&s)[NX], float a, float dl, float (&f)[NX],
+                                        float (&J)[NX][NX], float (&Ju)[NX][NU]) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) J[i][j] = 0.f;
+        Ju[i][0] = 0.f;
+        Ju[i][1] = 0.f;
+    }
+    if constexpr (MODEL == 0) {
+        const float L = prm[0];
+        float sp, cp;
+        sincosf(s[2], &sp, &cp);
+        const float td = tanf(dl);
+        const float v = s[3];
+        f[0] = v * cp;
+        f[1] = v * sp;
+        f[2] = v * td / L;
+        f[3] = a;
+        J[0][2] = -v * sp;
+        J[0][3] = cp;
+        J[1][2] = v * cp;
+        J[1][3] = sp;
+        J[2][3] = td / L;
+        Ju[2][1] = v * (1.f + td * td) / L;
+        Ju[3][0] = 1.f;
+    } else if constexpr (MODEL == 1) {
+        const float m = prm[1], Iz = prm[2], lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6];
+        const float vmin = prm[7], veps = prm[8];
+        const float psi = s[2], vx = s[3], vy = s[4], r = s[5];
+        const float dv = vx - vmin;
+        const float w = sqrtf(dv * dv + veps * veps);
+        const float vb = 0.5f * (vx + vmin + w);
+        const float dvb = 0.5f * (1.f + dv / w);
+        const float ivb = 1.f / vb;
+        const float tf = (vy + lf * r) * ivb, tr = (vy - lr * r) * ivb;
+        const float af = atanf(tf) - dl, ar = atanf(tr);
+        const float Ff = -Cf * af, Fr = -Cr * ar;
+        float sp, cp;
+        sincosf(psi, &sp, &cp);
+        f[0] = vx * cp - vy * sp;
+        f[1] = vx * sp + vy * cp;
+        f[2] = r;
+        f[3] = a + r * vy;
+        f[4] = (Ff + Fr) / m - r * vx;
+        f[5] = (lf * Ff - lr * Fr) / Iz;
+        const float gf = 1.f / (1.f + tf * tf), gr = 1.f / (1.f + tr * tr);
+        const float daf_vx = -gf * tf * ivb * dvb, daf_vy = gf * ivb, daf_r = gf * lf * ivb;
+        const float dar_vx = -gr * tr * ivb * dvb, dar_vy = gr * ivb, dar_r = -gr * lr * ivb;
+        const float dFf_vx = -Cf * daf_vx, dFf_vy = -Cf * daf_vy, dFf_r = -Cf * daf_r, dFf_d = Cf;
+        const float dFr_vx = -Cr * dar_vx, dFr_vy = -Cr * dar_vy, dFr_r = -Cr * dar_r;
+        J[0][2] = -vx * sp - vy * cp;
+        J[0][3] = cp;
+        J[0][4] = -sp;
+        J[1][2] = vx * cp - vy * sp;
+        J[1][3] = sp;
+        J[1][4] = cp;
+        J[2][5] = 1.f;
+        J[3][4] = r;
+        J[3][5] = vy;
+        Ju[3][0] = 1.f;
+        J[4][3] = (dFf_vx + dFr_vx) / m - r;
+        J[4][4] = (dFf_vy + dFr_vy) / m;
+        J[4][5] = (dFf_r + dFr_r) / m - vx;
+        Ju[4][1] = dFf_d / m;
+        J[5][3] = (lf * dFf_vx - lr * dFr_vx) / Iz;
+        J[5][4] = (lf * dFf_vy - lr * dFr_vy) / Iz;
+        J[5][5] = (lf * dFf_r - lr * dFr_r) / Iz;
+        Ju[5][1] = lf * dFf_d / Iz;
+    }
+}
+
+template <int NX, int MODEL>
+__device__ __forceinline__ void rhs(const float *prm, const float (&s)[NX], float a, float dl, float (&f)[NX]) {
+    if constexpr (MODEL == 0) {
+        const float L = prm[0];
+        float sp, cp;
+        sincosf(s[2], &sp, &cp);
+        f[0] = s[3] * cp;
+        f[1] = s[3] * sp;
+        f[2] = s[3] * tanf(dl) / L;
+        f[3] = a;
+    } else if constexpr (MODEL == 1) {
+        const float m = prm[1], Iz = prm[2], lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6];
+        const float vmin = prm[7], veps = prm[8];
+        const float vx = s[3], vy = s[4], r = s[5];
+        const float dv = vx - vmin;
+        const float vb = 0.5f * (vx + vmin + sqrtf(dv * dv + veps * veps));
+        const float ivb = 1.f / vb;
+        const float Ff = -Cf * (atanf((vy + lf * r) * ivb) - dl);
+        const float Fr = -Cr * atanf((vy - lr * r) * ivb);
+        float sp, cp;
+        sincosf(s[2], &sp, &cp);
+        f[0] = vx * cp - vy * sp;
+        f[1] = vx * sp + vy * cp;
+        f[2] = r;
+        f[3] = a + r * vy;
+        f[4] = (Ff + Fr) / m - r * vx;
+        f[5] = (lf * Ff - lr * Fr) / Iz;
+    }
+}
+
+/* x+ = f(x, u) with A = df/dx, B = df/du: n_sub classical RK4 steps, Jacobians by the
+ * forward-mode chain rule through every stage (tangent matrix S = dz/d(x, u)). */
+template <int NX, int MODEL>
+__device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], const float (&u)[NU],
+                                        float (&xn)[NX], float (&A)[NX][NX], float (&B)[NX][NU]) {
+    if constexpr (MODEL == 2) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < NX; ++j) {
+                A[i][j] = R.Alin[i * NX + j];
+                s += A[i][j] * x[j];
+            }
+#pragma unroll
+            for (int j = 0; j < NU; ++j) {
+                B[i][j] = R.Blin[i * NU + j];
+                s += B[i][j] * u[j];
+            }
+            xn[i] = s;
+        }
+    } else {
+        constexpr int NZ = NX + NU;
+        float S[NX][NZ];
+#pragma unroll
+        for (int i = 0; i < NX; ++i)
+#pragma unroll
+            for (int j = 0; j < NZ; ++j) S[i][j] = (i == j) ? 1.f : 0.f;
+        float z[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) z[i] = x[i];
+        const int nsub = max(1, (int)R.params[9]);
+        const float h = R.dt / (float)nsub;
+        for (int sub = 0; sub < nsub; ++sub) {
+            float ks[NX], Ds[NX][NZ], kp[NX], Dp[NX][NZ];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                ks[i] = 0.f;
+                kp[i] = 0.f;
+#pragma unroll
+                for (int j = 0; j < NZ; ++j) {
+                    Ds[i][j] = 0.f;
+                    Dp[i][j] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                const float c = (st == 0) ? 0.f : (st == 3 ? 1.f : 0.5f);
+                const float wg = (st == 0 || st == 3) ? 1.f : 2.f;
+                float zs[NX];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) zs[i] = z[i] + c * h * kp[i];
+                float f[NX], J[NX][NX], Ju[NX][NU];
+                rhs_jac<NX, MODEL>(R.params, zs, u[0], u[1], f, J, Ju);
+                float D[NX][NZ];
+#pragma unroll
+                for (int i = 0; i < NX; ++i)
+#pragma unroll
+                    for (int j = 0; j < NZ; ++j) {
+                        float acc = (j >= NX) ? Ju[i][j - NX] : 0.f;
+#pragma unroll
+                        for (int k = 0; k < NX; ++k) acc += J[i][k] * (S[k][j] + c * h * Dp[k][j]);
+                        D[i][j] = acc;
+                    }
+#pragma unroll
+                for (int i = 0; i < NX; ++i) {
+                    ks[i] += wg * f[i];
+                    kp[i] = f[i];
+#pragma unroll
+                    for (int j = 0; j < NZ; ++j) {
+                        Ds[i][j] += wg * D[i][j];
+                        Dp[i][j] = D[i][j];
+                    }
+                }
+            }
+            const float h6 = h / 6.f;
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                z[i] += h6 * ks[i];
+#pragma unroll
+                for (int j = 0; j < NZ; ++j) S[i][j] += h6 * Ds[i][j];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            xn[i] = z[i];
+#pragma unroll
+            for (int j = 0; j < NX; ++j) A[i][j] = S[i][j];
+#pragma unroll
+            for (int j = 0; j < NU; ++j) B[i][j] = S[i][NX + j];
+        }
+    }
+}
+
+template <int NX, int MODEL>
+__device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], const float (&u)[NU], float (&xn)[NX]) {
+    if constexpr (MODEL == 2) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < NX; ++j) s += R.Alin[i * NX + j] * x[j];
+#pragma unroll
+            for (int j = 0; j < NU; ++j) s += R.Blin[i * NU + j] * u[j];
+            xn[i] = s;
+        }
+    } else {
+        float z[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) z[i] = x[i];
+        const int nsub = max(1, (int)R.params[9]);
+        const float h = R.dt / (float)nsub;
+        for (int sub = 0; sub < nsub; ++sub) {
+            float ks[NX], kp[NX];
+#pragma unroll
+            for (int i = 0; i < NX; ++i) {
+                ks[i] = 0.f;
+                kp[i] = 0.f;
+            }
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                const float c = (st == 0) ? 0.f : (st == 3 ? 1.f : 0.5f);
+                const float wg = (st == 0 || st == 3) ? 1.f : 2.f;
+                float zs[NX], f[NX];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) zs[i] = z[i] + c * h * kp[i];
+                rhs<NX, MODEL>(R.params, zs, u[0], u[1], f);
+#pragma unroll
+                for (int i = 0; i < NX; ++i) {
+                    ks[i] += wg * f[i];
+                    kp[i] = f[i];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NX; ++i) z[i] += (h / 6.f) * ks[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NX; ++i) xn[i] = z[i];
+    }
+}
+
+/* ------------------------------------------------------------------ problem view */
+template <int NX>
+struct View {
+    int n, np, nc, nobs;
+    bool box, lane;
+    /* int rows */
+    const int32_t *parent, *nchild, *fchild, *stage, *leaf, *sstart;
+    /* inputs */
+    const float *xref, *w, *obs, *wx, *wu, *wl, *wy;
+    /* outputs */
+    float *X, *U, *L, *Y;
+    /* scratch */
+    float *A, *B, *f, *d, *q, *r, *hq, *hr, *K, *k, *P, *p, *dx, *du, *lq, *nv;
+
+    __device__ View(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout, float *fs) {
+        n = R.n;
+        np = R.npad;
+        nc = R.nc;
+        nobs = R.n_obs;
+        box = R.box_on != 0;
+        lane = R.lane_on != 0;
+        parent = ib + IntRows::parent * np;
+        nchild = ib + IntRows::nchild * np;
+        fchild = ib + IntRows::fchild * np;
+        stage = ib + IntRows::stage * np;
+        leaf = ib + IntRows::leaf * np;
+        sstart = ib + IntRows::stage_start * np;
+        const InRows ir = in_rows(NX, nobs);
+        xref = fin + (size_t)ir.xref * np;
+        w = fin + (size_t)ir.weight * np;
+        obs = fin + (size_t)ir.obs * np;
+        const WarmRows wr = warm_rows(NX, nc);
+        wx = fw + (size_t)wr.wx * np;
+        wu = fw + (size_t)wr.wu * np;
+        wl = fw + (size_t)wr.wl * np;
+        wy = fw + (size_t)wr.wy * np;
+        const OutRows orw = out_rows(NX, nc);
+        X = fout + (size_t)orw.x * np;
+        U = fout + (size_t)orw.u * np;
+        L = fout + (size_t)orw.lam * np;
+        Y = fout + (size_t)orw.y * np;
+        const ScrRows s = scr_rows(NX);
+        A = fs + (size_t)s.A * np;
+        B = fs + (size_t)s.B * np;
+        f = fs + (size_t)s.f * np;
+        d = fs + (size_t)s.d * np;
+        q = fs + (size_t)s.q * np;
+        r = fs + (size_t)s.r * np;
+        hq = fs + (size_t)s.hq * np;
+        hr = fs + (size_t)s.hr * np;
+        K = fs + (size_t)s.K * np;
+        k = fs + (size_t)s.k * np;
+        P = fs + (size_t)s.P * np;
+        p = fs + (size_t)s.p * np;
+        dx = fs + (size_t)s.dx * np;
+        du = fs + (size_t)s.du * np;
+        lq = fs + (size_t)s.lq * np;
+        nv = fs + (size_t)s.nv * np;
+    }
+    __device__ __forceinline__ void load_x(const float *base, int i, float (&v)[NX]) const {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) v[j] = base[(size_t)j * np + i];
+    }
+    __device__ __forceinline__ void store_x(float *base, int i, const float (&v)[NX]) const {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) base[(size_t)j * np + i] = v[j];
+    }
+    __device__ __forceinline__ void load_u(const float *base, int i, float (&v)[NU]) const {
+        v[0] = base[i];
+        v[1] = base[(size_t)np + i];
+    }
+    __device__ __forceinline__ void store_u(float *base, int i, const float (&v)[NU]) const {
+        base[i] = v[0];
+        base[(size_t)np + i] = v[1];
+    }
+};
+
+/* ------------------------------------------------------------------ node cost + constraints */
+/* Node part of L_a (Eq. AL) at (x, u) with multipliers y and penalty rho.  With grad != 0 also
+ * the gradient (q, r) and the Gauss-Newton Hessian terms of the penalty: hq = (xx, xy, yy) on
+ * the position block, hr on the input diagonal.  mode: 0 = value only. */
+template <int NX, bool GRAD>
+__device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, int i, bool is_leaf,
+                                         const float (&x)[NX], const float (&u)[NU], float rho, float (&q)[NX],
+                                         float (&r)[NU], float (&hq)[3], float (&hr)[NU]) {
+    const float w = V.w[i];
+    const float *Qd = is_leaf ? R.QNw : R.Qw;
+    float la = 0.f;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+        const float e = x[j] - V.xref[(size_t)j * V.np + i];
+        la += 0.5f * w * Qd[j] * e * e;
+        if (GRAD) q[j] = w * Qd[j] * e;
+    }
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+        if (GRAD) {
+            r[j] = 0.f;
+            hr[j] = 0.f;
+        }
+        if (!is_leaf) {
+            la += 0.5f * w * R.Rw[j] * u[j] * u[j];
+            if (GRAD) r[j] = w * R.Rw[j] * u[j];
+        }
+    }
+    if (GRAD) hq[0] = hq[1] = hq[2] = 0.f;
+    int row = 0;
+    if (V.box) {
+        if (!is_leaf) {
+#pragma unroll
+            for (int j = 0; j < NU; ++j) {
+#pragma unroll
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    const int rr = row + sgn * NU + j;
+                    const float g = sgn == 0 ? u[j] - R.u_hi[j] : R.u_lo[j] - u[j];
+                    const float s = V.Y[(size_t)rr * V.np + i] + rho * g;
+                    if (s > 0.f) {
+                        la += 0.5f * s * s / rho;
+                        if (GRAD) {
+                            r[j] += sgn == 0 ? s : -s;
+                            hr[j] += rho;
+                        }
+                    }
+                }
+            }
+        }
+        row += 2 * NU;
+    }
+    if (i != 0) {
+        for (int o = 0; o < V.nobs; ++o) {
+            const float *ob = V.obs + (size_t)(5 * o) * V.np + i;
+            const float cx = ob[0], cy = ob[V.np], hd = ob[2 * (size_t)V.np];
+            const float ea = ob[3 * (size_t)V.np], eb = ob[4 * (size_t)V.np];
+            float sh, ch;
+            sincosf(hd, &sh, &ch);
+            const float dxo = x[0] - cx, dyo = x[1] - cy;
+            const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
+            const float ia2 = 1.f / (ea * ea), ib2 = 1.f / (eb * eb);
+            const float rr2 = sqrtf(dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f);
+            const float g = 1.f - rr2;
+            const float s = V.Y[(size_t)(row + o) * V.np + i] + rho * g;
+            if (s > 0.f) {
+                la += 0.5f * s * s / rho;
+                if (GRAD) {
+                    const float irr = 1.f / rr2;
+                    const float gx = -(dpar * ia2 * ch - dper * ib2 * sh) * irr;
+                    const float gy = -(dpar * ia2 * sh + dper * ib2 * ch) * irr;
+                    q[0] += s * gx;
+                    q[1] += s * gy;
+                    hq[0] += rho * gx * gx;
+                    hq[1] += rho * gx * gy;
+                    hq[2] += rho * gy * gy;
+                }
+            }
+        }
+        row += V.nobs;
+        if (V.lane) {
+            const float g0 = x[1] - R.lane_hi, g1 = R.lane_lo - x[1];
+            const float s0 = V.Y[(size_t)row * V.np + i] + rho * g0;
+            const float s1 = V.Y[(size_t)(row + 1) * V.np + i] + rho * g1;
+            if (s0 > 0.f) {
+                la += 0.5f * s0 * s0 / rho;
+                if (GRAD) {
+                    q[1] += s0;
+                    hq[2] += rho;
+                }
+            }
+            if (s1 > 0.f) {
+                la += 0.5f * s1 * s1 / rho;
+                if (GRAD) {
+                    q[1] -= s1;
+                    hq[2] += rho;
+                }
+            }
+        }
+    }
+    return la;
+}
+
+/* Constraint rows g (existing rows only, others skipped): calls fn(row, g). */
+template <int NX, typename Fn>
+__device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX> &V, int i, bool is_leaf,
+                                                const float (&x)[NX], const float (&u)[NU], Fn fn) {
+    int row = 0;
+    if (V.box) {
+        if (!is_leaf) {
+#pragma unroll
+            for (int j = 0; j < NU; ++j) {
+                fn(row + j, u[j] - R.u_hi[j]);
+                fn(row + NU + j, R.u_lo[j] - u[j]);
+            }
+        }
+        row += 2 * NU;
+    }
+    if (i != 0) {
+        for (int o = 0; o < V.nobs; ++o) {
+            const float *ob = V.obs + (size_t)(5 * o) * V.np + i;
+            const float cx = ob[0], cy = ob[V.np], hd = ob[2 * (size_t)V.np];
+            const float ea = ob[3 * (size_t)V.np], eb = ob[4 * (size_t)V.np];
+            float sh, ch;
+            sincosf(hd, &sh, &ch);
+            const float dxo = x[0] - cx, dyo = x[1] - cy;
+            const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
+            fn(row + o, 1.f - sqrtf(dpar * dpar / (ea * ea) + dper * dper / (eb * eb) + 1e-6f));
+        }
+        row += V.nobs;
+        if (V.lane) {
+            fn(row, x[1] - R.lane_hi);
+            fn(row + 1, R.lane_lo - x[1]);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ the per-problem solver */
+template <int NX, int MODEL>
+__device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
+                              float *fs, Stats *stat, const KOpts &O, Shared &sh) {
+    constexpr int NS = nsym(NX);
+    const View<NX> V(R, ib, fin, fw, fout, fs);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n = V.n, np = V.np, nc = V.nc;
+    const int n_stage = R.n_stage;
+    long long t_start = clock64(), c_lin = 0, c_bwd = 0, c_fwd = 0, c_ls = 0;
+
+    /* ---- initial iterate: warm start or the cold start of Sec. V-B */
+    for (int i = tid; i < n; i += nt) {
+        const bool is_leaf = V.nchild[i] == 0;
+        float x[NX], u[NU], l[NX];
+        if (R.has_warm) {
+            V.load_x(V.wx, i, x);
+            V.load_u(V.wu, i, u);
+            V.load_x(V.wl, i, l);
+            for (int c = 0; c < nc; ++c) V.Y[(size_t)c * np + i] = V.wy[(size_t)c * np + i];
+        } else {
+            const int lf = V.leaf[i];
+            const float s = V.stage[lf] > 0 ? (float)V.stage[i] / (float)V.stage[lf] : 0.f;
+#pragma unroll
+            for (int j = 0; j < NX; ++j) x[j] = R.x0[j] + s * (V.xref[(size_t)j * np + lf] - R.x0[j]);
+            u[0] = u[1] = 0.f;
+#pragma unroll
+            for (int j = 0; j < NX; ++j) l[j] = 0.f;
+            for (int c = 0; c < nc; ++c) V.Y[(size_t)c * np + i] = 0.f;
+        }
+        if (i == 0) {
+#pragma unroll
+            for (int j = 0; j < NX; ++j) {
+                x[j] = R.x0[j];
+                l[j] = 0.f;
+            }
+        }
+        if (is_leaf) u[0] = u[1] = 0.f;
+        V.store_x(V.X, i, x);
+        V.store_u(V.U, i, u);
+        V.store_x(V.L, i, l);
+    }
+    __syncthreads();
+
+    float rho = O.rho0, mu = O.mu0, omega = O.omega0, eta = O.eta0;
+    float r_kkt = INFINITY, cviol = INFINITY;
+    int inner = 0, outer = 0, ls_fail = 0, ls_fail_total = 0, ls_evals = 0, status = 1 /* MAX_ITER */;
+    const int G = (O.ls_chunk <= 0 || O.ls_chunk > MAX_CHUNK) ? min(O.n_alpha, MAX_CHUNK) : O.ls_chunk;
+
+    while (outer < O.max_outer) {
+        ++outer;
+        for (;;) {
+            /* ===== linearise + quadratise at the current point */
+            long long t0 = clock64();
+            for (int i = tid; i < n; i += nt) {
+                const bool is_leaf = V.nchild[i] == 0;
+                float x[NX], u[NU], q[NX], r[NU], hq[3], hr[NU];
+                V.load_x(V.X, i, x);
+                V.load_u(V.U, i, u);
+                const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, rho, q, r, hq, hr);
+                V.store_x(V.q, i, q);
+                V.store_u(V.r, i, r);
+                V.hq[i] = hq[0];
+                V.hq[(size_t)np + i] = hq[1];
+                V.hq[2 * (size_t)np + i] = hq[2];
+                V.store_u(V.hr, i, hr);
+                V.nv[i] = la;
+                if (!is_leaf) {
+                    float xn[NX], A[NX][NX], B[NX][NU];
+                    dyn_lin<NX, MODEL>(R, x, u, xn, A, B);
+                    V.store_x(V.f, i, xn);
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+                        for (int b = 0; b < NX; ++b) V.A[(size_t)(a * NX + b) * np + i] = A[a][b];
+#pragma unroll
+                        for (int b = 0; b < NU; ++b) V.B[(size_t)(a * NU + b) * np + i] = B[a][b];
+                    }
+                }
+            }
+            __syncthreads();
+            /* ===== defects and the KKT residual of the relaxed problem */
+            float rk = 0.f;
+            float sums[3] = {0.f, 0.f, 0.f};   /* L_a, lam'd, |d|^2 */
+            for (int i = tid; i < n; i += nt) {
+                const int nch = V.nchild[i], fc = V.fchild[i];
+                float lsum[NX];
+#pragma unroll
+                for (int j = 0; j < NX; ++j) lsum[j] = 0.f;
+                for (int m = fc; m < fc + nch; ++m)
+#pragma unroll
+                    for (int j = 0; j < NX; ++j) lsum[j] += V.L[(size_t)j * np + m];
+                float ld = 0.f, dd = 0.f;
+                if (i != 0) {
+                    const int pa = V.parent[i];
+                    float gx[NX];
+#pragma unroll
+                    for (int j = 0; j < NX; ++j) {
+                        const float dj = V.f[(size_t)j * np + pa] - V.X[(size_t)j * np + i];
+                        V.d[(size_t)j * np + i] = dj;
+                        const float lj = V.L[(size_t)j * np + i];
+                        ld += lj * dj;
+                        dd += dj * dj;
+                        rk = fmaxf(rk, fabsf(dj));
+                        gx[j] = V.q[(size_t)j * np + i] - lj;
+                    }
+                    if (nch) {
+#pragma unroll
+                        for (int a = 0; a < NX; ++a)
+#pragma unroll
+                            for (int b = 0; b < NX; ++b) gx[b] += V.A[(size_t)(a * NX + b) * np + i] * lsum[a];
+                    }
+#pragma unroll
+                    for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
+                }
+                if (nch) {
+#pragma unroll
+                    for (int b = 0; b < NU; ++b) {
+                        float gu = V.r[(size_t)b * np + i];
+#pragma unroll
+                        for (int a = 0; a < NX; ++a) gu += V.B[(size_t)(a * NU + b) * np + i] * lsum[a];
+                        rk = fmaxf(rk, fabsf(gu));
+                    }
+                }
+                if (!(rk == rk)) rk = INFINITY;
+                V.nv[(size_t)np + i] = ld;
+                V.nv[2 * (size_t)np + i] = dd;
+                sums[0] += V.nv[i];
+                sums[1] += ld;
+                sums[2] += dd;
+            }
+            r_kkt = block_max(rk, sh);
+            block_sum<3>(sums, sh);
+            c_lin += clock64() - t0;
+            if (!(r_kkt < INFINITY) || !(fabsf(sums[0]) < INFINITY)) {
+                status = -3;
+                goto done;
+            }
+            if (r_kkt <= omega) break;
+            if (inner >= O.max_iters) goto done;
+
+            /* ===== backward: tree Riccati recursion, leaves to root */
+            t0 = clock64();
+            if (tid == 0) sh.flag = 0;
+            __syncthreads();
+            for (int st = n_stage - 1; st >= 0; --st) {
+                const int s0 = V.sstart[st], s1 = V.sstart[st + 1];
+                for (int i = s0 + tid; i < s1; i += nt) {
+                    const int nch = V.nchild[i], fc = V.fchild[i];
+                    const float w = V.w[i];
+                    float q[NX];
+                    V.load_x(V.q, i, q);
+                    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+                    if (nch == 0) {
+#pragma unroll
+                        for (int a = 0; a < NX; ++a)
+#pragma unroll
+                            for (int b = a; b < NX; ++b) {
+                                float v = (a == b) ? w * R.QNw[a] : 0.f;
+                                if (a == 0 && b == 0) v += hxx;
+                                if (a == 0 && b == 1) v += hxy;
+                                if (a == 1 && b == 1) v += hyy;
+                                V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
+                            }
+                        V.store_x(V.p, i, q);
+                        continue;
+                    }
+                    /* child sums: Pbar = sum P_m, pbar = sum (p_m + P_m d_m) */
+                    float Pb[NS], pb[NX];
+#pragma unroll
+                    for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) pb[a] = 0.f;
+                    for (int m = fc; m < fc + nch; ++m) {
+                        float Pm[NS], dm[NX];
+#pragma unroll
+                        for (int e = 0; e < NS; ++e) {
+                            Pm[e] = V.P[(size_t)e * np + m];
+                            Pb[e] += Pm[e];
+                        }
+                        V.load_x(V.d, m, dm);
+#pragma unroll
+                        for (int a = 0; a < NX; ++a) {
+                            float v = V.p[(size_t)a * np + m];
+#pragma unroll
+                            for (int b = 0; b < NX; ++b) v += Pm[sidx<NX>(a, b)] * dm[b];
+                            pb[a] += v;
+                        }
+                    }
+                    float A[NX][NX], B[NX][NU];
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+                        for (int b = 0; b < NX; ++b) A[a][b] = V.A[(size_t)(a * NX + b) * np + i];
+#pragma unroll
+                        for (int b = 0; b < NU; ++b) B[a][b] = V.B[(size_t)(a * NU + b) * np + i];
+                    }
+                    /* PA = Pbar A, PB = Pbar B */
+                    float PA[NX][NX], PB[NX][NU];
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+                        for (int b = 0; b < NX; ++b) {
+                            float v = 0.f;
+#pragma unroll
+                            for (int t = 0; t < NX; ++t) v += Pb[sidx<NX>(a, t)] * A[t][b];
+                            PA[a][b] = v;
+                        }
+#pragma unroll
+                        for (int b = 0; b < NU; ++b) {
+                            float v = 0.f;
+#pragma unroll
+                            for (int t = 0; t < NX; ++t) v += Pb[sidx<NX>(a, t)] * B[t][b];
+                            PB[a][b] = v;
+                        }
+                    }
+                    /* H blocks: Quu = R + B'PB, Qux = B'PA, qu = r + B'pbar, qx = q + A'pbar */
+                    float Quu[NU][NU], Qux[NU][NX], qu[NU], qx[NX];
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) {
+#pragma unroll
+                        for (int b = 0; b < NU; ++b) {
+                            float v = (a == b) ? w * R.Rw[a] + V.hr[(size_t)a * np + i] : 0.f;
+#pragma unroll
+                            for (int t = 0; t < NX; ++t) v += B[t][a] * PB[t][b];
+                            Quu[a][b] = v;
+                        }
+#pragma unroll
+                        for (int b = 0; b < NX; ++b) {
+                            float v = 0.f;
+#pragma unroll
+                            for (int t = 0; t < NX; ++t) v += B[t][a] * PA[t][b];
+                            Qux[a][b] = v;
+                        }
+                        float v = V.r[(size_t)a * np + i];
+#pragma unroll
+                        for (int t = 0; t < NX; ++t) v += B[t][a] * pb[t];
+                        qu[a] = v;
+                    }
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) {
+                        float v = q[a];
+#pragma unroll
+                        for (int t = 0; t < NX; ++t) v += A[t][a] * pb[t];
+                        qx[a] = v;
+                    }
+                    /* Cholesky of the 2x2 H_n, K = -H^-1 Qux, k = -H^-1 qu */
+                    const float l00s = Quu[0][0];
+                    const float l00 = sqrtf(fmaxf(l00s, 0.f));
+                    const float l10 = Quu[1][0] / l00;
+                    const float l11s = Quu[1][1] - l10 * l10;
+                    if (!(l00s > 0.f) || !(l11s > 0.f)) sh.flag = 1;
+                    const float l11 = sqrtf(fmaxf(l11s, 0.f));
+                    float Kn[NU][NX], kn[NU];
+#pragma unroll
+                    for (int b = 0; b < NX + 1; ++b) {
+                        const float rhs0 = (b < NX) ? Qux[0][b] : qu[0];
+                        const float rhs1 = (b < NX) ? Qux[1][b] : qu[1];
+                        const float z0 = rhs0 / l00;
+                        const float z1 = (rhs1 - l10 * z0) / l11;
+                        const float s1 = z1 / l11;
+                        const float s0 = (z0 - l10 * s1) / l00;
+                        if (b < NX) {
+                            Kn[0][b] = -s0;
+                            Kn[1][b] = -s1;
+                        } else {
+                            kn[0] = -s0;
+                            kn[1] = -s1;
+                        }
+                    }
+                    /* P = Qxx + Qux'K with Qxx = Q + A'PA; p = qx + Qux'k */
+#pragma unroll
+                    for (int a = 0; a < NX; ++a)
+#pragma unroll
+                        for (int b = a; b < NX; ++b) {
+                            float v = (a == b) ? w * R.Qw[a] : 0.f;
+                            if (a == 0 && b == 0) v += hxx;
+                            if (a == 0 && b == 1) v += hxy;
+                            if (a == 1 && b == 1) v += hyy;
+#pragma unroll
+                            for (int t = 0; t < NX; ++t) v += A[t][a] * PA[t][b];
+#pragma unroll
+                            for (int t = 0; t < NU; ++t) v += Qux[t][a] * Kn[t][b];
+                            V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
+                        }
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) {
+                        float v = qx[a];
+#pragma unroll
+                        for (int t = 0; t < NU; ++t) v += Qux[t][a] * kn[t];
+                        V.p[(size_t)a * np + i] = v;
+                    }
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) {
+#pragma unroll
+                        for (int b = 0; b < NX; ++b) V.K[(size_t)(a * NX + b) * np + i] = Kn[a][b];
+                        V.k[(size_t)a * np + i] = kn[a];
+                    }
+                }
+                __syncthreads();
+            }
+            c_bwd += clock64() - t0;
+            if (sh.flag) {
+                status = -3;
+                goto done;
+            }
+
+            /* ===== forward: linear rollout from the root, QP multipliers */
+            t0 = clock64();
+            float dir[3] = {0.f, 0.f, 0.f};   /* grad'dz, dz'W dz, (dlam - lam)'d */
+            for (int st = 0; st < n_stage; ++st) {
+                const int s0 = V.sstart[st], s1 = V.sstart[st + 1];
+                for (int i = s0 + tid; i < s1; i += nt) {
+                    const int nch = V.nchild[i];
+                    const float w = V.w[i];
+                    float dxv[NX], duv[NU] = {0.f, 0.f};
+                    if (i == 0) {
+#pragma unroll
+                        for (int j = 0; j < NX; ++j) dxv[j] = 0.f;
+                    } else {
+                        const int pa = V.parent[i];
+                        float dxp[NX], dup[NU];
+                        V.load_x(V.dx, pa, dxp);
+                        V.load_u(V.du, pa, dup);
+#pragma unroll
+                        for (int a = 0; a < NX; ++a) {
+                            float v = V.d[(size_t)a * np + i];
+#pragma unroll
+                            for (int b = 0; b < NX; ++b) v += V.A[(size_t)(a * NX + b) * np + pa] * dxp[b];
+#pragma unroll
+                            for (int b = 0; b < NU; ++b) v += V.B[(size_t)(a * NU + b) * np + pa] * dup[b];
+                            dxv[a] = v;
+                        }
+                    }
+                    if (nch) {
+#pragma unroll
+                        for (int a = 0; a < NU; ++a) {
+                            float v = V.k[(size_t)a * np + i];
+#pragma unroll
+                            for (int b = 0; b < NX; ++b) v += V.K[(size_t)(a * NX + b) * np + i] * dxv[b];
+                            duv[a] = v;
+                        }
+                    }
+                    V.store_x(V.dx, i, dxv);
+                    V.store_u(V.du, i, duv);
+                    /* directional terms of the merit */
+                    const float *Qd = nch ? R.Qw : R.QNw;
+                    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) {
+                        dir[0] += V.q[(size_t)a * np + i] * dxv[a];
+                        dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+                    }
+                    dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
+                    if (nch) {
+#pragma unroll
+                        for (int a = 0; a < NU; ++a) {
+                            dir[0] += V.r[(size_t)a * np + i] * duv[a];
+                            dir[1] += (w * R.Rw[a] + V.hr[(size_t)a * np + i]) * duv[a] * duv[a];
+                        }
+                    }
+                    if (i != 0) {
+#pragma unroll
+                        for (int a = 0; a < NX; ++a) {
+                            float v = V.p[(size_t)a * np + i];
+#pragma unroll
+                            for (int b = 0; b < NX; ++b) v += V.P[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
+                            V.lq[(size_t)a * np + i] = v;
+                            const float lam = V.L[(size_t)a * np + i];
+                            dir[2] += ((v - lam) - lam) * V.d[(size_t)a * np + i];
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            block_sum<3>(dir, sh);
+            c_fwd += clock64() - t0;
+
+            /* ===== merit penalty mu and phi(0), phi'(0) */
+            t0 = clock64();
+            const float La0 = sums[0], ld0 = sums[1], dd0 = sums[2];
+            const float dphi0 = dir[0] + dir[2];
+            if (dd0 > 0.f && dphi0 - mu * dd0 > -0.5f * dir[1]) {
+                const float need = 2.f * (dphi0 + 0.5f * dir[1]) / dd0;
+                if (need > mu) mu = need;
+            }
+            const float phi0 = La0 + ld0 + 0.5f * mu * dd0;
+            const float dphi = dphi0 - mu * dd0;
+
+            /* ===== line search over alpha_i = 2^-i in chunks of G evaluated in parallel */
+            float alpha = ldexpf(1.f, -(O.n_alpha - 1));
+            bool accepted = false;
+            for (int a0 = 0; a0 < O.n_alpha && !accepted; a0 += G) {
+                float acc[MAX_CHUNK];
+#pragma unroll
+                for (int a = 0; a < MAX_CHUNK; ++a) acc[a] = 0.f;
+                for (int i = tid; i < n; i += nt) {
+                    const int nch = V.nchild[i], fc = V.fchild[i];
+                    const bool is_leaf = nch == 0;
+                    float x[NX], u[NU], dxv[NX], duv[NU];
+                    V.load_x(V.X, i, x);
+                    V.load_u(V.U, i, u);
+                    V.load_x(V.dx, i, dxv);
+                    V.load_u(V.du, i, duv);
+                    float base = V.nv[i];
+                    for (int m = fc; m < fc + nch; ++m) base += V.nv[(size_t)np + m] + 0.5f * mu * V.nv[2 * (size_t)np + m];
+#pragma unroll
+                    for (int a = 0; a < MAX_CHUNK; ++a) {
+                        if (a >= G || a0 + a >= O.n_alpha) break;
+                        const float al = ldexpf(1.f, -(a0 + a));
+                        float xt[NX], ut[NU], qd[NX], rd[NU], hqd[3], hrd[NU];
+#pragma unroll
+                        for (int j = 0; j < NX; ++j) xt[j] = x[j] + al * dxv[j];
+                        ut[0] = u[0] + al * duv[0];
+                        ut[1] = u[1] + al * duv[1];
+                        float v = node_la<NX, false>(R, V, i, is_leaf, xt, ut, rho, qd, rd, hqd, hrd);
+                        if (!is_leaf) {
+                            float ft[NX];
+                            dyn<NX, MODEL>(R, xt, ut, ft);
+                            for (int m = fc; m < fc + nch; ++m) {
+#pragma unroll
+                                for (int j = 0; j < NX; ++j) {
+                                    const float lm = V.L[(size_t)j * np + m];
+                                    const float ltj = lm + al * (V.lq[(size_t)j * np + m] - lm);
+                                    const float dm = ft[j] - (V.X[(size_t)j * np + m] + al * V.dx[(size_t)j * np + m]);
+                                    v += ltj * dm + 0.5f * mu * dm * dm;
+                                }
+                            }
+                        }
+                        acc[a] += v - base;
+                    }
+                }
+                block_sum<MAX_CHUNK>(acc, sh);
+                ls_evals += min(G, O.n_alpha - a0);
+#pragma unroll
+                for (int a = 0; a < MAX_CHUNK; ++a) {
+                    if (a >= G || a0 + a >= O.n_alpha || accepted) continue;
+                    const float al = ldexpf(1.f, -(a0 + a));
+                    if (acc[a] <= O.beta * al * dphi + O.ls_rel_eps * fabsf(phi0)) {
+                        alpha = al;
+                        accepted = true;
+                    }
+                }
+            }
+            if (accepted) ls_fail = 0;
+            else {
+                ++ls_fail;
+                ++ls_fail_total;
+            }
+            /* ===== update x, u, lam */
+            for (int i = tid; i < n; i += nt) {
+#pragma unroll
+                for (int j = 0; j < NX; ++j) {
+                    V.X[(size_t)j * np + i] += alpha * V.dx[(size_t)j * np + i];
+                    if (i != 0) {
+                        const float lm = V.L[(size_t)j * np + i];
+                        V.L[(size_t)j * np + i] = lm + alpha * (V.lq[(size_t)j * np + i] - lm);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NU; ++j) V.U[(size_t)j * np + i] += alpha * V.du[(size_t)j * np + i];
+            }
+            __syncthreads();
+            c_ls += clock64() - t0;
+            ++inner;
+            if (ls_fail >= 3) {
+                status = 2;
+                goto done;
+            }
+        }
+        /* ===== outer loop: BCL update (Sec. IV-B, Algorithm 1) */
+        {
+            float cv = 0.f;
+            for (int i = tid; i < n; i += nt) {
+                const bool is_leaf = V.nchild[i] == 0;
+                float x[NX], u[NU];
+                V.load_x(V.X, i, x);
+                V.load_u(V.U, i, u);
+                for_constraints<NX>(R, V, i, is_leaf, x, u, [&](int row, float g) {
+                    const float yv = V.Y[(size_t)row * np + i];
+                    cv = fmaxf(cv, fabsf(fmaxf(g, -yv / rho)));
+                });
+            }
+            cviol = block_max(cv, sh);
+            if (cviol <= eta) {
+                for (int i = tid; i < n; i += nt) {
+                    const bool is_leaf = V.nchild[i] == 0;
+                    float x[NX], u[NU];
+                    V.load_x(V.X, i, x);
+                    V.load_u(V.U, i, u);
+                    for_constraints<NX>(R, V, i, is_leaf, x, u, [&](int row, float g) {
+                        float *yp = V.Y + (size_t)row * np + i;
+                        *yp = fmaxf(0.f, *yp + rho * g);
+                    });
+                }
+                __syncthreads();
+                if (fmaxf(r_kkt, cviol) < O.eps_tol) {
+                    status = 0;
+                    goto done;
+                }
+                omega = omega * powf(rho, -O.b_omega);
+                eta = eta * powf(rho, -O.b_eta);
+            } else {
+                rho = fminf(O.tau * rho, O.rho_max);
+                omega = O.omega0 * powf(rho, -O.a_omega);
+                eta = O.eta0 * powf(rho, -O.a_eta);
+            }
+            omega = fmaxf(omega, O.eps_tol);
+            eta = fmaxf(eta, O.eps_tol);
+        }
+    }
+done:
+    __syncthreads();
+    if (tid == 0) {
+        stat->status = status;
+        stat->inner_iters = inner;
+        stat->outer_iters = outer;
+        stat->ls_fail_total = ls_fail_total;
+        stat->ls_evals = ls_evals;
+        stat->reserved = 0;
+        stat->r_kkt = r_kkt;
+        stat->c = cviol;
+        stat->rho = rho;
+        stat->mu = mu;
+        stat->cyc_lin = c_lin;
+        stat->cyc_bwd = c_bwd;
+        stat->cyc_fwd = c_fwd;
+        stat->cyc_ls = c_ls;
+        stat->cyc_total = clock64() - t_start;
+    }
+}
+
+__global__ void __launch_bounds__(MAX_BLOCK) bmpc_solve_kernel(KernelArgs args) {
+    __shared__ Shared sh;
+    __shared__ int pid_s;
+    for (;;) {
+        if (threadIdx.x == 0) pid_s = atomicAdd(args.queue, 1);
+        __syncthreads();
+        const int slot = pid_s;
+        __syncthreads();
+        if (slot >= args.n_problems) break;
+        const int pid = args.order[slot];
+        const ProbRec &R = args.recs[pid];
+        const int32_t *ib = args.ibase + R.off_int;
+        const float *fin = args.inbase + R.off_in;
+        const float *fw = args.warmbase + R.off_warm;
+        float *fout = args.outbase + R.off_out;
+        float *fs = args.scr + R.off_scr;
+        Stats *st = args.stats + pid;
+        if (R.model == 0) solve_problem<4, 0>(R, ib, fin, fw, fout, fs, st, args.opts, sh);
+        else if (R.model == 1) solve_problem<6, 1>(R, ib, fin, fw, fout, fs, st, args.opts, sh);
+        else solve_problem<4, 2>(R, ib, fin, fw, fout, fs, st, args.opts, sh);
+    }
+}
+
+/* Launch helper used by the host API. */
+cudaError_t launch_solve(const KernelArgs &args, int grid, int block, cudaStream_t stream) {
+    bmpc_solve_kernel<<<grid, block, 0, stream>>>(args);
+    return cudaGetLastError();
+}
+
+int max_block_threads() { return MAX_BLOCK; }
+
+cudaError_t occupancy(int block, int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel, block, 0);
+}
+
+}  // namespace bmpc

@@ -1,0 +1,143 @@
+/*
+ * Device memory layout of a batch of branch-MPC problems.  Shared by the host
+ * API (which builds the tables) and the solver kernel (which reads them).
+ *
+ * All per-node arrays are component-major, [component][npad] with npad = n
+ * rounded up to a multiple of 32, so that the threads of a warp that work on
+ * consecutive nodes of one stage read consecutive addresses.  Nodes are in
+ * level order, so the nodes of a stage and the children of a node are
+ * contiguous.
+ */
+#pragma once
+#include <stdint.h>
+
+namespace bmpc {
+
+constexpr int NU = 2;
+constexpr int MAX_NX = 6;
+constexpr int MAX_OBS = 8;
+constexpr int MAX_NC = 2 * NU + MAX_OBS + 2;
+
+__host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+__host__ __device__ constexpr int nsym(int nx) { return nx * (nx + 1) / 2; }
+
+/* One record per problem; 16-byte aligned, plain data. */
+struct alignas(16) ProbRec {
+    int32_t n, npad, nx, nu, model, n_obs, nc, box_on, lane_on, n_stage, has_warm, pad0;
+    int64_t off_int;   /* int32 elements from the int region base      */
+    int64_t off_in;    /* float elements from the input region base    */
+    int64_t off_warm;  /* float elements from the warm-start region base */
+    int64_t off_out;   /* float elements from the output region base   */
+    int64_t off_scr;   /* float elements from the scratch arena base   */
+    float dt, lane_lo, lane_hi, pad1;
+    float params[10];  /* L, m, Iz, lf, lr, Cf, Cr, vmin, veps, n_sub  */
+    float Qw[MAX_NX], QNw[MAX_NX], Rw[NU], u_lo[NU], u_hi[NU];
+    float x0[MAX_NX];
+    float Alin[16], Blin[8];
+};
+
+/* int region of one problem, in rows of npad int32 */
+struct IntRows {
+    static constexpr int parent = 0, nchild = 1, fchild = 2, stage = 3, leaf = 4, stage_start = 5;
+    /* stage_start occupies round_up(n_stage + 1, 32) ints after the 5 node rows */
+};
+__host__ __device__ inline int64_t int_elems(int npad, int n_stage) {
+    return 5LL * npad + round_up(n_stage + 1, 32);
+}
+
+/* input region: xref[nx] weight[1] obs[5*n_obs] (rows of npad) */
+struct InRows {
+    int xref, weight, obs, total;
+};
+__host__ __device__ inline InRows in_rows(int nx, int n_obs) {
+    InRows r;
+    r.xref = 0;
+    r.weight = nx;
+    r.obs = r.weight + 1;
+    r.total = r.obs + 5 * n_obs;
+    return r;
+}
+
+/* warm-start region (read only when has_warm): wx[nx] wu[nu] wl[nx] wy[nc] */
+struct WarmRows {
+    int wx, wu, wl, wy, total;
+};
+__host__ __device__ inline WarmRows warm_rows(int nx, int nc) {
+    WarmRows r;
+    r.wx = 0;
+    r.wu = nx;
+    r.wl = r.wu + NU;
+    r.wy = r.wl + nx;
+    r.total = r.wy + nc;
+    return r;
+}
+
+/* output region: x[nx] u[nu] lam[nx] y[nc] */
+struct OutRows {
+    int x, u, lam, y, total;
+};
+__host__ __device__ inline OutRows out_rows(int nx, int nc) {
+    OutRows r;
+    r.x = 0;
+    r.u = nx;
+    r.lam = r.u + NU;
+    r.y = r.lam + nx;
+    r.total = r.y + nc;
+    return r;
+}
+
+/* scratch: A[nx*nx] B[nx*nu] f[nx] d[nx] q[nx] r[nu] hq[3] hr[nu] K[nu*nx] k[nu] P[nsym] p[nx]
+ *          dx[nx] du[nu] lq[nx] nv[3] */
+struct ScrRows {
+    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, total;
+};
+__host__ __device__ inline ScrRows scr_rows(int nx) {
+    ScrRows s;
+    s.A = 0;
+    s.B = s.A + nx * nx;
+    s.f = s.B + nx * NU;
+    s.d = s.f + nx;
+    s.q = s.d + nx;
+    s.r = s.q + nx;
+    s.hq = s.r + NU;
+    s.hr = s.hq + 3;
+    s.K = s.hr + NU;
+    s.k = s.K + NU * nx;
+    s.P = s.k + NU;
+    s.p = s.P + nsym(nx);
+    s.dx = s.p + nx;
+    s.du = s.dx + nx;
+    s.lq = s.du + NU;
+    s.nv = s.lq + nx;
+    s.total = s.nv + 3;
+    return s;
+}
+
+/* Kernel-side copy of the solver options (Algorithm 1 constants). */
+struct KOpts {
+    int32_t max_iters, max_outer, n_alpha, ls_chunk;
+    float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps;
+};
+
+/* Per-problem statistics, same layout as the public bmpc_stats. */
+struct Stats {
+    int32_t status, inner_iters, outer_iters, ls_fail_total, ls_evals, reserved;
+    float r_kkt, c, rho, mu;
+    int64_t cyc_lin, cyc_bwd, cyc_fwd, cyc_ls, cyc_total;
+};
+
+struct KernelArgs {
+    const ProbRec *recs;
+    const int32_t *order;     /* problem visiting order (largest first) */
+    int32_t n_problems;
+    int32_t *queue;           /* work-queue counter, zeroed before each launch */
+    const int32_t *ibase;
+    const float *inbase;
+    const float *warmbase;
+    float *outbase;
+    float *scr;
+    Stats *stats;
+    KOpts opts;
+};
+
+}  // namespace bmpc

@@ -1,0 +1,93 @@
+"""Host-only checks of the C ABI: the library loads, exports every symbol that
+include/bmpc.h declares, and its host-side validation and sizing work without a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import scenes
+from paper_2506_13624_b300 import bmpc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "bmpc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(bmpc_[a-z_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = bmpc.lib()
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(declared) == set(bmpc.EXPORTED)
+
+
+def test_version_and_status_strings():
+    assert b"sm_103a" in bmpc.lib().bmpc_version()
+    for s in (0, 1, 2, -1, -2, -3, -4, -5):
+        assert bmpc.status_str(s) != "unknown status"
+
+
+def _sizes(problems):
+    descs = (bmpc.TreeDesc * len(problems))()
+    keep = []
+    for k, p in enumerate(problems):
+        d, par = bmpc.tree_desc(p)
+        descs[k] = d
+        keep.append(par)
+    db, sb, hb = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    rc = bmpc.lib().bmpc_batch_bytes(descs, len(problems), C.byref(db), C.byref(sb), C.byref(hb))
+    return rc, db.value, sb.value, hb.value
+
+
+def test_batch_bytes_scale_with_nodes():
+    rc1, d1, s1, h1 = _sizes([scenes.config1(0)])
+    rc3, d3, s3, h3 = _sizes([scenes.config3(0)])
+    assert rc1 == 0 and rc3 == 0
+    assert s3 > 20 * s1 and d3 > 10 * d1 and h1 == d1
+    rc, d, s, h = _sizes(scenes.config4(4, 16))
+    assert rc == 0 and s % 4 == 0
+
+
+@pytest.mark.parametrize("mutate", ["not_level_order", "parent_after", "bad_root", "bad_model", "too_many_obs",
+                                    "one_node", "bad_substeps"])
+def test_invalid_trees_rejected_on_host(mutate):
+    p = dict(scenes.config1(0))
+    par = p["parent"].copy()
+    if mutate == "not_level_order":
+        par[5], par[6] = par[6], par[5]          # children of a node not contiguous
+        par[4] = 30
+    elif mutate == "parent_after":
+        par[10] = 11
+    elif mutate == "bad_root":
+        par[0] = 0
+    elif mutate == "bad_model":
+        p["model"] = 1                            # nx = 4 with the dynamic model
+    elif mutate == "too_many_obs":
+        p["n_obs"] = 9
+    elif mutate == "one_node":
+        par = par[:1]
+        p["n"] = 1
+    elif mutate == "bad_substeps":
+        p["params"] = p["params"].copy()
+        p["params"][9] = 0.0
+    p["parent"] = par
+    rc, *_ = _sizes([p])
+    assert rc == bmpc.ERR_INVALID
+
+
+def test_default_opts_match_the_oracle_constants():
+    import oracle
+    o, r = bmpc.default_opts(), oracle.default_opts()
+    for f in ("max_iters", "max_outer", "n_alpha"):
+        assert getattr(o, f) == getattr(r, f)
+    for f in ("eps_tol", "tau", "omega0", "eta0", "a_omega", "b_omega", "a_eta", "b_eta", "rho0", "rho_max",
+              "mu0", "beta", "ls_rel_eps"):
+        assert np.float32(getattr(o, f)) == np.float32(getattr(r, f)), f

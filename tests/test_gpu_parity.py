@@ -1,0 +1,211 @@
+"""GPU (FP32, CUDA through the C ABI) versus the FP64 oracle on identical seeded inputs.
+
+Parity bar (per converged problem):
+  * controls: |u_gpu - u_oracle|_inf <= 1e-4 * max(|u_oracle|_inf, 1);
+  * the oracle's FP64 KKT conditions of Eq. (bmpc) evaluated at the GPU's returned
+    (x, u, lambda, y) are below 1e-5 (stationarity, defects, feasibility, complementarity).
+The method is an iteration on a nonconvex problem, so FP32 and FP64 may stop at two
+different KKT points; such a pair counts as "distinct local minimum" only if the oracle,
+warm-started from the GPU solution, confirms it as a KKT point of its own within two
+iterations.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U_REL = 1e-4
+KKT_TOL = 1e-5
+
+
+def _gpu(problems, **kw):
+    from paper_2506_13624_b300 import bmpc
+    opts = bmpc.default_opts(**kw)
+    b = bmpc.Batch(problems)
+    b.set_problems()
+    b.solve(opts)
+    res = b.get_solutions()
+    b.close()
+    return res
+
+
+def _check_pair(p, g, r):
+    """Returns 'match', 'distinct' or raises AssertionError with a reason."""
+    assert g["status"] == oracle.OK, f"GPU status {g['status']} (oracle {r['status']}), r_kkt={g['r_kkt']:.2e}"
+    nl = np.ones(p["n"], bool)
+    nl[np.unique(p["parent"][1:])] = False
+    inner = ~nl
+    k = oracle.kkt(p, g["x"], g["u"], g["lam"], g["y"])
+    assert k[:4].max() <= KKT_TOL, f"FP64 KKT at the GPU point: {k}"
+    assert (g["y"] >= 0).all()
+    du = np.abs(g["u"][inner] - r["u"][inner]).max()
+    if du <= U_REL * max(np.abs(r["u"][inner]).max(), 1.0):
+        return "match"
+    w = oracle.solve(p, warm=(g["x"], g["u"], g["lam"], g["y"]))
+    assert w["status"] == oracle.OK and w["inner_iters"] <= 2, "GPU point not confirmed by the oracle"
+    assert np.abs(w["u"][inner] - g["u"][inner]).max() <= U_REL * max(np.abs(g["u"][inner]).max(), 1.0)
+    return "distinct"
+
+
+def _run_config(problems, min_match=0.8, **kw):
+    gres = _gpu(problems, **kw)
+    counts = {"match": 0, "distinct": 0, "oracle_fail": 0}
+    for p, g in zip(problems, gres):
+        r = oracle.solve(p)
+        if r["status"] != oracle.OK:
+            counts["oracle_fail"] += 1
+            assert g["status"] in (oracle.OK, oracle.MAX_ITER, oracle.LS_FAIL)
+            continue
+        counts[_check_pair(p, g, r)] += 1
+    solved = counts["match"] + counts["distinct"]
+    assert solved >= 1
+    assert counts["match"] >= min_match * solved, counts
+    return counts
+
+
+def test_config1_parity():
+    print(_run_config(scenes.instances(1, 12)))
+
+
+def test_config2_parity():
+    print(_run_config(scenes.instances(2, 6)))
+
+
+def test_config3_parity():
+    print(_run_config(scenes.instances(3, 2, seed0=1), min_match=0.5))
+
+
+def test_mixed_batch_parity():
+    print(_run_config(scenes.config4(4, 24)))
+
+
+def test_linear_quadratic_one_iteration():
+    ps = [scenes.linear_problem(s, N=12, splits={2: 2, 6: 3}) for s in range(3)]
+    gres = _gpu(ps)
+    for p, g in zip(ps, gres):
+        r = oracle.solve(p)
+        assert g["status"] == oracle.OK and g["inner_iters"] == 1
+        np.testing.assert_allclose(g["u"], r["u"], atol=1e-4 * max(1.0, np.abs(r["u"]).max()))
+        np.testing.assert_allclose(g["x"], r["x"], atol=1e-4 * max(1.0, np.abs(r["x"]).max()))
+
+
+def test_constrained_linear_problem_parity():
+    ps = [scenes.linear_problem(s, N=15, splits={3: 2, 8: 2}, constrained=True) for s in range(3)]
+    print(_run_config(ps, min_match=1.0))
+
+
+def test_nonanticipativity_bitwise():
+    p = scenes.linear_problem(5, N=10, splits={2: 3, 5: 2})
+    st = p["stage"]
+    xr = np.zeros((st.max() + 1, p["nx"]))
+    for i in range(p["n"]):
+        xr[st[i]] = p["xref"][i]
+    p["xref"] = xr[st]
+    g = _gpu([p])[0]
+    for k in range(st.max() + 1):
+        rows = g["x"][st == k]
+        assert (rows == rows[0]).all()
+
+
+def test_edge_trees():
+    """Smallest tree, ragged leaves, more nodes per stage than threads, 8 obstacles, no constraints."""
+    base = scenes.linear_problem(1, N=1, splits={})
+    assert base["n"] == 2
+    wide = scenes.linear_problem(2, N=4, splits={1: 8, 2: 8, 3: 6})      # 384 nodes per stage
+    many = scenes.config2(1)
+    obs8 = dict(many)
+    extra = np.repeat(many["obs"][:, :1, :], 5, axis=1)
+    extra[:, :, 1] += 1000.0
+    obs8["obs"] = np.concatenate([many["obs"], extra], axis=1)
+    obs8["n_obs"] = 8
+    ps = [base, wide, obs8]
+    gres = _gpu(ps, block_threads=128)
+    for p, g in zip(ps, gres):
+        r = oracle.solve(p)
+        assert r["status"] == oracle.OK
+        _check_pair(p, g, r)
+
+
+def test_ragged_tree_parity():
+    """Leaves at different depths (a hand-built level-ordered tree)."""
+    p = scenes.linear_problem(9, N=6, splits={2: 3})
+    # cut two of the three branches short: keep nodes of branch 0 to the end, others to stage 4
+    st, par = p["stage"], p["parent"]
+    keep = np.ones(p["n"], bool)
+    branch = np.zeros(p["n"], int)
+    for i in range(1, p["n"]):
+        branch[i] = branch[par[i]] if st[i] > 2 else (i % 3 if st[i] == 2 else 0)
+    keep[(branch != 0) & (st > 4)] = False
+    idx = np.where(keep)[0]
+    remap = -np.ones(p["n"], int)
+    remap[idx] = np.arange(len(idx))
+    q = dict(p)
+    q["parent"] = np.array([-1] + [remap[par[i]] for i in idx[1:]], np.int32)
+    q["stage"] = st[idx]
+    q["n"] = len(idx)
+    for key in ("xref", "weight", "obs"):
+        q[key] = p[key][idx]
+    r = oracle.solve(q)
+    g = _gpu([q])[0]
+    assert r["status"] == oracle.OK
+    assert _check_pair(q, g, r) == "match"
+
+
+def test_graph_replay_and_determinism():
+    from paper_2506_13624_b300 import bmpc
+    ps = scenes.config4(4, 8)
+    b = bmpc.Batch(ps)
+    b.set_problems()
+    b.solve()
+    r1 = b.get_solutions()
+    b.solve(graph=True)
+    r2 = b.get_solutions()
+    b.solve(graph=True)
+    r3 = b.get_solutions()
+    b.close()
+    for a, c, d in zip(r1, r2, r3):
+        for key in ("x", "u", "lam", "y"):
+            assert np.array_equal(a[key], c[key]) and np.array_equal(c[key], d[key])
+        assert a["inner_iters"] == c["inner_iters"]
+
+
+def test_batch_equals_single():
+    ps = scenes.config4(4, 6)
+    batch = _gpu(ps, block_threads=64)
+    for p, g in zip(ps, batch):
+        s = _gpu([p], block_threads=64)[0]
+        for key in ("x", "u", "lam", "y"):
+            assert np.array_equal(g[key], s[key])
+
+
+def test_invalid_problem_rejected():
+    from paper_2506_13624_b300 import bmpc
+    p = dict(scenes.config1(0))
+    par = p["parent"].copy()
+    par[10] = 12
+    p["parent"] = par
+    with pytest.raises(RuntimeError):
+        bmpc.Batch([p])
+
+
+def test_full_size_batch_sampled():
+    """The launch configuration the benchmark times: 4,096 mixed problems in one launch."""
+    ps = scenes.config4(4, 4096)
+    gres = _gpu(ps)
+    conv = np.mean([g["status"] == oracle.OK for g in gres])
+    assert conv >= 0.85, conv
+    rng = np.random.default_rng(0)
+    small = [k for k in range(len(ps)) if ps[k]["n"] < 700]
+    counts = {"match": 0, "distinct": 0, "skip": 0}
+    for k in rng.choice(small, 6, replace=False):
+        r = oracle.solve(ps[k])
+        if r["status"] != oracle.OK or gres[k]["status"] != oracle.OK:
+            counts["skip"] += 1
+            continue
+        counts[_check_pair(ps[k], gres[k], r)] += 1
+    print(counts, conv)
+    assert counts["match"] + counts["distinct"] >= 3
