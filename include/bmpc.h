@@ -103,7 +103,7 @@ typedef struct {
     float omega0, eta0;     /* 1, 0.1 */
     float a_omega, b_omega; /* 1, 1 */
     float a_eta, b_eta;     /* 0.1, 0.9 */
-    float rho0, rho_max;    /* 10, 1e6 */
+    float rho0, rho_max;    /* 10, 100 (a failed outer step at rho_max updates y instead) */
     float mu0;              /* 1 */
     float beta;             /* Armijo constant, 1e-4 */
     float ls_rel_eps;       /* Armijo slack relative to |phi(0)|, 1e-6 */
@@ -158,7 +158,8 @@ int bmpc_solve_batch_graph(bmpc_batch *b, const bmpc_opts *opts);
 int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats);
 
 /* Device pointers of the output arrays of problem i (component-major [comp][npad]) and its
- * padded node count, for callers that keep results on the GPU. */
+ * padded node count, for callers that keep results on the GPU.  The state array holds the
+ * deviation x - xref of every node from its reference (the solver's coordinates). */
 int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float **u, float **lam, float **y,
                                 int32_t *npad);
 

@@ -23,6 +23,9 @@
  *   - multiplier update y <- max(0, y + rho g) (standard PHR, Algorithm 1 drops y);
  *   - tolerance schedules omega <- omega rho^-b_omega, eta <- eta rho^-b_eta on success,
  *     omega <- omega0 rho^-a_omega, eta <- eta0 rho^-a_eta on failure, both floored at eps_tol;
+ *   - rho is capped at rho_max; a failed outer step at the cap applies the multiplier update
+ *     y <- max(0, y + rho g) instead of raising rho (the cap keeps rho * FP32 rounding of g
+ *     below the tolerance on the GPU);
  *   - the merit uses J = L_a and moves (x, u, lambda) jointly; lambda_QP = P dx + p;
  *   - mu rule: phi'(0; mu) <= -1/2 dz'W dz, else mu <- max(mu, 2(phi'(0;0) + 1/2 dz'W dz)/|d|^2);
  *   - alpha_i = 2^-i; Armijo with an absolute slack ls_rel_eps*|phi(0)| for finite precision;
@@ -684,7 +687,7 @@ void orc_default_opts(orc_opts *o) {
     o->a_eta = 0.1;
     o->b_eta = 0.9;
     o->rho0 = 10.0;
-    o->rho_max = 1e6;
+    o->rho_max = 100.0;
     o->mu0 = 1.0;
     o->beta = 1e-4;
     o->ls_rel_eps = 1e-6;
@@ -812,8 +815,17 @@ int orc_solve(const orc_problem *P, const orc_opts *O_in, const double *wx, cons
             omega = omega * pow(rho, -O.b_omega);
             eta = eta * pow(rho, -O.b_eta);
         } else {
-            rho = O.tau * rho;
-            if (rho > O.rho_max) rho = O.rho_max;
+            if (rho < O.rho_max) {
+                rho = O.tau * rho;
+                if (rho > O.rho_max) rho = O.rho_max;
+            } else {
+                /* penalty at its cap: first-order multiplier step instead of a larger rho */
+                for (int e = 0; e < n * nc; ++e) {
+                    if (!W.ex[e]) continue;
+                    double v = y[e] + rho * W.g[e];
+                    y[e] = v > 0.0 ? v : 0.0;
+                }
+            }
             omega = O.omega0 * pow(rho, -O.a_omega);
             eta = O.eta0 * pow(rho, -O.a_eta);
         }

@@ -253,7 +253,7 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->a_eta = 0.1f;
     o->b_eta = 0.9f;
     o->rho0 = 10.f;
-    o->rho_max = 1e6f;
+    o->rho_max = 100.f;
     o->mu0 = 1.f;
     o->beta = 1e-4f;
     o->ls_rel_eps = 1e-6f;
@@ -490,15 +490,19 @@ int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return BMPC_ERR_CUDA;
     const float *fo = at<const float>(b->stage, b->L.out);
+    const float *fi = at<const float>(b->stage, b->L.in);
     size_t ox = 0, ou = 0, ol = 0, oy = 0;
     for (int k = 0; k < b->n; ++k) {
         const ProbRec &R = b->recs[k];
         const OutRows orw = out_rows(R.nx, R.nc);
+        const InRows ir = in_rows(R.nx, R.n_obs);
         const float *base = fo + R.off_out;
+        const float *xref = fi + R.off_in + (size_t)ir.xref * R.npad;
         const int nn = R.n, np = R.npad;
         for (int i = 0; i < nn; ++i) {
             for (int j = 0; j < R.nx; ++j) {
-                if (x) x[ox + (size_t)i * R.nx + j] = base[(size_t)(orw.x + j) * np + i];
+                /* the device keeps the deviation from the reference; absolute state on output */
+                if (x) x[ox + (size_t)i * R.nx + j] = xref[(size_t)j * np + i] + base[(size_t)(orw.x + j) * np + i];
                 if (lam) lam[ol + (size_t)i * R.nx + j] = base[(size_t)(orw.lam + j) * np + i];
             }
             for (int j = 0; j < NU; ++j)

@@ -6,7 +6,7 @@
  * solves a whole batch of trees of uneven size.
  *
  * Per inner iteration the block runs, with a block barrier between phases:
- *   linearise   every node in parallel: RK4 step with forward-mode Jacobians
+ *   linearise   every node in parallel: RK4 increment with forward-mode Jacobians
  *               A_n, B_n, cost gradient, PHR penalty gradient and its
  *               Gauss-Newton Hessian (Sec. IV-A, Eq. AL);
  *   kkt         defects d_m = f_p(m) - x_m, KKT residual of the relaxed problem
@@ -23,6 +23,11 @@
  *   update      x, u, lam moved by alpha.
  * After the inner loop the block evaluates the constraint violation c and
  * applies the BCL update of (y_e, rho, omega, eta) (Sec. IV-B).
+ *
+ * State coordinates: the kernel iterates on the deviation xi = x - xref of every node
+ * state from its reference, so that FP32 resolves states far from the origin; defects
+ * are formed from reference increments, state deviations and RK4 increments without
+ * subtracting two large absolute positions.  Absolute states are formed only on output.
  *
  * Scalar control (rho, mu, omega, eta, counters) is replicated in every
  * thread: block reductions return identical totals to all threads, so all
@@ -194,8 +199,10 @@ __device__ __forceinline__ void rhs(const float *prm, const float (&s)[NX], floa
     }
 }
 
-/* x+ = f(x, u) with A = df/dx, B = df/du: n_sub classical RK4 steps, Jacobians by the
- * forward-mode chain rule through every stage (tangent matrix S = dz/d(x, u)). */
+/* Increment dlt = f(x, u) - x of the discrete dynamics with A = df/dx, B = df/du: n_sub
+ * classical RK4 steps, Jacobians by the forward-mode chain rule through every stage (tangent
+ * matrix S = dz/d(x, u)).  The increment is returned instead of f so that the defect
+ * f(x_p, u_p) - x_m = (x_p - x_m) + dlt never subtracts two large absolute positions in FP32. */
 template <int NX, int MODEL>
 __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], const float (&u)[NU],
                                         float (&xn)[NX], float (&A)[NX][NX], float (&B)[NX][NU]) {
@@ -206,7 +213,7 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
 #pragma unroll
             for (int j = 0; j < NX; ++j) {
                 A[i][j] = R.Alin[i * NX + j];
-                s += A[i][j] * x[j];
+                s += (i == j ? A[i][j] - 1.f : A[i][j]) * x[j];
             }
 #pragma unroll
             for (int j = 0; j < NU; ++j) {
@@ -222,9 +229,9 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
         for (int i = 0; i < NX; ++i)
 #pragma unroll
             for (int j = 0; j < NZ; ++j) S[i][j] = (i == j) ? 1.f : 0.f;
-        float z[NX];
+        float z[NX];   /* increment accumulated over the substeps */
 #pragma unroll
-        for (int i = 0; i < NX; ++i) z[i] = x[i];
+        for (int i = 0; i < NX; ++i) z[i] = 0.f;
         const int nsub = max(1, (int)R.params[9]);
         const float h = R.dt / (float)nsub;
         for (int sub = 0; sub < nsub; ++sub) {
@@ -245,7 +252,7 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
                 const float wg = (st == 0 || st == 3) ? 1.f : 2.f;
                 float zs[NX];
 #pragma unroll
-                for (int i = 0; i < NX; ++i) zs[i] = z[i] + c * h * kp[i];
+                for (int i = 0; i < NX; ++i) zs[i] = x[i] + (z[i] + c * h * kp[i]);
                 float f[NX], J[NX][NX], Ju[NX][NU];
                 rhs_jac<NX, MODEL>(R.params, zs, u[0], u[1], f, J, Ju);
                 float D[NX][NZ];
@@ -288,6 +295,7 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
     }
 }
 
+/* Increment f(x, u) - x of the discrete dynamics (no Jacobians). */
 template <int NX, int MODEL>
 __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], const float (&u)[NU], float (&xn)[NX]) {
     if constexpr (MODEL == 2) {
@@ -295,15 +303,15 @@ __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], cons
         for (int i = 0; i < NX; ++i) {
             float s = 0.f;
 #pragma unroll
-            for (int j = 0; j < NX; ++j) s += R.Alin[i * NX + j] * x[j];
+            for (int j = 0; j < NX; ++j) s += (i == j ? R.Alin[i * NX + j] - 1.f : R.Alin[i * NX + j]) * x[j];
 #pragma unroll
             for (int j = 0; j < NU; ++j) s += R.Blin[i * NU + j] * u[j];
             xn[i] = s;
         }
     } else {
-        float z[NX];
+        float z[NX];   /* increment */
 #pragma unroll
-        for (int i = 0; i < NX; ++i) z[i] = x[i];
+        for (int i = 0; i < NX; ++i) z[i] = 0.f;
         const int nsub = max(1, (int)R.params[9]);
         const float h = R.dt / (float)nsub;
         for (int sub = 0; sub < nsub; ++sub) {
@@ -319,7 +327,7 @@ __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], cons
                 const float wg = (st == 0 || st == 3) ? 1.f : 2.f;
                 float zs[NX], f[NX];
 #pragma unroll
-                for (int i = 0; i < NX; ++i) zs[i] = z[i] + c * h * kp[i];
+                for (int i = 0; i < NX; ++i) zs[i] = x[i] + (z[i] + c * h * kp[i]);
                 rhs<NX, MODEL>(R.params, zs, u[0], u[1], f);
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
@@ -420,12 +428,13 @@ template <int NX, bool GRAD>
 __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, int i, bool is_leaf,
                                          const float (&x)[NX], const float (&u)[NU], float rho, float (&q)[NX],
                                          float (&r)[NU], float (&hq)[3], float (&hr)[NU]) {
+    /* x is the deviation from the node's reference (the kernel's state coordinates) */
     const float w = V.w[i];
     const float *Qd = is_leaf ? R.QNw : R.Qw;
     float la = 0.f;
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
-        const float e = x[j] - V.xref[(size_t)j * V.np + i];
+        const float e = x[j];
         la += 0.5f * w * Qd[j] * e * e;
         if (GRAD) q[j] = w * Qd[j] * e;
     }
@@ -470,7 +479,7 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
             const float ea = ob[3 * (size_t)V.np], eb = ob[4 * (size_t)V.np];
             float sh, ch;
             sincosf(hd, &sh, &ch);
-            const float dxo = x[0] - cx, dyo = x[1] - cy;
+            const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
             const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
             const float ia2 = 1.f / (ea * ea), ib2 = 1.f / (eb * eb);
             const float rr2 = sqrtf(dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f);
@@ -492,7 +501,8 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
         }
         row += V.nobs;
         if (V.lane) {
-            const float g0 = x[1] - R.lane_hi, g1 = R.lane_lo - x[1];
+            const float yr = V.xref[(size_t)V.np + i];
+            const float g0 = (yr - R.lane_hi) + x[1], g1 = (R.lane_lo - yr) - x[1];
             const float s0 = V.Y[(size_t)row * V.np + i] + rho * g0;
             const float s1 = V.Y[(size_t)(row + 1) * V.np + i] + rho * g1;
             if (s0 > 0.f) {
@@ -514,7 +524,7 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
     return la;
 }
 
-/* Constraint rows g (existing rows only, others skipped): calls fn(row, g). */
+/* Constraint rows g (existing rows only, others skipped) at the deviation x: calls fn(row, g). */
 template <int NX, typename Fn>
 __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX> &V, int i, bool is_leaf,
                                                 const float (&x)[NX], const float (&u)[NU], Fn fn) {
@@ -536,14 +546,15 @@ __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX>
             const float ea = ob[3 * (size_t)V.np], eb = ob[4 * (size_t)V.np];
             float sh, ch;
             sincosf(hd, &sh, &ch);
-            const float dxo = x[0] - cx, dyo = x[1] - cy;
+            const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
             const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
             fn(row + o, 1.f - sqrtf(dpar * dpar / (ea * ea) + dper * dper / (eb * eb) + 1e-6f));
         }
         row += V.nobs;
         if (V.lane) {
-            fn(row, x[1] - R.lane_hi);
-            fn(row + 1, R.lane_lo - x[1]);
+            const float yr = V.xref[(size_t)V.np + i];
+            fn(row, (yr - R.lane_hi) + x[1]);
+            fn(row + 1, (R.lane_lo - yr) - x[1]);
         }
     }
 }
@@ -586,6 +597,8 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             }
         }
         if (is_leaf) u[0] = u[1] = 0.f;
+#pragma unroll
+        for (int j = 0; j < NX; ++j) x[j] -= V.xref[(size_t)j * np + i];   /* deviation coordinates */
         V.store_x(V.X, i, x);
         V.store_u(V.U, i, u);
         V.store_x(V.L, i, l);
@@ -616,8 +629,10 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                 V.store_u(V.hr, i, hr);
                 V.nv[i] = la;
                 if (!is_leaf) {
-                    float xn[NX], A[NX][NX], B[NX][NU];
-                    dyn_lin<NX, MODEL>(R, x, u, xn, A, B);
+                    float xa[NX], xn[NX], A[NX][NX], B[NX][NU];
+#pragma unroll
+                    for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
+                    dyn_lin<NX, MODEL>(R, xa, u, xn, A, B);
                     V.store_x(V.f, i, xn);
 #pragma unroll
                     for (int a = 0; a < NX; ++a) {
@@ -646,7 +661,9 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                     float gx[NX];
 #pragma unroll
                     for (int j = 0; j < NX; ++j) {
-                        const float dj = V.f[(size_t)j * np + pa] - V.X[(size_t)j * np + i];
+                        const float dref = V.xref[(size_t)j * np + pa] - V.xref[(size_t)j * np + i];
+                        const float dj = (dref + (V.X[(size_t)j * np + pa] - V.X[(size_t)j * np + i])) +
+                                         V.f[(size_t)j * np + pa];
                         V.d[(size_t)j * np + i] = dj;
                         const float lj = V.L[(size_t)j * np + i];
                         ld += lj * dj;
@@ -965,14 +982,18 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                         ut[1] = u[1] + al * duv[1];
                         float v = node_la<NX, false>(R, V, i, is_leaf, xt, ut, rho, qd, rd, hqd, hrd);
                         if (!is_leaf) {
-                            float ft[NX];
-                            dyn<NX, MODEL>(R, xt, ut, ft);
+                            float xa[NX], ft[NX];
+#pragma unroll
+                            for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + xt[j];
+                            dyn<NX, MODEL>(R, xa, ut, ft);
                             for (int m = fc; m < fc + nch; ++m) {
 #pragma unroll
                                 for (int j = 0; j < NX; ++j) {
                                     const float lm = V.L[(size_t)j * np + m];
                                     const float ltj = lm + al * (V.lq[(size_t)j * np + m] - lm);
-                                    const float dm = ft[j] - (V.X[(size_t)j * np + m] + al * V.dx[(size_t)j * np + m]);
+                                    const float dref = V.xref[(size_t)j * np + i] - V.xref[(size_t)j * np + m];
+                                    const float dm = (dref + ((x[j] - V.X[(size_t)j * np + m]) +
+                                                              al * (dxv[j] - V.dx[(size_t)j * np + m]))) + ft[j];
                                     v += ltj * dm + 0.5f * mu * dm * dm;
                                 }
                             }
@@ -1051,7 +1072,22 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                 omega = omega * powf(rho, -O.b_omega);
                 eta = eta * powf(rho, -O.b_eta);
             } else {
-                rho = fminf(O.tau * rho, O.rho_max);
+                if (rho < O.rho_max) {
+                    rho = fminf(O.tau * rho, O.rho_max);
+                } else {
+                    /* penalty at its cap: first-order multiplier step instead of a larger rho */
+                    for (int i = tid; i < n; i += nt) {
+                        const bool is_leaf = V.nchild[i] == 0;
+                        float x[NX], u[NU];
+                        V.load_x(V.X, i, x);
+                        V.load_u(V.U, i, u);
+                        for_constraints<NX>(R, V, i, is_leaf, x, u, [&](int row, float g) {
+                            float *yp = V.Y + (size_t)row * np + i;
+                            *yp = fmaxf(0.f, *yp + rho * g);
+                        });
+                    }
+                    __syncthreads();
+                }
                 omega = O.omega0 * powf(rho, -O.a_omega);
                 eta = O.eta0 * powf(rho, -O.a_eta);
             }
