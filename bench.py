@@ -215,7 +215,9 @@ def run_gpu(args):
     b = bmpc.Batch(problems, stream=stream)
     b.set_problems()
     opts = bmpc.default_opts(block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm,
-                             ls_chunk=args.ls_chunk)
+                             ls_chunk=args.ls_chunk, variant=args.variant)
+    if args.max_iters > 0:
+        opts.max_iters = args.max_iters
     for _ in range(args.warmup):
         b.solve(opts, graph=True)
     res = b.get_solutions(want_arrays=False)
@@ -275,6 +277,10 @@ def run_gpu(args):
     ric_us_iter = float(np.sum(bwd_us) / max(1, iters.sum()))
     tot_us = np.array([r["cycles"]["total"] for r in res]) / (clk * 1e6) * 1e6
     out_bytes = int(sum(int(p["n"]) * (2 * int(p["nx"]) + 2 + bmpc.n_con(p)) * 4 for p in problems))
+    phases = {}
+    for ph in ("linearise", "backward", "forward", "linesearch", "total"):
+        cyc = np.array([r["cycles"][ph] for r in res], dtype=np.float64)
+        phases[ph] = float(cyc.sum() / max(1, iters.sum()) / clk)   # microseconds per problem-iteration
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -285,6 +291,7 @@ def run_gpu(args):
                    "launch": "one persistent kernel per step, CUDA graph replay"},
         "converged_fraction": float(conv.mean()),
         "tree_riccati_us_per_iter": ric_us_iter,
+        "phase_us_per_iter": phases,
         "solve_latency_us": {"mean": float(tot_us.mean()), "max": float(tot_us.max())},
         "inner_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
         "gpu_launches": args.steps,
@@ -312,7 +319,9 @@ def main():
     ap.add_argument("--batch", type=int, default=2048)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--ls-chunk", type=int, default=0)
+    ap.add_argument("--ls-chunk", type=int, default=2)
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--max-iters", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

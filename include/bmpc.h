@@ -95,7 +95,7 @@ typedef struct {
 
 /* Algorithm 1 constants (defaults: the values of Sec. V-B plus the readings of the oracle). */
 typedef struct {
-    int32_t max_iters;      /* cap on inner iterations (tree-LQR solves), default 100 */
+    int32_t max_iters;      /* cap on inner iterations (tree-LQR solves), default 50 */
     int32_t max_outer;      /* cap on outer iterations, default 60 */
     int32_t n_alpha;        /* step sizes alpha_i = 2^-i, i < n_alpha (<= 16), default 10 */
     float eps_tol;          /* 1e-5 */
@@ -107,9 +107,14 @@ typedef struct {
     float mu0;              /* 1 */
     float beta;             /* Armijo constant, 1e-4 */
     float ls_rel_eps;       /* Armijo slack relative to |phi(0)|, 1e-6 */
-    int32_t ls_chunk;       /* step sizes evaluated per parallel round (1..n_alpha); 0 = all */
+    int32_t ls_chunk;       /* step sizes evaluated per parallel round (1..16), default 2; 0 = all.
+                               The accepted step (the largest alpha_i meeting Armijo) does not
+                               depend on it: it only trades parallel work for extra rounds. */
     int32_t block_threads;  /* threads per problem (32..1024, multiple of 32); 0 = automatic */
     int32_t blocks_per_sm;  /* resident problems per SM; 0 = automatic */
+    int32_t variant;        /* tree sweeps: 0 automatic (per-path), 1 level-synchronous (one barrier per
+                               stage, nodes of a stage in parallel), 2 per-scenario-path (one thread per
+                               root-to-leaf path, barriers only at branch stages); same search direction */
 } bmpc_opts;
 
 typedef struct {
@@ -143,8 +148,9 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
  * pass into the staging buffer and one host-to-device copy on the handle's stream. */
 int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *problems);
 
-/* Run Algorithm 1 on every problem of the batch from its warm (or cold) start in one
- * persistent kernel launch on the handle's stream (asynchronous).  opts may be NULL. */
+/* Run Algorithm 1 on every problem of the batch from its warm (or cold) start: one persistent
+ * kernel launch per dynamics model present in the batch, on the handle's stream
+ * (asynchronous).  opts may be NULL. */
 int bmpc_solve_batch(bmpc_batch *b, const bmpc_opts *opts);
 
 /* Same work captured once into a CUDA graph (queue reset + persistent kernel) and

@@ -675,7 +675,7 @@ void orc_cold_start(const orc_problem *P, double *x, double *u, double *lam, dou
 }
 
 void orc_default_opts(orc_opts *o) {
-    o->max_iters = 100;
+    o->max_iters = 50;
     o->max_outer = 60;
     o->n_alpha = 10;
     o->eps_tol = 1e-5;

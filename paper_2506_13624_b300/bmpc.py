@@ -44,7 +44,7 @@ class Opts(C.Structure):
                 ("a_omega", C.c_float), ("b_omega", C.c_float), ("a_eta", C.c_float), ("b_eta", C.c_float),
                 ("rho0", C.c_float), ("rho_max", C.c_float), ("mu0", C.c_float), ("beta", C.c_float),
                 ("ls_rel_eps", C.c_float), ("ls_chunk", C.c_int32), ("block_threads", C.c_int32),
-                ("blocks_per_sm", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("variant", C.c_int32)]
 
 
 class Stats(C.Structure):

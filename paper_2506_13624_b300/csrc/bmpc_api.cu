@@ -19,9 +19,9 @@
 #include "bmpc_layout.h"
 
 namespace bmpc {
-cudaError_t launch_solve(const KernelArgs &args, int grid, int block, cudaStream_t stream);
+cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, cudaStream_t stream);
 int max_block_threads();
-cudaError_t occupancy(int block, int *blocks_per_sm);
+cudaError_t occupancy(int model, int block, int *blocks_per_sm);
 }  // namespace bmpc
 
 using namespace bmpc;
@@ -73,6 +73,7 @@ struct bmpc_batch {
     std::vector<ProbRec> recs;
     std::vector<int32_t> order;
     std::vector<int> nodes;
+    int model_begin[4] = {0, 0, 0, 0};   /* order[model_begin[m] .. model_begin[m+1]) has model m */
     Layout L{};
     char *data = nullptr;
     float *scr = nullptr;
@@ -99,11 +100,19 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         const bmpc_tree_desc &d = descs[k];
         ProbRec &R = recs[k];
         std::memset(&R, 0, sizeof R);
-        int max_stage = 0;
+        int max_stage = 0, n_paths = 0, n_bstage = 0;
         {
             std::vector<int> stage;
             validate(d, &stage);
             max_stage = stage.back();
+            std::vector<int> nch(d.num_nodes, 0);
+            for (int i = 1; i < d.num_nodes; ++i) nch[d.parent[i]]++;
+            std::vector<char> bst(max_stage + 1, 0);
+            for (int i = 0; i < d.num_nodes; ++i) {
+                if (nch[i] == 0) ++n_paths;
+                if (nch[i] > 1) bst[stage[i]] = 1;
+            }
+            for (int s = 0; s <= max_stage; ++s) n_bstage += bst[s];
         }
         R.n = d.num_nodes;
         R.npad = round_up(d.num_nodes, 32);
@@ -115,6 +124,8 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         R.box_on = d.box_on ? 1 : 0;
         R.lane_on = d.lane_on ? 1 : 0;
         R.n_stage = max_stage + 1;
+        R.n_paths = n_paths;
+        R.n_bstage = n_bstage;
         R.dt = d.dt;
         std::memcpy(R.params, d.params, sizeof R.params);
         R.off_int = (int64_t)oi;
@@ -122,7 +133,7 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         R.off_warm = (int64_t)ow;
         R.off_out = (int64_t)oo;
         R.off_scr = (int64_t)os;
-        oi += (size_t)int_elems(R.npad, R.n_stage);
+        oi += (size_t)int_off(R.npad, R.n_stage, R.n_paths).total;
         oin += (size_t)in_rows(R.nx, R.n_obs).total * R.npad;
         ow += (size_t)warm_rows(R.nx, R.nc).total * R.npad;
         oo += (size_t)out_rows(R.nx, R.nc).total * R.npad;
@@ -162,6 +173,7 @@ KOpts to_kopts(const bmpc_opts &o) {
     k.max_outer = o.max_outer;
     k.n_alpha = o.n_alpha;
     k.ls_chunk = o.ls_chunk;
+    k.variant = o.variant;
     k.eps_tol = o.eps_tol;
     k.tau = o.tau;
     k.omega0 = o.omega0;
@@ -186,6 +198,7 @@ int check_opts(const bmpc_opts &o) {
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > max_block_threads() || o.block_threads % 32))
         return BMPC_ERR_INVALID;
     if (o.blocks_per_sm < 0) return BMPC_ERR_INVALID;
+    if (o.variant < 0 || o.variant > 2) return BMPC_ERR_INVALID;
     return BMPC_OK;
 }
 
@@ -196,30 +209,23 @@ T *at(char *base, size_t off) {
     return reinterpret_cast<T *>(base + off);
 }
 
-/* Launch geometry: threads per problem and number of persistent blocks. */
-void geometry(const bmpc_batch *b, const bmpc_opts &o, int *grid, int *block) {
+/* Launch geometry for the problems of one model: threads per problem and persistent blocks. */
+void geometry(const bmpc_batch *b, const bmpc_opts &o, int model, int count, int *grid, int *block) {
     int bt = o.block_threads;
-    if (bt == 0) {
-        int maxn = 0;
-        for (int v : b->nodes) maxn = std::max(maxn, v);
-        bt = b->n == 1 ? (maxn > 1024 ? 256 : 128) : 64;
-    }
+    if (bt == 0) bt = count == 1 ? 128 : 32;
     int per_sm = o.blocks_per_sm;
     if (per_sm == 0) {
         int occ = 1;
-        if (occupancy(bt, &occ) != cudaSuccess || occ < 1) occ = 1;
+        if (occupancy(model, bt, &occ) != cudaSuccess || occ < 1) occ = 1;
         per_sm = occ;
     }
     *block = bt;
-    *grid = std::max(1, std::min(b->n, b->sm_count * per_sm));
+    *grid = std::max(1, std::min(count, b->sm_count * per_sm));
 }
 
 int launch(bmpc_batch *b, const bmpc_opts &o) {
     KernelArgs a;
     a.recs = at<const ProbRec>(b->data, b->L.recs);
-    a.order = at<const int32_t>(b->data, b->L.order);
-    a.n_problems = b->n;
-    a.queue = at<int32_t>(b->data, b->L.queue);
     a.ibase = at<const int32_t>(b->data, b->L.ints);
     a.inbase = at<const float>(b->data, b->L.in);
     a.warmbase = at<const float>(b->data, b->L.warm);
@@ -227,11 +233,21 @@ int launch(bmpc_batch *b, const bmpc_opts &o) {
     a.scr = b->scr;
     a.stats = at<Stats>(b->data, b->L.stats);
     a.opts = to_kopts(o);
-    int grid, block;
-    geometry(b, o, &grid, &block);
-    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), b->stream);
+    int32_t *queue = at<int32_t>(b->data, b->L.queue);
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t) * 4, b->stream);
     if (e != cudaSuccess) return BMPC_ERR_CUDA;
-    return cuda_status(launch_solve(a, grid, block, b->stream));
+    for (int m = 0; m < 3; ++m) {
+        const int cnt = b->model_begin[m + 1] - b->model_begin[m];
+        if (cnt == 0) continue;
+        a.order = at<const int32_t>(b->data, b->L.order) + b->model_begin[m];
+        a.n_problems = cnt;
+        a.queue = queue + m;
+        int grid, block;
+        geometry(b, o, m, cnt, &grid, &block);
+        e = launch_solve(a, m, grid, block, b->stream);
+        if (e != cudaSuccess) return BMPC_ERR_CUDA;
+    }
+    return BMPC_OK;
 }
 
 }  // namespace
@@ -241,7 +257,7 @@ extern "C" {
 void bmpc_default_opts(bmpc_opts *o) {
     if (!o) return;
     std::memset(o, 0, sizeof *o);
-    o->max_iters = 100;
+    o->max_iters = 50;
     o->max_outer = 60;
     o->n_alpha = 10;
     o->eps_tol = 1e-5f;
@@ -257,9 +273,10 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->mu0 = 1.f;
     o->beta = 1e-4f;
     o->ls_rel_eps = 1e-6f;
-    o->ls_chunk = 0;
+    o->ls_chunk = 2;
     o->block_threads = 0;
     o->blocks_per_sm = 0;
+    o->variant = 0;
 }
 
 int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
@@ -313,10 +330,17 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
     }
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
-    /* visiting order: largest trees first (longest-processing-time-first on the work queue) */
+    /* visiting order: grouped by model (one kernel each), largest trees first within a model
+       (longest-processing-time-first on the work queue) */
     b->order.resize(n);
     std::iota(b->order.begin(), b->order.end(), 0);
-    std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return b->nodes[a] > b->nodes[c]; });
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) {
+        if (b->recs[a].model != b->recs[c].model) return b->recs[a].model < b->recs[c].model;
+        return b->nodes[a] > b->nodes[c];
+    });
+    for (int m = 0; m < 4; ++m) b->model_begin[m] = 0;
+    for (int k = 0; k < n; ++k) b->model_begin[b->recs[k].model + 1]++;
+    for (int m = 0; m < 3; ++m) b->model_begin[m + 1] += b->model_begin[m];
     /* int tables of every tree, packed into the staging buffer and uploaded once */
     int32_t *ib = at<int32_t>(b->stage, b->L.ints);
     std::memset(ib, 0, sizeof(int32_t) * b->L.ints_n);
@@ -324,9 +348,11 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
         const bmpc_tree_desc &d = descs[k];
         const ProbRec &R = b->recs[k];
         int32_t *t = ib + R.off_int;
-        const int nn = R.n, np = R.npad;
-        int32_t *parent = t + IntRows::parent * np, *nch = t + IntRows::nchild * np, *fch = t + IntRows::fchild * np;
-        int32_t *stg = t + IntRows::stage * np, *leaf = t + IntRows::leaf * np, *ss = t + IntRows::stage_start * np;
+        const int nn = R.n, np = R.npad, ns = R.n_stage, S = R.n_paths;
+        const IntOff io = int_off(np, ns, S);
+        int32_t *parent = t + io.parent, *nch = t + io.nchild, *fch = t + io.fchild, *stg = t + io.stage;
+        int32_t *leaf = t + io.leaf, *owner = t + io.owner, *ss = t + io.sstart, *bst = t + io.bstage;
+        int32_t *ptab = t + io.ptab, *pdepth = t + io.pdepth, *ptop = t + io.ptop;
         for (int i = 0; i < nn; ++i) {
             parent[i] = d.parent[i];
             nch[i] = 0;
@@ -340,9 +366,34 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
             stg[i] = stg[p] + 1;
         }
         for (int i = nn - 1; i >= 0; --i) leaf[i] = nch[i] ? leaf[fch[i]] : i;
-        for (int s = 0; s <= R.n_stage; ++s) ss[s] = 0;
+        for (int s = 0; s <= ns; ++s) ss[s] = 0;
         for (int i = 0; i < nn; ++i) ss[stg[i] + 1]++;
-        for (int s = 0; s < R.n_stage; ++s) ss[s + 1] += ss[s];
+        for (int s = 0; s < ns; ++s) ss[s + 1] += ss[s];
+        /* paths: one per leaf in node order; a node belongs to the path of its first leaf */
+        std::vector<int> rank(nn, -1);
+        int np_ = 0;
+        for (int i = 0; i < nn; ++i)
+            if (nch[i] == 0) rank[i] = np_++;
+        for (int i = 0; i < nn; ++i) owner[i] = rank[leaf[i]];
+        for (int i = 0; i < nn; ++i) {
+            if (nch[i] != 0) continue;
+            const int s = rank[i];
+            pdepth[s] = stg[i];
+            for (int k = 0; k < ns; ++k) ptab[(size_t)s * ns + k] = -1;
+            int top = 0;
+            for (int j = i; j >= 0; j = parent[j]) {
+                ptab[(size_t)s * ns + stg[j]] = j;
+                if (owner[j] == s) top = stg[j];
+                if (j == 0) break;
+            }
+            ptop[s] = top;
+        }
+        int nb = 0;
+        for (int s = ns - 1; s >= 0; --s) {
+            bool branch = false;
+            for (int i = ss[s]; i < ss[s + 1]; ++i) branch |= nch[i] > 1;
+            if (branch) bst[nb++] = s;
+        }
     }
     std::memcpy(b->stage + b->L.order, b->order.data(), sizeof(int32_t) * n);
     cudaError_t e = cudaMemcpyAsync(b->data + b->L.order, b->stage + b->L.order, sizeof(int32_t) * n,

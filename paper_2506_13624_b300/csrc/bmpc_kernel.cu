@@ -43,8 +43,11 @@
 namespace bmpc {
 
 constexpr int MAX_BLOCK = 256;
+#ifndef BMPC_MIN_BLOCKS
+#define BMPC_MIN_BLOCKS 2   /* 256 threads x 2 blocks: at most 128 registers per thread */
+#endif
 constexpr int MAX_WARPS = MAX_BLOCK / 32;
-constexpr int MAX_CHUNK = 16;
+constexpr int MAX_CHUNK = 16;   /* at most 16 step sizes per line-search round */
 
 struct Shared {
     float red[MAX_WARPS][MAX_CHUNK + 1];
@@ -223,6 +226,9 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
             xn[i] = s;
         }
     } else {
+        /* The positions X, Y never enter the vehicle right-hand side, so their tangent columns
+         * stay the unit vectors: only the columns of (psi, ..., a, delta) are propagated. */
+        constexpr int C0 = 2;
         constexpr int NZ = NX + NU;
         float S[NX][NZ];
 #pragma unroll
@@ -259,10 +265,10 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
 #pragma unroll
                 for (int i = 0; i < NX; ++i)
 #pragma unroll
-                    for (int j = 0; j < NZ; ++j) {
+                    for (int j = C0; j < NZ; ++j) {
                         float acc = (j >= NX) ? Ju[i][j - NX] : 0.f;
 #pragma unroll
-                        for (int k = 0; k < NX; ++k) acc += J[i][k] * (S[k][j] + c * h * Dp[k][j]);
+                        for (int k = C0; k < NX; ++k) acc += J[i][k] * (S[k][j] + c * h * Dp[k][j]);
                         D[i][j] = acc;
                     }
 #pragma unroll
@@ -270,7 +276,7 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
                     ks[i] += wg * f[i];
                     kp[i] = f[i];
 #pragma unroll
-                    for (int j = 0; j < NZ; ++j) {
+                    for (int j = C0; j < NZ; ++j) {
                         Ds[i][j] += wg * D[i][j];
                         Dp[i][j] = D[i][j];
                     }
@@ -281,7 +287,7 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
             for (int i = 0; i < NX; ++i) {
                 z[i] += h6 * ks[i];
 #pragma unroll
-                for (int j = 0; j < NZ; ++j) S[i][j] += h6 * Ds[i][j];
+                for (int j = C0; j < NZ; ++j) S[i][j] += h6 * Ds[i][j];
             }
         }
 #pragma unroll
@@ -343,13 +349,22 @@ __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], cons
     }
 }
 
+/* Entry (a, b) of a stored Jacobian A_n.  For the vehicle models the columns of the positions
+ * X, Y are the unit vectors (positions do not enter the dynamics): they are compile-time
+ * constants, never stored or loaded. */
+template <int NX, int MODEL>
+__device__ __forceinline__ float aload(const float *A, int np, int i, int a, int b) {
+    if (MODEL != 2 && b < 2) return a == b ? 1.f : 0.f;
+    return A[(size_t)(a * NX + b) * np + i];
+}
+
 /* ------------------------------------------------------------------ problem view */
 template <int NX>
 struct View {
     int n, np, nc, nobs;
     bool box, lane;
     /* int rows */
-    const int32_t *parent, *nchild, *fchild, *stage, *leaf, *sstart;
+    const int32_t *parent, *nchild, *fchild, *stage, *leaf, *owner, *sstart, *bstage, *ptab, *pdepth, *ptop;
     /* inputs */
     const float *xref, *w, *obs, *wx, *wu, *wl, *wy;
     /* outputs */
@@ -364,12 +379,18 @@ struct View {
         nobs = R.n_obs;
         box = R.box_on != 0;
         lane = R.lane_on != 0;
-        parent = ib + IntRows::parent * np;
-        nchild = ib + IntRows::nchild * np;
-        fchild = ib + IntRows::fchild * np;
-        stage = ib + IntRows::stage * np;
-        leaf = ib + IntRows::leaf * np;
-        sstart = ib + IntRows::stage_start * np;
+        const IntOff io = int_off(np, R.n_stage, R.n_paths);
+        parent = ib + io.parent;
+        nchild = ib + io.nchild;
+        fchild = ib + io.fchild;
+        stage = ib + io.stage;
+        leaf = ib + io.leaf;
+        owner = ib + io.owner;
+        sstart = ib + io.sstart;
+        bstage = ib + io.bstage;
+        ptab = ib + io.ptab;
+        pdepth = ib + io.pdepth;
+        ptop = ib + io.ptop;
         const InRows ir = in_rows(NX, nobs);
         xref = fin + (size_t)ir.xref * np;
         w = fin + (size_t)ir.weight * np;
@@ -559,6 +580,376 @@ __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX>
     }
 }
 
+
+/* ------------------------------------------------------------------ tree Riccati step */
+/* Terminal value function of a leaf: P = Q_N + penalty Hessian, p = q (stored and returned). */
+template <int NX>
+__device__ __forceinline__ void leaf_value(const ProbRec &R, const View<NX> &V, int i, float (&P)[nsym(NX)],
+                                           float (&p)[NX]) {
+    constexpr int NS = nsym(NX);
+    const int np = V.np;
+    const float w = V.w[i];
+    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+#pragma unroll
+    for (int a = 0; a < NX; ++a)
+#pragma unroll
+        for (int b = a; b < NX; ++b) {
+            float v = (a == b) ? w * R.QNw[a] : 0.f;
+            if (a == 0 && b == 0) v += hxx;
+            if (a == 0 && b == 1) v += hxy;
+            if (a == 1 && b == 1) v += hyy;
+            P[sidx<NX>(a, b)] = v;
+        }
+#pragma unroll
+    for (int e = 0; e < NS; ++e) V.P[(size_t)e * np + i] = P[e];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        p[a] = V.q[(size_t)a * np + i];
+        V.p[(size_t)a * np + i] = p[a];
+    }
+}
+
+/* Adds the value function of child m to (Pb, pb): Pb += P_m, pb += p_m + P_m d_m, with
+ * P_m, p_m, d_m read from memory (Eq. tree_Riccati, sum over ch(n)). */
+template <int NX>
+__device__ __forceinline__ void add_child_mem(const View<NX> &V, int m, float (&Pb)[nsym(NX)], float (&pb)[NX]) {
+    constexpr int NS = nsym(NX);
+    const int np = V.np;
+    float Pm[NS], dm[NX];
+#pragma unroll
+    for (int e = 0; e < NS; ++e) {
+        Pm[e] = V.P[(size_t)e * np + m];
+        Pb[e] += Pm[e];
+    }
+    V.load_x(V.d, m, dm);
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        float v = V.p[(size_t)a * np + m];
+#pragma unroll
+        for (int b = 0; b < NX; ++b) v += Pm[sidx<NX>(a, b)] * dm[b];
+        pb[a] += v;
+    }
+}
+
+/* Riccati step of a non-leaf node n from the summed child value functions (Pb, pb):
+ * H_n = R_n + B'Pb B, K_n = -H^-1 (M_n + B'Pb A), k_n = -H^-1 (r_n + B'pb) of
+ * Eq. (tree_feedback_laws) (M_n = 0 here: no constraint couples x and u), then
+ * P_n = Q_n + A'Pb A + Qux'K, p_n = q_n + A'pb + Qux'k.  Stores K, k, P, p; returns P, p. */
+template <int NX, int MODEL>
+__device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V, int i, const float (&Pb)[nsym(NX)],
+                                             const float (&pb)[NX], float (&P)[nsym(NX)], float (&p)[NX],
+                                             Shared &sh) {
+    const int np = V.np;
+    const float w = V.w[i];
+    float q[NX];
+    V.load_x(V.q, i, q);
+    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+    float A[NX][NX], B[NX][NU];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+        for (int b = 0; b < NX; ++b) A[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
+#pragma unroll
+        for (int b = 0; b < NU; ++b) B[a][b] = V.B[(size_t)(a * NU + b) * np + i];
+    }
+    /* PA = Pbar A, PB = Pbar B */
+    float PA[NX][NX], PB[NX][NU];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+        for (int b = 0; b < NX; ++b) {
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += Pb[sidx<NX>(a, t)] * A[t][b];
+            PA[a][b] = v;
+        }
+#pragma unroll
+        for (int b = 0; b < NU; ++b) {
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += Pb[sidx<NX>(a, t)] * B[t][b];
+            PB[a][b] = v;
+        }
+    }
+    /* H blocks: Quu = R + B'PB, Qux = B'PA, qu = r + B'pbar, qx = q + A'pbar */
+    float Quu[NU][NU], Qux[NU][NX], qu[NU], qx[NX];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+#pragma unroll
+        for (int b = 0; b < NU; ++b) {
+            float v = (a == b) ? w * R.Rw[a] + V.hr[(size_t)a * np + i] : 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += B[t][a] * PB[t][b];
+            Quu[a][b] = v;
+        }
+#pragma unroll
+        for (int b = 0; b < NX; ++b) {
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += B[t][a] * PA[t][b];
+            Qux[a][b] = v;
+        }
+        float v = V.r[(size_t)a * np + i];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v += B[t][a] * pb[t];
+        qu[a] = v;
+    }
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        float v = q[a];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v += A[t][a] * pb[t];
+        qx[a] = v;
+    }
+    /* Cholesky of the 2x2 H_n, K = -H^-1 Qux, k = -H^-1 qu */
+    const float l00s = Quu[0][0];
+    const float l00 = sqrtf(fmaxf(l00s, 0.f));
+    const float l10 = Quu[1][0] / l00;
+    const float l11s = Quu[1][1] - l10 * l10;
+    if (!(l00s > 0.f) || !(l11s > 0.f)) sh.flag = 1;
+    const float l11 = sqrtf(fmaxf(l11s, 0.f));
+    float Kn[NU][NX], kn[NU];
+#pragma unroll
+    for (int b = 0; b < NX + 1; ++b) {
+        const float rhs0 = (b < NX) ? Qux[0][b] : qu[0];
+        const float rhs1 = (b < NX) ? Qux[1][b] : qu[1];
+        const float z0 = rhs0 / l00;
+        const float z1 = (rhs1 - l10 * z0) / l11;
+        const float s1 = z1 / l11;
+        const float s0 = (z0 - l10 * s1) / l00;
+        if (b < NX) {
+            Kn[0][b] = -s0;
+            Kn[1][b] = -s1;
+        } else {
+            kn[0] = -s0;
+            kn[1] = -s1;
+        }
+    }
+    /* P = Qxx + Qux'K with Qxx = Q + A'PA; p = qx + Qux'k */
+#pragma unroll
+    for (int a = 0; a < NX; ++a)
+#pragma unroll
+        for (int b = a; b < NX; ++b) {
+            float v = (a == b) ? w * R.Qw[a] : 0.f;
+            if (a == 0 && b == 0) v += hxx;
+            if (a == 0 && b == 1) v += hxy;
+            if (a == 1 && b == 1) v += hyy;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += A[t][a] * PA[t][b];
+#pragma unroll
+            for (int t = 0; t < NU; ++t) v += Qux[t][a] * Kn[t][b];
+            P[sidx<NX>(a, b)] = v;
+            V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
+        }
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        float v = qx[a];
+#pragma unroll
+        for (int t = 0; t < NU; ++t) v += Qux[t][a] * kn[t];
+        p[a] = v;
+        V.p[(size_t)a * np + i] = v;
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+#pragma unroll
+        for (int b = 0; b < NX; ++b) V.K[(size_t)(a * NX + b) * np + i] = Kn[a][b];
+        V.k[(size_t)a * np + i] = kn[a];
+    }
+}
+
+/* Level-synchronous backward sweep: all nodes of a stage in parallel, one barrier per stage. */
+template <int NX, int MODEL>
+__device__ void backward_level(const ProbRec &R, const View<NX> &V, Shared &sh) {
+    constexpr int NS = nsym(NX);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int st = R.n_stage - 1; st >= 0; --st) {
+        const int s0 = V.sstart[st], s1 = V.sstart[st + 1];
+        for (int i = s0 + tid; i < s1; i += nt) {
+            const int nch = V.nchild[i], fc = V.fchild[i];
+            float P[NS], p[NX];
+            if (nch == 0) {
+                leaf_value<NX>(R, V, i, P, p);
+                continue;
+            }
+            float Pb[NS], pb[NX];
+#pragma unroll
+            for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
+#pragma unroll
+            for (int a = 0; a < NX; ++a) pb[a] = 0.f;
+            for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
+            riccati_node<NX, MODEL>(R, V, i, Pb, pb, P, p, sh);
+        }
+        __syncthreads();
+    }
+}
+
+/* Per-scenario-path backward sweep: path s walks up from its leaf through the nodes it owns
+ * (the nodes whose first leaf descendant is its leaf), carrying the value function of the
+ * child in registers; the block synchronises only before the stages that hold branch nodes,
+ * where the children's value functions are summed from memory. */
+template <int NX, int MODEL>
+__device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
+    constexpr int NS = nsym(NX);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int S = R.n_paths, ns = R.n_stage, nb = R.n_bstage;
+    int hi = ns - 1;
+    for (int ph = 0; ph <= nb; ++ph) {
+        const int lo = (ph < nb) ? V.bstage[ph] : -1;    /* this phase covers stages (lo, hi] */
+        for (int s = tid; s < S; s += nt) {
+            const int depth = V.pdepth[s], top = V.ptop[s];
+            const int khi = min(depth, hi), klo = max(top, lo + 1);
+            if (khi < klo) continue;
+            const int32_t *path = V.ptab + (size_t)s * ns;
+            float P[NS], p[NX];
+            int k = khi;
+            {
+                const int i = path[k];
+                const int nch = V.nchild[i];
+                if (nch == 0) {
+                    leaf_value<NX>(R, V, i, P, p);
+                } else {
+                    float Pb[NS], pb[NX];
+#pragma unroll
+                    for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) pb[a] = 0.f;
+                    const int fc = V.fchild[i];
+                    for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
+                    riccati_node<NX, MODEL>(R, V, i, Pb, pb, P, p, sh);
+                }
+            }
+            for (k = khi - 1; k >= klo; --k) {
+                const int i = path[k], c = path[k + 1];   /* single child c, its value function in P, p */
+                float dm[NX], Pb[NS], pb[NX];
+                V.load_x(V.d, c, dm);
+#pragma unroll
+                for (int e = 0; e < NS; ++e) Pb[e] = 0.f + P[e];
+#pragma unroll
+                for (int a = 0; a < NX; ++a) {
+                    float v = p[a];
+#pragma unroll
+                    for (int b = 0; b < NX; ++b) v += P[sidx<NX>(a, b)] * dm[b];
+                    pb[a] = 0.f + v;
+                }
+                riccati_node<NX, MODEL>(R, V, i, Pb, pb, P, p, sh);
+            }
+        }
+        hi = lo;
+        __syncthreads();
+    }
+}
+
+/* Forward rollout at node i given the parent's (dx, du): dx_i = A_p dx_p + B_p du_p + d_i,
+ * du_i = K_i dx_i + k_i; with `own` also stores them, the QP multiplier lam_i = P_i dx_i + p_i
+ * and accumulates the directional terms of the merit. */
+template <int NX, int MODEL>
+__device__ __forceinline__ void forward_node(const ProbRec &R, const View<NX> &V, int i, const float (&dxp)[NX],
+                                             const float (&dup)[NU], float (&dxv)[NX], float (&duv)[NU], bool own,
+                                             float (&dir)[3]) {
+    const int np = V.np;
+    const int nch = V.nchild[i];
+    if (i == 0) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) dxv[j] = 0.f;
+    } else {
+        const int pa = V.parent[i];
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+            float v = V.d[(size_t)a * np + i];
+#pragma unroll
+            for (int b = 0; b < NX; ++b) v += aload<NX, MODEL>(V.A, np, pa, a, b) * dxp[b];
+#pragma unroll
+            for (int b = 0; b < NU; ++b) v += V.B[(size_t)(a * NU + b) * np + pa] * dup[b];
+            dxv[a] = v;
+        }
+    }
+    duv[0] = duv[1] = 0.f;
+    if (nch) {
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+            float v = V.k[(size_t)a * np + i];
+#pragma unroll
+            for (int b = 0; b < NX; ++b) v += V.K[(size_t)(a * NX + b) * np + i] * dxv[b];
+            duv[a] = v;
+        }
+    }
+    if (!own) return;
+    V.store_x(V.dx, i, dxv);
+    V.store_u(V.du, i, duv);
+    const float w = V.w[i];
+    const float *Qd = nch ? R.Qw : R.QNw;
+    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        dir[0] += V.q[(size_t)a * np + i] * dxv[a];
+        dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+    }
+    dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
+    if (nch) {
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+            dir[0] += V.r[(size_t)a * np + i] * duv[a];
+            dir[1] += (w * R.Rw[a] + V.hr[(size_t)a * np + i]) * duv[a] * duv[a];
+        }
+    }
+    if (i != 0) {
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+            float v = V.p[(size_t)a * np + i];
+#pragma unroll
+            for (int b = 0; b < NX; ++b) v += V.P[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
+            V.lq[(size_t)a * np + i] = v;
+            const float lam = V.L[(size_t)a * np + i];
+            dir[2] += ((v - lam) - lam) * V.d[(size_t)a * np + i];
+        }
+    }
+}
+
+/* Level-synchronous forward sweep: one barrier per stage, parents' (dx, du) read from memory. */
+template <int NX, int MODEL>
+__device__ void forward_level(const ProbRec &R, const View<NX> &V, float (&dir)[3]) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int st = 0; st < R.n_stage; ++st) {
+        const int s0 = V.sstart[st], s1 = V.sstart[st + 1];
+        for (int i = s0 + tid; i < s1; i += nt) {
+            float dxp[NX], dup[NU] = {0.f, 0.f}, dxv[NX], duv[NU];
+#pragma unroll
+            for (int j = 0; j < NX; ++j) dxp[j] = 0.f;
+            if (i != 0) {
+                V.load_x(V.dx, V.parent[i], dxp);
+                V.load_u(V.du, V.parent[i], dup);
+            }
+            forward_node<NX, MODEL>(R, V, i, dxp, dup, dxv, duv, true, dir);
+        }
+        __syncthreads();
+    }
+}
+
+/* Per-scenario-path forward sweep: path s rolls out from the root to its leaf with (dx, du) in
+ * registers and no barrier; nodes shared by several paths are recomputed identically by each
+ * and written only by their owner path. */
+template <int NX, int MODEL>
+__device__ void forward_path(const ProbRec &R, const View<NX> &V, float (&dir)[3]) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int S = R.n_paths, ns = R.n_stage;
+    for (int s = tid; s < S; s += nt) {
+        const int32_t *path = V.ptab + (size_t)s * ns;
+        const int depth = V.pdepth[s], top = V.ptop[s];
+        float dxp[NX], dup[NU] = {0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < NX; ++j) dxp[j] = 0.f;
+        for (int k = 0; k <= depth; ++k) {
+            float dxv[NX], duv[NU];
+            forward_node<NX, MODEL>(R, V, path[k], dxp, dup, dxv, duv, k >= top, dir);
+#pragma unroll
+            for (int j = 0; j < NX; ++j) dxp[j] = dxv[j];
+            dup[0] = duv[0];
+            dup[1] = duv[1];
+        }
+    }
+    __syncthreads();
+}
+
 /* ------------------------------------------------------------------ the per-problem solver */
 template <int NX, int MODEL>
 __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
@@ -609,6 +1000,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
     float r_kkt = INFINITY, cviol = INFINITY;
     int inner = 0, outer = 0, ls_fail = 0, ls_fail_total = 0, ls_evals = 0, status = 1 /* MAX_ITER */;
     const int G = (O.ls_chunk <= 0 || O.ls_chunk > MAX_CHUNK) ? min(O.n_alpha, MAX_CHUNK) : O.ls_chunk;
+    const bool path_variant = O.variant != 1;   /* 1: level-synchronous sweeps, else per-path */
 
     while (outer < O.max_outer) {
         ++outer;
@@ -637,7 +1029,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
 #pragma unroll
                     for (int a = 0; a < NX; ++a) {
 #pragma unroll
-                        for (int b = 0; b < NX; ++b) V.A[(size_t)(a * NX + b) * np + i] = A[a][b];
+                        for (int b = (MODEL == 2 ? 0 : 2); b < NX; ++b) V.A[(size_t)(a * NX + b) * np + i] = A[a][b];
 #pragma unroll
                         for (int b = 0; b < NU; ++b) V.B[(size_t)(a * NU + b) * np + i] = B[a][b];
                     }
@@ -675,7 +1067,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
 #pragma unroll
                         for (int a = 0; a < NX; ++a)
 #pragma unroll
-                            for (int b = 0; b < NX; ++b) gx[b] += V.A[(size_t)(a * NX + b) * np + i] * lsum[a];
+                            for (int b = 0; b < NX; ++b) gx[b] += aload<NX, MODEL>(V.A, np, i, a, b) * lsum[a];
                     }
 #pragma unroll
                     for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
@@ -710,162 +1102,9 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             t0 = clock64();
             if (tid == 0) sh.flag = 0;
             __syncthreads();
-            for (int st = n_stage - 1; st >= 0; --st) {
-                const int s0 = V.sstart[st], s1 = V.sstart[st + 1];
-                for (int i = s0 + tid; i < s1; i += nt) {
-                    const int nch = V.nchild[i], fc = V.fchild[i];
-                    const float w = V.w[i];
-                    float q[NX];
-                    V.load_x(V.q, i, q);
-                    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
-                    if (nch == 0) {
-#pragma unroll
-                        for (int a = 0; a < NX; ++a)
-#pragma unroll
-                            for (int b = a; b < NX; ++b) {
-                                float v = (a == b) ? w * R.QNw[a] : 0.f;
-                                if (a == 0 && b == 0) v += hxx;
-                                if (a == 0 && b == 1) v += hxy;
-                                if (a == 1 && b == 1) v += hyy;
-                                V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
-                            }
-                        V.store_x(V.p, i, q);
-                        continue;
-                    }
-                    /* child sums: Pbar = sum P_m, pbar = sum (p_m + P_m d_m) */
-                    float Pb[NS], pb[NX];
-#pragma unroll
-                    for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
-#pragma unroll
-                    for (int a = 0; a < NX; ++a) pb[a] = 0.f;
-                    for (int m = fc; m < fc + nch; ++m) {
-                        float Pm[NS], dm[NX];
-#pragma unroll
-                        for (int e = 0; e < NS; ++e) {
-                            Pm[e] = V.P[(size_t)e * np + m];
-                            Pb[e] += Pm[e];
-                        }
-                        V.load_x(V.d, m, dm);
-#pragma unroll
-                        for (int a = 0; a < NX; ++a) {
-                            float v = V.p[(size_t)a * np + m];
-#pragma unroll
-                            for (int b = 0; b < NX; ++b) v += Pm[sidx<NX>(a, b)] * dm[b];
-                            pb[a] += v;
-                        }
-                    }
-                    float A[NX][NX], B[NX][NU];
-#pragma unroll
-                    for (int a = 0; a < NX; ++a) {
-#pragma unroll
-                        for (int b = 0; b < NX; ++b) A[a][b] = V.A[(size_t)(a * NX + b) * np + i];
-#pragma unroll
-                        for (int b = 0; b < NU; ++b) B[a][b] = V.B[(size_t)(a * NU + b) * np + i];
-                    }
-                    /* PA = Pbar A, PB = Pbar B */
-                    float PA[NX][NX], PB[NX][NU];
-#pragma unroll
-                    for (int a = 0; a < NX; ++a) {
-#pragma unroll
-                        for (int b = 0; b < NX; ++b) {
-                            float v = 0.f;
-#pragma unroll
-                            for (int t = 0; t < NX; ++t) v += Pb[sidx<NX>(a, t)] * A[t][b];
-                            PA[a][b] = v;
-                        }
-#pragma unroll
-                        for (int b = 0; b < NU; ++b) {
-                            float v = 0.f;
-#pragma unroll
-                            for (int t = 0; t < NX; ++t) v += Pb[sidx<NX>(a, t)] * B[t][b];
-                            PB[a][b] = v;
-                        }
-                    }
-                    /* H blocks: Quu = R + B'PB, Qux = B'PA, qu = r + B'pbar, qx = q + A'pbar */
-                    float Quu[NU][NU], Qux[NU][NX], qu[NU], qx[NX];
-#pragma unroll
-                    for (int a = 0; a < NU; ++a) {
-#pragma unroll
-                        for (int b = 0; b < NU; ++b) {
-                            float v = (a == b) ? w * R.Rw[a] + V.hr[(size_t)a * np + i] : 0.f;
-#pragma unroll
-                            for (int t = 0; t < NX; ++t) v += B[t][a] * PB[t][b];
-                            Quu[a][b] = v;
-                        }
-#pragma unroll
-                        for (int b = 0; b < NX; ++b) {
-                            float v = 0.f;
-#pragma unroll
-                            for (int t = 0; t < NX; ++t) v += B[t][a] * PA[t][b];
-                            Qux[a][b] = v;
-                        }
-                        float v = V.r[(size_t)a * np + i];
-#pragma unroll
-                        for (int t = 0; t < NX; ++t) v += B[t][a] * pb[t];
-                        qu[a] = v;
-                    }
-#pragma unroll
-                    for (int a = 0; a < NX; ++a) {
-                        float v = q[a];
-#pragma unroll
-                        for (int t = 0; t < NX; ++t) v += A[t][a] * pb[t];
-                        qx[a] = v;
-                    }
-                    /* Cholesky of the 2x2 H_n, K = -H^-1 Qux, k = -H^-1 qu */
-                    const float l00s = Quu[0][0];
-                    const float l00 = sqrtf(fmaxf(l00s, 0.f));
-                    const float l10 = Quu[1][0] / l00;
-                    const float l11s = Quu[1][1] - l10 * l10;
-                    if (!(l00s > 0.f) || !(l11s > 0.f)) sh.flag = 1;
-                    const float l11 = sqrtf(fmaxf(l11s, 0.f));
-                    float Kn[NU][NX], kn[NU];
-#pragma unroll
-                    for (int b = 0; b < NX + 1; ++b) {
-                        const float rhs0 = (b < NX) ? Qux[0][b] : qu[0];
-                        const float rhs1 = (b < NX) ? Qux[1][b] : qu[1];
-                        const float z0 = rhs0 / l00;
-                        const float z1 = (rhs1 - l10 * z0) / l11;
-                        const float s1 = z1 / l11;
-                        const float s0 = (z0 - l10 * s1) / l00;
-                        if (b < NX) {
-                            Kn[0][b] = -s0;
-                            Kn[1][b] = -s1;
-                        } else {
-                            kn[0] = -s0;
-                            kn[1] = -s1;
-                        }
-                    }
-                    /* P = Qxx + Qux'K with Qxx = Q + A'PA; p = qx + Qux'k */
-#pragma unroll
-                    for (int a = 0; a < NX; ++a)
-#pragma unroll
-                        for (int b = a; b < NX; ++b) {
-                            float v = (a == b) ? w * R.Qw[a] : 0.f;
-                            if (a == 0 && b == 0) v += hxx;
-                            if (a == 0 && b == 1) v += hxy;
-                            if (a == 1 && b == 1) v += hyy;
-#pragma unroll
-                            for (int t = 0; t < NX; ++t) v += A[t][a] * PA[t][b];
-#pragma unroll
-                            for (int t = 0; t < NU; ++t) v += Qux[t][a] * Kn[t][b];
-                            V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
-                        }
-#pragma unroll
-                    for (int a = 0; a < NX; ++a) {
-                        float v = qx[a];
-#pragma unroll
-                        for (int t = 0; t < NU; ++t) v += Qux[t][a] * kn[t];
-                        V.p[(size_t)a * np + i] = v;
-                    }
-#pragma unroll
-                    for (int a = 0; a < NU; ++a) {
-#pragma unroll
-                        for (int b = 0; b < NX; ++b) V.K[(size_t)(a * NX + b) * np + i] = Kn[a][b];
-                        V.k[(size_t)a * np + i] = kn[a];
-                    }
-                }
-                __syncthreads();
-            }
+            if (path_variant) backward_path<NX, MODEL>(R, V, sh);
+            else backward_level<NX, MODEL>(R, V, sh);
+            __syncthreads();
             c_bwd += clock64() - t0;
             if (sh.flag) {
                 status = -3;
@@ -875,71 +1114,8 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             /* ===== forward: linear rollout from the root, QP multipliers */
             t0 = clock64();
             float dir[3] = {0.f, 0.f, 0.f};   /* grad'dz, dz'W dz, (dlam - lam)'d */
-            for (int st = 0; st < n_stage; ++st) {
-                const int s0 = V.sstart[st], s1 = V.sstart[st + 1];
-                for (int i = s0 + tid; i < s1; i += nt) {
-                    const int nch = V.nchild[i];
-                    const float w = V.w[i];
-                    float dxv[NX], duv[NU] = {0.f, 0.f};
-                    if (i == 0) {
-#pragma unroll
-                        for (int j = 0; j < NX; ++j) dxv[j] = 0.f;
-                    } else {
-                        const int pa = V.parent[i];
-                        float dxp[NX], dup[NU];
-                        V.load_x(V.dx, pa, dxp);
-                        V.load_u(V.du, pa, dup);
-#pragma unroll
-                        for (int a = 0; a < NX; ++a) {
-                            float v = V.d[(size_t)a * np + i];
-#pragma unroll
-                            for (int b = 0; b < NX; ++b) v += V.A[(size_t)(a * NX + b) * np + pa] * dxp[b];
-#pragma unroll
-                            for (int b = 0; b < NU; ++b) v += V.B[(size_t)(a * NU + b) * np + pa] * dup[b];
-                            dxv[a] = v;
-                        }
-                    }
-                    if (nch) {
-#pragma unroll
-                        for (int a = 0; a < NU; ++a) {
-                            float v = V.k[(size_t)a * np + i];
-#pragma unroll
-                            for (int b = 0; b < NX; ++b) v += V.K[(size_t)(a * NX + b) * np + i] * dxv[b];
-                            duv[a] = v;
-                        }
-                    }
-                    V.store_x(V.dx, i, dxv);
-                    V.store_u(V.du, i, duv);
-                    /* directional terms of the merit */
-                    const float *Qd = nch ? R.Qw : R.QNw;
-                    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
-#pragma unroll
-                    for (int a = 0; a < NX; ++a) {
-                        dir[0] += V.q[(size_t)a * np + i] * dxv[a];
-                        dir[1] += w * Qd[a] * dxv[a] * dxv[a];
-                    }
-                    dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
-                    if (nch) {
-#pragma unroll
-                        for (int a = 0; a < NU; ++a) {
-                            dir[0] += V.r[(size_t)a * np + i] * duv[a];
-                            dir[1] += (w * R.Rw[a] + V.hr[(size_t)a * np + i]) * duv[a] * duv[a];
-                        }
-                    }
-                    if (i != 0) {
-#pragma unroll
-                        for (int a = 0; a < NX; ++a) {
-                            float v = V.p[(size_t)a * np + i];
-#pragma unroll
-                            for (int b = 0; b < NX; ++b) v += V.P[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
-                            V.lq[(size_t)a * np + i] = v;
-                            const float lam = V.L[(size_t)a * np + i];
-                            dir[2] += ((v - lam) - lam) * V.d[(size_t)a * np + i];
-                        }
-                    }
-                }
-                __syncthreads();
-            }
+            if (path_variant) forward_path<NX, MODEL>(R, V, dir);
+            else forward_level<NX, MODEL>(R, V, dir);
             block_sum<3>(dir, sh);
             c_fwd += clock64() - t0;
 
@@ -958,23 +1134,22 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             float alpha = ldexpf(1.f, -(O.n_alpha - 1));
             bool accepted = false;
             for (int a0 = 0; a0 < O.n_alpha && !accepted; a0 += G) {
-                float acc[MAX_CHUNK];
-#pragma unroll
-                for (int a = 0; a < MAX_CHUNK; ++a) acc[a] = 0.f;
-                for (int i = tid; i < n; i += nt) {
-                    const int nch = V.nchild[i], fc = V.fchild[i];
-                    const bool is_leaf = nch == 0;
-                    float x[NX], u[NU], dxv[NX], duv[NU];
-                    V.load_x(V.X, i, x);
-                    V.load_u(V.U, i, u);
-                    V.load_x(V.dx, i, dxv);
-                    V.load_u(V.du, i, duv);
-                    float base = V.nv[i];
-                    for (int m = fc; m < fc + nch; ++m) base += V.nv[(size_t)np + m] + 0.5f * mu * V.nv[2 * (size_t)np + m];
-#pragma unroll
-                    for (int a = 0; a < MAX_CHUNK; ++a) {
-                        if (a >= G || a0 + a >= O.n_alpha) break;
-                        const float al = ldexpf(1.f, -(a0 + a));
+                const int cnt = min(G, O.n_alpha - a0);
+#pragma unroll 1
+                for (int a = 0; a < cnt; ++a) {
+                    const float al = ldexpf(1.f, -(a0 + a));
+                    float acc = 0.f;
+                    for (int i = tid; i < n; i += nt) {
+                        const int nch = V.nchild[i], fc = V.fchild[i];
+                        const bool is_leaf = nch == 0;
+                        float x[NX], u[NU], dxv[NX], duv[NU];
+                        V.load_x(V.X, i, x);
+                        V.load_u(V.U, i, u);
+                        V.load_x(V.dx, i, dxv);
+                        V.load_u(V.du, i, duv);
+                        float base = V.nv[i];
+                        for (int m = fc; m < fc + nch; ++m)
+                            base += V.nv[(size_t)np + m] + 0.5f * mu * V.nv[2 * (size_t)np + m];
                         float xt[NX], ut[NU], qd[NX], rd[NU], hqd[3], hrd[NU];
 #pragma unroll
                         for (int j = 0; j < NX; ++j) xt[j] = x[j] + al * dxv[j];
@@ -998,20 +1173,25 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                                 }
                             }
                         }
-                        acc[a] += v - base;
+                        acc += v - base;
                     }
-                }
-                block_sum<MAX_CHUNK>(acc, sh);
-                ls_evals += min(G, O.n_alpha - a0);
 #pragma unroll
-                for (int a = 0; a < MAX_CHUNK; ++a) {
-                    if (a >= G || a0 + a >= O.n_alpha || accepted) continue;
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if ((tid & 31) == 0) sh.red[tid >> 5][a] = acc;
+                }
+                __syncthreads();
+                ls_evals += cnt;
+                const int nw = nt >> 5;
+                for (int a = 0; a < cnt && !accepted; ++a) {
+                    float s = 0.f;
+                    for (int w = 0; w < nw; ++w) s += sh.red[w][a];
                     const float al = ldexpf(1.f, -(a0 + a));
-                    if (acc[a] <= O.beta * al * dphi + O.ls_rel_eps * fabsf(phi0)) {
+                    if (s <= O.beta * al * dphi + O.ls_rel_eps * fabsf(phi0)) {
                         alpha = al;
                         accepted = true;
                     }
                 }
+                __syncthreads();
             }
             if (accepted) ls_fail = 0;
             else {
@@ -1116,7 +1296,10 @@ done:
     }
 }
 
-__global__ void __launch_bounds__(MAX_BLOCK) bmpc_solve_kernel(KernelArgs args) {
+/* One kernel per dynamics model, so that each carries only its own code and registers. */
+template <int MODEL>
+__global__ void __launch_bounds__(MAX_BLOCK, BMPC_MIN_BLOCKS) bmpc_solve_kernel(KernelArgs args) {
+    constexpr int NX = MODEL == 1 ? 6 : 4;
     __shared__ Shared sh;
     __shared__ int pid_s;
     for (;;) {
@@ -1127,28 +1310,25 @@ __global__ void __launch_bounds__(MAX_BLOCK) bmpc_solve_kernel(KernelArgs args) 
         if (slot >= args.n_problems) break;
         const int pid = args.order[slot];
         const ProbRec &R = args.recs[pid];
-        const int32_t *ib = args.ibase + R.off_int;
-        const float *fin = args.inbase + R.off_in;
-        const float *fw = args.warmbase + R.off_warm;
-        float *fout = args.outbase + R.off_out;
-        float *fs = args.scr + R.off_scr;
-        Stats *st = args.stats + pid;
-        if (R.model == 0) solve_problem<4, 0>(R, ib, fin, fw, fout, fs, st, args.opts, sh);
-        else if (R.model == 1) solve_problem<6, 1>(R, ib, fin, fw, fout, fs, st, args.opts, sh);
-        else solve_problem<4, 2>(R, ib, fin, fw, fout, fs, st, args.opts, sh);
+        solve_problem<NX, MODEL>(R, args.ibase + R.off_int, args.inbase + R.off_in, args.warmbase + R.off_warm,
+                                 args.outbase + R.off_out, args.scr + R.off_scr, args.stats + pid, args.opts, sh);
     }
 }
 
-/* Launch helper used by the host API. */
-cudaError_t launch_solve(const KernelArgs &args, int grid, int block, cudaStream_t stream) {
-    bmpc_solve_kernel<<<grid, block, 0, stream>>>(args);
+/* Launch helper used by the host API: `args.order` lists problems of `model` only. */
+cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, cudaStream_t stream) {
+    if (model == 0) bmpc_solve_kernel<0><<<grid, block, 0, stream>>>(args);
+    else if (model == 1) bmpc_solve_kernel<1><<<grid, block, 0, stream>>>(args);
+    else bmpc_solve_kernel<2><<<grid, block, 0, stream>>>(args);
     return cudaGetLastError();
 }
 
 int max_block_threads() { return MAX_BLOCK; }
 
-cudaError_t occupancy(int block, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel, block, 0);
+cudaError_t occupancy(int model, int block, int *blocks_per_sm) {
+    if (model == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<0>, block, 0);
+    if (model == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<1>, block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<2>, block, 0);
 }
 
 }  // namespace bmpc

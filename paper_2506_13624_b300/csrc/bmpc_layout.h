@@ -23,7 +23,8 @@ __host__ __device__ constexpr int nsym(int nx) { return nx * (nx + 1) / 2; }
 
 /* One record per problem; 16-byte aligned, plain data. */
 struct alignas(16) ProbRec {
-    int32_t n, npad, nx, nu, model, n_obs, nc, box_on, lane_on, n_stage, has_warm, pad0;
+    int32_t n, npad, nx, nu, model, n_obs, nc, box_on, lane_on, n_stage, has_warm, n_paths;
+    int32_t n_bstage, rsv0, rsv1, rsv2;  /* n_bstage: distinct stages holding branch nodes */
     int64_t off_int;   /* int32 elements from the int region base      */
     int64_t off_in;    /* float elements from the input region base    */
     int64_t off_warm;  /* float elements from the warm-start region base */
@@ -36,13 +37,34 @@ struct alignas(16) ProbRec {
     float Alin[16], Blin[8];
 };
 
-/* int region of one problem, in rows of npad int32 */
-struct IntRows {
-    static constexpr int parent = 0, nchild = 1, fchild = 2, stage = 3, leaf = 4, stage_start = 5;
-    /* stage_start occupies round_up(n_stage + 1, 32) ints after the 5 node rows */
+/* int region of one problem (int32 elements):
+ *   node rows (npad each): parent, nchild, fchild (first child), stage, leaf (first leaf
+ *   descendant), owner (index of the path of that leaf; the path that processes the node in
+ *   the per-path sweeps);
+ *   stage_start [n_stage + 1]   first node of every stage (level order);
+ *   bstage      [n_bstage]      stages holding nodes with more than one child, descending;
+ *   ptab        [n_paths][n_stage]  node of every root-to-leaf path at every stage (-1 past
+ *                                   the path's leaf);
+ *   pdepth, ptop [n_paths]      stage of the path's leaf, first stage the path owns.
+ * Every block is padded to a multiple of 32 elements. */
+struct IntOff {
+    int64_t parent, nchild, fchild, stage, leaf, owner, sstart, bstage, ptab, pdepth, ptop, total;
 };
-__host__ __device__ inline int64_t int_elems(int npad, int n_stage) {
-    return 5LL * npad + round_up(n_stage + 1, 32);
+__host__ __device__ inline IntOff int_off(int npad, int n_stage, int n_paths) {
+    IntOff o;
+    o.parent = 0;
+    o.nchild = npad;
+    o.fchild = 2LL * npad;
+    o.stage = 3LL * npad;
+    o.leaf = 4LL * npad;
+    o.owner = 5LL * npad;
+    o.sstart = 6LL * npad;
+    o.bstage = o.sstart + round_up(n_stage + 1, 32);
+    o.ptab = o.bstage + round_up(n_stage + 1, 32);
+    o.pdepth = o.ptab + round_up(n_paths * n_stage, 32);
+    o.ptop = o.pdepth + round_up(n_paths, 32);
+    o.total = o.ptop + round_up(n_paths, 32);
+    return o;
 }
 
 /* input region: xref[nx] weight[1] obs[5*n_obs] (rows of npad) */
@@ -115,7 +137,7 @@ __host__ __device__ inline ScrRows scr_rows(int nx) {
 
 /* Kernel-side copy of the solver options (Algorithm 1 constants). */
 struct KOpts {
-    int32_t max_iters, max_outer, n_alpha, ls_chunk;
+    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant;
     float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps;
 };
 

@@ -182,6 +182,19 @@ def test_batch_equals_single():
             assert np.array_equal(g[key], s[key])
 
 
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_level_and_path_variants_agree(cfg):
+    """The level-synchronous and per-path sweeps compute the same search directions."""
+    ps = scenes.instances(cfg, 3 if cfg == 2 else 1, seed0=3)
+    lev = _gpu(ps, variant=1)
+    pth = _gpu(ps, variant=2)
+    for p, a, b in zip(ps, lev, pth):
+        assert a["status"] == b["status"] == oracle.OK
+        assert abs(a["inner_iters"] - b["inner_iters"]) <= 1
+        tol = 1e-4 * max(1.0, np.abs(a["u"]).max())
+        np.testing.assert_allclose(a["u"], b["u"], atol=tol)
+
+
 def test_invalid_problem_rejected():
     from paper_2506_13624_b300 import bmpc
     p = dict(scenes.config1(0))
