@@ -171,6 +171,24 @@ int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float
 
 void bmpc_destroy_batch(bmpc_batch *b);
 
+/* ---- creation without a scratch arena (no counterpart in the paper) ----
+ * For callers that cannot allocate device memory for the solver, e.g. a real-time control
+ * loop that forbids allocation once running, or a plug-in whose host framework owns all device
+ * buffers.  Same as bmpc_create_batch except that the solver scratch is a fixed array of
+ * BMPC_STATIC_SCRATCH_BYTES (16 MiB) inside the library; the caller still provides the data
+ * arena with the inputs and outputs, and drives the handle with the usual calls.
+ *   - Allocates no device memory (no cudaMalloc, cudaFree or allocating library call).
+ *   - Returns BMPC_ERR_SPACE when the batch needs more scratch than the array holds
+ *     (bmpc_batch_bytes reports the need).
+ *   - The first call on a device looks up the array's device address with that device current;
+ *     make that first call before any stream capture starts.
+ *   - Every handle made this way shares the one array: solves of such handles must not overlap
+ *     on the GPU (they would race), e.g. issue them on one stream.  The array keeps the last
+ *     solve's contents; no entry needs to start at zero. */
+#define BMPC_STATIC_SCRATCH_BYTES (16u << 20)
+int bmpc_create_batch_static(const bmpc_tree_desc *descs, int32_t n, void *dev_data, size_t data_bytes,
+                             void *host_staging, size_t staging_bytes, void *stream, bmpc_batch **out);
+
 /* ---- single-tree interface of the paper's problem statement (a batch of one) ---- */
 typedef bmpc_batch bmpc_tree;
 int bmpc_tree_bytes(const bmpc_tree_desc *desc, size_t *data_bytes, size_t *scratch_bytes, size_t *staging_bytes);

@@ -77,6 +77,8 @@ def lib() -> C.CDLL:
         L.bmpc_get_solutions.argtypes = [C.c_void_p, _fp, _fp, _fp, _fp, C.POINTER(Stats)]
         L.bmpc_destroy_batch.argtypes = [C.c_void_p]
         L.bmpc_default_opts.argtypes = [C.POINTER(Opts)]
+        L.bmpc_create_batch_static.argtypes = [C.POINTER(TreeDesc), C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
+                                               C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]
         L.bmpc_problem_device_outputs.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
                                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                                   C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]
@@ -87,7 +89,9 @@ def lib() -> C.CDLL:
 EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_set_problems", "bmpc_solve_batch",
             "bmpc_solve_batch_graph", "bmpc_get_solutions", "bmpc_problem_device_outputs", "bmpc_destroy_batch",
             "bmpc_tree_bytes", "bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution",
-            "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version"]
+            "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static"]
+
+STATIC_SCRATCH_BYTES = 16 << 20
 
 
 def status_str(s: int) -> str:
@@ -267,3 +271,47 @@ def solve(problems, opts: Opts | None = None, warm=None, graph: bool = False):
     res = b.get_solutions()
     b.close()
     return res
+
+
+class StaticScratchBatch(Batch):
+    """A batch whose solver scratch is the library's fixed 16 MiB device array.
+
+    For callers that cannot allocate device memory for the solver (real-time loops, plug-ins
+    whose framework owns the device buffers): only the data arena (inputs and outputs) is
+    supplied here; bmpc_create_batch_static allocates nothing.  All such batches share the one
+    array, so their solves must not overlap on the GPU.
+    """
+
+    def __init__(self, problems, device=None, stream=None, pinned: bool = True):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("bmpc needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.problems = list(problems)
+        self.n = len(self.problems)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        descs = (TreeDesc * self.n)()
+        self._parents = []
+        for k, p in enumerate(self.problems):
+            d, par = tree_desc(p)
+            descs[k] = d
+            self._parents.append(par)
+        self._descs = descs
+        db, sb, hb = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        _check(lib().bmpc_batch_bytes(descs, self.n, C.byref(db), C.byref(sb), C.byref(hb)), "bmpc_batch_bytes")
+        self.data_bytes, self.scratch_bytes, self.staging_bytes = db.value, sb.value, hb.value
+        with torch.cuda.device(self.device):
+            self._data = torch.empty(self.data_bytes + 256, dtype=torch.uint8, device=self.device)
+        self._stage = torch.empty(self.staging_bytes, dtype=torch.uint8, pin_memory=pinned)
+        dptr = (self._data.data_ptr() + 255) // 256 * 256
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().bmpc_create_batch_static(descs, self.n, dptr, self.data_bytes, self._stage.data_ptr(),
+                                                  self.staging_bytes, C.c_void_p(self.stream.cuda_stream),
+                                                  C.byref(h)), "bmpc_create_batch_static")
+        self.handle = h
+        self.nodes = np.array([int(p["n"]) for p in self.problems])
+        self.nx = np.array([int(p["nx"]) for p in self.problems])
+        self.nc = np.array([n_con(p) for p in self.problems])
