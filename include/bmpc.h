@@ -112,9 +112,11 @@ typedef struct {
                                depend on it: it only trades parallel work for extra rounds. */
     int32_t block_threads;  /* threads per problem (32..1024, multiple of 32); 0 = automatic */
     int32_t blocks_per_sm;  /* resident problems per SM; 0 = automatic */
-    int32_t variant;        /* tree sweeps: 0 automatic (per-path), 1 level-synchronous (one barrier per
-                               stage, nodes of a stage in parallel), 2 per-scenario-path (one thread per
-                               root-to-leaf path, barriers only at branch stages); same search direction */
+    int32_t variant;        /* tree sweeps: 0 automatic (= 2), 1 level-synchronous (one barrier per stage,
+                               nodes of a stage in parallel), 2 per-scenario-path (one thread per
+                               root-to-leaf path, barriers only at branch stages), 3 per-scenario-path
+                               with 8 lanes per path (lane j owns column j of [A B], P and H);
+                               all compute the same search direction */
 } bmpc_opts;
 
 typedef struct {

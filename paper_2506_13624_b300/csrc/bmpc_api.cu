@@ -198,7 +198,8 @@ int check_opts(const bmpc_opts &o) {
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > max_block_threads() || o.block_threads % 32))
         return BMPC_ERR_INVALID;
     if (o.blocks_per_sm < 0) return BMPC_ERR_INVALID;
-    if (o.variant < 0 || o.variant > 2) return BMPC_ERR_INVALID;
+    if (o.variant < 0 || o.variant > 3) return BMPC_ERR_INVALID;
+    if ((o.variant == 0 || o.variant == 3) && o.block_threads != 0 && o.block_threads % 32) return BMPC_ERR_INVALID;
     return BMPC_OK;
 }
 

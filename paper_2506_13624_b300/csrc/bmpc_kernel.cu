@@ -49,8 +49,11 @@ constexpr int MAX_BLOCK = 256;
 constexpr int MAX_WARPS = MAX_BLOCK / 32;
 constexpr int MAX_CHUNK = 16;   /* at most 16 step sizes per line-search round */
 
+constexpr int GL = 8;   /* lanes per path in the cooperative sweeps (one per column of [A B], nx + nu <= 8) */
+
 struct Shared {
     float red[MAX_WARPS][MAX_CHUNK + 1];
+    float tr[MAX_BLOCK / GL][6][8];   /* per lane group: rows of P F, read back as columns */
     int flag;
 };
 
@@ -581,6 +584,9 @@ __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX>
 }
 
 
+/* L1 prefetch of one address (no register is consumed; the line is ready for the next step). */
+__device__ __forceinline__ void pf(const float *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 /* ------------------------------------------------------------------ tree Riccati step */
 /* Terminal value function of a leaf: P = Q_N + penalty Hessian, p = q (stored and returned). */
 template <int NX>
@@ -757,6 +763,29 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
     }
 }
 
+/* Prefetch the rows a backward step at node i (child c on the path) reads. */
+template <int NX, int MODEL>
+__device__ __forceinline__ void prefetch_backward(const View<NX> &V, int i, int c) {
+    const int np = V.np;
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        pf(V.d + (size_t)a * np + c);
+        pf(V.q + (size_t)a * np + i);
+#pragma unroll
+        for (int b = (MODEL == 2 ? 0 : 2); b < NX; ++b) pf(V.A + (size_t)(a * NX + b) * np + i);
+#pragma unroll
+        for (int b = 0; b < NU; ++b) pf(V.B + (size_t)(a * NU + b) * np + i);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pf(V.hq + (size_t)a * np + i);
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        pf(V.hr + (size_t)a * np + i);
+        pf(V.r + (size_t)a * np + i);
+    }
+    pf(V.w + i);
+}
+
 /* Level-synchronous backward sweep: all nodes of a stage in parallel, one barrier per stage. */
 template <int NX, int MODEL>
 __device__ void backward_level(const ProbRec &R, const View<NX> &V, Shared &sh) {
@@ -820,6 +849,7 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
             }
             for (k = khi - 1; k >= klo; --k) {
                 const int i = path[k], c = path[k + 1];   /* single child c, its value function in P, p */
+                if (k > klo) prefetch_backward<NX, MODEL>(V, path[k - 1], i);
                 float dm[NX], Pb[NS], pb[NX];
                 V.load_x(V.d, c, dm);
 #pragma unroll
@@ -839,13 +869,31 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
     }
 }
 
-/* Forward rollout at node i given the parent's (dx, du): dx_i = A_p dx_p + B_p du_p + d_i,
- * du_i = K_i dx_i + k_i; with `own` also stores them, the QP multiplier lam_i = P_i dx_i + p_i
- * and accumulates the directional terms of the merit. */
+/* Prefetch the rows a forward step at node i (with parent pa) reads. */
 template <int NX, int MODEL>
-__device__ __forceinline__ void forward_node(const ProbRec &R, const View<NX> &V, int i, const float (&dxp)[NX],
-                                             const float (&dup)[NU], float (&dxv)[NX], float (&duv)[NU], bool own,
-                                             float (&dir)[3]) {
+__device__ __forceinline__ void prefetch_forward(const View<NX> &V, int i, int pa) {
+    const int np = V.np;
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        pf(V.d + (size_t)a * np + i);
+#pragma unroll
+        for (int b = (MODEL == 2 ? 0 : 2); b < NX; ++b) pf(V.A + (size_t)(a * NX + b) * np + pa);
+#pragma unroll
+        for (int b = 0; b < NU; ++b) pf(V.B + (size_t)(a * NU + b) * np + pa);
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        pf(V.k + (size_t)a * np + i);
+#pragma unroll
+        for (int b = 0; b < NX; ++b) pf(V.K + (size_t)(a * NX + b) * np + i);
+    }
+}
+
+/* Forward rollout at node i given the parent's (dx, du): dx_i = A_p dx_p + B_p du_p + d_i,
+ * du_i = K_i dx_i + k_i (stored when `own`). */
+template <int NX, int MODEL>
+__device__ __forceinline__ void forward_node(const View<NX> &V, int i, const float (&dxp)[NX], const float (&dup)[NU],
+                                             float (&dxv)[NX], float (&duv)[NU], bool own) {
     const int np = V.np;
     const int nch = V.nchild[i];
     if (i == 0) {
@@ -873,41 +921,55 @@ __device__ __forceinline__ void forward_node(const ProbRec &R, const View<NX> &V
             duv[a] = v;
         }
     }
-    if (!own) return;
-    V.store_x(V.dx, i, dxv);
-    V.store_u(V.du, i, duv);
-    const float w = V.w[i];
-    const float *Qd = nch ? R.Qw : R.QNw;
-    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
-#pragma unroll
-    for (int a = 0; a < NX; ++a) {
-        dir[0] += V.q[(size_t)a * np + i] * dxv[a];
-        dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+    if (own) {
+        V.store_x(V.dx, i, dxv);
+        V.store_u(V.du, i, duv);
     }
-    dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
-    if (nch) {
-#pragma unroll
-        for (int a = 0; a < NU; ++a) {
-            dir[0] += V.r[(size_t)a * np + i] * duv[a];
-            dir[1] += (w * R.Rw[a] + V.hr[(size_t)a * np + i]) * duv[a] * duv[a];
-        }
-    }
-    if (i != 0) {
+}
+
+/* After the rollout, every node in parallel: QP multiplier lam_i = P_i dx_i + p_i and the
+ * directional terms of the merit (grad'dz, dz'W dz, (dlam - lam)'d). */
+template <int NX, int MODEL>
+__device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, const View<NX> &V, float (&dir)[3]) {
+    const int tid = threadIdx.x, nt = blockDim.x, np = V.np;
+    for (int i = tid; i < V.n; i += nt) {
+        const int nch = V.nchild[i];
+        float dxv[NX], duv[NU];
+        V.load_x(V.dx, i, dxv);
+        V.load_u(V.du, i, duv);
+        const float w = V.w[i];
+        const float *Qd = nch ? R.Qw : R.QNw;
+        const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
 #pragma unroll
         for (int a = 0; a < NX; ++a) {
-            float v = V.p[(size_t)a * np + i];
+            dir[0] += V.q[(size_t)a * np + i] * dxv[a];
+            dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+        }
+        dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
+        if (nch) {
 #pragma unroll
-            for (int b = 0; b < NX; ++b) v += V.P[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
-            V.lq[(size_t)a * np + i] = v;
-            const float lam = V.L[(size_t)a * np + i];
-            dir[2] += ((v - lam) - lam) * V.d[(size_t)a * np + i];
+            for (int a = 0; a < NU; ++a) {
+                dir[0] += V.r[(size_t)a * np + i] * duv[a];
+                dir[1] += (w * R.Rw[a] + V.hr[(size_t)a * np + i]) * duv[a] * duv[a];
+            }
+        }
+        if (i != 0) {
+#pragma unroll
+            for (int a = 0; a < NX; ++a) {
+                float v = V.p[(size_t)a * np + i];
+#pragma unroll
+                for (int b = 0; b < NX; ++b) v += V.P[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
+                V.lq[(size_t)a * np + i] = v;
+                const float lam = V.L[(size_t)a * np + i];
+                dir[2] += ((v - lam) - lam) * V.d[(size_t)a * np + i];
+            }
         }
     }
 }
 
 /* Level-synchronous forward sweep: one barrier per stage, parents' (dx, du) read from memory. */
 template <int NX, int MODEL>
-__device__ void forward_level(const ProbRec &R, const View<NX> &V, float (&dir)[3]) {
+__device__ void forward_level(const ProbRec &R, const View<NX> &V) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int st = 0; st < R.n_stage; ++st) {
         const int s0 = V.sstart[st], s1 = V.sstart[st + 1];
@@ -919,7 +981,7 @@ __device__ void forward_level(const ProbRec &R, const View<NX> &V, float (&dir)[
                 V.load_x(V.dx, V.parent[i], dxp);
                 V.load_u(V.du, V.parent[i], dup);
             }
-            forward_node<NX, MODEL>(R, V, i, dxp, dup, dxv, duv, true, dir);
+            forward_node<NX, MODEL>(V, i, dxp, dup, dxv, duv, true);
         }
         __syncthreads();
     }
@@ -927,9 +989,9 @@ __device__ void forward_level(const ProbRec &R, const View<NX> &V, float (&dir)[
 
 /* Per-scenario-path forward sweep: path s rolls out from the root to its leaf with (dx, du) in
  * registers and no barrier; nodes shared by several paths are recomputed identically by each
- * and written only by their owner path. */
+ * and written only by their owner path.  The next node's rows are prefetched into L1. */
 template <int NX, int MODEL>
-__device__ void forward_path(const ProbRec &R, const View<NX> &V, float (&dir)[3]) {
+__device__ void forward_path(const ProbRec &R, const View<NX> &V) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int S = R.n_paths, ns = R.n_stage;
     for (int s = tid; s < S; s += nt) {
@@ -939,12 +1001,287 @@ __device__ void forward_path(const ProbRec &R, const View<NX> &V, float (&dir)[3
 #pragma unroll
         for (int j = 0; j < NX; ++j) dxp[j] = 0.f;
         for (int k = 0; k <= depth; ++k) {
+            if (k < depth) prefetch_forward<NX, MODEL>(V, path[k + 1], path[k]);
             float dxv[NX], duv[NU];
-            forward_node<NX, MODEL>(R, V, path[k], dxp, dup, dxv, duv, k >= top, dir);
+            forward_node<NX, MODEL>(V, path[k], dxp, dup, dxv, duv, k >= top);
 #pragma unroll
             for (int j = 0; j < NX; ++j) dxp[j] = dxv[j];
             dup[0] = duv[0];
             dup[1] = duv[1];
+        }
+    }
+    __syncthreads();
+}
+
+
+/* ------------------------------------------------------------------ cooperative (8-lane) per-path sweeps */
+/* A group of GL lanes handles one root-to-leaf path.  In the backward step lane j owns column j of
+ * F = [A_n B_n], of the summed child value-function Hessian Pbar, of H = W + F' Pbar F and of the
+ * new P; the gradient-side vectors (pbar, p) are replicated.  Rows of Pbar F are written to a small
+ * shared tile and read back as columns; the u-block of H and its coupling columns are broadcast
+ * with 8-lane shuffles.  The arithmetic is that of riccati_node (Eq. tree_feedback_laws). */
+__device__ __forceinline__ float gshfl(float v, int src, unsigned mask) { return __shfl_sync(mask, v, src, GL); }
+
+template <int NX, int MODEL>
+__device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V, int i, const float (&Pbc)[NX],
+                                             const float (&pb)[NX], float (&Pc)[NX], float (&p)[NX], int lane,
+                                             unsigned gmask, float (*tr)[8], Shared &sh) {
+    constexpr int NZ = NX + NU;
+    const int np = V.np;
+    const float w = V.w[i];
+    float F[NX][NZ];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+        for (int b = 0; b < NX; ++b) F[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
+#pragma unroll
+        for (int b = 0; b < NU; ++b) F[a][NX + b] = V.B[(size_t)(a * NU + b) * np + i];
+    }
+    /* row `lane` of Pbar F (Pbar symmetric: this lane's column is also its row) */
+    if (lane < NX) {
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) {
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += Pbc[t] * F[t][c];
+            tr[lane][c] = v;
+        }
+    }
+    __syncwarp(gmask);
+    /* column `lane` of H = W + F' Pbar F and entry `lane` of g = [q; r] + F' pbar */
+    float Hc[NZ], g = 0.f;
+#pragma unroll
+    for (int a = 0; a < NZ; ++a) Hc[a] = 0.f;
+    if (lane < NZ) {
+        float PFc[NX], Fc[NX];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) {
+            PFc[t] = tr[t][lane];
+            Fc[t] = 0.f;
+#pragma unroll
+            for (int c = 0; c < NZ; ++c)
+                if (c == lane) Fc[t] = F[t][c];
+        }
+#pragma unroll
+        for (int a = 0; a < NZ; ++a) {
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += F[t][a] * PFc[t];
+            Hc[a] = v;
+        }
+        const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+#pragma unroll
+        for (int a = 0; a < NZ; ++a) {
+            if (a != lane) continue;
+            if (a < NX) Hc[a] += w * R.Qw[a];
+            else Hc[a] += w * R.Rw[a - NX] + V.hr[(size_t)(a - NX) * np + i];
+        }
+        if (lane == 0) {
+            Hc[0] += hxx;
+            Hc[1] += hxy;
+        } else if (lane == 1) {
+            Hc[0] += hxy;
+            Hc[1] += hyy;
+        }
+        g = lane < NX ? V.q[(size_t)lane * np + i] : V.r[(size_t)(lane - NX) * np + i];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) g += Fc[t] * pb[t];
+    }
+    __syncwarp(gmask);
+    /* 2x2 H_uu, g_u and the coupling columns H[:, nx], H[:, nx+1] to every lane */
+    const float h00 = gshfl(Hc[NX], NX, gmask), h10 = gshfl(Hc[NX + 1], NX, gmask);
+    const float h11 = gshfl(Hc[NX + 1], NX + 1, gmask);
+    const float gu0 = gshfl(g, NX, gmask), gu1 = gshfl(g, NX + 1, gmask);
+    float Hu0[NX], Hu1[NX], gx[NX];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        Hu0[a] = gshfl(Hc[a], NX, gmask);
+        Hu1[a] = gshfl(Hc[a], NX + 1, gmask);
+        gx[a] = gshfl(g, a, gmask);
+    }
+    const float l00 = sqrtf(fmaxf(h00, 0.f));
+    const float l10 = h10 / l00;
+    const float l11s = h11 - l10 * l10;
+    if (!(h00 > 0.f) || !(l11s > 0.f)) sh.flag = 1;
+    const float l11 = sqrtf(fmaxf(l11s, 0.f));
+    /* K column `lane` and k: -H_uu^-1 (Qux column, qu) */
+    float K0 = 0.f, K1 = 0.f;
+    {
+        const float z0 = Hc[NX] / l00;
+        const float z1 = (Hc[NX + 1] - l10 * z0) / l11;
+        K1 = -(z1 / l11);
+        K0 = -((z0 + l10 * K1) / l00);
+    }
+    const float kz0 = gu0 / l00;
+    const float kz1 = (gu1 - l10 * kz0) / l11;
+    const float k1 = -(kz1 / l11);
+    const float k0 = -((kz0 + l10 * k1) / l00);
+    /* new P column `lane` = H[0:nx, lane] + Qux' K[:, lane]; p = qx + Qux' k (replicated) */
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        Pc[a] = Hc[a] + Hu0[a] * K0 + Hu1[a] * K1;
+        p[a] = gx[a] + Hu0[a] * k0 + Hu1[a] * k1;
+    }
+    if (lane < NX) {
+#pragma unroll
+        for (int a = 0; a < NX; ++a)
+            if (a <= lane) V.P[(size_t)sidx<NX>(a, lane) * np + i] = Pc[a];
+        V.K[(size_t)lane * np + i] = K0;
+        V.K[(size_t)(NX + lane) * np + i] = K1;
+    } else if (lane == NX) {
+#pragma unroll
+        for (int a = 0; a < NX; ++a) V.p[(size_t)a * np + i] = p[a];
+        V.k[i] = k0;
+        V.k[(size_t)np + i] = k1;
+    }
+}
+
+/* pbar = p + P d (P distributed by columns over the lanes, p replicated): returns pbar replicated. */
+template <int NX>
+__device__ __forceinline__ void coop_pbar(const View<NX> &V, int c, const float (&Pc)[NX], const float (&p)[NX],
+                                          float (&pb)[NX], int lane, unsigned gmask) {
+    float dm[NX];
+    V.load_x(V.d, c, dm);
+    float v = 0.f;
+#pragma unroll
+    for (int t = 0; t < NX; ++t) v += Pc[t] * dm[t];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) pb[a] = p[a] + gshfl(v, a, gmask);
+}
+
+template <int NX, int MODEL>
+__device__ void backward_coop(const ProbRec &R, const View<NX> &V, Shared &sh) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & (GL - 1), grp = tid / GL, ngrp = nt / GL;
+    const unsigned gmask = 0xFFu << (tid & 31 & ~(GL - 1));
+    float(*tr)[8] = sh.tr[grp];
+    const int S = R.n_paths, ns = R.n_stage, nb = R.n_bstage;
+    const int np = V.np;
+    int hi = ns - 1;
+    for (int ph = 0; ph <= nb; ++ph) {
+        const int lo = (ph < nb) ? V.bstage[ph] : -1;
+        for (int s = grp; s < S; s += ngrp) {
+            const int depth = V.pdepth[s], top = V.ptop[s];
+            const int khi = min(depth, hi), klo = max(top, lo + 1);
+            if (khi < klo) continue;
+            const int32_t *path = V.ptab + (size_t)s * ns;
+            float Pc[NX], p[NX];
+            {
+                const int i = path[khi];
+                const int nch = V.nchild[i];
+                const int lc = min(lane, NX - 1);
+                if (nch == 0) {
+                    /* terminal value function of the leaf, column `lane` */
+                    const float w = V.w[i];
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) Pc[a] = (a == lc) ? w * R.QNw[a] : 0.f;
+                    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+                    if (lc == 0) {
+                        Pc[0] += hxx;
+                        Pc[1] += hxy;
+                    } else if (lc == 1) {
+                        Pc[0] += hxy;
+                        Pc[1] += hyy;
+                    }
+                    V.load_x(V.q, i, p);
+                    if (lane < NX) {
+#pragma unroll
+                        for (int a = 0; a < NX; ++a)
+                            if (a <= lane) V.P[(size_t)sidx<NX>(a, lane) * np + i] = Pc[a];
+                    } else if (lane == NX) {
+                        V.store_x(V.p, i, p);
+                    }
+                } else {
+                    /* children summed from memory: column `lane` of Pbar, pbar replicated */
+                    float Pbc[NX], pb[NX];
+                    float v = 0.f;
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) {
+                        Pbc[a] = 0.f;
+                        pb[a] = 0.f;
+                    }
+                    const int fc = V.fchild[i];
+                    for (int m = fc; m < fc + nch; ++m) {
+                        float dm[NX];
+                        V.load_x(V.d, m, dm);
+                        float vm = V.p[(size_t)lc * np + m];
+#pragma unroll
+                        for (int a = 0; a < NX; ++a) {
+                            const float Pa = V.P[(size_t)sidx<NX>(a, lc) * np + m];
+                            Pbc[a] += Pa;
+                            vm += Pa * dm[a];
+                        }
+                        v += vm;
+                    }
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) pb[a] = gshfl(v, a, gmask);
+                    coop_riccati<NX, MODEL>(R, V, i, Pbc, pb, Pc, p, lane, gmask, tr, sh);
+                }
+            }
+            for (int k = khi - 1; k >= klo; --k) {
+                const int i = path[k], c = path[k + 1];
+                if (k > klo && lane == 0) prefetch_backward<NX, MODEL>(V, path[k - 1], i);
+                float pb[NX];
+                coop_pbar<NX>(V, c, Pc, p, pb, lane, gmask);
+                float Pbc[NX];
+#pragma unroll
+                for (int a = 0; a < NX; ++a) Pbc[a] = Pc[a];
+                coop_riccati<NX, MODEL>(R, V, i, Pbc, pb, Pc, p, lane, gmask, tr, sh);
+            }
+        }
+        hi = lo;
+        __syncthreads();
+    }
+}
+
+/* Cooperative forward rollout: lane a < nx computes dx[a], lanes 0..nu-1 compute du; the vectors
+ * are replicated by 8-lane shuffles. */
+template <int NX, int MODEL>
+__device__ void forward_coop(const ProbRec &R, const View<NX> &V) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & (GL - 1), grp = tid / GL, ngrp = nt / GL;
+    const unsigned gmask = 0xFFu << (tid & 31 & ~(GL - 1));
+    const int S = R.n_paths, ns = R.n_stage, np = V.np;
+    const int la = min(lane, NX - 1), lu = min(lane, NU - 1);
+    for (int s = grp; s < S; s += ngrp) {
+        const int32_t *path = V.ptab + (size_t)s * ns;
+        const int depth = V.pdepth[s], top = V.ptop[s];
+        float dx[NX], du[NU] = {0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < NX; ++j) dx[j] = 0.f;
+        for (int k = 0; k <= depth; ++k) {
+            const int i = path[k];
+            if (k < depth && lane == 0) prefetch_forward<NX, MODEL>(V, path[k + 1], i);
+            if (i != 0) {
+                const int pa = path[k - 1];
+                float v = V.d[(size_t)la * np + i];
+#pragma unroll
+                for (int b = 0; b < NX; ++b) v += aload<NX, MODEL>(V.A, np, pa, la, b) * dx[b];
+#pragma unroll
+                for (int b = 0; b < NU; ++b) v += V.B[(size_t)(la * NU + b) * np + pa] * du[b];
+#pragma unroll
+                for (int a = 0; a < NX; ++a) dx[a] = gshfl(v, a, gmask);
+            }
+            if (V.nchild[i]) {
+                float v = V.k[(size_t)lu * np + i];
+#pragma unroll
+                for (int b = 0; b < NX; ++b) v += V.K[(size_t)(lu * NX + b) * np + i] * dx[b];
+                du[0] = gshfl(v, 0, gmask);
+                du[1] = gshfl(v, 1, gmask);
+            } else {
+                du[0] = du[1] = 0.f;
+            }
+            if (k >= top) {
+                if (lane < NX) {
+#pragma unroll
+                    for (int a = 0; a < NX; ++a)
+                        if (a == lane) V.dx[(size_t)a * np + i] = dx[a];
+                } else if (lane < NX + NU) {
+#pragma unroll
+                    for (int a = 0; a < NU; ++a)
+                        if (a == lane - NX) V.du[(size_t)a * np + i] = du[a];
+                }
+            }
         }
     }
     __syncthreads();
@@ -958,7 +1295,6 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
     const View<NX> V(R, ib, fin, fw, fout, fs);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n = V.n, np = V.np, nc = V.nc;
-    const int n_stage = R.n_stage;
     long long t_start = clock64(), c_lin = 0, c_bwd = 0, c_fwd = 0, c_ls = 0;
 
     /* ---- initial iterate: warm start or the cold start of Sec. V-B */
@@ -1000,7 +1336,8 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
     float r_kkt = INFINITY, cviol = INFINITY;
     int inner = 0, outer = 0, ls_fail = 0, ls_fail_total = 0, ls_evals = 0, status = 1 /* MAX_ITER */;
     const int G = (O.ls_chunk <= 0 || O.ls_chunk > MAX_CHUNK) ? min(O.n_alpha, MAX_CHUNK) : O.ls_chunk;
-    const bool path_variant = O.variant != 1;   /* 1: level-synchronous sweeps, else per-path */
+    /* sweeps: 1 level-synchronous, 2 (default) per-path with one thread per path, 3 per-path with 8 lanes */
+    const int variant = (O.variant == 1 || O.variant == 3) ? O.variant : 2;
 
     while (outer < O.max_outer) {
         ++outer;
@@ -1102,7 +1439,8 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             t0 = clock64();
             if (tid == 0) sh.flag = 0;
             __syncthreads();
-            if (path_variant) backward_path<NX, MODEL>(R, V, sh);
+            if (variant == 3) backward_coop<NX, MODEL>(R, V, sh);
+            else if (variant == 2) backward_path<NX, MODEL>(R, V, sh);
             else backward_level<NX, MODEL>(R, V, sh);
             __syncthreads();
             c_bwd += clock64() - t0;
@@ -1114,8 +1452,10 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             /* ===== forward: linear rollout from the root, QP multipliers */
             t0 = clock64();
             float dir[3] = {0.f, 0.f, 0.f};   /* grad'dz, dz'W dz, (dlam - lam)'d */
-            if (path_variant) forward_path<NX, MODEL>(R, V, dir);
-            else forward_level<NX, MODEL>(R, V, dir);
+            if (variant == 3) forward_coop<NX, MODEL>(R, V);
+            else if (variant == 2) forward_path<NX, MODEL>(R, V);
+            else forward_level<NX, MODEL>(R, V);
+            multipliers_and_directions<NX, MODEL>(R, V, dir);
             block_sum<3>(dir, sh);
             c_fwd += clock64() - t0;
 
