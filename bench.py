@@ -218,6 +218,11 @@ def run_gpu(args):
                              ls_chunk=args.ls_chunk, variant=args.variant)
     if args.max_iters > 0:
         opts.max_iters = args.max_iters
+    tuned = None
+    if args.autotune:
+        opts, us = b.autotune(opts)
+        tuned = dict(block_threads=opts.block_threads, variant=opts.variant, ls_chunk=opts.ls_chunk,
+                     us_per_problem=us)
     for _ in range(args.warmup):
         b.solve(opts, graph=True)
     res = b.get_solutions(want_arrays=False)
@@ -288,7 +293,9 @@ def run_gpu(args):
         "config": {"workload": args.workload, "batch_per_gpu": args.batch,
                    "nodes_per_gpu": int(sum(int(p["n"]) for p in problems)),
                    "l2": f"working set {(b.data_bytes + b.scratch_bytes) / 1e9:.2f} GB > 126 MB L2, no flush",
-                   "launch": "one persistent kernel per step, CUDA graph replay"},
+                   "launch": "one persistent kernel per model per step, CUDA graph replay",
+                   "opts": {"block_threads": opts.block_threads, "variant": opts.variant, "ls_chunk": opts.ls_chunk,
+                            "max_iters": opts.max_iters, "autotuned": tuned is not None}},
         "converged_fraction": float(conv.mean()),
         "tree_riccati_us_per_iter": ric_us_iter,
         "phase_us_per_iter": phases,
@@ -322,6 +329,7 @@ def main():
     ap.add_argument("--ls-chunk", type=int, default=2)
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--max-iters", type=int, default=0)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

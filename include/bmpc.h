@@ -159,6 +159,13 @@ int bmpc_solve_batch(bmpc_batch *b, const bmpc_opts *opts);
  * replayed; the graph is rebuilt when opts change.  Asynchronous. */
 int bmpc_solve_batch_graph(bmpc_batch *b, const bmpc_opts *opts);
 
+/* Autotuner: solves the batch once per candidate launch configuration (threads per problem 64 /
+ * 128 / 256, sweep variant 1 / 2 / 3, line-search chunk 1 / 2 / 4; the other fields from `base`,
+ * NULL = defaults), timing each with CUDA events on the handle's stream, and returns in *best the
+ * configuration with the most converged solves per second and in *best_us_per_solve its time per
+ * problem.  Synchronises the stream; leaves the last candidate's solution in the outputs. */
+int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *best_us_per_solve);
+
 /* Copy solutions back (synchronises the stream).  Host arrays, concatenated over problems
  * in batch order, node-major: x [sum n_i][nx_i], u [sum n_i][nu] (zero rows at leaves),
  * lam [sum n_i][nx_i] (row of each root zero), y [sum n_i][nc_i]; stats [n].

@@ -77,6 +77,7 @@ def lib() -> C.CDLL:
         L.bmpc_get_solutions.argtypes = [C.c_void_p, _fp, _fp, _fp, _fp, C.POINTER(Stats)]
         L.bmpc_destroy_batch.argtypes = [C.c_void_p]
         L.bmpc_default_opts.argtypes = [C.POINTER(Opts)]
+        L.bmpc_autotune.argtypes = [C.c_void_p, C.POINTER(Opts), C.POINTER(Opts), C.POINTER(C.c_float)]
         L.bmpc_create_batch_static.argtypes = [C.POINTER(TreeDesc), C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                                                C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]
         L.bmpc_problem_device_outputs.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
@@ -89,7 +90,7 @@ def lib() -> C.CDLL:
 EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_set_problems", "bmpc_solve_batch",
             "bmpc_solve_batch_graph", "bmpc_get_solutions", "bmpc_problem_device_outputs", "bmpc_destroy_batch",
             "bmpc_tree_bytes", "bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution",
-            "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static"]
+            "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -216,6 +217,14 @@ class Batch:
         fn = lib().bmpc_solve_batch_graph if graph else lib().bmpc_solve_batch
         with self.torch.cuda.device(self.device):
             _check(fn(self.handle, C.byref(o)), "bmpc_solve_batch")
+
+    def autotune(self, base: Opts | None = None) -> tuple[Opts, float]:
+        """Pick threads per problem, sweep variant and line-search chunk by timing them on this batch."""
+        o = base if base is not None else default_opts()
+        best, us = Opts(), C.c_float()
+        with self.torch.cuda.device(self.device):
+            _check(lib().bmpc_autotune(self.handle, C.byref(o), C.byref(best), C.byref(us)), "bmpc_autotune")
+        return best, us.value
 
     def get_solutions(self, want_arrays: bool = True):
         """Synchronise and return per-problem dicts with x, u, lam, y and the solver statistics."""

@@ -530,6 +530,66 @@ int bmpc_solve_batch_graph(bmpc_batch *b, const bmpc_opts *opts) {
     return cuda_status(cudaGraphLaunch(b->gexec, b->stream));
 }
 
+int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *best_us_per_solve) {
+    if (!b || !best) return BMPC_ERR_INVALID;
+    bmpc_opts o;
+    if (base) o = *base;
+    else bmpc_default_opts(&o);
+    int st = check_opts(o);
+    if (st != BMPC_OK) return st;
+    static const int kThreads[] = {64, 128, 256};
+    static const int kVariant[] = {1, 2, 3};
+    static const int kChunk[] = {1, 2, 4};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return BMPC_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return BMPC_ERR_CUDA;
+    }
+    std::vector<Stats> stats(b->n);
+    double best_rate = -1.0;
+    bmpc_opts best_o = o;
+    float best_ms = 0.f;
+    int rc = BMPC_OK;
+    for (int bt : kThreads)
+        for (int v : kVariant)
+            for (int ch : kChunk) {
+                bmpc_opts c = o;
+                c.block_threads = bt;
+                c.variant = v;
+                c.ls_chunk = ch;
+                c.blocks_per_sm = 0;
+                if (launch(b, c) != BMPC_OK) { rc = BMPC_ERR_CUDA; goto out; }       /* warm-up */
+                if (cudaEventRecord(e0, b->stream) != cudaSuccess || launch(b, c) != BMPC_OK ||
+                    cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = BMPC_ERR_CUDA;
+                    goto out;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (cudaMemcpy(stats.data(), b->data + b->L.stats, sizeof(Stats) * b->n, cudaMemcpyDeviceToHost) !=
+                    cudaSuccess) {
+                    rc = BMPC_ERR_CUDA;
+                    goto out;
+                }
+                int conv = 0;
+                for (const Stats &s : stats) conv += s.status == BMPC_OK;
+                const double rate = ms > 0.f ? conv / (double)ms : 0.0;
+                if (rate > best_rate) {
+                    best_rate = rate;
+                    best_o = c;
+                    best_ms = ms;
+                }
+            }
+out:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != BMPC_OK) return rc;
+    *best = best_o;
+    if (best_us_per_solve) *best_us_per_solve = best_ms * 1e3f / (float)b->n;
+    return BMPC_OK;
+}
+
 int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats) {
     if (!b) return BMPC_ERR_INVALID;
     cudaError_t e = cudaSuccess;

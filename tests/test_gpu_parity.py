@@ -196,6 +196,26 @@ def test_level_and_path_variants_agree(cfg):
             np.testing.assert_allclose(a["u"], b["u"], atol=tol)
 
 
+def test_autotuner_returns_a_valid_configuration():
+    from paper_2506_13624_b300 import bmpc
+    ps = scenes.config4(4, 32)
+    b = bmpc.Batch(ps)
+    b.set_problems()
+    best, us = b.autotune()
+    assert best.block_threads in (64, 128, 256) and best.variant in (1, 2, 3) and best.ls_chunk in (1, 2, 4)
+    assert us > 0
+    b.solve(best)
+    tuned = b.get_solutions()
+    b.solve(bmpc.default_opts())
+    ref = b.get_solutions()
+    b.close()
+    for p, a, r in zip(ps, tuned, ref):
+        assert a["status"] == r["status"]
+        if a["status"] == oracle.OK:
+            tol = 1e-4 * max(1.0, np.abs(r["u"]).max())
+            np.testing.assert_allclose(a["u"], r["u"], atol=tol)
+
+
 def test_invalid_problem_rejected():
     from paper_2506_13624_b300 import bmpc
     p = dict(scenes.config1(0))
