@@ -117,6 +117,9 @@ typedef struct {
                                root-to-leaf path, barriers only at branch stages), 3 per-scenario-path
                                with 8 lanes per path (lane j owns column j of [A B], P and H);
                                all compute the same search direction */
+    int32_t warm_select;    /* 1: start from warm slot 0 only if its merit is not above that of the fallback
+                               (warm slot 1 when set, else the cold start); default 0 */
+    float select_mu;        /* defect penalty mu of the merit used by warm_select (rho = rho0), default 100 */
 } bmpc_opts;
 
 typedef struct {
@@ -125,7 +128,7 @@ typedef struct {
     int32_t outer_iters;
     int32_t ls_fail_total;
     int32_t ls_evals;       /* step sizes evaluated by the line search, summed over iterations */
-    int32_t reserved;
+    int32_t start_used;     /* starting point: 0 cold start, 1 warm slot 0, 2 warm slot 1 */
     float r_kkt, c, rho, mu;
     int64_t cycles_linearise, cycles_backward, cycles_forward, cycles_linesearch, cycles_total;
 } bmpc_stats;
@@ -158,6 +161,17 @@ int bmpc_solve_batch(bmpc_batch *b, const bmpc_opts *opts);
 /* Same work captured once into a CUDA graph (queue reset + persistent kernel) and
  * replayed; the graph is rebuilt when opts change.  Asynchronous. */
 int bmpc_solve_batch_graph(bmpc_batch *b, const bmpc_opts *opts);
+
+/* Warm starts on the device.  Every problem has two warm-start slots: 0 (primary) and 1 (fallback).
+ * bmpc_set_problems fills slot 0 from host arrays.  These calls fill a slot for every problem of the
+ * batch on the handle's stream:
+ *   bmpc_set_warm_start_device: from a device array, problem k at dev_start + k*stride floats, packed
+ *     node-major x [n][nx] (absolute states) | u [n][nu] | lam [n][nx] | y [n][nc];
+ *   bmpc_shift_warm_start: the receding-horizon shift of `prev`'s solution (same trees, same models):
+ *     the node at stage k takes the previous solution at stage k+1 on the path of its first leaf,
+ *     the last stage appends the last control and propagates the dynamics. */
+int bmpc_set_warm_start_device(bmpc_batch *b, const float *dev_start, int64_t stride, int32_t slot);
+int bmpc_shift_warm_start(bmpc_batch *next, const bmpc_batch *prev, int32_t slot);
 
 /* Autotuner: solves the batch once per candidate launch configuration (threads per problem 64 /
  * 128 / 256, sweep variant 1 / 2 / 3, line-search chunk 1 / 2 / 4; the other fields from `base`,

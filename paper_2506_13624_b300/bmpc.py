@@ -44,12 +44,13 @@ class Opts(C.Structure):
                 ("a_omega", C.c_float), ("b_omega", C.c_float), ("a_eta", C.c_float), ("b_eta", C.c_float),
                 ("rho0", C.c_float), ("rho_max", C.c_float), ("mu0", C.c_float), ("beta", C.c_float),
                 ("ls_rel_eps", C.c_float), ("ls_chunk", C.c_int32), ("block_threads", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("variant", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("variant", C.c_int32), ("warm_select", C.c_int32),
+                ("select_mu", C.c_float)]
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("inner_iters", C.c_int32), ("outer_iters", C.c_int32),
-                ("ls_fail_total", C.c_int32), ("ls_evals", C.c_int32), ("reserved", C.c_int32),
+                ("ls_fail_total", C.c_int32), ("ls_evals", C.c_int32), ("start_used", C.c_int32),
                 ("r_kkt", C.c_float), ("c", C.c_float), ("rho", C.c_float),
                 ("mu", C.c_float), ("cycles_linearise", C.c_int64), ("cycles_backward", C.c_int64),
                 ("cycles_forward", C.c_int64), ("cycles_linesearch", C.c_int64), ("cycles_total", C.c_int64)]
@@ -78,6 +79,8 @@ def lib() -> C.CDLL:
         L.bmpc_destroy_batch.argtypes = [C.c_void_p]
         L.bmpc_default_opts.argtypes = [C.POINTER(Opts)]
         L.bmpc_autotune.argtypes = [C.c_void_p, C.POINTER(Opts), C.POINTER(Opts), C.POINTER(C.c_float)]
+        L.bmpc_set_warm_start_device.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32]
+        L.bmpc_shift_warm_start.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
         L.bmpc_create_batch_static.argtypes = [C.POINTER(TreeDesc), C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                                                C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]
         L.bmpc_problem_device_outputs.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
@@ -90,7 +93,8 @@ def lib() -> C.CDLL:
 EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_set_problems", "bmpc_solve_batch",
             "bmpc_solve_batch_graph", "bmpc_get_solutions", "bmpc_problem_device_outputs", "bmpc_destroy_batch",
             "bmpc_tree_bytes", "bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution",
-            "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune"]
+            "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune",
+            "bmpc_set_warm_start_device", "bmpc_shift_warm_start"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -218,6 +222,23 @@ class Batch:
         with self.torch.cuda.device(self.device):
             _check(fn(self.handle, C.byref(o)), "bmpc_solve_batch")
 
+    def start_stride(self) -> int:
+        """Floats per problem of a packed device start (x | u | lam | y, node-major), over the batch."""
+        return int(max(int(n) * (2 * int(nx) + NU + int(nc)) for n, nx, nc in zip(self.nodes, self.nx, self.nc)))
+
+    def set_warm_device(self, starts, slot: int = 0):
+        """Warm-start slot from a float32 CUDA tensor [n_problems, stride] of packed starts."""
+        t = starts
+        assert t.is_cuda and t.dtype == self.torch.float32 and t.is_contiguous() and t.shape[0] == self.n
+        with self.torch.cuda.device(self.device):
+            _check(lib().bmpc_set_warm_start_device(self.handle, t.data_ptr(), int(t.shape[1]), slot),
+                   "bmpc_set_warm_start_device")
+
+    def shift_from(self, prev: "Batch", slot: int = 0):
+        """Warm-start slot from the receding-horizon shift of prev's solution (same trees)."""
+        with self.torch.cuda.device(self.device):
+            _check(lib().bmpc_shift_warm_start(self.handle, prev.handle, slot), "bmpc_shift_warm_start")
+
     def autotune(self, base: Opts | None = None) -> tuple[Opts, float]:
         """Pick threads per problem, sweep variant and line-search chunk by timing them on this batch."""
         o = base if base is not None else default_opts()
@@ -245,7 +266,7 @@ class Batch:
             n_, nx, nc = int(self.nodes[k]), int(self.nx[k]), int(self.nc[k])
             s = st[k]
             rec = dict(status=s.status, inner_iters=s.inner_iters, outer_iters=s.outer_iters,
-                       ls_fail_total=s.ls_fail_total, ls_evals=s.ls_evals, r_kkt=s.r_kkt, c=s.c, rho=s.rho, mu=s.mu,
+                       ls_fail_total=s.ls_fail_total, ls_evals=s.ls_evals, start_used=s.start_used, r_kkt=s.r_kkt, c=s.c, rho=s.rho, mu=s.mu,
                        cycles=dict(linearise=s.cycles_linearise, backward=s.cycles_backward,
                                    forward=s.cycles_forward, linesearch=s.cycles_linesearch,
                                    total=s.cycles_total))

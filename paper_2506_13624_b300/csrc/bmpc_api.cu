@@ -22,6 +22,8 @@ namespace bmpc {
 cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, cudaStream_t stream);
 int max_block_threads();
 cudaError_t occupancy(int model, int block, int *blocks_per_sm);
+cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
+cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream);
 }  // namespace bmpc
 
 using namespace bmpc;
@@ -73,6 +75,7 @@ struct bmpc_batch {
     std::vector<ProbRec> recs;
     std::vector<int32_t> order;
     std::vector<int> nodes;
+    std::vector<int32_t> parents;        /* all trees' parent arrays, concatenated */
     int model_begin[4] = {0, 0, 0, 0};   /* order[model_begin[m] .. model_begin[m+1]) has model m */
     Layout L{};
     char *data = nullptr;
@@ -135,7 +138,7 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         R.off_scr = (int64_t)os;
         oi += (size_t)int_off(R.npad, R.n_stage, R.n_paths).total;
         oin += (size_t)in_rows(R.nx, R.n_obs).total * R.npad;
-        ow += (size_t)warm_rows(R.nx, R.nc).total * R.npad;
+        ow += 2 * (size_t)warm_rows(R.nx, R.nc).total * R.npad;   /* primary and fallback slots */
         oo += (size_t)out_rows(R.nx, R.nc).total * R.npad;
         os += (size_t)scr_rows(R.nx).total * R.npad;
         nodes[k] = d.num_nodes;
@@ -174,6 +177,7 @@ KOpts to_kopts(const bmpc_opts &o) {
     k.n_alpha = o.n_alpha;
     k.ls_chunk = o.ls_chunk;
     k.variant = o.variant;
+    k.warm_select = o.warm_select;
     k.eps_tol = o.eps_tol;
     k.tau = o.tau;
     k.omega0 = o.omega0;
@@ -187,6 +191,7 @@ KOpts to_kopts(const bmpc_opts &o) {
     k.mu0 = o.mu0;
     k.beta = o.beta;
     k.ls_rel_eps = o.ls_rel_eps;
+    k.select_mu = o.select_mu;
     return k;
 }
 
@@ -199,6 +204,7 @@ int check_opts(const bmpc_opts &o) {
         return BMPC_ERR_INVALID;
     if (o.blocks_per_sm < 0) return BMPC_ERR_INVALID;
     if (o.variant < 0 || o.variant > 3) return BMPC_ERR_INVALID;
+    if (o.warm_select < 0 || o.warm_select > 1 || !(o.select_mu >= 0.f)) return BMPC_ERR_INVALID;
     if ((o.variant == 0 || o.variant == 3) && o.block_threads != 0 && o.block_threads % 32) return BMPC_ERR_INVALID;
     return BMPC_OK;
 }
@@ -278,6 +284,8 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->block_threads = 0;
     o->blocks_per_sm = 0;
     o->variant = 0;
+    o->warm_select = 0;
+    o->select_mu = 100.f;
 }
 
 int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
@@ -342,6 +350,7 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
     for (int m = 0; m < 4; ++m) b->model_begin[m] = 0;
     for (int k = 0; k < n; ++k) b->model_begin[b->recs[k].model + 1]++;
     for (int m = 0; m < 3; ++m) b->model_begin[m + 1] += b->model_begin[m];
+    for (int k = 0; k < n; ++k) b->parents.insert(b->parents.end(), descs[k].parent, descs[k].parent + descs[k].num_nodes);
     /* int tables of every tree, packed into the staging buffer and uploaded once */
     int32_t *ib = at<int32_t>(b->stage, b->L.ints);
     std::memset(ib, 0, sizeof(int32_t) * b->L.ints_n);
@@ -530,6 +539,66 @@ int bmpc_solve_batch_graph(bmpc_batch *b, const bmpc_opts *opts) {
     return cuda_status(cudaGraphLaunch(b->gexec, b->stream));
 }
 
+namespace {
+int upload_recs(bmpc_batch *b) {
+    std::memcpy(b->stage + b->L.recs, b->recs.data(), sizeof(ProbRec) * b->n);
+    return cuda_status(cudaMemcpyAsync(b->data + b->L.recs, b->stage + b->L.recs, sizeof(ProbRec) * b->n,
+                                       cudaMemcpyHostToDevice, b->stream));
+}
+WarmArgs warm_args(bmpc_batch *b, int slot) {
+    WarmArgs w{};
+    w.recs = at<const ProbRec>(b->data, b->L.recs);
+    w.ibase = at<const int32_t>(b->data, b->L.ints);
+    w.inbase = at<const float>(b->data, b->L.in);
+    w.warmbase = at<float>(b->data, b->L.warm);
+    w.order = at<const int32_t>(b->data, b->L.order);
+    w.n_problems = b->n;
+    w.slot = slot;
+    return w;
+}
+}  // namespace
+
+int bmpc_set_warm_start_device(bmpc_batch *b, const float *dev_start, int64_t stride, int32_t slot) {
+    if (!b || !dev_start || slot < 0 || slot > 1) return BMPC_ERR_INVALID;
+    for (int k = 0; k < b->n; ++k) {
+        const ProbRec &R = b->recs[k];
+        if ((int64_t)R.n * (2 * R.nx + NU + R.nc) > stride) return BMPC_ERR_INVALID;
+    }
+    WarmArgs w = warm_args(b, slot);
+    w.src = dev_start;
+    w.stride = stride;
+    for (ProbRec &R : b->recs) R.has_warm |= 1 << slot;
+    int st = upload_recs(b);
+    if (st != BMPC_OK) return st;
+    return cuda_status(launch_scatter_warm(w, b->stream));
+}
+
+int bmpc_shift_warm_start(bmpc_batch *next, const bmpc_batch *prev, int32_t slot) {
+    if (!next || !prev || slot < 0 || slot > 1 || next->n != prev->n) return BMPC_ERR_INVALID;
+    if (next->parents != prev->parents) return BMPC_ERR_INVALID;
+    for (int k = 0; k < next->n; ++k)
+        if (next->recs[k].model != prev->recs[k].model || next->recs[k].nc != prev->recs[k].nc ||
+            next->recs[k].npad != prev->recs[k].npad)
+            return BMPC_ERR_INVALID;
+    WarmArgs w = warm_args(next, slot);
+    w.prev_recs = at<const ProbRec>(prev->data, prev->L.recs);
+    w.prev_ibase = at<const int32_t>(prev->data, prev->L.ints);
+    w.prev_inbase = at<const float>(prev->data, prev->L.in);
+    w.prev_outbase = at<const float>(prev->data, prev->L.out);
+    for (ProbRec &R : next->recs) R.has_warm |= 1 << slot;
+    int st = upload_recs(next);
+    if (st != BMPC_OK) return st;
+    for (int m = 0; m < 3; ++m) {
+        const int cnt = next->model_begin[m + 1] - next->model_begin[m];
+        if (!cnt) continue;
+        WarmArgs wm = w;
+        wm.order = at<const int32_t>(next->data, next->L.order) + next->model_begin[m];
+        wm.n_problems = cnt;
+        if (launch_shift_warm(wm, m, next->stream) != cudaSuccess) return BMPC_ERR_CUDA;
+    }
+    return BMPC_OK;
+}
+
 int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *best_us_per_solve) {
     if (!b || !best) return BMPC_ERR_INVALID;
     bmpc_opts o;
@@ -635,7 +704,7 @@ int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, 
             stats[k].outer_iters = s[k].outer_iters;
             stats[k].ls_fail_total = s[k].ls_fail_total;
             stats[k].ls_evals = s[k].ls_evals;
-            stats[k].reserved = 0;
+            stats[k].start_used = s[k].start_used;
             stats[k].r_kkt = s[k].r_kkt;
             stats[k].c = s[k].c;
             stats[k].rho = s[k].rho;

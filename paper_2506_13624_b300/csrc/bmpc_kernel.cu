@@ -398,11 +398,8 @@ struct View {
         xref = fin + (size_t)ir.xref * np;
         w = fin + (size_t)ir.weight * np;
         obs = fin + (size_t)ir.obs * np;
-        const WarmRows wr = warm_rows(NX, nc);
-        wx = fw + (size_t)wr.wx * np;
-        wu = fw + (size_t)wr.wu * np;
-        wl = fw + (size_t)wr.wl * np;
-        wy = fw + (size_t)wr.wy * np;
+        fwarm = fw;
+        set_slot(0);
         const OutRows orw = out_rows(NX, nc);
         X = fout + (size_t)orw.x * np;
         U = fout + (size_t)orw.u * np;
@@ -425,6 +422,16 @@ struct View {
         du = fs + (size_t)s.du * np;
         lq = fs + (size_t)s.lq * np;
         nv = fs + (size_t)s.nv * np;
+    }
+    const float *fwarm;
+    /* point wx .. wy at warm-start slot s */
+    __device__ __forceinline__ void set_slot(int s) {
+        const WarmRows wr = warm_rows(NX, nc);
+        const float *b = fwarm + (size_t)s * wr.total * np;
+        wx = b + (size_t)wr.wx * np;
+        wu = b + (size_t)wr.wu * np;
+        wl = b + (size_t)wr.wl * np;
+        wy = b + (size_t)wr.wy * np;
     }
     __device__ __forceinline__ void load_x(const float *base, int i, float (&v)[NX]) const {
 #pragma unroll
@@ -1287,21 +1294,18 @@ __device__ void forward_coop(const ProbRec &R, const View<NX> &V) {
     __syncthreads();
 }
 
-/* ------------------------------------------------------------------ the per-problem solver */
-template <int NX, int MODEL>
-__device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
-                              float *fs, Stats *stat, const KOpts &O, Shared &sh) {
-    constexpr int NS = nsym(NX);
-    const View<NX> V(R, ib, fin, fw, fout, fs);
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int n = V.n, np = V.np, nc = V.nc;
-    long long t_start = clock64(), c_lin = 0, c_bwd = 0, c_fwd = 0, c_ls = 0;
-
-    /* ---- initial iterate: warm start or the cold start of Sec. V-B */
-    for (int i = tid; i < n; i += nt) {
+/* ------------------------------------------------------------------ starting points */
+/* Fill the iterate (state deviation, u, lam, y) from start `which`: 0 the cold start of Sec. V-B
+ * (x linearly interpolated from x0 to the final reference of the node's first leaf, u = lam = y
+ * = 0), 1 warm-start slot 0, 2 warm-start slot 1.  The root state is x0 and its lam is zero. */
+template <int NX>
+__device__ void load_start(const ProbRec &R, View<NX> &V, int which) {
+    const int tid = threadIdx.x, nt = blockDim.x, np = V.np, nc = V.nc;
+    if (which > 0) V.set_slot(which - 1);
+    for (int i = tid; i < V.n; i += nt) {
         const bool is_leaf = V.nchild[i] == 0;
         float x[NX], u[NU], l[NX];
-        if (R.has_warm) {
+        if (which > 0) {
             V.load_x(V.wx, i, x);
             V.load_u(V.wu, i, u);
             V.load_x(V.wl, i, l);
@@ -1330,6 +1334,64 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
         V.store_u(V.U, i, u);
         V.store_x(V.L, i, l);
     }
+}
+
+/* Merit phi = L_a + lam'd + mu/2 |d|^2 (Eq. merit with J = L_a) at the current iterate. */
+template <int NX, int MODEL>
+__device__ float start_merit(const ProbRec &R, const View<NX> &V, float rho, float mu, Shared &sh) {
+    const int tid = threadIdx.x, nt = blockDim.x, np = V.np;
+    float acc[1] = {0.f};
+    for (int i = tid; i < V.n; i += nt) {
+        const int nch = V.nchild[i], fc = V.fchild[i];
+        float x[NX], u[NU], qd[NX], rd[NU], hqd[3], hrd[NU];
+        V.load_x(V.X, i, x);
+        V.load_u(V.U, i, u);
+        float v = node_la<NX, false>(R, V, i, nch == 0, x, u, rho, qd, rd, hqd, hrd);
+        if (nch) {
+            float xa[NX], ft[NX];
+#pragma unroll
+            for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
+            dyn<NX, MODEL>(R, xa, u, ft);
+            for (int m = fc; m < fc + nch; ++m) {
+#pragma unroll
+                for (int j = 0; j < NX; ++j) {
+                    const float dref = V.xref[(size_t)j * np + i] - V.xref[(size_t)j * np + m];
+                    const float dm = (dref + (x[j] - V.X[(size_t)j * np + m])) + ft[j];
+                    v += V.L[(size_t)j * np + m] * dm + 0.5f * mu * dm * dm;
+                }
+            }
+        }
+        acc[0] += v;
+    }
+    block_sum<1>(acc, sh);
+    return acc[0];
+}
+
+/* ------------------------------------------------------------------ the per-problem solver */
+template <int NX, int MODEL>
+__device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
+                              float *fs, Stats *stat, const KOpts &O, Shared &sh) {
+    constexpr int NS = nsym(NX);
+    View<NX> V(R, ib, fin, fw, fout, fs);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n = V.n, np = V.np, nc = V.nc;
+    long long t_start = clock64(), c_lin = 0, c_bwd = 0, c_fwd = 0, c_ls = 0;
+
+    /* ---- initial iterate: a warm-start slot or the cold start of Sec. V-B.  With warm_select the
+     * primary start is used only when its merit (at rho0, with the defect penalty select_mu) is not
+     * above the fallback's (slot 1, or the cold start). */
+    int start = (R.has_warm & 1) ? 1 : ((R.has_warm & 2) ? 2 : 0);
+    if (O.warm_select && (R.has_warm & 1)) {
+        const int fb = (R.has_warm & 2) ? 2 : 0;
+        load_start<NX>(R, V, 1);
+        __syncthreads();
+        const float m1 = start_merit<NX, MODEL>(R, V, O.rho0, O.select_mu, sh);
+        load_start<NX>(R, V, fb);
+        __syncthreads();
+        const float m2 = start_merit<NX, MODEL>(R, V, O.rho0, O.select_mu, sh);
+        start = (m1 == m1 && !(m1 > m2)) ? 1 : fb;
+    }
+    load_start<NX>(R, V, start);
     __syncthreads();
 
     float rho = O.rho0, mu = O.mu0, omega = O.omega0, eta = O.eta0;
@@ -1623,7 +1685,7 @@ done:
         stat->outer_iters = outer;
         stat->ls_fail_total = ls_fail_total;
         stat->ls_evals = ls_evals;
-        stat->reserved = 0;
+        stat->start_used = start;
         stat->r_kkt = r_kkt;
         stat->c = cviol;
         stat->rho = rho;
@@ -1653,6 +1715,94 @@ __global__ void __launch_bounds__(MAX_BLOCK, BMPC_MIN_BLOCKS) bmpc_solve_kernel(
         solve_problem<NX, MODEL>(R, args.ibase + R.off_int, args.inbase + R.off_in, args.warmbase + R.off_warm,
                                  args.outbase + R.off_out, args.scr + R.off_scr, args.stats + pid, args.opts, sh);
     }
+}
+
+
+/* ------------------------------------------------------------------ warm-start kernels */
+/* Device scatter: problem `order[blockIdx.x]` takes its start from a dense device array, node-major
+ * x | u | lam | y (absolute states), into warm-start slot `slot`. */
+__global__ void bmpc_scatter_warm_kernel(WarmArgs a) {
+    const int pid = a.order[blockIdx.x];
+    const ProbRec &R = a.recs[pid];
+    const int n = R.n, np = R.npad, nx = R.nx, nc = R.nc;
+    const WarmRows wr = warm_rows(nx, nc);
+    float *w = a.warmbase + R.off_warm + (size_t)a.slot * wr.total * np;
+    const float *src = a.src + (size_t)pid * a.stride;
+    const float *sx = src, *su = sx + (size_t)n * nx, *sl = su + (size_t)n * NU, *sy = sl + (size_t)n * nx;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int j = 0; j < nx; ++j) {
+            w[(size_t)(wr.wx + j) * np + i] = sx[(size_t)i * nx + j];
+            w[(size_t)(wr.wl + j) * np + i] = sl[(size_t)i * nx + j];
+        }
+        for (int j = 0; j < NU; ++j) w[(size_t)(wr.wu + j) * np + i] = su[(size_t)i * NU + j];
+        for (int c = 0; c < nc; ++c) w[(size_t)(wr.wy + c) * np + i] = sy[(size_t)i * nc + c];
+    }
+}
+
+/* Receding-horizon shift of a previous solution on the same tree into warm-start slot `slot`:
+ * the node at stage k takes the previous value at stage k+1 on the path of its first leaf (the
+ * lowest-index scenario through it); the last stage appends the last control and propagates the
+ * dynamics; u, lam and y are shifted the same way (input rows from the last non-leaf node). */
+template <int MODEL>
+__global__ void bmpc_shift_warm_kernel(WarmArgs a) {
+    constexpr int NX = MODEL == 1 ? 6 : 4;
+    const int pid = a.order[blockIdx.x];
+    const ProbRec &R = a.recs[pid];
+    const ProbRec &Q = a.prev_recs[pid];
+    const int n = R.n, np = R.npad, nc = R.nc, ns = R.n_stage;
+    const IntOff io = int_off(np, ns, R.n_paths);
+    const int32_t *ib = a.ibase + R.off_int;
+    const int32_t *owner = ib + io.owner, *stage = ib + io.stage, *ptab = ib + io.ptab, *pdepth = ib + io.pdepth;
+    const IntOff qo = int_off(Q.npad, Q.n_stage, Q.n_paths);
+    const int32_t *qparent = a.prev_ibase + Q.off_int + qo.parent;
+    const InRows qi = in_rows(NX, Q.n_obs);
+    const float *qxref = a.prev_inbase + Q.off_in + (size_t)qi.xref * np;
+    const OutRows qr = out_rows(NX, nc);
+    const float *qout = a.prev_outbase + Q.off_out;
+    const float *qX = qout + (size_t)qr.x * np, *qU = qout + (size_t)qr.u * np;
+    const float *qL = qout + (size_t)qr.lam * np, *qY = qout + (size_t)qr.y * np;
+    const WarmRows wr = warm_rows(NX, nc);
+    float *w = a.warmbase + R.off_warm + (size_t)a.slot * wr.total * np;
+    const int box_rows = R.box_on ? 2 * NU : 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int s = owner[i], k = stage[i], depth = pdepth[s];
+        const int32_t *path = ptab + (size_t)s * ns;
+        const int jx = path[min(k + 1, depth)], ju = path[min(k + 1, max(depth - 1, 0))];
+        float xa[NX];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) xa[j] = qxref[(size_t)j * np + jx] + qX[(size_t)j * np + jx];
+        if (k + 1 > depth) {       /* beyond the previous leaf: append the last control and propagate */
+            const int jp = qparent[jx];
+            float ua[NU] = {qU[jp], qU[(size_t)np + jp]}, dl[NX];
+            dyn<NX, MODEL>(Q, xa, ua, dl);
+#pragma unroll
+            for (int j = 0; j < NX; ++j) xa[j] += dl[j];
+        }
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+            w[(size_t)(wr.wx + j) * np + i] = xa[j];
+            w[(size_t)(wr.wl + j) * np + i] = qL[(size_t)j * np + jx];
+        }
+        for (int j = 0; j < NU; ++j) w[(size_t)(wr.wu + j) * np + i] = qU[(size_t)j * np + ju];
+        for (int c = 0; c < nc; ++c) {
+            const int src = c < box_rows ? ju : jx;
+            w[(size_t)(wr.wy + c) * np + i] = qY[(size_t)c * np + src];
+        }
+    }
+}
+
+cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    bmpc_scatter_warm_kernel<<<a.n_problems, 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream) {
+    if (a.n_problems <= 0) return cudaSuccess;
+    if (model == 0) bmpc_shift_warm_kernel<0><<<a.n_problems, 256, 0, stream>>>(a);
+    else if (model == 1) bmpc_shift_warm_kernel<1><<<a.n_problems, 256, 0, stream>>>(a);
+    else bmpc_shift_warm_kernel<2><<<a.n_problems, 256, 0, stream>>>(a);
+    return cudaGetLastError();
 }
 
 /* Launch helper used by the host API: `args.order` lists problems of `model` only. */

@@ -80,7 +80,8 @@ __host__ __device__ inline InRows in_rows(int nx, int n_obs) {
     return r;
 }
 
-/* warm-start region (read only when has_warm): wx[nx] wu[nu] wl[nx] wy[nc] */
+/* warm-start region: two slots per problem (slot 0 = primary start, slot 1 = fallback start), each
+ * wx[nx] wu[nu] wl[nx] wy[nc]; has_warm bit s says slot s holds a start */
 struct WarmRows {
     int wx, wu, wl, wy, total;
 };
@@ -137,15 +138,27 @@ __host__ __device__ inline ScrRows scr_rows(int nx) {
 
 /* Kernel-side copy of the solver options (Algorithm 1 constants). */
 struct KOpts {
-    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant;
-    float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps;
+    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant, warm_select;
+    float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps, select_mu;
 };
 
 /* Per-problem statistics, same layout as the public bmpc_stats. */
 struct Stats {
-    int32_t status, inner_iters, outer_iters, ls_fail_total, ls_evals, reserved;
+    int32_t status, inner_iters, outer_iters, ls_fail_total, ls_evals, start_used;
     float r_kkt, c, rho, mu;
     int64_t cyc_lin, cyc_bwd, cyc_fwd, cyc_ls, cyc_total;
+};
+
+/* Arguments of the warm-start kernels (device scatter and receding-horizon shift). */
+struct WarmArgs {
+    const ProbRec *recs, *prev_recs;
+    const int32_t *ibase, *prev_ibase;
+    const float *inbase, *prev_inbase, *prev_outbase;
+    float *warmbase;
+    const float *src;          /* device scatter: [problem][stride] packed x | u | lam | y (node-major) */
+    int64_t stride;
+    const int32_t *order;      /* problems of one model */
+    int32_t n_problems, slot;
 };
 
 struct KernelArgs {

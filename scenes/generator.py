@@ -158,7 +158,7 @@ def _obstacle_tree(rng, parent, stage, dt, init_states, families):
     obs[:, :, 0:3] = st[:, :, 0:3]
     obs[:, :, 3] = ELLIPSE_A
     obs[:, :, 4] = ELLIPSE_B
-    return obs
+    return obs, st
 
 
 def _inside_any(obs_root, X, Y):
@@ -232,7 +232,9 @@ def config1(seed: int):
     p["x0"] = f32(x0)
     p["xref"] = _reference(p["x0"], p["stage"], p["nx"], p["dt"], y_line=float(p["x0"][1]))
     init = [(x0[0] + rng.uniform(15.0, 30.0), x0[1] + rng.uniform(-1.0, 1.0), 0.0, 0.0, 0.0, 0.0)]
-    p["obs"] = _obstacle_tree(rng, p["parent"], p["stage"], p["dt"], init, "line")
+    p["obs"], p["obs_state"] = _obstacle_tree(rng, p["parent"], p["stage"], p["dt"], init, "line")
+    p["obs_family"] = ["line"]
+    p["y_line"] = float(p["x0"][1])
     p["lane_on"] = 0
     return _finish(p)
 
@@ -247,7 +249,9 @@ def _multi_obstacle(rng, p, n_obs, n_cross, cross_dist=(30.0, 50.0)):
         else:
             init.append(_adjacent_obstacle(rng, x0[0]))
             fam.append("adjacent")
-    p["obs"] = _obstacle_tree(rng, p["parent"], p["stage"], p["dt"], init, fam)
+    p["obs"], p["obs_state"] = _obstacle_tree(rng, p["parent"], p["stage"], p["dt"], init, fam)
+    p["obs_family"] = fam
+    p["y_line"] = 0.0
     p["lane_on"] = 1
     return p
 
@@ -314,3 +318,16 @@ def instances(config: int, count: int, seed0: int = 0):
     """Seeded instances of a configuration (1-3), seeds seed0 .. seed0+count-1."""
     gen = {1: config1, 2: config2, 3: config3}[config]
     return [gen(seed0 + s) for s in range(count)]
+
+
+def advance(p, x0_next, seed: int):
+    """The next receding-horizon problem of scene p: the same tree and costs, measured state
+    x0_next, the reference restarted from it, and every obstacle continuing from its state at the
+    first scenario's stage-1 node with behaviours resampled for the new branches."""
+    rng = np.random.default_rng([9, seed])
+    q = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+    q["x0"] = f32(np.asarray(x0_next, dtype=np.float64))
+    q["xref"] = _reference(q["x0"], p["stage"], p["nx"], p["dt"], y_line=p.get("y_line", 0.0))
+    init = [tuple(v) for v in p["obs_state"][1]]
+    q["obs"], q["obs_state"] = _obstacle_tree(rng, p["parent"], p["stage"], p["dt"], init, p["obs_family"])
+    return _finish(q)

@@ -216,6 +216,62 @@ def test_autotuner_returns_a_valid_configuration():
             np.testing.assert_allclose(a["u"], r["u"], atol=tol)
 
 
+def test_shifted_warm_start_receding_horizon():
+    """Solve, advance the scenes one step, warm-start from the shifted solution: converged, matches
+    the oracle on the new problem, and needs fewer iterations than the cold start."""
+    from paper_2506_13624_b300 import bmpc
+    prev_ps = scenes.instances(2, 6, seed0=20)
+    prev = bmpc.Batch(prev_ps)
+    prev.set_problems()
+    prev.solve()
+    pres = prev.get_solutions()
+    next_ps = [scenes.advance(p, r["x"][1], seed=k) for k, (p, r) in enumerate(zip(prev_ps, pres))]
+    cold = _gpu(next_ps)
+    nb = bmpc.Batch(next_ps)
+    nb.set_problems()
+    nb.shift_from(prev, slot=0)
+    nb.solve()
+    warm = nb.get_solutions()
+    nb.close()
+    prev.close()
+    assert all(w["start_used"] == 1 for w in warm)
+    for p, w in zip(next_ps, warm):
+        r = oracle.solve(p)
+        if r["status"] == oracle.OK:
+            _check_pair(p, w, r)
+    assert sum(w["inner_iters"] for w in warm) < sum(c["inner_iters"] for c in cold)
+
+
+def test_merit_selection_between_starts():
+    """warm_select keeps a good primary start and rejects a bad one for the fallback."""
+    import torch as T
+    from paper_2506_13624_b300 import bmpc
+    ps = scenes.instances(1, 4, seed0=30)
+    first = _gpu(ps)
+    b = bmpc.Batch(ps)
+    b.set_problems()
+    stride = b.start_stride()
+    good = np.zeros((len(ps), stride), np.float32)
+    for k, (p, g) in enumerate(zip(ps, first)):
+        packed = np.concatenate([g["x"].ravel(), g["u"].ravel(), g["lam"].ravel(), g["y"].ravel()])
+        good[k, :packed.size] = packed
+    bad = good.copy()
+    bad[:, :] = 50.0
+    opts = bmpc.default_opts(warm_select=1)
+    b.set_warm_device(T.from_numpy(good).cuda(), slot=0)
+    b.solve(opts)
+    rg = b.get_solutions()
+    b.set_problems()
+    b.set_warm_device(T.from_numpy(bad).cuda(), slot=0)
+    b.solve(opts)
+    rb = b.get_solutions()
+    b.close()
+    for a, c, f in zip(rg, rb, first):
+        assert a["start_used"] == 1 and a["status"] == oracle.OK and a["inner_iters"] <= 2
+        assert c["start_used"] == 0 and c["status"] == f["status"]
+        assert np.array_equal(c["u"], f["u"])
+
+
 def test_invalid_problem_rejected():
     from paper_2506_13624_b300 import bmpc
     p = dict(scenes.config1(0))
