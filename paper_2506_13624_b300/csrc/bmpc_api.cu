@@ -17,6 +17,7 @@
 
 #include "../../include/bmpc.h"
 #include "bmpc_layout.h"
+#include "../../include/bmpc_mlp.h"
 
 namespace bmpc {
 cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, cudaStream_t stream);
@@ -24,6 +25,17 @@ int max_block_threads();
 cudaError_t occupancy(int model, int block, int *blocks_per_sm);
 cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
 cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream);
+struct GlueArgs {
+    const ProbRec *recs;
+    const int32_t *ibase;
+    const float *inbase, *outbase;
+    float *out;
+    int64_t stride;
+    const float *pred, *mean, *std;
+    int64_t ld_pred;
+    int32_t n_scen, n_obs_max;
+};
+cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream_t stream);
 }  // namespace bmpc
 
 using namespace bmpc;
@@ -597,6 +609,56 @@ int bmpc_shift_warm_start(bmpc_batch *next, const bmpc_batch *prev, int32_t slot
         if (launch_shift_warm(wm, m, next->stream) != cudaSuccess) return BMPC_ERR_CUDA;
     }
     return BMPC_OK;
+}
+
+namespace {
+GlueArgs glue_args(const bmpc_batch *b) {
+    GlueArgs g{};
+    g.recs = reinterpret_cast<const ProbRec *>(b->data + b->L.recs);
+    g.ibase = reinterpret_cast<const int32_t *>(b->data + b->L.ints);
+    g.inbase = reinterpret_cast<const float *>(b->data + b->L.in);
+    g.outbase = reinterpret_cast<const float *>(b->data + b->L.out);
+    return g;
+}
+}  // namespace
+
+int bmpc_mlp_features(const bmpc_batch *b, float *feat, int32_t dim, int32_t n_scen, int32_t n_obs_max) {
+    if (!b || !feat || n_scen < 0 || n_obs_max < 0) return BMPC_ERR_INVALID;
+    for (const ProbRec &R : b->recs)
+        if (dim < R.nx - 1 + 5 * n_scen * n_obs_max) return BMPC_ERR_INVALID;
+    GlueArgs g = glue_args(b);
+    g.out = feat;
+    g.stride = dim;
+    g.n_scen = n_scen;
+    g.n_obs_max = n_obs_max;
+    return cuda_status(launch_glue(0, g, b->n, b->stream));
+}
+
+int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride) {
+    if (!b || !tgt) return BMPC_ERR_INVALID;
+    for (const ProbRec &R : b->recs)
+        if ((int64_t)R.n * (2 * R.nx + NU + R.nc) > stride) return BMPC_ERR_INVALID;
+    GlueArgs g = glue_args(b);
+    g.out = tgt;
+    g.stride = stride;
+    return cuda_status(launch_glue(1, g, b->n, b->stream));
+}
+
+int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, const float *mean, const float *std,
+                   float *start, int64_t stride) {
+    if (!b || !pred || !mean || !std || !start) return BMPC_ERR_INVALID;
+    for (const ProbRec &R : b->recs) {
+        const int64_t used = (int64_t)R.n * (2 * R.nx + NU + R.nc);
+        if (used > stride || used > ld_pred) return BMPC_ERR_INVALID;
+    }
+    GlueArgs g = glue_args(b);
+    g.out = start;
+    g.stride = stride;
+    g.pred = pred;
+    g.ld_pred = ld_pred;
+    g.mean = mean;
+    g.std = std;
+    return cuda_status(launch_glue(2, g, b->n, b->stream));
 }
 
 int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *best_us_per_solve) {

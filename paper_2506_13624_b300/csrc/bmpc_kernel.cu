@@ -1805,6 +1805,95 @@ cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream)
     return cudaGetLastError();
 }
 
+
+/* ------------------------------------------------------------------ learned warm start: glue kernels */
+struct GlueArgs {
+    const ProbRec *recs;
+    const int32_t *ibase;
+    const float *inbase, *outbase;
+    float *out;                 /* features / targets / starts, problem k at out + k*stride */
+    int64_t stride;
+    const float *pred, *mean, *std;
+    int64_t ld_pred;
+    int32_t n_scen, n_obs_max;
+};
+
+/* Features: x0 without X, then per scenario and obstacle (cx - X0, cy) at the path's middle node
+ * and (cx - X0, cy, heading) at its leaf. */
+__global__ void bmpc_features_kernel(GlueArgs a) {
+    const int pid = blockIdx.x;
+    const ProbRec &R = a.recs[pid];
+    const int np = R.npad, nx = R.nx;
+    const IntOff io = int_off(np, R.n_stage, R.n_paths);
+    const int32_t *ib = a.ibase + R.off_int;
+    const InRows ir = in_rows(nx, R.n_obs);
+    const float *obs = a.inbase + R.off_in + (size_t)ir.obs * np;
+    float *f = a.out + (size_t)pid * a.stride;
+    for (int j = threadIdx.x; j < a.stride; j += blockDim.x) f[j] = 0.f;
+    __syncthreads();
+    if (threadIdx.x < nx - 1) f[threadIdx.x] = R.x0[threadIdx.x + 1];
+    const int S = min(a.n_scen, R.n_paths), O = min(a.n_obs_max, R.n_obs);
+    for (int t = threadIdx.x; t < S * O; t += blockDim.x) {
+        const int s = t / O, o = t % O;
+        const int depth = ib[io.pdepth + s];
+        const int32_t *path = ib + io.ptab + (size_t)s * R.n_stage;
+        const int mid = path[depth / 2], leaf = path[depth];
+        const float *ob = obs + (size_t)(5 * o) * np;
+        float *g = f + (nx - 1) + 5 * (s * a.n_obs_max + o);
+        g[0] = ob[mid] - R.x0[0];
+        g[1] = ob[(size_t)np + mid];
+        g[2] = ob[leaf] - R.x0[0];
+        g[3] = ob[(size_t)np + leaf];
+        g[4] = ob[2 * (size_t)np + leaf];
+    }
+}
+
+/* Targets: the current solution packed node-major x | u | lam | y, X0 subtracted from the X of
+ * every state. */
+__global__ void bmpc_targets_kernel(GlueArgs a) {
+    const int pid = blockIdx.x;
+    const ProbRec &R = a.recs[pid];
+    const int n = R.n, np = R.npad, nx = R.nx, nc = R.nc;
+    const InRows ir = in_rows(nx, R.n_obs);
+    const float *xref = a.inbase + R.off_in + (size_t)ir.xref * np;
+    const OutRows orw = out_rows(nx, nc);
+    const float *o = a.outbase + R.off_out;
+    float *t = a.out + (size_t)pid * a.stride;
+    float *tx = t, *tu = tx + (size_t)n * nx, *tl = tu + (size_t)n * NU, *ty = tl + (size_t)n * nx;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int j = 0; j < nx; ++j) {
+            const float dv = o[(size_t)(orw.x + j) * np + i];
+            tx[(size_t)i * nx + j] = j == 0 ? (xref[i] - R.x0[0]) + dv : xref[(size_t)j * np + i] + dv;
+            tl[(size_t)i * nx + j] = o[(size_t)(orw.lam + j) * np + i];
+        }
+        for (int j = 0; j < NU; ++j) tu[(size_t)i * NU + j] = o[(size_t)(orw.u + j) * np + i];
+        for (int c = 0; c < nc; ++c) ty[(size_t)i * nc + c] = o[(size_t)(orw.y + c) * np + i];
+    }
+    const int64_t used = (int64_t)n * (2 * nx + NU + nc);
+    for (int64_t j = used + threadIdx.x; j < a.stride; j += blockDim.x) t[j] = 0.f;
+}
+
+/* Starts from network outputs: mean + std * pred, X0 added back to the X of every state. */
+__global__ void bmpc_starts_kernel(GlueArgs a) {
+    const int pid = blockIdx.x;
+    const ProbRec &R = a.recs[pid];
+    const int64_t used = (int64_t)R.n * (2 * R.nx + NU + R.nc);
+    const float *p = a.pred + (size_t)pid * a.ld_pred;
+    float *s = a.out + (size_t)pid * a.stride;
+    for (int64_t j = threadIdx.x; j < used; j += blockDim.x) {
+        float v = a.mean[j] + a.std[j] * p[j];
+        if (j < (int64_t)R.n * R.nx && j % R.nx == 0) v += R.x0[0];
+        s[j] = v;
+    }
+}
+
+cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream_t stream) {
+    if (which == 0) bmpc_features_kernel<<<n_problems, 256, 0, stream>>>(a);
+    else if (which == 1) bmpc_targets_kernel<<<n_problems, 256, 0, stream>>>(a);
+    else bmpc_starts_kernel<<<n_problems, 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
 /* Launch helper used by the host API: `args.order` lists problems of `model` only. */
 cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, cudaStream_t stream) {
     if (model == 0) bmpc_solve_kernel<0><<<grid, block, 0, stream>>>(args);

@@ -1,0 +1,147 @@
+"""Thin binding of the learned warm-start network (include/bmpc_mlp.h).
+
+Torch tensors hold the weights, AdamW moments, gradients and activations; every
+computation (tensor-core GEMMs, GELU, loss, back-propagation, AdamW, feature and
+start kernels) runs in libbmpc.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from .bmpc import _check, lib
+
+MAX_LAYERS = 8
+_u16p = C.POINTER(C.c_uint16)
+_fp = C.POINTER(C.c_float)
+
+
+class Layer(C.Structure):
+    _fields_ = [("in_", C.c_int32), ("out", C.c_int32), ("w_bf16", C.c_void_p), ("w", C.c_void_p),
+                ("w_m", C.c_void_p), ("w_v", C.c_void_p), ("b", C.c_void_p), ("b_m", C.c_void_p),
+                ("b_v", C.c_void_p), ("dw", C.c_void_p), ("db", C.c_void_p)]
+
+
+class Work(C.Structure):
+    _fields_ = [("pre", C.c_void_p * MAX_LAYERS), ("act", C.c_void_p * MAX_LAYERS), ("dy0", C.c_void_p),
+                ("dy1", C.c_void_p), ("pred", C.c_void_p), ("loss", C.c_void_p)]
+
+
+def _setup():
+    L = lib()
+    if getattr(L, "_mlp_ready", False):
+        return L
+    L.bmpc_mlp_init.argtypes = [C.POINTER(Layer), C.c_int32, C.c_uint64, C.c_void_p]
+    L.bmpc_mlp_forward.argtypes = [C.POINTER(Layer), C.c_int32, C.c_void_p, C.c_int32, C.POINTER(Work), C.c_void_p]
+    L.bmpc_mlp_train_step.argtypes = [C.POINTER(Layer), C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                      C.c_float, C.c_int32, C.POINTER(Work), C.c_void_p]
+    L.bmpc_mlp_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
+    L.bmpc_mlp_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32]
+    L.bmpc_mlp_targets.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    L.bmpc_mlp_start.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+    L.bmpc_mlp_standardize.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                       C.c_void_p]
+    L._mlp_ready = True
+    return L
+
+
+def _stream(torch):
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def gemm(A, B, trans_a=False, trans_b=False):
+    """C = op(A) op(B) in fp32 from bf16 CUDA tensors (dimensions multiples of 128 / 32)."""
+    import torch
+    L = _setup()
+    M = A.shape[1] if trans_a else A.shape[0]
+    K = A.shape[0] if trans_a else A.shape[1]
+    N = B.shape[0] if trans_b else B.shape[1]
+    Cm = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    rc = L.bmpc_mlp_gemm(A.data_ptr(), A.shape[1], int(trans_a), B.data_ptr(), B.shape[1], int(trans_b),
+                         Cm.data_ptr(), N, M, N, K, _stream(torch))
+    if rc != 0:
+        raise RuntimeError(f"bmpc_mlp_gemm failed: {rc}")
+    return Cm
+
+
+class MLP:
+    """Multilayer perceptron dims[0] -> ... -> dims[-1] (GELU between layers), widths multiples of 128."""
+
+    def __init__(self, dims, device="cuda", seed=0):
+        import torch
+        assert all(d % 128 == 0 for d in dims) and 2 <= len(dims) <= MAX_LAYERS + 1
+        self.torch = torch
+        self.dims = list(dims)
+        self.device = torch.device(device)
+        self.params = []
+        self.c_layers = (Layer * (len(dims) - 1))()
+        for l, (a, b) in enumerate(zip(dims[:-1], dims[1:])):
+            f32 = dict(dtype=torch.float32, device=self.device)
+            t = dict(w_bf16=torch.empty((a, b), dtype=torch.bfloat16, device=self.device),
+                     w=torch.empty((a, b), **f32), w_m=torch.empty((a, b), **f32), w_v=torch.empty((a, b), **f32),
+                     b=torch.empty(b, **f32), b_m=torch.empty(b, **f32), b_v=torch.empty(b, **f32),
+                     dw=torch.empty((a, b), **f32), db=torch.empty(b, **f32))
+            self.params.append(t)
+            cl = self.c_layers[l]
+            cl.in_, cl.out = a, b
+            for k, v in t.items():
+                setattr(cl, k, v.data_ptr())
+        _check(_setup().bmpc_mlp_init(self.c_layers, len(self.params), seed, _stream(torch)), "bmpc_mlp_init")
+        self._work = {}
+        self.step_count = 0
+
+    def work(self, batch: int):
+        if batch in self._work:
+            return self._work[batch]
+        torch = self.torch
+        w = Work()
+        keep = []
+        for l, d in enumerate(self.dims[1:-1]):
+            pre = torch.empty((batch, d), dtype=torch.bfloat16, device=self.device)
+            act = torch.empty((batch, d), dtype=torch.bfloat16, device=self.device)
+            keep += [pre, act]
+            w.pre[l], w.act[l] = pre.data_ptr(), act.data_ptr()
+        widest = max(self.dims[1:])
+        dy0 = torch.empty((batch, widest), dtype=torch.bfloat16, device=self.device)
+        dy1 = torch.empty((batch, widest), dtype=torch.bfloat16, device=self.device)
+        pred = torch.empty((batch, self.dims[-1]), dtype=torch.float32, device=self.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        keep += [dy0, dy1, pred, loss]
+        w.dy0, w.dy1, w.pred, w.loss = dy0.data_ptr(), dy1.data_ptr(), pred.data_ptr(), loss.data_ptr()
+        self._work[batch] = (w, keep, pred, loss)
+        return self._work[batch]
+
+    def forward(self, x):
+        """x: bf16 CUDA tensor [batch, dims[0]] -> fp32 prediction [batch, dims[-1]] (a view)."""
+        w, _, pred, _ = self.work(x.shape[0])
+        _check(_setup().bmpc_mlp_forward(self.c_layers, len(self.params), x.data_ptr(), x.shape[0], C.byref(w),
+                                         _stream(self.torch)), "bmpc_mlp_forward")
+        return pred
+
+    def train_step(self, x, target, lr, weight_decay=0.0):
+        """One AdamW step on (x, target), both bf16 [batch, ...]; returns the loss tensor (device)."""
+        w, _, _, loss = self.work(x.shape[0])
+        self.step_count += 1
+        _check(_setup().bmpc_mlp_train_step(self.c_layers, len(self.params), x.data_ptr(), target.data_ptr(),
+                                            x.shape[0], lr, weight_decay, self.step_count, C.byref(w),
+                                            _stream(self.torch)), "bmpc_mlp_train_step")
+        return loss
+
+
+def features(batch, out, n_scen, n_obs):
+    _check(_setup().bmpc_mlp_features(batch.handle, out.data_ptr(), out.shape[1], n_scen, n_obs), "bmpc_mlp_features")
+
+
+def targets(batch, out):
+    _check(_setup().bmpc_mlp_targets(batch.handle, out.data_ptr(), out.shape[1]), "bmpc_mlp_targets")
+
+
+def starts(batch, pred, mean, std, out):
+    _check(_setup().bmpc_mlp_start(batch.handle, pred.data_ptr(), pred.shape[1], mean.data_ptr(), std.data_ptr(),
+                                   out.data_ptr(), out.shape[1]), "bmpc_mlp_start")
+
+
+def standardize(raw, mean, std, out):
+    import torch
+    _check(_setup().bmpc_mlp_standardize(raw.data_ptr(), mean.data_ptr(), std.data_ptr(), out.data_ptr(),
+                                         raw.shape[0], raw.shape[1], _stream(torch)), "bmpc_mlp_standardize")

@@ -331,3 +331,130 @@ def advance(p, x0_next, seed: int):
     init = [tuple(v) for v in p["obs_state"][1]]
     q["obs"], q["obs_state"] = _obstacle_tree(rng, p["parent"], p["stage"], p["dt"], init, p["obs_family"])
     return _finish(q)
+
+
+# ---------------------------------------------------------------- vectorised batches (one tree)
+def _modes_batch(rng, fam, side, shape):
+    """Vectorised _sample_mode for obstacles of one family: (speed or nan, yaw_rate, decel)."""
+    r = rng.uniform(size=shape)
+    sp = np.full(shape, np.nan)
+    yr = np.zeros(shape)
+    dc = np.zeros(shape)
+    if fam == "line":
+        sp = rng.uniform(0.0, 10.0, size=shape)
+        return sp, yr, dc
+    if fam == "adjacent":
+        dc = np.where((r >= 0.4) & (r < 0.7), 2.0, 0.0)
+        yr = np.where(r >= 0.7, -side * 0.05, 0.0)
+        return sp, yr, dc
+    turn = rng.choice([-0.2, 0.2], size=shape)
+    dc = np.where((r >= 0.4) & (r < 0.75), 2.0, 0.0)
+    yr = np.where(r >= 0.75, turn, 0.0)
+    return sp, yr, dc
+
+
+def _obstacle_tree_batch(rng, parent, stage, dt, init, families):
+    """Obstacle propagation along one tree for P scenes at once; init [P, n_obs, 6].  Returns the
+    per-node ellipses [P, n, n_obs, 5] (float32 values) and the obstacle states at node 1."""
+    P, n_obs = init.shape[0], init.shape[1]
+    n = parent.shape[0]
+    nch = np.bincount(parent[1:], minlength=n)
+    obs = np.zeros((P, n, n_obs, 5), np.float32)
+    obs[:, :, :, 3] = ELLIPSE_A
+    obs[:, :, :, 4] = ELLIPSE_B
+    obs[:, 0, :, 0:3] = init[:, :, 0:3]
+    side = np.sign(init[:, :, 1])
+    side[side == 0] = 1.0
+    prev_nodes, prev_state = np.array([0]), init[:, None].copy()      # [P, m, n_obs, 6]
+    st1 = None
+    for k in range(1, int(stage.max()) + 1):
+        nodes = np.where(stage == k)[0]
+        par = parent[nodes]
+        loc = np.searchsorted(prev_nodes, par)
+        prev = prev_state[:, loc]
+        sp, yr, dc = prev[..., 3].copy(), prev[..., 4].copy(), prev[..., 5].copy()
+        branch = nch[par] > 1
+        if branch.any():
+            bi = np.where(branch)[0]
+            for j, fam in enumerate(families):
+                m_sp, m_yr, m_dc = _modes_batch(rng, fam, side[:, None, j], (P, bi.size))
+                cur = sp[:, bi, j]
+                sp[:, bi, j] = np.where(np.isnan(m_sp), cur, m_sp)
+                yr[:, bi, j] = m_yr
+                dc[:, bi, j] = m_dc
+        sp_new = np.maximum(0.0, sp - dc * dt)
+        hd_new = prev[..., 2] + yr * dt
+        vmean = 0.5 * (sp + sp_new)
+        cur = np.empty_like(prev)
+        cur[..., 0] = prev[..., 0] + vmean * np.cos(hd_new) * dt
+        cur[..., 1] = prev[..., 1] + vmean * np.sin(hd_new) * dt
+        cur[..., 2] = hd_new
+        cur[..., 3] = sp_new
+        cur[..., 4] = yr
+        cur[..., 5] = dc
+        obs[:, nodes, :, 0:3] = cur[..., 0:3]
+        if k == 1:
+            st1 = cur[:, 0].copy()
+        prev_nodes, prev_state = nodes, cur
+    return obs, st1
+
+
+def _reference_batch(x0, stage, nx, dt, y_line):
+    """Vectorised _reference for P initial states x0 [P, nx]."""
+    N = int(stage.max())
+    k = np.arange(N + 1)
+    v0 = x0[:, 3:4]
+    v = v0 + np.clip(V_REF - v0, -REF_ACCEL * k * dt, REF_ACCEL * k * dt)
+    X = np.concatenate([x0[:, 0:1], x0[:, 0:1] + np.cumsum(0.5 * (v[:, :-1] + v[:, 1:]) * dt, axis=1)], axis=1)
+    ref = np.zeros((x0.shape[0], N + 1, nx))
+    ref[:, :, 0] = X
+    ref[:, :, 1] = np.asarray(y_line)[:, None] if np.ndim(y_line) else y_line
+    ref[:, :, 3] = v
+    return ref[:, stage]
+
+
+def batch_problems(seed: int, count: int, model=MODEL_DYNAMIC, N=60, splits=None, n_obs=5, n_cross=2,
+                   cross_dist=(45.0, 70.0)):
+    """`count` scenes on one tree (default: the config-3 recipe), generated vectorised from one
+    seed: initial states, references and per-node obstacle predictions as in config3()."""
+    splits = {1: 4, 10: 4, 20: 4} if splits is None else splits
+    rng = np.random.default_rng([11, seed])
+    base = _base(model, N, splits)
+    parent, stage, nx = base["parent"], base["stage"], base["nx"]
+    vr = (2.0, 10.0) if model == MODEL_DYNAMIC else (0.0, 10.0)
+    x0 = np.zeros((count, nx))
+    x0[:, 0] = rng.uniform(-10.0, 10.0, count)
+    x0[:, 1] = rng.uniform(-1.5, 1.5, count)
+    x0[:, 2] = rng.uniform(-math.pi / 12, math.pi / 12, count)
+    x0[:, 3] = rng.uniform(*vr, count)
+    x0 = f32(x0)
+    xref = _reference_batch(x0, stage, nx, base["dt"], 0.0)
+    init = np.zeros((count, n_obs, 6))
+    fam = []
+    for j in range(n_obs):
+        if j < n_cross:
+            side = rng.choice([-1.0, 1.0], count)
+            init[:, j] = np.stack([x0[:, 0] + rng.uniform(*cross_dist, count), side * rng.uniform(10.0, 18.0, count),
+                                   -side * math.pi / 2, rng.uniform(3.0, 8.0, count), np.zeros(count),
+                                   np.zeros(count)], 1)
+            fam.append("crossing")
+        else:
+            side = rng.choice([-1.0, 1.0], count)
+            init[:, j] = np.stack([x0[:, 0] + rng.uniform(5.0, 30.0, count), side * 3.5, np.zeros(count),
+                                   rng.uniform(4.0, 9.0, count), np.zeros(count), np.zeros(count)], 1)
+            fam.append("adjacent")
+    obs, st1 = _obstacle_tree_batch(rng, parent, stage, base["dt"], init, fam)
+    obs, xref = obs.astype(np.float64), f32(xref)
+    shared = _finish(dict(base, x0=x0[0], xref=xref[0], obs=obs[0], lane_on=1))
+    out = []
+    for i in range(count):
+        p = dict(shared)
+        p["x0"] = x0[i]
+        p["xref"] = xref[i]
+        p["obs"] = obs[i]
+        p["obs_state"] = np.zeros((2,) + st1.shape[1:])
+        p["obs_state"][1] = st1[i]
+        p["obs_family"] = fam
+        p["y_line"] = 0.0
+        out.append(p)
+    return out

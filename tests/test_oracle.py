@@ -392,3 +392,44 @@ def test_invalid_tree_rejected():
     bad["parent"] = par
     r = oracle.solve(bad)
     assert r["status"] == -1
+
+
+# ------------------------------------------------------------------ learned warm-start network (reference)
+def test_mlp_reference_gradients_match_central_differences():
+    from oracle import mlp_ref
+    rng = np.random.default_rng(0)
+    dims = [7, 9, 6, 5]
+    Ws = [0.5 * rng.standard_normal((a, b)) for a, b in zip(dims[:-1], dims[1:])]
+    bs = [0.1 * rng.standard_normal(b) for b in dims[1:]]
+    x = rng.standard_normal((4, dims[0]))
+    t = rng.standard_normal((4, dims[-1]))
+    loss, dWs, dbs = mlp_ref.loss_and_grads(Ws, bs, x, t, bf=False)
+    h = 1e-6
+    for l in range(len(Ws)):
+        for (i, j) in [(0, 0), (dims[l] - 1, dims[l + 1] - 1), (2, 1)]:
+            Wp = [W.copy() for W in Ws]
+            Wm = [W.copy() for W in Ws]
+            Wp[l][i, j] += h
+            Wm[l][i, j] -= h
+            fd = (mlp_ref.loss_and_grads(Wp, bs, x, t, bf=False)[0] - mlp_ref.loss_and_grads(Wm, bs, x, t, bf=False)[0]) / (2 * h)
+            assert abs(fd - dWs[l][i, j]) < 1e-6 * max(1.0, abs(fd))
+        bp = [b.copy() for b in bs]
+        bm = [b.copy() for b in bs]
+        bp[l][1] += h
+        bm[l][1] -= h
+        fd = (mlp_ref.loss_and_grads(Ws, bp, x, t, bf=False)[0] - mlp_ref.loss_and_grads(Ws, bm, x, t, bf=False)[0]) / (2 * h)
+        assert abs(fd - dbs[l][1]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_gelu_and_bf16_rounding():
+    from oracle import mlp_ref
+    x = np.linspace(-4, 4, 41)
+    h = 1e-6
+    fd = (mlp_ref.gelu(x + h) - mlp_ref.gelu(x - h)) / (2 * h)
+    np.testing.assert_allclose(mlp_ref.gelu_grad(x), fd, atol=1e-8)
+    assert mlp_ref.gelu(np.array([0.0]))[0] == 0.0 and abs(mlp_ref.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
+    # bfloat16: 8 significant bits, ties to even
+    assert mlp_ref.bf16(1.0 + 2.0 ** -8) == 1.0                 # tie -> even (1.0)
+    assert mlp_ref.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6  # tie -> even (1 + 2^-6)
+    assert mlp_ref.bf16(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7      # exactly representable
+    assert mlp_ref.bf16(-3.0) == -3.0
