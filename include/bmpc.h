@@ -119,7 +119,9 @@ typedef struct {
                                all compute the same search direction */
     int32_t warm_select;    /* 1: start from warm slot 0 only if its merit is not above that of the fallback
                                (warm slot 1 when set, else the cold start); default 0 */
-    float select_mu;        /* defect penalty mu of the merit used by warm_select (rho = rho0), default 100 */
+    float select_mu;        /* defect penalty mu of the merit used by warm_select, default 100 */
+    float select_rho;       /* constraint penalty rho of the merit used by warm_select, default 1e4: a start
+                               that cuts through a keep-out region loses to one that does not */
 } bmpc_opts;
 
 typedef struct {

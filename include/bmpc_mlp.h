@@ -72,8 +72,9 @@ int bmpc_mlp_features(const bmpc_batch *b, float *feat, int32_t dim, int32_t n_s
  * x | u | lam | y (node-major) with X0 subtracted from every state's X. */
 int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride);
 /* Packed warm starts from network outputs: start[k] = mean + std * pred[k] with X0 added back to
- * every state's X (the inverse of bmpc_mlp_targets after standardisation); feed to
- * bmpc_set_warm_start_device. */
+ * every state's X (the inverse of bmpc_mlp_targets after standardisation), then the states
+ * replaced by the rollout of the predicted controls from x0 through the tree, so that the start
+ * satisfies the dynamics; feed to bmpc_set_warm_start_device. */
 int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, const float *mean, const float *std,
                    float *start, int64_t stride);
 /* out = bf16((raw - mean) / std) elementwise over rows x dim. */

@@ -45,7 +45,7 @@ class Opts(C.Structure):
                 ("rho0", C.c_float), ("rho_max", C.c_float), ("mu0", C.c_float), ("beta", C.c_float),
                 ("ls_rel_eps", C.c_float), ("ls_chunk", C.c_int32), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("variant", C.c_int32), ("warm_select", C.c_int32),
-                ("select_mu", C.c_float)]
+                ("select_mu", C.c_float), ("select_rho", C.c_float)]
 
 
 class Stats(C.Structure):

@@ -34,8 +34,9 @@ struct GlueArgs {
     const float *pred, *mean, *std;
     int64_t ld_pred;
     int32_t n_scen, n_obs_max;
+    const int32_t *order_base;
 };
-cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream_t stream);
+cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream_t stream, int model);
 }  // namespace bmpc
 
 using namespace bmpc;
@@ -204,6 +205,7 @@ KOpts to_kopts(const bmpc_opts &o) {
     k.beta = o.beta;
     k.ls_rel_eps = o.ls_rel_eps;
     k.select_mu = o.select_mu;
+    k.select_rho = o.select_rho;
     return k;
 }
 
@@ -216,7 +218,8 @@ int check_opts(const bmpc_opts &o) {
         return BMPC_ERR_INVALID;
     if (o.blocks_per_sm < 0) return BMPC_ERR_INVALID;
     if (o.variant < 0 || o.variant > 3) return BMPC_ERR_INVALID;
-    if (o.warm_select < 0 || o.warm_select > 1 || !(o.select_mu >= 0.f)) return BMPC_ERR_INVALID;
+    if (o.warm_select < 0 || o.warm_select > 1 || !(o.select_mu >= 0.f) ||
+        !(o.select_rho > 0.f)) return BMPC_ERR_INVALID;
     if ((o.variant == 0 || o.variant == 3) && o.block_threads != 0 && o.block_threads % 32) return BMPC_ERR_INVALID;
     return BMPC_OK;
 }
@@ -298,6 +301,7 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->variant = 0;
     o->warm_select = 0;
     o->select_mu = 100.f;
+    o->select_rho = 1e4f;
 }
 
 int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
@@ -631,7 +635,7 @@ int bmpc_mlp_features(const bmpc_batch *b, float *feat, int32_t dim, int32_t n_s
     g.stride = dim;
     g.n_scen = n_scen;
     g.n_obs_max = n_obs_max;
-    return cuda_status(launch_glue(0, g, b->n, b->stream));
+    return cuda_status(launch_glue(0, g, b->n, b->stream, 0));
 }
 
 int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride) {
@@ -641,7 +645,7 @@ int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride) {
     GlueArgs g = glue_args(b);
     g.out = tgt;
     g.stride = stride;
-    return cuda_status(launch_glue(1, g, b->n, b->stream));
+    return cuda_status(launch_glue(1, g, b->n, b->stream, 0));
 }
 
 int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, const float *mean, const float *std,
@@ -658,7 +662,12 @@ int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, cons
     g.ld_pred = ld_pred;
     g.mean = mean;
     g.std = std;
-    return cuda_status(launch_glue(2, g, b->n, b->stream));
+    for (int m = 0; m < 3; ++m) {
+        const int cnt = b->model_begin[m + 1] - b->model_begin[m];
+        g.order_base = reinterpret_cast<const int32_t *>(b->data + b->L.order) + b->model_begin[m];
+        if (launch_glue(2, g, cnt, b->stream, m) != cudaSuccess) return BMPC_ERR_CUDA;
+    }
+    return BMPC_OK;
 }
 
 int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *best_us_per_solve) {

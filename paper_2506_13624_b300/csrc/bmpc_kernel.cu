@@ -1378,17 +1378,17 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
     long long t_start = clock64(), c_lin = 0, c_bwd = 0, c_fwd = 0, c_ls = 0;
 
     /* ---- initial iterate: a warm-start slot or the cold start of Sec. V-B.  With warm_select the
-     * primary start is used only when its merit (at rho0, with the defect penalty select_mu) is not
+     * primary start is used only when its merit (penalties select_rho, select_mu) is not
      * above the fallback's (slot 1, or the cold start). */
     int start = (R.has_warm & 1) ? 1 : ((R.has_warm & 2) ? 2 : 0);
     if (O.warm_select && (R.has_warm & 1)) {
         const int fb = (R.has_warm & 2) ? 2 : 0;
         load_start<NX>(R, V, 1);
         __syncthreads();
-        const float m1 = start_merit<NX, MODEL>(R, V, O.rho0, O.select_mu, sh);
+        const float m1 = start_merit<NX, MODEL>(R, V, O.select_rho, O.select_mu, sh);
         load_start<NX>(R, V, fb);
         __syncthreads();
-        const float m2 = start_merit<NX, MODEL>(R, V, O.rho0, O.select_mu, sh);
+        const float m2 = start_merit<NX, MODEL>(R, V, O.select_rho, O.select_mu, sh);
         start = (m1 == m1 && !(m1 > m2)) ? 1 : fb;
     }
     load_start<NX>(R, V, start);
@@ -1816,6 +1816,7 @@ struct GlueArgs {
     const float *pred, *mean, *std;
     int64_t ld_pred;
     int32_t n_scen, n_obs_max;
+    const int32_t *order_base;  /* starts: problems of one model */
 };
 
 /* Features: x0 without X, then per scenario and obstacle (cx - X0, cy) at the path's middle node
@@ -1873,24 +1874,54 @@ __global__ void bmpc_targets_kernel(GlueArgs a) {
     for (int64_t j = used + threadIdx.x; j < a.stride; j += blockDim.x) t[j] = 0.f;
 }
 
-/* Starts from network outputs: mean + std * pred, X0 added back to the X of every state. */
+/* Starts from network outputs: mean + std * pred, X0 added back to the X of every state; then the
+ * states are replaced by the rollout of the predicted controls from x0 through the tree (level by
+ * level), so that the start satisfies the dynamics like the shifted start does. */
+template <int MODEL>
 __global__ void bmpc_starts_kernel(GlueArgs a) {
-    const int pid = blockIdx.x;
+    constexpr int NX = MODEL == 1 ? 6 : 4;
+    const int pid = a.order_base[blockIdx.x];
     const ProbRec &R = a.recs[pid];
-    const int64_t used = (int64_t)R.n * (2 * R.nx + NU + R.nc);
+    const int n = R.n;
+    const int64_t used = (int64_t)n * (2 * NX + NU + R.nc);
     const float *p = a.pred + (size_t)pid * a.ld_pred;
     float *s = a.out + (size_t)pid * a.stride;
     for (int64_t j = threadIdx.x; j < used; j += blockDim.x) {
         float v = a.mean[j] + a.std[j] * p[j];
-        if (j < (int64_t)R.n * R.nx && j % R.nx == 0) v += R.x0[0];
+        if (j < (int64_t)n * NX && j % NX == 0) v += R.x0[0];
+        if (j >= (int64_t)n * (2 * NX + NU)) v = fmaxf(v, 0.f);   /* AL multipliers are >= 0 */
         s[j] = v;
+    }
+    __syncthreads();
+    const IntOff io = int_off(R.npad, R.n_stage, R.n_paths);
+    const int32_t *ib = a.ibase + R.off_int;
+    const int32_t *parent = ib + io.parent, *nchild = ib + io.nchild, *ss = ib + io.sstart;
+    float *sx = s, *su = s + (size_t)n * NX;
+    if (threadIdx.x < NX) sx[threadIdx.x] = R.x0[threadIdx.x];
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (!nchild[i]) su[(size_t)i * NU] = su[(size_t)i * NU + 1] = 0.f;
+    __syncthreads();
+    for (int st = 1; st < R.n_stage; ++st) {
+        for (int i = ss[st] + threadIdx.x; i < ss[st + 1]; i += blockDim.x) {
+            const int pa = parent[i];
+            float xp[NX], up[NU] = {su[(size_t)pa * NU], su[(size_t)pa * NU + 1]}, dl[NX];
+#pragma unroll
+            for (int j = 0; j < NX; ++j) xp[j] = sx[(size_t)pa * NX + j];
+            dyn<NX, MODEL>(R, xp, up, dl);
+#pragma unroll
+            for (int j = 0; j < NX; ++j) sx[(size_t)i * NX + j] = xp[j] + dl[j];
+        }
+        __syncthreads();
     }
 }
 
-cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream_t stream) {
+cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream_t stream, int model) {
+    if (n_problems <= 0) return cudaSuccess;
     if (which == 0) bmpc_features_kernel<<<n_problems, 256, 0, stream>>>(a);
     else if (which == 1) bmpc_targets_kernel<<<n_problems, 256, 0, stream>>>(a);
-    else bmpc_starts_kernel<<<n_problems, 256, 0, stream>>>(a);
+    else if (model == 0) bmpc_starts_kernel<0><<<n_problems, 256, 0, stream>>>(a);
+    else if (model == 1) bmpc_starts_kernel<1><<<n_problems, 256, 0, stream>>>(a);
+    else bmpc_starts_kernel<2><<<n_problems, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

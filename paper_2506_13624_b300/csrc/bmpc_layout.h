@@ -139,7 +139,8 @@ __host__ __device__ inline ScrRows scr_rows(int nx) {
 /* Kernel-side copy of the solver options (Algorithm 1 constants). */
 struct KOpts {
     int32_t max_iters, max_outer, n_alpha, ls_chunk, variant, warm_select;
-    float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps, select_mu;
+    float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps, select_mu,
+        select_rho;
 };
 
 /* Per-problem statistics, same layout as the public bmpc_stats. */

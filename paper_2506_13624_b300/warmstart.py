@@ -6,8 +6,9 @@ and obstacle, the predicted obstacle position at the middle and the end of the s
 its final heading, positions relative to the ego's X.  Targets: the converged solution
 (states with X relative to the ego, controls, dynamics multipliers, AL multipliers), both
 standardised with statistics of the training set.  At run time the network's start goes into
-warm-start slot 0 and the shifted previous solution into slot 1; the solver starts from the
-network's start only when its merit is not above the shifted start's (bmpc_opts.warm_select).
+warm-start slot 0 and the shifted previous solution (or nothing: the cold start) into slot 1; the
+solver starts from the network's start only when its merit, with a large constraint penalty, is
+not above the fallback's (bmpc_opts.warm_select, select_rho).
 
 Bookkeeping of the data set (concatenation, statistics, shuffling) uses torch tensor ops;
 features, targets, standardisation, the network and the starts run in libbmpc.so.
@@ -113,7 +114,7 @@ def train(net, Xb, Yb, epochs, batch=512, lr=1e-3, weight_decay=1e-4, seed=0, lo
             x = Xb.index_select(0, idx)
             y = Yb.index_select(0, idx)
             lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * k / max(1, steps)))
-            tot += net.train_step(x, y, lr_k, weight_decay)
+            tot += net.train_step(x, y, lr_k, weight_decay)[0]
             k += 1
         hist.append(float(tot) / (n // batch))
         if log:
@@ -147,49 +148,140 @@ def timed_solve(b, opts):
     return res, e0.elapsed_time(e1)
 
 
+def summarise(res, ms):
+    it = np.array([r["inner_iters"] for r in res])
+    conv = np.array([r["status"] == 0 for r in res])
+    return dict(mean_iters=float(it.mean()), median_iters=float(np.median(it)), converged=float(conv.mean()),
+                ms_total=ms, us_per_solve=1e3 * ms / len(res),
+                used_primary=float(np.mean([r["start_used"] == 1 for r in res])))
+
+
 def evaluate(net, stats, make_prev, count, opts=None, seed=0):
-    """Receding-horizon comparison on held-out scenes: solve the previous problems, advance each
-    scene one step, then solve the next problems from the cold start, the shifted previous
-    solution, and the learned start (shifted start as fallback by merit)."""
+    """Two comparisons on held-out scenes.
+
+    First solve (no previous solution): cold start against the learned start alone and against the
+    learned start with the cold start as fallback.  Receding horizon: solve the scenes, advance
+    each one step, then solve the next problems from the cold start, the shifted previous solution,
+    and the learned start with the shifted start as fallback.  Learned times include the network
+    (features, forward pass, starts)."""
     import torch
 
     import scenes
     opts = opts if opts is not None else bmpc.default_opts()
-    prev_ps = make_prev(count)
-    prev = solve_batch(prev_ps, opts)
-    pres = prev.get_solutions()
-    next_ps = [scenes.advance(p, r["x"][1], seed=seed * 100000 + k) for k, (p, r) in enumerate(zip(prev_ps, pres))]
-    out = {}
-    b = bmpc.Batch(next_ps)
-    # cold
-    b.set_problems()
-    b.solve(opts)
-    b.get_solutions(want_arrays=False)
-    b.set_problems()
-    out["cold"] = timed_solve(b, opts)
-    # shifted
-    b.set_problems()
-    b.shift_from(prev, slot=0)
-    out["shifted"] = timed_solve(b, opts)
-    # learned, shifted as fallback
     sel = bmpc.Opts.from_buffer_copy(opts)
     sel.warm_select = 1
+    prev_ps = make_prev(count)
+    prev = bmpc.Batch(prev_ps)
+    first = {}
+
+    def learned(b, fallback):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        learned_starts(net, b, stats)
+        if fallback is not None:
+            b.shift_from(fallback, slot=1)
+        e1.record(b.stream)
+        res, ms = timed_solve(b, sel)
+        torch.cuda.synchronize()
+        return res, ms + e0.elapsed_time(e1)
+
+    prev.set_problems()
+    timed_solve(prev, opts)                       # warm-up of the launch path
+    prev.set_problems()
+    first["cold"] = timed_solve(prev, opts)
+    prev.set_problems()
+    o1 = bmpc.Opts.from_buffer_copy(opts)
+    learned_starts(net, prev, stats)
+    first["learned"] = timed_solve(prev, o1)
+    prev.set_problems()
+    first["learned_or_cold"] = learned(prev, None)
+    prev.set_problems()
+    timed_solve(prev, opts)                       # the previous solutions the next problems shift
+    pres = prev.get_solutions()
+    next_ps = [scenes.advance(p, r["x"][1], seed=seed * 100000 + k) for k, (p, r) in enumerate(zip(prev_ps, pres))]
+    nxt = {}
+    b = bmpc.Batch(next_ps)
     b.set_problems()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(b.stream)
-    learned_starts(net, b, stats)
-    b.shift_from(prev, slot=1)
-    e1.record(b.stream)
-    res, ms = timed_solve(b, sel)
-    torch.cuda.synchronize()
-    out["learned"] = (res, ms + e0.elapsed_time(e1))
+    nxt["cold"] = timed_solve(b, opts)
+    b.set_problems()
+    b.shift_from(prev, slot=0)
+    nxt["shifted"] = timed_solve(b, opts)
+    b.set_problems()
+    nxt["learned_or_shifted"] = learned(b, prev)
     prev.close()
     b.close()
-    summary = {}
-    for k, (res, ms) in out.items():
-        it = np.array([r["inner_iters"] for r in res])
-        conv = np.array([r["status"] == 0 for r in res])
-        summary[k] = dict(mean_iters=float(it.mean()), median_iters=float(np.median(it)),
-                          converged=float(conv.mean()), ms_total=ms, us_per_solve=1e3 * ms / len(res),
-                          used_primary=float(np.mean([r["start_used"] == 1 for r in res])))
-    return summary
+    return dict(first_solve={k: summarise(*v) for k, v in first.items()},
+                receding_horizon={k: summarise(*v) for k, v in nxt.items()})
+
+
+# ------------------------------------------------------------------ command line: the config-5 experiment
+def _gen_chunk(args):
+    import scenes
+    seed, count = args
+    ps = scenes.batch_problems(seed, count)
+    for p in ps:
+        p["obs"] = p["obs"].astype(np.float32)
+    return ps
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import multiprocessing as mp
+
+    ap = argparse.ArgumentParser(description="train and evaluate the learned warm start (config-3 scenes)")
+    ap.add_argument("--train", type=int, default=200000)
+    ap.add_argument("--chunk", type=int, default=4096)
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--hidden", type=int, default=512)
+    ap.add_argument("--eval", type=int, default=2000)
+    ap.add_argument("--train-seed", type=int, default=5)
+    ap.add_argument("--eval-seed", type=int, default=6)
+    ap.add_argument("--workers", type=int, default=12)
+    ap.add_argument("--out", default="")
+    a = ap.parse_args(argv)
+    pool = mp.get_context("spawn").Pool(a.workers)          # started before the first CUDA call
+    import torch
+    import scenes
+
+    def make(c, cnt):
+        per = (cnt + a.workers - 1) // a.workers
+        jobs = [(a.train_seed * 1000003 + c * 64 + w, min(per, cnt - w * per)) for w in range(a.workers)
+                if cnt - w * per > 0]
+        out = []
+        for part in pool.map(_gen_chunk, jobs):
+            out += part
+        return out
+
+    opts = bmpc.default_opts()
+    probe = bmpc.Batch(make(0, 512))
+    probe.set_problems()
+    opts, _ = probe.autotune(opts)
+    probe.close()
+    t0 = time.perf_counter()
+    X, Y, info = build_dataset(make, a.train, a.chunk, opts)
+    info["dataset_s"] = time.perf_counter() - t0
+    Xb, Yb, stats = standardise(X, Y)
+    del X, Y
+    torch.cuda.empty_cache()
+    dims = [Xb.shape[1], a.hidden, a.hidden, a.hidden, Yb.shape[1]]
+    net = mlp.MLP(dims, seed=1)
+    hist, t_train = train(net, Xb, Yb, a.epochs, a.batch, a.lr)
+    flops = 6.0 * a.batch * sum(x * y for x, y in zip(dims[:-1], dims[1:])) * a.epochs * (Xb.shape[0] // a.batch)
+    eval_make = lambda cnt: scenes.batch_problems(a.eval_seed * 1000003, cnt)
+    summary = evaluate(net, stats, eval_make, a.eval, opts)
+    pool.close()
+    res = dict(dataset=info, dims=dims, train_loss=hist, train_s=t_train, train_tflops=flops / t_train / 1e12,
+               eval=summary, opts=dict(block_threads=opts.block_threads, variant=opts.variant,
+                                       ls_chunk=opts.ls_chunk))
+    print(json.dumps(res))
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(res, f, indent=1)
+    return res
+
+
+if __name__ == "__main__":
+    main()
