@@ -20,9 +20,11 @@
 #include "../../include/bmpc_mlp.h"
 
 namespace bmpc {
-cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, cudaStream_t stream);
+cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, size_t smem, cudaStream_t stream);
+size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld);
+cudaError_t prepare_solve(int model, size_t smem);
 int max_block_threads();
-cudaError_t occupancy(int model, int block, int *blocks_per_sm);
+cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
 cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream);
 struct GlueArgs {
@@ -90,6 +92,8 @@ struct bmpc_batch {
     std::vector<int> nodes;
     std::vector<int32_t> parents;        /* all trees' parent arrays, concatenated */
     int model_begin[4] = {0, 0, 0, 0};   /* order[model_begin[m] .. model_begin[m+1]) has model m */
+    int tab_ints[3] = {0, 0, 0};         /* shared-memory stage/path tables per model (0: global) */
+    int max_paths[3] = {0, 0, 0};        /* most scenarios of a tree, per model */
     Layout L{};
     char *data = nullptr;
     float *scr = nullptr;
@@ -237,8 +241,9 @@ void geometry(const bmpc_batch *b, const bmpc_opts &o, int model, int count, int
     if (bt == 0) bt = count == 1 ? 128 : 32;
     int per_sm = o.blocks_per_sm;
     if (per_sm == 0) {
-        int occ = 1;
-        if (occupancy(model, bt, &occ) != cudaSuccess || occ < 1) occ = 1;
+        int occ = 1, ld;
+        const size_t smem = solve_smem(model, b->tab_ints[model], b->max_paths[model], bt, &ld);
+        if (occupancy(model, bt, smem, &occ) != cudaSuccess || occ < 1) occ = 1;
         per_sm = occ;
     }
     *block = bt;
@@ -264,9 +269,11 @@ int launch(bmpc_batch *b, const bmpc_opts &o) {
         a.order = at<const int32_t>(b->data, b->L.order) + b->model_begin[m];
         a.n_problems = cnt;
         a.queue = queue + m;
+        a.tab_ints = b->tab_ints[m];
         int grid, block;
         geometry(b, o, m, cnt, &grid, &block);
-        e = launch_solve(a, m, grid, block, b->stream);
+        const size_t smem = solve_smem(m, b->tab_ints[m], b->max_paths[m], block, &a.stg_ld);
+        e = launch_solve(a, m, grid, block, smem, b->stream);
         if (e != cudaSuccess) return BMPC_ERR_CUDA;
     }
     return BMPC_OK;
@@ -366,6 +373,26 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
     for (int m = 0; m < 4; ++m) b->model_begin[m] = 0;
     for (int k = 0; k < n; ++k) b->model_begin[b->recs[k].model + 1]++;
     for (int m = 0; m < 3; ++m) b->model_begin[m + 1] += b->model_begin[m];
+    /* tables of up to 32 KB per problem go to shared memory (below the 48 KB needing no opt-in) */
+    for (int k = 0; k < n; ++k) {
+        const ProbRec &r = b->recs[k];
+        const int64_t t = table_ints(r.npad, r.n_stage, r.n_paths);
+        b->tab_ints[r.model] = (int)std::max<int64_t>(b->tab_ints[r.model], t);
+        b->max_paths[r.model] = std::max(b->max_paths[r.model], r.n_paths);
+    }
+    for (int m = 0; m < 3; ++m) {
+        if (b->tab_ints[m] > 8192) b->tab_ints[m] = 0;
+        if (b->model_begin[m + 1] == b->model_begin[m]) continue;
+        size_t most = 0;   /* the largest launch over every allowed block size */
+        for (int bt = 32; bt <= max_block_threads(); bt += 32) {
+            int ld;
+            most = std::max(most, solve_smem(m, b->tab_ints[m], b->max_paths[m], bt, &ld));
+        }
+        if (prepare_solve(m, most) != cudaSuccess) {
+            bmpc_destroy_batch(b);
+            return BMPC_ERR_CUDA;
+        }
+    }
     for (int k = 0; k < n; ++k) b->parents.insert(b->parents.end(), descs[k].parent, descs[k].parent + descs[k].num_nodes);
     /* int tables of every tree, packed into the staging buffer and uploaded once */
     int32_t *ib = at<int32_t>(b->stage, b->L.ints);

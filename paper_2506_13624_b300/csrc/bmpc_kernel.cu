@@ -34,6 +34,7 @@
  * threads take the same branches.  Reductions use a fixed order and are
  * bitwise reproducible for a fixed block size.
  */
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -368,6 +369,7 @@ struct View {
     bool box, lane;
     /* int rows */
     const int32_t *parent, *nchild, *fchild, *stage, *leaf, *owner, *sstart, *bstage, *ptab, *pdepth, *ptop;
+    int64_t tab_off;
     /* inputs */
     const float *xref, *w, *obs, *wx, *wu, *wl, *wy;
     /* outputs */
@@ -394,6 +396,7 @@ struct View {
         ptab = ib + io.ptab;
         pdepth = ib + io.pdepth;
         ptop = ib + io.ptop;
+        tab_off = io.sstart;
         const InRows ir = in_rows(NX, nobs);
         xref = fin + (size_t)ir.xref * np;
         w = fin + (size_t)ir.weight * np;
@@ -591,8 +594,14 @@ __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX>
 }
 
 
-/* L1 prefetch of one address (no register is consumed; the line is ready for the next step). */
-__device__ __forceinline__ void pf(const float *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+/* Asynchronous 4-byte copy global -> shared (cp.async, cached in L1) and its group control. */
+__device__ __forceinline__ void cp4(float *dst, const float *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 /* ------------------------------------------------------------------ tree Riccati step */
 /* Terminal value function of a leaf: P = Q_N + penalty Hessian, p = q (stored and returned). */
@@ -644,27 +653,59 @@ __device__ __forceinline__ void add_child_mem(const View<NX> &V, int m, float (&
     }
 }
 
+/* Inputs of the Riccati step at a node: Jacobians (with the constant position columns), cost
+ * gradient q, r and the diagonal/penalty Hessian terms. */
+template <int NX>
+struct RicIn {
+    float A[NX][NX], B[NX][NU], q[NX], r[NU], hq[3], hr[NU], w;
+};
+
+template <int NX, int MODEL>
+__device__ __forceinline__ void ric_load(const View<NX> &V, int i, RicIn<NX> &in) {
+    const int np = V.np;
+    in.w = V.w[i];
+    V.load_x(V.q, i, in.q);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) in.hq[a] = V.hq[(size_t)a * np + i];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+        for (int b = 0; b < NX; ++b) in.A[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
+#pragma unroll
+        for (int b = 0; b < NU; ++b) in.B[a][b] = V.B[(size_t)(a * NU + b) * np + i];
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        in.r[a] = V.r[(size_t)a * np + i];
+        in.hr[a] = V.hr[(size_t)a * np + i];
+    }
+}
+
+/* Staging of the per-path forward sweep: each path thread streams the rows of the nodes it visits
+ * next into its own shared-memory slots (SWEEP_DEPTH buffers filled by cp.async), so that the loads
+ * of the next stages overlap the arithmetic of the current one.  Slot (buffer, row, thread) lives
+ * at stg[(buffer * rows + row) * ld + thread].  (The backward sweep loads directly: its Riccati
+ * step is long enough that staging did not pay for its extra instructions.) */
+constexpr int SWEEP_DEPTH = 3;
+template <int MODEL>
+__host__ __device__ constexpr int a_first() { return MODEL == 2 ? 0 : 2; }   /* first stored column of A */
+template <int NX, int MODEL>
+__host__ __device__ constexpr int rows_stage() { return NX + NX * (NX - a_first<MODEL>()) + 2 * NX * NU + NU; }
+
 /* Riccati step of a non-leaf node n from the summed child value functions (Pb, pb):
  * H_n = R_n + B'Pb B, K_n = -H^-1 (M_n + B'Pb A), k_n = -H^-1 (r_n + B'pb) of
  * Eq. (tree_feedback_laws) (M_n = 0 here: no constraint couples x and u), then
  * P_n = Q_n + A'Pb A + Qux'K, p_n = q_n + A'pb + Qux'k.  Stores K, k, P, p; returns P, p. */
 template <int NX, int MODEL>
-__device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V, int i, const float (&Pb)[nsym(NX)],
-                                             const float (&pb)[NX], float (&P)[nsym(NX)], float (&p)[NX],
-                                             Shared &sh) {
+__device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V, int i, const RicIn<NX> &in,
+                                             const float (&Pb)[nsym(NX)], const float (&pb)[NX],
+                                             float (&P)[nsym(NX)], float (&p)[NX], Shared &sh) {
     const int np = V.np;
-    const float w = V.w[i];
-    float q[NX];
-    V.load_x(V.q, i, q);
-    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
-    float A[NX][NX], B[NX][NU];
-#pragma unroll
-    for (int a = 0; a < NX; ++a) {
-#pragma unroll
-        for (int b = 0; b < NX; ++b) A[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
-#pragma unroll
-        for (int b = 0; b < NU; ++b) B[a][b] = V.B[(size_t)(a * NU + b) * np + i];
-    }
+    const float w = in.w;
+    const float(&q)[NX] = in.q;
+    const float hxx = in.hq[0], hxy = in.hq[1], hyy = in.hq[2];
+    const float(&A)[NX][NX] = in.A;
+    const float(&B)[NX][NU] = in.B;
     /* PA = Pbar A, PB = Pbar B */
     float PA[NX][NX], PB[NX][NU];
 #pragma unroll
@@ -690,7 +731,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
     for (int a = 0; a < NU; ++a) {
 #pragma unroll
         for (int b = 0; b < NU; ++b) {
-            float v = (a == b) ? w * R.Rw[a] + V.hr[(size_t)a * np + i] : 0.f;
+            float v = (a == b) ? w * R.Rw[a] + in.hr[a] : 0.f;
 #pragma unroll
             for (int t = 0; t < NX; ++t) v += B[t][a] * PB[t][b];
             Quu[a][b] = v;
@@ -702,7 +743,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
             for (int t = 0; t < NX; ++t) v += B[t][a] * PA[t][b];
             Qux[a][b] = v;
         }
-        float v = V.r[(size_t)a * np + i];
+        float v = in.r[a];
 #pragma unroll
         for (int t = 0; t < NX; ++t) v += B[t][a] * pb[t];
         qu[a] = v;
@@ -717,19 +758,20 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
     /* Cholesky of the 2x2 H_n, K = -H^-1 Qux, k = -H^-1 qu */
     const float l00s = Quu[0][0];
     const float l00 = sqrtf(fmaxf(l00s, 0.f));
-    const float l10 = Quu[1][0] / l00;
+    const float i00 = 1.f / l00;
+    const float l10 = Quu[1][0] * i00;
     const float l11s = Quu[1][1] - l10 * l10;
     if (!(l00s > 0.f) || !(l11s > 0.f)) sh.flag = 1;
-    const float l11 = sqrtf(fmaxf(l11s, 0.f));
+    const float i11 = 1.f / sqrtf(fmaxf(l11s, 0.f));
     float Kn[NU][NX], kn[NU];
 #pragma unroll
     for (int b = 0; b < NX + 1; ++b) {
         const float rhs0 = (b < NX) ? Qux[0][b] : qu[0];
         const float rhs1 = (b < NX) ? Qux[1][b] : qu[1];
-        const float z0 = rhs0 / l00;
-        const float z1 = (rhs1 - l10 * z0) / l11;
-        const float s1 = z1 / l11;
-        const float s0 = (z0 - l10 * s1) / l00;
+        const float z0 = rhs0 * i00;
+        const float z1 = (rhs1 - l10 * z0) * i11;
+        const float s1 = z1 * i11;
+        const float s0 = (z0 - l10 * s1) * i00;
         if (b < NX) {
             Kn[0][b] = -s0;
             Kn[1][b] = -s1;
@@ -770,29 +812,6 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
     }
 }
 
-/* Prefetch the rows a backward step at node i (child c on the path) reads. */
-template <int NX, int MODEL>
-__device__ __forceinline__ void prefetch_backward(const View<NX> &V, int i, int c) {
-    const int np = V.np;
-#pragma unroll
-    for (int a = 0; a < NX; ++a) {
-        pf(V.d + (size_t)a * np + c);
-        pf(V.q + (size_t)a * np + i);
-#pragma unroll
-        for (int b = (MODEL == 2 ? 0 : 2); b < NX; ++b) pf(V.A + (size_t)(a * NX + b) * np + i);
-#pragma unroll
-        for (int b = 0; b < NU; ++b) pf(V.B + (size_t)(a * NU + b) * np + i);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) pf(V.hq + (size_t)a * np + i);
-#pragma unroll
-    for (int a = 0; a < NU; ++a) {
-        pf(V.hr + (size_t)a * np + i);
-        pf(V.r + (size_t)a * np + i);
-    }
-    pf(V.w + i);
-}
-
 /* Level-synchronous backward sweep: all nodes of a stage in parallel, one barrier per stage. */
 template <int NX, int MODEL>
 __device__ void backward_level(const ProbRec &R, const View<NX> &V, Shared &sh) {
@@ -813,7 +832,9 @@ __device__ void backward_level(const ProbRec &R, const View<NX> &V, Shared &sh) 
 #pragma unroll
             for (int a = 0; a < NX; ++a) pb[a] = 0.f;
             for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
-            riccati_node<NX, MODEL>(R, V, i, Pb, pb, P, p, sh);
+            RicIn<NX> in;
+            ric_load<NX, MODEL>(V, i, in);
+            riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
         }
         __syncthreads();
     }
@@ -851,14 +872,17 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
                     for (int a = 0; a < NX; ++a) pb[a] = 0.f;
                     const int fc = V.fchild[i];
                     for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
-                    riccati_node<NX, MODEL>(R, V, i, Pb, pb, P, p, sh);
+                    RicIn<NX> in;
+                    ric_load<NX, MODEL>(V, i, in);
+                    riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
                 }
             }
             for (k = khi - 1; k >= klo; --k) {
-                const int i = path[k], c = path[k + 1];   /* single child c, its value function in P, p */
-                if (k > klo) prefetch_backward<NX, MODEL>(V, path[k - 1], i);
+                const int i = path[k];   /* single child path[k+1], its value function in P, p */
                 float dm[NX], Pb[NS], pb[NX];
-                V.load_x(V.d, c, dm);
+                RicIn<NX> in;
+                V.load_x(V.d, path[k + 1], dm);
+                ric_load<NX, MODEL>(V, i, in);
 #pragma unroll
                 for (int e = 0; e < NS; ++e) Pb[e] = 0.f + P[e];
 #pragma unroll
@@ -868,63 +892,108 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
                     for (int b = 0; b < NX; ++b) v += P[sidx<NX>(a, b)] * dm[b];
                     pb[a] = 0.f + v;
                 }
-                riccati_node<NX, MODEL>(R, V, i, Pb, pb, P, p, sh);
+                riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
             }
+
         }
         hi = lo;
         __syncthreads();
     }
 }
 
-/* Prefetch the rows a forward step at node i (with parent pa) reads. */
+/* Inputs of the forward step at node i: its defect, the parent's Jacobians and its gains. */
+template <int NX>
+struct FwdIn {
+    float d[NX], A[NX][NX], B[NX][NU], K[NU][NX], k[NU];
+};
+
 template <int NX, int MODEL>
-__device__ __forceinline__ void prefetch_forward(const View<NX> &V, int i, int pa) {
+__device__ __forceinline__ void fwd_load(const View<NX> &V, int i, int pa, FwdIn<NX> &in) {
     const int np = V.np;
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
-        pf(V.d + (size_t)a * np + i);
+        in.d[a] = V.d[(size_t)a * np + i];
 #pragma unroll
-        for (int b = (MODEL == 2 ? 0 : 2); b < NX; ++b) pf(V.A + (size_t)(a * NX + b) * np + pa);
+        for (int b = 0; b < NX; ++b) in.A[a][b] = aload<NX, MODEL>(V.A, np, pa, a, b);
 #pragma unroll
-        for (int b = 0; b < NU; ++b) pf(V.B + (size_t)(a * NU + b) * np + pa);
+        for (int b = 0; b < NU; ++b) in.B[a][b] = V.B[(size_t)(a * NU + b) * np + pa];
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
-        pf(V.k + (size_t)a * np + i);
+        in.k[a] = V.k[(size_t)a * np + i];
 #pragma unroll
-        for (int b = 0; b < NX; ++b) pf(V.K + (size_t)(a * NX + b) * np + i);
+        for (int b = 0; b < NX; ++b) in.K[a][b] = V.K[(size_t)(a * NX + b) * np + i];
     }
 }
 
-/* Forward rollout at node i given the parent's (dx, du): dx_i = A_p dx_p + B_p du_p + d_i,
- * du_i = K_i dx_i + k_i (stored when `own`). */
 template <int NX, int MODEL>
-__device__ __forceinline__ void forward_node(const View<NX> &V, int i, const float (&dxp)[NX], const float (&dup)[NU],
-                                             float (&dxv)[NX], float (&duv)[NU], bool own) {
+__device__ __forceinline__ void fwd_issue(const View<NX> &V, int i, int pa, float *slot, int ld) {
     const int np = V.np;
-    const int nch = V.nchild[i];
-    if (i == 0) {
+    int j = 0;
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        cp4(slot + (j++) * ld, V.d + (size_t)a * np + i);
+#pragma unroll
+        for (int b = a_first<MODEL>(); b < NX; ++b) cp4(slot + (j++) * ld, V.A + (size_t)(a * NX + b) * np + pa);
+#pragma unroll
+        for (int b = 0; b < NU; ++b) cp4(slot + (j++) * ld, V.B + (size_t)(a * NU + b) * np + pa);
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        cp4(slot + (j++) * ld, V.k + (size_t)a * np + i);
+#pragma unroll
+        for (int b = 0; b < NX; ++b) cp4(slot + (j++) * ld, V.K + (size_t)(a * NX + b) * np + i);
+    }
+}
+
+template <int NX, int MODEL>
+__device__ __forceinline__ void fwd_read(const float *slot, int ld, FwdIn<NX> &in) {
+    int j = 0;
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        in.d[a] = slot[(j++) * ld];
+#pragma unroll
+        for (int b = 0; b < a_first<MODEL>(); ++b) in.A[a][b] = a == b ? 1.f : 0.f;
+#pragma unroll
+        for (int b = a_first<MODEL>(); b < NX; ++b) in.A[a][b] = slot[(j++) * ld];
+#pragma unroll
+        for (int b = 0; b < NU; ++b) in.B[a][b] = slot[(j++) * ld];
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        in.k[a] = slot[(j++) * ld];
+#pragma unroll
+        for (int b = 0; b < NX; ++b) in.K[a][b] = slot[(j++) * ld];
+    }
+}
+
+/* Forward rollout at node i (parent pa, -1 at the root) given the parent's (dx, du):
+ * dx_i = A_p dx_p + B_p du_p + d_i, du_i = K_i dx_i + k_i at non-leaves (stored when `own`). */
+template <int NX, int MODEL>
+__device__ __forceinline__ void forward_node(const View<NX> &V, int i, int pa, bool nonleaf, const FwdIn<NX> &in,
+                                             const float (&dxp)[NX], const float (&dup)[NU], float (&dxv)[NX],
+                                             float (&duv)[NU], bool own) {
+    if (pa < 0) {
 #pragma unroll
         for (int j = 0; j < NX; ++j) dxv[j] = 0.f;
     } else {
-        const int pa = V.parent[i];
 #pragma unroll
         for (int a = 0; a < NX; ++a) {
-            float v = V.d[(size_t)a * np + i];
+            float v = in.d[a];
 #pragma unroll
-            for (int b = 0; b < NX; ++b) v += aload<NX, MODEL>(V.A, np, pa, a, b) * dxp[b];
+            for (int b = 0; b < NX; ++b) v += in.A[a][b] * dxp[b];
 #pragma unroll
-            for (int b = 0; b < NU; ++b) v += V.B[(size_t)(a * NU + b) * np + pa] * dup[b];
+            for (int b = 0; b < NU; ++b) v += in.B[a][b] * dup[b];
             dxv[a] = v;
         }
     }
     duv[0] = duv[1] = 0.f;
-    if (nch) {
+    if (nonleaf) {
 #pragma unroll
         for (int a = 0; a < NU; ++a) {
-            float v = V.k[(size_t)a * np + i];
+            float v = in.k[a];
 #pragma unroll
-            for (int b = 0; b < NX; ++b) v += V.K[(size_t)(a * NX + b) * np + i] * dxv[b];
+            for (int b = 0; b < NX; ++b) v += in.K[a][b] * dxv[b];
             duv[a] = v;
         }
     }
@@ -984,11 +1053,14 @@ __device__ void forward_level(const ProbRec &R, const View<NX> &V) {
             float dxp[NX], dup[NU] = {0.f, 0.f}, dxv[NX], duv[NU];
 #pragma unroll
             for (int j = 0; j < NX; ++j) dxp[j] = 0.f;
-            if (i != 0) {
-                V.load_x(V.dx, V.parent[i], dxp);
-                V.load_u(V.du, V.parent[i], dup);
+            const int pa = i ? V.parent[i] : -1;
+            if (pa >= 0) {
+                V.load_x(V.dx, pa, dxp);
+                V.load_u(V.du, pa, dup);
             }
-            forward_node<NX, MODEL>(V, i, dxp, dup, dxv, duv, true);
+            FwdIn<NX> in;
+            fwd_load<NX, MODEL>(V, i, pa < 0 ? 0 : pa, in);
+            forward_node<NX, MODEL>(V, i, pa, V.nchild[i] != 0, in, dxp, dup, dxv, duv, true);
         }
         __syncthreads();
     }
@@ -996,9 +1068,10 @@ __device__ void forward_level(const ProbRec &R, const View<NX> &V) {
 
 /* Per-scenario-path forward sweep: path s rolls out from the root to its leaf with (dx, du) in
  * registers and no barrier; nodes shared by several paths are recomputed identically by each
- * and written only by their owner path.  The next node's rows are prefetched into L1. */
+ * and written only by their owner path.  The rows of the next nodes are streamed into shared
+ * memory ahead of use (cp.async). */
 template <int NX, int MODEL>
-__device__ void forward_path(const ProbRec &R, const View<NX> &V) {
+__device__ void forward_path(const ProbRec &R, const View<NX> &V, float *stg, int ld) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int S = R.n_paths, ns = R.n_stage;
     for (int s = tid; s < S; s += nt) {
@@ -1007,10 +1080,33 @@ __device__ void forward_path(const ProbRec &R, const View<NX> &V) {
         float dxp[NX], dup[NU] = {0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < NX; ++j) dxp[j] = 0.f;
+        const int nst = depth + 1;
+        float *slot = stg + tid;
+        const int bs = rows_stage<NX, MODEL>() * ld;
+        if (stg) {
+#pragma unroll
+            for (int q = 0; q < SWEEP_DEPTH - 1; ++q) {
+                if (q < nst) fwd_issue<NX, MODEL>(V, path[q], q ? path[q - 1] : 0, slot + q * bs, ld);
+                cp_commit();
+            }
+        }
+        int pa = -1;
         for (int k = 0; k <= depth; ++k) {
-            if (k < depth) prefetch_forward<NX, MODEL>(V, path[k + 1], path[k]);
+            const int i = path[k];
+            FwdIn<NX> in;
+            if (stg) {
+                const int q = k + SWEEP_DEPTH - 1;
+                if (q < nst) fwd_issue<NX, MODEL>(V, path[q], path[q - 1], slot + (q % SWEEP_DEPTH) * bs, ld);
+                cp_commit();
+                cp_wait<SWEEP_DEPTH - 1>();
+                fwd_read<NX, MODEL>(slot + (k % SWEEP_DEPTH) * bs, ld, in);
+            } else {
+                fwd_load<NX, MODEL>(V, i, pa < 0 ? 0 : pa, in);
+            }
             float dxv[NX], duv[NU];
-            forward_node<NX, MODEL>(V, path[k], dxp, dup, dxv, duv, k >= top);
+            forward_node<NX, MODEL>(V, i, pa, k < depth, in, dxp, dup, dxv, duv, k >= top);
+            pa = i;
+
 #pragma unroll
             for (int j = 0; j < NX; ++j) dxp[j] = dxv[j];
             dup[0] = duv[0];
@@ -1227,7 +1323,6 @@ __device__ void backward_coop(const ProbRec &R, const View<NX> &V, Shared &sh) {
             }
             for (int k = khi - 1; k >= klo; --k) {
                 const int i = path[k], c = path[k + 1];
-                if (k > klo && lane == 0) prefetch_backward<NX, MODEL>(V, path[k - 1], i);
                 float pb[NX];
                 coop_pbar<NX>(V, c, Pc, p, pb, lane, gmask);
                 float Pbc[NX];
@@ -1258,7 +1353,6 @@ __device__ void forward_coop(const ProbRec &R, const View<NX> &V) {
         for (int j = 0; j < NX; ++j) dx[j] = 0.f;
         for (int k = 0; k <= depth; ++k) {
             const int i = path[k];
-            if (k < depth && lane == 0) prefetch_forward<NX, MODEL>(V, path[k + 1], i);
             if (i != 0) {
                 const int pa = path[k - 1];
                 float v = V.d[(size_t)la * np + i];
@@ -1370,9 +1464,22 @@ __device__ float start_merit(const ProbRec &R, const View<NX> &V, float rho, flo
 /* ------------------------------------------------------------------ the per-problem solver */
 template <int NX, int MODEL>
 __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
-                              float *fs, Stats *stat, const KOpts &O, Shared &sh) {
+                              float *fs, Stats *stat, const KOpts &O, Shared &sh, int32_t *tab, int tab_cap,
+                              float *stg, int stg_ld) {
     constexpr int NS = nsym(NX);
     View<NX> V(R, ib, fin, fw, fout, fs);
+    /* stage and path tables into shared memory: the sweeps index through them at every stage */
+    const int64_t tn = table_ints(R.npad, R.n_stage, R.n_paths);
+    if (tn <= tab_cap) {
+        const int32_t *src = ib + V.tab_off;
+        for (int j = threadIdx.x; j < tn; j += blockDim.x) tab[j] = src[j];
+        V.sstart = tab + (V.sstart - src);
+        V.bstage = tab + (V.bstage - src);
+        V.ptab = tab + (V.ptab - src);
+        V.pdepth = tab + (V.pdepth - src);
+        V.ptop = tab + (V.ptop - src);
+        __syncthreads();
+    }
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n = V.n, np = V.np, nc = V.nc;
     long long t_start = clock64(), c_lin = 0, c_bwd = 0, c_fwd = 0, c_ls = 0;
@@ -1515,7 +1622,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             t0 = clock64();
             float dir[3] = {0.f, 0.f, 0.f};   /* grad'dz, dz'W dz, (dlam - lam)'d */
             if (variant == 3) forward_coop<NX, MODEL>(R, V);
-            else if (variant == 2) forward_path<NX, MODEL>(R, V);
+            else if (variant == 2) forward_path<NX, MODEL>(R, V, stg, stg_ld);
             else forward_level<NX, MODEL>(R, V);
             multipliers_and_directions<NX, MODEL>(R, V, dir);
             block_sum<3>(dir, sh);
@@ -1704,6 +1811,8 @@ __global__ void __launch_bounds__(MAX_BLOCK, BMPC_MIN_BLOCKS) bmpc_solve_kernel(
     constexpr int NX = MODEL == 1 ? 6 : 4;
     __shared__ Shared sh;
     __shared__ int pid_s;
+    extern __shared__ int32_t tab_s[];
+    float *stg = reinterpret_cast<float *>(tab_s + ((args.tab_ints + 3) & ~3));
     for (;;) {
         if (threadIdx.x == 0) pid_s = atomicAdd(args.queue, 1);
         __syncthreads();
@@ -1713,7 +1822,8 @@ __global__ void __launch_bounds__(MAX_BLOCK, BMPC_MIN_BLOCKS) bmpc_solve_kernel(
         const int pid = args.order[slot];
         const ProbRec &R = args.recs[pid];
         solve_problem<NX, MODEL>(R, args.ibase + R.off_int, args.inbase + R.off_in, args.warmbase + R.off_warm,
-                                 args.outbase + R.off_out, args.scr + R.off_scr, args.stats + pid, args.opts, sh);
+                                 args.outbase + R.off_out, args.scr + R.off_scr, args.stats + pid, args.opts, sh,
+                                 tab_s, args.tab_ints, args.stg_ld ? stg : nullptr, args.stg_ld);
     }
 }
 
@@ -1926,19 +2036,47 @@ cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream
 }
 
 /* Launch helper used by the host API: `args.order` lists problems of `model` only. */
-cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, cudaStream_t stream) {
-    if (model == 0) bmpc_solve_kernel<0><<<grid, block, 0, stream>>>(args);
-    else if (model == 1) bmpc_solve_kernel<1><<<grid, block, 0, stream>>>(args);
-    else bmpc_solve_kernel<2><<<grid, block, 0, stream>>>(args);
+cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, size_t smem, cudaStream_t stream) {
+    if (model == 0) bmpc_solve_kernel<0><<<grid, block, smem, stream>>>(args);
+    else if (model == 1) bmpc_solve_kernel<1><<<grid, block, smem, stream>>>(args);
+    else bmpc_solve_kernel<2><<<grid, block, smem, stream>>>(args);
     return cudaGetLastError();
 }
 
 int max_block_threads() { return MAX_BLOCK; }
 
-cudaError_t occupancy(int model, int block, int *blocks_per_sm) {
-    if (model == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<0>, block, 0);
-    if (model == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<1>, block, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<2>, block, 0);
+/* Dynamic shared memory of a solve launch: the stage/path tables (tab_ints) and, when it fits in
+ * 96 KB, the sweep staging of min(max_paths, block) path threads (*stg_ld, else 0). */
+size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld) {
+    const int rows = model == 0 ? rows_stage<4, 0>() : model == 1 ? rows_stage<6, 1>() : rows_stage<4, 2>();
+    const int ld = std::min(max_paths, block);
+    const size_t tab = sizeof(int32_t) * (size_t)((tab_ints + 3) & ~3);
+    const size_t stg = sizeof(float) * (size_t)SWEEP_DEPTH * rows * ld;
+    if (ld > 0 && tab + stg <= 96u * 1024u) {
+        *stg_ld = ld;
+        return tab + stg;
+    }
+    *stg_ld = 0;
+    return sizeof(int32_t) * (size_t)tab_ints;
+}
+
+/* Raises the dynamic shared-memory limit of a model's kernel to at least `smem` (never lowers it,
+ * so batches sharing the process keep theirs). */
+cudaError_t prepare_solve(int model, size_t smem) {
+    static size_t granted[3] = {48u * 1024u, 48u * 1024u, 48u * 1024u};
+    if (model < 0 || model > 2 || smem <= granted[model]) return cudaSuccess;
+    cudaError_t e;
+    if (model == 0) e = cudaFuncSetAttribute(bmpc_solve_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (model == 1) e = cudaFuncSetAttribute(bmpc_solve_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else e = cudaFuncSetAttribute(bmpc_solve_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) granted[model] = smem;
+    return e;
+}
+
+cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm) {
+    if (model == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<0>, block, smem);
+    if (model == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<1>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<2>, block, smem);
 }
 
 }  // namespace bmpc

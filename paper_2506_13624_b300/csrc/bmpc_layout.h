@@ -67,6 +67,13 @@ __host__ __device__ inline IntOff int_off(int npad, int n_stage, int n_paths) {
     return o;
 }
 
+/* The stage and path tables (sstart .. ptop) are contiguous: the solver copies them into shared
+ * memory per problem when they fit. */
+__host__ __device__ inline int64_t table_ints(int npad, int n_stage, int n_paths) {
+    const IntOff o = int_off(npad, n_stage, n_paths);
+    return o.total - o.sstart;
+}
+
 /* input region: xref[nx] weight[1] obs[5*n_obs] (rows of npad) */
 struct InRows {
     int xref, weight, obs, total;
@@ -174,6 +181,8 @@ struct KernelArgs {
     float *scr;
     Stats *stats;
     KOpts opts;
+    int32_t tab_ints;         /* dynamic shared memory for the stage/path tables, in ints (0: none) */
+    int32_t stg_ld;           /* path threads with sweep staging slots after the tables (0: no staging) */
 };
 
 }  // namespace bmpc
