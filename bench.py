@@ -215,7 +215,7 @@ def run_gpu(args):
     b = bmpc.Batch(problems, stream=stream)
     b.set_problems()
     opts = bmpc.default_opts(block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm,
-                             ls_chunk=args.ls_chunk, variant=args.variant)
+                             ls_chunk=args.ls_chunk, variant=args.variant, queue_order=args.queue_order)
     if args.max_iters > 0:
         opts.max_iters = args.max_iters
     tuned = None
@@ -274,6 +274,7 @@ def run_gpu(args):
     total_conv = float(nconv_all.item())
     value = total_conv / (ms / 1e3)
     flops = algorithmic_flops(problems, res)
+    n_models = len({int(p["model"]) for p in problems})   # one solve (+ one queue-order) kernel per model
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / (ms / 1e3) / 1e12
     iters = np.array([r["inner_iters"] for r in res])
@@ -295,13 +296,15 @@ def run_gpu(args):
                    "l2": f"working set {(b.data_bytes + b.scratch_bytes) / 1e9:.2f} GB > 126 MB L2, no flush",
                    "launch": "one persistent kernel per model per step, CUDA graph replay",
                    "opts": {"block_threads": opts.block_threads, "variant": opts.variant, "ls_chunk": opts.ls_chunk,
-                            "max_iters": opts.max_iters, "autotuned": tuned is not None}},
+                            "max_iters": opts.max_iters, "autotuned": tuned is not None,
+                            "queue_order": "longest predicted first (previous step's iterations)"
+                            if opts.queue_order == 1 else "largest tree first"}},
         "converged_fraction": float(conv.mean()),
         "tree_riccati_us_per_iter": ric_us_iter,
         "phase_us_per_iter": phases,
         "solve_latency_us": {"mean": float(tot_us.mean()), "max": float(tot_us.max())},
         "inner_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * n_models * (2 if opts.queue_order == 1 else 1),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"},
@@ -328,6 +331,7 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--ls-chunk", type=int, default=2)
     ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--queue-order", type=int, default=1, choices=[0, 1])
     ap.add_argument("--max-iters", type=int, default=0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=3)

@@ -122,6 +122,11 @@ typedef struct {
     float select_mu;        /* defect penalty mu of the merit used by warm_select, default 100 */
     float select_rho;       /* constraint penalty rho of the merit used by warm_select, default 1e4: a start
                                that cuts through a keep-out region loses to one that does not */
+    int32_t queue_order;    /* order in which the persistent blocks take problems: 1 (default) longest
+                               predicted first, the prediction being nodes x (inner iterations of the
+                               problem's previous solve in this batch + 1), sorted on the device before
+                               each launch (so also inside a captured graph); 0 largest tree first.
+                               The solutions do not depend on it. */
 } bmpc_opts;
 
 typedef struct {
@@ -193,6 +198,11 @@ int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, 
  * deviation x - xref of every node from its reference (the solver's coordinates). */
 int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float **u, float **lam, float **y,
                                 int32_t *npad);
+
+/* Copies the work-queue order of the last solve to `order` (host, caller-allocated, n_problems
+ * ints): problem ids grouped by model, in the order the persistent blocks took them.  Waits for
+ * the batch's stream.  BMPC_ERR_INVALID on a null argument. */
+int bmpc_get_queue_order(const bmpc_batch *b, int32_t *order);
 
 void bmpc_destroy_batch(bmpc_batch *b);
 

@@ -45,7 +45,7 @@ class Opts(C.Structure):
                 ("rho0", C.c_float), ("rho_max", C.c_float), ("mu0", C.c_float), ("beta", C.c_float),
                 ("ls_rel_eps", C.c_float), ("ls_chunk", C.c_int32), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("variant", C.c_int32), ("warm_select", C.c_int32),
-                ("select_mu", C.c_float), ("select_rho", C.c_float)]
+                ("select_mu", C.c_float), ("select_rho", C.c_float), ("queue_order", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -86,6 +86,7 @@ def lib() -> C.CDLL:
         L.bmpc_problem_device_outputs.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
                                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                                   C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]
+        L.bmpc_get_queue_order.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -94,7 +95,7 @@ EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_
             "bmpc_solve_batch_graph", "bmpc_get_solutions", "bmpc_problem_device_outputs", "bmpc_destroy_batch",
             "bmpc_tree_bytes", "bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution",
             "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune",
-            "bmpc_set_warm_start_device", "bmpc_shift_warm_start"]
+            "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -246,6 +247,14 @@ class Batch:
         with self.torch.cuda.device(self.device):
             _check(lib().bmpc_autotune(self.handle, C.byref(o), C.byref(best), C.byref(us)), "bmpc_autotune")
         return best, us.value
+
+    def device_order(self):
+        """The queue order of the last solve (problem ids, grouped by model)."""
+        out = np.zeros(self.n, np.int32)
+        with self.torch.cuda.device(self.device):
+            _check(lib().bmpc_get_queue_order(self.handle, out.ctypes.data_as(C.POINTER(C.c_int32))),
+                   "bmpc_get_queue_order")
+        return out
 
     def get_solutions(self, want_arrays: bool = True):
         """Synchronise and return per-problem dicts with x, u, lam, y and the solver statistics."""

@@ -23,6 +23,7 @@ namespace bmpc {
 cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, size_t smem, cudaStream_t stream);
 size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld);
 cudaError_t prepare_solve(int model, size_t smem);
+cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order, int cnt, cudaStream_t stream);
 int max_block_threads();
 cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
@@ -224,6 +225,7 @@ int check_opts(const bmpc_opts &o) {
     if (o.variant < 0 || o.variant > 3) return BMPC_ERR_INVALID;
     if (o.warm_select < 0 || o.warm_select > 1 || !(o.select_mu >= 0.f) ||
         !(o.select_rho > 0.f)) return BMPC_ERR_INVALID;
+    if (o.queue_order < 0 || o.queue_order > 1) return BMPC_ERR_INVALID;
     if ((o.variant == 0 || o.variant == 3) && o.block_threads != 0 && o.block_threads % 32) return BMPC_ERR_INVALID;
     return BMPC_OK;
 }
@@ -266,7 +268,10 @@ int launch(bmpc_batch *b, const bmpc_opts &o) {
     for (int m = 0; m < 3; ++m) {
         const int cnt = b->model_begin[m + 1] - b->model_begin[m];
         if (cnt == 0) continue;
-        a.order = at<const int32_t>(b->data, b->L.order) + b->model_begin[m];
+        int32_t *ord = at<int32_t>(b->data, b->L.order) + b->model_begin[m];
+        if (o.queue_order == 1 && launch_order(a.recs, a.stats, ord, cnt, b->stream) != cudaSuccess)
+            return BMPC_ERR_CUDA;
+        a.order = ord;
         a.n_problems = cnt;
         a.queue = queue + m;
         a.tab_ints = b->tab_ints[m];
@@ -309,6 +314,7 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->warm_select = 0;
     o->select_mu = 100.f;
     o->select_rho = 1e4f;
+    o->queue_order = 1;
 }
 
 int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
@@ -454,6 +460,7 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->data + b->L.ints, b->stage + b->L.ints, sizeof(int32_t) * b->L.ints_n,
                             cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->data + b->L.stats, 0, sizeof(Stats) * n, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         bmpc_destroy_batch(b);
@@ -828,6 +835,15 @@ int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float
     if (lam) *lam = base + (size_t)orw.lam * R.npad;
     if (y) *y = base + (size_t)orw.y * R.npad;
     if (npad) *npad = R.npad;
+    return BMPC_OK;
+}
+
+int bmpc_get_queue_order(const bmpc_batch *b, int32_t *order) {
+    if (!b || !order) return BMPC_ERR_INVALID;
+    if (cudaMemcpyAsync(order, b->data + b->L.order, sizeof(int32_t) * b->n, cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return BMPC_ERR_CUDA;
     return BMPC_OK;
 }
 

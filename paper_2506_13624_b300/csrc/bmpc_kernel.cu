@@ -1828,6 +1828,54 @@ __global__ void __launch_bounds__(MAX_BLOCK, BMPC_MIN_BLOCKS) bmpc_solve_kernel(
 }
 
 
+/* ------------------------------------------------------------------ work-queue order */
+/* Longest-predicted-first order of the problems of one model (list scheduling of the persistent
+ * blocks): the key is nodes x (previous inner iterations + 1), ties broken by problem id, so the
+ * order is deterministic.  One block sorts a tile of ORDER_TILE entries of `order` in place
+ * (bitonic sort in shared memory); batches longer than a tile are ordered tile by tile. */
+constexpr int ORDER_TILE = 4096;
+
+__global__ void __launch_bounds__(1024) bmpc_order_kernel(const ProbRec *recs, const Stats *stats, int32_t *order,
+                                                          int cnt) {
+    __shared__ unsigned long long key[ORDER_TILE];
+    const int base = blockIdx.x * ORDER_TILE;
+    const int m = min(ORDER_TILE, cnt - base);
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        unsigned long long k = ~0ull;
+        if (j < m) {
+            const int pid = order[base + j];
+            const int it = min(max(stats[pid].inner_iters, 0), 1 << 16);
+            unsigned long long cost = (unsigned long long)recs[pid].n * (unsigned long long)(it + 1);
+            if (cost > 0xFFFFFFFFull) cost = 0xFFFFFFFFull;
+            k = ((0xFFFFFFFFull - cost) << 32) | (unsigned)pid;
+        }
+        key[j] = k;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int j = threadIdx.x; j < P / 2; j += blockDim.x) {
+                const int lo = 2 * j - (j & (stride - 1)), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = key[lo], b = key[hi];
+                if ((a > b) == up) {
+                    key[lo] = b;
+                    key[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    for (int j = threadIdx.x; j < m; j += blockDim.x) order[base + j] = (int32_t)(key[j] & 0xFFFFFFFFull);
+}
+
+cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order, int cnt, cudaStream_t stream) {
+    if (cnt <= 1) return cudaSuccess;
+    bmpc_order_kernel<<<(cnt + ORDER_TILE - 1) / ORDER_TILE, 1024, 0, stream>>>(recs, stats, order, cnt);
+    return cudaGetLastError();
+}
+
 /* ------------------------------------------------------------------ warm-start kernels */
 /* Device scatter: problem `order[blockIdx.x]` takes its start from a dense device array, node-major
  * x | u | lam | y (absolute states), into warm-start slot `slot`. */

@@ -171,7 +171,7 @@ struct WarmArgs {
 
 struct KernelArgs {
     const ProbRec *recs;
-    const int32_t *order;     /* problem visiting order (largest first) */
+    const int32_t *order;     /* queue order of the problems of one model */
     int32_t n_problems;
     int32_t *queue;           /* work-queue counter, zeroed before each launch */
     const int32_t *ibase;

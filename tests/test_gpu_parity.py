@@ -173,6 +173,32 @@ def test_graph_replay_and_determinism():
         assert a["inner_iters"] == c["inner_iters"]
 
 
+def test_queue_order_changes_nothing_but_the_schedule():
+    """Longest-predicted-first (sorted on the device from the previous solve's iterations) and
+    largest-tree-first queues give bit-identical solutions; the sorted order is a permutation."""
+    from paper_2506_13624_b300 import bmpc
+    ps = scenes.config4(5, 40)
+    b = bmpc.Batch(ps)
+    res = []
+    for qo in (0, 1, 1):
+        b.set_problems()
+        b.solve(bmpc.default_opts(queue_order=qo), graph=qo == 1)
+        res.append(b.get_solutions())
+    order = b.device_order()
+    b.close()
+    assert sorted(order.tolist()) == list(range(len(ps)))
+    for a, c, d in zip(*res):
+        for key in ("x", "u", "lam", "y"):
+            assert np.array_equal(a[key], c[key]) and np.array_equal(a[key], d[key])
+        assert a["inner_iters"] == c["inner_iters"] == d["inner_iters"]
+    # within a model, the last solve visited the problems by decreasing nodes x (iterations + 1)
+    cost = {k: int(ps[k]["n"]) * (r["inner_iters"] + 1) for k, r in enumerate(res[-1])}
+    models = [int(ps[k]["model"]) for k in order]
+    for m in set(models):
+        seq = [cost[k] for k, mm in zip(order, models) if mm == m]
+        assert seq == sorted(seq, reverse=True)
+
+
 def test_batch_equals_single():
     ps = scenes.config4(4, 6)
     batch = _gpu(ps, block_threads=64)
