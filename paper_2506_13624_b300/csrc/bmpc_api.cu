@@ -103,6 +103,8 @@ struct bmpc_batch {
     size_t stage_bytes = 0;
     bool own_stage = false;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   /* per-model streams of mixed batches */
+    cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
     int sm_count = 148;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -265,12 +267,22 @@ int launch(bmpc_batch *b, const bmpc_opts &o) {
     int32_t *queue = at<int32_t>(b->data, b->L.queue);
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t) * 4, b->stream);
     if (e != cudaSuccess) return BMPC_ERR_CUDA;
+    /* one persistent kernel per model; with several models the kernels run concurrently on forked
+       streams, so that the blocks of one fill the tail of the other */
+    int models = 0;
+    for (int m = 0; m < 3; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
+    if (models > 1 && cudaEventRecord(b->fork, b->stream) != cudaSuccess) return BMPC_ERR_CUDA;
+    bool first = true;
     for (int m = 0; m < 3; ++m) {
         const int cnt = b->model_begin[m + 1] - b->model_begin[m];
         if (cnt == 0) continue;
+        cudaStream_t s = b->stream;
+        if (models > 1 && !first) {
+            s = b->aux[m];
+            if (cudaStreamWaitEvent(s, b->fork, 0) != cudaSuccess) return BMPC_ERR_CUDA;
+        }
         int32_t *ord = at<int32_t>(b->data, b->L.order) + b->model_begin[m];
-        if (o.queue_order == 1 && launch_order(a.recs, a.stats, ord, cnt, b->stream) != cudaSuccess)
-            return BMPC_ERR_CUDA;
+        if (o.queue_order == 1 && launch_order(a.recs, a.stats, ord, cnt, s) != cudaSuccess) return BMPC_ERR_CUDA;
         a.order = ord;
         a.n_problems = cnt;
         a.queue = queue + m;
@@ -278,8 +290,11 @@ int launch(bmpc_batch *b, const bmpc_opts &o) {
         int grid, block;
         geometry(b, o, m, cnt, &grid, &block);
         const size_t smem = solve_smem(m, b->tab_ints[m], b->max_paths[m], block, &a.stg_ld);
-        e = launch_solve(a, m, grid, block, smem, b->stream);
-        if (e != cudaSuccess) return BMPC_ERR_CUDA;
+        if (launch_solve(a, m, grid, block, smem, s) != cudaSuccess) return BMPC_ERR_CUDA;
+        if (s != b->stream &&
+            (cudaEventRecord(b->join[m], s) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->join[m], 0) != cudaSuccess))
+            return BMPC_ERR_CUDA;
+        first = false;
     }
     return BMPC_OK;
 }
@@ -395,6 +410,18 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
             most = std::max(most, solve_smem(m, b->tab_ints[m], b->max_paths[m], bt, &ld));
         }
         if (prepare_solve(m, most) != cudaSuccess) {
+            bmpc_destroy_batch(b);
+            return BMPC_ERR_CUDA;
+        }
+    }
+    int models = 0;
+    for (int m = 0; m < 3; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
+    if (models > 1) {   /* streams and events of the concurrent per-model launches */
+        bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int m = 0; m < 3 && ok; ++m)
+            ok = cudaStreamCreateWithFlags(&b->aux[m], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->join[m], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
             bmpc_destroy_batch(b);
             return BMPC_ERR_CUDA;
         }
@@ -851,6 +878,11 @@ void bmpc_destroy_batch(bmpc_batch *b) {
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    for (int m = 0; m < 3; ++m) {
+        if (b->aux[m]) cudaStreamDestroy(b->aux[m]);
+        if (b->join[m]) cudaEventDestroy(b->join[m]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->own_stage) std::free(b->stage);
     delete b;
 }
