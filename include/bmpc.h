@@ -199,6 +199,11 @@ int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, 
 int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float **u, float **lam, float **y,
                                 int32_t *npad);
 
+/* Bytes one bmpc_set_problems copies host to device (cold starts: problem records and inputs;
+ * with warm starts: plus the warm-start region) and one bmpc_get_solutions copies device to host
+ * (outputs and statistics).  BMPC_ERR_INVALID on a null batch. */
+int bmpc_transfer_bytes(const bmpc_batch *b, size_t *h2d_cold, size_t *h2d_warm, size_t *d2h);
+
 /* Copies the work-queue order of the last solve to `order` (host, caller-allocated, n_problems
  * ints): problem ids grouped by model, in the order the persistent blocks took them.  Waits for
  * the batch's stream.  BMPC_ERR_INVALID on a null argument. */

@@ -87,6 +87,8 @@ def lib() -> C.CDLL:
                                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                                   C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]
         L.bmpc_get_queue_order.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+        L.bmpc_transfer_bytes.argtypes = [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                          C.POINTER(C.c_size_t)]
         _lib = L
     return _lib
 
@@ -95,7 +97,7 @@ EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_
             "bmpc_solve_batch_graph", "bmpc_get_solutions", "bmpc_problem_device_outputs", "bmpc_destroy_batch",
             "bmpc_tree_bytes", "bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution",
             "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune",
-            "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order"]
+            "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order", "bmpc_transfer_bytes"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -205,16 +207,42 @@ class Batch:
         self.nx = np.array([int(p["nx"]) for p in self.problems])
         self.nc = np.array([n_con(p) for p in self.problems])
 
-    def set_problems(self, problems=None, warm=None):
-        """Upload problem data (and optional warm starts: list of (x, u, lam, y) or None)."""
-        probs = self.problems if problems is None else list(problems)
-        arr = (Problem * self.n)()
-        self._pd = [_ProblemData(p, None if warm is None else warm[k]) for k, p in enumerate(probs)]
-        for k, pd in enumerate(self._pd):
-            arr[k] = pd.s
-        self._arr = arr
+    def set_problems(self, problems=None, warm=None, reuse: bool = False):
+        """Upload problem data (and optional warm starts: list of (x, u, lam, y) or None).
+
+        With reuse=True the problem descriptors of the previous call are uploaded again: the caller
+        has updated the same float32 arrays in place (x0, xref, obstacles, ...), as a control loop
+        that keeps one buffer per problem does."""
+        if not (reuse and getattr(self, "_arr", None) is not None):
+            probs = self.problems if problems is None else list(problems)
+            arr = (Problem * self.n)()
+            self._pd = [_ProblemData(p, None if warm is None else warm[k]) for k, p in enumerate(probs)]
+            for k, pd in enumerate(self._pd):
+                arr[k] = pd.s
+            self._arr = arr
         with self.torch.cuda.device(self.device):
-            _check(lib().bmpc_set_problems(self.handle, arr), "bmpc_set_problems")
+            _check(lib().bmpc_set_problems(self.handle, self._arr), "bmpc_set_problems")
+
+    def transfer_bytes(self):
+        """(host-to-device bytes per set_problems cold, with warm starts, device-to-host bytes per
+        get_solutions with arrays)."""
+        h, w, d = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        _check(lib().bmpc_transfer_bytes(self.handle, C.byref(h), C.byref(w), C.byref(d)), "bmpc_transfer_bytes")
+        return h.value, w.value, d.value
+
+    def get_solutions_flat(self):
+        """Synchronise and return node-major float32 arrays x, u, lam, y of all problems concatenated
+        (problem k's rows follow problem k-1's) and the statistics as a ctypes array."""
+        tot_x = int(np.sum(self.nodes * self.nx))
+        tot_u = int(np.sum(self.nodes * NU))
+        tot_y = int(np.sum(self.nodes * self.nc))
+        x, lam = np.empty(max(tot_x, 1), np.float32), np.empty(max(tot_x, 1), np.float32)
+        u, y = np.empty(max(tot_u, 1), np.float32), np.empty(max(tot_y, 1), np.float32)
+        st = (Stats * self.n)()
+        with self.torch.cuda.device(self.device):
+            _check(lib().bmpc_get_solutions(self.handle, *(a.ctypes.data_as(_fp) for a in (x, u, lam, y)), st),
+                   "bmpc_get_solutions")
+        return x, u, lam, y, st
 
     def solve(self, opts: Opts | None = None, graph: bool = False):
         """Launch the persistent solver (asynchronous on the batch's stream)."""

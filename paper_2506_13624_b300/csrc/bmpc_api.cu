@@ -8,11 +8,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "../../include/bmpc.h"
@@ -233,6 +235,26 @@ int check_opts(const bmpc_opts &o) {
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? BMPC_OK : BMPC_ERR_CUDA; }
+
+/* Runs f(k) for k in [0, n) on up to 16 host threads (problems are independent in the host
+ * packing and unpacking: each writes its own region of the staging buffer or of the outputs). */
+template <typename F>
+void for_problems(int n, F &&f) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int T = std::min<int>(std::min<unsigned>(hw ? hw : 1u, 16u), std::max(1, n / 64));
+    if (T <= 1) {
+        for (int k = 0; k < n; ++k) f(k);
+        return;
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    pool.reserve(T);
+    for (int t = 0; t < T; ++t)
+        pool.emplace_back([&] {
+            for (int k; (k = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(k);
+        });
+    for (std::thread &t : pool) t.join();
+}
 
 template <typename T>
 T *at(char *base, size_t off) {
@@ -500,28 +522,36 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
 int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
     if (!b || !probs) return BMPC_ERR_INVALID;
     const int n = b->n;
-    bool any_warm = false;
-    float *fin = at<float>(b->stage, b->L.in);
-    float *fw = at<float>(b->stage, b->L.warm);
+    /* validation first (nothing is changed when a problem is invalid) */
     for (int k = 0; k < n; ++k) {
         const bmpc_problem &P = probs[k];
-        ProbRec &R = b->recs[k];
-        const int nn = R.n, np = R.npad, nx = R.nx, nc = R.nc;
+        const ProbRec &R = b->recs[k];
         if (!P.x0 || !P.xref || (R.n_obs > 0 && !P.obs)) return BMPC_ERR_INVALID;
         if (R.model == 2 && (!P.Alin || !P.Blin)) return BMPC_ERR_INVALID;
         const bool warm = P.warm_x || P.warm_u || P.warm_lam || P.warm_y;
-        if (warm && (!P.warm_x || !P.warm_u || !P.warm_lam || (nc > 0 && !P.warm_y))) return BMPC_ERR_INVALID;
+        if (warm && (!P.warm_x || !P.warm_u || !P.warm_lam || (R.nc > 0 && !P.warm_y))) return BMPC_ERR_INVALID;
+        for (int j = 0; j < R.nx; ++j)
+            if (!std::isfinite(P.x0[j])) return BMPC_ERR_INVALID;
+        for (int j = 0; j < NU; ++j)
+            if (!(P.Rw[j] > 0.f)) return BMPC_ERR_INVALID;
+    }
+    std::atomic<bool> any_warm{false};
+    float *fin = at<float>(b->stage, b->L.in);
+    float *fw = at<float>(b->stage, b->L.warm);
+    for_problems(n, [&](int k) {
+        const bmpc_problem &P = probs[k];
+        ProbRec &R = b->recs[k];
+        const int nn = R.n, np = R.npad, nx = R.nx, nc = R.nc;
+        const bool warm = P.warm_x || P.warm_u || P.warm_lam || P.warm_y;
         for (int j = 0; j < nx; ++j) {
             R.x0[j] = P.x0[j];
             R.Qw[j] = P.Qw[j];
             R.QNw[j] = P.QNw[j];
-            if (!std::isfinite(P.x0[j])) return BMPC_ERR_INVALID;
         }
         for (int j = 0; j < NU; ++j) {
             R.Rw[j] = P.Rw[j];
             R.u_lo[j] = P.u_lo[j];
             R.u_hi[j] = P.u_hi[j];
-            if (!(P.Rw[j] > 0.f)) return BMPC_ERR_INVALID;
         }
         R.lane_lo = P.lane_lo;
         R.lane_hi = P.lane_hi;
@@ -530,7 +560,7 @@ int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
             std::memcpy(R.Blin, P.Blin, sizeof(float) * nx * NU);
         }
         R.has_warm = warm ? 1 : 0;
-        any_warm |= warm;
+        if (warm) any_warm.store(true, std::memory_order_relaxed);
         const InRows ir = in_rows(nx, R.n_obs);
         float *base = fin + R.off_in;
         std::memset(base, 0, sizeof(float) * (size_t)ir.total * np);
@@ -554,14 +584,14 @@ int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
                 for (int c = 0; c < nc; ++c) wb[(size_t)(wr.wy + c) * np + i] = P.warm_y[(size_t)i * nc + c];
             }
         }
-    }
+    });
     std::memcpy(b->stage + b->L.recs, b->recs.data(), sizeof(ProbRec) * n);
     cudaError_t e = cudaMemcpyAsync(b->data + b->L.recs, b->stage + b->L.recs, sizeof(ProbRec) * n,
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->data + b->L.in, b->stage + b->L.in, sizeof(float) * b->L.in_n, cudaMemcpyHostToDevice,
                             b->stream);
-    if (e == cudaSuccess && any_warm)
+    if (e == cudaSuccess && any_warm.load())
         e = cudaMemcpyAsync(b->data + b->L.warm, b->stage + b->L.warm, sizeof(float) * b->L.warm_n,
                             cudaMemcpyHostToDevice, b->stream);
     return cuda_status(e);
@@ -804,9 +834,16 @@ int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, 
     if (e != cudaSuccess) return BMPC_ERR_CUDA;
     const float *fo = at<const float>(b->stage, b->L.out);
     const float *fi = at<const float>(b->stage, b->L.in);
-    size_t ox = 0, ou = 0, ol = 0, oy = 0;
+    std::vector<size_t> offx(b->n + 1, 0), offu(b->n + 1, 0), offy(b->n + 1, 0);   /* node-major offsets */
     for (int k = 0; k < b->n; ++k) {
         const ProbRec &R = b->recs[k];
+        offx[k + 1] = offx[k] + (size_t)R.n * R.nx;
+        offu[k + 1] = offu[k] + (size_t)R.n * NU;
+        offy[k + 1] = offy[k] + (size_t)R.n * R.nc;
+    }
+    for_problems((x || u || lam || y) ? b->n : 0, [&](int k) {
+        const ProbRec &R = b->recs[k];
+        const size_t ox = offx[k], ol = offx[k], ou = offu[k], oy = offy[k];
         const OutRows orw = out_rows(R.nx, R.nc);
         const InRows ir = in_rows(R.nx, R.n_obs);
         const float *base = fo + R.off_out;
@@ -823,11 +860,7 @@ int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, 
             for (int c = 0; c < R.nc; ++c)
                 if (y) y[oy + (size_t)i * R.nc + c] = base[(size_t)(orw.y + c) * np + i];
         }
-        ox += (size_t)nn * R.nx;
-        ol += (size_t)nn * R.nx;
-        ou += (size_t)nn * NU;
-        oy += (size_t)nn * R.nc;
-    }
+    });
     if (stats) {
         const Stats *s = at<const Stats>(b->stage, b->L.stats);
         for (int k = 0; k < b->n; ++k) {
@@ -862,6 +895,15 @@ int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float
     if (lam) *lam = base + (size_t)orw.lam * R.npad;
     if (y) *y = base + (size_t)orw.y * R.npad;
     if (npad) *npad = R.npad;
+    return BMPC_OK;
+}
+
+int bmpc_transfer_bytes(const bmpc_batch *b, size_t *h2d_cold, size_t *h2d_warm, size_t *d2h) {
+    if (!b) return BMPC_ERR_INVALID;
+    const size_t cold = sizeof(ProbRec) * (size_t)b->n + sizeof(float) * b->L.in_n;
+    if (h2d_cold) *h2d_cold = cold;
+    if (h2d_warm) *h2d_warm = cold + sizeof(float) * b->L.warm_n;
+    if (d2h) *d2h = sizeof(float) * b->L.out_n + sizeof(Stats) * (size_t)b->n;
     return BMPC_OK;
 }
 
