@@ -36,6 +36,8 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
 
 def workload(name: str, batch: int, rank: int = 0):
     """Seeded problems of the named configuration; each rank gets its own seeds."""
+    if name == "config1":
+        return [scenes.config1(rank * batch + i) for i in range(batch)]
     if name == "config2":
         return [scenes.config2(rank * batch + i) for i in range(batch)]
     if name == "config4":
@@ -192,6 +194,38 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- ncu traffic
+PROFILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "bmpc_solve_kernel_config2.md")
+KERNEL_SOURCES = ("paper_2506_13624_b300/csrc/bmpc_kernel.cu", "paper_2506_13624_b300/csrc/bmpc_layout.h")
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_name, batch):
+    """DRAM bytes (read + write) of one solve launch, scaled by problems from the committed ncu
+    capture of config-2 problems; None for other workloads or when the kernel sources changed
+    since the capture."""
+    if workload_name != "config2" or not os.path.exists(PROFILE):
+        return None
+    kv = {}
+    with open(PROFILE) as fh:
+        for line in fh:
+            k, _, v = line.partition(":")
+            if k in ("kernel_sha256", "dram_bytes_per_problem"):
+                kv[k] = v.strip()
+    if kv.get("kernel_sha256") != kernel_sha() or "dram_bytes_per_problem" not in kv:
+        return None
+    return float(kv["dram_bytes_per_problem"]) * batch
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -307,7 +341,8 @@ def run_gpu(args):
         "inner_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
         "gpu_launches": args.steps * n_models * (2 if opts.queue_order == 1 else 1),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload, args.batch),
+                     "traffic_unit": "bytes per launch (ncu dram read + write, scaled by problems)",
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"},
         "e2e": {"value": total_conv / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -323,10 +358,10 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="config2", choices=["config2", "config3", "config4"])
+    ap.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "config4"])
     ap.add_argument("--batch", type=int, default=2048)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
