@@ -433,3 +433,15 @@ def test_gelu_and_bf16_rounding():
     assert mlp_ref.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6  # tie -> even (1 + 2^-6)
     assert mlp_ref.bf16(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7      # exactly representable
     assert mlp_ref.bf16(-3.0) == -3.0
+
+
+def test_adamw_first_step_closed_form():
+    """AdamW's bias-corrected first step moves every weight by lr (g / (|g| + eps) + wd w)."""
+    from oracle import mlp_ref
+    rng = np.random.default_rng(7)
+    w, g = rng.standard_normal(50), rng.standard_normal(50)
+    lr, wd, eps = 1e-3, 0.1, 1e-8
+    w1, m1, v1 = mlp_ref.adamw(w, np.zeros(50), np.zeros(50), g, 1, lr, wd, eps=eps)
+    np.testing.assert_allclose(w1, w - lr * (g / (np.abs(g) + eps) + wd * w), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(m1, 0.1 * g, rtol=1e-12)
+    np.testing.assert_allclose(v1, 0.001 * g * g, rtol=1e-12)
