@@ -226,6 +226,19 @@ def profiled_traffic(workload_name, batch):
     return float(kv["dram_bytes_per_problem"]) * batch
 
 
+# ----------------------------------------------------------------- weak scaling over ranks
+def reduce_over_ranks(ms, e2e_s, n_conv, dist=None, device="cpu"):
+    """The slowest rank's step times and the converged solves of all ranks: every rank solves its
+    own shard of independent problems, so the whole job's rate is their sum over the max time."""
+    import torch
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    c = torch.tensor([float(n_conv)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(c[0])
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -295,19 +308,12 @@ def run_gpu(args):
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     h2d, _, d2h = b.transfer_bytes()
 
-    ms_all = torch.tensor([ms], device="cuda")
-    e2e_all = torch.tensor([e2e_s], device="cuda")
-    nconv_all = torch.tensor([n_conv], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e2e_all, op=dist.ReduceOp.MAX)
-        dist.all_reduce(nconv_all, op=dist.ReduceOp.SUM)
+    ms_max, e2e_max, total_conv = reduce_over_ranks(ms, e2e_s, n_conv, dist if world > 1 else None, "cuda")
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    ms = float(ms_all.item())
-    total_conv = float(nconv_all.item())
+    ms, e2e_s = ms_max, e2e_max
     value = total_conv / (ms / 1e3)
     flops = algorithmic_flops(problems, res)
     n_models = len({int(p["model"]) for p in problems})   # one solve (+ one queue-order) kernel per model

@@ -1,0 +1,49 @@
+"""The N > 1 path of bench.py on CPU: two gloo ranks, disjoint problem shards, and the weak-scaling
+reduction (slowest rank's time, all ranks' converged solves)."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms, e2e, conv = bench.reduce_over_ranks(10.0 + rank, 50.0 - rank, 100 + rank, dist, "cpu")
+    x0 = np.stack([p["x0"] for p in bench.workload("config2", 3, rank)])
+    gathered = [None] * world
+    dist.all_gather_object(gathered, x0.tolist())
+    dist.destroy_process_group()
+    out.put((rank, ms, e2e, conv, gathered))
+
+
+def test_two_gloo_ranks_shard_and_reduce():
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, e2e, conv, gathered in res:
+        assert ms == 11.0 and e2e == 50.0 and conv == 201.0
+        a, b = np.array(gathered[0]), np.array(gathered[1])
+        assert a.shape == b.shape and not np.any(np.all(a[:, None, :] == b[None, :, :], axis=2))
