@@ -567,9 +567,16 @@ int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
         for (int i = 0; i < nn; ++i) {
             for (int j = 0; j < nx; ++j) base[(size_t)(ir.xref + j) * np + i] = P.xref[(size_t)i * nx + j];
             base[(size_t)ir.weight * np + i] = P.weight ? P.weight[i] : 1.f;
-            for (int o = 0; o < R.n_obs; ++o)
-                for (int c = 0; c < 5; ++c)
-                    base[(size_t)(ir.obs + 5 * o + c) * np + i] = P.obs[((size_t)i * R.n_obs + o) * 5 + c];
+            for (int o = 0; o < R.n_obs; ++o) {
+                const float *ob = P.obs + ((size_t)i * R.n_obs + o) * 5;   /* cx, cy, heading, a, b */
+                float *row = base + (size_t)(ir.obs + OBS_ROWS * o) * np + i;
+                row[0] = ob[0];
+                row[(size_t)np] = ob[1];
+                row[2 * (size_t)np] = (float)std::cos((double)ob[2]);
+                row[3 * (size_t)np] = (float)std::sin((double)ob[2]);
+                row[4 * (size_t)np] = (float)(1.0 / ((double)ob[3] * ob[3]));
+                row[5 * (size_t)np] = (float)(1.0 / ((double)ob[4] * ob[4]));
+            }
         }
         if (warm) {
             const WarmRows wr = warm_rows(nx, nc);

@@ -465,6 +465,7 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
     /* x is the deviation from the node's reference (the kernel's state coordinates) */
     const float w = V.w[i];
     const float *Qd = is_leaf ? R.QNw : R.Qw;
+    const float irho = 1.f / rho;
     float la = 0.f;
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
@@ -495,7 +496,7 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
                     const float g = sgn == 0 ? u[j] - R.u_hi[j] : R.u_lo[j] - u[j];
                     const float s = V.Y[(size_t)rr * V.np + i] + rho * g;
                     if (s > 0.f) {
-                        la += 0.5f * s * s / rho;
+                        la += 0.5f * s * s * irho;
                         if (GRAD) {
                             r[j] += sgn == 0 ? s : -s;
                             hr[j] += rho;
@@ -508,19 +509,16 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
     }
     if (i != 0) {
         for (int o = 0; o < V.nobs; ++o) {
-            const float *ob = V.obs + (size_t)(5 * o) * V.np + i;
-            const float cx = ob[0], cy = ob[V.np], hd = ob[2 * (size_t)V.np];
-            const float ea = ob[3 * (size_t)V.np], eb = ob[4 * (size_t)V.np];
-            float sh, ch;
-            sincosf(hd, &sh, &ch);
+            const float *ob = V.obs + (size_t)(OBS_ROWS * o) * V.np + i;
+            const float cx = ob[0], cy = ob[V.np], ch = ob[2 * (size_t)V.np], sh = ob[3 * (size_t)V.np];
+            const float ia2 = ob[4 * (size_t)V.np], ib2 = ob[5 * (size_t)V.np];
             const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
             const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
-            const float ia2 = 1.f / (ea * ea), ib2 = 1.f / (eb * eb);
             const float rr2 = sqrtf(dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f);
             const float g = 1.f - rr2;
             const float s = V.Y[(size_t)(row + o) * V.np + i] + rho * g;
             if (s > 0.f) {
-                la += 0.5f * s * s / rho;
+                la += 0.5f * s * s * irho;
                 if (GRAD) {
                     const float irr = 1.f / rr2;
                     const float gx = -(dpar * ia2 * ch - dper * ib2 * sh) * irr;
@@ -540,14 +538,14 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
             const float s0 = V.Y[(size_t)row * V.np + i] + rho * g0;
             const float s1 = V.Y[(size_t)(row + 1) * V.np + i] + rho * g1;
             if (s0 > 0.f) {
-                la += 0.5f * s0 * s0 / rho;
+                la += 0.5f * s0 * s0 * irho;
                 if (GRAD) {
                     q[1] += s0;
                     hq[2] += rho;
                 }
             }
             if (s1 > 0.f) {
-                la += 0.5f * s1 * s1 / rho;
+                la += 0.5f * s1 * s1 * irho;
                 if (GRAD) {
                     q[1] -= s1;
                     hq[2] += rho;
@@ -575,14 +573,12 @@ __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX>
     }
     if (i != 0) {
         for (int o = 0; o < V.nobs; ++o) {
-            const float *ob = V.obs + (size_t)(5 * o) * V.np + i;
-            const float cx = ob[0], cy = ob[V.np], hd = ob[2 * (size_t)V.np];
-            const float ea = ob[3 * (size_t)V.np], eb = ob[4 * (size_t)V.np];
-            float sh, ch;
-            sincosf(hd, &sh, &ch);
+            const float *ob = V.obs + (size_t)(OBS_ROWS * o) * V.np + i;
+            const float cx = ob[0], cy = ob[V.np], ch = ob[2 * (size_t)V.np], sh = ob[3 * (size_t)V.np];
+            const float ia2 = ob[4 * (size_t)V.np], ib2 = ob[5 * (size_t)V.np];
             const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
             const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
-            fn(row + o, 1.f - sqrtf(dpar * dpar / (ea * ea) + dper * dper / (eb * eb) + 1e-6f));
+            fn(row + o, 1.f - sqrtf(dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f));
         }
         row += V.nobs;
         if (V.lane) {
@@ -1997,13 +1993,13 @@ __global__ void bmpc_features_kernel(GlueArgs a) {
         const int depth = ib[io.pdepth + s];
         const int32_t *path = ib + io.ptab + (size_t)s * R.n_stage;
         const int mid = path[depth / 2], leaf = path[depth];
-        const float *ob = obs + (size_t)(5 * o) * np;
+        const float *ob = obs + (size_t)(OBS_ROWS * o) * np;
         float *g = f + (nx - 1) + 5 * (s * a.n_obs_max + o);
         g[0] = ob[mid] - R.x0[0];
         g[1] = ob[(size_t)np + mid];
         g[2] = ob[leaf] - R.x0[0];
         g[3] = ob[(size_t)np + leaf];
-        g[4] = ob[2 * (size_t)np + leaf];
+        g[4] = atan2f(ob[3 * (size_t)np + leaf], ob[2 * (size_t)np + leaf]);   /* heading */
     }
 }
 

@@ -74,7 +74,10 @@ __host__ __device__ inline int64_t table_ints(int npad, int n_stage, int n_paths
     return o.total - o.sstart;
 }
 
-/* input region: xref[nx] weight[1] obs[5*n_obs] (rows of npad) */
+/* input region: xref[nx] weight[1] obs[6*n_obs] (rows of npad).  Per obstacle the rows hold the
+ * ellipse centre cx, cy, the cosine and sine of its heading and 1/a^2, 1/b^2 (computed once by the
+ * host packing from the caller's cx, cy, heading, a, b). */
+constexpr int OBS_ROWS = 6;
 struct InRows {
     int xref, weight, obs, total;
 };
@@ -83,7 +86,7 @@ __host__ __device__ inline InRows in_rows(int nx, int n_obs) {
     r.xref = 0;
     r.weight = nx;
     r.obs = r.weight + 1;
-    r.total = r.obs + 5 * n_obs;
+    r.total = r.obs + OBS_ROWS * n_obs;
     return r;
 }
 
