@@ -295,18 +295,20 @@ def run_gpu(args):
     res = b.get_solutions(want_arrays=False)
     n_conv = int(sum(r["status"] == 0 for r in res))
 
-    # end to end through the C ABI with host buffers, every step: pack the problems' host arrays
-    # (updated in place, as a control loop does) + H2D, solve, D2H + unpack to node-major arrays
-    b.set_problems(reuse=True)
+    # end to end through the C ABI with host buffers, every step: the batch's node-major inputs
+    # (pinned host arrays a control loop overwrites in place) copied host to device and laid out
+    # on the device, the solve, and the node-major solutions copied back into pinned host arrays
+    fin, fout = b.flat_inputs(), b.flat_outputs()
+    b.set_problems_flat(*fin)
     b.solve(opts, graph=True)
-    b.get_solutions_flat()
+    b.get_solutions_flat(fout)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        b.set_problems(reuse=True)
+        b.set_problems_flat(*fin)
         b.solve(opts, graph=True)
-        b.get_solutions_flat()
+        b.get_solutions_flat(fout)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    h2d, _, d2h = b.transfer_bytes()
+    h2d, d2h = b.transfer_bytes_flat()
 
     ms_max, e2e_max, total_conv = reduce_over_ranks(ms, e2e_s, n_conv, dist if world > 1 else None, "cuda")
     if rank != 0:

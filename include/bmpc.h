@@ -199,6 +199,30 @@ int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, 
 int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float **u, float **lam, float **y,
                                 int32_t *npad);
 
+/* Flat transfers for callers that keep the per-node data of the whole batch in three node-major
+ * arrays, concatenated in problem order (best in pinned host memory or on the device; any
+ * memory cudaMemcpy accepts):
+ *   xref   [sum_k n_k * nx_k]       reference states;
+ *   weight [sum_k n_k] or NULL      node probabilities (NULL: 1);
+ *   obs    [sum_k n_k * n_obs_k * 5] obstacle ellipses (cx, cy, heading, a, b).
+ * The per-problem scalars (x0, Q, R, Q_N, bounds, lane, linear model) still come from `probs`
+ * (their array pointers and warm starts are ignored: this upload clears the warm-start slots).
+ * One copy per array and a device kernel replace the host packing of bmpc_set_problems; the data
+ * the solver sees are identical.  Asynchronous on the handle's stream; the caller keeps the
+ * arrays unchanged until the stream has consumed them. */
+int bmpc_set_problems_flat(bmpc_batch *b, const bmpc_problem *probs, const float *xref, const float *weight,
+                           const float *obs);
+
+/* Solutions as node-major arrays concatenated in problem order: x [sum n_k nx_k] (absolute
+ * states), u [sum n_k nu], lam [sum n_k nx_k], y [sum n_k nc_k] (any may be NULL), packed on the
+ * device and copied with one transfer each (fast into pinned memory), and per-problem statistics.
+ * Synchronises the handle's stream.  Values equal bmpc_get_solutions'. */
+int bmpc_get_solutions_flat(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats);
+
+/* Bytes one bmpc_set_problems_flat copies host to device (records, xref, weight, obs) and one
+ * bmpc_get_solutions_flat copies device to host (x, u, lam, y, statistics). */
+int bmpc_transfer_bytes_flat(const bmpc_batch *b, size_t *h2d, size_t *d2h);
+
 /* Bytes one bmpc_set_problems copies host to device (cold starts: problem records and inputs;
  * with warm starts: plus the warm-start region) and one bmpc_get_solutions copies device to host
  * (outputs and statistics).  BMPC_ERR_INVALID on a null batch. */

@@ -89,6 +89,10 @@ def lib() -> C.CDLL:
         L.bmpc_get_queue_order.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
         L.bmpc_transfer_bytes.argtypes = [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
                                           C.POINTER(C.c_size_t)]
+        L.bmpc_transfer_bytes_flat.argtypes = [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        L.bmpc_set_problems_flat.argtypes = [C.c_void_p, C.POINTER(Problem), C.c_void_p, C.c_void_p, C.c_void_p]
+        L.bmpc_get_solutions_flat.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.POINTER(Stats)]
         _lib = L
     return _lib
 
@@ -97,7 +101,8 @@ EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_
             "bmpc_solve_batch_graph", "bmpc_get_solutions", "bmpc_problem_device_outputs", "bmpc_destroy_batch",
             "bmpc_tree_bytes", "bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution",
             "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune",
-            "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order", "bmpc_transfer_bytes"]
+            "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order", "bmpc_transfer_bytes",
+            "bmpc_set_problems_flat", "bmpc_get_solutions_flat", "bmpc_transfer_bytes_flat"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -230,19 +235,59 @@ class Batch:
         _check(lib().bmpc_transfer_bytes(self.handle, C.byref(h), C.byref(w), C.byref(d)), "bmpc_transfer_bytes")
         return h.value, w.value, d.value
 
-    def get_solutions_flat(self):
-        """Synchronise and return node-major float32 arrays x, u, lam, y of all problems concatenated
-        (problem k's rows follow problem k-1's) and the statistics as a ctypes array."""
-        tot_x = int(np.sum(self.nodes * self.nx))
-        tot_u = int(np.sum(self.nodes * NU))
-        tot_y = int(np.sum(self.nodes * self.nc))
-        x, lam = np.empty(max(tot_x, 1), np.float32), np.empty(max(tot_x, 1), np.float32)
-        u, y = np.empty(max(tot_u, 1), np.float32), np.empty(max(tot_y, 1), np.float32)
-        st = (Stats * self.n)()
+    def flat_inputs(self, pinned: bool = True):
+        """The batch's per-node inputs as node-major float32 tensors concatenated in problem order:
+        (xref [sum n*nx], weight [sum n], obs [sum n*n_obs*5]) in pinned host memory, for
+        set_problems_flat.  A control loop keeps them and overwrites them in place."""
+        torch = self.torch
+        cat = lambda key: np.concatenate([np.asarray(p[key], np.float32).reshape(-1) for p in self.problems])
+        arrs = (cat("xref"), cat("weight"), cat("obs"))
+        out = []
+        for a in arrs:
+            t = torch.from_numpy(np.ascontiguousarray(a))
+            out.append(t.pin_memory() if pinned else t)
+        return tuple(out)
+
+    def flat_outputs(self, pinned: bool = True):
+        """Reusable node-major float32 tensors (x, u, lam, y) for get_solutions_flat."""
+        torch = self.torch
+        sizes = (int(np.sum(self.nodes * self.nx)), int(np.sum(self.nodes * NU)), int(np.sum(self.nodes * self.nx)),
+                 int(np.sum(self.nodes * self.nc)))
+        return tuple((torch.empty(max(s, 1), dtype=torch.float32).pin_memory() if pinned
+                      else torch.empty(max(s, 1), dtype=torch.float32)) for s in sizes)
+
+    def set_problems_flat(self, xref, weight, obs):
+        """Upload from flat node-major tensors (see flat_inputs); per-problem scalars come from the
+        problem dicts.  Warm-start slots are cleared."""
+        if getattr(self, "_arr", None) is None:
+            arr = (Problem * self.n)()
+            self._pd = [_ProblemData(p) for p in self.problems]
+            for k, pd in enumerate(self._pd):
+                arr[k] = pd.s
+            self._arr = arr
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
         with self.torch.cuda.device(self.device):
-            _check(lib().bmpc_get_solutions(self.handle, *(a.ctypes.data_as(_fp) for a in (x, u, lam, y)), st),
-                   "bmpc_get_solutions")
-        return x, u, lam, y, st
+            _check(lib().bmpc_set_problems_flat(self.handle, self._arr, ptr(xref), ptr(weight), ptr(obs)),
+                   "bmpc_set_problems_flat")
+
+    def get_solutions_flat(self, out=None):
+        """Synchronise and return node-major arrays x, u, lam, y of all problems concatenated in
+        problem order (into `out`, a tuple from flat_outputs, when given) and the statistics as a
+        ctypes array."""
+        torch = self.torch
+        if out is None:
+            out = self.flat_outputs(pinned=False)
+        st = (Stats * self.n)()
+        with torch.cuda.device(self.device):
+            _check(lib().bmpc_get_solutions_flat(self.handle, *(C.c_void_p(t.data_ptr()) for t in out), st),
+                   "bmpc_get_solutions_flat")
+        return (*out, st)
+
+    def transfer_bytes_flat(self):
+        """(host-to-device bytes per set_problems_flat, device-to-host bytes per get_solutions_flat)."""
+        h, d = C.c_size_t(), C.c_size_t()
+        _check(lib().bmpc_transfer_bytes_flat(self.handle, C.byref(h), C.byref(d)), "bmpc_transfer_bytes_flat")
+        return h.value, d.value
 
     def solve(self, opts: Opts | None = None, graph: bool = False):
         """Launch the persistent solver (asynchronous on the batch's stream)."""

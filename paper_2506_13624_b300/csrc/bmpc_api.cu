@@ -26,6 +26,7 @@ cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block,
 size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld);
 cudaError_t prepare_solve(int model, size_t smem);
 cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order, int cnt, cudaStream_t stream);
+cudaError_t launch_flat(int which, const FlatArgs &a, int n_problems, cudaStream_t stream);
 int max_block_threads();
 cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
@@ -81,8 +82,9 @@ int validate(const bmpc_tree_desc &d, std::vector<int> *stage_out) {
 }
 
 struct Layout {
-    size_t recs, order, queue, ints, in, warm, out, stats, data_total;   /* byte offsets in the data arena */
-    size_t ints_n, in_n, warm_n, out_n, scr_n;                           /* element counts */
+    size_t recs, order, queue, ints, in, warm, out, stats, raw, data_total;   /* byte offsets in the data arena */
+    size_t ints_n, in_n, warm_n, out_n, scr_n, raw_n;                         /* element counts */
+    int64_t T_n, T_nx, T_nc, T_obs;                                          /* node-major flat totals */
     size_t staging;
 };
 
@@ -97,6 +99,7 @@ struct bmpc_batch {
     int model_begin[4] = {0, 0, 0, 0};   /* order[model_begin[m] .. model_begin[m+1]) has model m */
     int tab_ints[3] = {0, 0, 0};         /* shared-memory stage/path tables per model (0: global) */
     int max_paths[3] = {0, 0, 0};        /* most scenarios of a tree, per model */
+    bool host_inputs = false;            /* staging holds the inputs of the last upload */
     Layout L{};
     char *data = nullptr;
     float *scr = nullptr;
@@ -121,6 +124,7 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
     recs.assign(n, ProbRec{});
     nodes.resize(n);
     size_t oi = 0, oin = 0, ow = 0, oo = 0, os = 0;
+    int64_t fn = 0, fnx = 0, fnc = 0, fobs = 0;
     for (int k = 0; k < n; ++k) {
         const bmpc_tree_desc &d = descs[k];
         ProbRec &R = recs[k];
@@ -158,6 +162,14 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         R.off_warm = (int64_t)ow;
         R.off_out = (int64_t)oo;
         R.off_scr = (int64_t)os;
+        R.off_node = fn;
+        R.off_nx = fnx;
+        R.off_nc = fnc;
+        R.off_obs = fobs;
+        fn += R.n;
+        fnx += (int64_t)R.n * R.nx;
+        fnc += (int64_t)R.n * R.nc;
+        fobs += (int64_t)R.n * R.n_obs * 5;
         oi += (size_t)int_off(R.npad, R.n_stage, R.n_paths).total;
         oin += (size_t)in_rows(R.nx, R.n_obs).total * R.npad;
         ow += 2 * (size_t)warm_rows(R.nx, R.nc).total * R.npad;   /* primary and fallback slots */
@@ -170,6 +182,11 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
     L.warm_n = ow;
     L.out_n = oo;
     L.scr_n = os;
+    L.T_n = fn;
+    L.T_nx = fnx;
+    L.T_nc = fnc;
+    L.T_obs = fobs;
+    L.raw_n = (size_t)std::max(fnx + fn + fobs, 2 * fnx + 2 * fn + fnc);
     size_t off = 0;
     L.recs = off;
     off = align_up(off + sizeof(ProbRec) * n);
@@ -187,9 +204,11 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
     off = align_up(off + sizeof(float) * oo);
     L.stats = off;
     off = align_up(off + sizeof(Stats) * n);
+    /* staging mirrors [recs .. stats] of the data arena; the raw region (flat transfers) is device only */
+    L.staging = off;
+    L.raw = off;
+    off = align_up(off + sizeof(float) * L.raw_n);
     L.data_total = off;
-    /* staging mirrors [recs .. stats] of the data arena */
-    L.staging = L.data_total;
 }
 
 KOpts to_kopts(const bmpc_opts &o) {
@@ -259,6 +278,39 @@ void for_problems(int n, F &&f) {
 template <typename T>
 T *at(char *base, size_t off) {
     return reinterpret_cast<T *>(base + off);
+}
+
+/* The per-problem scalars of a bmpc_problem (x0, weights, bounds, linear model) into its record. */
+void copy_params(ProbRec &R, const bmpc_problem &P) {
+    for (int j = 0; j < R.nx; ++j) {
+        R.x0[j] = P.x0[j];
+        R.Qw[j] = P.Qw[j];
+        R.QNw[j] = P.QNw[j];
+    }
+    for (int j = 0; j < NU; ++j) {
+        R.Rw[j] = P.Rw[j];
+        R.u_lo[j] = P.u_lo[j];
+        R.u_hi[j] = P.u_hi[j];
+    }
+    R.lane_lo = P.lane_lo;
+    R.lane_hi = P.lane_hi;
+    if (R.model == 2) {
+        std::memcpy(R.Alin, P.Alin, sizeof(float) * R.nx * R.nx);
+        std::memcpy(R.Blin, P.Blin, sizeof(float) * R.nx * NU);
+    }
+}
+
+FlatArgs flat_args(bmpc_batch *b) {
+    FlatArgs f{};
+    f.recs = at<const ProbRec>(b->data, b->L.recs);
+    f.inbase = at<float>(b->data, b->L.in);
+    f.outbase = at<const float>(b->data, b->L.out);
+    f.raw = at<float>(b->data, b->L.raw);
+    f.T_n = b->L.T_n;
+    f.T_nx = b->L.T_nx;
+    f.T_nc = b->L.T_nc;
+    f.T_obs = b->L.T_obs;
+    return f;
 }
 
 /* Launch geometry for the problems of one model: threads per problem and persistent blocks. */
@@ -543,22 +595,7 @@ int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
         ProbRec &R = b->recs[k];
         const int nn = R.n, np = R.npad, nx = R.nx, nc = R.nc;
         const bool warm = P.warm_x || P.warm_u || P.warm_lam || P.warm_y;
-        for (int j = 0; j < nx; ++j) {
-            R.x0[j] = P.x0[j];
-            R.Qw[j] = P.Qw[j];
-            R.QNw[j] = P.QNw[j];
-        }
-        for (int j = 0; j < NU; ++j) {
-            R.Rw[j] = P.Rw[j];
-            R.u_lo[j] = P.u_lo[j];
-            R.u_hi[j] = P.u_hi[j];
-        }
-        R.lane_lo = P.lane_lo;
-        R.lane_hi = P.lane_hi;
-        if (R.model == 2) {
-            std::memcpy(R.Alin, P.Alin, sizeof(float) * nx * nx);
-            std::memcpy(R.Blin, P.Blin, sizeof(float) * nx * NU);
-        }
+        copy_params(R, P);
         R.has_warm = warm ? 1 : 0;
         if (warm) any_warm.store(true, std::memory_order_relaxed);
         const InRows ir = in_rows(nx, R.n_obs);
@@ -570,12 +607,11 @@ int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
             for (int o = 0; o < R.n_obs; ++o) {
                 const float *ob = P.obs + ((size_t)i * R.n_obs + o) * 5;   /* cx, cy, heading, a, b */
                 float *row = base + (size_t)(ir.obs + OBS_ROWS * o) * np + i;
-                row[0] = ob[0];
+                row[0] = ob[0];                  /* rows 2..5 are converted on the device */
                 row[(size_t)np] = ob[1];
-                row[2 * (size_t)np] = (float)std::cos((double)ob[2]);
-                row[3 * (size_t)np] = (float)std::sin((double)ob[2]);
-                row[4 * (size_t)np] = (float)(1.0 / ((double)ob[3] * ob[3]));
-                row[5 * (size_t)np] = (float)(1.0 / ((double)ob[4] * ob[4]));
+                row[2 * (size_t)np] = ob[2];
+                row[4 * (size_t)np] = ob[3];
+                row[5 * (size_t)np] = ob[4];
             }
         }
         if (warm) {
@@ -598,9 +634,46 @@ int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->data + b->L.in, b->stage + b->L.in, sizeof(float) * b->L.in_n, cudaMemcpyHostToDevice,
                             b->stream);
+    if (e == cudaSuccess && b->L.T_obs > 0) e = launch_flat(2, flat_args(b), n, b->stream);
+    b->host_inputs = e == cudaSuccess;
     if (e == cudaSuccess && any_warm.load())
         e = cudaMemcpyAsync(b->data + b->L.warm, b->stage + b->L.warm, sizeof(float) * b->L.warm_n,
                             cudaMemcpyHostToDevice, b->stream);
+    return cuda_status(e);
+}
+
+int bmpc_set_problems_flat(bmpc_batch *b, const bmpc_problem *probs, const float *xref, const float *weight,
+                           const float *obs) {
+    if (!b || !probs || !xref || (b->L.T_obs > 0 && !obs)) return BMPC_ERR_INVALID;
+    const int n = b->n;
+    for (int k = 0; k < n; ++k) {
+        const bmpc_problem &P = probs[k];
+        const ProbRec &R = b->recs[k];
+        if (!P.x0 || (R.model == 2 && (!P.Alin || !P.Blin))) return BMPC_ERR_INVALID;
+        for (int j = 0; j < R.nx; ++j)
+            if (!std::isfinite(P.x0[j])) return BMPC_ERR_INVALID;
+        for (int j = 0; j < NU; ++j)
+            if (!(P.Rw[j] > 0.f)) return BMPC_ERR_INVALID;
+    }
+    for (int k = 0; k < n; ++k) {
+        copy_params(b->recs[k], probs[k]);
+        b->recs[k].has_warm = 0;
+    }
+    std::memcpy(b->stage + b->L.recs, b->recs.data(), sizeof(ProbRec) * n);
+    FlatArgs f = flat_args(b);
+    f.has_weight = weight != nullptr;
+    float *raw = at<float>(b->data, b->L.raw);
+    cudaError_t e = cudaMemcpyAsync(b->data + b->L.recs, b->stage + b->L.recs, sizeof(ProbRec) * n,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(raw, xref, sizeof(float) * b->L.T_nx, cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess && weight)
+        e = cudaMemcpyAsync(raw + b->L.T_nx, weight, sizeof(float) * b->L.T_n, cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess && b->L.T_obs > 0)
+        e = cudaMemcpyAsync(raw + b->L.T_nx + b->L.T_n, obs, sizeof(float) * b->L.T_obs, cudaMemcpyDefault,
+                            b->stream);
+    if (e == cudaSuccess) e = launch_flat(0, f, n, b->stream);
+    b->host_inputs = false;
     return cuda_status(e);
 }
 
@@ -831,7 +904,12 @@ out:
 int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats) {
     if (!b) return BMPC_ERR_INVALID;
     cudaError_t e = cudaSuccess;
-    if (x || u || lam || y)
+    if (x && !b->host_inputs) {   /* absolute states need the references of the last upload */
+        e = cudaMemcpyAsync(b->stage + b->L.in, b->data + b->L.in, sizeof(float) * b->L.in_n,
+                            cudaMemcpyDeviceToHost, b->stream);
+        b->host_inputs = e == cudaSuccess;
+    }
+    if (e == cudaSuccess && (x || u || lam || y))
         e = cudaMemcpyAsync(b->stage + b->L.out, b->data + b->L.out, sizeof(float) * b->L.out_n,
                             cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess)
@@ -902,6 +980,32 @@ int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float
     if (lam) *lam = base + (size_t)orw.lam * R.npad;
     if (y) *y = base + (size_t)orw.y * R.npad;
     if (npad) *npad = R.npad;
+    return BMPC_OK;
+}
+
+int bmpc_get_solutions_flat(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats) {
+    if (!b) return BMPC_ERR_INVALID;
+    const FlatArgs f = flat_args(b);
+    const float *raw = f.raw;
+    cudaError_t e = cudaSuccess;
+    if (x || u || lam || y) e = launch_flat(1, f, b->n, b->stream);
+    const size_t nx = sizeof(float) * (size_t)b->L.T_nx, nu = sizeof(float) * 2 * (size_t)b->L.T_n;
+    if (e == cudaSuccess && x && nx) e = cudaMemcpyAsync(x, raw, nx, cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess && u && nu) e = cudaMemcpyAsync(u, raw + b->L.T_nx, nu, cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess && lam && nx)
+        e = cudaMemcpyAsync(lam, raw + b->L.T_nx + 2 * b->L.T_n, nx, cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess && y && b->L.T_nc)
+        e = cudaMemcpyAsync(y, raw + 2 * b->L.T_nx + 2 * b->L.T_n, sizeof(float) * (size_t)b->L.T_nc,
+                            cudaMemcpyDefault, b->stream);
+    if (e != cudaSuccess) return BMPC_ERR_CUDA;
+    return bmpc_get_solutions(b, nullptr, nullptr, nullptr, nullptr, stats);   /* statistics; synchronises */
+}
+
+int bmpc_transfer_bytes_flat(const bmpc_batch *b, size_t *h2d, size_t *d2h) {
+    if (!b) return BMPC_ERR_INVALID;
+    const size_t T_n = (size_t)b->L.T_n, T_nx = (size_t)b->L.T_nx, T_nc = (size_t)b->L.T_nc;
+    if (h2d) *h2d = sizeof(ProbRec) * (size_t)b->n + sizeof(float) * (T_nx + T_n + (size_t)b->L.T_obs);
+    if (d2h) *d2h = sizeof(float) * (2 * T_nx + 2 * T_n + T_nc) + sizeof(Stats) * (size_t)b->n;
     return BMPC_OK;
 }
 

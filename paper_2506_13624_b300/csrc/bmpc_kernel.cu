@@ -1872,6 +1872,87 @@ cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order
     return cudaGetLastError();
 }
 
+/* ------------------------------------------------------------------ input transfers */
+/* Obstacle row values from the caller's heading and semi-axes: cos and sin of the heading and
+ * 1/a^2, 1/b^2, each in double precision rounded once (one definition for both upload paths). */
+__device__ __forceinline__ float obstacle_row(int c, float h, float ea, float eb) {
+    if (c == 2) return (float)cos((double)h);
+    if (c == 3) return (float)sin((double)h);
+    const double s = c == 4 ? (double)ea : (double)eb;
+    return (float)(1.0 / (s * s));
+}
+
+/* After bmpc_set_problems' copy: obstacle rows hold cx, cy, heading, -, a, b as packed by the
+ * host; rows 2..5 become cos, sin, 1/a^2, 1/b^2 in place. */
+__global__ void bmpc_obstacle_rows_kernel(FlatArgs a) {
+    const ProbRec &R = a.recs[blockIdx.x];
+    const int n = R.n, np = R.npad;
+    float *ob = a.inbase + R.off_in + (size_t)in_rows(R.nx, R.n_obs).obs * np;
+    for (int e = threadIdx.x; e < R.n_obs * n; e += blockDim.x) {
+        const int o = e / n, i = e % n;
+        float *r = ob + (size_t)(OBS_ROWS * o) * np + i;
+        const float h = r[2 * (size_t)np], ea = r[4 * (size_t)np], eb = r[5 * (size_t)np];
+        for (int c = 2; c < OBS_ROWS; ++c) r[(size_t)c * np] = obstacle_row(c, h, ea, eb);
+    }
+}
+
+/* Inputs of problem blockIdx.x from the node-major flat arrays into its component-major input
+ * region (the device side of bmpc_set_problems_flat), padding nodes zeroed. */
+__global__ void bmpc_flat_in_kernel(FlatArgs a) {
+    const ProbRec &R = a.recs[blockIdx.x];
+    const int n = R.n, np = R.npad, nx = R.nx, no = R.n_obs;
+    const InRows ir = in_rows(nx, no);
+    float *base = a.inbase + R.off_in;
+    const float *xr = a.raw + R.off_nx;
+    const float *wt = a.raw + a.T_nx + R.off_node;
+    const float *ob = a.raw + a.T_nx + a.T_n + R.off_obs;
+    const int64_t total = (int64_t)ir.total * np;
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int row = (int)(e / np), i = (int)(e % np);
+        float v = 0.f;
+        if (i < n) {
+            if (row < ir.weight) v = xr[(size_t)i * nx + row];
+            else if (row == ir.weight) v = a.has_weight ? wt[i] : 1.f;
+            else {
+                const int o = (row - ir.obs) / OBS_ROWS, c = (row - ir.obs) % OBS_ROWS;
+                const float *q = ob + ((size_t)i * no + o) * 5;   /* cx, cy, heading, a, b */
+                v = c < 2 ? q[c] : obstacle_row(c, q[2], q[3], q[4]);
+            }
+        }
+        base[e] = v;
+    }
+}
+
+/* Outputs of problem blockIdx.x into the node-major flat arrays (absolute states x = xref + xi,
+ * the same sum as the host unpacking) for bmpc_get_solutions_flat. */
+__global__ void bmpc_flat_out_kernel(FlatArgs a) {
+    const ProbRec &R = a.recs[blockIdx.x];
+    const int n = R.n, np = R.npad, nx = R.nx, nc = R.nc;
+    const OutRows orw = out_rows(nx, nc);
+    const InRows ir = in_rows(nx, R.n_obs);
+    const float *o = a.outbase + R.off_out;
+    const float *xref = a.inbase + R.off_in + (size_t)ir.xref * np;
+    float *fx = a.raw + R.off_nx;
+    float *fu = a.raw + a.T_nx + 2 * R.off_node;
+    float *fl = a.raw + a.T_nx + 2 * a.T_n + R.off_nx;
+    float *fy = a.raw + 2 * a.T_nx + 2 * a.T_n + R.off_nc;
+    for (int e = threadIdx.x; e < n * nx; e += blockDim.x) {
+        const int i = e / nx, j = e % nx;
+        fx[e] = xref[(size_t)j * np + i] + o[(size_t)(orw.x + j) * np + i];
+        fl[e] = o[(size_t)(orw.lam + j) * np + i];
+    }
+    for (int e = threadIdx.x; e < n * NU; e += blockDim.x) fu[e] = o[(size_t)(orw.u + e % NU) * np + e / NU];
+    for (int e = threadIdx.x; e < n * nc; e += blockDim.x) fy[e] = o[(size_t)(orw.y + e % nc) * np + e / nc];
+}
+
+cudaError_t launch_flat(int which, const FlatArgs &a, int n_problems, cudaStream_t stream) {
+    if (n_problems <= 0) return cudaSuccess;
+    if (which == 0) bmpc_flat_in_kernel<<<n_problems, 256, 0, stream>>>(a);
+    else if (which == 1) bmpc_flat_out_kernel<<<n_problems, 256, 0, stream>>>(a);
+    else bmpc_obstacle_rows_kernel<<<n_problems, 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
 /* ------------------------------------------------------------------ warm-start kernels */
 /* Device scatter: problem `order[blockIdx.x]` takes its start from a dense device array, node-major
  * x | u | lam | y (absolute states), into warm-start slot `slot`. */

@@ -30,6 +30,8 @@ struct alignas(16) ProbRec {
     int64_t off_warm;  /* float elements from the warm-start region base */
     int64_t off_out;   /* float elements from the output region base   */
     int64_t off_scr;   /* float elements from the scratch arena base   */
+    int64_t off_node, off_nx, off_nc, off_obs;   /* offsets in the node-major flat arrays of the batch:
+                                                    sums of n, n*nx, n*nc, n*n_obs*5 over earlier problems */
     float dt, lane_lo, lane_hi, pad1;
     float params[10];  /* L, m, Iz, lf, lr, Cf, Cr, vmin, veps, n_sub  */
     float Qw[MAX_NX], QNw[MAX_NX], Rw[NU], u_lo[NU], u_hi[NU];
@@ -75,8 +77,8 @@ __host__ __device__ inline int64_t table_ints(int npad, int n_stage, int n_paths
 }
 
 /* input region: xref[nx] weight[1] obs[6*n_obs] (rows of npad).  Per obstacle the rows hold the
- * ellipse centre cx, cy, the cosine and sine of its heading and 1/a^2, 1/b^2 (computed once by the
- * host packing from the caller's cx, cy, heading, a, b). */
+ * ellipse centre cx, cy, the cosine and sine of its heading and 1/a^2, 1/b^2, converted once per
+ * upload on the device from the caller's cx, cy, heading, a, b. */
 constexpr int OBS_ROWS = 6;
 struct InRows {
     int xref, weight, obs, total;
@@ -158,6 +160,18 @@ struct Stats {
     int32_t status, inner_iters, outer_iters, ls_fail_total, ls_evals, start_used;
     float r_kkt, c, rho, mu;
     int64_t cyc_lin, cyc_bwd, cyc_fwd, cyc_ls, cyc_total;
+};
+
+/* Node-major flat arrays of a batch in the raw region of the data arena.  Inputs: xref [T_nx] |
+ * weight [T_n] | obs [T_obs] (caller layout, 5 values per obstacle); outputs: x [T_nx] (absolute
+ * states) | u [2 T_n] | lam [T_nx] | y [T_nc]. */
+struct FlatArgs {
+    const ProbRec *recs;
+    float *inbase;
+    const float *outbase;
+    float *raw;
+    int64_t T_n, T_nx, T_nc, T_obs;
+    int32_t has_weight;
 };
 
 /* Arguments of the warm-start kernels (device scatter and receding-horizon shift). */

@@ -51,7 +51,11 @@ def test_batch_bytes_scale_with_nodes():
     rc1, d1, s1, h1 = _sizes([scenes.config1(0)])
     rc3, d3, s3, h3 = _sizes([scenes.config3(0)])
     assert rc1 == 0 and rc3 == 0
-    assert s3 > 20 * s1 and d3 > 10 * d1 and h1 == d1
+    assert s3 > 20 * s1 and d3 > 10 * d1
+    # staging mirrors the data arena up to the statistics; the device-only flat-transfer region
+    # (at least one float per node and state component) follows
+    p1 = scenes.config1(0)
+    assert h1 < d1 and d1 - h1 >= 4 * p1["n"] * (p1["nx"] + 1)
     rc, d, s, h = _sizes(scenes.config4(4, 16))
     assert rc == 0 and s % 4 == 0
 

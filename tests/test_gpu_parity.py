@@ -199,6 +199,30 @@ def test_queue_order_changes_nothing_but_the_schedule():
         assert seq == sorted(seq, reverse=True)
 
 
+def test_flat_transfers_equal_the_packed_path():
+    """Node-major flat uploads and downloads (device transposition) give the packed host path's
+    solutions bit for bit, and the packed download after a flat upload still has absolute states."""
+    from paper_2506_13624_b300 import bmpc
+    ps = scenes.config4(6, 24)
+    b = bmpc.Batch(ps)
+    b.set_problems()
+    b.solve()
+    ref = b.get_solutions()
+    b.set_problems_flat(*b.flat_inputs())
+    b.solve()
+    x, u, lam, y, st = b.get_solutions_flat(b.flat_outputs())
+    again = b.get_solutions()
+    b.close()
+    cat = lambda key: np.concatenate([r[key].astype(np.float32).ravel() for r in ref])
+    for key, got in (("x", x), ("u", u), ("lam", lam), ("y", y)):
+        want = cat(key)
+        assert np.array_equal(got.numpy()[:want.size], want), key
+    assert [s.inner_iters for s in st] == [r["inner_iters"] for r in ref]
+    for a, c in zip(ref, again):
+        for key in ("x", "u", "lam", "y"):
+            assert np.array_equal(a[key], c[key])
+
+
 def test_batch_equals_single():
     ps = scenes.config4(4, 6)
     batch = _gpu(ps, block_threads=64)
