@@ -210,48 +210,52 @@ __device__ __forceinline__ void rhs(const float *prm, const float (&s)[NX], floa
  * classical RK4 steps, Jacobians by the forward-mode chain rule through every stage (tangent
  * matrix S = dz/d(x, u)).  The increment is returned instead of f so that the defect
  * f(x_p, u_p) - x_m = (x_p - x_m) + dlt never subtracts two large absolute positions in FP32. */
-template <int NX, int MODEL>
+template <int NX, int MODEL, typename Store>
 __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], const float (&u)[NU],
-                                        float (&xn)[NX], float (&A)[NX][NX], float (&B)[NX][NU]) {
+                                        float (&xn)[NX], Store store) {
     if constexpr (MODEL == 2) {
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
             float s = 0.f;
 #pragma unroll
             for (int j = 0; j < NX; ++j) {
-                A[i][j] = R.Alin[i * NX + j];
-                s += (i == j ? A[i][j] - 1.f : A[i][j]) * x[j];
+                const float a = R.Alin[i * NX + j];
+                store(i, j, a);
+                s += (i == j ? a - 1.f : a) * x[j];
             }
 #pragma unroll
             for (int j = 0; j < NU; ++j) {
-                B[i][j] = R.Blin[i * NU + j];
-                s += B[i][j] * u[j];
+                const float b = R.Blin[i * NU + j];
+                store(i, NX + j, b);
+                s += b * u[j];
             }
             xn[i] = s;
         }
     } else {
         /* The positions X, Y never enter the vehicle right-hand side, so their tangent columns
-         * stay the unit vectors: only the columns of (psi, ..., a, delta) are propagated. */
+         * stay the unit vectors: only the columns of (psi, ..., a, delta) are propagated (forward
+         * mode through every RK4 stage), and each entry is handed to `store` as soon as it is final. */
         constexpr int C0 = 2;
         constexpr int NZ = NX + NU;
-        float S[NX][NZ];
+        constexpr int GW = NZ - C0;   /* propagated tangent columns C0 .. NZ-1 */
+        const int nsub = max(1, (int)R.params[9]);
+        const float h = R.dt / (float)nsub;
+        float S[NX][GW];
 #pragma unroll
         for (int i = 0; i < NX; ++i)
 #pragma unroll
-            for (int j = 0; j < NZ; ++j) S[i][j] = (i == j) ? 1.f : 0.f;
+            for (int j = 0; j < GW; ++j) S[i][j] = (i == C0 + j) ? 1.f : 0.f;
         float z[NX];   /* increment accumulated over the substeps */
 #pragma unroll
         for (int i = 0; i < NX; ++i) z[i] = 0.f;
-        const int nsub = max(1, (int)R.params[9]);
-        const float h = R.dt / (float)nsub;
         for (int sub = 0; sub < nsub; ++sub) {
-            float ks[NX], Ds[NX][NZ], kp[NX], Dp[NX][NZ];
+            float ks[NX], Ds[NX][GW], kp[NX], Dp[NX][GW];
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
                 ks[i] = 0.f;
                 kp[i] = 0.f;
 #pragma unroll
-                for (int j = 0; j < NZ; ++j) {
+                for (int j = 0; j < GW; ++j) {
                     Ds[i][j] = 0.f;
                     Dp[i][j] = 0.f;
                 }
@@ -265,25 +269,25 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
                 for (int i = 0; i < NX; ++i) zs[i] = x[i] + (z[i] + c * h * kp[i]);
                 float f[NX], J[NX][NX], Ju[NX][NU];
                 rhs_jac<NX, MODEL>(R.params, zs, u[0], u[1], f, J, Ju);
-                float D[NX][NZ];
 #pragma unroll
-                for (int i = 0; i < NX; ++i)
+                for (int j = 0; j < GW; ++j) {
+                    const int jj = C0 + j;
+                    float t[NX];
 #pragma unroll
-                    for (int j = C0; j < NZ; ++j) {
-                        float acc = (j >= NX) ? Ju[i][j - NX] : 0.f;
+                    for (int k = C0; k < NX; ++k) t[k] = S[k][j] + c * h * Dp[k][j];
 #pragma unroll
-                        for (int k = C0; k < NX; ++k) acc += J[i][k] * (S[k][j] + c * h * Dp[k][j]);
-                        D[i][j] = acc;
+                    for (int i = 0; i < NX; ++i) {
+                        float acc = (jj >= NX) ? Ju[i][jj - NX] : 0.f;
+#pragma unroll
+                        for (int k = C0; k < NX; ++k) acc += J[i][k] * t[k];
+                        Ds[i][j] += wg * acc;
+                        Dp[i][j] = acc;
                     }
+                }
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
                     ks[i] += wg * f[i];
                     kp[i] = f[i];
-#pragma unroll
-                    for (int j = C0; j < NZ; ++j) {
-                        Ds[i][j] += wg * D[i][j];
-                        Dp[i][j] = D[i][j];
-                    }
                 }
             }
             const float h6 = h / 6.f;
@@ -291,16 +295,14 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
             for (int i = 0; i < NX; ++i) {
                 z[i] += h6 * ks[i];
 #pragma unroll
-                for (int j = C0; j < NZ; ++j) S[i][j] += h6 * Ds[i][j];
+                for (int j = 0; j < GW; ++j) S[i][j] += h6 * Ds[i][j];
             }
         }
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
             xn[i] = z[i];
 #pragma unroll
-            for (int j = 0; j < NX; ++j) A[i][j] = S[i][j];
-#pragma unroll
-            for (int j = 0; j < NU; ++j) B[i][j] = S[i][NX + j];
+            for (int j = 0; j < GW; ++j) store(i, C0 + j, S[i][j]);
         }
     }
 }
@@ -751,23 +753,20 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
         for (int t = 0; t < NX; ++t) v += A[t][a] * pb[t];
         qx[a] = v;
     }
-    /* Cholesky of the 2x2 H_n, K = -H^-1 Qux, k = -H^-1 qu */
-    const float l00s = Quu[0][0];
-    const float l00 = sqrtf(fmaxf(l00s, 0.f));
-    const float i00 = 1.f / l00;
-    const float l10 = Quu[1][0] * i00;
-    const float l11s = Quu[1][1] - l10 * l10;
-    if (!(l00s > 0.f) || !(l11s > 0.f)) sh.flag = 1;
-    const float i11 = 1.f / sqrtf(fmaxf(l11s, 0.f));
+    /* K = -H^-1 Qux, k = -H^-1 qu with the closed-form inverse of the 2x2 H_n (one reciprocal of
+     * the determinant on the critical path; H_n must be positive definite) */
+    const float h00 = Quu[0][0], h01 = Quu[1][0], h11 = Quu[1][1];
+    const float det = h00 * h11 - h01 * h01;
+    if (!(h00 > 0.f) || !(det > 0.f)) sh.flag = 1;
+    const float idet = 1.f / det;
+    const float g00 = h11 * idet, g01 = -h01 * idet, g11 = h00 * idet;
     float Kn[NU][NX], kn[NU];
 #pragma unroll
     for (int b = 0; b < NX + 1; ++b) {
         const float rhs0 = (b < NX) ? Qux[0][b] : qu[0];
         const float rhs1 = (b < NX) ? Qux[1][b] : qu[1];
-        const float z0 = rhs0 * i00;
-        const float z1 = (rhs1 - l10 * z0) * i11;
-        const float s1 = z1 * i11;
-        const float s0 = (z0 - l10 * s1) * i00;
+        const float s0 = g00 * rhs0 + g01 * rhs1;
+        const float s1 = g01 * rhs0 + g11 * rhs1;
         if (b < NX) {
             Kn[0][b] = -s0;
             Kn[1][b] = -s1;
@@ -1198,23 +1197,15 @@ __device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V
         Hu1[a] = gshfl(Hc[a], NX + 1, gmask);
         gx[a] = gshfl(g, a, gmask);
     }
-    const float l00 = sqrtf(fmaxf(h00, 0.f));
-    const float l10 = h10 / l00;
-    const float l11s = h11 - l10 * l10;
-    if (!(h00 > 0.f) || !(l11s > 0.f)) sh.flag = 1;
-    const float l11 = sqrtf(fmaxf(l11s, 0.f));
-    /* K column `lane` and k: -H_uu^-1 (Qux column, qu) */
-    float K0 = 0.f, K1 = 0.f;
-    {
-        const float z0 = Hc[NX] / l00;
-        const float z1 = (Hc[NX + 1] - l10 * z0) / l11;
-        K1 = -(z1 / l11);
-        K0 = -((z0 + l10 * K1) / l00);
-    }
-    const float kz0 = gu0 / l00;
-    const float kz1 = (gu1 - l10 * kz0) / l11;
-    const float k1 = -(kz1 / l11);
-    const float k0 = -((kz0 + l10 * k1) / l00);
+    /* K column `lane` and k: -H_uu^-1 (Qux column, qu), closed-form 2x2 inverse as in riccati_node */
+    const float det = h00 * h11 - h10 * h10;
+    if (!(h00 > 0.f) || !(det > 0.f)) sh.flag = 1;
+    const float idet = 1.f / det;
+    const float g00 = h11 * idet, g01 = -h10 * idet, g11 = h00 * idet;
+    const float K0 = -(g00 * Hc[NX] + g01 * Hc[NX + 1]);
+    const float K1 = -(g01 * Hc[NX] + g11 * Hc[NX + 1]);
+    const float k0 = -(g00 * gu0 + g01 * gu1);
+    const float k1 = -(g01 * gu0 + g11 * gu1);
     /* new P column `lane` = H[0:nx, lane] + Qux' K[:, lane]; p = qx + Qux' k (replicated) */
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
@@ -1523,18 +1514,15 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                 V.store_u(V.hr, i, hr);
                 V.nv[i] = la;
                 if (!is_leaf) {
-                    float xa[NX], xn[NX], A[NX][NX], B[NX][NU];
+                    float xa[NX], xn[NX];
 #pragma unroll
                     for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
-                    dyn_lin<NX, MODEL>(R, xa, u, xn, A, B);
+                    /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
+                    dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
+                        if (c < NX) V.A[(size_t)(a * NX + c) * np + i] = v;
+                        else V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                    });
                     V.store_x(V.f, i, xn);
-#pragma unroll
-                    for (int a = 0; a < NX; ++a) {
-#pragma unroll
-                        for (int b = (MODEL == 2 ? 0 : 2); b < NX; ++b) V.A[(size_t)(a * NX + b) * np + i] = A[a][b];
-#pragma unroll
-                        for (int b = 0; b < NU; ++b) V.B[(size_t)(a * NU + b) * np + i] = B[a][b];
-                    }
                 }
             }
             __syncthreads();
