@@ -180,7 +180,7 @@ int bmpc_solve_batch_graph(bmpc_batch *b, const bmpc_opts *opts);
 int bmpc_set_warm_start_device(bmpc_batch *b, const float *dev_start, int64_t stride, int32_t slot);
 int bmpc_shift_warm_start(bmpc_batch *next, const bmpc_batch *prev, int32_t slot);
 
-/* Autotuner: solves the batch once per candidate launch configuration (threads per problem 64 /
+/* Autotuner: solves the batch once per candidate launch configuration (threads per problem 32 / 64 /
  * 128 / 256, sweep variant 1 / 2 / 3, line-search chunk 1 / 2 / 4; the other fields from `base`,
  * NULL = defaults), timing each with CUDA events on the handle's stream, and returns in *best the
  * configuration with the most converged solves per second and in *best_us_per_solve its time per
