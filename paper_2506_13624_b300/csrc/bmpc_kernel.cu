@@ -1448,6 +1448,23 @@ __device__ float start_merit(const ProbRec &R, const View<NX> &V, float rho, flo
     return acc[0];
 }
 
+/* The accepted step at node i: x += a dx, u += a du (in registers, caller stores) and, except at
+ * the root, lam += a (lam_QP - lam) in memory (Algorithm 1, update after the line search). */
+template <int NX>
+__device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU]) {
+    const int np = V.np;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+        x[j] += a * V.dx[(size_t)j * np + i];
+        if (i != 0) {
+            const float lm = V.L[(size_t)j * np + i];
+            V.L[(size_t)j * np + i] = lm + a * (V.lq[(size_t)j * np + i] - lm);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NU; ++j) u[j] += a * V.du[(size_t)j * np + i];
+}
+
 /* ------------------------------------------------------------------ the per-problem solver */
 template <int NX, int MODEL>
 __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
@@ -1489,6 +1506,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
     __syncthreads();
 
     float rho = O.rho0, mu = O.mu0, omega = O.omega0, eta = O.eta0;
+    float pending = 0.f;   /* step of the last line search, not yet applied to (x, u, lam) */
     float r_kkt = INFINITY, cviol = INFINITY;
     int inner = 0, outer = 0, ls_fail = 0, ls_fail_total = 0, ls_evals = 0, status = 1 /* MAX_ITER */;
     const int G = (O.ls_chunk <= 0 || O.ls_chunk > MAX_CHUNK) ? min(O.n_alpha, MAX_CHUNK) : O.ls_chunk;
@@ -1498,13 +1516,19 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
     while (outer < O.max_outer) {
         ++outer;
         for (;;) {
-            /* ===== linearise + quadratise at the current point */
+            /* ===== linearise + quadratise at the current point (first applying the step of the
+             * previous line search, node by node: x += a dx, u += a du, lam += a (lam_QP - lam)) */
             long long t0 = clock64();
             for (int i = tid; i < n; i += nt) {
                 const bool is_leaf = V.nchild[i] == 0;
                 float x[NX], u[NU], q[NX], r[NU], hq[3], hr[NU];
                 V.load_x(V.X, i, x);
                 V.load_u(V.U, i, u);
+                if (pending > 0.f) {
+                    apply_step<NX>(V, i, pending, x, u);
+                    V.store_x(V.X, i, x);
+                    V.store_u(V.U, i, u);
+                }
                 const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, rho, q, r, hq, hr);
                 V.store_x(V.q, i, q);
                 V.store_u(V.r, i, r);
@@ -1526,6 +1550,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                 }
             }
             __syncthreads();
+            pending = 0.f;
             /* ===== defects and the KKT residual of the relaxed problem */
             float rk = 0.f;
             float sums[3] = {0.f, 0.f, 0.f};   /* L_a, lam'd, |d|^2 */
@@ -1691,23 +1716,20 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                 ++ls_fail;
                 ++ls_fail_total;
             }
-            /* ===== update x, u, lam */
-            for (int i = tid; i < n; i += nt) {
-#pragma unroll
-                for (int j = 0; j < NX; ++j) {
-                    V.X[(size_t)j * np + i] += alpha * V.dx[(size_t)j * np + i];
-                    if (i != 0) {
-                        const float lm = V.L[(size_t)j * np + i];
-                        V.L[(size_t)j * np + i] = lm + alpha * (V.lq[(size_t)j * np + i] - lm);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < NU; ++j) V.U[(size_t)j * np + i] += alpha * V.du[(size_t)j * np + i];
-            }
-            __syncthreads();
+            /* ===== the step x, u, lam += alpha (...) is applied by the next linearisation */
+            pending = alpha;
             c_ls += clock64() - t0;
             ++inner;
             if (ls_fail >= 3) {
+                for (int i = tid; i < n; i += nt) {
+                    float x[NX], u[NU];
+                    V.load_x(V.X, i, x);
+                    V.load_u(V.U, i, u);
+                    apply_step<NX>(V, i, pending, x, u);
+                    V.store_x(V.X, i, x);
+                    V.store_u(V.U, i, u);
+                }
+                __syncthreads();
                 status = 2;
                 goto done;
             }
