@@ -112,7 +112,8 @@ typedef struct {
                                depend on it: it only trades parallel work for extra rounds. */
     int32_t block_threads;  /* threads per problem (32..1024, multiple of 32); 0 = automatic */
     int32_t blocks_per_sm;  /* resident problems per SM; 0 = automatic */
-    int32_t variant;        /* tree sweeps: 0 automatic (= 2), 1 level-synchronous (one barrier per stage,
+    int32_t variant;        /* tree sweeps: 0 automatic by tree shape (2 when the tree has at most as many
+                               scenario paths as threads per problem, else 1), 1 level-synchronous (one barrier per stage,
                                nodes of a stage in parallel), 2 per-scenario-path (one thread per
                                root-to-leaf path, barriers only at branch stages), 3 per-scenario-path
                                with 8 lanes per path (lane j owns column j of [A B], P and H);

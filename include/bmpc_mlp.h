@@ -58,9 +58,15 @@ int bmpc_mlp_train_step(const bmpc_mlp_layer *layers, int32_t n_layers, const ui
                         void *stream);
 
 /* C [M][N] (fp32) = op(A) op(B) with op(A) [M][K], op(B) [K][N]; trans_a: A stored [K][M]; trans_b:
- * B stored [N][K]; lda/ldb/ldc are row lengths of the stored matrices. */
+ * B stored [N][K]; lda/ldb/ldc are row lengths of the stored matrices.  M and N must be multiples
+ * of 128, K of 32 and the row lengths of 8 (else -1); runs on the tcgen05 tensor cores. */
 int bmpc_mlp_gemm(const uint16_t *A, int32_t lda, int32_t trans_a, const uint16_t *B, int32_t ldb, int32_t trans_b,
                   float *C, int32_t ldc, int32_t M, int32_t N, int32_t K, void *stream);
+
+/* Waits for `stream`, then reports whether a GEMM gave up waiting for its tensor-core MMAs since the
+ * last call (each mbarrier wait is bounded at about 2 s): 0 none, BMPC_ERR_TIMEOUT (-4) one did
+ * (its output tile was not written; the flag is cleared), BMPC_ERR_CUDA (-2) on a CUDA error. */
+int bmpc_mlp_status(void *stream);
 
 /* ---- glue with a BMPC batch (all problems must share one tree) ----
  * Features of problem k (fp32, feat + k*dim): x0 without its X coordinate (nx - 1 values), then for

@@ -1511,7 +1511,10 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
     int inner = 0, outer = 0, ls_fail = 0, ls_fail_total = 0, ls_evals = 0, status = 1 /* MAX_ITER */;
     const int G = (O.ls_chunk <= 0 || O.ls_chunk > MAX_CHUNK) ? min(O.n_alpha, MAX_CHUNK) : O.ls_chunk;
     /* sweeps: 1 level-synchronous, 2 (default) per-path with one thread per path, 3 per-path with 8 lanes */
-    const int variant = (O.variant == 1 || O.variant == 3) ? O.variant : 2;
+    /* automatic choice by tree shape: one thread per scenario path while the paths fit the block,
+     * else stage by stage (a thread would otherwise walk several paths one after another) */
+    const int variant = (O.variant == 1 || O.variant == 3) ? O.variant
+                        : (O.variant == 2 || R.n_paths <= nt) ? 2 : 1;
 
     while (outer < O.max_outer) {
         ++outer;

@@ -2,10 +2,15 @@
  * Learned warm start: a multilayer perceptron with BF16 weights and activations, FP32
  * accumulation, trained and evaluated by the kernels in this file.
  *
- *   gemm_bf16<TA, TB, EPI>   C[M x N] = op(A)[M x K] op(B)[K x N] on the tensor cores
- *                            (mma.sync m16n8k16 bf16 -> f32), operands staged in shared memory by
- *                            cp.async with double buffering and read with ldmatrix; op(X) is X or
- *                            X^T.  Epilogues: plain f32 (weight gradients), + bias in f32 (output
+ *   gemm_tc<TA, TB, EPI>     C[M x N] = op(A)[M x K] op(B)[K x N] on the 5th-generation tensor
+ *                            cores: tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) issued by one
+ *                            thread from shared-memory descriptors, the 128 x 128 accumulator in
+ *                            tensor memory (TMEM), operand tiles staged by cp.async in a 4-stage
+ *                            ring whose stages are reused once an mbarrier reports the MMAs that
+ *                            read them complete; the epilogue reads TMEM with tcgen05.ld.  op(X) is
+ *                            X or X^T: K-major and MN-major operands are both laid out in the
+ *                            canonical no-swizzle core-matrix form (8 rows x 16 bytes).
+ *                            Epilogues: plain f32 (weight gradients), + bias in f32 (output
  *                            layer), + bias then GELU in bf16 with the pre-activation kept (hidden
  *                            layers), times GELU'(pre) in bf16 (back-propagation through a hidden
  *                            layer).
@@ -14,7 +19,7 @@
  *   adamw                    AdamW on fp32 master weights, refreshing the bf16 copy.
  *   init                     uniform(-1/sqrt(in), 1/sqrt(in)) weights from a counter-based hash.
  *
- * Every matrix is row-major with dimensions that are multiples of 128 (the host pads).
+ * Every matrix is row-major; M and N are multiples of 128 and K of 32 (the host pads).
  */
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -23,10 +28,11 @@
 
 namespace bmpc_mlp {
 
-constexpr int BM = 128, BN = 128, BK = 32, THREADS = 256;
-constexpr int LD_MK = BK + 8;     /* padded row length of a [128][32] tile (bf16) */
-constexpr int LD_KM = BM + 8;     /* padded row length of a [32][128] tile (bf16) */
-constexpr int TILE = 128 * LD_MK > BK * LD_KM ? 128 * LD_MK : BK * LD_KM;
+constexpr int BM = 128, BN = 128, BK = 32, THREADS = 128, NSTAGE = 4;
+constexpr int TILE_BYTES = 128 * BK * 2;                       /* one 128 x 32 bf16 operand tile */
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;                    /* A and B tiles of one k-step */
+constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES;                /* 64 KB of dynamic shared memory */
+constexpr int TMEM_COLS = 128;                                 /* FP32 accumulator: 128 lanes x 128 */
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_DGELU = 3 };
 
@@ -40,147 +46,216 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
-/* Copy one 128 x 32 (MK) or 32 x 128 (KM) bf16 tile from global into a padded shared tile. */
-template <bool KM>
-__device__ __forceinline__ void load_tile(__nv_bfloat16 *s, const __nv_bfloat16 *g, int ld, int r0, int c0) {
+/* ------------------------------------------------------------------ tcgen05 GEMM */
+__device__ int g_gemm_timeout;   /* set when an mbarrier wait of a GEMM gave up (read by bmpc_mlp_status) */
+
+/* Shared-memory matrix descriptor of a canonical no-swizzle operand tile: start address, byte
+ * offset between core matrices along K (leading, 128) and along M/N (stride, BK/8 cores of 128 B),
+ * descriptor version 1, no swizzle.  Both majors use the same offsets; the major is in the
+ * instruction descriptor and in how the 16-byte rows of a core matrix are filled. */
+__device__ __forceinline__ uint64_t tile_desc(uint32_t addr) {
+    constexpr uint64_t LBO = 128, SBO = (BK / 8) * 128;
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((LBO >> 4) << 16) | ((SBO >> 4) << 32) | (1ull << 46);
+}
+
+/* Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5), BF16 A and B
+ * (bits 7-9, 10-12), A and B majors (bit 15, 16: 0 K-major, 1 M/N-major), N/8 (bits 17-22),
+ * M/16 (bits 24-28). */
+__host__ __device__ constexpr uint32_t mma_idesc(bool a_mn, bool b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+/* Stage the 128 x BK slice of an operand into the canonical layout: core matrix (row group g, k
+ * chunk c) of 8 rows x 16 bytes at byte (g * BK/8 + c) * 128.  KMAJ: the stored matrix runs along
+ * k, row r of the tile at g + (r0 + r) ld + k0, and a 16-byte row of a core matrix is 8 k of one
+ * tile row.  Otherwise it runs along the tile rows, element (r, k) at g + (k0 + k) ld + r0 + r, and
+ * a 16-byte row of a core matrix is 8 tile rows of one k. */
+template <bool KMAJ>
+__device__ __forceinline__ void stage_tile(unsigned char *s, const __nv_bfloat16 *g, int ld, int r0, int k0) {
     const int t = threadIdx.x;
 #pragma unroll
-    for (int rep = 0; rep < 2; ++rep) {
-        const int idx = t + rep * THREADS;          /* 512 chunks of 8 elements */
-        if (!KM) {
-            const int r = idx >> 2, c = (idx & 3) * 8;
-            cp_async16(s + r * LD_MK + c, g + (size_t)(r0 + r) * ld + c0 + c);
+    for (int rep = 0; rep < (128 * BK / 8) / THREADS; ++rep) {      /* 512 chunks of 8 elements */
+        const int idx = t + rep * THREADS;
+        if (KMAJ) {
+            const int r = idx >> 2, c = idx & 3;                     /* tile row, k chunk */
+            cp_async16(s + ((r >> 3) * (BK / 8) + c) * 128 + (r & 7) * 16, g + (size_t)(r0 + r) * ld + k0 + c * 8);
         } else {
-            const int r = idx >> 4, c = (idx & 15) * 8;
-            cp_async16(s + r * LD_KM + c, g + (size_t)(r0 + r) * ld + c0 + c);
+            const int k = idx >> 4, gr = idx & 15;                   /* k, tile row group */
+            cp_async16(s + (gr * (BK / 8) + (k >> 3)) * 128 + (k & 7) * 16,
+                       g + (size_t)(k0 + k) * ld + r0 + gr * 8);
         }
     }
 }
 
-/* C = op(A) op(B).  TA: A is given transposed (stored K x M); TB: B is given transposed (stored
- * N x K).  lda/ldb are the row lengths of the stored matrices, ldc of C. */
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(THREADS) gemm_bf16(const __nv_bfloat16 *__restrict__ A, int lda,
-                                                      const __nv_bfloat16 *__restrict__ B, int ldb, void *C, int ldc,
-                                                      int K, const float *__restrict__ bias,
-                                                      __nv_bfloat16 *__restrict__ pre) {
-    __shared__ __align__(16) __nv_bfloat16 sA[2][TILE];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][TILE];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
-    float acc[4][4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+/* Waits (at most about 2 s of SM clock) for the phase of `bar` with the given parity; 0 on timeout. */
+__device__ __forceinline__ int mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    const long long t0 = clock64();
+    do {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return 1;
+    } while (clock64() - t0 < 4000000000ll);
+    return 0;
+}
 
-    auto load_stage = [&](int st, int k0) {
-        if (!TA) load_tile<false>(sA[st], A, lda, m0, k0);     /* A[m][k] */
-        else load_tile<true>(sA[st], A, lda, k0, m0);          /* A^T stored [k][m] */
-        if (!TB) load_tile<true>(sB[st], B, ldb, k0, n0);      /* B[k][n] */
-        else load_tile<false>(sB[st], B, ldb, n0, k0);         /* B^T stored [n][k] */
-        cp_commit();
-    };
+/* 32 consecutive accumulator columns of this thread's TMEM lane. */
+__device__ __forceinline__ void tmem_ld32(uint32_t (&r)[32], uint32_t taddr) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+/* C = op(A) op(B) for one 128 x 128 tile of C per block (4 warps).  TA: A is given transposed
+ * (stored K x M); TB: B is given transposed (stored N x K).  lda/ldb are the row lengths of the
+ * stored matrices, ldc of C.  Thread 0 issues the MMAs (BK/16 per k-step) and commits each k-step
+ * to the mbarrier of its stage; a stage is refilled two k-steps later, after that mbarrier phase.
+ * Warp w reads accumulator lanes 32w .. 32w + 31 (rows of C) in the epilogue. */
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(THREADS) gemm_tc(const __nv_bfloat16 *__restrict__ A, int lda,
+                                                    const __nv_bfloat16 *__restrict__ B, int ldb, void *C, int ldc,
+                                                    int K, const float *__restrict__ bias,
+                                                    __nv_bfloat16 *__restrict__ pre) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[NSTAGE];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int KT = K / BK;
-    load_stage(0, 0);
-    const int mat = lane >> 3, r8 = lane & 7;
-    for (int kt = 0; kt < KT; ++kt) {
-        if (kt + 1 < KT) {
-            load_stage((kt + 1) & 1, (kt + 1) * BK);
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
-        __syncthreads();
-        const __nv_bfloat16 *a = sA[kt & 1], *b = sB[kt & 1];
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[4][4], bf[2][4];
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi) {
-                const int mb = wm + mi * 16;
-                if (!TA) {
-                    const int m = mb + r8 + ((mat & 1) ? 8 : 0), k = kk + ((mat >= 2) ? 8 : 0);
-                    ldsm_x4(af[mi], a + m * LD_MK + k);
-                } else {
-                    const int k = kk + r8 + ((mat >= 2) ? 8 : 0), m = mb + ((mat & 1) ? 8 : 0);
-                    ldsm_x4_t(af[mi], a + k * LD_KM + m);
-                }
-            }
-#pragma unroll
-            for (int nj = 0; nj < 2; ++nj) {
-                const int nb = wn + nj * 16;
-                if (TB) {
-                    const int n = nb + r8 + ((mat >= 2) ? 8 : 0), k = kk + ((mat & 1) ? 8 : 0);
-                    ldsm_x4(bf[nj], b + n * LD_MK + k);
-                } else {
-                    const int k = kk + r8 + ((mat & 1) ? 8 : 0), n = nb + ((mat >= 2) ? 8 : 0);
-                    ldsm_x4_t(bf[nj], b + k * LD_KM + n);
-                }
-            }
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni)
-                    mma16816(acc[mi][ni], af[mi], bf[ni >> 1][(ni & 1) * 2], bf[ni >> 1][(ni & 1) * 2 + 1]);
-        }
-        __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    /* epilogue */
+    if (tid == 0)
+        for (int s = 0; s < NSTAGE; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[s])));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    constexpr uint32_t idesc = mma_idesc(TA, !TB);
+
+    auto stage = [&](int kt) {
+        unsigned char *sa = smem + (kt % NSTAGE) * STAGE_BYTES, *sb = sa + TILE_BYTES;
+        const int k0 = kt * BK;
+        stage_tile<!TA>(sa, A, lda, m0, k0);
+        stage_tile<TB>(sb, B, ldb, n0, k0);
+    };
+    int ok = 1;
 #pragma unroll
-    for (int mi = 0; mi < 4; ++mi)
+    for (int p = 0; p < 2; ++p) {
+        if (p < KT) stage(p);
+        cp_commit();
+    }
+    for (int kt = 0; kt < KT; ++kt) {
+        if (kt >= 2) ok &= mbar_wait(&mbar[(kt - 2) % NSTAGE], ((kt - 2) / NSTAGE) & 1);
+        if (kt + 2 < KT) stage(kt + 2);
+        cp_commit();
+        cp_wait<2>();   /* the tile of this k-step has landed */
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_addr(smem + (kt % NSTAGE) * STAGE_BYTES), sb = sa + TILE_BYTES;
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
+            for (int j = 0; j < BK / 16; ++j) {
+                const uint64_t da = tile_desc(sa + j * 256), db = tile_desc(sb + j * 256);
+                const uint32_t accumulate = (kt | j) != 0;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                             "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&mbar[kt % NSTAGE]))
+                         : "memory");
+        }
+    }
+    ok &= mbar_wait(&mbar[(KT - 1) % NSTAGE], ((KT - 1) / NSTAGE) & 1);   /* every MMA of the tile done */
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int r = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int cc = 0; cc < BN / 32; ++cc) {
+            uint32_t v[32];
+            tmem_ld32(v, tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32));
+            const int c0 = n0 + cc * 32;
+            const size_t o = (size_t)r * ldc + c0;
+            if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
+                float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(C) + o);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = m0 + wm + mi * 16 + (lane >> 2) + h * 8;
-                const int c = n0 + wn + ni * 8 + (lane & 3) * 2;
-                float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
-                const size_t o = (size_t)r * ldc + c;
-                if (EPI == EPI_F32) {
-                    *reinterpret_cast<float2 *>(static_cast<float *>(C) + o) = make_float2(v0, v1);
-                } else if (EPI == EPI_BIAS_F32) {
-                    v0 += bias[c];
-                    v1 += bias[c + 1];
-                    *reinterpret_cast<float2 *>(static_cast<float *>(C) + o) = make_float2(v0, v1);
-                } else if (EPI == EPI_BIAS_GELU) {
-                    const __nv_bfloat162 pz = __floats2bfloat162_rn(v0 + bias[c], v1 + bias[c + 1]);
-                    *reinterpret_cast<__nv_bfloat162 *>(pre + o) = pz;
-                    const float2 pf = __bfloat1622float2(pz);
-                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + o) =
-                        __floats2bfloat162_rn(gelu(pf.x), gelu(pf.y));
-                } else {   /* EPI_DGELU: dX = (dY W^T) * gelu'(pre) */
-                    const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(pre + o));
-                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + o) =
-                        __floats2bfloat162_rn(v0 * gelu_grad(pf.x), v1 * gelu_grad(pf.y));
+                for (int q = 0; q < 8; ++q) {
+                    float4 f = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                           __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+                    if (EPI == EPI_BIAS_F32) {
+                        f.x += bias[c0 + 4 * q];
+                        f.y += bias[c0 + 4 * q + 1];
+                        f.z += bias[c0 + 4 * q + 2];
+                        f.w += bias[c0 + 4 * q + 3];
+                    }
+                    dst[q] = f;
+                }
+            } else if (EPI == EPI_BIAS_GELU) {
+                uint4 *dp = reinterpret_cast<uint4 *>(pre + o);
+                uint4 *dc = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(C) + o);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t pz[4], az[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int j = 8 * q + 2 * h;
+                        pz[h] = pack_bf16(__uint_as_float(v[j]) + bias[c0 + j], __uint_as_float(v[j + 1]) + bias[c0 + j + 1]);
+                        const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pz[h]));
+                        az[h] = pack_bf16(gelu(pf.x), gelu(pf.y));
+                    }
+                    dp[q] = make_uint4(pz[0], pz[1], pz[2], pz[3]);
+                    dc[q] = make_uint4(az[0], az[1], az[2], az[3]);
+                }
+            } else {   /* EPI_DGELU: dX = (dY W^T) * gelu'(pre) */
+                const uint4 *sp = reinterpret_cast<const uint4 *>(pre + o);
+                uint4 *dc = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(C) + o);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 pq = sp[q];
+                    const uint32_t pw[4] = {pq.x, pq.y, pq.z, pq.w};
+                    uint32_t oz[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int j = 8 * q + 2 * h;
+                        const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pw[h]));
+                        oz[h] = pack_bf16(__uint_as_float(v[j]) * gelu_grad(pf.x), __uint_as_float(v[j + 1]) * gelu_grad(pf.y));
+                    }
+                    dc[q] = make_uint4(oz[0], oz[1], oz[2], oz[3]);
                 }
             }
+        }
+    } else if (lane == 0) {
+        atomicExch(&g_gemm_timeout, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 /* loss = mean (pred - target)^2 over rows x cols; dY = 2 (pred - target) / (rows cols) in bf16. */
@@ -274,10 +349,17 @@ bool dims_ok(int M, int N, int K) { return M > 0 && N > 0 && K > 0 && M % BM == 
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ldc, int M, int N, int K, const float *bias,
                  void *pre, cudaStream_t s) {
+    static bool attr = false;   /* 64 KB of dynamic shared memory needs the opt-in, once per instance */
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(gemm_tc<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   GEMM_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     dim3 grid(N / BN, M / BM);
-    gemm_bf16<TA, TB, EPI><<<grid, THREADS, 0, s>>>(static_cast<const __nv_bfloat16 *>(A), lda,
-                                                    static_cast<const __nv_bfloat16 *>(B), ldb, C, ldc, K, bias,
-                                                    static_cast<__nv_bfloat16 *>(pre));
+    gemm_tc<TA, TB, EPI><<<grid, THREADS, GEMM_SMEM, s>>>(static_cast<const __nv_bfloat16 *>(A), lda,
+                                                          static_cast<const __nv_bfloat16 *>(B), ldb, C, ldc, K, bias,
+                                                          static_cast<__nv_bfloat16 *>(pre));
     return cudaGetLastError();
 }
 
@@ -383,7 +465,8 @@ int bmpc_mlp_standardize(const float *raw, const float *mean, const float *std, 
 
 int bmpc_mlp_gemm(const uint16_t *A, int32_t lda, int32_t trans_a, const uint16_t *B, int32_t ldb, int32_t trans_b,
                   float *C, int32_t ldc, int32_t M, int32_t N, int32_t K, void *stream) {
-    if (!dims_ok(M, N, K) || !A || !B || !C) return -1;
+    /* 16-byte rows for the cp.async staging and the vector stores of the epilogue */
+    if (!dims_ok(M, N, K) || !A || !B || !C || lda % 8 || ldb % 8 || ldc % 8) return -1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (!trans_a && !trans_b) e = gemm<false, false, EPI_F32>(A, lda, B, ldb, C, ldc, M, N, K, nullptr, nullptr, s);
@@ -391,6 +474,16 @@ int bmpc_mlp_gemm(const uint16_t *A, int32_t lda, int32_t trans_a, const uint16_
     else if (!trans_a && trans_b) e = gemm<false, true, EPI_F32>(A, lda, B, ldb, C, ldc, M, N, K, nullptr, nullptr, s);
     else e = gemm<true, true, EPI_F32>(A, lda, B, ldb, C, ldc, M, N, K, nullptr, nullptr, s);
     return e == cudaSuccess ? 0 : -2;
+}
+
+int bmpc_mlp_status(void *stream) {
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return -2;
+    int flag = 0;
+    if (cudaMemcpyFromSymbol(&flag, g_gemm_timeout, sizeof flag) != cudaSuccess) return -2;
+    if (!flag) return 0;
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_gemm_timeout, &zero, sizeof zero);
+    return -4;
 }
 
 }  // extern "C"

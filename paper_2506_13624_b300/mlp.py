@@ -36,6 +36,7 @@ def _setup():
                                       C.c_float, C.c_int32, C.POINTER(Work), C.c_void_p]
     L.bmpc_mlp_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                 C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
+    L.bmpc_mlp_status.argtypes = [C.c_void_p]
     L.bmpc_mlp_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32]
     L.bmpc_mlp_targets.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
     L.bmpc_mlp_start.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
@@ -126,6 +127,12 @@ class MLP:
                                             x.shape[0], lr, weight_decay, self.step_count, C.byref(w),
                                             _stream(self.torch)), "bmpc_mlp_train_step")
         return loss
+
+
+def status():
+    """Synchronise the current stream; raise if a GEMM gave up waiting for its MMAs."""
+    import torch
+    _check(_setup().bmpc_mlp_status(_stream(torch)), "bmpc_mlp_status")
 
 
 def features(batch, out, n_scen, n_obs):

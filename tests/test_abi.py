@@ -29,6 +29,16 @@ def test_library_exports_every_declared_symbol():
     assert set(declared) == set(bmpc.EXPORTED)
 
 
+def test_library_exports_every_mlp_symbol():
+    src = open(os.path.join(ROOT, "include", "bmpc_mlp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(bmpc_mlp_[a-z_]+)\s*\(", src))
+    assert len(names) >= 9
+    L = bmpc.lib()
+    for name in names:
+        assert hasattr(L, name), name
+
+
 def test_version_and_status_strings():
     assert b"sm_103a" in bmpc.lib().bmpc_version()
     for s in (0, 1, 2, -1, -2, -3, -4, -5):

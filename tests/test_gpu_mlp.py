@@ -19,14 +19,17 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+@pytest.mark.parametrize("K", [160, 1024])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
-def test_gemm_variants_match_fp64(ta, tb):
+def test_gemm_variants_match_fp64(ta, tb, K):
+    """Every operand major on the tcgen05 path; K = 1024 cycles the 4-stage ring eight times."""
     from paper_2506_13624_b300 import mlp
-    rng = np.random.default_rng(int(ta) * 2 + int(tb))
-    M, N, K = 256, 384, 160
+    rng = np.random.default_rng(int(ta) * 2 + int(tb) + K)
+    M, N = 256, 384
     A = mlp_ref.bf16(rng.standard_normal((K, M) if ta else (M, K)))
     B = mlp_ref.bf16(rng.standard_normal((N, K) if tb else (K, N)))
     C = mlp.gemm(_bf(A), _bf(B), ta, tb).cpu().numpy()
+    mlp.status()
     ref = (A.T if ta else A) @ (B.T if tb else B)
     assert _rel(C, ref) < 1e-5
 
@@ -43,15 +46,18 @@ def _net_and_ref(dims, seed=0):
 
 
 def test_forward_matches_reference():
+    from paper_2506_13624_b300 import mlp
     dims = [256, 128, 128, 384]
     net, Ws, bs = _net_and_ref(dims)
     x = mlp_ref.bf16(np.random.default_rng(1).standard_normal((128, dims[0])))
     pred = net.forward(_bf(x)).cpu().numpy()
+    mlp.status()
     ref, _ = mlp_ref.forward(Ws, bs, x, bf=True)
     assert _rel(pred, ref) < 5e-3
 
 
 def test_training_step_gradients_and_adamw_match_reference():
+    from paper_2506_13624_b300 import mlp
     dims = [256, 128, 128, 384]
     net, Ws, bs = _net_and_ref(dims, seed=3)
     rng = np.random.default_rng(2)
@@ -59,6 +65,7 @@ def test_training_step_gradients_and_adamw_match_reference():
     t = mlp_ref.bf16(rng.standard_normal((128, dims[-1])))
     w_before = [p["w"].cpu().numpy().astype(np.float64) for p in net.params]
     loss = float(net.train_step(_bf(x), _bf(t), lr=1e-3, weight_decay=1e-2))
+    mlp.status()
     rl, dWs, dbs = mlp_ref.loss_and_grads(Ws, bs, x, t, bf=True)
     assert abs(loss - rl) < 1e-3 * rl
     for l, p in enumerate(net.params):
