@@ -41,6 +41,8 @@ typedef struct {
     uint16_t *dy0, *dy1;                   /* back-propagated gradients, [batch][widest layer] each */
     float *pred;                           /* network output [batch][out_last] (fp32) */
     float *loss;                           /* device scalar: mean squared error of the last step */
+    float *splitk;                         /* split-K workspace (NULL: GEMMs are not split) */
+    int64_t splitk_floats;                 /* its size, bmpc_mlp_workspace_floats for this batch */
 } bmpc_mlp_work;
 
 /* Weights uniform in [-1/sqrt(in), 1/sqrt(in)) from SplitMix64 of (seed, index); bias and moments 0. */
@@ -62,6 +64,13 @@ int bmpc_mlp_train_step(const bmpc_mlp_layer *layers, int32_t n_layers, const ui
  * of 128, K of 32 and the row lengths of 8 (else -1); runs on the tcgen05 tensor cores. */
 int bmpc_mlp_gemm(const uint16_t *A, int32_t lda, int32_t trans_a, const uint16_t *B, int32_t ldb, int32_t trans_b,
                   float *C, int32_t ldc, int32_t M, int32_t N, int32_t K, void *stream);
+
+/* Floats of split-K workspace the forward pass and training step need for this batch size: GEMMs
+ * with fewer 128 x 128 output tiles than SMs and a long K (the hidden layers, the back-propagation
+ * through the output layer) are split along K into partial products that a reduction kernel sums
+ * in a fixed order, so results do not depend on the split.  0 when nothing splits, -1 on invalid
+ * layers or batch. */
+int64_t bmpc_mlp_workspace_floats(const bmpc_mlp_layer *layers, int32_t n_layers, int32_t batch);
 
 /* Waits for `stream`, then reports whether a GEMM gave up waiting for its tensor-core MMAs since the
  * last call (each mbarrier wait is bounded at about 2 s): 0 none, BMPC_ERR_TIMEOUT (-4) one did

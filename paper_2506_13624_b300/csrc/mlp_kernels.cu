@@ -26,6 +26,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 namespace bmpc_mlp {
 
 constexpr int BM = 128, BN = 128, BK = 32, THREADS = 128, NSTAGE = 4;
@@ -136,13 +138,17 @@ template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(THREADS) gemm_tc(const __nv_bfloat16 *__restrict__ A, int lda,
                                                     const __nv_bfloat16 *__restrict__ B, int ldb, void *C, int ldc,
                                                     int K, const float *__restrict__ bias,
-                                                    __nv_bfloat16 *__restrict__ pre) {
+                                                    __nv_bfloat16 *__restrict__ pre, int kps, int64_t c_split) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[NSTAGE];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int KT = K / BK;
+    /* split K: block z takes k-steps [z kps, min(K/BK, (z+1) kps)) and writes its partial product
+     * (EPI_F32) to C + z c_split */
+    const int kbeg = blockIdx.z * kps;
+    const int KT = min(K / BK - kbeg, kps);
+    C = static_cast<float *>(C) + (EPI == EPI_F32 ? blockIdx.z * c_split : 0);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                      "r"(TMEM_COLS));
@@ -159,7 +165,7 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __nv_bfloat16 *__restri
 
     auto stage = [&](int kt) {
         unsigned char *sa = smem + (kt % NSTAGE) * STAGE_BYTES, *sb = sa + TILE_BYTES;
-        const int k0 = kt * BK;
+        const int k0 = (kbeg + kt) * BK;
         stage_tile<!TA>(sa, A, lda, m0, k0);
         stage_tile<TB>(sb, B, ldb, n0, k0);
     };
@@ -258,6 +264,38 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __nv_bfloat16 *__restri
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+/* Split-K reduction: C = epilogue(sum over the S partial products in ws, in split order). */
+template <int EPI>
+__global__ void splitk_reduce(const float *__restrict__ ws, int S, int M, int N, void *C, int ldc,
+                              const float *__restrict__ bias, __nv_bfloat16 *__restrict__ pre) {
+    const int64_t pairs = (int64_t)M * N / 2;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < pairs; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = 2 * p;
+        const int r = (int)(e / N), c = (int)(e % N);
+        float v0 = 0.f, v1 = 0.f;
+        for (int z = 0; z < S; ++z) {
+            const float2 w = *reinterpret_cast<const float2 *>(ws + (int64_t)z * M * N + e);
+            v0 += w.x;
+            v1 += w.y;
+        }
+        const size_t o = (size_t)r * ldc + c;
+        if (EPI == EPI_F32) {
+            *reinterpret_cast<float2 *>(static_cast<float *>(C) + o) = make_float2(v0, v1);
+        } else if (EPI == EPI_BIAS_F32) {
+            *reinterpret_cast<float2 *>(static_cast<float *>(C) + o) = make_float2(v0 + bias[c], v1 + bias[c + 1]);
+        } else if (EPI == EPI_BIAS_GELU) {
+            const uint32_t pz = pack_bf16(v0 + bias[c], v1 + bias[c + 1]);
+            *reinterpret_cast<uint32_t *>(pre + o) = pz;
+            const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pz));
+            *reinterpret_cast<uint32_t *>(static_cast<__nv_bfloat16 *>(C) + o) = pack_bf16(gelu(pf.x), gelu(pf.y));
+        } else {
+            const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(pre + o));
+            *reinterpret_cast<uint32_t *>(static_cast<__nv_bfloat16 *>(C) + o) =
+                pack_bf16(v0 * gelu_grad(pf.x), v1 * gelu_grad(pf.y));
+        }
+    }
+}
+
 /* loss = mean (pred - target)^2 over rows x cols; dY = 2 (pred - target) / (rows cols) in bf16. */
 __global__ void mse_grad(const float *__restrict__ pred, const __nv_bfloat16 *__restrict__ tgt, __nv_bfloat16 *dy,
                          int64_t count, float scale, float *loss) {
@@ -346,20 +384,55 @@ using namespace bmpc_mlp;
 
 bool dims_ok(int M, int N, int K) { return M > 0 && N > 0 && K > 0 && M % BM == 0 && N % BN == 0 && K % BK == 0; }
 
+/* K-steps per split for a GEMM with few output tiles: enough splits to give every SM about two
+ * blocks, at least 8 k-steps each; returns K/BK (one split) when splitting does not pay. */
+int split_kps(int M, int N, int K) {
+    const int tiles = (M / BM) * (N / BN), KT = K / BK;
+    if (tiles >= 148) return KT;
+    int S = std::min((2 * 148 + tiles - 1) / tiles, KT / 8);
+    if (S < 2) return KT;
+    return (KT + S - 1) / S;
+}
+
+int64_t split_floats(int M, int N, int K) {
+    const int kps = split_kps(M, N, K), KT = K / BK;
+    return kps >= KT ? 0 : (int64_t)((KT + kps - 1) / kps) * M * N;
+}
+
+template <bool TA, bool TB, int EPI>
+cudaError_t set_smem() {
+    static bool done = false;   /* 64 KB of dynamic shared memory needs the opt-in, once per instance */
+    if (done) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(gemm_tc<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    done = e == cudaSuccess;
+    return e;
+}
+
+/* C = epilogue(op(A) op(B)); GEMMs with few output tiles and a long K are split along K into the
+ * workspace ws (ws_floats floats, may be 0) and reduced in split order by splitk_reduce. */
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ldc, int M, int N, int K, const float *bias,
-                 void *pre, cudaStream_t s) {
-    static bool attr = false;   /* 64 KB of dynamic shared memory needs the opt-in, once per instance */
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(gemm_tc<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   GEMM_SMEM);
+                 void *pre, cudaStream_t s, float *ws = nullptr, int64_t ws_floats = 0) {
+    const int KT = K / BK, kps = split_kps(M, N, K), S = (KT + kps - 1) / kps;
+    const auto *a = static_cast<const __nv_bfloat16 *>(A);
+    const auto *b = static_cast<const __nv_bfloat16 *>(B);
+    if (S > 1 && ws && (int64_t)S * M * N <= ws_floats) {
+        cudaError_t e = set_smem<TA, TB, EPI_F32>();
         if (e != cudaSuccess) return e;
-        attr = true;
+        gemm_tc<TA, TB, EPI_F32><<<dim3(N / BN, M / BM, S), THREADS, GEMM_SMEM, s>>>(a, lda, b, ldb, ws, N, K, nullptr,
+                                                                                   nullptr, kps, (int64_t)M * N);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t pairs = (int64_t)M * N / 2;
+        const int grid = (int)std::min<int64_t>((pairs + 255) / 256, 4096);
+        splitk_reduce<EPI><<<grid, 256, 0, s>>>(ws, S, M, N, C, ldc, bias, static_cast<__nv_bfloat16 *>(pre));
+        return cudaGetLastError();
     }
-    dim3 grid(N / BN, M / BM);
-    gemm_tc<TA, TB, EPI><<<grid, THREADS, GEMM_SMEM, s>>>(static_cast<const __nv_bfloat16 *>(A), lda,
-                                                          static_cast<const __nv_bfloat16 *>(B), ldb, C, ldc, K, bias,
-                                                          static_cast<__nv_bfloat16 *>(pre));
+    const cudaError_t e = set_smem<TA, TB, EPI>();
+    if (e != cudaSuccess) return e;
+    gemm_tc<TA, TB, EPI><<<dim3(N / BN, M / BM, 1), THREADS, GEMM_SMEM, s>>>(a, lda, b, ldb, C, ldc, K, bias,
+                                                                           static_cast<__nv_bfloat16 *>(pre), KT, 0);
     return cudaGetLastError();
 }
 
@@ -380,10 +453,10 @@ int forward(const bmpc_mlp_layer *L, int n, const uint16_t *x, int batch, const 
         cudaError_t e;
         if (l + 1 < n)
             e = gemm<false, false, EPI_BIAS_GELU>(in, L[l].in, L[l].w_bf16, L[l].out, w->act[l], L[l].out, batch,
-                                                  L[l].out, L[l].in, L[l].b, w->pre[l], s);
+                                                  L[l].out, L[l].in, L[l].b, w->pre[l], s, w->splitk, w->splitk_floats);
         else
             e = gemm<false, false, EPI_BIAS_F32>(in, L[l].in, L[l].w_bf16, L[l].out, w->pred, L[l].out, batch,
-                                                 L[l].out, L[l].in, L[l].b, nullptr, s);
+                                                 L[l].out, L[l].in, L[l].b, nullptr, s, w->splitk, w->splitk_floats);
         if (e != cudaSuccess) return -2;
         in = w->act[l];
     }
@@ -427,13 +500,14 @@ int bmpc_mlp_train_step(const bmpc_mlp_layer *L, int32_t n, const uint16_t *x, c
         const void *in = l == 0 ? static_cast<const void *>(x) : static_cast<const void *>(w->act[l - 1]);
         /* dW = in^T g, db = column sums of g */
         if (gemm<true, false, EPI_F32>(in, L[l].in, g, L[l].out, L[l].dw, L[l].out, L[l].in, L[l].out, batch, nullptr,
-                                       nullptr, s) != cudaSuccess)
+                                       nullptr, s, w->splitk, w->splitk_floats) != cudaSuccess)
             return -2;
         bias_grad<<<(L[l].out + 255) / 256, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(g), batch, L[l].out,
                                                          L[l].db);
         if (l > 0) {   /* g_prev = (g W^T) * gelu'(pre_{l-1}) */
             if (gemm<false, true, EPI_DGELU>(g, L[l].out, L[l].w_bf16, L[l].out, gn, L[l].in, batch, L[l].in,
-                                             L[l].out, nullptr, w->pre[l - 1], s) != cudaSuccess)
+                                             L[l].out, nullptr, w->pre[l - 1], s, w->splitk, w->splitk_floats) !=
+                cudaSuccess)
                 return -2;
             uint16_t *t = g;
             g = gn;
@@ -474,6 +548,17 @@ int bmpc_mlp_gemm(const uint16_t *A, int32_t lda, int32_t trans_a, const uint16_
     else if (!trans_a && trans_b) e = gemm<false, true, EPI_F32>(A, lda, B, ldb, C, ldc, M, N, K, nullptr, nullptr, s);
     else e = gemm<true, true, EPI_F32>(A, lda, B, ldb, C, ldc, M, N, K, nullptr, nullptr, s);
     return e == cudaSuccess ? 0 : -2;
+}
+
+int64_t bmpc_mlp_workspace_floats(const bmpc_mlp_layer *L, int32_t n, int32_t batch) {
+    if (check_layers(L, n) || batch <= 0 || batch % 128) return -1;
+    int64_t f = 0;
+    for (int l = 0; l < n; ++l) {
+        f = std::max(f, split_floats(batch, L[l].out, L[l].in));        /* forward */
+        f = std::max(f, split_floats(L[l].in, L[l].out, batch));        /* dW = in^T g */
+        if (l > 0) f = std::max(f, split_floats(batch, L[l].in, L[l].out));   /* g W^T */
+    }
+    return f;
 }
 
 int bmpc_mlp_status(void *stream) {

@@ -23,7 +23,8 @@ class Layer(C.Structure):
 
 class Work(C.Structure):
     _fields_ = [("pre", C.c_void_p * MAX_LAYERS), ("act", C.c_void_p * MAX_LAYERS), ("dy0", C.c_void_p),
-                ("dy1", C.c_void_p), ("pred", C.c_void_p), ("loss", C.c_void_p)]
+                ("dy1", C.c_void_p), ("pred", C.c_void_p), ("loss", C.c_void_p), ("splitk", C.c_void_p),
+                ("splitk_floats", C.c_int64)]
 
 
 def _setup():
@@ -37,6 +38,8 @@ def _setup():
     L.bmpc_mlp_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                 C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
     L.bmpc_mlp_status.argtypes = [C.c_void_p]
+    L.bmpc_mlp_workspace_floats.argtypes = [C.POINTER(Layer), C.c_int32, C.c_int32]
+    L.bmpc_mlp_workspace_floats.restype = C.c_int64
     L.bmpc_mlp_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32]
     L.bmpc_mlp_targets.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
     L.bmpc_mlp_start.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
@@ -107,8 +110,11 @@ class MLP:
         dy1 = torch.empty((batch, widest), dtype=torch.bfloat16, device=self.device)
         pred = torch.empty((batch, self.dims[-1]), dtype=torch.float32, device=self.device)
         loss = torch.zeros(1, dtype=torch.float32, device=self.device)
-        keep += [dy0, dy1, pred, loss]
+        nws = _setup().bmpc_mlp_workspace_floats(self.c_layers, len(self.params), batch)
+        ws = torch.empty(max(nws, 1), dtype=torch.float32, device=self.device)
+        keep += [dy0, dy1, pred, loss, ws]
         w.dy0, w.dy1, w.pred, w.loss = dy0.data_ptr(), dy1.data_ptr(), pred.data_ptr(), loss.data_ptr()
+        w.splitk, w.splitk_floats = (ws.data_ptr(), nws) if nws > 0 else (None, 0)
         self._work[batch] = (w, keep, pred, loss)
         return self._work[batch]
 

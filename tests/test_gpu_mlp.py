@@ -76,6 +76,30 @@ def test_training_step_gradients_and_adamw_match_reference():
         assert _rel(p["w"].cpu().numpy(), w_ref) < 1e-6
 
 
+def test_split_k_forward_and_gradients_match_reference():
+    """Shapes whose GEMMs split along K (long inner dimension, few output tiles): the first layer's
+    forward (bias + GELU epilogue) and the back-propagation through the output layer (GELU'
+    epilogue) go through partial products and the split-K reduction."""
+    from paper_2506_13624_b300 import mlp
+    dims = [1664, 128, 128, 1024]
+    net, Ws, bs = _net_and_ref(dims, seed=5)
+    w_, _, _, _ = net.work(128)
+    assert w_.splitk_floats > 0
+    rng = np.random.default_rng(4)
+    x = mlp_ref.bf16(rng.standard_normal((128, dims[0])))
+    t = mlp_ref.bf16(rng.standard_normal((128, dims[-1])))
+    pred = net.forward(_bf(x)).cpu().numpy()
+    mlp.status()
+    ref, _ = mlp_ref.forward(Ws, bs, x, bf=True)
+    assert _rel(pred, ref) < 5e-3
+    net.train_step(_bf(x), _bf(t), lr=1e-3)
+    mlp.status()
+    _, dWs, dbs = mlp_ref.loss_and_grads(Ws, bs, x, t, bf=True)
+    for l, p in enumerate(net.params):
+        assert _rel(p["dw"].cpu().numpy(), dWs[l]) < 2e-2, l
+        assert _rel(p["db"].cpu().numpy(), dbs[l]) < 2e-2, l
+
+
 def test_targets_and_starts_round_trip():
     from paper_2506_13624_b300 import bmpc, mlp, warmstart
     ps = scenes.batch_problems(1, 4, model=scenes.MODEL_KINEMATIC, N=20, splits={1: 3}, n_obs=2, n_cross=1,
