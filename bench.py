@@ -166,30 +166,42 @@ def oracle_rate(name: str, seconds: float, max_problems: int, rank: int = 0):
                 sample=f"{done} {name} problems solved sequentially with the FP64 oracle ({dt:.1f} s)")
 
 
+def _oracle_converged(p):
+    import oracle
+    return int(oracle.solve(p)["status"] == oracle.OK)
+
+
 def run_reference(args):
+    """The FP64 oracle, unchanged, on the host cores: each step solves a bounded sample of the
+    workload (ref_sample problems per worker process) and counts the converged solves."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    workers = max(1, args.ref_workers or (os.cpu_count() or 1))
+    pool = mp.get_context("spawn").Pool(workers) if workers > 1 else None
     steps = []
     for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        probs = workload(args.workload, args.ref_sample, rank=1000 + s)
-        import oracle
-        oracle.build()
+        probs = workload(args.workload, args.ref_sample * workers, rank=1000 + s)
         tsolve = time.perf_counter()
-        solved = sum(int(oracle.solve(p)["status"] == oracle.OK) for p in probs)
+        flags = pool.map(_oracle_converged, probs, chunksize=1) if pool else [_oracle_converged(p) for p in probs]
         dt = time.perf_counter() - tsolve
         if s >= args.warmup:
-            steps.append((solved, dt))
-        del t0
+            steps.append((sum(flags), dt))
+    if pool:
+        pool.close()
     tot_s = sum(d for _, d in steps)
     value = sum(n for n, _ in steps) / tot_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / len(steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "batch": args.ref_sample},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.ref_sample} {args.workload} problems per step, FP64 oracle, one thread"},
+            "data": "synthetic", "config": {"workload": args.workload, "batch": args.ref_sample * workers},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": workers, "kind": "oracle",
+                             "sample": f"{args.ref_sample * workers} {args.workload} problems per step, FP64 oracle, "
+                                       f"one problem per process on {workers} processes"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -381,7 +393,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-sample", type=int, default=16)
+    ap.add_argument("--ref-sample", type=int, default=4, help="oracle problems per worker per reference step")
+    ap.add_argument("--ref-workers", type=int, default=0, help="oracle worker processes (0: all host cores)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "b300":
         args.warmup = 3
