@@ -5,11 +5,11 @@
  *   gemm_tc<TA, TB, EPI>     C[M x N] = op(A)[M x K] op(B)[K x N] on the 5th-generation tensor
  *                            cores: tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) issued by one
  *                            thread from shared-memory descriptors, the 128 x 128 accumulator in
- *                            tensor memory (TMEM), operand tiles staged by cp.async in a 4-stage
- *                            ring whose stages are reused once an mbarrier reports the MMAs that
- *                            read them complete; the epilogue reads TMEM with tcgen05.ld.  op(X) is
- *                            X or X^T: K-major and MN-major operands are both laid out in the
- *                            canonical no-swizzle core-matrix form (8 rows x 16 bytes).
+ *                            tensor memory (TMEM), operand tiles loaded by TMA
+ *                            (cp.async.bulk.tensor, 4-D maps) into a 4-stage ring of full/empty
+ *                            mbarriers; the epilogue reads TMEM with tcgen05.ld.  op(X) is X or
+ *                            X^T: K-major and MN-major operands both land in the canonical
+ *                            no-swizzle core-matrix form (8 rows x 16 bytes).
  *                            Epilogues: plain f32 (weight gradients), + bias in f32 (output
  *                            layer), + bias then GELU in bf16 with the pre-activation kept (hidden
  *                            layers), times GELU'(pre) in bf16 (back-propagation through a hidden
@@ -21,6 +21,7 @@
  *
  * Every matrix is row-major; M and N are multiples of 128 and K of 32 (the host pads).
  */
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -33,7 +34,7 @@ namespace bmpc_mlp {
 constexpr int BM = 128, BN = 128, BK = 32, THREADS = 128, NSTAGE = 4;
 constexpr int TILE_BYTES = 128 * BK * 2;                       /* one 128 x 32 bf16 operand tile */
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;                    /* A and B tiles of one k-step */
-constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES;                /* 64 KB of dynamic shared memory */
+constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + 1024;         /* 64 KB of stages + alignment slack */
 constexpr int TMEM_COLS = 128;                                 /* FP32 accumulator: 128 lanes x 128 */
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_DGELU = 3 };
@@ -41,12 +42,6 @@ enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_DGELU = 3 };
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async16(void *s, const void *g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
@@ -73,26 +68,17 @@ __host__ __device__ constexpr uint32_t mma_idesc(bool a_mn, bool b_mn) {
            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-/* Stage the 128 x BK slice of an operand into the canonical layout: core matrix (row group g, k
- * chunk c) of 8 rows x 16 bytes at byte (g * BK/8 + c) * 128.  KMAJ: the stored matrix runs along
- * k, row r of the tile at g + (r0 + r) ld + k0, and a 16-byte row of a core matrix is 8 k of one
- * tile row.  Otherwise it runs along the tile rows, element (r, k) at g + (k0 + k) ld + r0 + r, and
- * a 16-byte row of a core matrix is 8 tile rows of one k. */
-template <bool KMAJ>
-__device__ __forceinline__ void stage_tile(unsigned char *s, const __nv_bfloat16 *g, int ld, int r0, int k0) {
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int rep = 0; rep < (128 * BK / 8) / THREADS; ++rep) {      /* 512 chunks of 8 elements */
-        const int idx = t + rep * THREADS;
-        if (KMAJ) {
-            const int r = idx >> 2, c = idx & 3;                     /* tile row, k chunk */
-            cp_async16(s + ((r >> 3) * (BK / 8) + c) * 128 + (r & 7) * 16, g + (size_t)(r0 + r) * ld + k0 + c * 8);
-        } else {
-            const int k = idx >> 4, gr = idx & 15;                   /* k, tile row group */
-            cp_async16(s + (gr * (BK / 8) + (k >> 3)) * 128 + (k & 7) * 16,
-                       g + (size_t)(k0 + k) * ld + r0 + gr * 8);
-        }
-    }
+/* One 4-D TMA load (one thread) of an operand's 128 x BK slice into a stage, completing on `bar`.
+ * The tensor map (make_operand_map) views the stored matrix as (8 elements, 8 rows, k chunks of 8,
+ * row groups of 8) so that the box lands in the canonical no-swizzle core-matrix layout: core
+ * matrix (row group g, k chunk c) of 8 rows x 16 bytes at byte (g * BK/8 + c) * 128.  The innermost
+ * coordinate is always 0 (16-byte aligned). */
+__device__ __forceinline__ void tma_tile(void *dst, const CUtensorMap *map, int kchunk, int group, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(0), "r"(0), "r"(kchunk), "r"(group), "r"(smem_addr(bar))
+        : "memory");
 }
 
 /* Waits (at most about 2 s of SM clock) for the phase of `bar` with the given parity; 0 on timeout. */
@@ -130,17 +116,20 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 /* C = op(A) op(B) for one 128 x 128 tile of C per block (4 warps).  TA: A is given transposed
- * (stored K x M); TB: B is given transposed (stored N x K).  lda/ldb are the row lengths of the
- * stored matrices, ldc of C.  Thread 0 issues the MMAs (BK/16 per k-step) and commits each k-step
- * to the mbarrier of its stage; a stage is refilled two k-steps later, after that mbarrier phase.
- * Warp w reads accumulator lanes 32w .. 32w + 31 (rows of C) in the epilogue. */
+ * (stored K x M); TB: B is given transposed (stored N x K); amap/bmap are their TMA views and ldc
+ * the row length of C.  Thread 0 alone runs the k loop: it keeps NSTAGE-1 k-steps of operands in
+ * flight by TMA (stage s filled on full[s]), issues the BK/16 MMAs of each k-step once its stage
+ * has landed and commits them to empty[s]; a stage is refilled once its empty phase completes.  A
+ * final commit to `done` releases the epilogue, in which warp w reads accumulator lanes 32w ..
+ * 32w + 31 (rows of C). */
 template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(THREADS) gemm_tc(const __nv_bfloat16 *__restrict__ A, int lda,
-                                                    const __nv_bfloat16 *__restrict__ B, int ldb, void *C, int ldc,
-                                                    int K, const float *__restrict__ bias,
-                                                    __nv_bfloat16 *__restrict__ pre, int kps, int64_t c_split) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[NSTAGE];
+__global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUtensorMap amap,
+                                                    const __grid_constant__ CUtensorMap bmap, void *C, int ldc, int K,
+                                                    const float *__restrict__ bias, __nv_bfloat16 *__restrict__ pre,
+                                                    int kps, int64_t c_split) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], done;
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -154,37 +143,36 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __nv_bfloat16 *__restri
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0)
-        for (int s = 0; s < NSTAGE; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[s])));
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
     constexpr uint32_t idesc = mma_idesc(TA, !TB);
-
-    auto stage = [&](int kt) {
-        unsigned char *sa = smem + (kt % NSTAGE) * STAGE_BYTES, *sb = sa + TILE_BYTES;
-        const int k0 = (kbeg + kt) * BK;
-        stage_tile<!TA>(sa, A, lda, m0, k0);
-        stage_tile<TB>(sb, B, ldb, n0, k0);
-    };
     int ok = 1;
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        if (p < KT) stage(p);
-        cp_commit();
-    }
-    for (int kt = 0; kt < KT; ++kt) {
-        if (kt >= 2) ok &= mbar_wait(&mbar[(kt - 2) % NSTAGE], ((kt - 2) / NSTAGE) & 1);
-        if (kt + 2 < KT) stage(kt + 2);
-        cp_commit();
-        cp_wait<2>();   /* the tile of this k-step has landed */
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    if (tid == 0) {
+        auto load = [&](int t) {
+            const int s = t % NSTAGE;
+            unsigned char *sa = smem + s * STAGE_BYTES;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[s])),
+                         "r"(STAGE_BYTES)
+                         : "memory");
+            tma_tile(sa, &amap, (kbeg + t) * (BK / 8), m0 / 8, &full[s]);
+            tma_tile(sa + TILE_BYTES, &bmap, (kbeg + t) * (BK / 8), n0 / 8, &full[s]);
+        };
+        for (int p = 0; p < NSTAGE - 1 && p < KT; ++p) load(p);
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % NSTAGE;
+            ok &= mbar_wait(&full[s], (kt / NSTAGE) & 1);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_addr(smem + (kt % NSTAGE) * STAGE_BYTES), sb = sa + TILE_BYTES;
+            const uint32_t sa = smem_addr(smem + s * STAGE_BYTES), sb = sa + TILE_BYTES;
 #pragma unroll
             for (int j = 0; j < BK / 16; ++j) {
                 const uint64_t da = tile_desc(sa + j * 256), db = tile_desc(sb + j * 256);
@@ -194,11 +182,19 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __nv_bfloat16 *__restri
                              "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&mbar[kt % NSTAGE]))
+                             smem_addr(&empty[s]))
                          : "memory");
+            const int nk = kt + NSTAGE - 1;   /* refill the stage of k-step kt-1 once its MMAs are done */
+            if (nk < KT) {
+                if (nk >= NSTAGE) ok &= mbar_wait(&empty[nk % NSTAGE], ((nk - NSTAGE) / NSTAGE) & 1);
+                load(nk);
+            }
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(&done))
+                     : "memory");
     }
-    ok &= mbar_wait(&mbar[(KT - 1) % NSTAGE], ((KT - 1) / NSTAGE) & 1);   /* every MMA of the tile done */
+    ok &= mbar_wait(&done, 0);   /* a single phase: every MMA of the tile has completed */
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         const int r = m0 + warp * 32 + lane;
@@ -399,6 +395,48 @@ int64_t split_floats(int M, int N, int K) {
     return kps >= KT ? 0 : (int64_t)((KT + kps - 1) / kps) * M * N;
 }
 
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+/* cuTensorMapEncodeTiled from the driver, looked up once through the runtime. */
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+/* TMA view of a GEMM operand for gemm_tc (see tma_tile): a 4-D map (8 elements, 8 rows, k chunks,
+ * row groups) of the stored matrix.  kmajor: stored [mn][ld] with K along a row; else stored
+ * [k][ld] with MN along a row.  mn and k are the operand's extents (multiples of 128 and BK), ld the
+ * stored row length in elements (a multiple of 8, so that every stride is a multiple of 16 bytes). */
+bool make_operand_map(CUtensorMap *m, const void *ptr, int mn, int k, int ld, bool kmajor) {
+    const EncodeTiled enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t row = (cuuint64_t)ld * 2;
+    cuuint64_t dim[4] = {8, 8, (cuuint64_t)k / 8, (cuuint64_t)mn / 8}, str[3];
+    if (kmajor) {   /* element (k in chunk), row in group, k chunk (16 B on), row group */
+        str[0] = row;
+        str[1] = 16;
+        str[2] = 8 * row;
+    } else {        /* element (mn in group), k in chunk, k chunk, mn group (16 B on) */
+        str[0] = row;
+        str[1] = 8 * row;
+        str[2] = 16;
+    }
+    cuuint32_t box[4] = {8, 8, BK / 8, 16}, es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dim, str, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <bool TA, bool TB, int EPI>
 cudaError_t set_smem() {
     static bool done = false;   /* 64 KB of dynamic shared memory needs the opt-in, once per instance */
@@ -415,13 +453,14 @@ template <bool TA, bool TB, int EPI>
 cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ldc, int M, int N, int K, const float *bias,
                  void *pre, cudaStream_t s, float *ws = nullptr, int64_t ws_floats = 0) {
     const int KT = K / BK, kps = split_kps(M, N, K), S = (KT + kps - 1) / kps;
-    const auto *a = static_cast<const __nv_bfloat16 *>(A);
-    const auto *b = static_cast<const __nv_bfloat16 *>(B);
+    CUtensorMap am, bm;
+    if (!make_operand_map(&am, A, M, K, lda, !TA) || !make_operand_map(&bm, B, N, K, ldb, TB))
+        return cudaErrorInvalidValue;
     if (S > 1 && ws && (int64_t)S * M * N <= ws_floats) {
         cudaError_t e = set_smem<TA, TB, EPI_F32>();
         if (e != cudaSuccess) return e;
-        gemm_tc<TA, TB, EPI_F32><<<dim3(N / BN, M / BM, S), THREADS, GEMM_SMEM, s>>>(a, lda, b, ldb, ws, N, K, nullptr,
-                                                                                   nullptr, kps, (int64_t)M * N);
+        gemm_tc<TA, TB, EPI_F32><<<dim3(N / BN, M / BM, S), THREADS, GEMM_SMEM, s>>>(am, bm, ws, N, K, nullptr, nullptr,
+                                                                                   kps, (int64_t)M * N);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const int64_t pairs = (int64_t)M * N / 2;
@@ -431,7 +470,7 @@ cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ld
     }
     const cudaError_t e = set_smem<TA, TB, EPI>();
     if (e != cudaSuccess) return e;
-    gemm_tc<TA, TB, EPI><<<dim3(N / BN, M / BM, 1), THREADS, GEMM_SMEM, s>>>(a, lda, b, ldb, C, ldc, K, bias,
+    gemm_tc<TA, TB, EPI><<<dim3(N / BN, M / BM, 1), THREADS, GEMM_SMEM, s>>>(am, bm, C, ldc, K, bias,
                                                                            static_cast<__nv_bfloat16 *>(pre), KT, 0);
     return cudaGetLastError();
 }
