@@ -158,3 +158,35 @@ def standardize(raw, mean, std, out):
     import torch
     _check(_setup().bmpc_mlp_standardize(raw.data_ptr(), mean.data_ptr(), std.data_ptr(), out.data_ptr(),
                                          raw.shape[0], raw.shape[1], _stream(torch)), "bmpc_mlp_standardize")
+
+
+def _main(argv=None):
+    """Times C = A B on the tcgen05 GEMM for the given shape (used for profiling)."""
+    import argparse
+    import torch
+    ap = argparse.ArgumentParser(description="time one tcgen05 GEMM shape")
+    ap.add_argument("M", type=int)
+    ap.add_argument("N", type=int)
+    ap.add_argument("K", type=int)
+    ap.add_argument("--ta", action="store_true")
+    ap.add_argument("--tb", action="store_true")
+    ap.add_argument("--reps", type=int, default=20)
+    a = ap.parse_args(argv)
+    torch.manual_seed(0)
+    A = torch.randn((a.K, a.M) if a.ta else (a.M, a.K), device="cuda").to(torch.bfloat16)
+    B = torch.randn((a.N, a.K) if a.tb else (a.K, a.N), device="cuda").to(torch.bfloat16)
+    for _ in range(3):
+        gemm(A, B, a.ta, a.tb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        gemm(A, B, a.ta, a.tb)
+    e1.record()
+    status()
+    ms = e0.elapsed_time(e1) / a.reps
+    print(f"M={a.M} N={a.N} K={a.K} ta={int(a.ta)} tb={int(a.tb)}: {ms:.3f} ms, "
+          f"{2.0 * a.M * a.N * a.K / ms / 1e9:.1f} TFLOP/s")
+
+
+if __name__ == "__main__":
+    _main()
