@@ -61,7 +61,7 @@ int bmpc_mlp_train_step(const bmpc_mlp_layer *layers, int32_t n_layers, const ui
 
 /* C [M][N] (fp32) = op(A) op(B) with op(A) [M][K], op(B) [K][N]; trans_a: A stored [K][M]; trans_b:
  * B stored [N][K]; lda/ldb/ldc are row lengths of the stored matrices.  M and N must be multiples
- * of 128, K of 32 and the row lengths of 8 (else -1); runs on the tcgen05 tensor cores. */
+ * of 128, K of 64 and the row lengths of 8 (else -1); runs on the tcgen05 tensor cores. */
 int bmpc_mlp_gemm(const uint16_t *A, int32_t lda, int32_t trans_a, const uint16_t *B, int32_t ldb, int32_t trans_b,
                   float *C, int32_t ldc, int32_t M, int32_t N, int32_t K, void *stream);
 

@@ -6,10 +6,10 @@
  *                            cores: tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) issued by one
  *                            thread from shared-memory descriptors, the 128 x 128 accumulator in
  *                            tensor memory (TMEM), operand tiles loaded by TMA
- *                            (cp.async.bulk.tensor, 4-D maps) into a 4-stage ring of full/empty
- *                            mbarriers; the epilogue reads TMEM with tcgen05.ld.  op(X) is X or
- *                            X^T: K-major and MN-major operands both land in the canonical
- *                            no-swizzle core-matrix form (8 rows x 16 bytes).
+ *                            (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage ring of
+ *                            full/empty mbarriers; the epilogue reads TMEM with tcgen05.ld.
+ *                            op(X) is X or X^T: K-major and MN-major operands use the matching
+ *                            swizzled descriptor layouts.
  *                            Epilogues: plain f32 (weight gradients), + bias in f32 (output
  *                            layer), + bias then GELU in bf16 with the pre-activation kept (hidden
  *                            layers), times GELU'(pre) in bf16 (back-propagation through a hidden
@@ -19,7 +19,7 @@
  *   adamw                    AdamW on fp32 master weights, refreshing the bf16 copy.
  *   init                     uniform(-1/sqrt(in), 1/sqrt(in)) weights from a counter-based hash.
  *
- * Every matrix is row-major; M and N are multiples of 128 and K of 32 (the host pads).
+ * Every matrix is row-major; M and N are multiples of 128 and K of 64 (the host pads).
  */
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -31,10 +31,10 @@
 
 namespace bmpc_mlp {
 
-constexpr int BM = 128, BN = 128, BK = 32, THREADS = 128, NSTAGE = 4;
-constexpr int TILE_BYTES = 128 * BK * 2;                       /* one 128 x 32 bf16 operand tile */
+constexpr int BM = 128, BN = 128, BK = 64, THREADS = 128, NSTAGE = 3;
+constexpr int TILE_BYTES = 128 * BK * 2;                       /* one 128 x 64 bf16 operand tile (16 KB) */
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;                    /* A and B tiles of one k-step */
-constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + 1024;         /* 64 KB of stages + alignment slack */
+constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + 1024;         /* 96 KB of stages + alignment slack */
 constexpr int TMEM_COLS = 128;                                 /* FP32 accumulator: 128 lanes x 128 */
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_DGELU = 3 };
@@ -51,14 +51,19 @@ __device__ __forceinline__ float gelu_grad(float x) {
 /* ------------------------------------------------------------------ tcgen05 GEMM */
 __device__ int g_gemm_timeout;   /* set when an mbarrier wait of a GEMM gave up (read by bmpc_mlp_status) */
 
-/* Shared-memory matrix descriptor of a canonical no-swizzle operand tile: start address, byte
- * offset between core matrices along K (leading, 128) and along M/N (stride, BK/8 cores of 128 B),
- * descriptor version 1, no swizzle.  Both majors use the same offsets; the major is in the
- * instruction descriptor and in how the 16-byte rows of a core matrix are filled. */
-__device__ __forceinline__ uint64_t tile_desc(uint32_t addr) {
-    constexpr uint64_t LBO = 128, SBO = (BK / 8) * 128;
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((LBO >> 4) << 16) | ((SBO >> 4) << 32) | (1ull << 46);
+/* Shared-memory matrix descriptor (tcgen05) of an operand tile in the 128-byte-swizzled layout
+ * TMA writes with CU_TENSOR_MAP_SWIZZLE_128B: start address, leading and stride byte offsets,
+ * descriptor version 1, layout code 2 (128-byte swizzle).
+ *   K-major tile (128 rows x 64 k, one 128-byte row per tile row, 8-row atoms of 1024 bytes):
+ *     stride offset 1024 between 8-row atoms; the leading offset is unused; the MMA of k-slice j
+ *     (16 k) starts 32 j bytes into the tile.
+ *   M/N-major tile (64 k rows x 128 mn, two 64-wide halves of 8 KB): leading offset 8192 between
+ *     the halves, stride offset 1024 between 8-row groups of k; k-slice j starts 2048 j bytes in. */
+__device__ __forceinline__ uint64_t tile_desc(uint32_t addr, bool mn_major) {
+    const uint64_t lbo = mn_major ? 8192 : 16, sbo = 1024;
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
+__device__ __forceinline__ uint32_t slice_offset(int j, bool mn_major) { return mn_major ? 2048u * j : 32u * j; }
 
 /* Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5), BF16 A and B
  * (bits 7-9, 10-12), A and B majors (bit 15, 16: 0 K-major, 1 M/N-major), N/8 (bits 17-22),
@@ -68,17 +73,27 @@ __host__ __device__ constexpr uint32_t mma_idesc(bool a_mn, bool b_mn) {
            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-/* One 4-D TMA load (one thread) of an operand's 128 x BK slice into a stage, completing on `bar`.
- * The tensor map (make_operand_map) views the stored matrix as (8 elements, 8 rows, k chunks of 8,
- * row groups of 8) so that the box lands in the canonical no-swizzle core-matrix layout: core
- * matrix (row group g, k chunk c) of 8 rows x 16 bytes at byte (g * BK/8 + c) * 128.  The innermost
- * coordinate is always 0 (16-byte aligned). */
-__device__ __forceinline__ void tma_tile(void *dst, const CUtensorMap *map, int kchunk, int group, uint64_t *bar) {
+/* One 2-D TMA load (one thread) with 128-byte swizzle into `dst` (1024-byte aligned), completing
+ * on `bar`: the box at coordinates (x, y) of the operand's map; x, the innermost coordinate, is a
+ * multiple of 64 elements (128 bytes). */
+__device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(smem_addr(dst)),
-        "l"(map), "r"(0), "r"(0), "r"(kchunk), "r"(group), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
         : "memory");
+}
+
+/* The operand slice of k-step t: K-major, one box of 64 k x 128 rows; M/N-major, two boxes of 64 mn x
+ * 64 k (the two halves of the tile's 128 rows). */
+template <bool KMAJ>
+__device__ __forceinline__ void load_slice(unsigned char *dst, const CUtensorMap *map, int k0, int r0, uint64_t *bar) {
+    if (KMAJ) {
+        tma_box(dst, map, k0, r0, bar);
+    } else {
+        tma_box(dst, map, r0, k0, bar);
+        tma_box(dst + 8192, map, r0 + 64, k0, bar);
+    }
 }
 
 /* Waits (at most about 2 s of SM clock) for the phase of `bar` with the given parity; 0 on timeout. */
@@ -164,8 +179,8 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[s])),
                          "r"(STAGE_BYTES)
                          : "memory");
-            tma_tile(sa, &amap, (kbeg + t) * (BK / 8), m0 / 8, &full[s]);
-            tma_tile(sa + TILE_BYTES, &bmap, (kbeg + t) * (BK / 8), n0 / 8, &full[s]);
+            load_slice<!TA>(sa, &amap, (kbeg + t) * BK, m0, &full[s]);
+            load_slice<TB>(sa + TILE_BYTES, &bmap, (kbeg + t) * BK, n0, &full[s]);
         };
         for (int p = 0; p < NSTAGE - 1 && p < KT; ++p) load(p);
         for (int kt = 0; kt < KT; ++kt) {
@@ -175,7 +190,8 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
             const uint32_t sa = smem_addr(smem + s * STAGE_BYTES), sb = sa + TILE_BYTES;
 #pragma unroll
             for (int j = 0; j < BK / 16; ++j) {
-                const uint64_t da = tile_desc(sa + j * 256), db = tile_desc(sb + j * 256);
+                const uint64_t da = tile_desc(sa + slice_offset(j, TA), TA);
+                const uint64_t db = tile_desc(sb + slice_offset(j, !TB), !TB);
                 const uint32_t accumulate = (kt | j) != 0;
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
@@ -413,27 +429,28 @@ EncodeTiled encoder() {
     return fn;
 }
 
-/* TMA view of a GEMM operand for gemm_tc (see tma_tile): a 4-D map (8 elements, 8 rows, k chunks,
- * row groups) of the stored matrix.  kmajor: stored [mn][ld] with K along a row; else stored
- * [k][ld] with MN along a row.  mn and k are the operand's extents (multiples of 128 and BK), ld the
- * stored row length in elements (a multiple of 8, so that every stride is a multiple of 16 bytes). */
+/* TMA view of a GEMM operand for gemm_tc (see load_slice): a 2-D map of the stored matrix with
+ * 128-byte swizzle.  kmajor: stored [mn][ld] with K along a row, boxes of 64 k x 128 rows; else
+ * stored [k][ld] with MN along a row, boxes of 64 mn x 64 k.  mn and k are the operand's extents
+ * (multiples of 128 and BK), ld the stored row length in elements (a multiple of 8: 16-byte rows). */
 bool make_operand_map(CUtensorMap *m, const void *ptr, int mn, int k, int ld, bool kmajor) {
     const EncodeTiled enc = encoder();
     if (!enc) return false;
-    const cuuint64_t row = (cuuint64_t)ld * 2;
-    cuuint64_t dim[4] = {8, 8, (cuuint64_t)k / 8, (cuuint64_t)mn / 8}, str[3];
-    if (kmajor) {   /* element (k in chunk), row in group, k chunk (16 B on), row group */
-        str[0] = row;
-        str[1] = 16;
-        str[2] = 8 * row;
-    } else {        /* element (mn in group), k in chunk, k chunk, mn group (16 B on) */
-        str[0] = row;
-        str[1] = 8 * row;
-        str[2] = 16;
+    cuuint64_t dim[2], str[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2], es[2] = {1, 1};
+    if (kmajor) {
+        dim[0] = (cuuint64_t)k;
+        dim[1] = (cuuint64_t)mn;
+        box[0] = 64;
+        box[1] = 128;
+    } else {
+        dim[0] = (cuuint64_t)mn;
+        dim[1] = (cuuint64_t)k;
+        box[0] = 64;
+        box[1] = 64;
     }
-    cuuint32_t box[4] = {8, 8, BK / 8, 16}, es[4] = {1, 1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dim, str, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dim, str, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

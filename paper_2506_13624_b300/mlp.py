@@ -54,7 +54,7 @@ def _stream(torch):
 
 
 def gemm(A, B, trans_a=False, trans_b=False):
-    """C = op(A) op(B) in fp32 from bf16 CUDA tensors (dimensions multiples of 128 / 32)."""
+    """C = op(A) op(B) in fp32 from bf16 CUDA tensors (M, N multiples of 128, K of 64)."""
     import torch
     L = _setup()
     M = A.shape[1] if trans_a else A.shape[0]

@@ -19,10 +19,10 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("K", [160, 1024])
+@pytest.mark.parametrize("K", [192, 1024])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 def test_gemm_variants_match_fp64(ta, tb, K):
-    """Every operand major on the tcgen05 path; K = 1024 cycles the 4-stage ring eight times."""
+    """Every operand major on the tcgen05 path; K = 1024 cycles the 3-stage ring five times."""
     from paper_2506_13624_b300 import mlp
     rng = np.random.default_rng(int(ta) * 2 + int(tb) + K)
     M, N = 256, 384
