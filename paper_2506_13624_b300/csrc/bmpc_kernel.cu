@@ -100,12 +100,56 @@ __host__ __device__ constexpr int sidx(int a, int b) {
 }
 
 /* ------------------------------------------------------------------ dynamics */
+/* sin and cos of an angle by the special-function unit (__sincosf) after reducing the argument to
+ * [-pi, pi] with Cody and Waite's two-constant subtraction of k 2 pi (2 pi = C1 + C2, C1 the float
+ * nearest 2 pi).  On [-pi, pi] the intrinsic's absolute error is at most 2^-21.41; the reduction
+ * stays accurate to that level for |a| < 1e4 rad, far beyond any heading or steering angle. */
+__device__ __forceinline__ void sincos_red(float a, float *s, float *c) {
+    constexpr float INV_2PI = 0.159154943f, C1 = 6.28318548f, C2 = -1.74845553e-7f;
+    const float k = rintf(a * INV_2PI);
+    const float r = fmaf(-k, C2, fmaf(-k, C1, a));
+    __sincosf(r, s, c);
+}
+
+/* Reciprocal by the PTX approximate instruction (rcp.approx.ftz.f32: at most 1 ulp of error over
+ * the normal range).  Unlike the IEEE-rounded reciprocal it has no slow path: a single SFU
+ * operation on the Riccati critical path and in every RK4 stage. */
+__device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+/* 2^-k for 0 <= k <= 126, exactly (the step sizes alpha_i of the line search). */
+__device__ __forceinline__ float pow2neg(int k) { return __int_as_float((127 - k) << 23); }
+
+/* Per-call constants of a vehicle right-hand side: reciprocals of the model parameters that it
+ * divides by, and tan(delta) of the kinematic model (the steering input is constant over an RK4
+ * step).  Computed once per node instead of once per RK4 stage. */
+struct ModelK {
+    float iL, td, im, iIz;
+};
+template <int MODEL>
+__device__ __forceinline__ ModelK model_k(const float *prm, float dl) {
+    ModelK k{0.f, 0.f, 0.f, 0.f};
+    if constexpr (MODEL == 0) {
+        float sd, cd;
+        sincos_red(dl, &sd, &cd);
+        k.iL = rcp(prm[0]);
+        k.td = sd * rcp(cd);
+    } else if constexpr (MODEL == 1) {
+        k.im = rcp(prm[1]);
+        k.iIz = rcp(prm[2]);
+    }
+    return k;
+}
+
 /* Continuous right-hand side and its Jacobians (dense arrays; compile-time zero
  * entries are folded away after unrolling).  MODEL 0: kinematic bicycle, 1: dynamic
  * bicycle with linear tyres and small steering angle. */
 template <int NX, int MODEL>
-__device__ __forceinline__ void rhs_jac(const float *prm, const float (&s)[NX], float a, float dl, float (&f)[NX],
-                                        float (&J)[NX][NX], float (&Ju)[NX][NU]) {
+__device__ __forceinline__ void rhs_jac(const float *prm, const ModelK &mk, const float (&s)[NX], float a, float dl,
+                                        float (&f)[NX], float (&J)[NX][NX], float (&Ju)[NX][NU]) {
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
 #pragma unroll
@@ -114,43 +158,44 @@ __device__ __forceinline__ void rhs_jac(const float *prm, const float (&s)[NX], 
         Ju[i][1] = 0.f;
     }
     if constexpr (MODEL == 0) {
-        const float L = prm[0];
         float sp, cp;
-        sincosf(s[2], &sp, &cp);
-        const float td = tanf(dl);
+        sincos_red(s[2], &sp, &cp);
+        const float td = mk.td, iL = mk.iL;
         const float v = s[3];
         f[0] = v * cp;
         f[1] = v * sp;
-        f[2] = v * td / L;
+        f[2] = v * td * iL;
         f[3] = a;
         J[0][2] = -v * sp;
         J[0][3] = cp;
         J[1][2] = v * cp;
         J[1][3] = sp;
-        J[2][3] = td / L;
-        Ju[2][1] = v * (1.f + td * td) / L;
+        J[2][3] = td * iL;
+        Ju[2][1] = v * (1.f + td * td) * iL;
         Ju[3][0] = 1.f;
     } else if constexpr (MODEL == 1) {
-        const float m = prm[1], Iz = prm[2], lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6];
+        const float lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6];
         const float vmin = prm[7], veps = prm[8];
+        const float im = mk.im, iIz = mk.iIz;
         const float psi = s[2], vx = s[3], vy = s[4], r = s[5];
         const float dv = vx - vmin;
-        const float w = sqrtf(dv * dv + veps * veps);
-        const float vb = 0.5f * (vx + vmin + w);
-        const float dvb = 0.5f * (1.f + dv / w);
-        const float ivb = 1.f / vb;
+        const float w2 = dv * dv + veps * veps;
+        const float iw = rsqrtf(w2);   /* 1 / sqrt(dv^2 + veps^2) */
+        const float vb = 0.5f * (vx + vmin + w2 * iw);
+        const float dvb = 0.5f * (1.f + dv * iw);
+        const float ivb = rcp(vb);
         const float tf = (vy + lf * r) * ivb, tr = (vy - lr * r) * ivb;
         const float af = atanf(tf) - dl, ar = atanf(tr);
         const float Ff = -Cf * af, Fr = -Cr * ar;
         float sp, cp;
-        sincosf(psi, &sp, &cp);
+        sincos_red(psi, &sp, &cp);
         f[0] = vx * cp - vy * sp;
         f[1] = vx * sp + vy * cp;
         f[2] = r;
         f[3] = a + r * vy;
-        f[4] = (Ff + Fr) / m - r * vx;
-        f[5] = (lf * Ff - lr * Fr) / Iz;
-        const float gf = 1.f / (1.f + tf * tf), gr = 1.f / (1.f + tr * tr);
+        f[4] = (Ff + Fr) * im - r * vx;
+        f[5] = (lf * Ff - lr * Fr) * iIz;
+        const float gf = rcp(1.f + tf * tf), gr = rcp(1.f + tr * tr);
         const float daf_vx = -gf * tf * ivb * dvb, daf_vy = gf * ivb, daf_r = gf * lf * ivb;
         const float dar_vx = -gr * tr * ivb * dvb, dar_vy = gr * ivb, dar_r = -gr * lr * ivb;
         const float dFf_vx = -Cf * daf_vx, dFf_vy = -Cf * daf_vy, dFf_r = -Cf * daf_r, dFf_d = Cf;
@@ -165,44 +210,45 @@ __device__ __forceinline__ void rhs_jac(const float *prm, const float (&s)[NX], 
         J[3][4] = r;
         J[3][5] = vy;
         Ju[3][0] = 1.f;
-        J[4][3] = (dFf_vx + dFr_vx) / m - r;
-        J[4][4] = (dFf_vy + dFr_vy) / m;
-        J[4][5] = (dFf_r + dFr_r) / m - vx;
-        Ju[4][1] = dFf_d / m;
-        J[5][3] = (lf * dFf_vx - lr * dFr_vx) / Iz;
-        J[5][4] = (lf * dFf_vy - lr * dFr_vy) / Iz;
-        J[5][5] = (lf * dFf_r - lr * dFr_r) / Iz;
-        Ju[5][1] = lf * dFf_d / Iz;
+        J[4][3] = (dFf_vx + dFr_vx) * im - r;
+        J[4][4] = (dFf_vy + dFr_vy) * im;
+        J[4][5] = (dFf_r + dFr_r) * im - vx;
+        Ju[4][1] = dFf_d * im;
+        J[5][3] = (lf * dFf_vx - lr * dFr_vx) * iIz;
+        J[5][4] = (lf * dFf_vy - lr * dFr_vy) * iIz;
+        J[5][5] = (lf * dFf_r - lr * dFr_r) * iIz;
+        Ju[5][1] = lf * dFf_d * iIz;
     }
 }
 
 template <int NX, int MODEL>
-__device__ __forceinline__ void rhs(const float *prm, const float (&s)[NX], float a, float dl, float (&f)[NX]) {
+__device__ __forceinline__ void rhs(const float *prm, const ModelK &mk, const float (&s)[NX], float a, float dl,
+                                    float (&f)[NX]) {
     if constexpr (MODEL == 0) {
-        const float L = prm[0];
         float sp, cp;
-        sincosf(s[2], &sp, &cp);
+        sincos_red(s[2], &sp, &cp);
         f[0] = s[3] * cp;
         f[1] = s[3] * sp;
-        f[2] = s[3] * tanf(dl) / L;
+        f[2] = s[3] * mk.td * mk.iL;
         f[3] = a;
     } else if constexpr (MODEL == 1) {
-        const float m = prm[1], Iz = prm[2], lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6];
+        const float lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6];
         const float vmin = prm[7], veps = prm[8];
         const float vx = s[3], vy = s[4], r = s[5];
         const float dv = vx - vmin;
-        const float vb = 0.5f * (vx + vmin + sqrtf(dv * dv + veps * veps));
-        const float ivb = 1.f / vb;
+        const float w2 = dv * dv + veps * veps;
+        const float vb = 0.5f * (vx + vmin + w2 * rsqrtf(w2));
+        const float ivb = rcp(vb);
         const float Ff = -Cf * (atanf((vy + lf * r) * ivb) - dl);
         const float Fr = -Cr * atanf((vy - lr * r) * ivb);
         float sp, cp;
-        sincosf(s[2], &sp, &cp);
+        sincos_red(s[2], &sp, &cp);
         f[0] = vx * cp - vy * sp;
         f[1] = vx * sp + vy * cp;
         f[2] = r;
         f[3] = a + r * vy;
-        f[4] = (Ff + Fr) / m - r * vx;
-        f[5] = (lf * Ff - lr * Fr) / Iz;
+        f[4] = (Ff + Fr) * mk.im - r * vx;
+        f[5] = (lf * Ff - lr * Fr) * mk.iIz;
     }
 }
 
@@ -239,7 +285,8 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
         constexpr int NZ = NX + NU;
         constexpr int GW = NZ - C0;   /* propagated tangent columns C0 .. NZ-1 */
         const int nsub = max(1, (int)R.params[9]);
-        const float h = R.dt / (float)nsub;
+        const float h = nsub == 1 ? R.dt : R.dt * rcp((float)nsub), h6 = h * (1.f / 6.f);
+        const ModelK mk = model_k<MODEL>(R.params, u[1]);
         float S[NX][GW];
 #pragma unroll
         for (int i = 0; i < NX; ++i)
@@ -268,7 +315,7 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
 #pragma unroll
                 for (int i = 0; i < NX; ++i) zs[i] = x[i] + (z[i] + c * h * kp[i]);
                 float f[NX], J[NX][NX], Ju[NX][NU];
-                rhs_jac<NX, MODEL>(R.params, zs, u[0], u[1], f, J, Ju);
+                rhs_jac<NX, MODEL>(R.params, mk, zs, u[0], u[1], f, J, Ju);
 #pragma unroll
                 for (int j = 0; j < GW; ++j) {
                     const int jj = C0 + j;
@@ -290,7 +337,6 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
                     kp[i] = f[i];
                 }
             }
-            const float h6 = h / 6.f;
 #pragma unroll
             for (int i = 0; i < NX; ++i) {
                 z[i] += h6 * ks[i];
@@ -325,7 +371,8 @@ __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], cons
 #pragma unroll
         for (int i = 0; i < NX; ++i) z[i] = 0.f;
         const int nsub = max(1, (int)R.params[9]);
-        const float h = R.dt / (float)nsub;
+        const float h = nsub == 1 ? R.dt : R.dt * rcp((float)nsub), h6 = h * (1.f / 6.f);
+        const ModelK mk = model_k<MODEL>(R.params, u[1]);
         for (int sub = 0; sub < nsub; ++sub) {
             float ks[NX], kp[NX];
 #pragma unroll
@@ -340,7 +387,7 @@ __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], cons
                 float zs[NX], f[NX];
 #pragma unroll
                 for (int i = 0; i < NX; ++i) zs[i] = x[i] + (z[i] + c * h * kp[i]);
-                rhs<NX, MODEL>(R.params, zs, u[0], u[1], f);
+                rhs<NX, MODEL>(R.params, mk, zs, u[0], u[1], f);
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
                     ks[i] += wg * f[i];
@@ -348,7 +395,7 @@ __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], cons
                 }
             }
 #pragma unroll
-            for (int i = 0; i < NX; ++i) z[i] += (h / 6.f) * ks[i];
+            for (int i = 0; i < NX; ++i) z[i] += h6 * ks[i];
         }
 #pragma unroll
         for (int i = 0; i < NX; ++i) xn[i] = z[i];
@@ -467,7 +514,7 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
     /* x is the deviation from the node's reference (the kernel's state coordinates) */
     const float w = V.w[i];
     const float *Qd = is_leaf ? R.QNw : R.Qw;
-    const float irho = 1.f / rho;
+    const float irho = rcp(rho);
     float la = 0.f;
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
@@ -516,13 +563,14 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
             const float ia2 = ob[4 * (size_t)V.np], ib2 = ob[5 * (size_t)V.np];
             const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
             const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
-            const float rr2 = sqrtf(dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f);
+            const float q2 = dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f;
+            const float irr = rsqrtf(q2);   /* 1 / rr2 */
+            const float rr2 = q2 * irr;
             const float g = 1.f - rr2;
             const float s = V.Y[(size_t)(row + o) * V.np + i] + rho * g;
             if (s > 0.f) {
                 la += 0.5f * s * s * irho;
                 if (GRAD) {
-                    const float irr = 1.f / rr2;
                     const float gx = -(dpar * ia2 * ch - dper * ib2 * sh) * irr;
                     const float gy = -(dpar * ia2 * sh + dper * ib2 * ch) * irr;
                     q[0] += s * gx;
@@ -580,7 +628,8 @@ __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX>
             const float ia2 = ob[4 * (size_t)V.np], ib2 = ob[5 * (size_t)V.np];
             const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
             const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
-            fn(row + o, 1.f - sqrtf(dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f));
+            const float q2 = dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f;
+            fn(row + o, 1.f - q2 * rsqrtf(q2));
         }
         row += V.nobs;
         if (V.lane) {
@@ -758,7 +807,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
     const float h00 = Quu[0][0], h01 = Quu[1][0], h11 = Quu[1][1];
     const float det = h00 * h11 - h01 * h01;
     if (!(h00 > 0.f) || !(det > 0.f)) sh.flag = 1;
-    const float idet = 1.f / det;
+    const float idet = rcp(det);
     const float g00 = h11 * idet, g01 = -h01 * idet, g11 = h00 * idet;
     float Kn[NU][NX], kn[NU];
 #pragma unroll
@@ -1200,7 +1249,7 @@ __device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V
     /* K column `lane` and k: -H_uu^-1 (Qux column, qu), closed-form 2x2 inverse as in riccati_node */
     const float det = h00 * h11 - h10 * h10;
     if (!(h00 > 0.f) || !(det > 0.f)) sh.flag = 1;
-    const float idet = 1.f / det;
+    const float idet = rcp(det);
     const float g00 = h11 * idet, g01 = -h10 * idet, g11 = h00 * idet;
     const float K0 = -(g00 * Hc[NX] + g01 * Hc[NX + 1]);
     const float K1 = -(g01 * Hc[NX] + g11 * Hc[NX + 1]);
@@ -1393,7 +1442,7 @@ __device__ void load_start(const ProbRec &R, View<NX> &V, int which) {
             for (int c = 0; c < nc; ++c) V.Y[(size_t)c * np + i] = V.wy[(size_t)c * np + i];
         } else {
             const int lf = V.leaf[i];
-            const float s = V.stage[lf] > 0 ? (float)V.stage[i] / (float)V.stage[lf] : 0.f;
+            const float s = V.stage[lf] > 0 ? (float)V.stage[i] * rcp((float)V.stage[lf]) : 0.f;
 #pragma unroll
             for (int j = 0; j < NX; ++j) x[j] = R.x0[j] + s * (V.xref[(size_t)j * np + lf] - R.x0[j]);
             u[0] = u[1] = 0.f;
@@ -1645,20 +1694,20 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             const float La0 = sums[0], ld0 = sums[1], dd0 = sums[2];
             const float dphi0 = dir[0] + dir[2];
             if (dd0 > 0.f && dphi0 - mu * dd0 > -0.5f * dir[1]) {
-                const float need = 2.f * (dphi0 + 0.5f * dir[1]) / dd0;
+                const float need = 2.f * (dphi0 + 0.5f * dir[1]) * rcp(dd0);
                 if (need > mu) mu = need;
             }
             const float phi0 = La0 + ld0 + 0.5f * mu * dd0;
             const float dphi = dphi0 - mu * dd0;
 
             /* ===== line search over alpha_i = 2^-i in chunks of G evaluated in parallel */
-            float alpha = ldexpf(1.f, -(O.n_alpha - 1));
+            float alpha = pow2neg(O.n_alpha - 1);
             bool accepted = false;
             for (int a0 = 0; a0 < O.n_alpha && !accepted; a0 += G) {
                 const int cnt = min(G, O.n_alpha - a0);
 #pragma unroll 1
                 for (int a = 0; a < cnt; ++a) {
-                    const float al = ldexpf(1.f, -(a0 + a));
+                    const float al = pow2neg(a0 + a);
                     float acc = 0.f;
                     for (int i = tid; i < n; i += nt) {
                         const int nch = V.nchild[i], fc = V.fchild[i];
@@ -1706,7 +1755,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                 for (int a = 0; a < cnt && !accepted; ++a) {
                     float s = 0.f;
                     for (int w = 0; w < nw; ++w) s += sh.red[w][a];
-                    const float al = ldexpf(1.f, -(a0 + a));
+                    const float al = pow2neg(a0 + a);
                     if (s <= O.beta * al * dphi + O.ls_rel_eps * fabsf(phi0)) {
                         alpha = al;
                         accepted = true;
@@ -1747,7 +1796,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                 V.load_u(V.U, i, u);
                 for_constraints<NX>(R, V, i, is_leaf, x, u, [&](int row, float g) {
                     const float yv = V.Y[(size_t)row * np + i];
-                    cv = fmaxf(cv, fabsf(fmaxf(g, -yv / rho)));
+                    cv = fmaxf(cv, fabsf(fmaxf(g, -yv * rcp(rho))));
                 });
             }
             cviol = block_max(cv, sh);
