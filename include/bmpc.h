@@ -268,6 +268,12 @@ const char *bmpc_status_str(int status);
 /* Library build string (architecture and version). */
 const char *bmpc_version(void);
 
+/* Test support: the device sine and cosine that the vehicle dynamics use (Cody-Waite reduction by
+ * pi/2, Taylor polynomials on [-pi/4, pi/4]; about 1.5 ulp for |a| < 1e3) on n angles.  a, s, c
+ * are device arrays of n floats; asynchronous on `stream`.  BMPC_ERR_INVALID on n < 0 or null
+ * arrays, BMPC_ERR_CUDA if the launch fails. */
+int bmpc_selftest_sincos(const float *a, float *s, float *c, int32_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

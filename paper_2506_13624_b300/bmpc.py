@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
         L.bmpc_set_problems_flat.argtypes = [C.c_void_p, C.POINTER(Problem), C.c_void_p, C.c_void_p, C.c_void_p]
         L.bmpc_get_solutions_flat.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.POINTER(Stats)]
+        L.bmpc_selftest_sincos.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
         _lib = L
     return _lib
 
@@ -102,9 +103,20 @@ EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_
             "bmpc_tree_bytes", "bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution",
             "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune",
             "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order", "bmpc_transfer_bytes",
-            "bmpc_set_problems_flat", "bmpc_get_solutions_flat", "bmpc_transfer_bytes_flat"]
+            "bmpc_set_problems_flat", "bmpc_get_solutions_flat", "bmpc_transfer_bytes_flat", "bmpc_selftest_sincos"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
+
+
+def selftest_sincos(a):
+    """Device sine and cosine of the vehicle dynamics on a float32 CUDA tensor of angles."""
+    import torch
+    assert a.is_cuda and a.dtype == torch.float32 and a.is_contiguous()
+    s, c = torch.empty_like(a), torch.empty_like(a)
+    with torch.cuda.device(a.device):
+        _check(lib().bmpc_selftest_sincos(a.data_ptr(), s.data_ptr(), c.data_ptr(), a.numel(),
+                                          torch.cuda.current_stream(a.device).cuda_stream), "bmpc_selftest_sincos")
+    return s, c
 
 
 def status_str(s: int) -> str:

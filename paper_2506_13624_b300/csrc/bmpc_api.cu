@@ -27,6 +27,7 @@ size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld
 cudaError_t prepare_solve(int model, size_t smem);
 cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order, int cnt, cudaStream_t stream);
 cudaError_t launch_flat(int which, const FlatArgs &a, int n_problems, cudaStream_t stream);
+cudaError_t launch_sincos(const float *a, float *sn, float *cs, int n, cudaStream_t stream);
 int max_block_threads();
 cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
@@ -1080,5 +1081,11 @@ const char *bmpc_status_str(int s) {
 }
 
 const char *bmpc_version(void) { return "bmpc 0.1 sm_103a fp32"; }
+
+int bmpc_selftest_sincos(const float *a, float *s, float *c, int32_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!a || !s || !c))) return BMPC_ERR_INVALID;
+    return bmpc::launch_sincos(a, s, c, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? BMPC_OK
+                                                                                            : BMPC_ERR_CUDA;
+}
 
 }  // extern "C"

@@ -100,15 +100,31 @@ __host__ __device__ constexpr int sidx(int a, int b) {
 }
 
 /* ------------------------------------------------------------------ dynamics */
-/* sin and cos of an angle by the special-function unit (__sincosf) after reducing the argument to
- * [-pi, pi] with Cody and Waite's two-constant subtraction of k 2 pi (2 pi = C1 + C2, C1 the float
- * nearest 2 pi).  On [-pi, pi] the intrinsic's absolute error is at most 2^-21.41; the reduction
- * stays accurate to that level for |a| < 1e4 rad, far beyond any heading or steering angle. */
-__device__ __forceinline__ void sincos_red(float a, float *s, float *c) {
-    constexpr float INV_2PI = 0.159154943f, C1 = 6.28318548f, C2 = -1.74845553e-7f;
-    const float k = rintf(a * INV_2PI);
-    const float r = fmaf(-k, C2, fmaf(-k, C1, a));
-    __sincosf(r, s, c);
+/* sin and cos of an angle, accurate to about 1.5 ulp for |a| < 1e3 rad: Cody and Waite's reduction
+ * a = q pi/2 + r with pi/2 split into three floats (P1 the float nearest pi/2, P2 and P3 the next
+ * parts of the remainder), then the Taylor polynomials of sin r to r^9 and cos r to r^8 on
+ * |r| <= pi/4 (truncation below 2e-9) in Horner form, and the quadrant's swap and signs.  Only
+ * FMA-pipe arithmetic and no slow path: the dynamics evaluate it at every RK4 stage, and its
+ * values and the analytic Jacobians built from them stay consistent to rounding, which the KKT
+ * tolerance of 1e-5 in FP32 needs. */
+__device__ __forceinline__ void sincos_cw(float a, float *s, float *c) {
+    constexpr float TWO_OVER_PI = 0.636619772f;
+    constexpr float P1 = 1.57079637f, P2 = -4.37113883e-8f, P3 = -1.71512451e-15f;
+    const float qf = rintf(a * TWO_OVER_PI);
+    const int q = (int)qf;
+    const float r = fmaf(-qf, P3, fmaf(-qf, P2, fmaf(-qf, P1, a)));
+    const float r2 = r * r;
+    float ps = fmaf(r2, 1.f / 362880.f, -1.f / 5040.f);
+    ps = fmaf(ps, r2, 1.f / 120.f);
+    ps = fmaf(ps, r2, -1.f / 6.f);
+    const float sr = fmaf(ps * r2, r, r);
+    float pc = fmaf(r2, 1.f / 40320.f, -1.f / 720.f);
+    pc = fmaf(pc, r2, 1.f / 24.f);
+    pc = fmaf(pc, r2, -0.5f);
+    const float cr = fmaf(pc, r2, 1.f);
+    const float ss = (q & 1) ? cr : sr, cc = (q & 1) ? sr : cr;
+    *s = (q & 2) ? -ss : ss;
+    *c = ((q + 1) & 2) ? -cc : cc;
 }
 
 /* Reciprocal by the PTX approximate instruction (rcp.approx.ftz.f32: at most 1 ulp of error over
@@ -134,7 +150,7 @@ __device__ __forceinline__ ModelK model_k(const float *prm, float dl) {
     ModelK k{0.f, 0.f, 0.f, 0.f};
     if constexpr (MODEL == 0) {
         float sd, cd;
-        sincos_red(dl, &sd, &cd);
+        sincos_cw(dl, &sd, &cd);
         k.iL = rcp(prm[0]);
         k.td = sd * rcp(cd);
     } else if constexpr (MODEL == 1) {
@@ -159,7 +175,7 @@ __device__ __forceinline__ void rhs_jac(const float *prm, const ModelK &mk, cons
     }
     if constexpr (MODEL == 0) {
         float sp, cp;
-        sincos_red(s[2], &sp, &cp);
+        sincos_cw(s[2], &sp, &cp);
         const float td = mk.td, iL = mk.iL;
         const float v = s[3];
         f[0] = v * cp;
@@ -188,7 +204,7 @@ __device__ __forceinline__ void rhs_jac(const float *prm, const ModelK &mk, cons
         const float af = atanf(tf) - dl, ar = atanf(tr);
         const float Ff = -Cf * af, Fr = -Cr * ar;
         float sp, cp;
-        sincos_red(psi, &sp, &cp);
+        sincos_cw(psi, &sp, &cp);
         f[0] = vx * cp - vy * sp;
         f[1] = vx * sp + vy * cp;
         f[2] = r;
@@ -226,7 +242,7 @@ __device__ __forceinline__ void rhs(const float *prm, const ModelK &mk, const fl
                                     float (&f)[NX]) {
     if constexpr (MODEL == 0) {
         float sp, cp;
-        sincos_red(s[2], &sp, &cp);
+        sincos_cw(s[2], &sp, &cp);
         f[0] = s[3] * cp;
         f[1] = s[3] * sp;
         f[2] = s[3] * mk.td * mk.iL;
@@ -242,7 +258,7 @@ __device__ __forceinline__ void rhs(const float *prm, const ModelK &mk, const fl
         const float Ff = -Cf * (atanf((vy + lf * r) * ivb) - dl);
         const float Fr = -Cr * atanf((vy - lr * r) * ivb);
         float sp, cp;
-        sincos_red(s[2], &sp, &cp);
+        sincos_cw(s[2], &sp, &cp);
         f[0] = vx * cp - vy * sp;
         f[1] = vx * sp + vy * cp;
         f[2] = r;
@@ -807,7 +823,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
     const float h00 = Quu[0][0], h01 = Quu[1][0], h11 = Quu[1][1];
     const float det = h00 * h11 - h01 * h01;
     if (!(h00 > 0.f) || !(det > 0.f)) sh.flag = 1;
-    const float idet = rcp(det);
+    const float idet = 1.f / det;   /* IEEE-rounded: the direction's accuracy sets the FP32 KKT floor */
     const float g00 = h11 * idet, g01 = -h01 * idet, g11 = h00 * idet;
     float Kn[NU][NX], kn[NU];
 #pragma unroll
@@ -1249,7 +1265,7 @@ __device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V
     /* K column `lane` and k: -H_uu^-1 (Qux column, qu), closed-form 2x2 inverse as in riccati_node */
     const float det = h00 * h11 - h10 * h10;
     if (!(h00 > 0.f) || !(det > 0.f)) sh.flag = 1;
-    const float idet = rcp(det);
+    const float idet = 1.f / det;   /* IEEE-rounded: the direction's accuracy sets the FP32 KKT floor */
     const float g00 = h11 * idet, g01 = -h10 * idet, g11 = h00 * idet;
     const float K0 = -(g00 * Hc[NX] + g01 * Hc[NX + 1]);
     const float K1 = -(g01 * Hc[NX] + g11 * Hc[NX + 1]);
@@ -1931,6 +1947,17 @@ __global__ void __launch_bounds__(1024) bmpc_order_kernel(const ProbRec *recs, c
 cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order, int cnt, cudaStream_t stream) {
     if (cnt <= 1) return cudaSuccess;
     bmpc_order_kernel<<<(cnt + ORDER_TILE - 1) / ORDER_TILE, 1024, 0, stream>>>(recs, stats, order, cnt);
+    return cudaGetLastError();
+}
+
+/* Device sin/cos of the dynamics on n angles (self-test of sincos_cw against its error bound). */
+__global__ void bmpc_sincos_kernel(const float *a, float *sn, float *cs, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) sincos_cw(a[i], sn + i, cs + i);
+}
+
+cudaError_t launch_sincos(const float *a, float *sn, float *cs, int n, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    bmpc_sincos_kernel<<<(n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184, 256, 0, stream>>>(a, sn, cs, n);
     return cudaGetLastError();
 }
 
