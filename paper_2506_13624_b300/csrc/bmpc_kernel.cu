@@ -48,7 +48,13 @@ constexpr int MAX_BLOCK = 256;
 #define BMPC_MIN_BLOCKS 2   /* 256 threads x 2 blocks: at most 128 registers per thread */
 #endif
 constexpr int MAX_WARPS = MAX_BLOCK / 32;
-constexpr int MAX_CHUNK = 16;   /* at most 16 step sizes per line-search round */
+constexpr int MAX_CHUNK = 16;
+/* Node loops with their loads hoisted ahead of their stores (one or two batches of loads per node
+ * instead of one L2 round trip per stored component).  Only where the registers allow it: the
+ * dynamic model's kernel is at its register limit, and there the longer live ranges cost more in
+ * spills than the hoisting saves (measured), so it keeps the load-compute-store order per row. */
+template <int NX>
+constexpr bool hoist_loads() { return NX <= 4; }   /* at most 16 step sizes per line-search round */
 
 constexpr int GL = 8;   /* lanes per path in the cooperative sweeps (one per column of [A B], nx + nu <= 8) */
 
@@ -1067,37 +1073,86 @@ __device__ __forceinline__ void forward_node(const View<NX> &V, int i, int pa, b
  * directional terms of the merit (grad'dz, dz'W dz, (dlam - lam)'d). */
 template <int NX, int MODEL>
 __device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, const View<NX> &V, float (&dir)[3]) {
+    constexpr bool HOIST_LOADS = hoist_loads<NX>();
     const int tid = threadIdx.x, nt = blockDim.x, np = V.np;
     for (int i = tid; i < V.n; i += nt) {
-        const int nch = V.nchild[i];
-        float dxv[NX], duv[NU];
-        V.load_x(V.dx, i, dxv);
-        V.load_u(V.du, i, duv);
-        const float w = V.w[i];
-        const float *Qd = nch ? R.Qw : R.QNw;
-        const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
-#pragma unroll
-        for (int a = 0; a < NX; ++a) {
-            dir[0] += V.q[(size_t)a * np + i] * dxv[a];
-            dir[1] += w * Qd[a] * dxv[a] * dxv[a];
-        }
-        dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
-        if (nch) {
-#pragma unroll
-            for (int a = 0; a < NU; ++a) {
-                dir[0] += V.r[(size_t)a * np + i] * duv[a];
-                dir[1] += (w * R.Rw[a] + V.hr[(size_t)a * np + i]) * duv[a] * duv[a];
+        if constexpr (HOIST_LOADS) {
+            /* two batches of loads: the direction with the cost and penalty terms, then (after the
+             * first merit terms) the value function, multipliers and defect for lam_QP */
+            const int nch = V.nchild[i];
+            float dxv[NX], duv[NU], qv[NX], rv[NU], hrv[NU];
+            V.load_x(V.dx, i, dxv);
+            V.load_u(V.du, i, duv);
+            const float w = V.w[i];
+            const float *Qd = nch ? R.Qw : R.QNw;
+            const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+            V.load_x(V.q, i, qv);
+            if (nch) {
+                V.load_u(V.r, i, rv);
+                V.load_u(V.hr, i, hrv);
             }
-        }
-        if (i != 0) {
-#pragma unroll
+    #pragma unroll
             for (int a = 0; a < NX; ++a) {
-                float v = V.p[(size_t)a * np + i];
-#pragma unroll
-                for (int b = 0; b < NX; ++b) v += V.P[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
-                V.lq[(size_t)a * np + i] = v;
-                const float lam = V.L[(size_t)a * np + i];
-                dir[2] += ((v - lam) - lam) * V.d[(size_t)a * np + i];
+                dir[0] += qv[a] * dxv[a];
+                dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+            }
+            dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
+            if (nch) {
+    #pragma unroll
+                for (int a = 0; a < NU; ++a) {
+                    dir[0] += rv[a] * duv[a];
+                    dir[1] += (w * R.Rw[a] + hrv[a]) * duv[a] * duv[a];
+                }
+            }
+            if (i != 0) {
+                float pv[NX], Pv[nsym(NX)], lv[NX], dv[NX], lqv[NX];
+                V.load_x(V.p, i, pv);
+    #pragma unroll
+                for (int e = 0; e < nsym(NX); ++e) Pv[e] = V.P[(size_t)e * np + i];
+                V.load_x(V.L, i, lv);
+                V.load_x(V.d, i, dv);
+    #pragma unroll
+                for (int a = 0; a < NX; ++a) {
+                    float v = pv[a];
+    #pragma unroll
+                    for (int b = 0; b < NX; ++b) v += Pv[sidx<NX>(a, b)] * dxv[b];
+                    lqv[a] = v;
+                    const float lam = lv[a];
+                    dir[2] += ((v - lam) - lam) * dv[a];
+                }
+                V.store_x(V.lq, i, lqv);
+            }
+        } else {
+            const int nch = V.nchild[i];
+            float dxv[NX], duv[NU];
+            V.load_x(V.dx, i, dxv);
+            V.load_u(V.du, i, duv);
+            const float w = V.w[i];
+            const float *Qd = nch ? R.Qw : R.QNw;
+            const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+    #pragma unroll
+            for (int a = 0; a < NX; ++a) {
+                dir[0] += V.q[(size_t)a * np + i] * dxv[a];
+                dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+            }
+            dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
+            if (nch) {
+    #pragma unroll
+                for (int a = 0; a < NU; ++a) {
+                    dir[0] += V.r[(size_t)a * np + i] * duv[a];
+                    dir[1] += (w * R.Rw[a] + V.hr[(size_t)a * np + i]) * duv[a] * duv[a];
+                }
+            }
+            if (i != 0) {
+    #pragma unroll
+                for (int a = 0; a < NX; ++a) {
+                    float v = V.p[(size_t)a * np + i];
+    #pragma unroll
+                    for (int b = 0; b < NX; ++b) v += V.P[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
+                    V.lq[(size_t)a * np + i] = v;
+                    const float lam = V.L[(size_t)a * np + i];
+                    dir[2] += ((v - lam) - lam) * V.d[(size_t)a * np + i];
+                }
             }
         }
     }
@@ -1516,7 +1571,30 @@ __device__ float start_merit(const ProbRec &R, const View<NX> &V, float rho, flo
 /* The accepted step at node i: x += a dx, u += a du (in registers, caller stores) and, except at
  * the root, lam += a (lam_QP - lam) in memory (Algorithm 1, update after the line search). */
 template <int NX>
-__device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU]) {
+__device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU],
+                                           float (&lam)[NX]) {
+    /* every row is loaded before anything is computed or stored, so the loads go out together;
+     * the caller stores x, u and (for i != 0) lam after the rest of its node work */
+    float dxv[NX], duv[NU], lmv[NX], lqv[NX];
+    V.load_x(V.dx, i, dxv);
+    V.load_u(V.du, i, duv);
+    if (i != 0) {
+        V.load_x(V.L, i, lmv);
+        V.load_x(V.lq, i, lqv);
+    }
+#pragma unroll
+    for (int j = 0; j < NX; ++j) x[j] += a * dxv[j];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) u[j] += a * duv[j];
+    if (i != 0) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) lam[j] = lmv[j] + a * (lqv[j] - lmv[j]);
+    }
+}
+
+/* The same step row by row, storing lam_i as it goes (the register-lean form; see hoist_loads). */
+template <int NX>
+__device__ __forceinline__ void apply_step_serial(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU]) {
     const int np = V.np;
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
@@ -1532,10 +1610,11 @@ __device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, fl
 
 /* ------------------------------------------------------------------ the per-problem solver */
 template <int NX, int MODEL>
-__device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
+__device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
                               float *fs, Stats *stat, const KOpts &O, Shared &sh, int32_t *tab, int tab_cap,
                               float *stg, int stg_ld) {
     constexpr int NS = nsym(NX);
+    constexpr bool HOIST_LOADS = hoist_loads<NX>();
     View<NX> V(R, ib, fin, fw, fout, fs);
     /* stage and path tables into shared memory: the sweeps index through them at every stage */
     const int64_t tn = table_ints(R.npad, R.n_stage, R.n_paths);
@@ -1588,33 +1667,71 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
              * previous line search, node by node: x += a dx, u += a du, lam += a (lam_QP - lam)) */
             long long t0 = clock64();
             for (int i = tid; i < n; i += nt) {
-                const bool is_leaf = V.nchild[i] == 0;
-                float x[NX], u[NU], q[NX], r[NU], hq[3], hr[NU];
-                V.load_x(V.X, i, x);
-                V.load_u(V.U, i, u);
-                if (pending > 0.f) {
-                    apply_step<NX>(V, i, pending, x, u);
-                    V.store_x(V.X, i, x);
-                    V.store_u(V.U, i, u);
-                }
-                const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, rho, q, r, hq, hr);
-                V.store_x(V.q, i, q);
-                V.store_u(V.r, i, r);
-                V.hq[i] = hq[0];
-                V.hq[(size_t)np + i] = hq[1];
-                V.hq[2 * (size_t)np + i] = hq[2];
-                V.store_u(V.hr, i, hr);
-                V.nv[i] = la;
-                if (!is_leaf) {
-                    float xa[NX], xn[NX];
-#pragma unroll
-                    for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
-                    /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
-                    dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
-                        if (c < NX) V.A[(size_t)(a * NX + c) * np + i] = v;
-                        else V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
-                    });
-                    V.store_x(V.f, i, xn);
+                if constexpr (HOIST_LOADS) {
+                    /* loads first (the node's rows, the step, the constraint data), stores last: a
+                     * store the compiler cannot prove distinct would hold back every later load */
+                    const bool is_leaf = V.nchild[i] == 0;
+                    float x[NX], u[NU], lam[NX], q[NX], r[NU], hq[3], hr[NU];
+                    V.load_x(V.X, i, x);
+                    V.load_u(V.U, i, u);
+                    const bool step = pending > 0.f;
+                    if (step) apply_step<NX>(V, i, pending, x, u, lam);
+                    const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, rho, q, r, hq, hr);
+                    float xa[NX];
+                    if (!is_leaf) {
+    #pragma unroll
+                        for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
+                    }
+                    if (step) {
+                        V.store_x(V.X, i, x);
+                        V.store_u(V.U, i, u);
+                        if (i != 0) V.store_x(V.L, i, lam);
+                    }
+                    V.store_x(V.q, i, q);
+                    V.store_u(V.r, i, r);
+                    V.hq[i] = hq[0];
+                    V.hq[(size_t)np + i] = hq[1];
+                    V.hq[2 * (size_t)np + i] = hq[2];
+                    V.store_u(V.hr, i, hr);
+                    V.nv[i] = la;
+                    if (!is_leaf) {
+                        float xn[NX];
+                        /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
+                        dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
+                            if (c < NX) V.A[(size_t)(a * NX + c) * np + i] = v;
+                            else V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                        });
+                        V.store_x(V.f, i, xn);
+                    }
+                } else {
+                    const bool is_leaf = V.nchild[i] == 0;
+                    float x[NX], u[NU], q[NX], r[NU], hq[3], hr[NU];
+                    V.load_x(V.X, i, x);
+                    V.load_u(V.U, i, u);
+                    if (pending > 0.f) {
+                        apply_step_serial<NX>(V, i, pending, x, u);
+                        V.store_x(V.X, i, x);
+                        V.store_u(V.U, i, u);
+                    }
+                    const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, rho, q, r, hq, hr);
+                    V.store_x(V.q, i, q);
+                    V.store_u(V.r, i, r);
+                    V.hq[i] = hq[0];
+                    V.hq[(size_t)np + i] = hq[1];
+                    V.hq[2 * (size_t)np + i] = hq[2];
+                    V.store_u(V.hr, i, hr);
+                    V.nv[i] = la;
+                    if (!is_leaf) {
+                        float xa[NX], xn[NX];
+    #pragma unroll
+                        for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
+                        /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
+                        dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
+                            if (c < NX) V.A[(size_t)(a * NX + c) * np + i] = v;
+                            else V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                        });
+                        V.store_x(V.f, i, xn);
+                    }
                 }
             }
             __syncthreads();
@@ -1623,53 +1740,126 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
             float rk = 0.f;
             float sums[3] = {0.f, 0.f, 0.f};   /* L_a, lam'd, |d|^2 */
             for (int i = tid; i < n; i += nt) {
-                const int nch = V.nchild[i], fc = V.fchild[i];
-                float lsum[NX];
-#pragma unroll
-                for (int j = 0; j < NX; ++j) lsum[j] = 0.f;
-                for (int m = fc; m < fc + nch; ++m)
-#pragma unroll
-                    for (int j = 0; j < NX; ++j) lsum[j] += V.L[(size_t)j * np + m];
-                float ld = 0.f, dd = 0.f;
-                if (i != 0) {
-                    const int pa = V.parent[i];
-                    float gx[NX];
-#pragma unroll
-                    for (int j = 0; j < NX; ++j) {
-                        const float dref = V.xref[(size_t)j * np + pa] - V.xref[(size_t)j * np + i];
-                        const float dj = (dref + (V.X[(size_t)j * np + pa] - V.X[(size_t)j * np + i])) +
-                                         V.f[(size_t)j * np + pa];
-                        V.d[(size_t)j * np + i] = dj;
-                        const float lj = V.L[(size_t)j * np + i];
-                        ld += lj * dj;
-                        dd += dj * dj;
-                        rk = fmaxf(rk, fabsf(dj));
-                        gx[j] = V.q[(size_t)j * np + i] - lj;
+                if constexpr (HOIST_LOADS) {
+                    /* two batches of loads: the node's and its parent's rows with the children's
+                     * multipliers (defect and the first gradient terms, then the stores of d and the
+                     * merit terms), then the Jacobians A_i, B_i and r_i for the coupling terms */
+                    const int nch = V.nchild[i], fc = V.fchild[i];
+                    const int pa = i ? V.parent[i] : 0;
+                    const float la_i = V.nv[i];
+                    float lsum[NX];
+    #pragma unroll
+                    for (int j = 0; j < NX; ++j) lsum[j] = 0.f;
+                    for (int m = fc; m < fc + nch; ++m)
+    #pragma unroll
+                        for (int j = 0; j < NX; ++j) lsum[j] += V.L[(size_t)j * np + m];
+                    float xi[NX], xri[NX], li[NX], qi[NX], xp[NX], xrp[NX], fp[NX];
+                    V.load_x(V.X, i, xi);
+                    V.load_x(V.xref, i, xri);
+                    V.load_x(V.L, i, li);
+                    V.load_x(V.q, i, qi);
+                    V.load_x(V.X, pa, xp);
+                    V.load_x(V.xref, pa, xrp);
+                    V.load_x(V.f, pa, fp);
+                    float ld = 0.f, dd = 0.f, gx[NX];
+                    if (i != 0) {
+                        float dv[NX];
+    #pragma unroll
+                        for (int j = 0; j < NX; ++j) {
+                            const float dref = xrp[j] - xri[j];
+                            const float dj = (dref + (xp[j] - xi[j])) + fp[j];
+                            dv[j] = dj;
+                            const float lj = li[j];
+                            ld += lj * dj;
+                            dd += dj * dj;
+                            rk = fmaxf(rk, fabsf(dj));
+                            gx[j] = qi[j] - lj;
+                        }
+                        V.store_x(V.d, i, dv);
+                    }
+                    V.nv[(size_t)np + i] = ld;
+                    V.nv[2 * (size_t)np + i] = dd;
+                    if (nch) {
+                        float Ai[NX][NX], Bi[NX][NU], ri[NU];
+    #pragma unroll
+                        for (int a = 0; a < NX; ++a) {
+    #pragma unroll
+                            for (int b = 0; b < NX; ++b) Ai[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
+    #pragma unroll
+                            for (int b = 0; b < NU; ++b) Bi[a][b] = V.B[(size_t)(a * NU + b) * np + i];
+                        }
+                        V.load_u(V.r, i, ri);
+                        if (i != 0) {
+    #pragma unroll
+                            for (int a = 0; a < NX; ++a)
+    #pragma unroll
+                                for (int b = 0; b < NX; ++b) gx[b] += Ai[a][b] * lsum[a];
+                        }
+    #pragma unroll
+                        for (int b = 0; b < NU; ++b) {
+                            float gu = ri[b];
+    #pragma unroll
+                            for (int a = 0; a < NX; ++a) gu += Bi[a][b] * lsum[a];
+                            rk = fmaxf(rk, fabsf(gu));
+                        }
+                    }
+                    if (i != 0) {
+    #pragma unroll
+                        for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
+                    }
+                    if (!(rk == rk)) rk = INFINITY;
+                    sums[0] += la_i;
+                    sums[1] += ld;
+                    sums[2] += dd;
+                } else {
+                    const int nch = V.nchild[i], fc = V.fchild[i];
+                    float lsum[NX];
+    #pragma unroll
+                    for (int j = 0; j < NX; ++j) lsum[j] = 0.f;
+                    for (int m = fc; m < fc + nch; ++m)
+    #pragma unroll
+                        for (int j = 0; j < NX; ++j) lsum[j] += V.L[(size_t)j * np + m];
+                    float ld = 0.f, dd = 0.f;
+                    if (i != 0) {
+                        const int pa = V.parent[i];
+                        float gx[NX];
+    #pragma unroll
+                        for (int j = 0; j < NX; ++j) {
+                            const float dref = V.xref[(size_t)j * np + pa] - V.xref[(size_t)j * np + i];
+                            const float dj = (dref + (V.X[(size_t)j * np + pa] - V.X[(size_t)j * np + i])) +
+                                             V.f[(size_t)j * np + pa];
+                            V.d[(size_t)j * np + i] = dj;
+                            const float lj = V.L[(size_t)j * np + i];
+                            ld += lj * dj;
+                            dd += dj * dj;
+                            rk = fmaxf(rk, fabsf(dj));
+                            gx[j] = V.q[(size_t)j * np + i] - lj;
+                        }
+                        if (nch) {
+    #pragma unroll
+                            for (int a = 0; a < NX; ++a)
+    #pragma unroll
+                                for (int b = 0; b < NX; ++b) gx[b] += aload<NX, MODEL>(V.A, np, i, a, b) * lsum[a];
+                        }
+    #pragma unroll
+                        for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
                     }
                     if (nch) {
-#pragma unroll
-                        for (int a = 0; a < NX; ++a)
-#pragma unroll
-                            for (int b = 0; b < NX; ++b) gx[b] += aload<NX, MODEL>(V.A, np, i, a, b) * lsum[a];
+    #pragma unroll
+                        for (int b = 0; b < NU; ++b) {
+                            float gu = V.r[(size_t)b * np + i];
+    #pragma unroll
+                            for (int a = 0; a < NX; ++a) gu += V.B[(size_t)(a * NU + b) * np + i] * lsum[a];
+                            rk = fmaxf(rk, fabsf(gu));
+                        }
                     }
-#pragma unroll
-                    for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
+                    if (!(rk == rk)) rk = INFINITY;
+                    V.nv[(size_t)np + i] = ld;
+                    V.nv[2 * (size_t)np + i] = dd;
+                    sums[0] += V.nv[i];
+                    sums[1] += ld;
+                    sums[2] += dd;
                 }
-                if (nch) {
-#pragma unroll
-                    for (int b = 0; b < NU; ++b) {
-                        float gu = V.r[(size_t)b * np + i];
-#pragma unroll
-                        for (int a = 0; a < NX; ++a) gu += V.B[(size_t)(a * NU + b) * np + i] * lsum[a];
-                        rk = fmaxf(rk, fabsf(gu));
-                    }
-                }
-                if (!(rk == rk)) rk = INFINITY;
-                V.nv[(size_t)np + i] = ld;
-                V.nv[2 * (size_t)np + i] = dd;
-                sums[0] += V.nv[i];
-                sums[1] += ld;
-                sums[2] += dd;
             }
             r_kkt = block_max(rk, sh);
             block_sum<3>(sums, sh);
@@ -1793,7 +1983,7 @@ __device__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *
                     float x[NX], u[NU];
                     V.load_x(V.X, i, x);
                     V.load_u(V.U, i, u);
-                    apply_step<NX>(V, i, pending, x, u);
+                    apply_step_serial<NX>(V, i, pending, x, u);
                     V.store_x(V.X, i, x);
                     V.store_u(V.U, i, u);
                 }
@@ -1885,6 +2075,7 @@ __global__ void __launch_bounds__(MAX_BLOCK, BMPC_MIN_BLOCKS) bmpc_solve_kernel(
     constexpr int NX = MODEL == 1 ? 6 : 4;
     __shared__ Shared sh;
     __shared__ int pid_s;
+    __shared__ ProbRec rec_s;
     extern __shared__ int32_t tab_s[];
     float *stg = reinterpret_cast<float *>(tab_s + ((args.tab_ints + 3) & ~3));
     for (;;) {
@@ -1894,7 +2085,15 @@ __global__ void __launch_bounds__(MAX_BLOCK, BMPC_MIN_BLOCKS) bmpc_solve_kernel(
         __syncthreads();
         if (slot >= args.n_problems) break;
         const int pid = args.order[slot];
-        const ProbRec &R = args.recs[pid];
+        /* the problem record in shared memory: its constants are read inside every node loop, and
+         * from shared memory no global store can hold those reads back */
+        {
+            const int4 *src = reinterpret_cast<const int4 *>(args.recs + pid);
+            int4 *dst = reinterpret_cast<int4 *>(&rec_s);
+            for (int j = threadIdx.x; j < (int)(sizeof(ProbRec) / sizeof(int4)); j += blockDim.x) dst[j] = src[j];
+        }
+        __syncthreads();
+        const ProbRec &R = rec_s;
         solve_problem<NX, MODEL>(R, args.ibase + R.off_int, args.inbase + R.off_in, args.warmbase + R.off_warm,
                                  args.outbase + R.off_out, args.scr + R.off_scr, args.stats + pid, args.opts, sh,
                                  tab_s, args.tab_ints, args.stg_ld ? stg : nullptr, args.stg_ld);

@@ -39,6 +39,8 @@ struct alignas(16) ProbRec {
     float Alin[16], Blin[8];
 };
 
+static_assert(sizeof(ProbRec) % 16 == 0, "the solver copies a record to shared memory in 16-byte words");
+
 /* int region of one problem (int32 elements):
  *   node rows (npad each): parent, nchild, fchild (first child), stage, leaf (first leaf
  *   descendant), owner (index of the path of that leaf; the path that processes the node in
