@@ -48,13 +48,13 @@ constexpr int MAX_BLOCK = 256;
 #define BMPC_MIN_BLOCKS 2   /* 256 threads x 2 blocks: at most 128 registers per thread */
 #endif
 constexpr int MAX_WARPS = MAX_BLOCK / 32;
-constexpr int MAX_CHUNK = 16;
+constexpr int MAX_CHUNK = 16;   /* at most 16 step sizes per line-search round */
 /* Node loops with their loads hoisted ahead of their stores (one or two batches of loads per node
  * instead of one L2 round trip per stored component).  Only where the registers allow it: the
  * dynamic model's kernel is at its register limit, and there the longer live ranges cost more in
  * spills than the hoisting saves (measured), so it keeps the load-compute-store order per row. */
 template <int NX>
-constexpr bool hoist_loads() { return NX <= 4; }   /* at most 16 step sizes per line-search round */
+constexpr bool hoist_loads() { return NX <= 4; }
 
 constexpr int GL = 8;   /* lanes per path in the cooperative sweeps (one per column of [A B], nx + nu <= 8) */
 
