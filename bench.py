@@ -309,18 +309,31 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers, every step: the batch's node-major inputs
     # (pinned host arrays a control loop overwrites in place) copied host to device and laid out
-    # on the device, the solve, and the node-major solutions copied back into pinned host arrays
-    fin, fout = b.flat_inputs(), b.flat_outputs()
-    b.set_problems_flat(*fin)
-    b.solve(opts, graph=True)
-    b.get_solutions_flat(fout)
+    # on the device, the solve, and the node-major solutions copied back into pinned host arrays.
+    # Two handles on two streams take the steps in turn, so that one step's copies overlap the
+    # other handle's solve; a handle waits for its previous step before it is reused.
+    b2 = bmpc.Batch(problems, stream=torch.cuda.Stream())
+    b2.set_problems()
+    pipe = (b, b2)
+    fin = b.flat_inputs()
+    fouts = (b.flat_outputs(), b2.flat_outputs())
+    for j, bb in enumerate(pipe):
+        bb.set_problems_flat(*fin)
+        bb.solve(opts, graph=True)
+        bb.get_solutions_flat(fouts[j])
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        b.set_problems_flat(*fin)
-        b.solve(opts, graph=True)
-        b.get_solutions_flat(fout)
+    for k in range(args.e2e_steps):
+        bb = pipe[k % 2]
+        if k >= 2:
+            bb.wait_solutions(want_stats=False)
+        bb.set_problems_flat(*fin)
+        bb.solve(opts, graph=True)
+        bb.get_solutions_flat_async(fouts[k % 2])
+    e2e_stats = [bb.wait_solutions() for bb in pipe]
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_conv = [int(sum(st[i].status == 0 for i in range(bb.n))) for bb, st in zip(pipe, e2e_stats)]
     h2d, d2h = b.transfer_bytes_flat()
+    b2.close()
 
     ms_max, e2e_max, total_conv = reduce_over_ranks(ms, e2e_s, n_conv, dist if world > 1 else None, "cuda")
     if rank != 0:
@@ -365,7 +378,9 @@ def run_gpu(args):
                      "traffic_unit": "bytes per launch (ncu dram read + write, scaled by problems)",
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"},
         "e2e": {"value": total_conv / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+                "converged_per_step": e2e_conv,
+                "pipeline": "two handles on two streams in turn: one step's copies overlap the other's solve"},
         "clocks": clocks,
     }
     if cpu is not None:
@@ -390,7 +405,7 @@ def main():
     ap.add_argument("--queue-order", type=int, default=1, choices=[0, 1])
     ap.add_argument("--max-iters", type=int, default=0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4, help="oracle problems per worker per reference step")

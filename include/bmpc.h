@@ -220,6 +220,19 @@ int bmpc_set_problems_flat(bmpc_batch *b, const bmpc_problem *probs, const float
  * Synchronises the handle's stream.  Values equal bmpc_get_solutions'. */
 int bmpc_get_solutions_flat(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats);
 
+/* Asynchronous form of bmpc_get_solutions_flat. It enqueues on the handle's stream the device
+ * packing, one copy per array into x, u, lam, y (any may be NULL; pinned host memory for
+ * asynchronous copies), and the copy of the statistics into the handle's staging area. It then
+ * returns without waiting. The arrays hold the solutions once bmpc_wait_solutions has returned.
+ * Two handles on two streams can overlap one batch's transfers with another batch's solve.
+ * BMPC_ERR_INVALID on a null handle; BMPC_ERR_CUDA if a copy or launch is refused. */
+int bmpc_get_solutions_flat_async(bmpc_batch *b, float *x, float *u, float *lam, float *y);
+
+/* Waits for the handle's stream. With stats != NULL it fills the per-problem statistics that the
+ * last bmpc_get_solutions_flat_async copied. The handle's next bmpc_set_problems_flat may
+ * overwrite its staging area only after this wait. BMPC_ERR_CUDA on a failed stream. */
+int bmpc_wait_solutions(bmpc_batch *b, bmpc_stats *stats);
+
 /* Bytes one bmpc_set_problems_flat copies host to device (records, xref, weight, obs) and one
  * bmpc_get_solutions_flat copies device to host (x, u, lam, y, statistics). */
 int bmpc_transfer_bytes_flat(const bmpc_batch *b, size_t *h2d, size_t *d2h);

@@ -94,6 +94,8 @@ def lib() -> C.CDLL:
         L.bmpc_get_solutions_flat.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.POINTER(Stats)]
         L.bmpc_selftest_sincos.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+        L.bmpc_get_solutions_flat_async.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.bmpc_wait_solutions.argtypes = [C.c_void_p, C.POINTER(Stats)]
         _lib = L
     return _lib
 
@@ -103,7 +105,8 @@ EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_
             "bmpc_tree_bytes", "bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution",
             "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune",
             "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order", "bmpc_transfer_bytes",
-            "bmpc_set_problems_flat", "bmpc_get_solutions_flat", "bmpc_transfer_bytes_flat", "bmpc_selftest_sincos"]
+            "bmpc_set_problems_flat", "bmpc_get_solutions_flat", "bmpc_transfer_bytes_flat", "bmpc_selftest_sincos",
+            "bmpc_get_solutions_flat_async", "bmpc_wait_solutions"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -294,6 +297,20 @@ class Batch:
             _check(lib().bmpc_get_solutions_flat(self.handle, *(C.c_void_p(t.data_ptr()) for t in out), st),
                    "bmpc_get_solutions_flat")
         return (*out, st)
+
+    def get_solutions_flat_async(self, out):
+        """Enqueue the packing and the copies of the solutions into `out` (a tuple from
+        flat_outputs, pinned) and of the statistics, without waiting; see wait_solutions."""
+        with self.torch.cuda.device(self.device):
+            _check(lib().bmpc_get_solutions_flat_async(self.handle, *(C.c_void_p(t.data_ptr()) for t in out)),
+                   "bmpc_get_solutions_flat_async")
+
+    def wait_solutions(self, want_stats: bool = True):
+        """Wait for the batch's stream; the statistics of the last asynchronous read (ctypes array)."""
+        st = (Stats * self.n)() if want_stats else None
+        with self.torch.cuda.device(self.device):
+            _check(lib().bmpc_wait_solutions(self.handle, st), "bmpc_wait_solutions")
+        return st
 
     def transfer_bytes_flat(self):
         """(host-to-device bytes per set_problems_flat, device-to-host bytes per get_solutions_flat)."""

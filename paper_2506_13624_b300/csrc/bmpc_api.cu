@@ -902,6 +902,28 @@ out:
     return BMPC_OK;
 }
 
+/* Public statistics from the device records copied into the staging area. */
+static void stats_from_stage(const bmpc_batch *b, bmpc_stats *stats) {
+    const Stats *s = at<const Stats>(b->stage, b->L.stats);
+    for (int k = 0; k < b->n; ++k) {
+        stats[k].status = s[k].status;
+        stats[k].inner_iters = s[k].inner_iters;
+        stats[k].outer_iters = s[k].outer_iters;
+        stats[k].ls_fail_total = s[k].ls_fail_total;
+        stats[k].ls_evals = s[k].ls_evals;
+        stats[k].start_used = s[k].start_used;
+        stats[k].r_kkt = s[k].r_kkt;
+        stats[k].c = s[k].c;
+        stats[k].rho = s[k].rho;
+        stats[k].mu = s[k].mu;
+        stats[k].cycles_linearise = s[k].cyc_lin;
+        stats[k].cycles_backward = s[k].cyc_bwd;
+        stats[k].cycles_forward = s[k].cyc_fwd;
+        stats[k].cycles_linesearch = s[k].cyc_ls;
+        stats[k].cycles_total = s[k].cyc_total;
+    }
+}
+
 int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats) {
     if (!b) return BMPC_ERR_INVALID;
     cudaError_t e = cudaSuccess;
@@ -947,26 +969,7 @@ int bmpc_get_solutions(bmpc_batch *b, float *x, float *u, float *lam, float *y, 
                 if (y) y[oy + (size_t)i * R.nc + c] = base[(size_t)(orw.y + c) * np + i];
         }
     });
-    if (stats) {
-        const Stats *s = at<const Stats>(b->stage, b->L.stats);
-        for (int k = 0; k < b->n; ++k) {
-            stats[k].status = s[k].status;
-            stats[k].inner_iters = s[k].inner_iters;
-            stats[k].outer_iters = s[k].outer_iters;
-            stats[k].ls_fail_total = s[k].ls_fail_total;
-            stats[k].ls_evals = s[k].ls_evals;
-            stats[k].start_used = s[k].start_used;
-            stats[k].r_kkt = s[k].r_kkt;
-            stats[k].c = s[k].c;
-            stats[k].rho = s[k].rho;
-            stats[k].mu = s[k].mu;
-            stats[k].cycles_linearise = s[k].cyc_lin;
-            stats[k].cycles_backward = s[k].cyc_bwd;
-            stats[k].cycles_forward = s[k].cyc_fwd;
-            stats[k].cycles_linesearch = s[k].cyc_ls;
-            stats[k].cycles_total = s[k].cyc_total;
-        }
-    }
+    if (stats) stats_from_stage(b, stats);
     return BMPC_OK;
 }
 
@@ -984,7 +987,7 @@ int bmpc_problem_device_outputs(const bmpc_batch *b, int32_t i, float **x, float
     return BMPC_OK;
 }
 
-int bmpc_get_solutions_flat(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats) {
+int bmpc_get_solutions_flat_async(bmpc_batch *b, float *x, float *u, float *lam, float *y) {
     if (!b) return BMPC_ERR_INVALID;
     const FlatArgs f = flat_args(b);
     const float *raw = f.raw;
@@ -998,8 +1001,22 @@ int bmpc_get_solutions_flat(bmpc_batch *b, float *x, float *u, float *lam, float
     if (e == cudaSuccess && y && b->L.T_nc)
         e = cudaMemcpyAsync(y, raw + 2 * b->L.T_nx + 2 * b->L.T_n, sizeof(float) * (size_t)b->L.T_nc,
                             cudaMemcpyDefault, b->stream);
-    if (e != cudaSuccess) return BMPC_ERR_CUDA;
-    return bmpc_get_solutions(b, nullptr, nullptr, nullptr, nullptr, stats);   /* statistics; synchronises */
+    if (e == cudaSuccess)   /* the statistics into the pinned staging area, converted by bmpc_wait_solutions */
+        e = cudaMemcpyAsync(b->stage + b->L.stats, b->data + b->L.stats, sizeof(Stats) * b->n,
+                            cudaMemcpyDeviceToHost, b->stream);
+    return cuda_status(e);
+}
+
+int bmpc_wait_solutions(bmpc_batch *b, bmpc_stats *stats) {
+    if (!b) return BMPC_ERR_INVALID;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return BMPC_ERR_CUDA;
+    if (stats) stats_from_stage(b, stats);
+    return BMPC_OK;
+}
+
+int bmpc_get_solutions_flat(bmpc_batch *b, float *x, float *u, float *lam, float *y, bmpc_stats *stats) {
+    const int st = bmpc_get_solutions_flat_async(b, x, u, lam, y);
+    return st != BMPC_OK ? st : bmpc_wait_solutions(b, stats);
 }
 
 int bmpc_transfer_bytes_flat(const bmpc_batch *b, size_t *h2d, size_t *d2h) {

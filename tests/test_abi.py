@@ -105,3 +105,10 @@ def test_default_opts_match_the_oracle_constants():
     for f in ("eps_tol", "tau", "omega0", "eta0", "a_omega", "b_omega", "a_eta", "b_eta", "rho0", "rho_max",
               "mu0", "beta", "ls_rel_eps"):
         assert np.float32(getattr(o, f)) == np.float32(getattr(r, f)), f
+
+
+def test_async_read_and_wait_reject_null_handles():
+    """The asynchronous flat read and its wait check their handle before any CUDA call."""
+    L = bmpc.lib()
+    assert L.bmpc_get_solutions_flat_async(None, None, None, None, None) == bmpc.ERR_INVALID
+    assert L.bmpc_wait_solutions(None, None) == bmpc.ERR_INVALID

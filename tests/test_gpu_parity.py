@@ -223,6 +223,35 @@ def test_flat_transfers_equal_the_packed_path():
             assert np.array_equal(a[key], c[key])
 
 
+def test_async_flat_reads_on_two_streams_equal_the_synchronous_read():
+    """Two handles on two streams taking steps in turn (the end-to-end pipeline): every
+    asynchronous read, once waited for, equals the synchronous flat read bit for bit."""
+    from paper_2506_13624_b300 import bmpc
+    ps = scenes.config4(7, 20)
+    ref_b = bmpc.Batch(ps)
+    ref_b.set_problems_flat(*ref_b.flat_inputs())
+    ref_b.solve()
+    ref = ref_b.get_solutions_flat(ref_b.flat_outputs())
+    ref_b.close()
+    pipe = [bmpc.Batch(ps, stream=torch.cuda.Stream()) for _ in range(2)]
+    fin = pipe[0].flat_inputs()
+    outs = [bb.flat_outputs() for bb in pipe]
+    for k in range(5):
+        bb = pipe[k % 2]
+        if k >= 2:
+            bb.wait_solutions(want_stats=False)
+        bb.set_problems_flat(*fin)
+        bb.solve(graph=True)
+        bb.get_solutions_flat_async(outs[k % 2])
+    stats = [bb.wait_solutions() for bb in pipe]
+    for bb, out, st in zip(pipe, outs, stats):
+        for got, want in zip(out, ref[:4]):
+            assert torch.equal(got, want)
+        assert [s.inner_iters for s in st] == [s.inner_iters for s in ref[4]]
+        assert [s.status for s in st] == [s.status for s in ref[4]]
+        bb.close()
+
+
 def test_convergence_outcomes_follow_the_oracle_on_config3():
     """On config-3 scenes the FP32 GPU path converges exactly where the FP64 oracle does: the
     failures (a pass-before/after decision against a crossing car that 50 iterations do not settle)
