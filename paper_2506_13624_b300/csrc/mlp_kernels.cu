@@ -31,11 +31,12 @@
 
 namespace bmpc_mlp {
 
-constexpr int BM = 128, BN = 128, BK = 64, THREADS = 128, NSTAGE = 3;
+constexpr int BM = 128, BN = 128, BK = 64, NSTAGE = 4;
+constexpr int THREADS = 192;                                   /* warp 0 TMA, warp 1 MMA, warps 2-5 epilogue */
 constexpr int TILE_BYTES = 128 * BK * 2;                       /* one 128 x 64 bf16 operand tile (16 KB) */
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;                    /* A and B tiles of one k-step */
-constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + 1024;         /* 96 KB of stages + alignment slack */
-constexpr int TMEM_COLS = 128;                                 /* FP32 accumulator: 128 lanes x 128 */
+constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + 1024;         /* 128 KB of stages + alignment slack */
+constexpr int TMEM_COLS = 2 * BN;                              /* two FP32 accumulators of 128 lanes x 128 */
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_DGELU = 3 };
 
@@ -112,6 +113,24 @@ __device__ __forceinline__ int mbar_wait(uint64_t *bar, uint32_t parity) {
     return 0;
 }
 
+/* mbar_wait that also gives up (returning 0) as soon as another role of the block has set *abort. */
+__device__ __forceinline__ int mbar_wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    const uint32_t a = smem_addr(bar);
+    const long long t0 = clock64();
+    do {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return 1;
+        if (*abort) return 0;
+    } while (clock64() - t0 < 4000000000ll);
+    *abort = 1;
+    return 0;
+}
+
 /* 32 consecutive accumulator columns of this thread's TMEM lane. */
 __device__ __forceinline__ void tmem_ld32(uint32_t (&r)[32], uint32_t taddr) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -130,150 +149,209 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-/* C = op(A) op(B) for one 128 x 128 tile of C per block (4 warps).  TA: A is given transposed
- * (stored K x M); TB: B is given transposed (stored N x K); amap/bmap are their TMA views and ldc
- * the row length of C.  Thread 0 alone runs the k loop: it keeps NSTAGE-1 k-steps of operands in
- * flight by TMA (stage s filled on full[s]), issues the BK/16 MMAs of each k-step once its stage
- * has landed and commits them to empty[s]; a stage is refilled once its empty phase completes.  A
- * final commit to `done` releases the epilogue, in which warp w reads accumulator lanes 32w ..
- * 32w + 31 (rows of C). */
+/* C = op(A) op(B), persistent and warp-specialised.  TA: A is given transposed (stored K x M);
+ * TB: B is given transposed (stored N x K); amap/bmap are their TMA views and ldc the row length of
+ * C.  The grid's blocks take the 128 x 128 output tiles t = blockIdx.x, + gridDim.x, ... of the
+ * S x MT x NT tile space (split z, m-tile fastest, so the blocks that run together share each B
+ * tile in L2); split z covers k-steps [z kps, min(K/BK, (z+1) kps)) and, for EPI_F32, writes its
+ * partial product to C + z c_split.
+ *   warp 0, one thread: TMA producer over an NSTAGE ring of operand stages (full/empty mbarriers);
+ *   warp 1, one thread: issues the MMAs of each k-step once its stage has landed, commits them to
+ *     the stage's empty barrier, and after a tile's last k-step to tmem_full of its accumulator;
+ *     two TMEM accumulators alternate between tiles, so the MMAs of tile i+1 overlap the epilogue
+ *     of tile i;
+ *   warps 2-5: the epilogue.  Warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows of C), applies
+ *     the epilogue, and releases the accumulator on tmem_empty.
+ * Every wait is bounded; on a timeout the block records it in g_gemm_timeout, every role stops,
+ * the producer waits for its loads in flight, the MMA thread for its MMAs, and TMEM is freed. */
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUtensorMap amap,
                                                     const __grid_constant__ CUtensorMap bmap, void *C, int ldc, int K,
                                                     const float *__restrict__ bias, __nv_bfloat16 *__restrict__ pre,
-                                                    int kps, int64_t c_split) {
+                                                    int kps, int64_t c_split, int MT, int NT, int T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], done;
+    __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], tmem_full[2], tmem_empty[2], drain;
     __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    /* split K: block z takes k-steps [z kps, min(K/BK, (z+1) kps)) and writes its partial product
-     * (EPI_F32) to C + z c_split */
-    const int kbeg = blockIdx.z * kps;
-    const int KT = min(K / BK - kbeg, kps);
-    C = static_cast<float *>(C) + (EPI == EPI_F32 ? blockIdx.z * c_split : 0);
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
+        abort_flag = 0;
         for (int s = 0; s < NSTAGE; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&empty[s])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done)));
+        for (int a = 0; a < 2; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&tmem_full[a])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&tmem_empty[a])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&drain)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    constexpr uint32_t idesc = mma_idesc(TA, !TB);
-    int ok = 1;
-    if (tid == 0) {
-        auto load = [&](int t) {
-            const int s = t % NSTAGE;
-            unsigned char *sa = smem + s * STAGE_BYTES;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[s])),
-                         "r"(STAGE_BYTES)
-                         : "memory");
-            load_slice<!TA>(sa, &amap, (kbeg + t) * BK, m0, &full[s]);
-            load_slice<TB>(sa + TILE_BYTES, &bmap, (kbeg + t) * BK, n0, &full[s]);
-        };
-        for (int p = 0; p < NSTAGE - 1 && p < KT; ++p) load(p);
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % NSTAGE;
-            ok &= mbar_wait(&full[s], (kt / NSTAGE) & 1);
+    const int KT_all = K / BK;
+    auto tile_of = [&](int t, int &m0, int &n0, int &kbeg, int &KT, int &z) {
+        const int mt = t % MT, r = t / MT;
+        n0 = (r % NT) * BN;
+        z = r / NT;
+        m0 = mt * BM;
+        kbeg = z * kps;
+        KT = min(KT_all - kbeg, kps);
+    };
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < T && !abort_flag; t += gridDim.x) {
+                int m0, n0, kbeg, KT, z;
+                tile_of(t, m0, n0, kbeg, KT, z);
+                for (int kt = 0; kt < KT; ++kt, ++g) {
+                    const int s = g % NSTAGE;
+                    if (!mbar_wait_or_abort(&empty[s], ((g / NSTAGE) & 1) ^ 1, &abort_flag)) break;
+                    unsigned char *sa = smem + s * STAGE_BYTES;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[s])),
+                                 "r"(STAGE_BYTES)
+                                 : "memory");
+                    load_slice<!TA>(sa, &amap, (kbeg + kt) * BK, m0, &full[s]);
+                    load_slice<TB>(sa + TILE_BYTES, &bmap, (kbeg + kt) * BK, n0, &full[s]);
+                }
+            }
+            if (abort_flag) {   /* the last loads of every stage land before the block frees its memory */
+                for (uint32_t q = (g > NSTAGE ? g - NSTAGE : 0); q < g; ++q)
+                    mbar_wait(&full[q % NSTAGE], (q / NSTAGE) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = mma_idesc(TA, !TB);
+            uint32_t g = 0;
+            int i = 0;
+            for (int t = blockIdx.x; t < T && !abort_flag; t += gridDim.x, ++i) {
+                int m0, n0, kbeg, KT, z;
+                tile_of(t, m0, n0, kbeg, KT, z);
+                const int acc = i & 1;
+                if (!mbar_wait_or_abort(&tmem_empty[acc], ((i >> 1) & 1) ^ 1, &abort_flag)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(acc * BN);
+                bool fail = false;
+                for (int kt = 0; kt < KT; ++kt, ++g) {
+                    const int s = g % NSTAGE;
+                    if (!mbar_wait_or_abort(&full[s], (g / NSTAGE) & 1, &abort_flag)) {
+                        fail = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_addr(smem + s * STAGE_BYTES), sb = sa + TILE_BYTES;
+#pragma unroll
+                    for (int j = 0; j < BK / 16; ++j) {
+                        const uint64_t da = tile_desc(sa + slice_offset(j, TA), TA);
+                        const uint64_t db = tile_desc(sb + slice_offset(j, !TB), !TB);
+                        const uint32_t accumulate = (kt | j) != 0;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                                     "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_addr(&empty[s]))
+                                 : "memory");
+                }
+                if (fail) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_addr(&tmem_full[acc]))
+                             : "memory");
+            }
+            if (abort_flag) {   /* every MMA issued so far completes before TMEM is freed */
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_addr(&drain))
+                             : "memory");
+                mbar_wait(&drain, 0);
+            }
+        }
+    } else {
+        const int q = warp & 3;   /* TMEM lane quarter this warp may access */
+        int i = 0;
+        for (int t = blockIdx.x; t < T; t += gridDim.x, ++i) {
+            int m0, n0, kbeg, KT, z;
+            tile_of(t, m0, n0, kbeg, KT, z);
+            const int acc = i & 1;
+            if (!mbar_wait_or_abort(&tmem_full[acc], (i >> 1) & 1, &abort_flag)) break;
+            __syncwarp();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_addr(smem + s * STAGE_BYTES), sb = sa + TILE_BYTES;
-#pragma unroll
-            for (int j = 0; j < BK / 16; ++j) {
-                const uint64_t da = tile_desc(sa + slice_offset(j, TA), TA);
-                const uint64_t db = tile_desc(sb + slice_offset(j, !TB), !TB);
-                const uint32_t accumulate = (kt | j) != 0;
-                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                             "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&empty[s]))
-                         : "memory");
-            const int nk = kt + NSTAGE - 1;   /* refill the stage of k-step kt-1 once its MMAs are done */
-            if (nk < KT) {
-                if (nk >= NSTAGE) ok &= mbar_wait(&empty[nk % NSTAGE], ((nk - NSTAGE) / NSTAGE) & 1);
-                load(nk);
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_addr(&done))
-                     : "memory");
-    }
-    ok &= mbar_wait(&done, 0);   /* a single phase: every MMA of the tile has completed */
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        const int r = m0 + warp * 32 + lane;
+            void *Cz = EPI == EPI_F32 ? static_cast<void *>(static_cast<float *>(C) + z * c_split) : C;
+            const int r = m0 + q * 32 + lane;
 #pragma unroll 1
-        for (int cc = 0; cc < BN / 32; ++cc) {
-            uint32_t v[32];
-            tmem_ld32(v, tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32));
-            const int c0 = n0 + cc * 32;
-            const size_t o = (size_t)r * ldc + c0;
-            if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
-                float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(C) + o);
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                uint32_t v[32];
+                tmem_ld32(v, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + cc * 32));
+                const int c0 = n0 + cc * 32;
+                const size_t o = (size_t)r * ldc + c0;
+                if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
+                    float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(Cz) + o);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float4 f = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                           __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
-                    if (EPI == EPI_BIAS_F32) {
-                        f.x += bias[c0 + 4 * q];
-                        f.y += bias[c0 + 4 * q + 1];
-                        f.z += bias[c0 + 4 * q + 2];
-                        f.w += bias[c0 + 4 * q + 3];
+                    for (int qq = 0; qq < 8; ++qq) {
+                        float4 f = make_float4(__uint_as_float(v[4 * qq]), __uint_as_float(v[4 * qq + 1]),
+                                               __uint_as_float(v[4 * qq + 2]), __uint_as_float(v[4 * qq + 3]));
+                        if (EPI == EPI_BIAS_F32) {
+                            f.x += bias[c0 + 4 * qq];
+                            f.y += bias[c0 + 4 * qq + 1];
+                            f.z += bias[c0 + 4 * qq + 2];
+                            f.w += bias[c0 + 4 * qq + 3];
+                        }
+                        dst[qq] = f;
                     }
-                    dst[q] = f;
-                }
-            } else if (EPI == EPI_BIAS_GELU) {
-                uint4 *dp = reinterpret_cast<uint4 *>(pre + o);
-                uint4 *dc = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(C) + o);
+                } else if (EPI == EPI_BIAS_GELU) {
+                    uint4 *dp = reinterpret_cast<uint4 *>(pre + o);
+                    uint4 *dc = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Cz) + o);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t pz[4], az[4];
+                    for (int qq = 0; qq < 4; ++qq) {
+                        uint32_t pz[4], az[4];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int j = 8 * q + 2 * h;
-                        pz[h] = pack_bf16(__uint_as_float(v[j]) + bias[c0 + j], __uint_as_float(v[j + 1]) + bias[c0 + j + 1]);
-                        const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pz[h]));
-                        az[h] = pack_bf16(gelu(pf.x), gelu(pf.y));
+                        for (int h = 0; h < 4; ++h) {
+                            const int j = 8 * qq + 2 * h;
+                            pz[h] = pack_bf16(__uint_as_float(v[j]) + bias[c0 + j],
+                                              __uint_as_float(v[j + 1]) + bias[c0 + j + 1]);
+                            const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pz[h]));
+                            az[h] = pack_bf16(gelu(pf.x), gelu(pf.y));
+                        }
+                        dp[qq] = make_uint4(pz[0], pz[1], pz[2], pz[3]);
+                        dc[qq] = make_uint4(az[0], az[1], az[2], az[3]);
                     }
-                    dp[q] = make_uint4(pz[0], pz[1], pz[2], pz[3]);
-                    dc[q] = make_uint4(az[0], az[1], az[2], az[3]);
-                }
-            } else {   /* EPI_DGELU: dX = (dY W^T) * gelu'(pre) */
-                const uint4 *sp = reinterpret_cast<const uint4 *>(pre + o);
-                uint4 *dc = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(C) + o);
+                } else {   /* EPI_DGELU: dX = (dY W^T) * gelu'(pre) */
+                    const uint4 *sp = reinterpret_cast<const uint4 *>(pre + o);
+                    uint4 *dc = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Cz) + o);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 pq = sp[q];
-                    const uint32_t pw[4] = {pq.x, pq.y, pq.z, pq.w};
-                    uint32_t oz[4];
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const uint4 pq = sp[qq];
+                        const uint32_t pw[4] = {pq.x, pq.y, pq.z, pq.w};
+                        uint32_t oz[4];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int j = 8 * q + 2 * h;
-                        const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pw[h]));
-                        oz[h] = pack_bf16(__uint_as_float(v[j]) * gelu_grad(pf.x), __uint_as_float(v[j + 1]) * gelu_grad(pf.y));
+                        for (int h = 0; h < 4; ++h) {
+                            const int j = 8 * qq + 2 * h;
+                            const float2 pf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pw[h]));
+                            oz[h] = pack_bf16(__uint_as_float(v[j]) * gelu_grad(pf.x),
+                                              __uint_as_float(v[j + 1]) * gelu_grad(pf.y));
+                        }
+                        dc[qq] = make_uint4(oz[0], oz[1], oz[2], oz[3]);
                     }
-                    dc[q] = make_uint4(oz[0], oz[1], oz[2], oz[3]);
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tmem_empty[acc])) : "memory");
         }
-    } else if (lane == 0) {
-        atomicExch(&g_gemm_timeout, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    if (abort_flag && tid == 0) atomicExch(&g_gemm_timeout, 1);
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 /* Split-K reduction: C = epilogue(sum over the S partial products in ws, in split order). */
@@ -456,12 +534,25 @@ bool make_operand_map(CUtensorMap *m, const void *ptr, int mn, int k, int ld, bo
 
 template <bool TA, bool TB, int EPI>
 cudaError_t set_smem() {
-    static bool done = false;   /* 64 KB of dynamic shared memory needs the opt-in, once per instance */
+    static bool done = false;   /* 129 KB of dynamic shared memory needs the opt-in, once per instance */
     if (done) return cudaSuccess;
     const cudaError_t e =
         cudaFuncSetAttribute(gemm_tc<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
     done = e == cudaSuccess;
     return e;
+}
+
+/* Persistent blocks for T output tiles: one per SM (the shared-memory ring allows one block per
+ * SM), fewer when there are fewer tiles. */
+int gemm_grid(int T) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    return std::max(1, std::min(T, sms));
 }
 
 /* C = epilogue(op(A) op(B)); GEMMs with few output tiles and a long K are split along K into the
@@ -470,14 +561,16 @@ template <bool TA, bool TB, int EPI>
 cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ldc, int M, int N, int K, const float *bias,
                  void *pre, cudaStream_t s, float *ws = nullptr, int64_t ws_floats = 0) {
     const int KT = K / BK, kps = split_kps(M, N, K), S = (KT + kps - 1) / kps;
+    const int MT = M / BM, NT = N / BN;
     CUtensorMap am, bm;
     if (!make_operand_map(&am, A, M, K, lda, !TA) || !make_operand_map(&bm, B, N, K, ldb, TB))
         return cudaErrorInvalidValue;
     if (S > 1 && ws && (int64_t)S * M * N <= ws_floats) {
         cudaError_t e = set_smem<TA, TB, EPI_F32>();
         if (e != cudaSuccess) return e;
-        gemm_tc<TA, TB, EPI_F32><<<dim3(N / BN, M / BM, S), THREADS, GEMM_SMEM, s>>>(am, bm, ws, N, K, nullptr, nullptr,
-                                                                                   kps, (int64_t)M * N);
+        const int T = S * MT * NT;
+        gemm_tc<TA, TB, EPI_F32><<<gemm_grid(T), THREADS, GEMM_SMEM, s>>>(am, bm, ws, N, K, nullptr, nullptr, kps,
+                                                                         (int64_t)M * N, MT, NT, T);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const int64_t pairs = (int64_t)M * N / 2;
@@ -487,8 +580,9 @@ cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ld
     }
     const cudaError_t e = set_smem<TA, TB, EPI>();
     if (e != cudaSuccess) return e;
-    gemm_tc<TA, TB, EPI><<<dim3(N / BN, M / BM, 1), THREADS, GEMM_SMEM, s>>>(am, bm, C, ldc, K, bias,
-                                                                           static_cast<__nv_bfloat16 *>(pre), KT, 0);
+    gemm_tc<TA, TB, EPI><<<gemm_grid(MT * NT), THREADS, GEMM_SMEM, s>>>(am, bm, C, ldc, K, bias,
+                                                                       static_cast<__nv_bfloat16 *>(pre), KT, 0, MT,
+                                                                       NT, MT * NT);
     return cudaGetLastError();
 }
 
