@@ -35,7 +35,9 @@ constexpr int BM = 128, BN = 128, BK = 64, NSTAGE = 4;
 constexpr int THREADS = 192;                                   /* warp 0 TMA, warp 1 MMA, warps 2-5 epilogue */
 constexpr int TILE_BYTES = 128 * BK * 2;                       /* one 128 x 64 bf16 operand tile (16 KB) */
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;                    /* A and B tiles of one k-step */
-constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + 1024;         /* 128 KB of stages + alignment slack */
+constexpr int OUT_BUF = 32 * 32 * 4;                           /* one 32 x 32 FP32 chunk of C for a TMA store */
+constexpr int OUT_BYTES = 4 * 2 * OUT_BUF;                     /* two buffers per epilogue warp */
+constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024;   /* 160 KB + alignment slack */
 constexpr int TMEM_COLS = 2 * BN;                              /* two FP32 accumulators of 128 lanes x 128 */
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_DGELU = 3 };
@@ -83,6 +85,15 @@ __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *map, int x
             "r"(smem_addr(dst)),
         "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
         : "memory");
+}
+
+/* TMA store (one thread) of a 32 x 32 FP32 chunk from shared memory (128-byte-swizzled rows) to
+ * C at (x, y, z) of the output map; x, the column, is a multiple of 32 elements (128 bytes). */
+__device__ __forceinline__ void tma_store_chunk(const CUtensorMap *map, const void *src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map), "r"(x),
+                 "r"(y), "r"(z), "r"(smem_addr(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
 /* The operand slice of k-step t: K-major, one box of 64 k x 128 rows; M/N-major, two boxes of 64 mn x
@@ -166,7 +177,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
  * the producer waits for its loads in flight, the MMA thread for its MMAs, and TMEM is freed. */
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUtensorMap amap,
-                                                    const __grid_constant__ CUtensorMap bmap, void *C, int ldc, int K,
+                                                    const __grid_constant__ CUtensorMap bmap,
+                                                    const __grid_constant__ CUtensorMap cmap, void *C, int ldc, int K,
                                                     const float *__restrict__ bias, __nv_bfloat16 *__restrict__ pre,
                                                     int kps, int64_t c_split, int MT, int NT, int T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -276,6 +288,8 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
         }
     } else {
         const int q = warp & 3;   /* TMEM lane quarter this warp may access */
+        unsigned char *obuf = smem + NSTAGE * STAGE_BYTES;   /* 1024-byte aligned output chunk buffers */
+        int nst = 0;                                          /* TMA stores issued by this warp */
         int i = 0;
         for (int t = blockIdx.x; t < T; t += gridDim.x, ++i) {
             int m0, n0, kbeg, KT, z;
@@ -293,7 +307,12 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
                 const int c0 = n0 + cc * 32;
                 const size_t o = (size_t)r * ldc + c0;
                 if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
-                    float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(Cz) + o);
+                    /* the warp's 32 x 32 chunk goes through one of its two shared buffers and leaves by
+                     * one TMA store; lane l writes row l with its 16-byte pieces in the 128-byte
+                     * swizzle order (piece k at position k ^ (l mod 8)), free of bank conflicts */
+                    unsigned char *buf = obuf + (size_t)(((warp - 2) * 2 + (nst & 1)) * OUT_BUF);
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    __syncwarp();
 #pragma unroll
                     for (int qq = 0; qq < 8; ++qq) {
                         float4 f = make_float4(__uint_as_float(v[4 * qq]), __uint_as_float(v[4 * qq + 1]),
@@ -304,8 +323,12 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
                             f.z += bias[c0 + 4 * qq + 2];
                             f.w += bias[c0 + 4 * qq + 3];
                         }
-                        dst[qq] = f;
+                        *reinterpret_cast<float4 *>(buf + lane * 128 + ((qq ^ (lane & 7)) << 4)) = f;
                     }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) tma_store_chunk(&cmap, buf, c0, m0 + q * 32, EPI == EPI_F32 ? z : 0);
+                    ++nst;
                 } else if (EPI == EPI_BIAS_GELU) {
                     uint4 *dp = reinterpret_cast<uint4 *>(pre + o);
                     uint4 *dc = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Cz) + o);
@@ -347,6 +370,9 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
             if (lane == 0)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tmem_empty[acc])) : "memory");
         }
+        if ((EPI == EPI_F32 || EPI == EPI_BIAS_F32) && lane == 0)   /* the stores complete before exit */
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -532,9 +558,22 @@ bool make_operand_map(CUtensorMap *m, const void *ptr, int mn, int k, int ld, bo
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+/* TMA view of an FP32 output for the GEMM's stores: C [S][M][ldc] (S partial products c_split
+ * floats apart), boxes of 32 columns x 32 rows x 1 with 128-byte swizzle. */
+bool make_output_map(CUtensorMap *m, void *C, int M, int N, int ldc, int S, int64_t c_split) {
+    const EncodeTiled enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dim[3] = {(cuuint64_t)N, (cuuint64_t)M, (cuuint64_t)S};
+    cuuint64_t str[2] = {(cuuint64_t)ldc * 4, (cuuint64_t)(S > 1 ? c_split : (int64_t)M * ldc) * 4};
+    cuuint32_t box[3] = {32, 32, 1}, es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C, dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 template <bool TA, bool TB, int EPI>
 cudaError_t set_smem() {
-    static bool done = false;   /* 129 KB of dynamic shared memory needs the opt-in, once per instance */
+    static bool done = false;   /* 161 KB of dynamic shared memory needs the opt-in, once per instance */
     if (done) return cudaSuccess;
     const cudaError_t e =
         cudaFuncSetAttribute(gemm_tc<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
@@ -569,7 +608,9 @@ cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ld
         cudaError_t e = set_smem<TA, TB, EPI_F32>();
         if (e != cudaSuccess) return e;
         const int T = S * MT * NT;
-        gemm_tc<TA, TB, EPI_F32><<<gemm_grid(T), THREADS, GEMM_SMEM, s>>>(am, bm, ws, N, K, nullptr, nullptr, kps,
+        CUtensorMap cm;
+        if (!make_output_map(&cm, ws, M, N, N, S, (int64_t)M * N)) return cudaErrorInvalidValue;
+        gemm_tc<TA, TB, EPI_F32><<<gemm_grid(T), THREADS, GEMM_SMEM, s>>>(am, bm, cm, ws, N, K, nullptr, nullptr, kps,
                                                                          (int64_t)M * N, MT, NT, T);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -580,7 +621,13 @@ cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ld
     }
     const cudaError_t e = set_smem<TA, TB, EPI>();
     if (e != cudaSuccess) return e;
-    gemm_tc<TA, TB, EPI><<<gemm_grid(MT * NT), THREADS, GEMM_SMEM, s>>>(am, bm, C, ldc, K, bias,
+    CUtensorMap cm;
+    if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
+        if (!make_output_map(&cm, C, M, N, ldc, 1, 0)) return cudaErrorInvalidValue;
+    } else {
+        cm = am;   /* unused by the bf16 epilogues */
+    }
+    gemm_tc<TA, TB, EPI><<<gemm_grid(MT * NT), THREADS, GEMM_SMEM, s>>>(am, bm, cm, C, ldc, K, bias,
                                                                        static_cast<__nv_bfloat16 *>(pre), KT, 0, MT,
                                                                        NT, MT * NT);
     return cudaGetLastError();
