@@ -77,6 +77,13 @@ int64_t bmpc_mlp_workspace_floats(const bmpc_mlp_layer *layers, int32_t n_layers
  * (its output tile was not written; the flag is cleared), BMPC_ERR_CUDA (-2) on a CUDA error. */
 int bmpc_mlp_status(void *stream);
 
+/* Test support for the bounded waits: a one-thread kernel waits for an mbarrier phase that nothing
+ * completes, for at most `cycles` SM cycles (1 .. 1e8, about 50 ms at most), then records the
+ * timeout exactly as a GEMM does, so that the next bmpc_mlp_status returns BMPC_ERR_TIMEOUT.
+ * Nothing faults and the context stays usable.  -1 on cycles out of range, -2 if the launch fails;
+ * asynchronous on `stream`. */
+int bmpc_mlp_selftest_wait(int64_t cycles, void *stream);
+
 /* ---- glue with a BMPC batch (all problems must share one tree) ----
  * Features of problem k (fp32, feat + k*dim): x0 without its X coordinate (nx - 1 values), then for
  * every scenario s < n_scen and obstacle o < n_obs_max the obstacle's (cx - X0, cy) at the middle

@@ -108,8 +108,10 @@ __device__ __forceinline__ void load_slice(unsigned char *dst, const CUtensorMap
     }
 }
 
-/* Waits (at most about 2 s of SM clock) for the phase of `bar` with the given parity; 0 on timeout. */
-__device__ __forceinline__ int mbar_wait(uint64_t *bar, uint32_t parity) {
+constexpr long long WAIT_CYCLES = 4000000000ll;   /* about 2 s of SM clock */
+
+/* Waits (at most `limit` SM cycles) for the phase of `bar` with the given parity; 0 on timeout. */
+__device__ __forceinline__ int mbar_wait(uint64_t *bar, uint32_t parity, long long limit = WAIT_CYCLES) {
     const uint32_t a = smem_addr(bar);
     const long long t0 = clock64();
     do {
@@ -120,7 +122,7 @@ __device__ __forceinline__ int mbar_wait(uint64_t *bar, uint32_t parity) {
                      : "r"(a), "r"(parity)
                      : "memory");
         if (ok) return 1;
-    } while (clock64() - t0 < 4000000000ll);
+    } while (clock64() - t0 < limit);
     return 0;
 }
 
@@ -137,7 +139,7 @@ __device__ __forceinline__ int mbar_wait_or_abort(uint64_t *bar, uint32_t parity
                      : "memory");
         if (ok) return 1;
         if (*abort) return 0;
-    } while (clock64() - t0 < 4000000000ll);
+    } while (clock64() - t0 < WAIT_CYCLES);
     *abort = 1;
     return 0;
 }
@@ -378,6 +380,17 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
     __syncthreads();
     if (abort_flag && tid == 0) atomicExch(&g_gemm_timeout, 1);
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+/* Self-test of the bounded wait: one thread waits for the first phase of an mbarrier that nothing
+ * arrives on, for at most `cycles` SM cycles, and records the timeout as a GEMM does. */
+__global__ void wait_selftest_kernel(long long cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait(&bar, 0, cycles)) atomicExch(&g_gemm_timeout, 1);
+    }
 }
 
 /* Split-K reduction: C = epilogue(sum over the S partial products in ws, in split order). */
@@ -756,6 +769,12 @@ int64_t bmpc_mlp_workspace_floats(const bmpc_mlp_layer *L, int32_t n, int32_t ba
         if (l > 0) f = std::max(f, split_floats(batch, L[l].in, L[l].out));   /* g W^T */
     }
     return f;
+}
+
+int bmpc_mlp_selftest_wait(int64_t cycles, void *stream) {
+    if (cycles < 1 || cycles > 100000000) return -1;
+    wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((long long)cycles);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 int bmpc_mlp_status(void *stream) {

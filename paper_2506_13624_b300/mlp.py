@@ -38,6 +38,7 @@ def _setup():
     L.bmpc_mlp_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                 C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
     L.bmpc_mlp_status.argtypes = [C.c_void_p]
+    L.bmpc_mlp_selftest_wait.argtypes = [C.c_int64, C.c_void_p]
     L.bmpc_mlp_workspace_floats.argtypes = [C.POINTER(Layer), C.c_int32, C.c_int32]
     L.bmpc_mlp_workspace_floats.restype = C.c_int64
     L.bmpc_mlp_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32]
@@ -139,6 +140,19 @@ def status():
     """Synchronise the current stream; raise if a GEMM gave up waiting for its MMAs."""
     import torch
     _check(_setup().bmpc_mlp_status(_stream(torch)), "bmpc_mlp_status")
+
+
+def status_code() -> int:
+    """Synchronise the current stream; the raw status (0, -4 a GEMM wait gave up, -2 CUDA error)."""
+    import torch
+    return int(_setup().bmpc_mlp_status(_stream(torch)))
+
+
+def selftest_wait(cycles: int):
+    """Launch the bounded-wait self-test: a wait for a barrier phase that nothing completes, given
+    up after `cycles` SM cycles and recorded like a GEMM timeout."""
+    import torch
+    _check(_setup().bmpc_mlp_selftest_wait(int(cycles), _stream(torch)), "bmpc_mlp_selftest_wait")
 
 
 def features(batch, out, n_scen, n_obs):

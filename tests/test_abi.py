@@ -112,3 +112,11 @@ def test_async_read_and_wait_reject_null_handles():
     L = bmpc.lib()
     assert L.bmpc_get_solutions_flat_async(None, None, None, None, None) == bmpc.ERR_INVALID
     assert L.bmpc_wait_solutions(None, None) == bmpc.ERR_INVALID
+
+
+def test_wait_selftest_rejects_out_of_range_limits():
+    """The bounded-wait self-test checks its limit before launching anything."""
+    from paper_2506_13624_b300 import mlp
+    L = mlp._setup()
+    assert L.bmpc_mlp_selftest_wait(0, None) == -1
+    assert L.bmpc_mlp_selftest_wait(10 ** 9, None) == -1

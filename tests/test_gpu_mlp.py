@@ -128,3 +128,22 @@ def test_targets_and_starts_round_trip():
     leaf = int(np.where(p["stage"] == p["stage"].max())[0][0])
     assert abs(f[0, 3 + 2] - (p["obs"][leaf, 0, 0] - p["x0"][0])) < 1e-4
     b.close()
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A wait for an mbarrier phase that nothing completes gives up after its limit (about 1 ms here),
+    bmpc_mlp_status reports the timeout once and clears it, and a GEMM afterwards is exact: the
+    failure path of the tensor-core kernels, exercised without any fault."""
+    from paper_2506_13624_b300 import mlp
+    assert mlp.status_code() == 0
+    mlp.selftest_wait(2_000_000)
+    assert mlp.status_code() == -4
+    assert mlp.status_code() == 0
+    g = torch.Generator().manual_seed(3)
+    A = torch.randn(128, 64, generator=g).to(torch.bfloat16)
+    B = torch.randn(64, 128, generator=g).to(torch.bfloat16)
+    Cg = mlp.gemm(A.cuda(), B.cuda()).cpu().double()
+    ref = A.double() @ B.double()
+    assert torch.allclose(Cg, ref, rtol=1e-5, atol=1e-4)
+    assert mlp.status_code() == 0
+
