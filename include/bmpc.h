@@ -110,7 +110,7 @@ typedef struct {
     int32_t ls_chunk;       /* step sizes evaluated per parallel round (1..16), default 2; 0 = all.
                                The accepted step (the largest alpha_i meeting Armijo) does not
                                depend on it: it only trades parallel work for extra rounds. */
-    int32_t block_threads;  /* threads per problem (32..1024, multiple of 32); 0 = automatic */
+    int32_t block_threads;  /* threads per problem (32..512, multiple of 32); 0 = automatic */
     int32_t blocks_per_sm;  /* resident problems per SM; 0 = automatic */
     int32_t variant;        /* tree sweeps: 0 automatic by tree shape (2 when the tree has at most as many
                                scenario paths as threads per problem, else 1), 1 level-synchronous (one barrier per stage,

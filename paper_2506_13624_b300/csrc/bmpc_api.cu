@@ -849,7 +849,7 @@ int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *
     else bmpc_default_opts(&o);
     int st = check_opts(o);
     if (st != BMPC_OK) return st;
-    static const int kThreads[] = {32, 64, 128, 256};
+    static const int kThreads[] = {32, 64, 128, 256, 512};
     static const int kVariant[] = {1, 2, 3};
     static const int kChunk[] = {1, 2, 4};
     cudaEvent_t e0, e1;

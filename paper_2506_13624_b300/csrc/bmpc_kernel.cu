@@ -43,10 +43,11 @@
 
 namespace bmpc {
 
-constexpr int MAX_BLOCK = 256;
-#ifndef BMPC_MIN_BLOCKS
-#define BMPC_MIN_BLOCKS 2   /* 256 threads x 2 blocks: at most 128 registers per thread */
-#endif
+/* Two instances of the solver per model: blocks of up to 256 threads, two per SM, for batches;
+ * blocks of up to 512 threads, one per SM, for few large problems (single solves).  Both get at
+ * most 128 registers per thread.  The shared reduction arrays are sized for the larger. */
+constexpr int MAX_BLOCK = 512;
+constexpr int BATCH_BLOCK = 256;
 constexpr int MAX_WARPS = MAX_BLOCK / 32;
 constexpr int MAX_CHUNK = 16;   /* at most 16 step sizes per line-search round */
 /* Node loops with their loads hoisted ahead of their stores (one or two batches of loads per node
@@ -2070,8 +2071,8 @@ done:
 }
 
 /* One kernel per dynamics model, so that each carries only its own code and registers. */
-template <int MODEL>
-__global__ void __launch_bounds__(MAX_BLOCK, BMPC_MIN_BLOCKS) bmpc_solve_kernel(KernelArgs args) {
+template <int MODEL, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, BLOCK <= BATCH_BLOCK ? 2 : 1) bmpc_solve_kernel(KernelArgs args) {
     constexpr int NX = MODEL == 1 ? 6 : 4;
     __shared__ Shared sh;
     __shared__ int pid_s;
@@ -2449,10 +2450,17 @@ cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream
 }
 
 /* Launch helper used by the host API: `args.order` lists problems of `model` only. */
+/* The kernel instance of a model for a block size. */
+using SolveFn = void (*)(KernelArgs);
+SolveFn solve_fn(int model, int block) {
+    const bool big = block > BATCH_BLOCK;
+    if (model == 0) return big ? bmpc_solve_kernel<0, MAX_BLOCK> : bmpc_solve_kernel<0, BATCH_BLOCK>;
+    if (model == 1) return big ? bmpc_solve_kernel<1, MAX_BLOCK> : bmpc_solve_kernel<1, BATCH_BLOCK>;
+    return big ? bmpc_solve_kernel<2, MAX_BLOCK> : bmpc_solve_kernel<2, BATCH_BLOCK>;
+}
+
 cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, size_t smem, cudaStream_t stream) {
-    if (model == 0) bmpc_solve_kernel<0><<<grid, block, smem, stream>>>(args);
-    else if (model == 1) bmpc_solve_kernel<1><<<grid, block, smem, stream>>>(args);
-    else bmpc_solve_kernel<2><<<grid, block, smem, stream>>>(args);
+    solve_fn(model, block)<<<grid, block, smem, stream>>>(args);
     return cudaGetLastError();
 }
 
@@ -2473,23 +2481,23 @@ size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld
     return sizeof(int32_t) * (size_t)tab_ints;
 }
 
-/* Raises the dynamic shared-memory limit of a model's kernel to at least `smem` (never lowers it,
- * so batches sharing the process keep theirs). */
+/* Raises the dynamic shared-memory limit of a model's kernels to at least `smem` (never lowers it,
+ * so batches sharing the process keep theirs).  The attribute is always set: without it the 48 KB
+ * default bounds static and dynamic shared memory together, and the kernels' static part (the
+ * reduction arrays and the problem record) is about 14 KB. */
 cudaError_t prepare_solve(int model, size_t smem) {
-    static size_t granted[3] = {48u * 1024u, 48u * 1024u, 48u * 1024u};
+    static size_t granted[3] = {0, 0, 0};
     if (model < 0 || model > 2 || smem <= granted[model]) return cudaSuccess;
-    cudaError_t e;
-    if (model == 0) e = cudaFuncSetAttribute(bmpc_solve_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else if (model == 1) e = cudaFuncSetAttribute(bmpc_solve_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else e = cudaFuncSetAttribute(bmpc_solve_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(solve_fn(model, BATCH_BLOCK), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_fn(model, MAX_BLOCK), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) granted[model] = smem;
     return e;
 }
 
 cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm) {
-    if (model == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<0>, block, smem);
-    if (model == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<1>, block, smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bmpc_solve_kernel<2>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_fn(model, block), block, smem);
 }
 
 }  // namespace bmpc

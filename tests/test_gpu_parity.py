@@ -298,7 +298,7 @@ def test_autotuner_returns_a_valid_configuration():
     b = bmpc.Batch(ps)
     b.set_problems()
     best, us = b.autotune()
-    assert best.block_threads in (64, 128, 256) and best.variant in (1, 2, 3) and best.ls_chunk in (1, 2, 4)
+    assert best.block_threads in (32, 64, 128, 256, 512) and best.variant in (1, 2, 3) and best.ls_chunk in (1, 2, 4)
     assert us > 0
     b.solve(best)
     tuned = b.get_solutions()
