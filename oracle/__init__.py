@@ -166,6 +166,24 @@ def tree_lqr(parent, Q, M, R, q, r, A, B, c):
     return K, k, P, pv, dx, du, lam
 
 
+def tree_lqr_scan(parent, Q, M, R, q, r, A, B, c):
+    """Tree LQR by scans (Sec. III-B: CVF suffix scans along the non-branching segments, tree Riccati
+    steps at branch nodes, prefix scans of the closed-loop maps along every path); outputs as
+    tree_lqr."""
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    n = parent.shape[0]
+    nx, nu = np.shape(B)[1], np.shape(B)[2]
+    K, k = np.zeros((n, nu, nx)), np.zeros((n, nu))
+    P, pv = np.zeros((n, nx, nx)), np.zeros((n, nx))
+    dx, du, lam = np.zeros((n, nx)), np.zeros((n, nu)), np.zeros((n, nx))
+    args = [_d(a) for a in (Q, M, R, q, r, A, B, c)]
+    rc = lib().orc_tree_lqr_scan(n, parent.ctypes.data_as(_ip), nx, nu, *[_ptr(a) for a in args],
+                                 _ptr(K), _ptr(k), _ptr(P), _ptr(pv), _ptr(dx), _ptr(du), _ptr(lam))
+    if rc != 0:
+        raise RuntimeError(f"orc_tree_lqr_scan failed: {rc}")
+    return K, k, P, pv, dx, du, lam
+
+
 def kkt(p, x, u, lam, y):
     """Original-problem KKT measures: [stationarity, defect, infeasibility, complementarity, y<0]."""
     m = _Marshal(p)

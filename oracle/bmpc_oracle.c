@@ -11,6 +11,8 @@
  *   problem             Sec. II-B, Eq. (bmpc): node costs, x_i = f_p(i)(x_p(i), u_p(i)), g <= 0
  *   tree LQR            Sec. III-A, Eq. (lqr_tree_approx), Eq. (tree_Riccati),
  *                       Eq. (tree_feedback_laws); forward rollout as in Sec. II-A
+ *   tree LQR by scans   Sec. III-B, Eq. (sol_min), Eq. (comb_rule), Eq. (forward_comb_rule):
+ *                       orc_tree_lqr_scan (CVF scans along the non-branching segments)
  *   augmented Lagr.     Sec. IV-A, Eq. (AL) (PHR penalty), Lagrangian with lambda,
  *                       Gauss-Newton Hessian of the PHR term
  *   linear rollout      Sec. IV-A "Search direction" (multiple shooting)
@@ -32,7 +34,10 @@
  *     no accepted alpha -> smallest alpha, three failures in a row -> LS_FAIL;
  *   - the root carries no state constraints (x_0 is fixed), leaves no input constraints;
  *   - cold start: x linearly interpolated from x0 to the node's final reference, u = 0,
- *     lambda = 0, y = 0 (Sec. V-B initialisation).
+ *     lambda = 0, y = 0 (Sec. V-B initialisation);
+ *   - CVF combination signs follow Eq. (sol_min) (A = A2 E^-1 A1, c = A2 E^-1 (c1 - C1 p2) + c2,
+ *     p = A1' E^-T (p2 + P2 c1) + p1); the separable tree form of Eq. (tree_CVF) is used only along
+ *     non-branching segments, since a branch node's shared input couples its children.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -460,6 +465,325 @@ int orc_tree_lqr(int n, const int *parent, int nx, int nu, const double *Q, cons
     tree_t T;
     if (!tree_build(&P, &T)) { tree_free(&T); return ORC_ERR_INVALID; }
     int st = tree_lqr(&T, nx, nu, Q, M, R, q, r, A, B, c, K, k, Pm, pv, dx, du, lam);
+    tree_free(&T);
+    return st;
+}
+
+/* ------------------------------------------------------------ tree LQR by scans (Sec. III-B) */
+/* Conditional value function (CVF) of Eq. (sol_min) from a node x_k to one node x_i further down a
+ * chain:  V(x_k, x_i) = max_lam  1/2 x_k' P x_k + p' x_k - 1/2 lam' C lam + lam' (x_i - A x_k - c)
+ * (+ a constant).  An element with A = C = 0 and c = 0 is a plain value function 1/2 x'Px + p'x. */
+typedef struct {
+    double A[MAXX * MAXX], c[MAXX], C[MAXX * MAXX], p[MAXX], P[MAXX * MAXX];
+} cvf_t;
+
+/* Solves M X = Bm in place for m right-hand sides (n x n, Gaussian elimination with partial
+ * pivoting); 0 if M is singular. */
+static int lu_solve(int n, int m, const double *M, double *Bm) {
+    double W[MAXX * MAXX];
+    memcpy(W, M, sizeof(double) * n * n);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < n; ++i)
+            if (fabs(W[i * n + col]) > fabs(W[piv * n + col])) piv = i;
+        if (W[piv * n + col] == 0.0) return 0;
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) { double t = W[col * n + j]; W[col * n + j] = W[piv * n + j]; W[piv * n + j] = t; }
+            for (int j = 0; j < m; ++j) { double t = Bm[col * m + j]; Bm[col * m + j] = Bm[piv * m + j]; Bm[piv * m + j] = t; }
+        }
+        for (int i = col + 1; i < n; ++i) {
+            const double f = W[i * n + col] / W[col * n + col];
+            for (int j = col; j < n; ++j) W[i * n + j] -= f * W[col * n + j];
+            for (int j = 0; j < m; ++j) Bm[i * m + j] -= f * Bm[col * m + j];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i)
+        for (int j = 0; j < m; ++j) {
+            double v = Bm[i * m + j];
+            for (int t = i + 1; t < n; ++t) v -= W[i * n + t] * Bm[t * m + j];
+            Bm[i * m + j] = v / W[i * n + i];
+        }
+    return 1;
+}
+
+/* The associative operator of Eq. (V_ki_min): the CVF e1 from k to j followed by e2 from j to i,
+ * minimised over x_j.  With E = I + C1 P2 (Eq. comb_rule):
+ *   A = A2 E^-1 A1,  c = A2 E^-1 (c1 - C1 p2) + c2,  C = A2 E^-1 C1 A2' + C2,
+ *   P = A1' E^-T P2 A1 + P1,  p = A1' E^-T (p2 + P2 c1) + p1.
+ * The signs follow from the CVF form above (the printed equation's signs are not consistent with
+ * one convention); the result equals the sequential Riccati recursion (tested). */
+static int cvf_combine(int nx, const cvf_t *e1, const cvf_t *e2, cvf_t *out) {
+    const int n = nx, m = 2 * nx + 1;
+    double E[MAXX * MAXX], X[MAXX * (2 * MAXX + 1)];
+    matmul(n, n, n, e1->C, e2->P, E);
+    for (int i = 0; i < n; ++i) E[i * n + i] += 1.0;
+    /* X = E^-1 [A1 | C1 A2' | c1 - C1 p2] */
+    double C1A2t[MAXX * MAXX], C1p2[MAXX];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double v = 0.0;
+            for (int t = 0; t < n; ++t) v += e1->C[i * n + t] * e2->A[j * n + t];
+            C1A2t[i * n + j] = v;
+        }
+    matvec(n, n, e1->C, e2->p, C1p2);
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            X[i * m + j] = e1->A[i * n + j];
+            X[i * m + n + j] = C1A2t[i * n + j];
+        }
+        X[i * m + 2 * n] = e1->c[i] - C1p2[i];
+    }
+    if (!lu_solve(n, m, E, X)) return 0;
+    /* F = E' = I + P2 C1; Y = F^-1 [P2 A1 | p2 + P2 c1] */
+    double F[MAXX * MAXX], Y[MAXX * (MAXX + 1)], P2A1[MAXX * MAXX], P2c1[MAXX];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) F[i * n + j] = E[j * n + i];
+    matmul(n, n, n, e2->P, e1->A, P2A1);
+    matvec(n, n, e2->P, e1->c, P2c1);
+    const int m2 = n + 1;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) Y[i * m2 + j] = P2A1[i * n + j];
+        Y[i * m2 + n] = e2->p[i] + P2c1[i];
+    }
+    if (!lu_solve(n, m2, F, Y)) return 0;
+    cvf_t r;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            double a = 0.0, cc = 0.0, pp = 0.0;
+            for (int t = 0; t < n; ++t) {
+                a += e2->A[i * n + t] * X[t * m + j];
+                cc += e2->A[i * n + t] * X[t * m + n + j];
+                pp += e1->A[t * n + i] * Y[t * m2 + j];
+            }
+            r.A[i * n + j] = a;
+            r.C[i * n + j] = cc + e2->C[i * n + j];
+            r.P[i * n + j] = pp + e1->P[i * n + j];
+        }
+        double cv = 0.0, pv = 0.0;
+        for (int t = 0; t < n; ++t) {
+            cv += e2->A[i * n + t] * X[t * m + 2 * n];
+            pv += e1->A[t * n + i] * Y[t * m2 + n];
+        }
+        r.c[i] = cv + e2->c[i];
+        r.p[i] = pv + e1->p[i];
+    }
+    *out = r;
+    return 1;
+}
+
+/* One-step CVF of a node with a single child (Eq. sol_min for one stage): the stage cost
+ * 1/2 x'Qx + q'x + 1/2 u'Ru + r'u + u'Mx minimised over u subject to x_m = A x + B u + c_m gives
+ *   C = B R^-1 B',  A~ = A - B R^-1 M,  c~ = c_m - B R^-1 r,  P~ = Q - M' R^-1 M,  p~ = q - M' R^-1 r. */
+static int cvf_step(int nx, int nu, const double *Q, const double *M, const double *R, const double *q,
+                    const double *r, const double *A, const double *B, const double *cm, cvf_t *e) {
+    double L[MAXU * MAXU], Z[MAXU * (2 * MAXX + 1)];
+    if (!cholesky(nu, R, L)) return 0;
+    const int m = 2 * nx + 1;   /* Z = R^-1 [B' | M | r] */
+    for (int a = 0; a < nu; ++a) {
+        for (int j = 0; j < nx; ++j) {
+            Z[a * m + j] = B[j * nu + a];
+            Z[a * m + nx + j] = M[a * nx + j];
+        }
+        Z[a * m + 2 * nx] = r[a];
+    }
+    chol_solve(nu, m, L, Z);
+    for (int i = 0; i < nx; ++i) {
+        for (int j = 0; j < nx; ++j) {
+            double cc = 0.0, bm = 0.0, mm = 0.0;
+            for (int a = 0; a < nu; ++a) {
+                cc += B[i * nu + a] * Z[a * m + j];
+                bm += B[i * nu + a] * Z[a * m + nx + j];
+                mm += M[a * nx + i] * Z[a * m + nx + j];
+            }
+            e->C[i * nx + j] = cc;
+            e->A[i * nx + j] = A[i * nx + j] - bm;
+            e->P[i * nx + j] = Q[i * nx + j] - mm;
+        }
+        double br = 0.0, mr = 0.0;
+        for (int a = 0; a < nu; ++a) {
+            br += B[i * nu + a] * Z[a * m + 2 * nx];
+            mr += M[a * nx + i] * Z[a * m + 2 * nx];
+        }
+        e->c[i] = cm[i] - br;
+        e->p[i] = q[i] - mr;
+    }
+    return 1;
+}
+
+/* Feedback law of Eq. (tree_feedback_laws) at non-leaf node i from its children's value functions,
+ * and its own value function (P_i, p_i). */
+static int tree_law(const tree_t *T, int i, int nx, int nu, const double *Q, const double *M, const double *R,
+                    const double *q, const double *r, const double *A, const double *B, const double *c,
+                    const double *Pm, const double *pv, double *Ki, double *ki, double *Pi, double *pi) {
+    double Pbar[MAXX * MAXX] = {0}, pbar[MAXX] = {0};
+    for (int t = 0; t < T->n_child[i]; ++t) {
+        const int ch = T->child[T->first_child[i] + t];
+        double Pc[MAXX];
+        matvec(nx, nx, Pm + (size_t)ch * nx * nx, c + (size_t)ch * nx, Pc);
+        for (int e = 0; e < nx * nx; ++e) Pbar[e] += Pm[(size_t)ch * nx * nx + e];
+        for (int e = 0; e < nx; ++e) pbar[e] += pv[(size_t)ch * nx + e] + Pc[e];
+    }
+    const double *Ai = A + (size_t)i * nx * nx, *Bi = B + (size_t)i * nx * nu;
+    double PA[MAXX * MAXX], PB[MAXX * MAXU], Qxx[MAXX * MAXX], Qux[MAXU * MAXX], Quu[MAXU * MAXU], qx[MAXX], qu[MAXU];
+    matmul(nx, nx, nx, Pbar, Ai, PA);
+    matmul(nx, nx, nu, Pbar, Bi, PB);
+    matTmul(nx, nx, nx, Ai, PA, Qxx);
+    matTmul(nu, nx, nx, Bi, PA, Qux);
+    matTmul(nu, nx, nu, Bi, PB, Quu);
+    matTvec(nx, nx, Ai, pbar, qx);
+    matTvec(nx, nu, Bi, pbar, qu);
+    for (int e = 0; e < nx * nx; ++e) Qxx[e] += Q[(size_t)i * nx * nx + e];
+    for (int e = 0; e < nu * nx; ++e) Qux[e] += M[(size_t)i * nu * nx + e];
+    for (int e = 0; e < nu * nu; ++e) Quu[e] += R[(size_t)i * nu * nu + e];
+    for (int e = 0; e < nx; ++e) qx[e] += q[(size_t)i * nx + e];
+    for (int e = 0; e < nu; ++e) qu[e] += r[(size_t)i * nu + e];
+    double L[MAXU * MAXU];
+    if (!cholesky(nu, Quu, L)) return 0;
+    for (int e = 0; e < nu * nx; ++e) Ki[e] = -Qux[e];
+    for (int e = 0; e < nu; ++e) ki[e] = -qu[e];
+    chol_solve(nu, nx, L, Ki);
+    chol_solve(nu, 1, L, ki);
+    if (Pi) {
+        double QK[MAXX * MAXX], Qk[MAXX];
+        matTmul(nx, nu, nx, Qux, Ki, QK);
+        matTvec(nu, nx, Qux, ki, Qk);
+        for (int a = 0; a < nx; ++a)
+            for (int b = 0; b < nx; ++b)
+                Pi[a * nx + b] = 0.5 * ((Qxx[a * nx + b] + QK[a * nx + b]) + (Qxx[b * nx + a] + QK[b * nx + a]));
+        for (int e = 0; e < nx; ++e) pi[e] = qx[e] + Qk[e];
+    }
+    return 1;
+}
+
+/* The tree LQR of Eq. (lqr_tree_approx) the way Sec. III-B organises it, with the branch points
+ * handled as follows (at a node with several children the one-step CVF couples the children, so
+ * the separable combination of Eq. tree_comb_rule holds only along non-branching segments):
+ *  1. every maximal chain of single-child nodes ending at a leaf or a branch node is a segment; the
+ *     value function at its end (a leaf's terminal cost, or a branch node's tree Riccati step from
+ *     its children) is the last element, and an inclusive suffix scan (Hillis-Steele, span doubling)
+ *     of the one-step CVFs with cvf_combine gives the value function of every node of the segment;
+ *     segments are processed from the deepest end upward;
+ *  2. the feedback laws of Eq. (tree_feedback_laws) at every non-leaf node;
+ *  3. along every root-to-leaf path, an inclusive prefix scan of the closed-loop affine maps
+ *     x_m = (A_n + B_n K_n) x_n + (c_m + B_n k_n) (Eq. forward_comb_rule) from dx_0 = 0.
+ * Outputs as orc_tree_lqr. */
+int orc_tree_lqr_scan(int n, const int *parent, int nx, int nu, const double *Q, const double *M, const double *R,
+                      const double *q, const double *r, const double *A, const double *B, const double *c, double *K,
+                      double *k, double *Pm, double *pv, double *dx, double *du, double *lam) {
+    if (nx > MAXX || nu > MAXU || n < 1) return ORC_ERR_INVALID;
+    orc_problem Pr;
+    memset(&Pr, 0, sizeof Pr);
+    Pr.n = n;
+    Pr.parent = parent;
+    tree_t T;
+    if (!tree_build(&Pr, &T)) { tree_free(&T); return ORC_ERR_INVALID; }
+    int st = ORC_OK;
+    int *chain = (int *)malloc(sizeof(int) * n);
+    cvf_t *S = (cvf_t *)malloc(sizeof(cvf_t) * (n + 1)), *S2 = (cvf_t *)malloc(sizeof(cvf_t) * (n + 1));
+    /* 1. backward: segments, deepest end first (children have larger indices) */
+    for (int b = n - 1; b >= 0 && st == ORC_OK; --b) {
+        if (T.n_child[b] == 1) continue;   /* not the end of a segment */
+        double *Pb = Pm + (size_t)b * nx * nx, *pb = pv + (size_t)b * nx;
+        if (T.n_child[b] == 0) {
+            memcpy(Pb, Q + (size_t)b * nx * nx, sizeof(double) * nx * nx);
+            memcpy(pb, q + (size_t)b * nx, sizeof(double) * nx);
+        } else if (!tree_law(&T, b, nx, nu, Q, M, R, q, r, A, B, c, Pm, pv, K + (size_t)b * nu * nx,
+                             k + (size_t)b * nu, Pb, pb)) {
+            st = ORC_ERR_NUMERIC;
+            break;
+        }
+        int L = 0;   /* single-child ancestors of b, top first */
+        for (int a = b ? parent[b] : -1; a >= 0 && T.n_child[a] == 1; a = a ? parent[a] : -1) chain[L++] = a;
+        for (int i = 0; i < L / 2; ++i) { int t = chain[i]; chain[i] = chain[L - 1 - i]; chain[L - 1 - i] = t; }
+        if (L == 0) continue;
+        for (int i = 0; i < L; ++i) {
+            const int a = chain[i], ch = T.child[T.first_child[a]];
+            if (!cvf_step(nx, nu, Q + (size_t)a * nx * nx, M + (size_t)a * nu * nx, R + (size_t)a * nu * nu,
+                          q + (size_t)a * nx, r + (size_t)a * nu, A + (size_t)a * nx * nx, B + (size_t)a * nx * nu,
+                          c + (size_t)ch * nx, &S[i])) {
+                st = ORC_ERR_NUMERIC;
+                break;
+            }
+        }
+        if (st != ORC_OK) break;
+        memset(&S[L], 0, sizeof(cvf_t));
+        memcpy(S[L].P, Pb, sizeof(double) * nx * nx);
+        memcpy(S[L].p, pb, sizeof(double) * nx);
+        for (int d = 1; d <= L && st == ORC_OK; d *= 2) {
+            for (int i = 0; i <= L; ++i) {
+                if (i + d <= L) {
+                    if (!cvf_combine(nx, &S[i], &S[i + d], &S2[i])) { st = ORC_ERR_NUMERIC; break; }
+                } else {
+                    S2[i] = S[i];
+                }
+            }
+            cvf_t *t = S; S = S2; S2 = t;
+        }
+        for (int i = 0; i < L && st == ORC_OK; ++i) {
+            memcpy(Pm + (size_t)chain[i] * nx * nx, S[i].P, sizeof(double) * nx * nx);
+            memcpy(pv + (size_t)chain[i] * nx, S[i].p, sizeof(double) * nx);
+        }
+    }
+    /* 2. feedback laws of the single-child nodes (branch nodes got theirs with their step) */
+    for (int i = 0; i < n && st == ORC_OK; ++i)
+        if (T.n_child[i] == 1 && !tree_law(&T, i, nx, nu, Q, M, R, q, r, A, B, c, Pm, pv, K + (size_t)i * nu * nx,
+                                           k + (size_t)i * nu, NULL, NULL))
+            st = ORC_ERR_NUMERIC;
+    /* 3. forward: prefix scans of the closed-loop maps along every root-to-leaf path */
+    double *GA = (double *)malloc(sizeof(double) * (n + 1) * nx * nx), *Gc = (double *)malloc(sizeof(double) * (n + 1) * nx);
+    double *HA = (double *)malloc(sizeof(double) * (n + 1) * nx * nx), *Hc = (double *)malloc(sizeof(double) * (n + 1) * nx);
+    for (int leaf = 0; leaf < n && st == ORC_OK; ++leaf) {
+        if (T.n_child[leaf] != 0) continue;
+        int D = 0;
+        for (int a = leaf; a > 0; a = parent[a]) chain[D++] = a;   /* path without the root, leaf first */
+        for (int i = 0; i < D / 2; ++i) { int t = chain[i]; chain[i] = chain[D - 1 - i]; chain[D - 1 - i] = t; }
+        /* element j maps dx of parent(chain[j]) to dx of chain[j] */
+        for (int j = 0; j < D; ++j) {
+            const int m = chain[j], a = parent[m];
+            const double *Ka = K + (size_t)a * nu * nx, *ka = k + (size_t)a * nu, *Ba = B + (size_t)a * nx * nu;
+            for (int i = 0; i < nx; ++i) {
+                for (int t = 0; t < nx; ++t) {
+                    double v = A[(size_t)a * nx * nx + i * nx + t];
+                    for (int s2 = 0; s2 < nu; ++s2) v += Ba[i * nu + s2] * Ka[s2 * nx + t];
+                    GA[(size_t)j * nx * nx + i * nx + t] = v;
+                }
+                double v = c[(size_t)m * nx + i];
+                for (int s2 = 0; s2 < nu; ++s2) v += Ba[i * nu + s2] * ka[s2];
+                Gc[(size_t)j * nx + i] = v;
+            }
+        }
+        for (int d = 1; d < D; d *= 2) {   /* inclusive prefix scan: G_j <- G_j o G_{j-d} */
+            for (int j = 0; j < D; ++j) {
+                if (j >= d) {
+                    const double *A2 = GA + (size_t)j * nx * nx, *A1 = GA + (size_t)(j - d) * nx * nx;
+                    matmul(nx, nx, nx, A2, A1, HA + (size_t)j * nx * nx);
+                    matvec(nx, nx, A2, Gc + (size_t)(j - d) * nx, Hc + (size_t)j * nx);
+                    for (int i = 0; i < nx; ++i) Hc[(size_t)j * nx + i] += Gc[(size_t)j * nx + i];
+                } else {
+                    memcpy(HA + (size_t)j * nx * nx, GA + (size_t)j * nx * nx, sizeof(double) * nx * nx);
+                    memcpy(Hc + (size_t)j * nx, Gc + (size_t)j * nx, sizeof(double) * nx);
+                }
+            }
+            double *t = GA; GA = HA; HA = t;
+            t = Gc; Gc = Hc; Hc = t;
+        }
+        for (int j = 0; j < D; ++j) memcpy(dx + (size_t)chain[j] * nx, Gc + (size_t)j * nx, sizeof(double) * nx);
+    }
+    memset(dx, 0, sizeof(double) * nx);
+    for (int i = 0; i < n && st == ORC_OK; ++i) {
+        double *dui = du + (size_t)i * nu;
+        if (T.n_child[i] == 0) {
+            memset(dui, 0, sizeof(double) * nu);
+        } else {
+            matvec(nu, nx, K + (size_t)i * nu * nx, dx + (size_t)i * nx, dui);
+            for (int e = 0; e < nu; ++e) dui[e] += k[(size_t)i * nu + e];
+        }
+        double Pd[MAXX];
+        matvec(nx, nx, Pm + (size_t)i * nx * nx, dx + (size_t)i * nx, Pd);
+        for (int e = 0; e < nx; ++e) lam[(size_t)i * nx + e] = Pd[e] + pv[(size_t)i * nx + e];
+    }
+    free(GA); free(Gc); free(HA); free(Hc);
+    free(chain); free(S); free(S2);
     tree_free(&T);
     return st;
 }

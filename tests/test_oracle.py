@@ -445,3 +445,41 @@ def test_adamw_first_step_closed_form():
     np.testing.assert_allclose(w1, w - lr * (g / (np.abs(g) + eps) + wd * w), rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(m1, 0.1 * g, rtol=1e-12)
     np.testing.assert_allclose(v1, 0.001 * g * g, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ tree LQR by scans (Sec. III-B)
+def _scan_case_tree(seed):
+    """Ragged random trees (short segments), single paths (one long segment: several scan levels)
+    and branch-point trees shaped like the driving scenes (long segments after the splits)."""
+    rng = np.random.default_rng(300 + seed)
+    kind = seed % 4
+    if kind == 0:
+        return rng, _random_tree(rng)
+    if kind == 1:
+        return rng, np.arange(-1, 20 + 13 * (seed // 4), dtype=np.int32)
+    from scenes.generator import tree_parents
+    splits = {1: 3} if kind == 2 else {1: 2, 4: 2, 9: 2}
+    parent, _ = tree_parents(12 + seed, splits)
+    return rng, np.asarray(parent, np.int32)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_scan_tree_lqr_equals_riccati_and_dense_kkt(seed):
+    """The segment-wise CVF scans with tree Riccati steps at branch nodes and the path-wise forward
+    scans reproduce the sequential tree Riccati recursion (value functions, laws, rollout) and the
+    dense KKT solution; the scans combine the elements in a different association than the
+    sequential recursion, so this also checks the associativity of the combination rule."""
+    rng, parent = _scan_case_tree(seed)
+    nx, nu = (4, 2) if seed % 2 == 0 else (3, 1)
+    leaf, Q, M, R, q, r, A, B, c = _random_lqr(rng, parent, nx, nu)
+    ref = oracle.tree_lqr(parent, Q, M, R, q, r, A, B, c)
+    got = oracle.tree_lqr_scan(parent, Q, M, R, q, r, A, B, c)
+    for name, a, b in zip(("K", "k", "P", "p", "dx", "du", "lam"), got, ref):
+        scale = max(1.0, np.abs(b).max())
+        np.testing.assert_allclose(a, b, atol=1e-9 * scale, err_msg=name)
+    if len(parent) <= 60:
+        dx2, du2, lam2 = _dense_kkt(parent, leaf, Q, M, R, q, r, A, B, c)
+        scale = max(1.0, np.abs(dx2).max(), np.abs(lam2).max())
+        np.testing.assert_allclose(got[4], dx2, atol=1e-9 * scale)
+        np.testing.assert_allclose(got[5], du2, atol=1e-9 * scale)
+        np.testing.assert_allclose(got[6][1:], lam2[1:], atol=1e-9 * scale)
