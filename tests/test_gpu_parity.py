@@ -79,6 +79,16 @@ def test_config3_parity():
     print(_run_config(scenes.instances(3, 2, seed0=1), min_match=0.5))
 
 
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_512_thread_instance_parity(cfg):
+    """The one-block-per-SM instance (512 threads per problem, the single-solve choice of the
+    autotuner) against the oracle, both sweep forms."""
+    ps = scenes.instances(cfg, 3, seed0=40)
+    mm = 0.8 if cfg == 2 else 0.5
+    _run_config(ps, min_match=mm, block_threads=512)
+    _run_config(ps, min_match=mm, block_threads=512, variant=1)
+
+
 def test_mixed_batch_parity():
     print(_run_config(scenes.config4(4, 24)))
 
