@@ -50,10 +50,11 @@ constexpr int MAX_BLOCK = 512;
 constexpr int BATCH_BLOCK = 256;
 constexpr int MAX_WARPS = MAX_BLOCK / 32;
 constexpr int MAX_CHUNK = 16;   /* at most 16 step sizes per line-search round */
-/* Node loops with their loads hoisted ahead of their stores (one or two batches of loads per node
- * instead of one L2 round trip per stored component).  Only where the registers allow it: the
- * dynamic model's kernel is at its register limit, and there the longer live ranges cost more in
- * spills than the hoisting saves (measured), so it keeps the load-compute-store order per row. */
+/* The node loops load before they store (one or two batches of loads per node instead of one L2
+ * round trip per stored component).  The linearisation does so only where the registers allow it:
+ * the dynamic model's kernel is at its register limit, and hoisting there lengthens the live ranges
+ * across the RK4 tangents into spills that cost more than the hoisting saves (measured), so it keeps
+ * the load-compute-store order per row. */
 template <int NX>
 constexpr bool hoist_loads() { return NX <= 4; }
 
@@ -1074,87 +1075,52 @@ __device__ __forceinline__ void forward_node(const View<NX> &V, int i, int pa, b
  * directional terms of the merit (grad'dz, dz'W dz, (dlam - lam)'d). */
 template <int NX, int MODEL>
 __device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, const View<NX> &V, float (&dir)[3]) {
-    constexpr bool HOIST_LOADS = hoist_loads<NX>();
     const int tid = threadIdx.x, nt = blockDim.x, np = V.np;
     for (int i = tid; i < V.n; i += nt) {
-        if constexpr (HOIST_LOADS) {
-            /* two batches of loads: the direction with the cost and penalty terms, then (after the
-             * first merit terms) the value function, multipliers and defect for lam_QP */
-            const int nch = V.nchild[i];
-            float dxv[NX], duv[NU], qv[NX], rv[NU], hrv[NU];
-            V.load_x(V.dx, i, dxv);
-            V.load_u(V.du, i, duv);
-            const float w = V.w[i];
-            const float *Qd = nch ? R.Qw : R.QNw;
-            const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
-            V.load_x(V.q, i, qv);
-            if (nch) {
-                V.load_u(V.r, i, rv);
-                V.load_u(V.hr, i, hrv);
+        /* two batches of loads: the direction with the cost and penalty terms, then (after the
+         * first merit terms) the value function, multipliers and defect for lam_QP */
+        const int nch = V.nchild[i];
+        float dxv[NX], duv[NU], qv[NX], rv[NU], hrv[NU];
+        V.load_x(V.dx, i, dxv);
+        V.load_u(V.du, i, duv);
+        const float w = V.w[i];
+        const float *Qd = nch ? R.Qw : R.QNw;
+        const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+        V.load_x(V.q, i, qv);
+        if (nch) {
+            V.load_u(V.r, i, rv);
+            V.load_u(V.hr, i, hrv);
+        }
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+            dir[0] += qv[a] * dxv[a];
+            dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+        }
+        dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
+        if (nch) {
+#pragma unroll
+            for (int a = 0; a < NU; ++a) {
+                dir[0] += rv[a] * duv[a];
+                dir[1] += (w * R.Rw[a] + hrv[a]) * duv[a] * duv[a];
             }
-    #pragma unroll
+        }
+        if (i != 0) {
+            float pv[NX], Pv[nsym(NX)], lv[NX], dv[NX], lqv[NX];
+            V.load_x(V.p, i, pv);
+#pragma unroll
+            for (int e = 0; e < nsym(NX); ++e) Pv[e] = V.P[(size_t)e * np + i];
+            V.load_x(V.L, i, lv);
+            V.load_x(V.d, i, dv);
+#pragma unroll
             for (int a = 0; a < NX; ++a) {
-                dir[0] += qv[a] * dxv[a];
-                dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+                float v = pv[a];
+#pragma unroll
+                for (int b = 0; b < NX; ++b) v += Pv[sidx<NX>(a, b)] * dxv[b];
+                lqv[a] = v;
+                const float lam = lv[a];
+                dir[2] += ((v - lam) - lam) * dv[a];
             }
-            dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
-            if (nch) {
-    #pragma unroll
-                for (int a = 0; a < NU; ++a) {
-                    dir[0] += rv[a] * duv[a];
-                    dir[1] += (w * R.Rw[a] + hrv[a]) * duv[a] * duv[a];
-                }
-            }
-            if (i != 0) {
-                float pv[NX], Pv[nsym(NX)], lv[NX], dv[NX], lqv[NX];
-                V.load_x(V.p, i, pv);
-    #pragma unroll
-                for (int e = 0; e < nsym(NX); ++e) Pv[e] = V.P[(size_t)e * np + i];
-                V.load_x(V.L, i, lv);
-                V.load_x(V.d, i, dv);
-    #pragma unroll
-                for (int a = 0; a < NX; ++a) {
-                    float v = pv[a];
-    #pragma unroll
-                    for (int b = 0; b < NX; ++b) v += Pv[sidx<NX>(a, b)] * dxv[b];
-                    lqv[a] = v;
-                    const float lam = lv[a];
-                    dir[2] += ((v - lam) - lam) * dv[a];
-                }
-                V.store_x(V.lq, i, lqv);
-            }
-        } else {
-            const int nch = V.nchild[i];
-            float dxv[NX], duv[NU];
-            V.load_x(V.dx, i, dxv);
-            V.load_u(V.du, i, duv);
-            const float w = V.w[i];
-            const float *Qd = nch ? R.Qw : R.QNw;
-            const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
-    #pragma unroll
-            for (int a = 0; a < NX; ++a) {
-                dir[0] += V.q[(size_t)a * np + i] * dxv[a];
-                dir[1] += w * Qd[a] * dxv[a] * dxv[a];
-            }
-            dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
-            if (nch) {
-    #pragma unroll
-                for (int a = 0; a < NU; ++a) {
-                    dir[0] += V.r[(size_t)a * np + i] * duv[a];
-                    dir[1] += (w * R.Rw[a] + V.hr[(size_t)a * np + i]) * duv[a] * duv[a];
-                }
-            }
-            if (i != 0) {
-    #pragma unroll
-                for (int a = 0; a < NX; ++a) {
-                    float v = V.p[(size_t)a * np + i];
-    #pragma unroll
-                    for (int b = 0; b < NX; ++b) v += V.P[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
-                    V.lq[(size_t)a * np + i] = v;
-                    const float lam = V.L[(size_t)a * np + i];
-                    dir[2] += ((v - lam) - lam) * V.d[(size_t)a * np + i];
-                }
-            }
+            V.store_x(V.lq, i, lqv);
         }
     }
 }
@@ -1741,126 +1707,76 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
             float rk = 0.f;
             float sums[3] = {0.f, 0.f, 0.f};   /* L_a, lam'd, |d|^2 */
             for (int i = tid; i < n; i += nt) {
-                if constexpr (HOIST_LOADS) {
-                    /* two batches of loads: the node's and its parent's rows with the children's
-                     * multipliers (defect and the first gradient terms, then the stores of d and the
-                     * merit terms), then the Jacobians A_i, B_i and r_i for the coupling terms */
-                    const int nch = V.nchild[i], fc = V.fchild[i];
-                    const int pa = i ? V.parent[i] : 0;
-                    const float la_i = V.nv[i];
-                    float lsum[NX];
-    #pragma unroll
-                    for (int j = 0; j < NX; ++j) lsum[j] = 0.f;
-                    for (int m = fc; m < fc + nch; ++m)
-    #pragma unroll
-                        for (int j = 0; j < NX; ++j) lsum[j] += V.L[(size_t)j * np + m];
-                    float xi[NX], xri[NX], li[NX], qi[NX], xp[NX], xrp[NX], fp[NX];
-                    V.load_x(V.X, i, xi);
-                    V.load_x(V.xref, i, xri);
-                    V.load_x(V.L, i, li);
-                    V.load_x(V.q, i, qi);
-                    V.load_x(V.X, pa, xp);
-                    V.load_x(V.xref, pa, xrp);
-                    V.load_x(V.f, pa, fp);
-                    float ld = 0.f, dd = 0.f, gx[NX];
-                    if (i != 0) {
-                        float dv[NX];
-    #pragma unroll
-                        for (int j = 0; j < NX; ++j) {
-                            const float dref = xrp[j] - xri[j];
-                            const float dj = (dref + (xp[j] - xi[j])) + fp[j];
-                            dv[j] = dj;
-                            const float lj = li[j];
-                            ld += lj * dj;
-                            dd += dj * dj;
-                            rk = fmaxf(rk, fabsf(dj));
-                            gx[j] = qi[j] - lj;
-                        }
-                        V.store_x(V.d, i, dv);
+                /* two batches of loads: the node's and its parent's rows with the children's
+                 * multipliers (defect and the first gradient terms, then the stores of d and the
+                 * merit terms), then the Jacobians A_i, B_i and r_i for the coupling terms */
+                const int nch = V.nchild[i], fc = V.fchild[i];
+                const int pa = i ? V.parent[i] : 0;
+                const float la_i = V.nv[i];
+                float lsum[NX];
+#pragma unroll
+                for (int j = 0; j < NX; ++j) lsum[j] = 0.f;
+                for (int m = fc; m < fc + nch; ++m)
+#pragma unroll
+                    for (int j = 0; j < NX; ++j) lsum[j] += V.L[(size_t)j * np + m];
+                float xi[NX], xri[NX], li[NX], qi[NX], xp[NX], xrp[NX], fp[NX];
+                V.load_x(V.X, i, xi);
+                V.load_x(V.xref, i, xri);
+                V.load_x(V.L, i, li);
+                V.load_x(V.q, i, qi);
+                V.load_x(V.X, pa, xp);
+                V.load_x(V.xref, pa, xrp);
+                V.load_x(V.f, pa, fp);
+                float ld = 0.f, dd = 0.f, gx[NX];
+                if (i != 0) {
+                    float dv[NX];
+#pragma unroll
+                    for (int j = 0; j < NX; ++j) {
+                        const float dref = xrp[j] - xri[j];
+                        const float dj = (dref + (xp[j] - xi[j])) + fp[j];
+                        dv[j] = dj;
+                        const float lj = li[j];
+                        ld += lj * dj;
+                        dd += dj * dj;
+                        rk = fmaxf(rk, fabsf(dj));
+                        gx[j] = qi[j] - lj;
                     }
-                    V.nv[(size_t)np + i] = ld;
-                    V.nv[2 * (size_t)np + i] = dd;
-                    if (nch) {
-                        float Ai[NX][NX], Bi[NX][NU], ri[NU];
-    #pragma unroll
-                        for (int a = 0; a < NX; ++a) {
-    #pragma unroll
-                            for (int b = 0; b < NX; ++b) Ai[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
-    #pragma unroll
-                            for (int b = 0; b < NU; ++b) Bi[a][b] = V.B[(size_t)(a * NU + b) * np + i];
-                        }
-                        V.load_u(V.r, i, ri);
-                        if (i != 0) {
-    #pragma unroll
-                            for (int a = 0; a < NX; ++a)
-    #pragma unroll
-                                for (int b = 0; b < NX; ++b) gx[b] += Ai[a][b] * lsum[a];
-                        }
-    #pragma unroll
-                        for (int b = 0; b < NU; ++b) {
-                            float gu = ri[b];
-    #pragma unroll
-                            for (int a = 0; a < NX; ++a) gu += Bi[a][b] * lsum[a];
-                            rk = fmaxf(rk, fabsf(gu));
-                        }
-                    }
-                    if (i != 0) {
-    #pragma unroll
-                        for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
-                    }
-                    if (!(rk == rk)) rk = INFINITY;
-                    sums[0] += la_i;
-                    sums[1] += ld;
-                    sums[2] += dd;
-                } else {
-                    const int nch = V.nchild[i], fc = V.fchild[i];
-                    float lsum[NX];
-    #pragma unroll
-                    for (int j = 0; j < NX; ++j) lsum[j] = 0.f;
-                    for (int m = fc; m < fc + nch; ++m)
-    #pragma unroll
-                        for (int j = 0; j < NX; ++j) lsum[j] += V.L[(size_t)j * np + m];
-                    float ld = 0.f, dd = 0.f;
-                    if (i != 0) {
-                        const int pa = V.parent[i];
-                        float gx[NX];
-    #pragma unroll
-                        for (int j = 0; j < NX; ++j) {
-                            const float dref = V.xref[(size_t)j * np + pa] - V.xref[(size_t)j * np + i];
-                            const float dj = (dref + (V.X[(size_t)j * np + pa] - V.X[(size_t)j * np + i])) +
-                                             V.f[(size_t)j * np + pa];
-                            V.d[(size_t)j * np + i] = dj;
-                            const float lj = V.L[(size_t)j * np + i];
-                            ld += lj * dj;
-                            dd += dj * dj;
-                            rk = fmaxf(rk, fabsf(dj));
-                            gx[j] = V.q[(size_t)j * np + i] - lj;
-                        }
-                        if (nch) {
-    #pragma unroll
-                            for (int a = 0; a < NX; ++a)
-    #pragma unroll
-                                for (int b = 0; b < NX; ++b) gx[b] += aload<NX, MODEL>(V.A, np, i, a, b) * lsum[a];
-                        }
-    #pragma unroll
-                        for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
-                    }
-                    if (nch) {
-    #pragma unroll
-                        for (int b = 0; b < NU; ++b) {
-                            float gu = V.r[(size_t)b * np + i];
-    #pragma unroll
-                            for (int a = 0; a < NX; ++a) gu += V.B[(size_t)(a * NU + b) * np + i] * lsum[a];
-                            rk = fmaxf(rk, fabsf(gu));
-                        }
-                    }
-                    if (!(rk == rk)) rk = INFINITY;
-                    V.nv[(size_t)np + i] = ld;
-                    V.nv[2 * (size_t)np + i] = dd;
-                    sums[0] += V.nv[i];
-                    sums[1] += ld;
-                    sums[2] += dd;
+                    V.store_x(V.d, i, dv);
                 }
+                V.nv[(size_t)np + i] = ld;
+                V.nv[2 * (size_t)np + i] = dd;
+                if (nch) {
+                    float Ai[NX][NX], Bi[NX][NU], ri[NU];
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+                        for (int b = 0; b < NX; ++b) Ai[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
+#pragma unroll
+                        for (int b = 0; b < NU; ++b) Bi[a][b] = V.B[(size_t)(a * NU + b) * np + i];
+                    }
+                    V.load_u(V.r, i, ri);
+                    if (i != 0) {
+#pragma unroll
+                        for (int a = 0; a < NX; ++a)
+#pragma unroll
+                            for (int b = 0; b < NX; ++b) gx[b] += Ai[a][b] * lsum[a];
+                    }
+#pragma unroll
+                    for (int b = 0; b < NU; ++b) {
+                        float gu = ri[b];
+#pragma unroll
+                        for (int a = 0; a < NX; ++a) gu += Bi[a][b] * lsum[a];
+                        rk = fmaxf(rk, fabsf(gu));
+                    }
+                }
+                if (i != 0) {
+#pragma unroll
+                    for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
+                }
+                if (!(rk == rk)) rk = INFINITY;
+                sums[0] += la_i;
+                sums[1] += ld;
+                sums[2] += dd;
             }
             r_kkt = block_max(rk, sh);
             block_sum<3>(sums, sh);
