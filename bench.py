@@ -363,7 +363,9 @@ def run_gpu(args):
                    "nodes_per_gpu": int(sum(int(p["n"]) for p in problems)),
                    "l2": f"working set {(b.data_bytes + b.scratch_bytes) / 1e9:.2f} GB > 126 MB L2, no flush",
                    "launch": "one persistent kernel per model per step, CUDA graph replay",
-                   "opts": {"block_threads": opts.block_threads, "variant": opts.variant, "ls_chunk": opts.ls_chunk,
+                   "opts": {"block_threads": opts.block_threads,
+                            "block_threads_model": list(opts.block_threads_model),
+                            "variant": opts.variant, "ls_chunk": opts.ls_chunk,
                             "max_iters": opts.max_iters, "autotuned": tuned is not None,
                             "queue_order": "longest predicted first (previous step's iterations)"
                             if opts.queue_order == 1 else "largest tree first"}},

@@ -128,6 +128,11 @@ typedef struct {
                                problem's previous solve in this batch + 1), sorted on the device before
                                each launch (so also inside a captured graph); 0 largest tree first.
                                The solutions do not depend on it. */
+    int32_t block_threads_model[3]; /* threads per problem for the launch of one dynamics model (0
+                               kinematic, 1 dynamic, 2 linear) in a mixed batch (32..512, multiple of
+                               32); 0 = block_threads.  Each model has its own launch, so a mixed
+                               batch can run, e.g., its kinematic problems two per SM and its large
+                               dynamic ones one per SM. Default 0. */
 } bmpc_opts;
 
 typedef struct {

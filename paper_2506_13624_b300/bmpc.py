@@ -45,7 +45,8 @@ class Opts(C.Structure):
                 ("rho0", C.c_float), ("rho_max", C.c_float), ("mu0", C.c_float), ("beta", C.c_float),
                 ("ls_rel_eps", C.c_float), ("ls_chunk", C.c_int32), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("variant", C.c_int32), ("warm_select", C.c_int32),
-                ("select_mu", C.c_float), ("select_rho", C.c_float), ("queue_order", C.c_int32)]
+                ("select_mu", C.c_float), ("select_rho", C.c_float), ("queue_order", C.c_int32),
+                ("block_threads_model", C.c_int32 * 3)]
 
 
 class Stats(C.Structure):
@@ -136,6 +137,8 @@ def default_opts(**kw) -> Opts:
     o = Opts()
     lib().bmpc_default_opts(C.byref(o))
     for k, v in kw.items():
+        if k == "block_threads_model":
+            v = (C.c_int32 * 3)(*v)
         setattr(o, k, v)
     return o
 

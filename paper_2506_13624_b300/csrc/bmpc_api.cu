@@ -250,6 +250,10 @@ int check_opts(const bmpc_opts &o) {
     if (o.warm_select < 0 || o.warm_select > 1 || !(o.select_mu >= 0.f) ||
         !(o.select_rho > 0.f)) return BMPC_ERR_INVALID;
     if (o.queue_order < 0 || o.queue_order > 1) return BMPC_ERR_INVALID;
+    for (int m = 0; m < 3; ++m) {
+        const int bt = o.block_threads_model[m];
+        if (bt != 0 && (bt < 32 || bt > max_block_threads() || bt % 32)) return BMPC_ERR_INVALID;
+    }
     if ((o.variant == 0 || o.variant == 3) && o.block_threads != 0 && o.block_threads % 32) return BMPC_ERR_INVALID;
     return BMPC_OK;
 }
@@ -316,7 +320,7 @@ FlatArgs flat_args(bmpc_batch *b) {
 
 /* Launch geometry for the problems of one model: threads per problem and persistent blocks. */
 void geometry(const bmpc_batch *b, const bmpc_opts &o, int model, int count, int *grid, int *block) {
-    int bt = o.block_threads;
+    int bt = o.block_threads_model[model] ? o.block_threads_model[model] : o.block_threads;
     if (bt == 0) bt = count == 1 ? 128 : 32;
     int per_sm = o.blocks_per_sm;
     if (per_sm == 0) {
@@ -405,6 +409,7 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->select_mu = 100.f;
     o->select_rho = 1e4f;
     o->queue_order = 1;
+    for (int m = 0; m < 3; ++m) o->block_threads_model[m] = 0;
 }
 
 int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
@@ -863,36 +868,62 @@ int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *
     bmpc_opts best_o = o;
     float best_ms = 0.f;
     int rc = BMPC_OK;
+    /* converged solves per ms of configuration c (one warm-up launch, one timed); -1 on a CUDA error */
+    auto trial = [&](const bmpc_opts &c, float *ms_out) -> double {
+        if (launch(b, c) != BMPC_OK) return -1.0;
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess || launch(b, c) != BMPC_OK ||
+            cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+            return -1.0;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (cudaMemcpy(stats.data(), b->data + b->L.stats, sizeof(Stats) * b->n, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return -1.0;
+        int conv = 0;
+        for (const Stats &s : stats) conv += s.status == BMPC_OK;
+        *ms_out = ms;
+        return ms > 0.f ? conv / (double)ms : 0.0;
+    };
     for (int bt : kThreads)
         for (int v : kVariant)
             for (int ch : kChunk) {
                 bmpc_opts c = o;
                 c.block_threads = bt;
+                for (int m = 0; m < 3; ++m) c.block_threads_model[m] = 0;
                 c.variant = v;
                 c.ls_chunk = ch;
                 c.blocks_per_sm = 0;
-                if (launch(b, c) != BMPC_OK) { rc = BMPC_ERR_CUDA; goto out; }       /* warm-up */
-                if (cudaEventRecord(e0, b->stream) != cudaSuccess || launch(b, c) != BMPC_OK ||
-                    cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-                    rc = BMPC_ERR_CUDA;
-                    goto out;
-                }
                 float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (cudaMemcpy(stats.data(), b->data + b->L.stats, sizeof(Stats) * b->n, cudaMemcpyDeviceToHost) !=
-                    cudaSuccess) {
-                    rc = BMPC_ERR_CUDA;
-                    goto out;
-                }
-                int conv = 0;
-                for (const Stats &s : stats) conv += s.status == BMPC_OK;
-                const double rate = ms > 0.f ? conv / (double)ms : 0.0;
+                const double rate = trial(c, &ms);
+                if (rate < 0.0) { rc = BMPC_ERR_CUDA; goto out; }
                 if (rate > best_rate) {
                     best_rate = rate;
                     best_o = c;
                     best_ms = ms;
                 }
             }
+    /* mixed batches: then the threads per problem of each model's launch, one model at a time */
+    {
+        int models = 0;
+        for (int m = 0; m < 3; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
+        for (int m = 0; m < 3 && models > 1; ++m) {
+            if (b->model_begin[m + 1] == b->model_begin[m]) continue;
+            const bmpc_opts base_o = best_o;
+            for (int bt : kThreads) {
+                if (bt == base_o.block_threads) continue;
+                bmpc_opts c = base_o;
+                c.block_threads_model[m] = bt;
+                float ms = 0.f;
+                const double rate = trial(c, &ms);
+                if (rate < 0.0) { rc = BMPC_ERR_CUDA; goto out; }
+                if (rate > best_rate) {
+                    best_rate = rate;
+                    best_o = c;
+                    best_ms = ms;
+                }
+            }
+        }
+    }
 out:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -93,6 +93,12 @@ def test_mixed_batch_parity():
     print(_run_config(scenes.config4(4, 24)))
 
 
+def test_mixed_batch_with_per_model_block_sizes():
+    """A mixed batch whose kinematic launch uses 128 threads per problem and its dynamic launch 512:
+    the same parity as with one block size."""
+    print(_run_config(scenes.config4(4, 16), block_threads=256, block_threads_model=[128, 512, 0]))
+
+
 def test_linear_quadratic_one_iteration():
     ps = [scenes.linear_problem(s, N=12, splits={2: 2, 6: 3}) for s in range(3)]
     gres = _gpu(ps)
