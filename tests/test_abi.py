@@ -120,3 +120,20 @@ def test_wait_selftest_rejects_out_of_range_limits():
     L = mlp._setup()
     assert L.bmpc_mlp_selftest_wait(0, None) == -1
     assert L.bmpc_mlp_selftest_wait(10 ** 9, None) == -1
+
+
+def test_default_options_match_their_documentation():
+    """bmpc_default_opts (host only) sets the constants include/bmpc.h documents: the readings of the
+    paper's unstated constants (rho0 = 10, rho_max = 100, mu0 = 1, Armijo beta = 1e-4, alpha_i = 2^-i
+    for i < 10, 50 inner iterations) and automatic launch geometry."""
+    o = bmpc.default_opts()
+    assert (o.max_iters, o.max_outer, o.n_alpha) == (50, 60, 10)
+    assert o.eps_tol == np.float32(1e-5) and o.tau == 100.0
+    assert (o.omega0, o.a_omega, o.b_omega, o.a_eta) == (1.0, 1.0, 1.0, np.float32(0.1))
+    assert o.eta0 == np.float32(0.1) and o.b_eta == np.float32(0.9)
+    assert (o.rho0, o.rho_max, o.mu0) == (10.0, 100.0, 1.0)
+    assert o.beta == np.float32(1e-4) and o.ls_rel_eps == np.float32(1e-6)
+    assert (o.block_threads, o.blocks_per_sm, o.variant, o.warm_select, o.queue_order) == (0, 0, 0, 0, 1)
+    assert list(o.block_threads_model) == [0, 0, 0]
+    assert o.select_mu == 100.0 and o.select_rho == 1e4
+    assert C.sizeof(bmpc.Opts) == 27 * 4   # 27 four-byte fields, as in bmpc_opts
