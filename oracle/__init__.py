@@ -46,7 +46,7 @@ class Opts(C.Structure):
                 ("eta0", C.c_double), ("a_omega", C.c_double), ("b_omega", C.c_double),
                 ("a_eta", C.c_double), ("b_eta", C.c_double), ("rho0", C.c_double),
                 ("rho_max", C.c_double), ("mu0", C.c_double), ("beta", C.c_double),
-                ("ls_rel_eps", C.c_double)]
+                ("ls_rel_eps", C.c_double), ("lqr_scan", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -68,6 +68,7 @@ typedef struct {
     int max_iters, max_outer, n_alpha;
     double eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta;
     double rho0, rho_max, mu0, beta, ls_rel_eps;
+    int lqr_scan;           /* 1: the search direction by the scans of Sec. III-B (orc_tree_lqr_scan) */
 } orc_opts;
 
 typedef struct {
@@ -667,16 +668,12 @@ static int tree_law(const tree_t *T, int i, int nx, int nu, const double *Q, con
  *  3. along every root-to-leaf path, an inclusive prefix scan of the closed-loop affine maps
  *     x_m = (A_n + B_n K_n) x_n + (c_m + B_n k_n) (Eq. forward_comb_rule) from dx_0 = 0.
  * Outputs as orc_tree_lqr. */
-int orc_tree_lqr_scan(int n, const int *parent, int nx, int nu, const double *Q, const double *M, const double *R,
-                      const double *q, const double *r, const double *A, const double *B, const double *c, double *K,
-                      double *k, double *Pm, double *pv, double *dx, double *du, double *lam) {
-    if (nx > MAXX || nu > MAXU || n < 1) return ORC_ERR_INVALID;
-    orc_problem Pr;
-    memset(&Pr, 0, sizeof Pr);
-    Pr.n = n;
-    Pr.parent = parent;
-    tree_t T;
-    if (!tree_build(&Pr, &T)) { tree_free(&T); return ORC_ERR_INVALID; }
+static int tree_lqr_scan(const tree_t *Tp, const int *parent, int nx, int nu, const double *Q, const double *M,
+                         const double *R, const double *q, const double *r, const double *A, const double *B,
+                         const double *c, double *K, double *k, double *Pm, double *pv, double *dx, double *du,
+                         double *lam) {
+    const tree_t T = *Tp;
+    const int n = T.n;
     int st = ORC_OK;
     int *chain = (int *)malloc(sizeof(int) * n);
     cvf_t *S = (cvf_t *)malloc(sizeof(cvf_t) * (n + 1)), *S2 = (cvf_t *)malloc(sizeof(cvf_t) * (n + 1));
@@ -784,6 +781,20 @@ int orc_tree_lqr_scan(int n, const int *parent, int nx, int nu, const double *Q,
     }
     free(GA); free(Gc); free(HA); free(Hc);
     free(chain); free(S); free(S2);
+    return st;
+}
+
+int orc_tree_lqr_scan(int n, const int *parent, int nx, int nu, const double *Q, const double *M, const double *R,
+                      const double *q, const double *r, const double *A, const double *B, const double *c, double *K,
+                      double *k, double *Pm, double *pv, double *dx, double *du, double *lam) {
+    if (nx > MAXX || nu > MAXU || n < 1) return ORC_ERR_INVALID;
+    orc_problem Pr;
+    memset(&Pr, 0, sizeof Pr);
+    Pr.n = n;
+    Pr.parent = parent;
+    tree_t T;
+    if (!tree_build(&Pr, &T)) { tree_free(&T); return ORC_ERR_INVALID; }
+    const int st = tree_lqr_scan(&T, parent, nx, nu, Q, M, R, q, r, A, B, c, K, k, Pm, pv, dx, du, lam);
     tree_free(&T);
     return st;
 }
@@ -1015,16 +1026,19 @@ void orc_default_opts(orc_opts *o) {
     o->mu0 = 1.0;
     o->beta = 1e-4;
     o->ls_rel_eps = 1e-6;
+    o->lqr_scan = 0;
 }
 
 /* Directional data of one inner iteration at (x, u, lam) for fixed (y, rho, mu), with W
  * already linearised at (x, u): solves the tree LQR, and returns dx, du, dlam = lam_QP - lam,
  * phi(0), phi'(0) of the merit along (dx, du, dlam), dz'W dz and |d|^2. */
 static int direction(const orc_problem *P, work_t *W, const double *x, const double *u, const double *lam,
-                     const double *y, double rho, double mu, double *dlam, double out[6]) {
+                     const double *y, double rho, double mu, int scan, double *dlam, double out[6]) {
     int n = P->n, nx = P->nx, nu = P->nu;
-    int st = tree_lqr(&W->T, nx, nu, W->Q, W->M, W->R, W->q, W->r, W->A, W->B, W->d, W->K, W->k, W->P, W->p,
-                      W->dx, W->du, W->lqp);
+    int st = scan ? tree_lqr_scan(&W->T, P->parent, nx, nu, W->Q, W->M, W->R, W->q, W->r, W->A, W->B, W->d, W->K,
+                                  W->k, W->P, W->p, W->dx, W->du, W->lqp)
+                  : tree_lqr(&W->T, nx, nu, W->Q, W->M, W->R, W->q, W->r, W->A, W->B, W->d, W->K, W->k, W->P, W->p,
+                             W->dx, W->du, W->lqp);
     if (st) return st;
     double gd = 0.0, wq = 0.0, ld = 0.0, dd = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -1096,7 +1110,7 @@ int orc_solve(const orc_problem *P, const orc_opts *O_in, const double *wx, cons
             if (r_kkt <= omega) break;
             if (inner >= O.max_iters) goto done;
             double info[6];
-            int st = direction(P, &W, x, u, lam, y, rho, mu, dlam, info);
+            int st = direction(P, &W, x, u, lam, y, rho, mu, O.lqr_scan, dlam, info);
             if (st) { status = st; goto done; }
             double wq = info[2], dd = info[3], dphi0 = info[4];
             /* adaptive merit penalty (Gill et al. 1992 reading) */
@@ -1266,7 +1280,7 @@ int orc_direction(const orc_problem *P, const double *x, const double *u, const 
     if (!tree_build(P, &W.T)) { tree_free(&W.T); return ORC_ERR_INVALID; }
     work_alloc(&W, P);
     linearise(P, &W, x, u, y, rho);
-    int st = direction(P, &W, x, u, lam, y, rho, mu, dlam, info);
+    int st = direction(P, &W, x, u, lam, y, rho, mu, 0, dlam, info);
     memcpy(dx, W.dx, sizeof(double) * P->n * P->nx);
     memcpy(du, W.du, sizeof(double) * P->n * P->nu);
     work_free(&W);

@@ -483,3 +483,19 @@ def test_scan_tree_lqr_equals_riccati_and_dense_kkt(seed):
         np.testing.assert_allclose(got[4], dx2, atol=1e-9 * scale)
         np.testing.assert_allclose(got[5], du2, atol=1e-9 * scale)
         np.testing.assert_allclose(got[6][1:], lam2[1:], atol=1e-9 * scale)
+
+
+@pytest.mark.parametrize("cfg,seed", [(1, 0), (1, 5), (2, 3), (0, 4)])
+def test_full_solve_with_scan_lqr_equals_riccati(cfg, seed):
+    """The whole AL-iLQR solve with its search direction from the scans of Sec. III-B takes the same
+    iterations to the same point as with the sequential tree Riccati recursion: the scan form
+    replaces the recursion inside the method, not only on random LQ data."""
+    p = scenes.linear_problem(seed, N=14, splits={3: 2, 7: 3}, constrained=True) if cfg == 0 else \
+        scenes.instances(cfg, 1, seed0=seed)[0]
+    a = oracle.solve(p)
+    b = oracle.solve(p, lqr_scan=1)
+    assert a["status"] == b["status"]
+    assert (a["inner_iters"], a["outer_iters"]) == (b["inner_iters"], b["outer_iters"])
+    for key in ("x", "u", "lam", "y"):
+        scale = max(1.0, np.abs(a[key]).max())
+        np.testing.assert_allclose(b[key], a[key], atol=1e-8 * scale, err_msg=key)
