@@ -47,3 +47,17 @@ def test_two_gloo_ranks_shard_and_reduce():
         assert ms == 11.0 and e2e == 50.0 and conv == 201.0
         a, b = np.array(gathered[0]), np.array(gathered[1])
         assert a.shape == b.shape and not np.any(np.all(a[:, None, :] == b[None, :, :], axis=2))
+
+
+def test_profiled_traffic_only_for_the_captured_kernel(tmp_path, monkeypatch):
+    """bench.py reports the roofline traffic from an ncu capture only while the kernel sources hash
+    to the captured version; otherwise, and for other workloads, it reports null."""
+    import bench
+    sha = bench.kernel_sha()
+    prof = tmp_path / "capture.md"
+    prof.write_text(f"kernel_sha256: {sha}\ndram_bytes_per_problem: 1000\nproblems_captured: 512\n")
+    monkeypatch.setattr(bench, "PROFILE", str(prof))
+    assert bench.profiled_traffic("config2", 2048) == 1000.0 * 2048
+    assert bench.profiled_traffic("config3", 1024) is None
+    prof.write_text("kernel_sha256: 0000000000000000\ndram_bytes_per_problem: 1000\n")
+    assert bench.profiled_traffic("config2", 2048) is None
