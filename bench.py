@@ -3,13 +3,24 @@
 One step = one batch of seeded synthetic scenario-tree problems solved to
 convergence by the whole hot path (RK4 linearisation, tree Riccati recursion,
 forward rollout, merit line search, BCL update) in one persistent kernel
-launch, replayed from a captured CUDA graph.
+launch per dynamics model, replayed from a captured CUDA graph.  The default
+workload is the mixed batch: 4,096 problems with 2-64 scenarios, horizons
+20-60, 1-5 obstacles, kinematic and dynamic bicycles.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config2|config4] [--batch B]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config1..config4] [--batch B]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
+  python bench.py --single ...           # single-problem latency against its critical path
 
 Under torchrun every rank solves its own shard of B problems (weak scaling, no
 data-path collective); rank 0 prints one JSON line.
+
+Roofs.  The solver's work per problem is a chain of dependent steps (the tree
+sweeps walk the depth N + 1 twice per iteration), so the roof that binds is
+latency: a problem's iteration cannot be shorter than that of a single-path
+tree of the same depth and model run with one node per thread (its critical
+path, measured here on the same kernel).  The FP32 ALU roof uses the FP32 FMA
+peak measured by the library's own microbenchmark; the HBM roof the measured
+copy bandwidth (MEASURED_PEAKS.json).
 """
 from __future__ import annotations
 
@@ -30,6 +41,7 @@ sys.path.insert(0, ROOT)
 import scenes  # noqa: E402
 
 METRIC = "BMPC solves/sec at KKT<=1e-5 (FP32)"
+DEFAULT_WORKLOAD, DEFAULT_BATCH = "config4", 4096
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
 
@@ -77,6 +89,14 @@ def flops_model(p) -> dict:
         update=6 * nx,
         outer=con,
     )
+
+
+def algorithmic_bytes_per_node_iter(p) -> float:
+    """Minimum DRAM bytes per node and inner iteration: read and write x, u, lambda, y; read the
+    obstacle data (5 values each); write and read the feedback law K, k between the two sweeps."""
+    nx, nc, n_obs = int(p["nx"]), 2 * 2 * int(p["box_on"]) + int(p["n_obs"]) + 2 * int(p["lane_on"]), int(p["n_obs"])
+    state = 2 * nx + 2 + nc
+    return 4.0 * (2 * state + 5 * n_obs + 2 * (2 * nx + 2))
 
 
 def algorithmic_flops(problems, results) -> float:
@@ -156,19 +176,20 @@ def oracle_rate(name: str, seconds: float, max_problems: int, rank: int = 0):
     t0 = time.perf_counter()
     solved = done = 0
     for p in probs:
-        r = oracle.solve(p)
+        r = oracle.solve(p, **oracle.PRODUCT_RULE)
         done += 1
         solved += int(r["status"] == oracle.OK)
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
     return dict(value=solved / dt, attempted_per_s=done / dt, unit="solves/s", cores=1, kind="oracle",
-                sample=f"{done} {name} problems solved sequentially with the FP64 oracle ({dt:.1f} s)")
+                sample=f"{done} {name} problems solved sequentially with the FP64 oracle ({dt:.1f} s), "
+                       f"the library's failed-outer-step rule (oracle.PRODUCT_RULE)")
 
 
 def _oracle_converged(p):
     import oracle
-    return int(oracle.solve(p)["status"] == oracle.OK)
+    return int(oracle.solve(p, **oracle.PRODUCT_RULE)["status"] == oracle.OK)
 
 
 def run_reference(args):
@@ -207,7 +228,7 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- ncu traffic
-PROFILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "bmpc_solve_kernel_config2.md")
+PROFILES = {"config2": "bmpc_solve_kernel_config2.md", "config4": "bmpc_solve_kernel_config4.md"}
 KERNEL_SOURCES = ("paper_2506_13624_b300/csrc/bmpc_kernel.cu", "paper_2506_13624_b300/csrc/bmpc_layout.h")
 
 
@@ -221,21 +242,69 @@ def kernel_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_name, batch):
-    """DRAM bytes (read + write) of one solve launch, scaled by problems from the committed ncu
-    capture of config-2 problems; None for other workloads or when the kernel sources changed
-    since the capture."""
-    if workload_name != "config2" or not os.path.exists(PROFILE):
+def profiled_traffic(workload_name, node_iters):
+    """DRAM bytes (read + write) of one step's solve launches, scaled from the committed ncu capture
+    of the same workload on a reduced batch by node-iterations (a problem's traffic is its scratch
+    rows, written and read once or twice per node and iteration); None when there is no capture of
+    this workload or the kernel sources changed since it was taken."""
+    name = PROFILES.get(workload_name)
+    path = os.path.join(ROOT, "profiles", name) if name else None
+    if not path or not os.path.exists(path):
         return None
     kv = {}
-    with open(PROFILE) as fh:
+    with open(path) as fh:
         for line in fh:
             k, _, v = line.partition(":")
-            if k in ("kernel_sha256", "dram_bytes_per_problem"):
+            if k in ("kernel_sha256", "dram_bytes_per_node_iteration"):
                 kv[k] = v.strip()
-    if kv.get("kernel_sha256") != kernel_sha() or "dram_bytes_per_problem" not in kv:
+    if kv.get("kernel_sha256") != kernel_sha() or "dram_bytes_per_node_iteration" not in kv:
         return None
-    return float(kv["dram_bytes_per_problem"]) * batch
+    return float(kv["dram_bytes_per_node_iteration"]) * node_iters
+
+
+# ----------------------------------------------------------------- latency floor (critical path)
+CHAIN_N = (20, 40, 60)
+
+
+def chain_floor(bmpc, models, seeds=3):
+    """Cycles per inner iteration of single-path trees (one scenario) of depth N in CHAIN_N, per model,
+    solved one at a time with one node per thread (64 threads, per-path sweeps), and a straight-line
+    fit T(N) = a + b (N + 1): b is the per-stage latency of the two sweeps (t_bwd + t_fwd), a the
+    rest of an iteration (the node-parallel phases at one node per thread and their block
+    reductions).  Also the sweeps alone: backward and forward cycles per stage."""
+    fits = {}
+    for m in models:
+        xs, ys, bw, fw = [], [], [], []
+        for N in CHAIN_N:
+            ps = [scenes.chain_problem(s, m, N) for s in range(seeds)]
+            for p in ps:
+                b = bmpc.Batch([p])
+                b.set_problems()
+                o = bmpc.default_opts(block_threads=64, variant=2)
+                b.solve(o)
+                b.solve(o)
+                r = b.get_solutions(want_arrays=False)[0]
+                b.close()
+                it = max(1, r["inner_iters"])
+                c = r["cycles"]
+                per = (c["linearise"] + c["backward"] + c["forward"] + c["linesearch"]) / it
+                xs.append(N + 1)
+                ys.append(per)
+                bw.append(c["backward"] / it / (N + 1))
+                fw.append(c["forward"] / it / (N + 1))
+        slope, icpt = np.polyfit(np.asarray(xs, float), np.asarray(ys, float), 1)
+        fits[int(m)] = dict(a_cycles=float(icpt), b_cycles_per_stage=float(slope),
+                            t_bwd_cycles=float(np.median(bw)), t_fwd_cycles=float(np.median(fw)))
+    return fits
+
+
+def depth(p):
+    return int(np.max(p["stage"]))
+
+
+def crit_cycles_per_iter(p, fits):
+    f = fits[int(p["model"])]
+    return f["a_cycles"] + f["b_cycles_per_stage"] * (depth(p) + 1)
 
 
 # ----------------------------------------------------------------- weak scaling over ranks
@@ -286,6 +355,12 @@ def run_gpu(args):
         b.solve(opts, graph=True)
     res = b.get_solutions(want_arrays=False)
     conv = np.array([r["status"] == 0 for r in res])
+
+    # roof denominators measured on this device before the timed region: the FP32 FMA peak of the
+    # library's microbenchmark and the critical path of single-path trees of every model present
+    with torch.cuda.stream(stream):
+        fp32_peak = bmpc.fp32_peak_tflops()
+    fits = chain_floor(bmpc, sorted({int(p["model"]) for p in problems}))
 
     sampler = ClockSampler(local)
     if rank == 0:
@@ -344,9 +419,24 @@ def run_gpu(args):
     value = total_conv / (ms / 1e3)
     flops = algorithmic_flops(problems, res)
     n_models = len({int(p["model"]) for p in problems})   # one solve (+ one queue-order) kernel per model
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / (ms / 1e3) / 1e12
     iters = np.array([r["inner_iters"] for r in res])
+    # latency roof: every problem's iterations against its critical path (same cycle counter)
+    meas_cyc = np.array([sum(r["cycles"][k] for k in ("linearise", "backward", "forward", "linesearch"))
+                         for r in res], dtype=np.float64)
+    crit_cyc = np.array([crit_cycles_per_iter(p, fits) * r["inner_iters"] for p, r in zip(problems, res)])
+    lat_frac = float(crit_cyc.sum() / max(meas_cyc.sum(), 1.0))
+    clk_hz = ((clocks or {}).get("sm_mhz") or SM_MAX_MHZ) * 1e6
+    lat_achieved = float(iters.sum() / (meas_cyc.sum() / clk_hz))
+    lat_peak = float(iters.sum() / (crit_cyc.sum() / clk_hz))
+    node_iters = float(sum(int(p["n"]) * r["inner_iters"] for p, r in zip(problems, res)))
+    alg_bytes = float(sum(int(p["n"]) * r["inner_iters"] * algorithmic_bytes_per_node_iter(p)
+                          for p, r in zip(problems, res)))
+    hbm_peak = None
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as fh:
+            hbm_peak = json.load(fh).get("hbm_gbs")
+    hbm_achieved = alg_bytes / (ms / 1e3) / 1e9
     clk = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
     bwd_us = np.array([r["cycles"]["backward"] for r in res]) / (clk * 1e6) * 1e6
     ric_us_iter = float(np.sum(bwd_us) / max(1, iters.sum()))
@@ -375,10 +465,20 @@ def run_gpu(args):
         "solve_latency_us": {"mean": float(tot_us.mean()), "max": float(tot_us.max())},
         "inner_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
         "gpu_launches": args.steps * n_models * (2 if opts.queue_order == 1 else 1),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload, args.batch),
-                     "traffic_unit": "bytes per launch (ncu dram read + write, scaled by problems)",
-                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"},
+        "roofline": {"bound": "latency", "achieved": lat_achieved, "peak": lat_peak,
+                     "unit": "inner iterations/s per problem in flight", "frac": lat_frac,
+                     "traffic": profiled_traffic(args.workload, node_iters),
+                     "traffic_unit": "bytes per step (ncu dram read + write of the solve launches, scaled by "
+                                     "node-iterations from a reduced-batch capture)",
+                     "peak_source": "critical path per iteration: single-path trees of the same depth and model, "
+                                    "one node per thread, alone on the GPU (measured before the timed region)",
+                     "chain_fit_cycles": fits,
+                     "alu": {"achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                             "peak_source": "measured: the library's FP32 FMA microbenchmark (bmpc_selftest_fma)"},
+                     "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": (hbm_achieved / hbm_peak) if hbm_peak else None,
+                             "algorithmic_bytes_per_step": alg_bytes,
+                             "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"}},
         "e2e": {"value": total_conv / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
                 "converged_per_step": e2e_conv,
@@ -392,14 +492,56 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_single(args):
+    """Single-problem latency: each of the first P problems of the workload solved alone (a batch of
+    one, 512 threads per problem), timed with CUDA events over `steps` solves after `warmup`, against
+    the critical path of its depth and model (the chain floor)."""
+    import torch
+    from paper_2506_13624_b300 import bmpc
+    torch.cuda.set_device(0)
+    problems = workload(args.workload, args.single)
+    fits = chain_floor(bmpc, sorted({int(p["model"]) for p in problems}))
+    rows = []
+    for p in problems:
+        s = torch.cuda.Stream()
+        b = bmpc.Batch([p], stream=s)
+        b.set_problems()
+        o = bmpc.default_opts(block_threads=args.block_threads or 512, variant=args.variant)
+        for _ in range(args.warmup):
+            b.solve(o, graph=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            b.solve(o, graph=True)
+        e1.record(s)
+        e1.synchronize()
+        r = b.get_solutions(want_arrays=False)[0]
+        b.close()
+        ms = e0.elapsed_time(e1) / args.steps
+        it = max(1, r["inner_iters"])
+        c = r["cycles"]
+        per_cyc = (c["linearise"] + c["backward"] + c["forward"] + c["linesearch"]) / it
+        rows.append(dict(nodes=int(p["n"]), depth=depth(p), model=int(p["model"]), iters=r["inner_iters"],
+                         status=r["status"], ms=ms, us_per_iter=1e3 * ms / it,
+                         latency_frac=crit_cycles_per_iter(p, fits) / per_cyc,
+                         bwd_fwd_share=(c["backward"] + c["forward"]) / max(1, c["total"])))
+    out = {"workload": args.workload, "mode": "single problem per launch", "chain_fit_cycles": fits,
+           "mean_ms": float(np.mean([r["ms"] for r in rows])),
+           "mean_us_per_iter": float(np.mean([r["us_per_iter"] for r in rows])),
+           "mean_latency_frac": float(np.mean([r["latency_frac"] for r in rows])), "problems": rows}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "config4"])
-    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=["config1", "config2", "config3", "config4"])
+    ap.add_argument("--batch", type=int, default=DEFAULT_BATCH)
+    ap.add_argument("--single", type=int, default=0, metavar="P",
+                    help="single-problem latency of the first P problems of the workload (one per launch)")
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--ls-chunk", type=int, default=2)
@@ -417,6 +559,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.single:
+        run_single(args)
     else:
         run_gpu(args)
 

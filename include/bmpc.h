@@ -20,9 +20,10 @@
  * in (pinned memory gives asynchronous copies); with NULL the library uses
  * malloc.
  *
- * Streams.  Every device operation of a handle is issued on the stream given
- * at creation (a cudaStream_t passed as void*, NULL = legacy default stream).
- * bmpc_get_solutions synchronises that stream.  Handles are not thread safe.
+ * Streams.  Every device operation of a handle is issued on the handle's stream:
+ * the one given at creation (a cudaStream_t passed as void*, NULL = legacy default
+ * stream), or the one bmpc_set_stream set later.  bmpc_get_solutions synchronises
+ * that stream.  Handles are not thread safe.
  *
  * Errors.  Every function returns a bmpc_status; negative values are errors.
  * After BMPC_ERR_CUDA the handle should be destroyed.
@@ -103,7 +104,7 @@ typedef struct {
     float omega0, eta0;     /* 1, 0.1 */
     float a_omega, b_omega; /* 1, 1 */
     float a_eta, b_eta;     /* 0.1, 0.9 */
-    float rho0, rho_max;    /* 10, 100 (a failed outer step at rho_max updates y instead) */
+    float rho0, rho_max;    /* 10, 100 (see cap_rule) */
     float mu0;              /* 1 */
     float beta;             /* Armijo constant, 1e-4 */
     float ls_rel_eps;       /* Armijo slack relative to |phi(0)|, 1e-6 */
@@ -133,6 +134,14 @@ typedef struct {
                                32); 0 = block_threads.  Each model has its own launch, so a mixed
                                batch can run, e.g., its kinematic problems two per SM and its large
                                dynamic ones one per SM. Default 0. */
+    int32_t cap_rule;       /* what a failed outer step does (c > eta, Sec. IV-B):
+                               0 Algorithm 1: y kept, rho <- min(tau rho, rho_max);
+                               1 (default) the same below rho_max, but at rho_max the multiplier
+                               step y <- max(0, y + rho g) instead.  In FP32 the relaxed KKT residual
+                               holds rho * (rounding of g near the boundary, about 1e-7), so a large
+                               rho puts a floor near 1e-5 under it; the default caps rho at 100 and
+                               keeps the multipliers moving there.  With cap_rule 0 choose rho_max
+                               accordingly (the FP64 oracle's Algorithm-1 default is 1e6). */
 } bmpc_opts;
 
 typedef struct {
@@ -272,13 +281,48 @@ void bmpc_destroy_batch(bmpc_batch *b);
 int bmpc_create_batch_static(const bmpc_tree_desc *descs, int32_t n, void *dev_data, size_t data_bytes,
                              void *host_staging, size_t staging_bytes, void *stream, bmpc_batch **out);
 
-/* ---- single-tree interface of the paper's problem statement (a batch of one) ---- */
+/* Moves the handle to another stream (a cudaStream_t as void*, NULL = legacy default stream).
+ * Every later call of the handle issues its work there.  Work already issued on the old stream
+ * stays ordered before it: the new stream waits for an event recorded on the old one.  No
+ * synchronisation with the host.  A captured graph (bmpc_solve_batch_graph) stays valid and is
+ * launched on the new stream.  BMPC_ERR_INVALID on a null handle; BMPC_ERR_CUDA if the event
+ * cannot be recorded or waited for. */
+int bmpc_set_stream(bmpc_batch *b, void *stream);
+
+/* ---- single-tree interface of the paper's problem statement (a batch of one) ----
+ * The paper states one branch-MPC problem (Sec. II-B, Eq. bmpc): a scenario tree given by every
+ * node's parent (tree notation of Sec. II-B), the measured state x-bar fixed at the root, node
+ * costs l_i / l_f,i, dynamics x_i = f_p(i)(x_p(i), u_p(i)) and constraints g_i <= 0 per node, and
+ * the initialisation of Sec. V-B.  These calls hold exactly one such problem; they are the batch
+ * calls above with n = 1 (same arguments, layouts, ownership and errors). */
 typedef bmpc_batch bmpc_tree;
+
+/* Device and host bytes for one tree (Sec. II-B tree notation); as bmpc_batch_bytes with n = 1. */
 int bmpc_tree_bytes(const bmpc_tree_desc *desc, size_t *data_bytes, size_t *scratch_bytes, size_t *staging_bytes);
+
+/* The tree of Eq. (bmpc): desc->parent gives p(i) for every node in level order (Sec. II-B), with
+ * the dynamics model f_i and the constraint families.  Caller-owned arenas as for
+ * bmpc_create_batch; validates the tree (BMPC_ERR_INVALID), BMPC_ERR_SPACE on short arenas. */
 int bmpc_create_tree(const bmpc_tree_desc *desc, void *dev_data, size_t data_bytes, void *dev_scratch,
                      size_t scratch_bytes, void *host_staging, size_t staging_bytes, void *stream, bmpc_tree **out);
+
+/* The data of Eq. (bmpc) for the tree: x-bar (x_0 = x0), the stage and terminal costs l_i, l_f,i
+ * (tracking references and weights), the constraint data of g_i, and an optional warm start; NULL
+ * warm arrays give the cold start of Sec. V-B.  Host pointers, copied (bmpc_set_problems, n = 1). */
 int bmpc_set_problem(bmpc_tree *t, const bmpc_problem *problem);
+
+/* Solves the problem by the AL method of Algorithm 1 (Sec. IV): inner iLQR iterations on the
+ * relaxed problem Eq. (relax_bmpc), each one linearisation, tree Riccati recursion
+ * (Eq. tree_Riccati, Eq. tree_feedback_laws), linear rollout, merit line search (Eq. merit,
+ * Eq. sufficient_decrease), and the BCL update of y_e and rho (Sec. IV-B).  opts NULL = defaults.
+ * With stats != NULL it synchronises the stream, fills *stats and returns the problem's status
+ * (BMPC_OK, BMPC_MAX_ITER, BMPC_LS_FAIL or BMPC_ERR_NUMERIC); otherwise it is asynchronous. */
 int bmpc_solve(bmpc_tree *t, const bmpc_opts *opts, bmpc_stats *stats /* nullable; synchronises if given */);
+
+/* The solution of Eq. (bmpc) (Algorithm 1's return value x, u, y_e, plus the dynamics multipliers
+ * lambda of the Lagrangian of Sec. IV-A): host arrays, node-major x [n][nx] (absolute states),
+ * u [n][nu] (zero rows at leaves), lam [n][nx] (root row zero), y [n][nc]; any may be NULL.
+ * Synchronises the stream. */
 int bmpc_get_solution(bmpc_tree *t, float *x, float *u, float *lam, float *y);
 void bmpc_destroy_tree(bmpc_tree *t);
 
@@ -291,6 +335,14 @@ const char *bmpc_version(void);
  * are device arrays of n floats; asynchronous on `stream`.  BMPC_ERR_INVALID on n < 0 or null
  * arrays, BMPC_ERR_CUDA if the launch fails. */
 int bmpc_selftest_sincos(const float *a, float *s, float *c, int32_t n, void *stream);
+
+/* Measurement support (no counterpart in the paper): the FP32 FMA peak of the device, against which
+ * the solver's arithmetic rate is reported.  Launches `blocks` blocks of 256 threads; every thread
+ * runs eight independent FMA chains of `iters` rounds and writes one float to out[thread] (out: a
+ * device array of blocks * 256 floats).  The kernel performs 2 * 8 * iters * 256 * blocks FLOPs;
+ * the caller times it (CUDA events on `stream`).  Asynchronous.  BMPC_ERR_INVALID on a null array or
+ * a count below 1, BMPC_ERR_CUDA if the launch fails. */
+int bmpc_selftest_fma(float *out, int32_t blocks, int32_t iters, void *stream);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,16 @@ class Opts(C.Structure):
                 ("eta0", C.c_double), ("a_omega", C.c_double), ("b_omega", C.c_double),
                 ("a_eta", C.c_double), ("b_eta", C.c_double), ("rho0", C.c_double),
                 ("rho_max", C.c_double), ("mu0", C.c_double), ("beta", C.c_double),
-                ("ls_rel_eps", C.c_double), ("lqr_scan", C.c_int)]
+                ("ls_rel_eps", C.c_double), ("lqr_scan", C.c_int), ("cap_rule", C.c_int),
+                ("trace", C.c_void_p), ("trace_user", C.c_void_p)]
+
+
+# The rule of the FP32 product at a failed outer step (both sides implement it): the penalty is
+# capped at rho_max = 100, and a failure at the cap applies the multiplier step y <- max(0, y + rho g)
+# instead of keeping y.  The oracle's default is Algorithm 1 (y kept, rho <- tau rho up to 1e6).
+PRODUCT_RULE = dict(cap_rule=1, rho_max=100.0)
+
+TRACE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.POINTER(C.c_double), *([C.POINTER(C.c_double)] * 7))
 
 
 class Stats(C.Structure):
@@ -103,13 +112,31 @@ def default_opts(**kw) -> Opts:
     return o
 
 
-def solve(p, opts: Opts | None = None, warm=None, **kw):
-    """Run the AL method (Algorithm 1) to convergence; returns x, u, lam, y and stats."""
+def solve(p, opts: Opts | None = None, warm=None, trace: list | None = None, **kw):
+    """Run the AL method (Algorithm 1) to convergence; returns x, u, lam, y and stats.
+
+    With ``trace`` (a list) every inner iteration appends ("inner", info, x, u, lam, y, dx, du, dlam)
+    and every outer update ("outer", info, x, u, lam, y_before, y_after), as copies; the info fields
+    are listed at ``orc_trace_fn`` in bmpc_oracle.c."""
     m = _Marshal(p)
     n, nx, nu, nc = p["n"], p["nx"], p["nu"], n_con(p)
     x, u, lam, y = (np.zeros((n, nx)), np.zeros((n, nu)), np.zeros((n, nx)), np.zeros((n, max(nc, 1))))
     st = Stats()
     o = opts if opts is not None else default_opts(**kw)
+    if trace is not None:
+        shapes = [(n, nx), (n, nu), (n, nx), (n, max(nc, 1)), (n, nx), (n, nu), (n, nx)]
+
+        def _cb(_user, kind, info, *arrs):
+            k = 16 if kind == 0 else 10
+            rec = ["inner" if kind == 0 else "outer", np.ctypeslib.as_array(info, (k,)).copy()]
+            shp = shapes if kind == 0 else shapes[:4] + [shapes[3]]
+            for a, sh in zip(arrs, shp):
+                rec.append(np.ctypeslib.as_array(a, sh).copy()[:, :nc] if sh == shapes[3]
+                           else np.ctypeslib.as_array(a, sh).copy())
+            trace.append(tuple(rec))
+
+        cb = TRACE_FN(_cb)
+        o.trace = C.cast(cb, C.c_void_p)
     if warm is not None:
         w = [_d(a) for a in warm]
         if nc == 0:

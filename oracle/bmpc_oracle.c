@@ -25,9 +25,11 @@
  *   - multiplier update y <- max(0, y + rho g) (standard PHR, Algorithm 1 drops y);
  *   - tolerance schedules omega <- omega rho^-b_omega, eta <- eta rho^-b_eta on success,
  *     omega <- omega0 rho^-a_omega, eta <- eta0 rho^-a_eta on failure, both floored at eps_tol;
- *   - rho is capped at rho_max; a failed outer step at the cap applies the multiplier update
- *     y <- max(0, y + rho g) instead of raising rho (the cap keeps rho * FP32 rounding of g
- *     below the tolerance on the GPU);
+ *   - a failed outer step keeps y and raises rho <- min(tau rho, rho_max) (Algorithm 1; the paper
+ *     gives no cap, rho_max = 1e6 by default).  Option cap_rule = 1 is the FP32 product's rule
+ *     instead: at rho = rho_max a failed outer step applies the multiplier update
+ *     y <- max(0, y + rho g) (rho * FP32 rounding of g puts a floor under the KKT residual, so the
+ *     GPU caps rho low, at 100); both sides implement both rules;
  *   - the merit uses J = L_a and moves (x, u, lambda) jointly; lambda_QP = P dx + p;
  *   - mu rule: phi'(0; mu) <= -1/2 dz'W dz, else mu <- max(mu, 2(phi'(0;0) + 1/2 dz'W dz)/|d|^2);
  *   - alpha_i = 2^-i; Armijo with an absolute slack ls_rel_eps*|phi(0)| for finite precision;
@@ -64,11 +66,28 @@ typedef struct {
     const double *Alin, *Blin;
 } orc_problem;
 
+/* Trace of a solve, for tests that check each decision of Algorithm 1 from outside.  kind 0 (one
+ * call per inner iteration, after the line search and before the step is applied):
+ *   info = [inner, outer, rho, mu before the update, mu, phi(0), phi'(0; mu), phi'(0; 0), dz'W dz,
+ *           |d|^2, alpha, accepted, phi(alpha) (its merit), accepted only through the slack, r_kkt,
+ *           omega], a0..a6 = x, u, lam, y, dx, du, dlam;
+ * kind 1 (one call per outer update):
+ *   info = [outer, branch (0 y updated, 1 rho raised and y kept, 2 multiplier step at the cap
+ *           (cap_rule 1), 3 y kept at the cap), c, eta before, rho before, rho after, omega after,
+ *           eta after, r_kkt, converged], a0..a4 = x, u, lam, y before, y after (a5, a6 NULL). */
+typedef void (*orc_trace_fn)(void *user, int kind, const double *info, const double *a0, const double *a1,
+                             const double *a2, const double *a3, const double *a4, const double *a5,
+                             const double *a6);
+
 typedef struct {
     int max_iters, max_outer, n_alpha;
     double eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta;
     double rho0, rho_max, mu0, beta, ls_rel_eps;
     int lqr_scan;           /* 1: the search direction by the scans of Sec. III-B (orc_tree_lqr_scan) */
+    int cap_rule;           /* 0: Algorithm 1 (failure keeps y, rho <- min(tau rho, rho_max));
+                               1: a failure at rho_max applies y <- max(0, y + rho g) */
+    orc_trace_fn trace;     /* NULL: no trace */
+    void *trace_user;
 } orc_opts;
 
 typedef struct {
@@ -1022,11 +1041,14 @@ void orc_default_opts(orc_opts *o) {
     o->a_eta = 0.1;
     o->b_eta = 0.9;
     o->rho0 = 10.0;
-    o->rho_max = 100.0;
+    o->rho_max = 1e6;
     o->mu0 = 1.0;
     o->beta = 1e-4;
     o->ls_rel_eps = 1e-6;
     o->lqr_scan = 0;
+    o->cap_rule = 0;
+    o->trace = NULL;
+    o->trace_user = NULL;
 }
 
 /* Directional data of one inner iteration at (x, u, lam) for fixed (y, rho, mu), with W
@@ -1100,6 +1122,7 @@ int orc_solve(const orc_problem *P, const orc_opts *O_in, const double *wx, cons
     double *xt = (double *)calloc((size_t)n * nx, sizeof(double));
     double *ut = (double *)calloc((size_t)n * nu, sizeof(double));
     double *lt = (double *)calloc((size_t)n * nx, sizeof(double));
+    double *ybefore = (double *)calloc((size_t)n * (nc ? nc : 1), sizeof(double));
 
     while (outer < O.max_outer) {
         ++outer;
@@ -1113,6 +1136,7 @@ int orc_solve(const orc_problem *P, const orc_opts *O_in, const double *wx, cons
             int st = direction(P, &W, x, u, lam, y, rho, mu, O.lqr_scan, dlam, info);
             if (st) { status = st; goto done; }
             double wq = info[2], dd = info[3], dphi0 = info[4];
+            const double mu_prev = mu;
             /* adaptive merit penalty (Gill et al. 1992 reading) */
             if (dd > 0.0 && dphi0 - mu * dd > -0.5 * wq) {
                 double need = 2.0 * (dphi0 + 0.5 * wq) / dd;
@@ -1121,16 +1145,24 @@ int orc_solve(const orc_problem *P, const orc_opts *O_in, const double *wx, cons
             double phi0 = merit_at(P, &W.T, nc, x, u, lam, y, rho, mu);
             double dphi = dphi0 - mu * dd;
             /* all step sizes alpha_i = 2^-i, take the largest satisfying Eq. (sufficient_decrease) */
-            double alpha = ldexp(1.0, -(O.n_alpha - 1));
+            double alpha = ldexp(1.0, -(O.n_alpha - 1)), phi_alpha = NAN;
             int accepted = 0;
             for (int a = 0; a < O.n_alpha; ++a) {
                 double al = ldexp(1.0, -a);
                 for (int e = 0; e < n * nx; ++e) { xt[e] = x[e] + al * W.dx[e]; lt[e] = lam[e] + al * dlam[e]; }
                 for (int e = 0; e < n * nu; ++e) ut[e] = u[e] + al * W.du[e];
                 double phi = merit_at(P, &W.T, nc, xt, ut, lt, y, rho, mu);
+                phi_alpha = phi;
                 if (phi <= phi0 + O.beta * al * dphi + O.ls_rel_eps * fabs(phi0)) { alpha = al; accepted = 1; break; }
             }
             if (accepted) ls_fail = 0; else { ++ls_fail; ++ls_fail_total; }
+            if (O.trace) {
+                const double tinfo[16] = {(double)inner, (double)outer, rho, mu_prev, mu, phi0, dphi, dphi0, wq, dd,
+                                          alpha, (double)accepted, phi_alpha,
+                                          (double)(accepted && phi_alpha > phi0 + O.beta * alpha * dphi),
+                                          r_kkt, omega};
+                O.trace(O.trace_user, 0, tinfo, x, u, lam, y, W.dx, W.du, dlam);
+            }
             for (int e = 0; e < n * nx; ++e) { x[e] += alpha * W.dx[e]; lam[e] += alpha * dlam[e]; }
             for (int e = 0; e < n * nu; ++e) u[e] += alpha * W.du[e];
             ++inner;
@@ -1143,32 +1175,51 @@ int orc_solve(const orc_problem *P, const orc_opts *O_in, const double *wx, cons
             double v = W.g[e] > -y[e] / rho ? W.g[e] : -y[e] / rho;
             if (fabs(v) > cviol) cviol = fabs(v);
         }
+        const double eta_before = eta, rho_before = rho;
+        int branch, converged = 0;
+        if (nc) memcpy(ybefore, y, sizeof(double) * n * nc);
         if (cviol <= eta) {
+            /* success: multiplier update, rho kept */
+            branch = 0;
             for (int e = 0; e < n * nc; ++e) {
                 if (!W.ex[e]) continue;
                 double v = y[e] + rho * W.g[e];
                 y[e] = v > 0.0 ? v : 0.0;
             }
-            if ((r_kkt > cviol ? r_kkt : cviol) < O.eps_tol) { status = ORC_OK; goto done; }
-            omega = omega * pow(rho, -O.b_omega);
-            eta = eta * pow(rho, -O.b_eta);
-        } else {
-            if (rho < O.rho_max) {
-                rho = O.tau * rho;
-                if (rho > O.rho_max) rho = O.rho_max;
+            if ((r_kkt > cviol ? r_kkt : cviol) < O.eps_tol) {
+                converged = 1;
             } else {
-                /* penalty at its cap: first-order multiplier step instead of a larger rho */
+                omega = omega * pow(rho, -O.b_omega);
+                eta = eta * pow(rho, -O.b_eta);
+            }
+        } else {
+            if (O.cap_rule == 1 && rho >= O.rho_max) {
+                /* product rule at the cap: first-order multiplier step instead of a larger rho */
+                branch = 2;
                 for (int e = 0; e < n * nc; ++e) {
                     if (!W.ex[e]) continue;
                     double v = y[e] + rho * W.g[e];
                     y[e] = v > 0.0 ? v : 0.0;
                 }
+            } else {
+                /* Algorithm 1: y kept, rho <- tau rho (held at rho_max) */
+                branch = rho >= O.rho_max ? 3 : 1;
+                rho = O.tau * rho;
+                if (rho > O.rho_max) rho = O.rho_max;
             }
             omega = O.omega0 * pow(rho, -O.a_omega);
             eta = O.eta0 * pow(rho, -O.a_eta);
         }
-        if (omega < O.eps_tol) omega = O.eps_tol;
-        if (eta < O.eps_tol) eta = O.eps_tol;
+        if (!converged) {
+            if (omega < O.eps_tol) omega = O.eps_tol;
+            if (eta < O.eps_tol) eta = O.eps_tol;
+        }
+        if (O.trace) {
+            const double tinfo[10] = {(double)outer, (double)branch, cviol, eta_before, rho_before, rho, omega, eta,
+                                      r_kkt, (double)converged};
+            O.trace(O.trace_user, 1, tinfo, x, u, lam, ybefore, y, NULL, NULL);
+        }
+        if (converged) { status = ORC_OK; goto done; }
     }
 done:
     if (S) {
@@ -1183,7 +1234,7 @@ done:
         S->omega = omega;
         S->eta = eta;
     }
-    free(dlam); free(xt); free(ut); free(lt);
+    free(dlam); free(xt); free(ut); free(lt); free(ybefore);
     work_free(&W);
     return status;
 }

@@ -46,7 +46,7 @@ class Opts(C.Structure):
                 ("ls_rel_eps", C.c_float), ("ls_chunk", C.c_int32), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("variant", C.c_int32), ("warm_select", C.c_int32),
                 ("select_mu", C.c_float), ("select_rho", C.c_float), ("queue_order", C.c_int32),
-                ("block_threads_model", C.c_int32 * 3)]
+                ("block_threads_model", C.c_int32 * 3), ("cap_rule", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -97,6 +97,8 @@ def lib() -> C.CDLL:
         L.bmpc_selftest_sincos.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
         L.bmpc_get_solutions_flat_async.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.bmpc_wait_solutions.argtypes = [C.c_void_p, C.POINTER(Stats)]
+        L.bmpc_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+        L.bmpc_selftest_fma.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
         _lib = L
     return _lib
 
@@ -107,7 +109,7 @@ EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_
             "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune",
             "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order", "bmpc_transfer_bytes",
             "bmpc_set_problems_flat", "bmpc_get_solutions_flat", "bmpc_transfer_bytes_flat", "bmpc_selftest_sincos",
-            "bmpc_get_solutions_flat_async", "bmpc_wait_solutions"]
+            "bmpc_get_solutions_flat_async", "bmpc_wait_solutions", "bmpc_set_stream", "bmpc_selftest_fma"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -121,6 +123,26 @@ def selftest_sincos(a):
         _check(lib().bmpc_selftest_sincos(a.data_ptr(), s.data_ptr(), c.data_ptr(), a.numel(),
                                           torch.cuda.current_stream(a.device).cuda_stream), "bmpc_selftest_sincos")
     return s, c
+
+
+def fp32_peak_tflops(reps: int = 5) -> float:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s): the library's FMA kernel over
+    8 blocks of 256 threads per SM, timed with CUDA events on the current stream, best of `reps`."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, iters = 8 * sms, 50000
+    out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    best = 0.0
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _check(lib().bmpc_selftest_fma(out.data_ptr(), blocks, iters, C.c_void_p(s.cuda_stream)), "bmpc_selftest_fma")
+        e1.record(s)
+        e1.synchronize()
+        if r:
+            best = max(best, 2.0 * 8 * iters * 256 * blocks / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
 
 
 def status_str(s: int) -> str:
@@ -320,6 +342,12 @@ class Batch:
         h, d = C.c_size_t(), C.c_size_t()
         _check(lib().bmpc_transfer_bytes_flat(self.handle, C.byref(h), C.byref(d)), "bmpc_transfer_bytes_flat")
         return h.value, d.value
+
+    def set_stream(self, stream):
+        """Issue the batch's later work on `stream` (a torch.cuda.Stream), ordered after the old one."""
+        with self.torch.cuda.device(self.device):
+            _check(lib().bmpc_set_stream(self.handle, C.c_void_p(stream.cuda_stream)), "bmpc_set_stream")
+        self.stream = stream
 
     def solve(self, opts: Opts | None = None, graph: bool = False):
         """Launch the persistent solver (asynchronous on the batch's stream)."""

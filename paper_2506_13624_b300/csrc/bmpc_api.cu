@@ -28,6 +28,7 @@ cudaError_t prepare_solve(int model, size_t smem);
 cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order, int cnt, cudaStream_t stream);
 cudaError_t launch_flat(int which, const FlatArgs &a, int n_problems, cudaStream_t stream);
 cudaError_t launch_sincos(const float *a, float *sn, float *cs, int n, cudaStream_t stream);
+cudaError_t launch_fma(float *out, int blocks, int iters, cudaStream_t stream);
 int max_block_threads();
 cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
@@ -111,6 +112,7 @@ struct bmpc_batch {
     cudaStream_t stream = nullptr;
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   /* per-model streams of mixed batches */
     cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t handoff = nullptr;       /* orders a new stream after the old one (bmpc_set_stream) */
     int sm_count = 148;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -220,6 +222,7 @@ KOpts to_kopts(const bmpc_opts &o) {
     k.ls_chunk = o.ls_chunk;
     k.variant = o.variant;
     k.warm_select = o.warm_select;
+    k.cap_rule = o.cap_rule;
     k.eps_tol = o.eps_tol;
     k.tau = o.tau;
     k.omega0 = o.omega0;
@@ -250,6 +253,7 @@ int check_opts(const bmpc_opts &o) {
     if (o.warm_select < 0 || o.warm_select > 1 || !(o.select_mu >= 0.f) ||
         !(o.select_rho > 0.f)) return BMPC_ERR_INVALID;
     if (o.queue_order < 0 || o.queue_order > 1) return BMPC_ERR_INVALID;
+    if (o.cap_rule < 0 || o.cap_rule > 1) return BMPC_ERR_INVALID;
     for (int m = 0; m < 3; ++m) {
         const int bt = o.block_threads_model[m];
         if (bt != 0 && (bt < 32 || bt > max_block_threads() || bt % 32)) return BMPC_ERR_INVALID;
@@ -410,6 +414,7 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->select_rho = 1e4f;
     o->queue_order = 1;
     for (int m = 0; m < 3; ++m) o->block_threads_model[m] = 0;
+    o->cap_rule = 1;
 }
 
 int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
@@ -493,6 +498,10 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
             bmpc_destroy_batch(b);
             return BMPC_ERR_CUDA;
         }
+    }
+    if (cudaEventCreateWithFlags(&b->handoff, cudaEventDisableTiming) != cudaSuccess) {
+        bmpc_destroy_batch(b);
+        return BMPC_ERR_CUDA;
     }
     int models = 0;
     for (int m = 0; m < 3; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
@@ -1085,8 +1094,20 @@ void bmpc_destroy_batch(bmpc_batch *b) {
         if (b->join[m]) cudaEventDestroy(b->join[m]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->handoff) cudaEventDestroy(b->handoff);
     if (b->own_stage) std::free(b->stage);
     delete b;
+}
+
+int bmpc_set_stream(bmpc_batch *b, void *stream) {
+    if (!b) return BMPC_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (s == b->stream) return BMPC_OK;
+    /* the new stream waits for everything already issued on the old one */
+    if (cudaEventRecord(b->handoff, b->stream) != cudaSuccess || cudaStreamWaitEvent(s, b->handoff, 0) != cudaSuccess)
+        return BMPC_ERR_CUDA;
+    b->stream = s;
+    return BMPC_OK;
 }
 
 int bmpc_tree_bytes(const bmpc_tree_desc *desc, size_t *data_bytes, size_t *scratch_bytes, size_t *staging_bytes) {
@@ -1134,6 +1155,12 @@ int bmpc_selftest_sincos(const float *a, float *s, float *c, int32_t n, void *st
     if (n < 0 || (n > 0 && (!a || !s || !c))) return BMPC_ERR_INVALID;
     return bmpc::launch_sincos(a, s, c, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? BMPC_OK
                                                                                             : BMPC_ERR_CUDA;
+}
+
+int bmpc_selftest_fma(float *out, int32_t blocks, int32_t iters, void *stream) {
+    if (!out || blocks < 1 || iters < 1) return BMPC_ERR_INVALID;
+    return bmpc::launch_fma(out, blocks, iters, static_cast<cudaStream_t>(stream)) == cudaSuccess ? BMPC_OK
+                                                                                                 : BMPC_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -1942,10 +1942,11 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                 omega = omega * powf(rho, -O.b_omega);
                 eta = eta * powf(rho, -O.b_eta);
             } else {
-                if (rho < O.rho_max) {
+                if (!(O.cap_rule == 1 && rho >= O.rho_max)) {
+                    /* Algorithm 1: y kept, rho <- tau rho (held at rho_max) */
                     rho = fminf(O.tau * rho, O.rho_max);
                 } else {
-                    /* penalty at its cap: first-order multiplier step instead of a larger rho */
+                    /* cap rule: at rho_max a first-order multiplier step instead of a larger rho */
                     for (int i = tid; i < n; i += nt) {
                         const bool is_leaf = V.nchild[i] == 0;
                         float x[NX], u[NU];
@@ -2067,6 +2068,28 @@ cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order
 }
 
 /* Device sin/cos of the dynamics on n angles (self-test of sincos_cw against its error bound). */
+/* FP32 peak microbenchmark: every thread runs eight independent FMA chains (enough independent
+ * instructions to cover the FMA latency at full occupancy), iters rounds each, and stores the sum so
+ * that nothing is dead code.  FLOPs = 2 * 8 * iters * threads. */
+__global__ void __launch_bounds__(256) bmpc_fma_kernel(float *out, int iters, float b, float c) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 1e-3f * threadIdx.x + (float)k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], b, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fma(float *out, int blocks, int iters, cudaStream_t stream) {
+    bmpc_fma_kernel<<<blocks, 256, 0, stream>>>(out, iters, 0.999999f, 1e-7f);
+    return cudaGetLastError();
+}
+
 __global__ void bmpc_sincos_kernel(const float *a, float *sn, float *cs, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) sincos_cw(a[i], sn + i, cs + i);
 }

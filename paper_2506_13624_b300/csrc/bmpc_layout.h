@@ -152,7 +152,7 @@ __host__ __device__ inline ScrRows scr_rows(int nx) {
 
 /* Kernel-side copy of the solver options (Algorithm 1 constants). */
 struct KOpts {
-    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant, warm_select;
+    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant, warm_select, cap_rule;
     float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps, select_mu,
         select_rho;
 };

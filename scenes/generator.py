@@ -295,6 +295,18 @@ def config4(seed: int = 4, count: int = 4096):
     return [config4_problem(seed, i) for i in range(count)]
 
 
+def chain_problem(seed: int, model: int, N: int, n_obs: int = 3):
+    """A single-path tree (one scenario, N + 1 nodes) of the mixed-batch family: the given model,
+    horizon and obstacle count.  Its iterations run the sweeps' dependent chain with no branching,
+    which measures the per-stage latency of the sweeps."""
+    rng = np.random.default_rng([8, seed, model, N])
+    p = _base(model, N, {})
+    vr = (0.0, 10.0) if model == MODEL_KINEMATIC else (2.0, 10.0)
+    p["x0"] = f32(_x0(rng, model, 1.5, math.pi / 12, vr))
+    p["xref"] = _reference(p["x0"], p["stage"], p["nx"], p["dt"])
+    return _finish(_multi_obstacle(rng, p, n_obs, min(n_obs, 2)))
+
+
 def linear_problem(seed: int, N: int = 10, splits=None, nx: int = 4, nu: int = 2,
                    constrained: bool = False):
     """Linear dynamics x+ = A x + B u with quadratic cost (the LQ special case)."""

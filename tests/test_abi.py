@@ -98,13 +98,32 @@ def test_invalid_trees_rejected_on_host(mutate):
 
 
 def test_default_opts_match_the_oracle_constants():
+    """The library's defaults are the oracle's constants with the product's cap rule
+    (oracle.PRODUCT_RULE); the oracle's own default is Algorithm 1's failure branch."""
     import oracle
-    o, r = bmpc.default_opts(), oracle.default_opts()
-    for f in ("max_iters", "max_outer", "n_alpha"):
+    o, r = bmpc.default_opts(), oracle.default_opts(**oracle.PRODUCT_RULE)
+    for f in ("max_iters", "max_outer", "n_alpha", "cap_rule"):
         assert getattr(o, f) == getattr(r, f)
     for f in ("eps_tol", "tau", "omega0", "eta0", "a_omega", "b_omega", "a_eta", "b_eta", "rho0", "rho_max",
               "mu0", "beta", "ls_rel_eps"):
         assert np.float32(getattr(o, f)) == np.float32(getattr(r, f)), f
+    paper = oracle.default_opts()
+    assert paper.cap_rule == 0 and paper.rho_max == 1e6
+
+
+def test_single_tree_calls_cite_the_problem_statement():
+    """Each call of the single-tree interface carries, in the comment right above its declaration,
+    the passage of the paper that defines what it does."""
+    src = open(os.path.join(ROOT, "include", "bmpc.h")).read()
+    for name in ("bmpc_create_tree", "bmpc_set_problem", "bmpc_solve", "bmpc_get_solution"):
+        m = re.search(r"/\*((?:(?!\*/).)*)\*/\s*int\s+" + name + r"\(", src, flags=re.S)
+        assert m, name
+        assert re.search(r"(Eq\.|Sec\.|Algorithm) ", m.group(1)), name
+
+
+def test_set_stream_rejects_a_null_handle():
+    assert bmpc.lib().bmpc_set_stream(None, None) == bmpc.ERR_INVALID
+
 
 
 def test_async_read_and_wait_reject_null_handles():
@@ -131,9 +150,9 @@ def test_default_options_match_their_documentation():
     assert o.eps_tol == np.float32(1e-5) and o.tau == 100.0
     assert (o.omega0, o.a_omega, o.b_omega, o.a_eta) == (1.0, 1.0, 1.0, np.float32(0.1))
     assert o.eta0 == np.float32(0.1) and o.b_eta == np.float32(0.9)
-    assert (o.rho0, o.rho_max, o.mu0) == (10.0, 100.0, 1.0)
+    assert (o.rho0, o.rho_max, o.mu0, o.cap_rule) == (10.0, 100.0, 1.0, 1)
     assert o.beta == np.float32(1e-4) and o.ls_rel_eps == np.float32(1e-6)
     assert (o.block_threads, o.blocks_per_sm, o.variant, o.warm_select, o.queue_order) == (0, 0, 0, 0, 1)
     assert list(o.block_threads_model) == [0, 0, 0]
     assert o.select_mu == 100.0 and o.select_rho == 1e4
-    assert C.sizeof(bmpc.Opts) == 27 * 4   # 27 four-byte fields, as in bmpc_opts
+    assert C.sizeof(bmpc.Opts) == 28 * 4   # 28 four-byte fields, as in bmpc_opts

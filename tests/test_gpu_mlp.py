@@ -1,6 +1,17 @@
 """Learned warm start on the GPU: tensor-core GEMMs, forward, back-propagation and AdamW against
 the FP64 CPU reference (oracle/mlp_ref.py) on the same bf16-rounded weights and inputs, and the
-glue between BMPC batches and the network."""
+glue between BMPC batches and the network.
+
+Element-wise bars.  A GEMM sums K products in FP32: against the FP64 sum of the same bf16 operands
+its error is at most about K u (|A| |B|)_ij with u = 2^-24 (the bound of recursive summation; the
+tensor core's order is another order of the same sums), so every entry is checked against
+ACC * K u (|A| |B|)_ij.  A bf16 result (pre-activation, activation, back-propagated gradient) is
+bf16(v) of an FP32 value v that is within that bound of the FP64 one: it equals the reference's
+bf16 rounding except where v lies that close to a rounding boundary, and then differs by one bf16
+ulp.  Those checks compare layer by layer, each layer fed the GPU's own inputs (its bf16
+activations and gradients), so that a rounding flip in one layer does not blur the next layer's
+bar.  The end-to-end forward pass is also compared against the reference run from the input alone,
+by relative Frobenius norm (flips do propagate there)."""
 import numpy as np
 import pytest
 
@@ -19,6 +30,35 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+U32 = 2.0 ** -24          # FP32 unit roundoff
+ACC = 4.0                 # slack factor on the K u accumulation bound
+
+
+def _acc_bound(A, B, K):
+    """ACC K u (|A| |B|): the FP32 accumulation bound of every entry of A @ B."""
+    return ACC * K * U32 * (np.abs(A) @ np.abs(B))
+
+
+def _f64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def _bf_ulp(v):
+    """One bf16 ulp at |v| (8 significant bits)."""
+    e = np.floor(np.log2(np.maximum(np.abs(v), 2.0 ** -126)))
+    return 2.0 ** (e - 7)
+
+
+def _assert_bf16_matches(got, ref_exact, name, max_flip_frac=2e-3):
+    """got = bf16 of an FP32 value close to ref_exact: equal to bf16(ref_exact) except for one-ulp
+    rounding flips, which must be rare."""
+    want = mlp_ref.bf16(ref_exact)
+    diff = np.abs(got - want)
+    assert (diff <= _bf_ulp(ref_exact) * 1.0001 + 1e-30).all(), (name, float(diff.max()))
+    flips = np.count_nonzero(diff)
+    assert flips <= max(2, max_flip_frac * got.size), (name, flips, got.size)
+
+
 @pytest.mark.parametrize("K", [192, 1024])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 def test_gemm_variants_match_fp64(ta, tb, K):
@@ -30,7 +70,9 @@ def test_gemm_variants_match_fp64(ta, tb, K):
     B = mlp_ref.bf16(rng.standard_normal((N, K) if tb else (K, N)))
     C = mlp.gemm(_bf(A), _bf(B), ta, tb).cpu().numpy()
     mlp.status()
-    ref = (A.T if ta else A) @ (B.T if tb else B)
+    opA, opB = (A.T if ta else A), (B.T if tb else B)
+    ref = opA @ opB
+    assert (np.abs(C - ref) <= _acc_bound(opA, opB, K)).all()
     assert _rel(C, ref) < 1e-5
 
 
@@ -45,13 +87,32 @@ def _net_and_ref(dims, seed=0):
     return net, Ws, bs
 
 
+def _layerwise_forward(net, Ws, bs, x, pred):
+    """Every layer of the GPU forward pass element by element, fed the GPU's own inputs."""
+    w, keep, _, _ = net.work(x.shape[0])
+    hidden = len(Ws) - 1
+    h = x
+    for l in range(len(Ws)):
+        z = h @ Ws[l] + bs[l]
+        bound = _acc_bound(h, Ws[l], h.shape[1]) + 4 * U32 * np.abs(bs[l])
+        if l < hidden:
+            pre, act = _f64(keep[2 * l]), _f64(keep[2 * l + 1])
+            _assert_bf16_matches(pre, z, f"pre{l}")
+            assert (np.abs(pre - z) <= _bf_ulp(z) + bound).all()
+            _assert_bf16_matches(act, mlp_ref.gelu(pre), f"act{l}")
+            h = act
+        else:
+            assert (np.abs(pred - z) <= bound).all(), float(np.max(np.abs(pred - z) - bound))
+
+
 def test_forward_matches_reference():
     from paper_2506_13624_b300 import mlp
     dims = [256, 128, 128, 384]
     net, Ws, bs = _net_and_ref(dims)
     x = mlp_ref.bf16(np.random.default_rng(1).standard_normal((128, dims[0])))
-    pred = net.forward(_bf(x)).cpu().numpy()
+    pred = net.forward(_bf(x)).cpu().numpy().astype(np.float64)
     mlp.status()
+    _layerwise_forward(net, Ws, bs, x, pred)
     ref, _ = mlp_ref.forward(Ws, bs, x, bf=True)
     assert _rel(pred, ref) < 5e-3
 
@@ -68,12 +129,53 @@ def test_training_step_gradients_and_adamw_match_reference():
     mlp.status()
     rl, dWs, dbs = mlp_ref.loss_and_grads(Ws, bs, x, t, bf=True)
     assert abs(loss - rl) < 1e-3 * rl
+    _layerwise_backward(net, Ws, x, t)
     for l, p in enumerate(net.params):
         assert _rel(p["dw"].cpu().numpy(), dWs[l]) < 2e-2, l
         assert _rel(p["db"].cpu().numpy(), dbs[l]) < 2e-2, l
         g = p["dw"].cpu().numpy().astype(np.float64)
         w_ref, _, _ = mlp_ref.adamw(w_before[l], 0.0, 0.0, g, 1, 1e-3, 1e-2)
-        assert _rel(p["w"].cpu().numpy(), w_ref) < 1e-6
+        np.testing.assert_allclose(p["w"].cpu().numpy(), w_ref, rtol=1e-6, atol=1e-7)
+
+
+def _layerwise_backward(net, Ws, x, t):
+    """The back-propagation of a training step element by element, three layers (the work buffers
+    then hold g_1 and g_0, the gradients at the two hidden layers): the output gradient from the
+    GPU's own prediction, each hidden gradient from the GPU's own upper gradient and
+    pre-activation, and every dW, db from the GPU's own activations and gradients."""
+    assert len(Ws) == 3
+    B = x.shape[0]
+    w, keep, pred, _ = net.work(B)
+    pre = [_f64(keep[0]), _f64(keep[2])]
+    act = [_f64(keep[1]), _f64(keep[3])]
+    # dy0, dy1 hold contiguous [B][width] gradients: g_0 in dy0, g_1 in dy1 after the step
+    h0, h1 = Ws[0].shape[1], Ws[1].shape[1]
+    g0 = _f64(keep[-5]).reshape(-1)[:B * h0].reshape(B, h0)
+    g1 = _f64(keep[-4]).reshape(-1)[:B * h1].reshape(B, h1)
+    P = _f64(pred)
+    e = P - t
+    g2_exact = 2.0 * e / e.size
+    g2 = mlp_ref.bf16(g2_exact)
+    # hidden gradients: bf16((g W^T) * gelu'(pre)) from the GPU's own g and pre
+    up1 = g2 @ Ws[2].T
+    _assert_bf16_matches(g1, up1 * mlp_ref.gelu_grad(pre[1]), "g1")
+    up0 = g1 @ Ws[1].T
+    _assert_bf16_matches(g0, up0 * mlp_ref.gelu_grad(pre[0]), "g0")
+    ins = [x, act[0], act[1]]
+    gs = [g0, g1, g2]
+    for l, p in enumerate(net.params):
+        dw, db = _f64(p["dw"]), _f64(p["db"])
+        want = ins[l].T @ gs[l]
+        bound = _acc_bound(ins[l].T, gs[l], B)
+        if l == 2:
+            # the output gradient is recomputed here: allow a rare bf16 flip in it
+            bound = bound + np.abs(ins[l].T) @ _bf_ulp(g2_exact) * (np.abs(g2 - mlp_ref.bf16(g2_exact)) > 0)
+            flip = np.abs(dw - want) > bound
+            assert np.count_nonzero(flip) <= max(2, 1e-3 * dw.size), (l, np.count_nonzero(flip))
+            assert (np.abs(dw - want) <= bound + np.abs(ins[l].T) @ _bf_ulp(g2_exact)).all()
+        else:
+            assert (np.abs(dw - want) <= bound).all(), (l, float(np.max(np.abs(dw - want) - bound)))
+        assert (np.abs(db - gs[l].sum(axis=0)) <= ACC * B * U32 * np.abs(gs[l]).sum(axis=0) + 1e-30).all(), l
 
 
 def test_split_k_forward_and_gradients_match_reference():
@@ -88,12 +190,14 @@ def test_split_k_forward_and_gradients_match_reference():
     rng = np.random.default_rng(4)
     x = mlp_ref.bf16(rng.standard_normal((128, dims[0])))
     t = mlp_ref.bf16(rng.standard_normal((128, dims[-1])))
-    pred = net.forward(_bf(x)).cpu().numpy()
+    pred = net.forward(_bf(x)).cpu().numpy().astype(np.float64)
     mlp.status()
+    _layerwise_forward(net, Ws, bs, x, pred)
     ref, _ = mlp_ref.forward(Ws, bs, x, bf=True)
     assert _rel(pred, ref) < 5e-3
     net.train_step(_bf(x), _bf(t), lr=1e-3)
     mlp.status()
+    _layerwise_backward(net, Ws, x, t)
     _, dWs, dbs = mlp_ref.loss_and_grads(Ws, bs, x, t, bf=True)
     for l, p in enumerate(net.params):
         assert _rel(p["dw"].cpu().numpy(), dWs[l]) < 2e-2, l

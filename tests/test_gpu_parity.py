@@ -1,13 +1,23 @@
 """GPU (FP32, CUDA through the C ABI) versus the FP64 oracle on identical seeded inputs.
 
+Both sides run the same rule at a failed outer step: the library's default, the cap rule
+(oracle.PRODUCT_RULE: rho capped at 100, a multiplier step at the cap), which the oracle
+implements as an option beside Algorithm 1's own branch.
+
 Parity bar (per converged problem):
   * controls: |u_gpu - u_oracle|_inf <= 1e-4 * max(|u_oracle|_inf, 1);
   * the oracle's FP64 KKT conditions of Eq. (bmpc) evaluated at the GPU's returned
-    (x, u, lambda, y) are below 1e-5 (stationarity, defects, feasibility, complementarity).
+    (x, u, lambda, y) are below 1e-5 (stationarity, defects, feasibility, complementarity);
+  * inner-iteration counts: see ITER_ABS and ITER_MEAN.
 The method is an iteration on a nonconvex problem, so FP32 and FP64 may stop at two
 different KKT points; such a pair counts as "distinct local minimum" only if the oracle,
 warm-started from the GPU solution, confirms it as a KKT point of its own within two
-iterations.
+iterations, and such pairs must stay a small minority.
+
+One iteration (test_one_iteration_from_an_identical_iterate): from an identical FP32 iterate, both sides take
+exactly one inner iteration (max_iters = 1); the new (x, u, lambda, y) are compared element by
+element.  That checks the search direction, the step size and the multiplier updates directly,
+which a whole solve cannot (a slightly wrong direction still converges to the same point).
 """
 import numpy as np
 import pytest
@@ -20,6 +30,18 @@ pytestmark = pytest.mark.gpu
 
 U_REL = 1e-4
 KKT_TOL = 1e-5
+RULE = oracle.PRODUCT_RULE
+
+# Inner-iteration counts of a matched pair: FP32 rounding can move a borderline decision (an
+# inner-loop exit at r_kkt <= omega, an Armijo test, the c <= eta test) by one iteration, and such a
+# shift changes the later schedule too.  The rule: |delta| <= ITER_ABS for every matched pair, and
+# the mean |delta| over a test's matched pairs <= ITER_MEAN.
+ITER_ABS = 4
+ITER_MEAN = 1.0
+
+
+def _orc(p, **kw):
+    return oracle.solve(p, **RULE, **kw)
 
 
 def _gpu(problems, **kw):
@@ -45,7 +67,7 @@ def _check_pair(p, g, r):
     du = np.abs(g["u"][inner] - r["u"][inner]).max()
     if du <= U_REL * max(np.abs(r["u"][inner]).max(), 1.0):
         return "match"
-    w = oracle.solve(p, warm=(g["x"], g["u"], g["lam"], g["y"]))
+    w = _orc(p, warm=(g["x"], g["u"], g["lam"], g["y"]))
     assert w["status"] == oracle.OK and w["inner_iters"] <= 2, "GPU point not confirmed by the oracle"
     assert np.abs(w["u"][inner] - g["u"][inner]).max() <= U_REL * max(np.abs(g["u"][inner]).max(), 1.0)
     return "distinct"
@@ -54,17 +76,30 @@ def _check_pair(p, g, r):
 def _run_config(problems, min_match=0.8, **kw):
     gres = _gpu(problems, **kw)
     counts = {"match": 0, "distinct": 0, "oracle_fail": 0}
+    dits = []
     for p, g in zip(problems, gres):
-        r = oracle.solve(p)
+        r = _orc(p)
         if r["status"] != oracle.OK:
             counts["oracle_fail"] += 1
             assert g["status"] in (oracle.OK, oracle.MAX_ITER, oracle.LS_FAIL)
             continue
-        counts[_check_pair(p, g, r)] += 1
+        kind = _check_pair(p, g, r)
+        counts[kind] += 1
+        if kind == "match":
+            dits.append(g["inner_iters"] - r["inner_iters"])
     solved = counts["match"] + counts["distinct"]
     assert solved >= 1
     assert counts["match"] >= min_match * solved, counts
+    _iter_rule(dits)
+    counts["iter_delta"] = dits
     return counts
+
+
+def _iter_rule(dits):
+    if not dits:
+        return
+    d = np.abs(np.asarray(dits))
+    assert d.max() <= ITER_ABS and d.mean() <= ITER_MEAN, dits
 
 
 def test_config1_parity():
@@ -76,7 +111,7 @@ def test_config2_parity():
 
 
 def test_config3_parity():
-    print(_run_config(scenes.instances(3, 2, seed0=1), min_match=0.5))
+    print(_run_config(scenes.instances(3, 8, seed0=1), min_match=0.75))
 
 
 @pytest.mark.parametrize("cfg", [2, 3])
@@ -103,7 +138,7 @@ def test_linear_quadratic_one_iteration():
     ps = [scenes.linear_problem(s, N=12, splits={2: 2, 6: 3}) for s in range(3)]
     gres = _gpu(ps)
     for p, g in zip(ps, gres):
-        r = oracle.solve(p)
+        r = _orc(p)
         assert g["status"] == oracle.OK and g["inner_iters"] == 1
         np.testing.assert_allclose(g["u"], r["u"], atol=1e-4 * max(1.0, np.abs(r["u"]).max()))
         np.testing.assert_allclose(g["x"], r["x"], atol=1e-4 * max(1.0, np.abs(r["x"]).max()))
@@ -141,7 +176,7 @@ def test_edge_trees():
     ps = [base, wide, obs8]
     gres = _gpu(ps, block_threads=128)
     for p, g in zip(ps, gres):
-        r = oracle.solve(p)
+        r = _orc(p)
         assert r["status"] == oracle.OK
         _check_pair(p, g, r)
 
@@ -165,7 +200,7 @@ def test_ragged_tree_parity():
     q["n"] = len(idx)
     for key in ("xref", "weight", "obs"):
         q[key] = p[key][idx]
-    r = oracle.solve(q)
+    r = _orc(q)
     g = _gpu([q])[0]
     assert r["status"] == oracle.OK
     assert _check_pair(q, g, r) == "match"
@@ -277,7 +312,7 @@ def test_convergence_outcomes_follow_the_oracle_on_config3():
     gres = _gpu(ps, block_threads=256)
     failures = 0
     for p, g in zip(ps, gres):
-        r = oracle.solve(p)
+        r = _orc(p)
         if max(g["inner_iters"], r["inner_iters"]) >= 45 and (g["status"] == oracle.OK) != (r["status"] == oracle.OK):
             continue
         assert (g["status"] == oracle.OK) == (r["status"] == oracle.OK), (g["status"], r["status"], g["r_kkt"], r["r_kkt"])
@@ -348,7 +383,7 @@ def test_shifted_warm_start_receding_horizon():
     prev.close()
     assert all(w["start_used"] == 1 for w in warm)
     for p, w in zip(next_ps, warm):
-        r = oracle.solve(p)
+        r = _orc(p)
         if r["status"] == oracle.OK:
             _check_pair(p, w, r)
     assert sum(w["inner_iters"] for w in warm) < sum(c["inner_iters"] for c in cold)
@@ -395,19 +430,87 @@ def test_invalid_problem_rejected():
 
 
 def test_full_size_batch_sampled():
-    """The launch configuration the benchmark times: 4,096 mixed problems in one launch."""
+    """The launch configuration the benchmark times: 4,096 mixed problems in one launch (the
+    autotuned per-model block sizes of the benchmark, 256 threads per kinematic problem and 512 per
+    dynamic one).  Sampled problems are drawn from every tree size, in three bands by node count, both
+    models.  A problem the oracle solves and the GPU does not is a failure; one exception is allowed
+    where the oracle itself needs 40 or more of the 50 iterations (a borderline case at the cap)."""
     ps = scenes.config4(4, 4096)
-    gres = _gpu(ps)
+    gres = _gpu(ps, block_threads=256, block_threads_model=[256, 512, 0])
     conv = np.mean([g["status"] == oracle.OK for g in gres])
     assert conv >= 0.85, conv
     rng = np.random.default_rng(0)
-    small = [k for k in range(len(ps)) if ps[k]["n"] < 700]
-    counts = {"match": 0, "distinct": 0, "skip": 0}
-    for k in rng.choice(small, 6, replace=False):
-        r = oracle.solve(ps[k])
-        if r["status"] != oracle.OK or gres[k]["status"] != oracle.OK:
-            counts["skip"] += 1
+    nodes = np.array([int(p["n"]) for p in ps])
+    bands = [(0, 700), (700, 1500), (1500, 10 ** 6)]
+    picks = []
+    for lo, hi in bands:
+        idx = np.where((nodes >= lo) & (nodes < hi))[0]
+        picks += list(rng.choice(idx, 4, replace=False))
+    assert max(nodes[picks]) >= 1500 and any(int(ps[k]["model"]) == 1 for k in picks)
+    counts = {"match": 0, "distinct": 0, "oracle_fail": 0, "borderline": 0}
+    dits = []
+    for k in picks:
+        r = _orc(ps[k])
+        g = gres[k]
+        if r["status"] != oracle.OK:
+            counts["oracle_fail"] += 1
             continue
-        counts[_check_pair(ps[k], gres[k], r)] += 1
-    print(counts, conv)
-    assert counts["match"] + counts["distinct"] >= 3
+        if g["status"] != oracle.OK and r["inner_iters"] >= 40:
+            counts["borderline"] += 1
+            continue
+        kind = _check_pair(ps[k], g, r)
+        counts[kind] += 1
+        if kind == "match":
+            dits.append(g["inner_iters"] - r["inner_iters"])
+    print(counts, dits, conv)
+    assert counts["borderline"] <= 1, counts
+    assert counts["match"] >= 0.75 * (counts["match"] + counts["distinct"]) and counts["match"] >= 6, counts
+    _iter_rule(dits)
+
+
+def _fp32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def _one_iteration(p, k):
+    """Both sides take one inner iteration from the same FP32 iterate: the cold start (k = 0, each
+    side forms its own) or the oracle's iterate after k iterations, rounded to float32."""
+    if k == 0:
+        warm = None
+    else:
+        it = _orc(p, max_iters=k)
+        warm = tuple(_fp32(it[key]) for key in ("x", "u", "lam", "y"))
+    from paper_2506_13624_b300 import bmpc
+    b = bmpc.Batch([p])
+    b.set_problems(warm=None if warm is None else [warm])
+    b.solve(bmpc.default_opts(max_iters=1))
+    g = b.get_solutions()[0]
+    b.close()
+    r = _orc(p, max_iters=1, warm=warm)
+    return g, r
+
+
+# One iteration from an identical FP32 iterate.  The step solves a tree LQR assembled in FP32 from
+# FP32 data; its relative error is a few units of 2^-24 times the growth along the N + 1 Riccati
+# steps.  The bar is relative to each block's magnitude (max(1, |.|_inf) of the oracle's block):
+# STEP_REL for x, u, lambda and y alike.
+STEP_REL = 2e-4
+
+
+@pytest.mark.parametrize("cfg,k", [(1, 0), (1, 3), (2, 0), (2, 4), (3, 0), (3, 6)])
+def test_one_iteration_from_an_identical_iterate(cfg, k):
+    for seed in range(3 if cfg < 3 else 2):
+        p = scenes.instances(cfg, 1, seed0=seed)[0]
+        g, r = _one_iteration(p, k)
+        assert g["inner_iters"] == r["inner_iters"] == 1, (g["inner_iters"], r["inner_iters"])
+        assert g["status"] == r["status"]
+        worst = {}
+        for key in ("x", "u", "lam", "y"):
+            a, b = g[key], r[key]
+            if b.size == 0:
+                continue
+            scale = max(1.0, float(np.abs(b).max()))
+            d = float(np.abs(a - b).max()) / scale
+            worst[key] = d
+            assert d <= STEP_REL, (cfg, k, seed, key, d)
+        print(cfg, k, seed, worst)

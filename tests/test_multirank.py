@@ -51,13 +51,16 @@ def test_two_gloo_ranks_shard_and_reduce():
 
 def test_profiled_traffic_only_for_the_captured_kernel(tmp_path, monkeypatch):
     """bench.py reports the roofline traffic from an ncu capture only while the kernel sources hash
-    to the captured version; otherwise, and for other workloads, it reports null."""
+    to the captured version, scaled by node-iterations; otherwise, and for workloads without a
+    capture, it reports null."""
     import bench
     sha = bench.kernel_sha()
-    prof = tmp_path / "capture.md"
-    prof.write_text(f"kernel_sha256: {sha}\ndram_bytes_per_problem: 1000\nproblems_captured: 512\n")
-    monkeypatch.setattr(bench, "PROFILE", str(prof))
-    assert bench.profiled_traffic("config2", 2048) == 1000.0 * 2048
-    assert bench.profiled_traffic("config3", 1024) is None
-    prof.write_text("kernel_sha256: 0000000000000000\ndram_bytes_per_problem: 1000\n")
-    assert bench.profiled_traffic("config2", 2048) is None
+    (tmp_path / "profiles").mkdir()
+    prof = tmp_path / "profiles" / "capture.md"
+    prof.write_text(f"kernel_sha256: {sha}\ndram_bytes_per_node_iteration: 1000\nproblems_captured: 512\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "PROFILES", {"config4": "capture.md"})
+    assert bench.profiled_traffic("config4", 2048.0) == 1000.0 * 2048
+    assert bench.profiled_traffic("config3", 1024.0) is None
+    prof.write_text("kernel_sha256: 0000000000000000\ndram_bytes_per_node_iteration: 1000\n")
+    assert bench.profiled_traffic("config4", 2048.0) is None

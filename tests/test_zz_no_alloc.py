@@ -4,8 +4,10 @@ Callers that cannot allocate device memory for the solver (real-time control loo
 forbid allocation while running, plug-ins whose framework owns all device buffers) create
 the batch with bmpc_create_batch_static; the solver scratch is then the library's fixed
 16 MiB device array.  Through the C ABI, two solves in a row on such a batch must give the
-same results as the regular entry point, within the parity tolerance of the GPU tests, and a
-batch that needs more scratch than the array holds must be refused.
+same results as the regular entry point bit for bit (the same kernel, block size and inputs, so
+the same arithmetic), with a solve of a different batch through the same array in between (stale
+scratch from it would show), and a batch that needs more scratch than the array holds must be
+refused.
 """
 import numpy as np
 import pytest
@@ -15,18 +17,16 @@ import scenes
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-U_REL = 1e-4
-
 
 def _problems():
     return [scenes.config1(2), scenes.config2(3)] + scenes.config4(4, 5)
 
 
-def _close(a, b):
+def _same(a, b):
     for key in ("x", "u", "lam", "y"):
-        scale = max(1.0, float(np.abs(a[key]).max()) if a[key].size else 1.0)
-        np.testing.assert_allclose(b[key], a[key], rtol=0, atol=U_REL * scale)
-    assert a["status"] == b["status"]
+        assert np.array_equal(b[key], a[key]), key
+    for key in ("status", "inner_iters", "outer_iters", "ls_evals"):
+        assert a[key] == b[key], key
 
 
 def test_static_scratch_matches_regular_entry_point_twice():
@@ -42,11 +42,18 @@ def test_static_scratch_matches_regular_entry_point_twice():
     sb = bmpc.StaticScratchBatch(ps)
     assert sb.scratch_bytes <= bmpc.STATIC_SCRATCH_BYTES
     sb.set_problems()
-    for _ in range(2):
+    for call in range(2):
         sb.solve(opts)
         got = sb.get_solutions()
         for a, b in zip(want, got):
-            _close(a, b)
+            _same(a, b)
+        if call == 0:
+            # another batch through the shared array leaves its own data there
+            other = bmpc.StaticScratchBatch(scenes.config4(9, 6) + [scenes.config2(11)])
+            other.set_problems()
+            other.solve(opts)
+            assert all(r["inner_iters"] > 0 for r in other.get_solutions(want_arrays=False))
+            other.close()
     sb.close()
     assert sum(r["status"] == 0 for r in want) >= len(ps) - 1
 
