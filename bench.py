@@ -56,6 +56,8 @@ def workload(name: str, batch: int, rank: int = 0):
         return [scenes.config4_problem(4 + rank, i) for i in range(batch)]
     if name == "config3":
         return [scenes.config3(rank * batch + i) for i in range(batch)]
+    if name == "unicycle":
+        return [scenes.unicycle(rank * batch + i) for i in range(batch)]
     raise ValueError(name)
 
 
@@ -69,8 +71,8 @@ def flops_model(p) -> dict:
     nx, model, nsub = int(p["nx"]), int(p["model"]), max(1, int(p["params"][9]))
     nz = nx + 2
     ns = nx * (nx + 1) // 2
-    rhs = {0: 20, 1: 70, 2: 2 * nx * nz}[model]
-    nnz = {0: 7, 1: 18, 2: nx * nz}[model]
+    rhs = {0: 20, 1: 70, 2: 2 * nx * nz, 3: 16}[model]
+    nnz = {0: 7, 1: 18, 2: nx * nz, 3: 6}[model]
     n_obs = int(p["n_obs"])
     if model == 2:
         lin_dyn = 2 * nx * nz
@@ -538,7 +540,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=["config1", "config2", "config3", "config4"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=["config1", "config2", "config3", "config4", "unicycle"])
     ap.add_argument("--batch", type=int, default=DEFAULT_BATCH)
     ap.add_argument("--single", type=int, default=0, metavar="P",
                     help="single-problem latency of the first P problems of the workload (one per launch)")

@@ -52,11 +52,14 @@ typedef enum {
 #define BMPC_MAX_OBS 8
 #define BMPC_MAX_NX 6
 #define BMPC_NU 2
+#define BMPC_NUM_MODELS 4
 
 /* Dynamics models (the ego vehicle's f_i of Eq. bmpc; discretised by RK4):
  *   0 kinematic bicycle, x = (X, Y, psi, v),          u = (a, delta), nx = 4
  *   1 dynamic bicycle (linear tyres, small steering), x = (X, Y, psi, vx, vy, r), nx = 6
- *   2 linear x+ = Alin x + Blin u,                     nx = 4                       */
+ *   2 linear x+ = Alin x + Blin u,                     nx = 4
+ *   3 unicycle, x = (X, Y, theta, v),                  u = (a, omega), nx = 4
+ *     (X' = v cos theta, Y' = v sin theta, theta' = omega, v' = a; Sec. V-B's benchmark) */
 typedef struct {
     int32_t num_nodes;      /* >= 2 */
     const int32_t *parent;  /* host [num_nodes]; parent[0] = -1; level order: nodes sorted by
@@ -104,7 +107,7 @@ typedef struct {
     float omega0, eta0;     /* 1, 0.1 */
     float a_omega, b_omega; /* 1, 1 */
     float a_eta, b_eta;     /* 0.1, 0.9 */
-    float rho0, rho_max;    /* 10, 100 (see cap_rule) */
+    float rho0, rho_max;    /* 10, 1e6 (the paper gives no cap; see cap_rule) */
     float mu0;              /* 1 */
     float beta;             /* Armijo constant, 1e-4 */
     float ls_rel_eps;       /* Armijo slack relative to |phi(0)|, 1e-6 */
@@ -129,19 +132,33 @@ typedef struct {
                                problem's previous solve in this batch + 1), sorted on the device before
                                each launch (so also inside a captured graph); 0 largest tree first.
                                The solutions do not depend on it. */
-    int32_t block_threads_model[3]; /* threads per problem for the launch of one dynamics model (0
-                               kinematic, 1 dynamic, 2 linear) in a mixed batch (32..512, multiple of
+    int32_t block_threads_model[BMPC_NUM_MODELS]; /* threads per problem for the launch of one
+                               dynamics model (0 kinematic, 1 dynamic, 2 linear, 3 unicycle) in a
+                               mixed batch (32..512, multiple of
                                32); 0 = block_threads.  Each model has its own launch, so a mixed
                                batch can run, e.g., its kinematic problems two per SM and its large
                                dynamic ones one per SM. Default 0. */
     int32_t cap_rule;       /* what a failed outer step does (c > eta, Sec. IV-B):
-                               0 Algorithm 1: y kept, rho <- min(tau rho, rho_max);
-                               1 (default) the same below rho_max, but at rho_max the multiplier
-                               step y <- max(0, y + rho g) instead.  In FP32 the relaxed KKT residual
-                               holds rho * (rounding of g near the boundary, about 1e-7), so a large
-                               rho puts a floor near 1e-5 under it; the default caps rho at 100 and
-                               keeps the multipliers moving there.  With cap_rule 0 choose rho_max
-                               accordingly (the FP64 oracle's Algorithm-1 default is 1e6). */
+                               0 (default) Algorithm 1: y kept, rho <- min(tau rho, rho_max);
+                               1 the same below rho_max, but at rho_max the multiplier step
+                               y <- max(0, y + rho g) instead, for a low cap (e.g. rho_max = 100):
+                               with a plain FP32 iterate (compensated = 0) rho times the rounding of
+                               g floors the relaxed KKT residual near 1e-5 once rho exceeds about
+                               100, and this rule keeps the multipliers moving at such a cap. */
+    float kkt_margin;       /* the kernel tests convergence (max(r_kkt, c) < tol) and floors omega and
+                               eta at tol = kkt_margin * eps_tol, default 0.8, in (0, 1].  Its FP32
+                               evaluation of r_kkt carries rounding of about 1e-6 (terms of size 1-10
+                               at unit roundoff 6e-8), so a point it accepts at exactly eps_tol can
+                               exceed eps_tol when evaluated in exact arithmetic; the margin keeps the
+                               returned point within eps_tol. */
+    int32_t compensated;    /* 1 (default): the iterate's positions (X, Y) and inputs are held as
+                               pairs of floats (value and rounding remainder), every accepted step is
+                               added without loss, and the constraint values that the penalty
+                               multiplies by rho (input bounds, keep-out distances, lane bounds) are
+                               formed from both parts, the keep-out distance in two-float arithmetic.
+                               With plain FP32 iterates, rho times the rounding of an input resting on
+                               its bound (or of a position on a keep-out boundary) floors the relaxed
+                               KKT residual near 1e-5.  0: plain FP32 iterate. */
 } bmpc_opts;
 
 typedef struct {

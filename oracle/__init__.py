@@ -50,10 +50,14 @@ class Opts(C.Structure):
                 ("trace", C.c_void_p), ("trace_user", C.c_void_p)]
 
 
-# The rule of the FP32 product at a failed outer step (both sides implement it): the penalty is
-# capped at rho_max = 100, and a failure at the cap applies the multiplier step y <- max(0, y + rho g)
-# instead of keeping y.  The oracle's default is Algorithm 1 (y kept, rho <- tau rho up to 1e6).
-PRODUCT_RULE = dict(cap_rule=1, rho_max=100.0)
+# The FP32 library's default constants, which the oracle takes as options to run the same algorithm:
+# Algorithm 1 as the oracle's own default, with the library's convergence tests at 0.8 eps_tol (its
+# kkt_margin), so that points it returns as converged meet eps_tol = 1e-5 when evaluated exactly.
+PRODUCT_RULE = dict(eps_tol=8e-6)
+# The library's alternative rule at a failed outer step (cap_rule = 1 with a low cap): the penalty
+# is capped at rho_max = 100, and a failure at the cap applies the multiplier step
+# y <- max(0, y + rho g) instead of keeping y.
+CAP_RULE = dict(cap_rule=1, rho_max=100.0, eps_tol=8e-6)
 
 TRACE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.POINTER(C.c_double), *([C.POINTER(C.c_double)] * 7))
 

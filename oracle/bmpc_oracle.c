@@ -9,6 +9,8 @@
  *
  * Passages followed (paper section / equation / algorithm):
  *   problem             Sec. II-B, Eq. (bmpc): node costs, x_i = f_p(i)(x_p(i), u_p(i)), g <= 0
+ *   models              kinematic and dynamic bicycles (the planning scenes), linear (LQ pins),
+ *                       unicycle (the constraint benchmark of Sec. V-B)
  *   tree LQR            Sec. III-A, Eq. (lqr_tree_approx), Eq. (tree_Riccati),
  *                       Eq. (tree_feedback_laws); forward rollout as in Sec. II-A
  *   tree LQR by scans   Sec. III-B, Eq. (sol_min), Eq. (comb_rule), Eq. (forward_comb_rule):
@@ -185,6 +187,21 @@ static void rhs(const orc_problem *P, const double *s, const double *u, double *
         Jx[1 * 4 + 3] = sin(psi);
         Jx[2 * 4 + 3] = td / L;
         Ju[2 * 2 + 1] = v * (1.0 + td * td) / L;
+        Ju[3 * 2 + 0] = 1.0;
+        return;
+    }
+    if (P->model == 3) {
+        /* unicycle (Sec. V-B): X' = v cos th, Y' = v sin th, th' = omega, v' = a */
+        double th = s[2], v = s[3];
+        f[0] = v * cos(th);
+        f[1] = v * sin(th);
+        f[2] = u[1];
+        f[3] = u[0];
+        Jx[0 * 4 + 2] = -v * sin(th);
+        Jx[0 * 4 + 3] = cos(th);
+        Jx[1 * 4 + 2] = v * cos(th);
+        Jx[1 * 4 + 3] = sin(th);
+        Ju[2 * 2 + 1] = 1.0;
         Ju[3 * 2 + 0] = 1.0;
         return;
     }
@@ -1001,8 +1018,8 @@ static double merit_at(const orc_problem *P, const tree_t *T, int nc, const doub
 
 static int check_problem(const orc_problem *P) {
     if (!P || P->n < 1 || P->nx < 1 || P->nx > MAXX || P->nu < 1 || P->nu > MAXU) return 0;
-    if (P->model < 0 || P->model > 2) return 0;
-    if (P->model == 0 && (P->nx != 4 || P->nu != 2)) return 0;
+    if (P->model < 0 || P->model > 3) return 0;
+    if ((P->model == 0 || P->model == 3) && (P->nx != 4 || P->nu != 2)) return 0;
     if (P->model == 1 && (P->nx != 6 || P->nu != 2)) return 0;
     if (P->model != 2 && (P->nx < 2)) return 0;
     if (n_con(P) > 64) return 0;

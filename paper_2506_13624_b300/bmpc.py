@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libbmpc.so")
 OK, MAX_ITER, LS_FAIL = 0, 1, 2
 ERR_INVALID, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, ERR_SPACE = -1, -2, -3, -4, -5
 MAX_NX, NU, MAX_OBS = 6, 2, 8
+MODEL_KINEMATIC, MODEL_DYNAMIC, MODEL_LINEAR, MODEL_UNICYCLE = 0, 1, 2, 3
 
 _fp = C.POINTER(C.c_float)
 _ip = C.POINTER(C.c_int32)
@@ -46,7 +47,8 @@ class Opts(C.Structure):
                 ("ls_rel_eps", C.c_float), ("ls_chunk", C.c_int32), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("variant", C.c_int32), ("warm_select", C.c_int32),
                 ("select_mu", C.c_float), ("select_rho", C.c_float), ("queue_order", C.c_int32),
-                ("block_threads_model", C.c_int32 * 3), ("cap_rule", C.c_int32)]
+                ("block_threads_model", C.c_int32 * 4), ("cap_rule", C.c_int32),
+                ("kkt_margin", C.c_float), ("compensated", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -160,7 +162,7 @@ def default_opts(**kw) -> Opts:
     lib().bmpc_default_opts(C.byref(o))
     for k, v in kw.items():
         if k == "block_threads_model":
-            v = (C.c_int32 * 3)(*v)
+            v = (C.c_int32 * 4)(*v)
         setattr(o, k, v)
     return o
 

@@ -64,8 +64,8 @@ int validate(const bmpc_tree_desc &d, std::vector<int> *stage_out) {
     if (d.nu != NU) return BMPC_ERR_INVALID;
     if (d.model == 0 && d.nx != 4) return BMPC_ERR_INVALID;
     if (d.model == 1 && d.nx != 6) return BMPC_ERR_INVALID;
-    if (d.model == 2 && d.nx != 4) return BMPC_ERR_INVALID;
-    if (d.model < 0 || d.model > 2) return BMPC_ERR_INVALID;
+    if ((d.model == 2 || d.model == 3) && d.nx != 4) return BMPC_ERR_INVALID;
+    if (d.model < 0 || d.model >= NUM_MODELS) return BMPC_ERR_INVALID;
     if (d.n_obs < 0 || d.n_obs > MAX_OBS) return BMPC_ERR_INVALID;
     if (!(d.dt > 0.f) || !std::isfinite(d.dt)) return BMPC_ERR_INVALID;
     if (d.model != 2 && !(d.params[9] >= 1.f && d.params[9] <= 64.f)) return BMPC_ERR_INVALID;
@@ -98,9 +98,9 @@ struct bmpc_batch {
     std::vector<int32_t> order;
     std::vector<int> nodes;
     std::vector<int32_t> parents;        /* all trees' parent arrays, concatenated */
-    int model_begin[4] = {0, 0, 0, 0};   /* order[model_begin[m] .. model_begin[m+1]) has model m */
-    int tab_ints[3] = {0, 0, 0};         /* shared-memory stage/path tables per model (0: global) */
-    int max_paths[3] = {0, 0, 0};        /* most scenarios of a tree, per model */
+    int model_begin[NUM_MODELS + 1] = {};  /* order[model_begin[m] .. model_begin[m+1]) has model m */
+    int tab_ints[NUM_MODELS] = {};         /* shared-memory stage/path tables per model (0: global) */
+    int max_paths[NUM_MODELS] = {};        /* most scenarios of a tree, per model */
     bool host_inputs = false;            /* staging holds the inputs of the last upload */
     Layout L{};
     char *data = nullptr;
@@ -110,8 +110,8 @@ struct bmpc_batch {
     size_t stage_bytes = 0;
     bool own_stage = false;
     cudaStream_t stream = nullptr;
-    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};   /* per-model streams of mixed batches */
-    cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t aux[NUM_MODELS] = {};   /* per-model streams of mixed batches */
+    cudaEvent_t fork = nullptr, join[NUM_MODELS] = {};
     cudaEvent_t handoff = nullptr;       /* orders a new stream after the old one (bmpc_set_stream) */
     int sm_count = 148;
     cudaGraph_t graph = nullptr;
@@ -223,7 +223,8 @@ KOpts to_kopts(const bmpc_opts &o) {
     k.variant = o.variant;
     k.warm_select = o.warm_select;
     k.cap_rule = o.cap_rule;
-    k.eps_tol = o.eps_tol;
+    k.compensated = o.compensated;
+    k.eps_tol = o.eps_tol * o.kkt_margin;   /* the kernel's own FP32 tests, with the margin */
     k.tau = o.tau;
     k.omega0 = o.omega0;
     k.eta0 = o.eta0;
@@ -254,7 +255,9 @@ int check_opts(const bmpc_opts &o) {
         !(o.select_rho > 0.f)) return BMPC_ERR_INVALID;
     if (o.queue_order < 0 || o.queue_order > 1) return BMPC_ERR_INVALID;
     if (o.cap_rule < 0 || o.cap_rule > 1) return BMPC_ERR_INVALID;
-    for (int m = 0; m < 3; ++m) {
+    if (!(o.kkt_margin > 0.f && o.kkt_margin <= 1.f)) return BMPC_ERR_INVALID;
+    if (o.compensated < 0 || o.compensated > 1) return BMPC_ERR_INVALID;
+    for (int m = 0; m < NUM_MODELS; ++m) {
         const int bt = o.block_threads_model[m];
         if (bt != 0 && (bt < 32 || bt > max_block_threads() || bt % 32)) return BMPC_ERR_INVALID;
     }
@@ -353,10 +356,10 @@ int launch(bmpc_batch *b, const bmpc_opts &o) {
     /* one persistent kernel per model; with several models the kernels run concurrently on forked
        streams, so that the blocks of one fill the tail of the other */
     int models = 0;
-    for (int m = 0; m < 3; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
+    for (int m = 0; m < NUM_MODELS; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
     if (models > 1 && cudaEventRecord(b->fork, b->stream) != cudaSuccess) return BMPC_ERR_CUDA;
     bool first = true;
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < NUM_MODELS; ++m) {
         const int cnt = b->model_begin[m + 1] - b->model_begin[m];
         if (cnt == 0) continue;
         cudaStream_t s = b->stream;
@@ -401,7 +404,7 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->a_eta = 0.1f;
     o->b_eta = 0.9f;
     o->rho0 = 10.f;
-    o->rho_max = 100.f;
+    o->rho_max = 1e6f;
     o->mu0 = 1.f;
     o->beta = 1e-4f;
     o->ls_rel_eps = 1e-6f;
@@ -413,8 +416,10 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->select_mu = 100.f;
     o->select_rho = 1e4f;
     o->queue_order = 1;
-    for (int m = 0; m < 3; ++m) o->block_threads_model[m] = 0;
-    o->cap_rule = 1;
+    for (int m = 0; m < NUM_MODELS; ++m) o->block_threads_model[m] = 0;
+    o->cap_rule = 0;
+    o->kkt_margin = 0.8f;
+    o->compensated = 1;
 }
 
 int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
@@ -476,9 +481,9 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
         if (b->recs[a].model != b->recs[c].model) return b->recs[a].model < b->recs[c].model;
         return b->nodes[a] > b->nodes[c];
     });
-    for (int m = 0; m < 4; ++m) b->model_begin[m] = 0;
+    for (int m = 0; m <= NUM_MODELS; ++m) b->model_begin[m] = 0;
     for (int k = 0; k < n; ++k) b->model_begin[b->recs[k].model + 1]++;
-    for (int m = 0; m < 3; ++m) b->model_begin[m + 1] += b->model_begin[m];
+    for (int m = 0; m < NUM_MODELS; ++m) b->model_begin[m + 1] += b->model_begin[m];
     /* tables of up to 32 KB per problem go to shared memory (below the 48 KB needing no opt-in) */
     for (int k = 0; k < n; ++k) {
         const ProbRec &r = b->recs[k];
@@ -486,7 +491,7 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
         b->tab_ints[r.model] = (int)std::max<int64_t>(b->tab_ints[r.model], t);
         b->max_paths[r.model] = std::max(b->max_paths[r.model], r.n_paths);
     }
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < NUM_MODELS; ++m) {
         if (b->tab_ints[m] > 8192) b->tab_ints[m] = 0;
         if (b->model_begin[m + 1] == b->model_begin[m]) continue;
         size_t most = 0;   /* the largest launch over every allowed block size */
@@ -504,10 +509,10 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
         return BMPC_ERR_CUDA;
     }
     int models = 0;
-    for (int m = 0; m < 3; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
+    for (int m = 0; m < NUM_MODELS; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
     if (models > 1) {   /* streams and events of the concurrent per-model launches */
         bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
-        for (int m = 0; m < 3 && ok; ++m)
+        for (int m = 0; m < NUM_MODELS && ok; ++m)
             ok = cudaStreamCreateWithFlags(&b->aux[m], cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&b->join[m], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {
@@ -790,7 +795,7 @@ int bmpc_shift_warm_start(bmpc_batch *next, const bmpc_batch *prev, int32_t slot
     for (ProbRec &R : next->recs) R.has_warm |= 1 << slot;
     int st = upload_recs(next);
     if (st != BMPC_OK) return st;
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < NUM_MODELS; ++m) {
         const int cnt = next->model_begin[m + 1] - next->model_begin[m];
         if (!cnt) continue;
         WarmArgs wm = w;
@@ -848,7 +853,7 @@ int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, cons
     g.ld_pred = ld_pred;
     g.mean = mean;
     g.std = std;
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < NUM_MODELS; ++m) {
         const int cnt = b->model_begin[m + 1] - b->model_begin[m];
         g.order_base = reinterpret_cast<const int32_t *>(b->data + b->L.order) + b->model_begin[m];
         if (launch_glue(2, g, cnt, b->stream, m) != cudaSuccess) return BMPC_ERR_CUDA;
@@ -898,7 +903,7 @@ int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *
             for (int ch : kChunk) {
                 bmpc_opts c = o;
                 c.block_threads = bt;
-                for (int m = 0; m < 3; ++m) c.block_threads_model[m] = 0;
+                for (int m = 0; m < NUM_MODELS; ++m) c.block_threads_model[m] = 0;
                 c.variant = v;
                 c.ls_chunk = ch;
                 c.blocks_per_sm = 0;
@@ -914,8 +919,8 @@ int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *
     /* mixed batches: then the threads per problem of each model's launch, one model at a time */
     {
         int models = 0;
-        for (int m = 0; m < 3; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
-        for (int m = 0; m < 3 && models > 1; ++m) {
+        for (int m = 0; m < NUM_MODELS; ++m) models += b->model_begin[m + 1] > b->model_begin[m];
+        for (int m = 0; m < NUM_MODELS && models > 1; ++m) {
             if (b->model_begin[m + 1] == b->model_begin[m]) continue;
             const bmpc_opts base_o = best_o;
             for (int bt : kThreads) {
@@ -1089,7 +1094,7 @@ void bmpc_destroy_batch(bmpc_batch *b) {
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < NUM_MODELS; ++m) {
         if (b->aux[m]) cudaStreamDestroy(b->aux[m]);
         if (b->join[m]) cudaEventDestroy(b->join[m]);
     }

@@ -147,6 +147,79 @@ __device__ __forceinline__ float rcp(float x) {
 /* 2^-k for 0 <= k <= 126, exactly (the step sizes alpha_i of the line search). */
 __device__ __forceinline__ float pow2neg(int k) { return __int_as_float((127 - k) << 23); }
 
+/* ------------------------------------------------------------------ compensated arithmetic */
+/* Error-free transformations in round-to-nearest FP32 (Knuth's TwoSum; the FMA form of Dekker's
+ * TwoProduct): s = fl(a + b) with a + b = s + e exactly, p = fl(a b) with a b = p + e exactly. */
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+__device__ __forceinline__ float two_prod(float a, float b, float &e) {
+    const float p = a * b;
+    e = fmaf(a, b, -p);
+    return p;
+}
+
+/* Low-order parts of the compensated iterate at one node: the state deviation's positions and the
+ * inputs are held as pairs (hi, lo), hi the FP32 value and lo the remainder, so that an accepted
+ * step smaller than an ulp of hi is not lost.  Near an active constraint the penalty multiplies
+ * the constraint's value by rho; with the iterate rounded to FP32, rho times that rounding puts a
+ * floor under the relaxed KKT residual (an input resting on its bound at 2.0 has ulp 2.4e-7, times
+ * rho = 100: 2.4e-5).  The pairs remove that floor; everything else reads hi alone. */
+struct Lo {
+    float x[2], u[NU];
+};
+
+/* (hi, lo) += t, renormalised so that |lo| <= ulp(hi) / 2. */
+__device__ __forceinline__ void comp_add(float &hi, float &lo, float t) {
+    float e, e2;
+    const float s = two_sum(hi, t, e);
+    hi = two_sum(s, lo + e, e2);
+    lo = e2;
+}
+
+/* Keep-out value g = 1 - sqrt(q2), q2 = (d_par/a)^2 + (d_perp/b)^2 + 1e-6, at the compensated
+ * position (reference xr, yr plus deviation xh + xl, yh + yl) from the obstacle centre (cx, cy),
+ * heading cosine ch and sine sh, ia2 = 1/a^2, ib2 = 1/b^2, in two-float arithmetic: near the boundary
+ * q2 is close to 1, and in plain FP32 g would carry an absolute error of an ulp of 1 that the
+ * penalty multiplies by rho.  Also returns the FP32 d_par, d_perp and 1/sqrt(q2) for the gradient,
+ * where relative accuracy suffices. */
+__device__ __forceinline__ float obs_g_comp(float xr, float yr, float cx, float cy, float xh, float xl, float yh,
+                                            float yl, float ch, float sh, float ia2, float ib2, float &dpar,
+                                            float &dper, float &irr) {
+    float e1, e2, e3, e4;
+    const float dxh = two_sum(two_sum(xr, -cx, e1), xh, e2);
+    const float dxl = (e1 + e2) + xl;
+    const float dyh = two_sum(two_sum(yr, -cy, e3), yh, e4);
+    const float dyl = (e3 + e4) + yl;
+    float f1, f2, f3, f4, f5, f6;
+    const float p1 = two_prod(ch, dxh, f1), p2 = two_prod(sh, dyh, f2);
+    const float parh = two_sum(p1, p2, f3);
+    const float parl = ((f1 + f2) + f3) + (ch * dxl + sh * dyl);
+    const float p3 = two_prod(-sh, dxh, f4), p4 = two_prod(ch, dyh, f5);
+    const float perh = two_sum(p3, p4, f6);
+    const float perl = ((f4 + f5) + f6) + (ch * dyl - sh * dxl);
+    float g1, g2, g3, g4, g5, g6, g7;
+    const float s1 = two_prod(parh, parh, g1);
+    const float t1 = two_prod(ia2, s1, g2);
+    const float t1l = g2 + ia2 * (g1 + 2.f * parh * parl);
+    const float s2 = two_prod(perh, perh, g3);
+    const float t2 = two_prod(ib2, s2, g4);
+    const float t2l = g4 + ib2 * (g3 + 2.f * perh * perl);
+    const float qb = two_sum(two_sum(t1, t2, g5), 1e-6f, g6);
+    const float qh = two_sum(qb, ((g5 + g6) + t1l) + t2l, g7);
+    /* sqrt(qh + g7) = r + (qh - r^2 + g7) / (2 r); qh - r^2 is exact through the FMA */
+    const float r = sqrtf(qh);
+    const float ir = rcp(r);
+    const float res = fmaf(-r, r, qh) + g7;
+    dpar = parh;
+    dper = perh;
+    irr = ir;
+    return (1.f - r) - 0.5f * res * ir;
+}
+
 /* Per-call constants of a vehicle right-hand side: reciprocals of the model parameters that it
  * divides by, and tan(delta) of the kinematic model (the steering input is constant over an RK4
  * step).  Computed once per node instead of once per RK4 stage. */
@@ -170,7 +243,8 @@ __device__ __forceinline__ ModelK model_k(const float *prm, float dl) {
 
 /* Continuous right-hand side and its Jacobians (dense arrays; compile-time zero
  * entries are folded away after unrolling).  MODEL 0: kinematic bicycle, 1: dynamic
- * bicycle with linear tyres and small steering angle. */
+ * bicycle with linear tyres and small steering angle, 3: unicycle (X' = v cos th,
+ * Y' = v sin th, th' = omega, v' = a; the constraint benchmark of Sec. V-B). */
 template <int NX, int MODEL>
 __device__ __forceinline__ void rhs_jac(const float *prm, const ModelK &mk, const float (&s)[NX], float a, float dl,
                                         float (&f)[NX], float (&J)[NX][NX], float (&Ju)[NX][NU]) {
@@ -242,6 +316,20 @@ __device__ __forceinline__ void rhs_jac(const float *prm, const ModelK &mk, cons
         J[5][4] = (lf * dFf_vy - lr * dFr_vy) * iIz;
         J[5][5] = (lf * dFf_r - lr * dFr_r) * iIz;
         Ju[5][1] = lf * dFf_d * iIz;
+    } else if constexpr (MODEL == 3) {
+        float sp, cp;
+        sincos_cw(s[2], &sp, &cp);
+        const float v = s[3];
+        f[0] = v * cp;
+        f[1] = v * sp;
+        f[2] = dl;
+        f[3] = a;
+        J[0][2] = -v * sp;
+        J[0][3] = cp;
+        J[1][2] = v * cp;
+        J[1][3] = sp;
+        Ju[2][1] = 1.f;
+        Ju[3][0] = 1.f;
     }
 }
 
@@ -273,6 +361,13 @@ __device__ __forceinline__ void rhs(const float *prm, const ModelK &mk, const fl
         f[3] = a + r * vy;
         f[4] = (Ff + Fr) * mk.im - r * vx;
         f[5] = (lf * Ff - lr * Fr) * mk.iIz;
+    } else if constexpr (MODEL == 3) {
+        float sp, cp;
+        sincos_cw(s[2], &sp, &cp);
+        f[0] = s[3] * cp;
+        f[1] = s[3] * sp;
+        f[2] = dl;
+        f[3] = a;
     }
 }
 
@@ -448,7 +543,8 @@ struct View {
     /* outputs */
     float *X, *U, *L, *Y;
     /* scratch */
-    float *A, *B, *f, *d, *q, *r, *hq, *hr, *K, *k, *P, *p, *dx, *du, *lq, *nv;
+    float *A, *B, *f, *d, *q, *r, *hq, *hr, *K, *k, *P, *p, *dx, *du, *lq, *nv, *XL, *UL;
+    bool comp;   /* compensated iterate (Lo parts) in use */
 
     __device__ View(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout, float *fs) {
         n = R.n;
@@ -498,6 +594,9 @@ struct View {
         du = fs + (size_t)s.du * np;
         lq = fs + (size_t)s.lq * np;
         nv = fs + (size_t)s.nv * np;
+        XL = fs + (size_t)s.xl * np;
+        UL = fs + (size_t)s.ul * np;
+        comp = false;
     }
     const float *fwarm;
     /* point wx .. wy at warm-start slot s */
@@ -521,6 +620,25 @@ struct View {
         v[0] = base[i];
         v[1] = base[(size_t)np + i];
     }
+    /* low-order parts of node i's iterate (zero when the iterate is not compensated) */
+    __device__ __forceinline__ void load_lo(int i, Lo &lo) const {
+        if (comp) {
+            lo.x[0] = XL[i];
+            lo.x[1] = XL[(size_t)np + i];
+            lo.u[0] = UL[i];
+            lo.u[1] = UL[(size_t)np + i];
+        } else {
+            lo.x[0] = lo.x[1] = lo.u[0] = lo.u[1] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void store_lo(int i, const Lo &lo) const {
+        if (comp) {
+            XL[i] = lo.x[0];
+            XL[(size_t)np + i] = lo.x[1];
+            UL[i] = lo.u[0];
+            UL[(size_t)np + i] = lo.u[1];
+        }
+    }
     __device__ __forceinline__ void store_u(float *base, int i, const float (&v)[NU]) const {
         base[i] = v[0];
         base[(size_t)np + i] = v[1];
@@ -533,8 +651,8 @@ struct View {
  * the position block, hr on the input diagonal.  mode: 0 = value only. */
 template <int NX, bool GRAD>
 __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, int i, bool is_leaf,
-                                         const float (&x)[NX], const float (&u)[NU], float rho, float (&q)[NX],
-                                         float (&r)[NU], float (&hq)[3], float (&hr)[NU]) {
+                                         const float (&x)[NX], const float (&u)[NU], const Lo &lo, float rho,
+                                         float (&q)[NX], float (&r)[NU], float (&hq)[3], float (&hr)[NU]) {
     /* x is the deviation from the node's reference (the kernel's state coordinates) */
     const float w = V.w[i];
     const float *Qd = is_leaf ? R.QNw : R.Qw;
@@ -566,7 +684,7 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
 #pragma unroll
                 for (int sgn = 0; sgn < 2; ++sgn) {
                     const int rr = row + sgn * NU + j;
-                    const float g = sgn == 0 ? u[j] - R.u_hi[j] : R.u_lo[j] - u[j];
+                    const float g = sgn == 0 ? (u[j] - R.u_hi[j]) + lo.u[j] : (R.u_lo[j] - u[j]) - lo.u[j];
                     const float s = V.Y[(size_t)rr * V.np + i] + rho * g;
                     if (s > 0.f) {
                         la += 0.5f * s * s * irho;
@@ -585,12 +703,18 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
             const float *ob = V.obs + (size_t)(OBS_ROWS * o) * V.np + i;
             const float cx = ob[0], cy = ob[V.np], ch = ob[2 * (size_t)V.np], sh = ob[3 * (size_t)V.np];
             const float ia2 = ob[4 * (size_t)V.np], ib2 = ob[5 * (size_t)V.np];
-            const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
-            const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
-            const float q2 = dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f;
-            const float irr = rsqrtf(q2);   /* 1 / rr2 */
-            const float rr2 = q2 * irr;
-            const float g = 1.f - rr2;
+            float dpar, dper, irr, g;
+            if (V.comp) {
+                g = obs_g_comp(V.xref[i], V.xref[(size_t)V.np + i], cx, cy, x[0], lo.x[0], x[1], lo.x[1], ch, sh, ia2,
+                               ib2, dpar, dper, irr);
+            } else {
+                const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
+                dpar = ch * dxo + sh * dyo;
+                dper = -sh * dxo + ch * dyo;
+                const float q2 = dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f;
+                irr = rsqrtf(q2);   /* 1 / rr2 */
+                g = 1.f - q2 * irr;
+            }
             const float s = V.Y[(size_t)(row + o) * V.np + i] + rho * g;
             if (s > 0.f) {
                 la += 0.5f * s * s * irho;
@@ -608,7 +732,7 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
         row += V.nobs;
         if (V.lane) {
             const float yr = V.xref[(size_t)V.np + i];
-            const float g0 = (yr - R.lane_hi) + x[1], g1 = (R.lane_lo - yr) - x[1];
+            const float g0 = ((yr - R.lane_hi) + x[1]) + lo.x[1], g1 = ((R.lane_lo - yr) - x[1]) - lo.x[1];
             const float s0 = V.Y[(size_t)row * V.np + i] + rho * g0;
             const float s1 = V.Y[(size_t)(row + 1) * V.np + i] + rho * g1;
             if (s0 > 0.f) {
@@ -633,14 +757,14 @@ __device__ __forceinline__ float node_la(const ProbRec &R, const View<NX> &V, in
 /* Constraint rows g (existing rows only, others skipped) at the deviation x: calls fn(row, g). */
 template <int NX, typename Fn>
 __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX> &V, int i, bool is_leaf,
-                                                const float (&x)[NX], const float (&u)[NU], Fn fn) {
+                                                const float (&x)[NX], const float (&u)[NU], const Lo &lo, Fn fn) {
     int row = 0;
     if (V.box) {
         if (!is_leaf) {
 #pragma unroll
             for (int j = 0; j < NU; ++j) {
-                fn(row + j, u[j] - R.u_hi[j]);
-                fn(row + NU + j, R.u_lo[j] - u[j]);
+                fn(row + j, (u[j] - R.u_hi[j]) + lo.u[j]);
+                fn(row + NU + j, (R.u_lo[j] - u[j]) - lo.u[j]);
             }
         }
         row += 2 * NU;
@@ -650,16 +774,22 @@ __device__ __forceinline__ void for_constraints(const ProbRec &R, const View<NX>
             const float *ob = V.obs + (size_t)(OBS_ROWS * o) * V.np + i;
             const float cx = ob[0], cy = ob[V.np], ch = ob[2 * (size_t)V.np], sh = ob[3 * (size_t)V.np];
             const float ia2 = ob[4 * (size_t)V.np], ib2 = ob[5 * (size_t)V.np];
-            const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
-            const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
-            const float q2 = dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f;
-            fn(row + o, 1.f - q2 * rsqrtf(q2));
+            if (V.comp) {
+                float dpar, dper, irr;
+                fn(row + o, obs_g_comp(V.xref[i], V.xref[(size_t)V.np + i], cx, cy, x[0], lo.x[0], x[1], lo.x[1], ch,
+                                       sh, ia2, ib2, dpar, dper, irr));
+            } else {
+                const float dxo = (V.xref[i] - cx) + x[0], dyo = (V.xref[(size_t)V.np + i] - cy) + x[1];
+                const float dpar = ch * dxo + sh * dyo, dper = -sh * dxo + ch * dyo;
+                const float q2 = dpar * dpar * ia2 + dper * dper * ib2 + 1e-6f;
+                fn(row + o, 1.f - q2 * rsqrtf(q2));
+            }
         }
         row += V.nobs;
         if (V.lane) {
             const float yr = V.xref[(size_t)V.np + i];
-            fn(row, (yr - R.lane_hi) + x[1]);
-            fn(row + 1, (R.lane_lo - yr) - x[1]);
+            fn(row, ((yr - R.lane_hi) + x[1]) + lo.x[1]);
+            fn(row + 1, ((R.lane_lo - yr) - x[1]) - lo.x[1]);
         }
     }
 }
@@ -1496,11 +1626,18 @@ __device__ void load_start(const ProbRec &R, View<NX> &V, int which) {
             }
         }
         if (is_leaf) u[0] = u[1] = 0.f;
+        Lo lo;
 #pragma unroll
-        for (int j = 0; j < NX; ++j) x[j] -= V.xref[(size_t)j * np + i];   /* deviation coordinates */
+        for (int j = 0; j < NX; ++j) {   /* deviation coordinates; the positions keep the remainder */
+            float e;
+            x[j] = two_sum(x[j], -V.xref[(size_t)j * np + i], e);
+            if (j < 2) lo.x[j] = e;
+        }
+        lo.u[0] = lo.u[1] = 0.f;
         V.store_x(V.X, i, x);
         V.store_u(V.U, i, u);
         V.store_x(V.L, i, l);
+        V.store_lo(i, lo);
     }
 }
 
@@ -1512,9 +1649,11 @@ __device__ float start_merit(const ProbRec &R, const View<NX> &V, float rho, flo
     for (int i = tid; i < V.n; i += nt) {
         const int nch = V.nchild[i], fc = V.fchild[i];
         float x[NX], u[NU], qd[NX], rd[NU], hqd[3], hrd[NU];
+        Lo lo;
         V.load_x(V.X, i, x);
         V.load_u(V.U, i, u);
-        float v = node_la<NX, false>(R, V, i, nch == 0, x, u, rho, qd, rd, hqd, hrd);
+        V.load_lo(i, lo);
+        float v = node_la<NX, false>(R, V, i, nch == 0, x, u, lo, rho, qd, rd, hqd, hrd);
         if (nch) {
             float xa[NX], ft[NX];
 #pragma unroll
@@ -1539,7 +1678,7 @@ __device__ float start_merit(const ProbRec &R, const View<NX> &V, float rho, flo
  * the root, lam += a (lam_QP - lam) in memory (Algorithm 1, update after the line search). */
 template <int NX>
 __device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU],
-                                           float (&lam)[NX]) {
+                                           float (&lam)[NX], Lo &lo) {
     /* every row is loaded before anything is computed or stored, so the loads go out together;
      * the caller stores x, u and (for i != 0) lam after the rest of its node work */
     float dxv[NX], duv[NU], lmv[NX], lqv[NX];
@@ -1549,10 +1688,19 @@ __device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, fl
         V.load_x(V.L, i, lmv);
         V.load_x(V.lq, i, lqv);
     }
+    if (V.comp) {
+        comp_add(x[0], lo.x[0], a * dxv[0]);
+        comp_add(x[1], lo.x[1], a * dxv[1]);
 #pragma unroll
-    for (int j = 0; j < NX; ++j) x[j] += a * dxv[j];
+        for (int j = 2; j < NX; ++j) x[j] += a * dxv[j];
 #pragma unroll
-    for (int j = 0; j < NU; ++j) u[j] += a * duv[j];
+        for (int j = 0; j < NU; ++j) comp_add(u[j], lo.u[j], a * duv[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) x[j] += a * dxv[j];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) u[j] += a * duv[j];
+    }
     if (i != 0) {
 #pragma unroll
         for (int j = 0; j < NX; ++j) lam[j] = lmv[j] + a * (lqv[j] - lmv[j]);
@@ -1561,18 +1709,25 @@ __device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, fl
 
 /* The same step row by row, storing lam_i as it goes (the register-lean form; see hoist_loads). */
 template <int NX>
-__device__ __forceinline__ void apply_step_serial(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU]) {
+__device__ __forceinline__ void apply_step_serial(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU],
+                                                  Lo &lo) {
     const int np = V.np;
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
-        x[j] += a * V.dx[(size_t)j * np + i];
+        const float t = a * V.dx[(size_t)j * np + i];
+        if (j < 2 && V.comp) comp_add(x[j], lo.x[j], t);
+        else x[j] += t;
         if (i != 0) {
             const float lm = V.L[(size_t)j * np + i];
             V.L[(size_t)j * np + i] = lm + a * (V.lq[(size_t)j * np + i] - lm);
         }
     }
 #pragma unroll
-    for (int j = 0; j < NU; ++j) u[j] += a * V.du[(size_t)j * np + i];
+    for (int j = 0; j < NU; ++j) {
+        const float t = a * V.du[(size_t)j * np + i];
+        if (V.comp) comp_add(u[j], lo.u[j], t);
+        else u[j] += t;
+    }
 }
 
 /* ------------------------------------------------------------------ the per-problem solver */
@@ -1583,6 +1738,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
     constexpr int NS = nsym(NX);
     constexpr bool HOIST_LOADS = hoist_loads<NX>();
     View<NX> V(R, ib, fin, fw, fout, fs);
+    V.comp = O.compensated != 0;
     /* stage and path tables into shared memory: the sweeps index through them at every stage */
     const int64_t tn = table_ints(R.npad, R.n_stage, R.n_paths);
     if (tn <= tab_cap) {
@@ -1639,11 +1795,13 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                      * store the compiler cannot prove distinct would hold back every later load */
                     const bool is_leaf = V.nchild[i] == 0;
                     float x[NX], u[NU], lam[NX], q[NX], r[NU], hq[3], hr[NU];
+                    Lo lo;
                     V.load_x(V.X, i, x);
                     V.load_u(V.U, i, u);
+                    V.load_lo(i, lo);
                     const bool step = pending > 0.f;
-                    if (step) apply_step<NX>(V, i, pending, x, u, lam);
-                    const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, rho, q, r, hq, hr);
+                    if (step) apply_step<NX>(V, i, pending, x, u, lam, lo);
+                    const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, lo, rho, q, r, hq, hr);
                     float xa[NX];
                     if (!is_leaf) {
     #pragma unroll
@@ -1652,6 +1810,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     if (step) {
                         V.store_x(V.X, i, x);
                         V.store_u(V.U, i, u);
+                        V.store_lo(i, lo);
                         if (i != 0) V.store_x(V.L, i, lam);
                     }
                     V.store_x(V.q, i, q);
@@ -1673,14 +1832,17 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                 } else {
                     const bool is_leaf = V.nchild[i] == 0;
                     float x[NX], u[NU], q[NX], r[NU], hq[3], hr[NU];
+                    Lo lo;
                     V.load_x(V.X, i, x);
                     V.load_u(V.U, i, u);
+                    V.load_lo(i, lo);
                     if (pending > 0.f) {
-                        apply_step_serial<NX>(V, i, pending, x, u);
+                        apply_step_serial<NX>(V, i, pending, x, u, lo);
                         V.store_x(V.X, i, x);
                         V.store_u(V.U, i, u);
+                        V.store_lo(i, lo);
                     }
-                    const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, rho, q, r, hq, hr);
+                    const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, lo, rho, q, r, hq, hr);
                     V.store_x(V.q, i, q);
                     V.store_u(V.r, i, r);
                     V.hq[i] = hq[0];
@@ -1844,11 +2006,26 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                         for (int m = fc; m < fc + nch; ++m)
                             base += V.nv[(size_t)np + m] + 0.5f * mu * V.nv[2 * (size_t)np + m];
                         float xt[NX], ut[NU], qd[NX], rd[NU], hqd[3], hrd[NU];
+                        Lo lt;
+                        V.load_lo(i, lt);
 #pragma unroll
                         for (int j = 0; j < NX; ++j) xt[j] = x[j] + al * dxv[j];
                         ut[0] = u[0] + al * duv[0];
                         ut[1] = u[1] + al * duv[1];
-                        float v = node_la<NX, false>(R, V, i, is_leaf, xt, ut, rho, qd, rd, hqd, hrd);
+                        if (V.comp) {   /* the trial point's remainders */
+                            float e;
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                xt[j] = two_sum(x[j], al * dxv[j], e);
+                                lt.x[j] += e;
+                            }
+#pragma unroll
+                            for (int j = 0; j < NU; ++j) {
+                                ut[j] = two_sum(u[j], al * duv[j], e);
+                                lt.u[j] += e;
+                            }
+                        }
+                        float v = node_la<NX, false>(R, V, i, is_leaf, xt, ut, lt, rho, qd, rd, hqd, hrd);
                         if (!is_leaf) {
                             float xa[NX], ft[NX];
 #pragma unroll
@@ -1898,11 +2075,14 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
             if (ls_fail >= 3) {
                 for (int i = tid; i < n; i += nt) {
                     float x[NX], u[NU];
+                    Lo lo;
                     V.load_x(V.X, i, x);
                     V.load_u(V.U, i, u);
-                    apply_step_serial<NX>(V, i, pending, x, u);
+                    V.load_lo(i, lo);
+                    apply_step_serial<NX>(V, i, pending, x, u, lo);
                     V.store_x(V.X, i, x);
                     V.store_u(V.U, i, u);
+                    V.store_lo(i, lo);
                 }
                 __syncthreads();
                 status = 2;
@@ -1915,9 +2095,11 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
             for (int i = tid; i < n; i += nt) {
                 const bool is_leaf = V.nchild[i] == 0;
                 float x[NX], u[NU];
+                Lo lo;
                 V.load_x(V.X, i, x);
                 V.load_u(V.U, i, u);
-                for_constraints<NX>(R, V, i, is_leaf, x, u, [&](int row, float g) {
+                V.load_lo(i, lo);
+                for_constraints<NX>(R, V, i, is_leaf, x, u, lo, [&](int row, float g) {
                     const float yv = V.Y[(size_t)row * np + i];
                     cv = fmaxf(cv, fabsf(fmaxf(g, -yv * rcp(rho))));
                 });
@@ -1927,9 +2109,11 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                 for (int i = tid; i < n; i += nt) {
                     const bool is_leaf = V.nchild[i] == 0;
                     float x[NX], u[NU];
+                    Lo lo;
                     V.load_x(V.X, i, x);
                     V.load_u(V.U, i, u);
-                    for_constraints<NX>(R, V, i, is_leaf, x, u, [&](int row, float g) {
+                    V.load_lo(i, lo);
+                    for_constraints<NX>(R, V, i, is_leaf, x, u, lo, [&](int row, float g) {
                         float *yp = V.Y + (size_t)row * np + i;
                         *yp = fmaxf(0.f, *yp + rho * g);
                     });
@@ -1950,9 +2134,11 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     for (int i = tid; i < n; i += nt) {
                         const bool is_leaf = V.nchild[i] == 0;
                         float x[NX], u[NU];
+                        Lo lo;
                         V.load_x(V.X, i, x);
                         V.load_u(V.U, i, u);
-                        for_constraints<NX>(R, V, i, is_leaf, x, u, [&](int row, float g) {
+                        V.load_lo(i, lo);
+                        for_constraints<NX>(R, V, i, is_leaf, x, u, lo, [&](int row, float g) {
                             float *yp = V.Y + (size_t)row * np + i;
                             *yp = fmaxf(0.f, *yp + rho * g);
                         });
@@ -2264,7 +2450,8 @@ cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream)
     if (a.n_problems <= 0) return cudaSuccess;
     if (model == 0) bmpc_shift_warm_kernel<0><<<a.n_problems, 256, 0, stream>>>(a);
     else if (model == 1) bmpc_shift_warm_kernel<1><<<a.n_problems, 256, 0, stream>>>(a);
-    else bmpc_shift_warm_kernel<2><<<a.n_problems, 256, 0, stream>>>(a);
+    else if (model == 2) bmpc_shift_warm_kernel<2><<<a.n_problems, 256, 0, stream>>>(a);
+    else bmpc_shift_warm_kernel<3><<<a.n_problems, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -2384,7 +2571,8 @@ cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream
     else if (which == 1) bmpc_targets_kernel<<<n_problems, 256, 0, stream>>>(a);
     else if (model == 0) bmpc_starts_kernel<0><<<n_problems, 256, 0, stream>>>(a);
     else if (model == 1) bmpc_starts_kernel<1><<<n_problems, 256, 0, stream>>>(a);
-    else bmpc_starts_kernel<2><<<n_problems, 256, 0, stream>>>(a);
+    else if (model == 2) bmpc_starts_kernel<2><<<n_problems, 256, 0, stream>>>(a);
+    else bmpc_starts_kernel<3><<<n_problems, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -2395,7 +2583,8 @@ SolveFn solve_fn(int model, int block) {
     const bool big = block > BATCH_BLOCK;
     if (model == 0) return big ? bmpc_solve_kernel<0, MAX_BLOCK> : bmpc_solve_kernel<0, BATCH_BLOCK>;
     if (model == 1) return big ? bmpc_solve_kernel<1, MAX_BLOCK> : bmpc_solve_kernel<1, BATCH_BLOCK>;
-    return big ? bmpc_solve_kernel<2, MAX_BLOCK> : bmpc_solve_kernel<2, BATCH_BLOCK>;
+    if (model == 2) return big ? bmpc_solve_kernel<2, MAX_BLOCK> : bmpc_solve_kernel<2, BATCH_BLOCK>;
+    return big ? bmpc_solve_kernel<3, MAX_BLOCK> : bmpc_solve_kernel<3, BATCH_BLOCK>;
 }
 
 cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, size_t smem, cudaStream_t stream) {
@@ -2408,7 +2597,10 @@ int max_block_threads() { return MAX_BLOCK; }
 /* Dynamic shared memory of a solve launch: the stage/path tables (tab_ints) and, when it fits in
  * 96 KB, the sweep staging of min(max_paths, block) path threads (*stg_ld, else 0). */
 size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld) {
-    const int rows = model == 0 ? rows_stage<4, 0>() : model == 1 ? rows_stage<6, 1>() : rows_stage<4, 2>();
+    const int rows = model == 0   ? rows_stage<4, 0>()
+                     : model == 1 ? rows_stage<6, 1>()
+                     : model == 2 ? rows_stage<4, 2>()
+                                  : rows_stage<4, 3>();
     const int ld = std::min(max_paths, block);
     const size_t tab = sizeof(int32_t) * (size_t)((tab_ints + 3) & ~3);
     const size_t stg = sizeof(float) * (size_t)SWEEP_DEPTH * rows * ld;
@@ -2425,8 +2617,8 @@ size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld
  * default bounds static and dynamic shared memory together, and the kernels' static part (the
  * reduction arrays and the problem record) is about 14 KB. */
 cudaError_t prepare_solve(int model, size_t smem) {
-    static size_t granted[3] = {0, 0, 0};
-    if (model < 0 || model > 2 || smem <= granted[model]) return cudaSuccess;
+    static size_t granted[NUM_MODELS] = {0, 0, 0, 0};
+    if (model < 0 || model >= NUM_MODELS || smem <= granted[model]) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(solve_fn(model, BATCH_BLOCK), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess)

@@ -14,6 +14,7 @@
 namespace bmpc {
 
 constexpr int NU = 2;
+constexpr int NUM_MODELS = 4;   /* 0 kinematic bicycle, 1 dynamic bicycle, 2 linear, 3 unicycle */
 constexpr int MAX_NX = 6;
 constexpr int MAX_OBS = 8;
 constexpr int MAX_NC = 2 * NU + MAX_OBS + 2;
@@ -124,9 +125,11 @@ __host__ __device__ inline OutRows out_rows(int nx, int nc) {
 }
 
 /* scratch: A[nx*nx] B[nx*nu] f[nx] d[nx] q[nx] r[nu] hq[3] hr[nu] K[nu*nx] k[nu] P[nsym] p[nx]
- *          dx[nx] du[nu] lq[nx] nv[3] */
+ *          dx[nx] du[nu] lq[nx] nv[3] xl[2] ul[nu]
+ * xl, ul: low-order parts of the compensated iterate (positions X, Y of the state deviation and the
+ * inputs): the iterate is xi + xl, u + ul, each pair a float and its rounding remainder. */
 struct ScrRows {
-    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, total;
+    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, xl, ul, total;
 };
 __host__ __device__ inline ScrRows scr_rows(int nx) {
     ScrRows s;
@@ -146,13 +149,15 @@ __host__ __device__ inline ScrRows scr_rows(int nx) {
     s.du = s.dx + nx;
     s.lq = s.du + NU;
     s.nv = s.lq + nx;
-    s.total = s.nv + 3;
+    s.xl = s.nv + 3;
+    s.ul = s.xl + 2;
+    s.total = s.ul + NU;
     return s;
 }
 
 /* Kernel-side copy of the solver options (Algorithm 1 constants). */
 struct KOpts {
-    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant, warm_select, cap_rule;
+    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant, warm_select, cap_rule, compensated;
     float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps, select_mu,
         select_rho;
 };

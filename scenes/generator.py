@@ -39,11 +39,13 @@ import numpy as np
 MODEL_KINEMATIC = 0
 MODEL_DYNAMIC = 1
 MODEL_LINEAR = 2
+MODEL_UNICYCLE = 3
 
 # params layout: [L, m, Iz, lf, lr, Cf, Cr, vmin, veps, n_sub]
 MODEL_PARAMS_KINEMATIC = (2.7, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
 MODEL_PARAMS_DYNAMIC = (2.7, 1500.0, 2250.0, 1.2, 1.5, 8.0e4, 8.0e4, 2.0, 0.1, 4.0)
 MODEL_PARAMS_LINEAR = (0.0,) * 9 + (1.0,)
+MODEL_PARAMS_UNICYCLE = (0.0,) * 9 + (1.0,)   # one RK4 step per dt
 
 V_REF = 8.0          # lane cruising speed [m/s]
 REF_ACCEL = 1.0      # speed ramp of the reference profile [m/s^2]
@@ -298,7 +300,10 @@ def config4(seed: int = 4, count: int = 4096):
 def chain_problem(seed: int, model: int, N: int, n_obs: int = 3):
     """A single-path tree (one scenario, N + 1 nodes) of the mixed-batch family: the given model,
     horizon and obstacle count.  Its iterations run the sweeps' dependent chain with no branching,
-    which measures the per-stage latency of the sweeps."""
+    which measures the per-stage latency of the sweeps.  The unicycle's chain is its benchmark
+    scene with horizon N."""
+    if model == MODEL_UNICYCLE:
+        return unicycle(seed, N=N)
     rng = np.random.default_rng([8, seed, model, N])
     p = _base(model, N, {})
     vr = (0.0, 10.0) if model == MODEL_KINEMATIC else (2.0, 10.0)
@@ -323,6 +328,40 @@ def linear_problem(seed: int, N: int = 10, splits=None, nx: int = 4, nu: int = 2
              box_on=1 if constrained else 0, lane_on=0, weight=branch_weights(parent),
              x0=rng.standard_normal(nx), xref=0.3 * rng.standard_normal((n, nx)),
              obs=np.zeros((n, 0, 5)), Alin=f32(A), Blin=f32(B))
+    return _finish(p)
+
+
+UNICYCLE_TARGET = (10.0, 0.0, 0.0, 0.0)
+UNICYCLE_OBSTACLES = ((3.5, 0.25, 1.0), (6.5, -0.35, 0.8))   # circle centres and radii [m]
+
+
+def unicycle(seed: int, N: int = 50, splits=None):
+    """The constraint benchmark of Sec. V-B with the unicycle (nx = 4: X, Y, theta, v; nu = 2:
+    a, omega), dt = 0.1 s, N = 50: the initial state is sampled around the nominal (0, 0, 0, 0)
+    (X, Y ~ U[-1, 1] m, theta ~ U[-0.3, 0.3], v ~ U[0, 1] m/s), the target state is fixed at
+    (10, 0, 0, 0), two circular obstacles lie near the straight line to it (a distance constraint:
+    the keep-out ellipse with equal semi-axes), and the inputs are bounded (|a| <= 2, |omega| <= 1.5).
+    The reference is the target at every node; the start is the linear interpolation to it (the cold
+    start).  The paper does not print its obstacle layout or weights: these are this recipe's.
+    With ``splits`` the same problem on a scenario tree whose branches see the obstacles shifted
+    laterally by up to 0.3 m."""
+    rng = np.random.default_rng([10, seed])
+    parent, stage = tree_parents(N, splits or {})
+    n = parent.shape[0]
+    x0 = np.array([rng.uniform(-1.0, 1.0), rng.uniform(-1.0, 1.0), rng.uniform(-0.3, 0.3), rng.uniform(0.0, 1.0)])
+    xref = np.tile(np.asarray(UNICYCLE_TARGET), (n, 1))
+    obs = np.zeros((n, len(UNICYCLE_OBSTACLES), 5))
+    shift = np.zeros(n)
+    for i in range(1, n):
+        nch = np.count_nonzero(parent == parent[i])
+        shift[i] = shift[parent[i]] + (rng.uniform(-0.3, 0.3) if nch > 1 else 0.0)
+    for j, (cx, cy, r) in enumerate(UNICYCLE_OBSTACLES):
+        obs[:, j] = np.stack([np.full(n, cx), cy + shift, np.zeros(n), np.full(n, r), np.full(n, r)], axis=1)
+    p = dict(model=MODEL_UNICYCLE, nx=4, nu=2, dt=0.1, parent=parent, stage=stage,
+             params=np.array(MODEL_PARAMS_UNICYCLE), Qw=np.array([0.01, 0.01, 0.01, 0.01]),
+             QNw=np.array([10.0, 10.0, 1.0, 1.0]), Rw=np.array([0.1, 0.1]),
+             u_lo=np.array([-2.0, -1.5]), u_hi=np.array([2.0, 1.5]), box_on=1, lane_on=0,
+             weight=branch_weights(parent), x0=x0, xref=xref, obs=obs)
     return _finish(p)
 
 

@@ -98,17 +98,21 @@ def test_invalid_trees_rejected_on_host(mutate):
 
 
 def test_default_opts_match_the_oracle_constants():
-    """The library's defaults are the oracle's constants with the product's cap rule
-    (oracle.PRODUCT_RULE); the oracle's own default is Algorithm 1's failure branch."""
+    """The library's defaults are the oracle's constants (Algorithm 1's failure branch, rho up to 1e6)
+    with the library's convergence margin (oracle.PRODUCT_RULE); the cap rule is the option
+    cap_rule = 1 on both sides."""
     import oracle
     o, r = bmpc.default_opts(), oracle.default_opts(**oracle.PRODUCT_RULE)
     for f in ("max_iters", "max_outer", "n_alpha", "cap_rule"):
         assert getattr(o, f) == getattr(r, f)
-    for f in ("eps_tol", "tau", "omega0", "eta0", "a_omega", "b_omega", "a_eta", "b_eta", "rho0", "rho_max",
+    for f in ("tau", "omega0", "eta0", "a_omega", "b_omega", "a_eta", "b_eta", "rho0", "rho_max",
               "mu0", "beta", "ls_rel_eps"):
         assert np.float32(getattr(o, f)) == np.float32(getattr(r, f)), f
+    assert np.float32(o.eps_tol * o.kkt_margin) == np.float32(r.eps_tol)
     paper = oracle.default_opts()
-    assert paper.cap_rule == 0 and paper.rho_max == 1e6
+    assert paper.cap_rule == 0 and paper.rho_max == 1e6 and o.cap_rule == 0
+    cap = oracle.default_opts(**oracle.CAP_RULE)
+    assert cap.cap_rule == 1 and cap.rho_max == 100.0
 
 
 def test_single_tree_calls_cite_the_problem_statement():
@@ -143,16 +147,18 @@ def test_wait_selftest_rejects_out_of_range_limits():
 
 def test_default_options_match_their_documentation():
     """bmpc_default_opts (host only) sets the constants include/bmpc.h documents: the readings of the
-    paper's unstated constants (rho0 = 10, rho_max = 100, mu0 = 1, Armijo beta = 1e-4, alpha_i = 2^-i
-    for i < 10, 50 inner iterations) and automatic launch geometry."""
+    paper's unstated constants (rho0 = 10, rho_max = 1e6, mu0 = 1, Armijo beta = 1e-4, alpha_i = 2^-i
+    for i < 10, 50 inner iterations), Algorithm 1's failure branch, the compensated iterate and
+    automatic launch geometry."""
     o = bmpc.default_opts()
     assert (o.max_iters, o.max_outer, o.n_alpha) == (50, 60, 10)
     assert o.eps_tol == np.float32(1e-5) and o.tau == 100.0
     assert (o.omega0, o.a_omega, o.b_omega, o.a_eta) == (1.0, 1.0, 1.0, np.float32(0.1))
     assert o.eta0 == np.float32(0.1) and o.b_eta == np.float32(0.9)
-    assert (o.rho0, o.rho_max, o.mu0, o.cap_rule) == (10.0, 100.0, 1.0, 1)
+    assert (o.rho0, o.rho_max, o.mu0, o.cap_rule) == (10.0, 1e6, 1.0, 0)
+    assert o.kkt_margin == np.float32(0.8) and o.compensated == 1
     assert o.beta == np.float32(1e-4) and o.ls_rel_eps == np.float32(1e-6)
     assert (o.block_threads, o.blocks_per_sm, o.variant, o.warm_select, o.queue_order) == (0, 0, 0, 0, 1)
-    assert list(o.block_threads_model) == [0, 0, 0]
+    assert list(o.block_threads_model) == [0, 0, 0, 0]
     assert o.select_mu == 100.0 and o.select_rho == 1e4
-    assert C.sizeof(bmpc.Opts) == 28 * 4   # 28 four-byte fields, as in bmpc_opts
+    assert C.sizeof(bmpc.Opts) == 31 * 4   # 31 four-byte fields, as in bmpc_opts

@@ -1,8 +1,8 @@
 """GPU (FP32, CUDA through the C ABI) versus the FP64 oracle on identical seeded inputs.
 
-Both sides run the same rule at a failed outer step: the library's default, the cap rule
-(oracle.PRODUCT_RULE: rho capped at 100, a multiplier step at the cap), which the oracle
-implements as an option beside Algorithm 1's own branch.
+Both sides run Algorithm 1 with the same constants (oracle.PRODUCT_RULE: the library's
+convergence tests at 0.8 eps_tol); the cap rule (cap_rule = 1, rho capped at 100) is compared
+too, on both sides, and so is the plain FP32 iterate (compensated = 0) with that rule.
 
 Parity bar (per converged problem):
   * controls: |u_gpu - u_oracle|_inf <= 1e-4 * max(|u_oracle|_inf, 1);
@@ -33,11 +33,11 @@ KKT_TOL = 1e-5
 RULE = oracle.PRODUCT_RULE
 
 # Inner-iteration counts of a matched pair: FP32 rounding can move a borderline decision (an
-# inner-loop exit at r_kkt <= omega, an Armijo test, the c <= eta test) by one iteration, and such a
-# shift changes the later schedule too.  The rule: |delta| <= ITER_ABS for every matched pair, and
-# the mean |delta| over a test's matched pairs <= ITER_MEAN.
-ITER_ABS = 4
-ITER_MEAN = 1.0
+# inner-loop exit at r_kkt <= omega, an Armijo test, the c <= eta test) by one iteration.  Measured on
+# B300 over 83 matched pairs of configs 1-4: 82 equal, one differing by 1.  The rule: |delta| <= 1
+# for every matched pair and at most a quarter of a test's matched pairs differing at all.
+ITER_ABS = 1
+ITER_MEAN = 0.25
 
 
 def _orc(p, **kw):
@@ -99,7 +99,7 @@ def _iter_rule(dits):
     if not dits:
         return
     d = np.abs(np.asarray(dits))
-    assert d.max() <= ITER_ABS and d.mean() <= ITER_MEAN, dits
+    assert d.max() <= ITER_ABS and np.mean(d > 0) <= ITER_MEAN, dits
 
 
 def test_config1_parity():
@@ -474,10 +474,12 @@ def _fp32(a):
 
 def _one_iteration(p, k):
     """Both sides take one inner iteration from the same FP32 iterate: the cold start (k = 0, each
-    side forms its own) or the oracle's iterate after k iterations, rounded to float32."""
+    side forms its own) or the oracle's iterate after k iterations, rounded to float32 (k is lowered
+    below the oracle's own iteration count, so that the iterate is not already converged)."""
     if k == 0:
         warm = None
     else:
+        k = max(1, min(k, _orc(p)["inner_iters"] - 2))
         it = _orc(p, max_iters=k)
         warm = tuple(_fp32(it[key]) for key in ("x", "u", "lam", "y"))
     from paper_2506_13624_b300 import bmpc
@@ -490,11 +492,13 @@ def _one_iteration(p, k):
     return g, r
 
 
-# One iteration from an identical FP32 iterate.  The step solves a tree LQR assembled in FP32 from
-# FP32 data; its relative error is a few units of 2^-24 times the growth along the N + 1 Riccati
-# steps.  The bar is relative to each block's magnitude (max(1, |.|_inf) of the oracle's block):
-# STEP_REL for x, u, lambda and y alike.
-STEP_REL = 2e-4
+# One iteration from an identical FP32 iterate, compared relative to each block's magnitude
+# (max(1, |.|_inf) of the oracle's block).  The step solves a tree LQR assembled in FP32 from FP32
+# data: x moves by a small step on states of tens of metres (an ulp of the state, 6e-8 relative,
+# dominates); u and lambda carry the rounding of the linearisation through the N + 1 Riccati steps
+# (up to 4e-6 measured on B300, about 60 ulps); y <- max(0, y + rho g) multiplies the FP32 rounding
+# of g by rho = 100 (up to 3.5e-5 measured).  Bars: five times the measured worst case.
+STEP_TOL = {"x": 1e-6, "u": 2e-5, "lam": 2e-5, "y": 2e-4}
 
 
 @pytest.mark.parametrize("cfg,k", [(1, 0), (1, 3), (2, 0), (2, 4), (3, 0), (3, 6)])
@@ -512,5 +516,61 @@ def test_one_iteration_from_an_identical_iterate(cfg, k):
             scale = max(1.0, float(np.abs(b).max()))
             d = float(np.abs(a - b).max()) / scale
             worst[key] = d
-            assert d <= STEP_REL, (cfg, k, seed, key, d)
+            assert d <= STEP_TOL[key], (cfg, k, seed, key, d)
         print(cfg, k, seed, worst)
+
+
+# ------------------------------------------------------------------ the unicycle benchmark (Sec. V-B)
+def test_unicycle_parity():
+    """The constraint benchmark of Sec. V-B (unicycle, N = 50, input bounds, circular obstacles,
+    linear-interpolation start): GPU against the oracle on 16 instances."""
+    print(_run_config([scenes.unicycle(s) for s in range(16)]))
+
+
+def test_unicycle_tree_parity():
+    """The same benchmark on scenario trees (branches at stages 1 and 10, obstacles shifted per
+    branch)."""
+    print(_run_config([scenes.unicycle(s, splits={1: 2, 10: 2}) for s in range(4)]))
+
+
+def test_unicycle_solved_fraction_follows_the_oracle():
+    """Sec. V-B reports the fraction of 50 instances solved against the iteration count.  On the GPU
+    the fraction solved within k iterations equals the oracle's (same rule) at every k, up to one
+    instance."""
+    ps = [scenes.unicycle(s) for s in range(50)]
+    g = _gpu(ps)
+    r = [_orc(p) for p in ps]
+    gi = np.array([x["inner_iters"] if x["status"] == oracle.OK else 10 ** 6 for x in g])
+    ri = np.array([x["inner_iters"] if x["status"] == oracle.OK else 10 ** 6 for x in r])
+    for k in range(1, 51):
+        assert abs(int(np.sum(gi <= k)) - int(np.sum(ri <= k))) <= 1, k
+    print("solved within 10/20/30/50:", [int(np.sum(gi <= k)) for k in (10, 20, 30, 50)],
+          [int(np.sum(ri <= k)) for k in (10, 20, 30, 50)])
+
+
+# ------------------------------------------------------------------ the alternative rule, the plain iterate
+@pytest.mark.parametrize("compensated", [1, 0])
+def test_cap_rule_parity(compensated):
+    """The cap rule (cap_rule = 1, rho_max = 100: a multiplier step at the cap) on both sides, with
+    the compensated iterate and with the plain FP32 one (the rule it was made for)."""
+    global RULE
+    saved = RULE
+    RULE = oracle.CAP_RULE
+    try:
+        ps = scenes.instances(1, 8) + scenes.instances(2, 4) + scenes.config4(4, 12)
+        print(_run_config(ps, cap_rule=1, rho_max=100.0, compensated=compensated))
+    finally:
+        RULE = saved
+
+
+def test_plain_iterate_stalls_where_the_compensated_one_converges():
+    """Algorithm 1 on the unicycle benchmark: with the plain FP32 iterate most problems stop at the
+    iteration cap with the relaxed KKT residual just above the tolerance (rho times the rounding of
+    an input on its bound), with the compensated iterate they converge like the oracle."""
+    ps = [scenes.unicycle(s) for s in range(16)]
+    plain = _gpu(ps, compensated=0)
+    comp = _gpu(ps)
+    orc = [_orc(p) for p in ps]
+    n_orc = sum(r["status"] == oracle.OK for r in orc)
+    assert sum(g["status"] == oracle.OK for g in comp) >= n_orc - 1
+    assert sum(g["status"] == oracle.OK for g in plain) <= n_orc // 2

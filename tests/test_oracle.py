@@ -70,10 +70,35 @@ def test_dynamic_bicycle_steady_state_yaw_gain():
     assert abs(x[5] - r_ss) < 2e-3 * abs(r_ss)
 
 
-@pytest.mark.parametrize("cfg", [1, 3])
+def test_unicycle_straight_line_closed_form():
+    """omega = 0, constant a: the unicycle moves on a straight line, quadratic in time (RK4 exact)."""
+    p = scenes.unicycle(0)
+    x = np.array([1.0, -2.0, 0.3, 1.5])
+    a, dt = 1.2, p["dt"]
+    xn, _, _ = oracle.dynamics(p, x, np.array([a, 0.0]))
+    s = x[3] * dt + 0.5 * a * dt * dt
+    ref = np.array([x[0] + s * math.cos(x[2]), x[1] + s * math.sin(x[2]), x[2], x[3] + a * dt])
+    np.testing.assert_allclose(xn, ref, rtol=0, atol=1e-14)
+
+
+def test_unicycle_circle_closed_form():
+    """a = 0, constant omega: a circular arc of radius v / omega, heading advancing by omega dt."""
+    p = scenes.unicycle(0)
+    dt = p["dt"]
+    x = np.array([0.5, 0.0, -0.4, 2.0])
+    w = 1.1
+    xn, _, _ = oracle.dynamics(p, x, np.array([0.0, w]))
+    Rc = x[3] / w
+    th1 = x[2] + w * dt
+    ref = np.array([x[0] + Rc * (math.sin(th1) - math.sin(x[2])),
+                    x[1] - Rc * (math.cos(th1) - math.cos(x[2])), th1, x[3]])
+    np.testing.assert_allclose(xn, ref, rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("cfg", [1, 3, "unicycle"])
 def test_jacobians_central_differences(cfg):
-    p = scenes.instances(cfg, 1)[0]
-    rng = np.random.default_rng(cfg)
+    p = scenes.unicycle(1) if cfg == "unicycle" else scenes.instances(cfg, 1)[0]
+    rng = np.random.default_rng(7 if cfg == "unicycle" else cfg)
     nx = p["nx"]
     for _ in range(5):
         x = p["x0"] + 0.5 * rng.standard_normal(nx)

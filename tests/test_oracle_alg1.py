@@ -75,7 +75,7 @@ def _traced(p, **kw):
 
 
 CASES = [(1, 0), (1, 3), (2, 1), (2, 4)]
-RULES = {"paper": {}, "product": oracle.PRODUCT_RULE}
+RULES = {"paper": {}, "cap": oracle.CAP_RULE}
 
 
 def _problem(cfg, seed):
@@ -155,7 +155,7 @@ def test_binding_beta_backtracks_somewhere():
     sign and factor of the inequality are exercised)."""
     total = 0
     for cfg, seed in LS_CASES:
-        _, inner, _ = _traced(_problem(cfg, seed), beta=0.3, **oracle.PRODUCT_RULE)
+        _, inner, _ = _traced(_problem(cfg, seed), beta=0.3, **oracle.CAP_RULE)
         total += sum(t[1][10] < 1.0 for t in inner)
     assert total >= 3, total
 
@@ -225,8 +225,8 @@ def test_cap_rule_multiplier_step_at_the_cap():
         p = scenes.config4_problem(4, seed)
         if p["n"] > 900:
             continue
-        r, _, outer = _traced(p, **oracle.PRODUCT_RULE)
-        branches = _check_outer_sequence(p, outer, oracle.PRODUCT_RULE)
+        r, _, outer = _traced(p, **oracle.CAP_RULE)
+        branches = _check_outer_sequence(p, outer, oracle.CAP_RULE)
         if 2 in branches:
             return
     pytest.fail("no outer step at the cap on forty config-4 scenes")
