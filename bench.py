@@ -523,14 +523,19 @@ def run_single(args):
         it = max(1, r["inner_iters"])
         c = r["cycles"]
         per_cyc = (c["linearise"] + c["backward"] + c["forward"] + c["linesearch"]) / it
+        clk = 2032.0   # cycles -> microseconds at the maximum SM clock (single solves: the GPU is otherwise idle)
+        phases = {k: c[k] / it / clk for k in ("linearise", "backward", "forward", "linesearch")}
         rows.append(dict(nodes=int(p["n"]), depth=depth(p), model=int(p["model"]), iters=r["inner_iters"],
-                         status=r["status"], ms=ms, us_per_iter=1e3 * ms / it,
+                         status=r["status"], ms=ms, us_per_iter=1e3 * ms / it, phase_us_per_iter=phases,
                          latency_frac=crit_cycles_per_iter(p, fits) / per_cyc,
                          bwd_fwd_share=(c["backward"] + c["forward"]) / max(1, c["total"])))
     out = {"workload": args.workload, "mode": "single problem per launch", "chain_fit_cycles": fits,
            "mean_ms": float(np.mean([r["ms"] for r in rows])),
            "mean_us_per_iter": float(np.mean([r["us_per_iter"] for r in rows])),
-           "mean_latency_frac": float(np.mean([r["latency_frac"] for r in rows])), "problems": rows}
+           "mean_latency_frac": float(np.mean([r["latency_frac"] for r in rows])),
+           "mean_phase_us_per_iter": {k: float(np.mean([r["phase_us_per_iter"][k] for r in rows]))
+                                      for k in ("linearise", "backward", "forward", "linesearch")},
+           "problems": rows}
     print(json.dumps(out), flush=True)
 
 

@@ -120,8 +120,15 @@ typedef struct {
                                scenario paths as threads per problem, else 1), 1 level-synchronous (one barrier per stage,
                                nodes of a stage in parallel), 2 per-scenario-path (one thread per
                                root-to-leaf path, barriers only at branch stages), 3 per-scenario-path
-                               with 8 lanes per path (lane j owns column j of [A B], P and H);
-                               all compute the same search direction */
+                               with 8 lanes per path (lane j owns column j of [A B], P and H),
+                               4 scan sweeps (Sec. III-B): conditional value functions combined by
+                               suffix scans along every non-branching segment (Eq. comb_rule), tree
+                               Riccati steps at branch nodes, and pointer jumping over the closed-loop
+                               maps (Eq. forward_comb_rule) forward, so that the sweeps' dependent
+                               steps grow with log2 of the depth (a kernel instance of its own, up to
+                               512 threads per problem), 5 the per-path backward sweep of 2 with the
+                               pointer-jumping forward sweep of 4 (the fastest single solves of deep
+                               paths); all compute the same search direction */
     int32_t warm_select;    /* 1: start from warm slot 0 only if its merit is not above that of the fallback
                                (warm slot 1 when set, else the cold start); default 0 */
     float select_mu;        /* defect penalty mu of the merit used by warm_select, default 100 */
@@ -213,7 +220,7 @@ int bmpc_set_warm_start_device(bmpc_batch *b, const float *dev_start, int64_t st
 int bmpc_shift_warm_start(bmpc_batch *next, const bmpc_batch *prev, int32_t slot);
 
 /* Autotuner: solves the batch once per candidate launch configuration (threads per problem 32 / 64 /
- * 128 / 256, sweep variant 1 / 2 / 3, line-search chunk 1 / 2 / 4; the other fields from `base`,
+ * 128 / 256 / 512, sweep variant 1 to 5, line-search chunk 1 / 2 / 4; the other fields from `base`,
  * NULL = defaults), timing each with CUDA events on the handle's stream, and returns in *best the
  * configuration with the most converged solves per second and in *best_us_per_solve its time per
  * problem.  Synchronises the stream; leaves the last candidate's solution in the outputs. */

@@ -30,7 +30,7 @@ cudaError_t launch_flat(int which, const FlatArgs &a, int n_problems, cudaStream
 cudaError_t launch_sincos(const float *a, float *sn, float *cs, int n, cudaStream_t stream);
 cudaError_t launch_fma(float *out, int blocks, int iters, cudaStream_t stream);
 int max_block_threads();
-cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm, bool scan);
 cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
 cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream);
 struct GlueArgs {
@@ -81,6 +81,51 @@ int validate(const bmpc_tree_desc &d, std::vector<int> *stage_out) {
     }
     if (stage_out) *stage_out = std::move(stage);
     return BMPC_OK;
+}
+
+/* Segment order of the scan sweeps (layout in bmpc_layout.h): the node at every position, the
+ * position of its segment's end, the first position of every wave and the longest segment (in
+ * nodes) of every wave.  Nodes are in level order with contiguous children. */
+struct Segments {
+    std::vector<int32_t> fnode, fend, wstart, wmax;
+};
+void segments(int n, const int32_t *parent, Segments &S) {
+    std::vector<int> nch(n, 0), fch(n, 0), stage(n, 0), end(n, 0), wave(n, 0), size(n, 0);
+    for (int i = 1; i < n; ++i) {
+        const int p = parent[i];
+        if (nch[p] == 0) fch[p] = i;
+        nch[p]++;
+        stage[i] = stage[p] + 1;
+    }
+    for (int i = n - 1; i >= 0; --i) end[i] = nch[i] == 1 ? end[fch[i]] : i;
+    int W = 0;
+    for (int i = n - 1; i >= 0; --i) {
+        size[end[i]]++;
+        if (nch[i] == 1) continue;
+        int w = 0;
+        for (int c = fch[i]; c < fch[i] + nch[i]; ++c) w = std::max(w, wave[end[c]] + 1);
+        wave[i] = w;
+        W = std::max(W, w + 1);
+    }
+    std::vector<int> idx(n), pos(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        const int ea = end[a], eb = end[b];
+        if (wave[ea] != wave[eb]) return wave[ea] < wave[eb];
+        if (ea != eb) return ea < eb;
+        return stage[a] < stage[b];
+    });
+    S.fnode.assign(idx.begin(), idx.end());
+    for (int f = 0; f < n; ++f) pos[idx[f]] = f;
+    S.fend.resize(n);
+    for (int f = 0; f < n; ++f) S.fend[f] = pos[end[idx[f]]];
+    S.wstart.assign(W + 1, 0);
+    S.wmax.assign(W, 0);
+    for (int i = 0; i < n; ++i) {
+        S.wstart[wave[end[i]] + 1]++;
+        if (end[i] == i) S.wmax[wave[i]] = std::max(S.wmax[wave[i]], size[i]);
+    }
+    for (int w = 0; w < W; ++w) S.wstart[w + 1] += S.wstart[w];
 }
 
 struct Layout {
@@ -158,6 +203,11 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         R.n_stage = max_stage + 1;
         R.n_paths = n_paths;
         R.n_bstage = n_bstage;
+        {
+            Segments sg;
+            segments(d.num_nodes, d.parent, sg);
+            R.n_waves = (int32_t)sg.wmax.size();
+        }
         R.dt = d.dt;
         std::memcpy(R.params, d.params, sizeof R.params);
         R.off_int = (int64_t)oi;
@@ -173,7 +223,7 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         fnx += (int64_t)R.n * R.nx;
         fnc += (int64_t)R.n * R.nc;
         fobs += (int64_t)R.n * R.n_obs * 5;
-        oi += (size_t)int_off(R.npad, R.n_stage, R.n_paths).total;
+        oi += (size_t)int_off(R.npad, R.n_stage, R.n_paths, R.n_waves).total;
         oin += (size_t)in_rows(R.nx, R.n_obs).total * R.npad;
         ow += 2 * (size_t)warm_rows(R.nx, R.nc).total * R.npad;   /* primary and fallback slots */
         oo += (size_t)out_rows(R.nx, R.nc).total * R.npad;
@@ -250,7 +300,7 @@ int check_opts(const bmpc_opts &o) {
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > max_block_threads() || o.block_threads % 32))
         return BMPC_ERR_INVALID;
     if (o.blocks_per_sm < 0) return BMPC_ERR_INVALID;
-    if (o.variant < 0 || o.variant > 3) return BMPC_ERR_INVALID;
+    if (o.variant < 0 || o.variant > 5) return BMPC_ERR_INVALID;
     if (o.warm_select < 0 || o.warm_select > 1 || !(o.select_mu >= 0.f) ||
         !(o.select_rho > 0.f)) return BMPC_ERR_INVALID;
     if (o.queue_order < 0 || o.queue_order > 1) return BMPC_ERR_INVALID;
@@ -333,7 +383,7 @@ void geometry(const bmpc_batch *b, const bmpc_opts &o, int model, int count, int
     if (per_sm == 0) {
         int occ = 1, ld;
         const size_t smem = solve_smem(model, b->tab_ints[model], b->max_paths[model], bt, &ld);
-        if (occupancy(model, bt, smem, &occ) != cudaSuccess || occ < 1) occ = 1;
+        if (occupancy(model, bt, smem, &occ, o.variant == 4) != cudaSuccess || occ < 1) occ = 1;
         per_sm = occ;
     }
     *block = bt;
@@ -529,7 +579,15 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
         const ProbRec &R = b->recs[k];
         int32_t *t = ib + R.off_int;
         const int nn = R.n, np = R.npad, ns = R.n_stage, S = R.n_paths;
-        const IntOff io = int_off(np, ns, S);
+        const IntOff io = int_off(np, ns, S, R.n_waves);
+        {
+            Segments sg;
+            segments(nn, d.parent, sg);
+            std::copy(sg.fnode.begin(), sg.fnode.end(), t + io.fnode);
+            std::copy(sg.fend.begin(), sg.fend.end(), t + io.fend);
+            std::copy(sg.wstart.begin(), sg.wstart.end(), t + io.wave);
+            std::copy(sg.wmax.begin(), sg.wmax.end(), t + io.wave + R.n_waves + 1);
+        }
         int32_t *parent = t + io.parent, *nch = t + io.nchild, *fch = t + io.fchild, *stg = t + io.stage;
         int32_t *leaf = t + io.leaf, *owner = t + io.owner, *ss = t + io.sstart, *bst = t + io.bstage;
         int32_t *ptab = t + io.ptab, *pdepth = t + io.pdepth, *ptop = t + io.ptop;
@@ -869,7 +927,7 @@ int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *
     int st = check_opts(o);
     if (st != BMPC_OK) return st;
     static const int kThreads[] = {32, 64, 128, 256, 512};
-    static const int kVariant[] = {1, 2, 3};
+    static const int kVariant[] = {1, 2, 3, 4, 5};
     static const int kChunk[] = {1, 2, 4};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return BMPC_ERR_CUDA;

@@ -537,6 +537,7 @@ struct View {
     bool box, lane;
     /* int rows */
     const int32_t *parent, *nchild, *fchild, *stage, *leaf, *owner, *sstart, *bstage, *ptab, *pdepth, *ptop;
+    const int32_t *fnode, *fend, *wave;   /* segment order of the scan sweeps */
     int64_t tab_off;
     /* inputs */
     const float *xref, *w, *obs, *wx, *wu, *wl, *wy;
@@ -544,6 +545,7 @@ struct View {
     float *X, *U, *L, *Y;
     /* scratch */
     float *A, *B, *f, *d, *q, *r, *hq, *hr, *K, *k, *P, *p, *dx, *du, *lq, *nv, *XL, *UL;
+    float *CV0, *CV1, *JA0, *JA1;   /* scan buffers (two of each) */
     bool comp;   /* compensated iterate (Lo parts) in use */
 
     __device__ View(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout, float *fs) {
@@ -553,7 +555,10 @@ struct View {
         nobs = R.n_obs;
         box = R.box_on != 0;
         lane = R.lane_on != 0;
-        const IntOff io = int_off(np, R.n_stage, R.n_paths);
+        const IntOff io = int_off(np, R.n_stage, R.n_paths, R.n_waves);
+        fnode = ib + io.fnode;
+        fend = ib + io.fend;
+        wave = ib + io.wave;
         parent = ib + io.parent;
         nchild = ib + io.nchild;
         fchild = ib + io.fchild;
@@ -596,6 +601,10 @@ struct View {
         nv = fs + (size_t)s.nv * np;
         XL = fs + (size_t)s.xl * np;
         UL = fs + (size_t)s.ul * np;
+        CV0 = fs + (size_t)s.cv * np;
+        CV1 = CV0 + (size_t)cvf_rows(NX) * np;
+        JA0 = fs + (size_t)s.ja * np;
+        JA1 = JA0 + np;
         comp = false;
     }
     const float *fwarm;
@@ -897,7 +906,7 @@ __host__ __device__ constexpr int rows_stage() { return NX + NX * (NX - a_first<
  * H_n = R_n + B'Pb B, K_n = -H^-1 (M_n + B'Pb A), k_n = -H^-1 (r_n + B'pb) of
  * Eq. (tree_feedback_laws) (M_n = 0 here: no constraint couples x and u), then
  * P_n = Q_n + A'Pb A + Qux'K, p_n = q_n + A'pb + Qux'k.  Stores K, k, P, p; returns P, p. */
-template <int NX, int MODEL>
+template <int NX, int MODEL, bool STORE_PV = true>
 __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V, int i, const RicIn<NX> &in,
                                              const float (&Pb)[nsym(NX)], const float (&pb)[NX],
                                              float (&P)[nsym(NX)], float (&p)[NX], Shared &sh) {
@@ -992,7 +1001,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
 #pragma unroll
             for (int t = 0; t < NU; ++t) v += Qux[t][a] * Kn[t][b];
             P[sidx<NX>(a, b)] = v;
-            V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
+            if (STORE_PV) V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
         }
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
@@ -1000,7 +1009,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
 #pragma unroll
         for (int t = 0; t < NU; ++t) v += Qux[t][a] * kn[t];
         p[a] = v;
-        V.p[(size_t)a * np + i] = v;
+        if (STORE_PV) V.p[(size_t)a * np + i] = v;
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
@@ -1328,6 +1337,476 @@ __device__ void forward_path(const ProbRec &R, const View<NX> &V, float *stg, in
     __syncthreads();
 }
 
+
+/* ------------------------------------------------------------------ scan sweeps (Sec. III-B) */
+/* The tree LQR of Sec. III-B with the sweeps' depth cut from N + 1 dependent steps to a logarithm
+ * of it (sweep variant 4).  Backward: along every non-branching segment the value functions come
+ * from an inclusive suffix scan of conditional value functions (CVFs, Eq. sol_min) with the
+ * combination of Eq. (comb_rule); a node with several children takes the tree Riccati step of
+ * Eq. (tree_Riccati) from its children (where the one-step CVF would couple the children, the
+ * separable form of Eq. tree_CVF holds only along non-branching segments), and segments are
+ * processed wave by wave from the leaves.  Forward: pointer jumping over the closed-loop affine
+ * maps dx_m = (A_n + B_n K_n) dx_n + (d_m + B_n k_n) (Eq. forward_comb_rule) on the tree itself, so
+ * that every node composes the maps of its ancestors in ceil(log2 depth) rounds. */
+
+/* Row offsets of the fields of a CVF element: V(x_k, x_i) = max_lam 1/2 x_k'P x_k + p'x_k
+ * - 1/2 lam'C lam + lam'(x_i - A x_k - c). */
+template <int NX>
+struct Cvf {
+    static constexpr int A = 0, c = NX * NX, C = NX * NX + NX, P = NX * NX + NX + nsym(NX),
+                         p = NX * NX + NX + 2 * nsym(NX);
+};
+
+/* One-step CVF of node i with the single child m, at position f of buffer S (M = 0 and a diagonal
+ * R here): C = B R^-1 B', A~ = A, c~ = d_m - B R^-1 r, P~ = Q, p~ = q. */
+template <int NX, int MODEL>
+__device__ __forceinline__ void cvf_step(const ProbRec &R, const View<NX> &V, int i, int m, float *S, int f,
+                                         Shared &sh) {
+    const int np = V.np;
+    RicIn<NX> in;
+    ric_load<NX, MODEL>(V, i, in);
+    float ir[NU];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        const float h = in.w * R.Rw[a] + in.hr[a];
+        if (!(h > 0.f)) sh.flag = 1;
+        ir[a] = 1.f / h;
+    }
+    float dm[NX];
+    V.load_x(V.d, m, dm);
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+#pragma unroll
+        for (int b = a; b < NX; ++b) {
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NU; ++t) v += in.B[a][t] * ir[t] * in.B[b][t];
+            S[(size_t)(Cvf<NX>::C + sidx<NX>(a, b)) * np + f] = v;
+            float qv = (a == b) ? in.w * R.Qw[a] : 0.f;
+            if (a == 0 && b == 0) qv += in.hq[0];
+            if (a == 0 && b == 1) qv += in.hq[1];
+            if (a == 1 && b == 1) qv += in.hq[2];
+            S[(size_t)(Cvf<NX>::P + sidx<NX>(a, b)) * np + f] = qv;
+        }
+#pragma unroll
+        for (int b = 0; b < NX; ++b) S[(size_t)(Cvf<NX>::A + a * NX + b) * np + f] = in.A[a][b];
+        float cv = dm[a];
+#pragma unroll
+        for (int t = 0; t < NU; ++t) cv -= in.B[a][t] * ir[t] * in.r[t];
+        S[(size_t)(Cvf<NX>::c + a) * np + f] = cv;
+        S[(size_t)(Cvf<NX>::p + a) * np + f] = in.q[a];
+    }
+}
+
+/* The element of a segment's end: the value function 1/2 x'Px + p'x itself (A = C = 0, c = 0). */
+template <int NX>
+__device__ __forceinline__ void cvf_end(const View<NX> &V, float *S, int f, const float (&P)[nsym(NX)],
+                                        const float (&p)[NX]) {
+    const int np = V.np;
+#pragma unroll
+    for (int e = 0; e < NX * NX + NX + nsym(NX); ++e) S[(size_t)e * np + f] = 0.f;
+#pragma unroll
+    for (int e = 0; e < nsym(NX); ++e) S[(size_t)(Cvf<NX>::P + e) * np + f] = P[e];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) S[(size_t)(Cvf<NX>::p + a) * np + f] = p[a];
+}
+
+template <int NX>
+__device__ __forceinline__ void cvf_copy(const View<NX> &V, const float *S, int f, float *O) {
+    const int np = V.np;
+#pragma unroll
+    for (int e = 0; e < cvf_rows(NX); ++e) O[(size_t)e * np + f] = S[(size_t)e * np + f];
+}
+
+/* LU factors of an NX x NX matrix with partial pivoting, in registers (indices fixed at compile
+ * time; the pivot choice only selects between register values). */
+template <int NX>
+struct Lu {
+    float M[NX][NX], id[NX];
+    int piv[NX];
+    __device__ __forceinline__ bool factor() {
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+            int pr = k;
+            float best = fabsf(M[k][k]);
+#pragma unroll
+            for (int r = k + 1; r < NX; ++r) {
+                const float v = fabsf(M[r][k]);
+                if (v > best) {
+                    best = v;
+                    pr = r;
+                }
+            }
+            piv[k] = pr;
+#pragma unroll
+            for (int r = k + 1; r < NX; ++r)
+                if (pr == r) {
+#pragma unroll
+                    for (int c = 0; c < NX; ++c) {
+                        const float t = M[k][c];
+                        M[k][c] = M[r][c];
+                        M[r][c] = t;
+                    }
+                }
+            ok = ok && best > 0.f && best < INFINITY;
+            id[k] = 1.f / M[k][k];
+#pragma unroll
+            for (int r = k + 1; r < NX; ++r) {
+                const float l = M[r][k] * id[k];
+                M[r][k] = l;
+#pragma unroll
+                for (int c = k + 1; c < NX; ++c) M[r][c] -= l * M[k][c];
+            }
+        }
+        return ok;
+    }
+    /* x <- M^-1 x */
+    __device__ __forceinline__ void solve(float (&x)[NX]) const {
+#pragma unroll
+        for (int k = 0; k < NX; ++k)
+#pragma unroll
+            for (int r = k + 1; r < NX; ++r)
+                if (piv[k] == r) {
+                    const float t = x[k];
+                    x[k] = x[r];
+                    x[r] = t;
+                }
+#pragma unroll
+        for (int r = 1; r < NX; ++r)
+#pragma unroll
+            for (int c = 0; c < r; ++c) x[r] -= M[r][c] * x[c];
+#pragma unroll
+        for (int r = NX - 1; r >= 0; --r) {
+#pragma unroll
+            for (int c = r + 1; c < NX; ++c) x[r] -= M[r][c] * x[c];
+            x[r] *= id[r];
+        }
+    }
+    /* x <- M^-T x */
+    __device__ __forceinline__ void solve_t(float (&x)[NX]) const {
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+#pragma unroll
+            for (int c = 0; c < r; ++c) x[r] -= M[c][r] * x[c];
+            x[r] *= id[r];
+        }
+#pragma unroll
+        for (int r = NX - 2; r >= 0; --r)
+#pragma unroll
+            for (int c = r + 1; c < NX; ++c) x[r] -= M[c][r] * x[c];
+#pragma unroll
+        for (int k = NX - 1; k >= 0; --k)
+#pragma unroll
+            for (int r = k + 1; r < NX; ++r)
+                if (piv[k] == r) {
+                    const float t = x[k];
+                    x[k] = x[r];
+                    x[r] = t;
+                }
+    }
+};
+
+/* The combination of Eq. (comb_rule), e1 at position f1 (from x_k to x_j) followed by e2 at f2
+ * (from x_j to x_i), written at position f1 of O; with E = I + C1 P2 and the signs of the CVF form of
+ * Eq. (sol_min): A = A2 E^-1 A1, c = A2 E^-1 (c1 - C1 p2) + c2, C = A2 E^-1 C1 A2' + C2,
+ * P = A1' E^-T P2 A1 + P1, p = A1' E^-T (p2 + P2 c1) + p1. */
+template <int NX>
+__device__ void cvf_combine(const View<NX> &V, const float *S, int f1, int f2, float *O, Shared &sh) {
+    using F = Cvf<NX>;
+    const int np = V.np;
+    auto at = [&](int row, int f) { return S[(size_t)row * np + f]; };
+    float C1[nsym(NX)], P2[nsym(NX)];
+#pragma unroll
+    for (int e = 0; e < nsym(NX); ++e) {
+        C1[e] = at(F::C + e, f1);
+        P2[e] = at(F::P + e, f2);
+    }
+    Lu<NX> E;
+#pragma unroll
+    for (int a = 0; a < NX; ++a)
+#pragma unroll
+        for (int b = 0; b < NX; ++b) {
+            float v = (a == b) ? 1.f : 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += C1[sidx<NX>(a, t)] * P2[sidx<NX>(t, b)];
+            E.M[a][b] = v;
+        }
+    if (!E.factor()) sh.flag = 1;
+    {
+        float A2[NX][NX];
+#pragma unroll
+        for (int a = 0; a < NX; ++a)
+#pragma unroll
+            for (int b = 0; b < NX; ++b) A2[a][b] = at(F::A + a * NX + b, f2);
+        /* A = A2 E^-1 A1, column by column */
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+            float x[NX];
+#pragma unroll
+            for (int a = 0; a < NX; ++a) x[a] = at(F::A + a * NX + j, f1);
+            E.solve(x);
+#pragma unroll
+            for (int a = 0; a < NX; ++a) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += A2[a][t] * x[t];
+                O[(size_t)(F::A + a * NX + j) * np + f1] = v;
+            }
+        }
+        /* C = A2 E^-1 C1 A2' + C2, column j from C1 A2[j, :]' (upper triangle stored) */
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+            float x[NX];
+#pragma unroll
+            for (int a = 0; a < NX; ++a) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += C1[sidx<NX>(a, t)] * A2[j][t];
+                x[a] = v;
+            }
+            E.solve(x);
+#pragma unroll
+            for (int a = 0; a <= j; ++a) {
+                float v = at(F::C + sidx<NX>(a, j), f2);
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += A2[a][t] * x[t];
+                O[(size_t)(F::C + sidx<NX>(a, j)) * np + f1] = v;
+            }
+        }
+        /* c = A2 E^-1 (c1 - C1 p2) + c2 */
+        float x[NX];
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+            float v = at(F::c + a, f1);
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v -= C1[sidx<NX>(a, t)] * at(F::p + t, f2);
+            x[a] = v;
+        }
+        E.solve(x);
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+            float v = at(F::c + a, f2);
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += A2[a][t] * x[t];
+            O[(size_t)(F::c + a) * np + f1] = v;
+        }
+    }
+    {
+        float A1[NX][NX];
+#pragma unroll
+        for (int a = 0; a < NX; ++a)
+#pragma unroll
+            for (int b = 0; b < NX; ++b) A1[a][b] = at(F::A + a * NX + b, f1);
+        /* P = A1' E^-T P2 A1 + P1, column j from P2 A1[:, j] (upper triangle stored) */
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+            float y[NX];
+#pragma unroll
+            for (int a = 0; a < NX; ++a) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += P2[sidx<NX>(a, t)] * A1[t][j];
+                y[a] = v;
+            }
+            E.solve_t(y);
+#pragma unroll
+            for (int a = 0; a <= j; ++a) {
+                float v = at(F::P + sidx<NX>(a, j), f1);
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += A1[t][a] * y[t];
+                O[(size_t)(F::P + sidx<NX>(a, j)) * np + f1] = v;
+            }
+        }
+        /* p = A1' E^-T (p2 + P2 c1) + p1 */
+        float y[NX];
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+            float v = at(F::p + a, f2);
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += P2[sidx<NX>(a, t)] * at(F::c + t, f1);
+            y[a] = v;
+        }
+        E.solve_t(y);
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+            float v = at(F::p + a, f1);
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += A1[t][a] * y[t];
+            O[(size_t)(F::p + a) * np + f1] = v;
+        }
+    }
+}
+
+/* Backward sweep by scans (variant 4): wave by wave, the segments' end elements (a leaf's value or
+ * a branch node's tree Riccati step), the one-step CVFs of the segment members, the inclusive suffix
+ * scan by span doubling (Hillis-Steele), and the members' value functions; then the feedback laws of
+ * the single-child nodes from their children's value functions, all nodes at once. */
+template <int NX, int MODEL>
+__device__ void backward_scan(const ProbRec &R, const View<NX> &V, Shared &sh) {
+    constexpr int NS = nsym(NX);
+    const int tid = threadIdx.x, nt = blockDim.x, W = R.n_waves, np = V.np;
+    for (int w = 0; w < W; ++w) {
+        const int f0 = V.wave[w], f1 = V.wave[w + 1], span = V.wave[W + 1 + w];
+        for (int f = f0 + tid; f < f1; f += nt) {
+            const int i = V.fnode[f];
+            if (V.fend[f] == f) {
+                float P[NS], p[NX];
+                const int nch = V.nchild[i];
+                if (nch == 0) {
+                    leaf_value<NX>(R, V, i, P, p);
+                } else {
+                    float Pb[NS], pb[NX];
+#pragma unroll
+                    for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
+#pragma unroll
+                    for (int a = 0; a < NX; ++a) pb[a] = 0.f;
+                    const int fc = V.fchild[i];
+                    for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
+                    RicIn<NX> in;
+                    ric_load<NX, MODEL>(V, i, in);
+                    riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
+                }
+                cvf_end<NX>(V, V.CV0, f, P, p);
+            } else {
+                cvf_step<NX, MODEL>(R, V, i, V.fchild[i], V.CV0, f, sh);
+            }
+        }
+        __syncthreads();
+        float *cur = V.CV0, *nxt = V.CV1;
+        for (int d = 1; d < span; d *= 2) {
+            for (int f = f0 + tid; f < f1; f += nt) {
+                if (f + d <= V.fend[f]) cvf_combine<NX>(V, cur, f, f + d, nxt, sh);
+                else cvf_copy<NX>(V, cur, f, nxt);
+            }
+            __syncthreads();
+            float *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        for (int f = f0 + tid; f < f1; f += nt) {
+            if (V.fend[f] == f) continue;
+            const int i = V.fnode[f];
+#pragma unroll
+            for (int e = 0; e < NS; ++e) V.P[(size_t)e * np + i] = cur[(size_t)(Cvf<NX>::P + e) * np + f];
+#pragma unroll
+            for (int a = 0; a < NX; ++a) V.p[(size_t)a * np + i] = cur[(size_t)(Cvf<NX>::p + a) * np + f];
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < V.n; i += nt) {
+        if (V.nchild[i] != 1) continue;
+        float Pb[NS], pb[NX], P[NS], p[NX];
+#pragma unroll
+        for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
+#pragma unroll
+        for (int a = 0; a < NX; ++a) pb[a] = 0.f;
+        add_child_mem<NX>(V, V.fchild[i], Pb, pb);
+        RicIn<NX> in;
+        ric_load<NX, MODEL>(V, i, in);
+        riccati_node<NX, MODEL, false>(R, V, i, in, Pb, pb, P, p, sh);
+    }
+}
+
+/* Forward sweep by pointer jumping (variant 4): every non-root node m holds the closed-loop map
+ * G_m: dx_a -> dx_m from an ancestor a (first its parent); each round composes G_m with G_a and
+ * replaces a by a's ancestor, until every map starts at the root, where dx_0 = 0 and so dx_m = c_m.
+ * Then du_n = K_n dx_n + k_n. */
+template <int NX, int MODEL>
+__device__ void forward_jump(const ProbRec &R, const View<NX> &V) {
+    using F = Cvf<NX>;
+    const int tid = threadIdx.x, nt = blockDim.x, np = V.np, n = V.n;
+    for (int m = 1 + tid; m < n; m += nt) {
+        const int a = V.parent[m];
+        FwdIn<NX> in;
+        fwd_load<NX, MODEL>(V, m, a, in);   /* d_m, A_a, B_a; K, k of m are not used here */
+        float Ka[NU][NX], ka[NU];
+#pragma unroll
+        for (int t = 0; t < NU; ++t) {
+            ka[t] = V.k[(size_t)t * np + a];
+#pragma unroll
+            for (int b = 0; b < NX; ++b) Ka[t][b] = V.K[(size_t)(t * NX + b) * np + a];
+        }
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+#pragma unroll
+            for (int b = 0; b < NX; ++b) {
+                float v = in.A[r][b];
+#pragma unroll
+                for (int t = 0; t < NU; ++t) v += in.B[r][t] * Ka[t][b];
+                V.CV0[(size_t)(F::A + r * NX + b) * np + m] = v;
+            }
+            float v = in.d[r];
+#pragma unroll
+            for (int t = 0; t < NU; ++t) v += in.B[r][t] * ka[t];
+            V.CV0[(size_t)(F::c + r) * np + m] = v;
+        }
+        V.JA0[m] = __int_as_float(a);
+    }
+    __syncthreads();
+    float *cur = V.CV0, *nxt = V.CV1, *jc = V.JA0, *jn = V.JA1;
+    for (int span = 1; span < R.n_stage; span *= 2) {
+        for (int m = 1 + tid; m < n; m += nt) {
+            const int a = __float_as_int(jc[m]);
+            if (a == 0) {
+#pragma unroll
+                for (int e = 0; e < NX * NX + NX; ++e) nxt[(size_t)e * np + m] = cur[(size_t)e * np + m];
+                jn[m] = jc[m];
+                continue;
+            }
+            float Am[NX][NX], cm[NX], Aa[NX][NX], ca[NX];
+#pragma unroll
+            for (int r = 0; r < NX; ++r) {
+#pragma unroll
+                for (int b = 0; b < NX; ++b) {
+                    Am[r][b] = cur[(size_t)(F::A + r * NX + b) * np + m];
+                    Aa[r][b] = cur[(size_t)(F::A + r * NX + b) * np + a];
+                }
+                cm[r] = cur[(size_t)(F::c + r) * np + m];
+                ca[r] = cur[(size_t)(F::c + r) * np + a];
+            }
+#pragma unroll
+            for (int r = 0; r < NX; ++r) {
+#pragma unroll
+                for (int b = 0; b < NX; ++b) {
+                    float v = 0.f;
+#pragma unroll
+                    for (int t = 0; t < NX; ++t) v += Am[r][t] * Aa[t][b];
+                    nxt[(size_t)(F::A + r * NX + b) * np + m] = v;
+                }
+                float v = cm[r];
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += Am[r][t] * ca[t];
+                nxt[(size_t)(F::c + r) * np + m] = v;
+            }
+            jn[m] = jc[a];
+        }
+        __syncthreads();
+        float *t = cur;
+        cur = nxt;
+        nxt = t;
+        t = jc;
+        jc = jn;
+        jn = t;
+    }
+    for (int i = tid; i < n; i += nt) {
+        float dxv[NX], du0 = 0.f, du1 = 0.f;
+#pragma unroll
+        for (int r = 0; r < NX; ++r) dxv[r] = i ? cur[(size_t)(F::c + r) * np + i] : 0.f;
+        V.store_x(V.dx, i, dxv);
+        if (V.nchild[i]) {
+            du0 = V.k[i];
+            du1 = V.k[(size_t)np + i];
+#pragma unroll
+            for (int b = 0; b < NX; ++b) {
+                du0 += V.K[(size_t)b * np + i] * dxv[b];
+                du1 += V.K[(size_t)(NX + b) * np + i] * dxv[b];
+            }
+        }
+        V.du[i] = du0;
+        V.du[(size_t)np + i] = du1;
+    }
+}
 
 /* ------------------------------------------------------------------ cooperative (8-lane) per-path sweeps */
 /* A group of GL lanes handles one root-to-leaf path.  In the backward step lane j owns column j of
@@ -1731,7 +2210,7 @@ __device__ __forceinline__ void apply_step_serial(const View<NX> &V, int i, floa
 }
 
 /* ------------------------------------------------------------------ the per-problem solver */
-template <int NX, int MODEL>
+template <int NX, int MODEL, bool SCAN>
 __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
                               float *fs, Stats *stat, const KOpts &O, Shared &sh, int32_t *tab, int tab_cap,
                               float *stg, int stg_ld) {
@@ -1780,7 +2259,10 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
     /* sweeps: 1 level-synchronous, 2 (default) per-path with one thread per path, 3 per-path with 8 lanes */
     /* automatic choice by tree shape: one thread per scenario path while the paths fit the block,
      * else stage by stage (a thread would otherwise walk several paths one after another) */
-    const int variant = (O.variant == 1 || O.variant == 3) ? O.variant
+    /* 4 (scan sweeps) has its own kernel instance, so that the registers its CVF combinations need
+     * leave the others' alone; 5 is the per-path backward sweep with the pointer-jumping forward one */
+    const int variant = SCAN ? 4
+                        : (O.variant == 1 || O.variant == 3 || O.variant == 5) ? O.variant
                         : (O.variant == 2 || R.n_paths <= nt) ? 2 : 1;
 
     while (outer < O.max_outer) {
@@ -1954,8 +2436,9 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
             t0 = clock64();
             if (tid == 0) sh.flag = 0;
             __syncthreads();
-            if (variant == 3) backward_coop<NX, MODEL>(R, V, sh);
-            else if (variant == 2) backward_path<NX, MODEL>(R, V, sh);
+            if constexpr (SCAN) backward_scan<NX, MODEL>(R, V, sh);
+            else if (variant == 3) backward_coop<NX, MODEL>(R, V, sh);
+            else if (variant == 2 || variant == 5) backward_path<NX, MODEL>(R, V, sh);
             else backward_level<NX, MODEL>(R, V, sh);
             __syncthreads();
             c_bwd += clock64() - t0;
@@ -1967,7 +2450,8 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
             /* ===== forward: linear rollout from the root, QP multipliers */
             t0 = clock64();
             float dir[3] = {0.f, 0.f, 0.f};   /* grad'dz, dz'W dz, (dlam - lam)'d */
-            if (variant == 3) forward_coop<NX, MODEL>(R, V);
+            if (SCAN || variant == 5) forward_jump<NX, MODEL>(R, V);
+            else if (variant == 3) forward_coop<NX, MODEL>(R, V);
             else if (variant == 2) forward_path<NX, MODEL>(R, V, stg, stg_ld);
             else forward_level<NX, MODEL>(R, V);
             multipliers_and_directions<NX, MODEL>(R, V, dir);
@@ -2174,7 +2658,7 @@ done:
 }
 
 /* One kernel per dynamics model, so that each carries only its own code and registers. */
-template <int MODEL, int BLOCK>
+template <int MODEL, int BLOCK, bool SCAN = false>
 __global__ void __launch_bounds__(BLOCK, BLOCK <= BATCH_BLOCK ? 2 : 1) bmpc_solve_kernel(KernelArgs args) {
     constexpr int NX = MODEL == 1 ? 6 : 4;
     __shared__ Shared sh;
@@ -2198,7 +2682,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK <= BATCH_BLOCK ? 2 : 1) bmpc_solv
         }
         __syncthreads();
         const ProbRec &R = rec_s;
-        solve_problem<NX, MODEL>(R, args.ibase + R.off_int, args.inbase + R.off_in, args.warmbase + R.off_warm,
+        solve_problem<NX, MODEL, SCAN>(R, args.ibase + R.off_int, args.inbase + R.off_in, args.warmbase + R.off_warm,
                                  args.outbase + R.off_out, args.scr + R.off_scr, args.stats + pid, args.opts, sh,
                                  tab_s, args.tab_ints, args.stg_ld ? stg : nullptr, args.stg_ld);
     }
@@ -2579,7 +3063,13 @@ cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream
 /* Launch helper used by the host API: `args.order` lists problems of `model` only. */
 /* The kernel instance of a model for a block size. */
 using SolveFn = void (*)(KernelArgs);
-SolveFn solve_fn(int model, int block) {
+SolveFn solve_fn(int model, int block, bool scan = false) {
+    if (scan) {   /* sweep variant 4: one instance per model, up to 512 threads per problem */
+        if (model == 0) return bmpc_solve_kernel<0, MAX_BLOCK, true>;
+        if (model == 1) return bmpc_solve_kernel<1, MAX_BLOCK, true>;
+        if (model == 2) return bmpc_solve_kernel<2, MAX_BLOCK, true>;
+        return bmpc_solve_kernel<3, MAX_BLOCK, true>;
+    }
     const bool big = block > BATCH_BLOCK;
     if (model == 0) return big ? bmpc_solve_kernel<0, MAX_BLOCK> : bmpc_solve_kernel<0, BATCH_BLOCK>;
     if (model == 1) return big ? bmpc_solve_kernel<1, MAX_BLOCK> : bmpc_solve_kernel<1, BATCH_BLOCK>;
@@ -2588,7 +3078,7 @@ SolveFn solve_fn(int model, int block) {
 }
 
 cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, size_t smem, cudaStream_t stream) {
-    solve_fn(model, block)<<<grid, block, smem, stream>>>(args);
+    solve_fn(model, block, args.opts.variant == 4)<<<grid, block, smem, stream>>>(args);
     return cudaGetLastError();
 }
 
@@ -2623,12 +3113,15 @@ cudaError_t prepare_solve(int model, size_t smem) {
                                          (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(solve_fn(model, MAX_BLOCK), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(solve_fn(model, MAX_BLOCK, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
     if (e == cudaSuccess) granted[model] = smem;
     return e;
 }
 
-cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_fn(model, block), block, smem);
+cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm, bool scan) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_fn(model, block, scan), block, smem);
 }
 
 }  // namespace bmpc

@@ -25,7 +25,8 @@ __host__ __device__ constexpr int nsym(int nx) { return nx * (nx + 1) / 2; }
 /* One record per problem; 16-byte aligned, plain data. */
 struct alignas(16) ProbRec {
     int32_t n, npad, nx, nu, model, n_obs, nc, box_on, lane_on, n_stage, has_warm, n_paths;
-    int32_t n_bstage, rsv0, rsv1, rsv2;  /* n_bstage: distinct stages holding branch nodes */
+    int32_t n_bstage, n_waves, rsv1, rsv2;  /* n_bstage: distinct stages holding branch nodes;
+                                              n_waves: waves of the segment scans (variant 4) */
     int64_t off_int;   /* int32 elements from the int region base      */
     int64_t off_in;    /* float elements from the input region base    */
     int64_t off_warm;  /* float elements from the warm-start region base */
@@ -45,17 +46,24 @@ static_assert(sizeof(ProbRec) % 16 == 0, "the solver copies a record to shared m
 /* int region of one problem (int32 elements):
  *   node rows (npad each): parent, nchild, fchild (first child), stage, leaf (first leaf
  *   descendant), owner (index of the path of that leaf; the path that processes the node in
- *   the per-path sweeps);
+ *   the per-path sweeps), fnode, fend (the segment order of the scan sweeps, below);
  *   stage_start [n_stage + 1]   first node of every stage (level order);
  *   bstage      [n_bstage]      stages holding nodes with more than one child, descending;
  *   ptab        [n_paths][n_stage]  node of every root-to-leaf path at every stage (-1 past
  *                                   the path's leaf);
- *   pdepth, ptop [n_paths]      stage of the path's leaf, first stage the path owns.
+ *   pdepth, ptop [n_paths]      stage of the path's leaf, first stage the path owns;
+ *   wave        [n_waves + 1] [n_waves]  first position of every wave in the segment order, then
+ *                                   the longest segment of every wave (in nodes).
+ * Segments (scan sweeps, Sec. III-B): a segment is a maximal chain of single-child nodes together
+ * with the node that ends it (a leaf or a node with several children).  Its wave is 0 for a leaf's
+ * segment, else one more than the largest wave among the segments of the end node's children.  The
+ * segment order lists the nodes wave by wave, segment by segment, each segment from its top to its
+ * end: fnode[f] is the node at position f, fend[f] the position of its segment's end.
  * Every block is padded to a multiple of 32 elements. */
 struct IntOff {
-    int64_t parent, nchild, fchild, stage, leaf, owner, sstart, bstage, ptab, pdepth, ptop, total;
+    int64_t parent, nchild, fchild, stage, leaf, owner, fnode, fend, sstart, bstage, ptab, pdepth, ptop, wave, total;
 };
-__host__ __device__ inline IntOff int_off(int npad, int n_stage, int n_paths) {
+__host__ __device__ inline IntOff int_off(int npad, int n_stage, int n_paths, int n_waves = 0) {
     IntOff o;
     o.parent = 0;
     o.nchild = npad;
@@ -63,12 +71,15 @@ __host__ __device__ inline IntOff int_off(int npad, int n_stage, int n_paths) {
     o.stage = 3LL * npad;
     o.leaf = 4LL * npad;
     o.owner = 5LL * npad;
-    o.sstart = 6LL * npad;
+    o.fnode = 6LL * npad;
+    o.fend = 7LL * npad;
+    o.sstart = 8LL * npad;
     o.bstage = o.sstart + round_up(n_stage + 1, 32);
     o.ptab = o.bstage + round_up(n_stage + 1, 32);
     o.pdepth = o.ptab + round_up(n_paths * n_stage, 32);
     o.ptop = o.pdepth + round_up(n_paths, 32);
-    o.total = o.ptop + round_up(n_paths, 32);
+    o.wave = o.ptop + round_up(n_paths, 32);
+    o.total = o.wave + round_up(2 * n_waves + 1, 32);
     return o;
 }
 
@@ -76,7 +87,7 @@ __host__ __device__ inline IntOff int_off(int npad, int n_stage, int n_paths) {
  * memory per problem when they fit. */
 __host__ __device__ inline int64_t table_ints(int npad, int n_stage, int n_paths) {
     const IntOff o = int_off(npad, n_stage, n_paths);
-    return o.total - o.sstart;
+    return o.wave - o.sstart;
 }
 
 /* input region: xref[nx] weight[1] obs[6*n_obs] (rows of npad).  Per obstacle the rows hold the
@@ -124,12 +135,18 @@ __host__ __device__ inline OutRows out_rows(int nx, int nc) {
     return r;
 }
 
+/* Rows of one conditional value function (CVF, Sec. III-B) element of the scan sweeps: A[nx*nx]
+ * c[nx] C[nsym] P[nsym] p[nx] (C and P symmetric, packed). */
+__host__ __device__ constexpr int cvf_rows(int nx) { return nx * nx + 2 * nx + 2 * nsym(nx); }
+
 /* scratch: A[nx*nx] B[nx*nu] f[nx] d[nx] q[nx] r[nu] hq[3] hr[nu] K[nu*nx] k[nu] P[nsym] p[nx]
- *          dx[nx] du[nu] lq[nx] nv[3] xl[2] ul[nu]
+ *          dx[nx] du[nu] lq[nx] nv[3] xl[2] ul[nu] cv[2 * cvf_rows] ja[2]
  * xl, ul: low-order parts of the compensated iterate (positions X, Y of the state deviation and the
- * inputs): the iterate is xi + xl, u + ul, each pair a float and its rounding remainder. */
+ * inputs): the iterate is xi + xl, u + ul, each pair a float and its rounding remainder.
+ * cv: two buffers of scan elements, indexed by position in the segment order (backward) or by node
+ * (forward: closed-loop maps in the A, c rows); ja: two rows of ancestor indices (forward). */
 struct ScrRows {
-    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, xl, ul, total;
+    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, xl, ul, cv, ja, total;
 };
 __host__ __device__ inline ScrRows scr_rows(int nx) {
     ScrRows s;
@@ -151,7 +168,9 @@ __host__ __device__ inline ScrRows scr_rows(int nx) {
     s.nv = s.lq + nx;
     s.xl = s.nv + 3;
     s.ul = s.xl + 2;
-    s.total = s.ul + NU;
+    s.cv = s.ul + NU;
+    s.ja = s.cv + 2 * cvf_rows(nx);
+    s.total = s.ja + 2;
     return s;
 }
 
