@@ -58,6 +58,9 @@ def workload(name: str, batch: int, rank: int = 0):
         return [scenes.config3(rank * batch + i) for i in range(batch)]
     if name == "unicycle":
         return [scenes.unicycle(rank * batch + i) for i in range(batch)]
+    if name.startswith("mass_spring"):   # mass_spring or mass_springNr: per-branch spring constants
+        nr = int(name[len("mass_spring"):] or 5)
+        return [scenes.mass_spring(rank * batch + i, N=30, Nr=nr, constrained=True) for i in range(batch)]
     raise ValueError(name)
 
 
@@ -545,7 +548,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=["config1", "config2", "config3", "config4", "unicycle"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=["config1", "config2", "config3", "config4", "unicycle", "mass_spring1",
+                                                            "mass_spring3", "mass_spring5", "mass_spring7", "mass_spring9"])
     ap.add_argument("--batch", type=int, default=DEFAULT_BATCH)
     ap.add_argument("--single", type=int, default=0, metavar="P",
                     help="single-problem latency of the first P problems of the workload (one per launch)")

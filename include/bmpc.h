@@ -71,6 +71,12 @@ typedef struct {
     int32_t lane_on;        /* lateral lane rows on non-root nodes */
     float dt;               /* discretisation step */
     float params[10];       /* L, m, Iz, lf, lr, Cf, Cr, vmin, veps, n_sub (RK4 substeps) */
+    int32_t edge_dynamics;  /* 1: model 2 with its own (A_m, B_m) on every tree edge, x_m = A_m x_p(m) +
+                               B_m u_p(m) (per-branch models, the mass-spring trees of Sec. V-A);
+                               0: one model per node, shared by its children.  Per-edge problems
+                               take sweep variants 0-2 (BMPC_ERR_INVALID otherwise), upload through
+                               bmpc_set_problems (not the flat path) and have no device warm-start
+                               shift or learned start. */
 } bmpc_tree_desc;
 
 /* Problem data of one tree (host pointers, copied by bmpc_set_problems).
@@ -87,14 +93,17 @@ typedef struct {
     float u_lo[BMPC_NU], u_hi[BMPC_NU];
     float lane_lo, lane_hi;
     const float *obs;       /* [num_nodes][n_obs][5]: cx, cy, heading, a, b (may be NULL if n_obs = 0) */
-    const float *Alin;      /* [nx][nx] row-major, model 2 only */
-    const float *Blin;      /* [nx][nu] row-major, model 2 only */
+    const float *Alin;      /* [nx][nx] row-major, model 2 only (not read with edge_dynamics) */
+    const float *Blin;      /* [nx][nu] row-major, model 2 only (not read with edge_dynamics) */
     /* optional warm start; all four NULL = cold start of Sec. V-B (x linearly interpolated
        from x0 to the final reference of the node's first leaf, u = lam = y = 0) */
     const float *warm_x;    /* [num_nodes][nx] */
     const float *warm_u;    /* [num_nodes][nu] */
     const float *warm_lam;  /* [num_nodes][nx] */
     const float *warm_y;    /* [num_nodes][nc], nc = 2*nu*box_on + n_obs + 2*lane_on */
+    const float *Aedge;     /* with edge_dynamics: [num_nodes][nx][nx], row m the edge into node m (row 0
+                               unused); else NULL */
+    const float *Bedge;     /* with edge_dynamics: [num_nodes][nx][nu], likewise */
 } bmpc_problem;
 
 /* Algorithm 1 constants (defaults: the values of Sec. V-B plus the readings of the oracle). */

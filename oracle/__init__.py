@@ -37,7 +37,7 @@ class Problem(C.Structure):
                 ("parent", _ip), ("dt", C.c_double), ("params", _dp), ("x0", _dp),
                 ("xref", _dp), ("weight", _dp), ("Qw", _dp), ("QNw", _dp), ("Rw", _dp),
                 ("u_lo", _dp), ("u_hi", _dp), ("lane_lo", C.c_double), ("lane_hi", C.c_double),
-                ("obs", _dp), ("Alin", _dp), ("Blin", _dp)]
+                ("obs", _dp), ("Alin", _dp), ("Blin", _dp), ("Aedge", _dp), ("Bedge", _dp)]
 
 
 class Opts(C.Structure):
@@ -99,13 +99,17 @@ class _Marshal:
     def __init__(self, p):
         self.keep = {k: _d(p[k]) for k in ("params", "x0", "xref", "weight", "Qw", "QNw", "Rw",
                                            "u_lo", "u_hi", "obs", "Alin", "Blin")}
+        edge = p.get("Aedge") is not None
+        if edge:
+            self.keep["Aedge"], self.keep["Bedge"] = _d(p["Aedge"]), _d(p["Bedge"])
         self.parent = np.ascontiguousarray(p["parent"], dtype=np.int32)
         k = self.keep
         self.s = Problem(p["n"], p["nx"], p["nu"], p["model"], p["n_obs"], p["box_on"],
                          p["lane_on"], self.parent.ctypes.data_as(_ip), p["dt"], _ptr(k["params"]),
                          _ptr(k["x0"]), _ptr(k["xref"]), _ptr(k["weight"]), _ptr(k["Qw"]),
                          _ptr(k["QNw"]), _ptr(k["Rw"]), _ptr(k["u_lo"]), _ptr(k["u_hi"]),
-                         p["lane_lo"], p["lane_hi"], _ptr(k["obs"]), _ptr(k["Alin"]), _ptr(k["Blin"]))
+                         p["lane_lo"], p["lane_hi"], _ptr(k["obs"]), _ptr(k["Alin"]), _ptr(k["Blin"]),
+                         _ptr(k["Aedge"]) if edge else None, _ptr(k["Bedge"]) if edge else None)
 
 
 def default_opts(**kw) -> Opts:
@@ -181,8 +185,10 @@ def constraints(p, node, is_leaf, x, u):
     return g[:nc], Jx[:nc], Ju[:nc], ex[:nc].astype(bool)
 
 
-def tree_lqr(parent, Q, M, R, q, r, A, B, c):
-    """Tree LQR of Eq. (lqr_tree_approx): returns K, k, P, p, dx, du, lam."""
+def tree_lqr(parent, Q, M, R, q, r, A, B, c, edge=False):
+    """Tree LQR of Eq. (lqr_tree_approx): returns K, k, P, p, dx, du, lam.  A, B per parent (row i: the
+    Jacobians of node i's dynamics, shared by its children) or, with edge=True, per edge (row m: the
+    edge into node m)."""
     parent = np.ascontiguousarray(parent, dtype=np.int32)
     n = parent.shape[0]
     nx, nu = np.shape(B)[1], np.shape(B)[2]
@@ -191,13 +197,13 @@ def tree_lqr(parent, Q, M, R, q, r, A, B, c):
     dx, du, lam = np.zeros((n, nx)), np.zeros((n, nu)), np.zeros((n, nx))
     args = [_d(a) for a in (Q, M, R, q, r, A, B, c)]
     rc = lib().orc_tree_lqr(n, parent.ctypes.data_as(_ip), nx, nu, *[_ptr(a) for a in args],
-                            _ptr(K), _ptr(k), _ptr(P), _ptr(pv), _ptr(dx), _ptr(du), _ptr(lam))
+                            _ptr(K), _ptr(k), _ptr(P), _ptr(pv), _ptr(dx), _ptr(du), _ptr(lam), int(edge))
     if rc != 0:
         raise RuntimeError(f"orc_tree_lqr failed: {rc}")
     return K, k, P, pv, dx, du, lam
 
 
-def tree_lqr_scan(parent, Q, M, R, q, r, A, B, c):
+def tree_lqr_scan(parent, Q, M, R, q, r, A, B, c, edge=False):
     """Tree LQR by scans (Sec. III-B: CVF suffix scans along the non-branching segments, tree Riccati
     steps at branch nodes, prefix scans of the closed-loop maps along every path); outputs as
     tree_lqr."""
@@ -209,7 +215,7 @@ def tree_lqr_scan(parent, Q, M, R, q, r, A, B, c):
     dx, du, lam = np.zeros((n, nx)), np.zeros((n, nu)), np.zeros((n, nx))
     args = [_d(a) for a in (Q, M, R, q, r, A, B, c)]
     rc = lib().orc_tree_lqr_scan(n, parent.ctypes.data_as(_ip), nx, nu, *[_ptr(a) for a in args],
-                                 _ptr(K), _ptr(k), _ptr(P), _ptr(pv), _ptr(dx), _ptr(du), _ptr(lam))
+                                 _ptr(K), _ptr(k), _ptr(P), _ptr(pv), _ptr(dx), _ptr(du), _ptr(lam), int(edge))
     if rc != 0:
         raise RuntimeError(f"orc_tree_lqr_scan failed: {rc}")
     return K, k, P, pv, dx, du, lam

@@ -10,7 +10,9 @@
  * Passages followed (paper section / equation / algorithm):
  *   problem             Sec. II-B, Eq. (bmpc): node costs, x_i = f_p(i)(x_p(i), u_p(i)), g <= 0
  *   models              kinematic and dynamic bicycles (the planning scenes), linear (LQ pins),
- *                       unicycle (the constraint benchmark of Sec. V-B)
+ *                       unicycle (the constraint benchmark of Sec. V-B); dynamics per tree edge
+ *                       (x_m = f_m(x_p(m), u_p(m)), the per-branch models of Sec. V-A) for the
+ *                       linear model, per parent otherwise (every child of a node shares its f)
  *   tree LQR            Sec. III-A, Eq. (lqr_tree_approx), Eq. (tree_Riccati),
  *                       Eq. (tree_feedback_laws); forward rollout as in Sec. II-A
  *   tree LQR by scans   Sec. III-B, Eq. (sol_min), Eq. (comb_rule), Eq. (forward_comb_rule):
@@ -66,6 +68,8 @@ typedef struct {
     double lane_lo, lane_hi;
     const double *obs;      /* [n][n_obs][5] cx, cy, heading, a, b */
     const double *Alin, *Blin;
+    const double *Aedge, *Bedge;   /* model 2 only, or NULL: per-edge dynamics [n][nx][nx], [n][nx][nu],
+                                      row m the edge into node m (row 0 unused) */
 } orc_problem;
 
 /* Trace of a solve, for tests that check each decision of Algorithm 1 from outside.  kind 0 (one
@@ -318,6 +322,24 @@ int orc_dynamics(const orc_problem *P, const double *x, const double *u, double 
     return 0;
 }
 
+/* Dynamics of the edge into node m from its parent's (x, u): the per-edge linear model when the
+ * problem has one, else the parent's model (shared by all its children). */
+static int edge_dynamics(const orc_problem *P, int m, const double *x, const double *u, double *xn, double *A,
+                         double *B) {
+    if (P->model == 2 && P->Aedge) {
+        const int nx = P->nx, nu = P->nu;
+        const double *Am = P->Aedge + (size_t)m * nx * nx, *Bm = P->Bedge + (size_t)m * nx * nu;
+        double t[MAXX];
+        matvec(nx, nx, Am, x, xn);
+        matvec(nx, nu, Bm, u, t);
+        for (int i = 0; i < nx; ++i) xn[i] += t[i];
+        if (A) memcpy(A, Am, sizeof(double) * nx * nx);
+        if (B) memcpy(B, Bm, sizeof(double) * nx * nu);
+        return 0;
+    }
+    return orc_dynamics(P, x, u, xn, A, B);
+}
+
 /* ------------------------------------------------------------ tree helpers */
 typedef struct {
     int n;
@@ -409,12 +431,15 @@ int orc_constraints(const orc_problem *P, int node, int is_leaf, const double *x
 /* ------------------------------------------------------------ tree LQR (Sec. III-A) */
 /* Solves the tree LQR problem of Eq. (lqr_tree_approx):
  *   min sum_i 1/2 dx'Q dx + du'M dx + 1/2 du'R du + q'dx + r'du   (leaves: Q, q only)
- *   s.t. dx_m = A_i dx_i + B_i du_i + c_m for m in ch(i), dx_0 = 0.
- * Backward: the modified Riccati recursion of Eq. (tree_Riccati) that sums the child value
- * functions, with the feedback law of Eq. (tree_feedback_laws); forward: the affine rollout
- * along every root-to-leaf path.  lam_m = P_m dx_m + p_m are the multipliers of the dynamics.
- * Arrays are per node, row-major: Q[n][nx][nx], M[n][nu][nx], R[n][nu][nu], A[n][nx][nx],
- * B[n][nx][nu], c[n][nx] (edge into node m; c[0] unused). */
+ *   s.t. dx_m = A_m dx_i + B_m du_i + c_m for m in ch(i), dx_0 = 0.
+ * Backward: the modified Riccati recursion of Eq. (tree_Riccati) that sums the children's value
+ * functions carried back through their edges (Q_xx = Q + sum A_m'P_m A_m, Q_ux = M + sum B_m'P_m A_m,
+ * H = R + sum B_m'P_m B_m, q_x = q + sum A_m'(p_m + P_m c_m), q_u = r + sum B_m'(p_m + P_m c_m); with
+ * the same A, B on every edge of a node this is the sum of P_m, p_m + P_m c_m first), with the
+ * feedback law of Eq. (tree_feedback_laws); forward: the affine rollout along every root-to-leaf
+ * path.  lam_m = P_m dx_m + p_m are the multipliers of the dynamics.
+ * Arrays are per node, row-major: Q[n][nx][nx], M[n][nu][nx], R[n][nu][nu], q, r; A[n][nx][nx],
+ * B[n][nx][nu], c[n][nx] of the edge into node m (row 0 unused). */
 static int tree_lqr(const tree_t *T, int nx, int nu, const double *Q, const double *M, const double *R,
                     const double *q, const double *r, const double *A, const double *B, const double *c,
                     double *K, double *k, double *Pm, double *pv, double *dx, double *du, double *lam) {
@@ -426,26 +451,29 @@ static int tree_lqr(const tree_t *T, int nx, int nu, const double *Q, const doub
             memcpy(pi, q + (size_t)i * nx, sizeof(double) * nx);
             continue;
         }
-        /* child sums: Pbar = sum P_m, pbar = sum (p_m + P_m c_m) */
-        double Pbar[MAXX * MAXX] = {0}, pbar[MAXX] = {0};
+        /* children's value functions through their edges */
+        double Qxx[MAXX * MAXX] = {0}, Qux[MAXU * MAXX] = {0}, Quu[MAXU * MAXU] = {0}, qx[MAXX] = {0}, qu[MAXU] = {0};
         for (int t = 0; t < T->n_child[i]; ++t) {
             int m = T->child[T->first_child[i] + t];
             const double *Pc = Pm + (size_t)m * nx * nx, *pc = pv + (size_t)m * nx;
-            double Pcc[MAXX];
-            matvec(nx, nx, Pc, c + (size_t)m * nx, Pcc);
-            for (int e = 0; e < nx * nx; ++e) Pbar[e] += Pc[e];
-            for (int e = 0; e < nx; ++e) pbar[e] += pc[e] + Pcc[e];
+            const double *Am = A + (size_t)m * nx * nx, *Bm = B + (size_t)m * nx * nu;
+            double pbar[MAXX], PA[MAXX * MAXX], PB[MAXX * MAXU], t1[MAXX * MAXX], t2[MAXU * MAXX], t3[MAXU * MAXU];
+            double v1[MAXX], v2[MAXU];
+            matvec(nx, nx, Pc, c + (size_t)m * nx, pbar);
+            for (int e = 0; e < nx; ++e) pbar[e] += pc[e];
+            matmul(nx, nx, nx, Pc, Am, PA);
+            matmul(nx, nx, nu, Pc, Bm, PB);
+            matTmul(nx, nx, nx, Am, PA, t1);
+            matTmul(nu, nx, nx, Bm, PA, t2);
+            matTmul(nu, nx, nu, Bm, PB, t3);
+            matTvec(nx, nx, Am, pbar, v1);
+            matTvec(nx, nu, Bm, pbar, v2);
+            for (int e = 0; e < nx * nx; ++e) Qxx[e] += t1[e];
+            for (int e = 0; e < nu * nx; ++e) Qux[e] += t2[e];
+            for (int e = 0; e < nu * nu; ++e) Quu[e] += t3[e];
+            for (int e = 0; e < nx; ++e) qx[e] += v1[e];
+            for (int e = 0; e < nu; ++e) qu[e] += v2[e];
         }
-        const double *Ai = A + (size_t)i * nx * nx, *Bi = B + (size_t)i * nx * nu;
-        double PA[MAXX * MAXX], PB[MAXX * MAXU];
-        double Qxx[MAXX * MAXX], Qux[MAXU * MAXX], Quu[MAXU * MAXU], qx[MAXX], qu[MAXU];
-        matmul(nx, nx, nx, Pbar, Ai, PA);
-        matmul(nx, nx, nu, Pbar, Bi, PB);
-        matTmul(nx, nx, nx, Ai, PA, Qxx);
-        matTmul(nu, nx, nx, Bi, PA, Qux);
-        matTmul(nu, nx, nu, Bi, PB, Quu);
-        matTvec(nx, nx, Ai, pbar, qx);
-        matTvec(nx, nu, Bi, pbar, qu);
         for (int e = 0; e < nx * nx; ++e) Qxx[e] += Q[(size_t)i * nx * nx + e];
         for (int e = 0; e < nu * nx; ++e) Qux[e] += M[(size_t)i * nu * nx + e];
         for (int e = 0; e < nu * nu; ++e) Quu[e] += R[(size_t)i * nu * nu + e];
@@ -475,11 +503,11 @@ static int tree_lqr(const tree_t *T, int nx, int nu, const double *Q, const doub
         double *dui = du + (size_t)i * nu;
         matvec(nu, nx, Ki, dx + (size_t)i * nx, dui);
         for (int e = 0; e < nu; ++e) dui[e] += ki[e];
-        double Ax[MAXX], Bu[MAXX];
-        matvec(nx, nx, A + (size_t)i * nx * nx, dx + (size_t)i * nx, Ax);
-        matvec(nx, nu, B + (size_t)i * nx * nu, dui, Bu);
         for (int t = 0; t < T->n_child[i]; ++t) {
             int m = T->child[T->first_child[i] + t];
+            double Ax[MAXX], Bu[MAXX];
+            matvec(nx, nx, A + (size_t)m * nx * nx, dx + (size_t)i * nx, Ax);
+            matvec(nx, nu, B + (size_t)m * nx * nu, dui, Bu);
             for (int e = 0; e < nx; ++e) dx[(size_t)m * nx + e] = Ax[e] + Bu[e] + c[(size_t)m * nx + e];
         }
     }
@@ -491,9 +519,22 @@ static int tree_lqr(const tree_t *T, int nx, int nu, const double *Q, const doub
     return ORC_OK;
 }
 
+/* Per-edge copies of per-parent Jacobians: edge m takes the Jacobians of parent(m). */
+static void parent_to_edge(int n, const int *parent, int nx, int nu, const double *A, const double *B, double *Ae,
+                           double *Be) {
+    memset(Ae, 0, sizeof(double) * nx * nx);
+    memset(Be, 0, sizeof(double) * nx * nu);
+    for (int m = 1; m < n; ++m) {
+        memcpy(Ae + (size_t)m * nx * nx, A + (size_t)parent[m] * nx * nx, sizeof(double) * nx * nx);
+        memcpy(Be + (size_t)m * nx * nu, B + (size_t)parent[m] * nx * nu, sizeof(double) * nx * nu);
+    }
+}
+
+/* The tree LQR with A, B per parent (edge = 0: row i the Jacobians of node i's dynamics, shared by its
+ * children) or per edge (edge = 1: row m the Jacobians of the edge into m). */
 int orc_tree_lqr(int n, const int *parent, int nx, int nu, const double *Q, const double *M, const double *R,
                  const double *q, const double *r, const double *A, const double *B, const double *c,
-                 double *K, double *k, double *Pm, double *pv, double *dx, double *du, double *lam) {
+                 double *K, double *k, double *Pm, double *pv, double *dx, double *du, double *lam, int edge) {
     if (nx > MAXX || nu > MAXU || n < 1) return ORC_ERR_INVALID;
     orc_problem P;
     memset(&P, 0, sizeof P);
@@ -501,7 +542,14 @@ int orc_tree_lqr(int n, const int *parent, int nx, int nu, const double *Q, cons
     P.parent = parent;
     tree_t T;
     if (!tree_build(&P, &T)) { tree_free(&T); return ORC_ERR_INVALID; }
-    int st = tree_lqr(&T, nx, nu, Q, M, R, q, r, A, B, c, K, k, Pm, pv, dx, du, lam);
+    double *Ae = NULL, *Be = NULL;
+    if (!edge) {
+        Ae = (double *)malloc(sizeof(double) * n * nx * nx);
+        Be = (double *)malloc(sizeof(double) * n * nx * nu);
+        parent_to_edge(n, parent, nx, nu, A, B, Ae, Be);
+    }
+    int st = tree_lqr(&T, nx, nu, Q, M, R, q, r, edge ? A : Ae, edge ? B : Be, c, K, k, Pm, pv, dx, du, lam);
+    free(Ae); free(Be);
     tree_free(&T);
     return st;
 }
@@ -652,23 +700,27 @@ static int cvf_step(int nx, int nu, const double *Q, const double *M, const doub
 static int tree_law(const tree_t *T, int i, int nx, int nu, const double *Q, const double *M, const double *R,
                     const double *q, const double *r, const double *A, const double *B, const double *c,
                     const double *Pm, const double *pv, double *Ki, double *ki, double *Pi, double *pi) {
-    double Pbar[MAXX * MAXX] = {0}, pbar[MAXX] = {0};
-    for (int t = 0; t < T->n_child[i]; ++t) {
+    double Qxx[MAXX * MAXX] = {0}, Qux[MAXU * MAXX] = {0}, Quu[MAXU * MAXU] = {0}, qx[MAXX] = {0}, qu[MAXU] = {0};
+    for (int t = 0; t < T->n_child[i]; ++t) {   /* children through their edges (A, B, c of edge ch) */
         const int ch = T->child[T->first_child[i] + t];
-        double Pc[MAXX];
-        matvec(nx, nx, Pm + (size_t)ch * nx * nx, c + (size_t)ch * nx, Pc);
-        for (int e = 0; e < nx * nx; ++e) Pbar[e] += Pm[(size_t)ch * nx * nx + e];
-        for (int e = 0; e < nx; ++e) pbar[e] += pv[(size_t)ch * nx + e] + Pc[e];
+        const double *Pc = Pm + (size_t)ch * nx * nx, *Am = A + (size_t)ch * nx * nx, *Bm = B + (size_t)ch * nx * nu;
+        double pbar[MAXX], PA[MAXX * MAXX], PB[MAXX * MAXU], t1[MAXX * MAXX], t2[MAXU * MAXX], t3[MAXU * MAXU];
+        double v1[MAXX], v2[MAXU];
+        matvec(nx, nx, Pc, c + (size_t)ch * nx, pbar);
+        for (int e = 0; e < nx; ++e) pbar[e] += pv[(size_t)ch * nx + e];
+        matmul(nx, nx, nx, Pc, Am, PA);
+        matmul(nx, nx, nu, Pc, Bm, PB);
+        matTmul(nx, nx, nx, Am, PA, t1);
+        matTmul(nu, nx, nx, Bm, PA, t2);
+        matTmul(nu, nx, nu, Bm, PB, t3);
+        matTvec(nx, nx, Am, pbar, v1);
+        matTvec(nx, nu, Bm, pbar, v2);
+        for (int e = 0; e < nx * nx; ++e) Qxx[e] += t1[e];
+        for (int e = 0; e < nu * nx; ++e) Qux[e] += t2[e];
+        for (int e = 0; e < nu * nu; ++e) Quu[e] += t3[e];
+        for (int e = 0; e < nx; ++e) qx[e] += v1[e];
+        for (int e = 0; e < nu; ++e) qu[e] += v2[e];
     }
-    const double *Ai = A + (size_t)i * nx * nx, *Bi = B + (size_t)i * nx * nu;
-    double PA[MAXX * MAXX], PB[MAXX * MAXU], Qxx[MAXX * MAXX], Qux[MAXU * MAXX], Quu[MAXU * MAXU], qx[MAXX], qu[MAXU];
-    matmul(nx, nx, nx, Pbar, Ai, PA);
-    matmul(nx, nx, nu, Pbar, Bi, PB);
-    matTmul(nx, nx, nx, Ai, PA, Qxx);
-    matTmul(nu, nx, nx, Bi, PA, Qux);
-    matTmul(nu, nx, nu, Bi, PB, Quu);
-    matTvec(nx, nx, Ai, pbar, qx);
-    matTvec(nx, nu, Bi, pbar, qu);
     for (int e = 0; e < nx * nx; ++e) Qxx[e] += Q[(size_t)i * nx * nx + e];
     for (int e = 0; e < nu * nx; ++e) Qux[e] += M[(size_t)i * nu * nx + e];
     for (int e = 0; e < nu * nu; ++e) Quu[e] += R[(size_t)i * nu * nu + e];
@@ -732,7 +784,7 @@ static int tree_lqr_scan(const tree_t *Tp, const int *parent, int nx, int nu, co
         for (int i = 0; i < L; ++i) {
             const int a = chain[i], ch = T.child[T.first_child[a]];
             if (!cvf_step(nx, nu, Q + (size_t)a * nx * nx, M + (size_t)a * nu * nx, R + (size_t)a * nu * nu,
-                          q + (size_t)a * nx, r + (size_t)a * nu, A + (size_t)a * nx * nx, B + (size_t)a * nx * nu,
+                          q + (size_t)a * nx, r + (size_t)a * nu, A + (size_t)ch * nx * nx, B + (size_t)ch * nx * nu,
                           c + (size_t)ch * nx, &S[i])) {
                 st = ORC_ERR_NUMERIC;
                 break;
@@ -773,10 +825,10 @@ static int tree_lqr_scan(const tree_t *Tp, const int *parent, int nx, int nu, co
         /* element j maps dx of parent(chain[j]) to dx of chain[j] */
         for (int j = 0; j < D; ++j) {
             const int m = chain[j], a = parent[m];
-            const double *Ka = K + (size_t)a * nu * nx, *ka = k + (size_t)a * nu, *Ba = B + (size_t)a * nx * nu;
+            const double *Ka = K + (size_t)a * nu * nx, *ka = k + (size_t)a * nu, *Ba = B + (size_t)m * nx * nu;
             for (int i = 0; i < nx; ++i) {
                 for (int t = 0; t < nx; ++t) {
-                    double v = A[(size_t)a * nx * nx + i * nx + t];
+                    double v = A[(size_t)m * nx * nx + i * nx + t];
                     for (int s2 = 0; s2 < nu; ++s2) v += Ba[i * nu + s2] * Ka[s2 * nx + t];
                     GA[(size_t)j * nx * nx + i * nx + t] = v;
                 }
@@ -822,7 +874,7 @@ static int tree_lqr_scan(const tree_t *Tp, const int *parent, int nx, int nu, co
 
 int orc_tree_lqr_scan(int n, const int *parent, int nx, int nu, const double *Q, const double *M, const double *R,
                       const double *q, const double *r, const double *A, const double *B, const double *c, double *K,
-                      double *k, double *Pm, double *pv, double *dx, double *du, double *lam) {
+                      double *k, double *Pm, double *pv, double *dx, double *du, double *lam, int edge) {
     if (nx > MAXX || nu > MAXU || n < 1) return ORC_ERR_INVALID;
     orc_problem Pr;
     memset(&Pr, 0, sizeof Pr);
@@ -830,7 +882,15 @@ int orc_tree_lqr_scan(int n, const int *parent, int nx, int nu, const double *Q,
     Pr.parent = parent;
     tree_t T;
     if (!tree_build(&Pr, &T)) { tree_free(&T); return ORC_ERR_INVALID; }
-    const int st = tree_lqr_scan(&T, parent, nx, nu, Q, M, R, q, r, A, B, c, K, k, Pm, pv, dx, du, lam);
+    double *Ae = NULL, *Be = NULL;
+    if (!edge) {
+        Ae = (double *)malloc(sizeof(double) * n * nx * nx);
+        Be = (double *)malloc(sizeof(double) * n * nx * nu);
+        parent_to_edge(n, parent, nx, nu, A, B, Ae, Be);
+    }
+    const int st = tree_lqr_scan(&T, parent, nx, nu, Q, M, R, q, r, edge ? A : Ae, edge ? B : Be, c, K, k, Pm, pv, dx,
+                                 du, lam);
+    free(Ae); free(Be);
     tree_free(&T);
     return st;
 }
@@ -839,7 +899,7 @@ int orc_tree_lqr_scan(int n, const int *parent, int nx, int nu, const double *Q,
 typedef struct {
     tree_t T;
     int nc;
-    double *A, *B, *f;              /* per node (non-leaf): Jacobians and f(x_i, u_i) */
+    double *A, *B, *f;              /* per edge (row m: into node m): Jacobians and f_m(x_p(m), u_p(m)) */
     double *d;                      /* defect d_m = f_p(m) - x_m per node (row 0 zero) */
     double *Q, *M, *R, *q, *r;      /* GN quadratisation of L_a */
     double *g;                      /* constraint values [n][nc] */
@@ -906,7 +966,6 @@ static void linearise(const orc_problem *P, work_t *W, const double *x, const do
     for (int i = 0; i < n; ++i) {
         int leaf = T->n_child[i] == 0;
         const double *xi = x + (size_t)i * nx, *ui = u + (size_t)i * nu;
-        if (!leaf) orc_dynamics(P, xi, ui, W->f + (size_t)i * nx, W->A + (size_t)i * nx * nx, W->B + (size_t)i * nx * nu);
         double lx[MAXX] = {0}, lu[MAXU] = {0};
         La += node_cost(P, i, leaf, xi, ui, lx, lu);
         double *Qi = W->Q + (size_t)i * nx * nx, *Mi = W->M + (size_t)i * nu * nx, *Ri = W->R + (size_t)i * nu * nu;
@@ -940,10 +999,13 @@ static void linearise(const orc_problem *P, work_t *W, const double *x, const do
             }
         }
     }
+    /* the dynamics of every edge (into node m, from its parent) and the defects d_m = f_m - x_m */
     memset(W->d, 0, sizeof(double) * nx);
     for (int m = 1; m < n; ++m) {
         int pnt = P->parent[m];
-        for (int j = 0; j < nx; ++j) W->d[(size_t)m * nx + j] = W->f[(size_t)pnt * nx + j] - x[(size_t)m * nx + j];
+        edge_dynamics(P, m, x + (size_t)pnt * nx, u + (size_t)pnt * nu, W->f + (size_t)m * nx,
+                      W->A + (size_t)m * nx * nx, W->B + (size_t)m * nx * nu);
+        for (int j = 0; j < nx; ++j) W->d[(size_t)m * nx + j] = W->f[(size_t)m * nx + j] - x[(size_t)m * nx + j];
     }
     W->La = La;
 }
@@ -955,14 +1017,16 @@ static double kkt_relaxed(const orc_problem *P, const work_t *W, const double *l
     const tree_t *T = &W->T;
     double r = 0.0;
     for (int i = 0; i < n; ++i) {
-        double lsum[MAXX] = {0};
+        double Al[MAXX] = {0}, Bl[MAXU] = {0};   /* sum over children of A_m' lam_m, B_m' lam_m */
         for (int t = 0; t < T->n_child[i]; ++t) {
             int m = T->child[T->first_child[i] + t];
-            for (int e = 0; e < nx; ++e) lsum[e] += lam[(size_t)m * nx + e];
+            double a1[MAXX], b1[MAXU];
+            matTvec(nx, nx, W->A + (size_t)m * nx * nx, lam + (size_t)m * nx, a1);
+            matTvec(nx, nu, W->B + (size_t)m * nx * nu, lam + (size_t)m * nx, b1);
+            for (int e = 0; e < nx; ++e) Al[e] += a1[e];
+            for (int e = 0; e < nu; ++e) Bl[e] += b1[e];
         }
         if (i != 0) {
-            double Al[MAXX] = {0};
-            if (T->n_child[i]) matTvec(nx, nx, W->A + (size_t)i * nx * nx, lsum, Al);
             for (int e = 0; e < nx; ++e) {
                 double gx = W->q[(size_t)i * nx + e] + Al[e] - lam[(size_t)i * nx + e];
                 if (fabs(gx) > r) r = fabs(gx);
@@ -970,8 +1034,6 @@ static double kkt_relaxed(const orc_problem *P, const work_t *W, const double *l
             for (int e = 0; e < nx; ++e) if (fabs(W->d[(size_t)i * nx + e]) > r) r = fabs(W->d[(size_t)i * nx + e]);
         }
         if (T->n_child[i]) {
-            double Bl[MAXU];
-            matTvec(nx, nu, W->B + (size_t)i * nx * nu, lsum, Bl);
             for (int e = 0; e < nu; ++e) {
                 double gu = W->r[(size_t)i * nu + e] + Bl[e];
                 if (fabs(gu) > r) r = fabs(gu);
@@ -1001,10 +1063,10 @@ static double merit_at(const orc_problem *P, const tree_t *T, int nc, const doub
             }
         }
         if (!leaf) {
-            double fx[MAXX];
-            orc_dynamics(P, xi, ui, fx, NULL, NULL);
             for (int t = 0; t < T->n_child[i]; ++t) {
                 int m = T->child[T->first_child[i] + t];
+                double fx[MAXX];
+                edge_dynamics(P, m, xi, ui, fx, NULL, NULL);
                 for (int e = 0; e < nx; ++e) {
                     double dm = fx[e] - x[(size_t)m * nx + e];
                     ld += lam[(size_t)m * nx + e] * dm;
@@ -1023,6 +1085,7 @@ static int check_problem(const orc_problem *P) {
     if (P->model == 1 && (P->nx != 6 || P->nu != 2)) return 0;
     if (P->model != 2 && (P->nx < 2)) return 0;
     if (n_con(P) > 64) return 0;
+    if ((P->Aedge != NULL) != (P->Bedge != NULL) || (P->Aedge && P->model != 2)) return 0;
     return 1;
 }
 
@@ -1292,14 +1355,16 @@ int orc_kkt(const orc_problem *P, const double *x, const double *u, const double
     }
     double stat = 0.0, dmax = 0.0, inf = 0.0, comp = 0.0, neg = 0.0;
     for (int i = 0; i < n; ++i) {
-        double lsum[MAXX] = {0};
+        double Al[MAXX] = {0}, Bl[MAXU] = {0};   /* sum over children of A_m' lam_m, B_m' lam_m */
         for (int t = 0; t < W.T.n_child[i]; ++t) {
             int m = W.T.child[W.T.first_child[i] + t];
-            for (int e = 0; e < nx; ++e) lsum[e] += lam[(size_t)m * nx + e];
+            double a1[MAXX], b1[MAXU];
+            matTvec(nx, nx, W.A + (size_t)m * nx * nx, lam + (size_t)m * nx, a1);
+            matTvec(nx, nu, W.B + (size_t)m * nx * nu, lam + (size_t)m * nx, b1);
+            for (int e = 0; e < nx; ++e) Al[e] += a1[e];
+            for (int e = 0; e < nu; ++e) Bl[e] += b1[e];
         }
         if (i) {
-            double Al[MAXX] = {0};
-            if (W.T.n_child[i]) matTvec(nx, nx, W.A + (size_t)i * nx * nx, lsum, Al);
             for (int e = 0; e < nx; ++e) {
                 double gx = W.q[(size_t)i * nx + e] + Al[e] - lam[(size_t)i * nx + e];
                 if (fabs(gx) > stat) stat = fabs(gx);
@@ -1307,8 +1372,6 @@ int orc_kkt(const orc_problem *P, const double *x, const double *u, const double
             }
         }
         if (W.T.n_child[i]) {
-            double Bl[MAXU];
-            matTvec(nx, nu, W.B + (size_t)i * nx * nu, lsum, Bl);
             for (int e = 0; e < nu; ++e) {
                 double gu = W.r[(size_t)i * nu + e] + Bl[e];
                 if (fabs(gu) > stat) stat = fabs(gu);

@@ -28,7 +28,7 @@ _ip = C.POINTER(C.c_int32)
 class TreeDesc(C.Structure):
     _fields_ = [("num_nodes", C.c_int32), ("parent", _ip), ("nx", C.c_int32), ("nu", C.c_int32),
                 ("model", C.c_int32), ("n_obs", C.c_int32), ("box_on", C.c_int32), ("lane_on", C.c_int32),
-                ("dt", C.c_float), ("params", C.c_float * 10)]
+                ("dt", C.c_float), ("params", C.c_float * 10), ("edge_dynamics", C.c_int32)]
 
 
 class Problem(C.Structure):
@@ -36,7 +36,7 @@ class Problem(C.Structure):
                 ("QNw", C.c_float * MAX_NX), ("Rw", C.c_float * NU), ("u_lo", C.c_float * NU),
                 ("u_hi", C.c_float * NU), ("lane_lo", C.c_float), ("lane_hi", C.c_float), ("obs", _fp),
                 ("Alin", _fp), ("Blin", _fp), ("warm_x", _fp), ("warm_u", _fp), ("warm_lam", _fp),
-                ("warm_y", _fp)]
+                ("warm_y", _fp), ("Aedge", _fp), ("Bedge", _fp)]
 
 
 class Opts(C.Structure):
@@ -185,6 +185,7 @@ def tree_desc(p) -> tuple[TreeDesc, np.ndarray]:
     d.dt = float(p["dt"])
     for j, v in enumerate(np.asarray(p["params"], dtype=np.float64)[:10]):
         d.params[j] = float(v)
+    d.edge_dynamics = 1 if p.get("Aedge") is not None else 0
     return d, parent
 
 
@@ -197,6 +198,10 @@ class _ProblemData:
                      _f32(p["Alin"]), _f32(p["Blin"])]
         s = Problem()
         s.x0, s.xref, s.weight, s.obs, s.Alin, s.Blin = (a.ctypes.data_as(_fp) for a in self.keep)
+        if p.get("Aedge") is not None:
+            ae, be = _f32(p["Aedge"]), _f32(p["Bedge"])
+            self.keep += [ae, be]
+            s.Aedge, s.Bedge = ae.ctypes.data_as(_fp), be.ctypes.data_as(_fp)
         for j in range(nx):
             s.Qw[j], s.QNw[j] = float(p["Qw"][j]), float(p["QNw"][j])
         for j in range(NU):

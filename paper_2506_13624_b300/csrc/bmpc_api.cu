@@ -69,6 +69,7 @@ int validate(const bmpc_tree_desc &d, std::vector<int> *stage_out) {
     if (d.n_obs < 0 || d.n_obs > MAX_OBS) return BMPC_ERR_INVALID;
     if (!(d.dt > 0.f) || !std::isfinite(d.dt)) return BMPC_ERR_INVALID;
     if (d.model != 2 && !(d.params[9] >= 1.f && d.params[9] <= 64.f)) return BMPC_ERR_INVALID;
+    if (d.edge_dynamics != 0 && (d.edge_dynamics != 1 || d.model != 2)) return BMPC_ERR_INVALID;
     const int n = d.num_nodes;
     std::vector<int> stage(n, 0);
     if (d.parent[0] != -1) return BMPC_ERR_INVALID;
@@ -158,6 +159,7 @@ struct bmpc_batch {
     cudaStream_t aux[NUM_MODELS] = {};   /* per-model streams of mixed batches */
     cudaEvent_t fork = nullptr, join[NUM_MODELS] = {};
     cudaEvent_t handoff = nullptr;       /* orders a new stream after the old one (bmpc_set_stream) */
+    bool any_edge = false;               /* some problem has per-edge dynamics */
     int sm_count = 148;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -203,6 +205,7 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         R.n_stage = max_stage + 1;
         R.n_paths = n_paths;
         R.n_bstage = n_bstage;
+        R.edge_dyn = d.edge_dynamics;
         {
             Segments sg;
             segments(d.num_nodes, d.parent, sg);
@@ -224,7 +227,7 @@ void compute_layout(const bmpc_tree_desc *descs, int n, std::vector<ProbRec> &re
         fnc += (int64_t)R.n * R.nc;
         fobs += (int64_t)R.n * R.n_obs * 5;
         oi += (size_t)int_off(R.npad, R.n_stage, R.n_paths, R.n_waves).total;
-        oin += (size_t)in_rows(R.nx, R.n_obs).total * R.npad;
+        oin += (size_t)in_rows(R.nx, R.n_obs, R.edge_dyn).total * R.npad;
         ow += 2 * (size_t)warm_rows(R.nx, R.nc).total * R.npad;   /* primary and fallback slots */
         oo += (size_t)out_rows(R.nx, R.nc).total * R.npad;
         os += (size_t)scr_rows(R.nx).total * R.npad;
@@ -356,7 +359,7 @@ void copy_params(ProbRec &R, const bmpc_problem &P) {
     }
     R.lane_lo = P.lane_lo;
     R.lane_hi = P.lane_hi;
-    if (R.model == 2) {
+    if (R.model == 2 && P.Alin && P.Blin) {
         std::memcpy(R.Alin, P.Alin, sizeof(float) * R.nx * R.nx);
         std::memcpy(R.Blin, P.Blin, sizeof(float) * R.nx * NU);
     }
@@ -391,6 +394,7 @@ void geometry(const bmpc_batch *b, const bmpc_opts &o, int model, int count, int
 }
 
 int launch(bmpc_batch *b, const bmpc_opts &o) {
+    if (o.variant >= 3 && b->any_edge) return BMPC_ERR_INVALID;   /* per-edge dynamics: sweeps 1 and 2 */
     KernelArgs a;
     a.recs = at<const ProbRec>(b->data, b->L.recs);
     a.ibase = at<const int32_t>(b->data, b->L.ints);
@@ -504,6 +508,7 @@ int bmpc_create_batch(const bmpc_tree_desc *descs, int32_t n, void *dev_data, si
     if (!b) return BMPC_ERR_SPACE;
     b->n = n;
     compute_layout(descs, n, b->recs, b->nodes, b->L);
+    for (const ProbRec &r : b->recs) b->any_edge = b->any_edge || r.edge_dyn != 0;
     b->data = static_cast<char *>(dev_data);
     b->scr = static_cast<float *>(dev_scratch);
     b->data_bytes = data_bytes;
@@ -657,7 +662,8 @@ int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
         const bmpc_problem &P = probs[k];
         const ProbRec &R = b->recs[k];
         if (!P.x0 || !P.xref || (R.n_obs > 0 && !P.obs)) return BMPC_ERR_INVALID;
-        if (R.model == 2 && (!P.Alin || !P.Blin)) return BMPC_ERR_INVALID;
+        if (R.model == 2 && !R.edge_dyn && (!P.Alin || !P.Blin)) return BMPC_ERR_INVALID;
+        if (R.edge_dyn && (!P.Aedge || !P.Bedge)) return BMPC_ERR_INVALID;
         const bool warm = P.warm_x || P.warm_u || P.warm_lam || P.warm_y;
         if (warm && (!P.warm_x || !P.warm_u || !P.warm_lam || (R.nc > 0 && !P.warm_y))) return BMPC_ERR_INVALID;
         for (int j = 0; j < R.nx; ++j)
@@ -676,9 +682,15 @@ int bmpc_set_problems(bmpc_batch *b, const bmpc_problem *probs) {
         copy_params(R, P);
         R.has_warm = warm ? 1 : 0;
         if (warm) any_warm.store(true, std::memory_order_relaxed);
-        const InRows ir = in_rows(nx, R.n_obs);
+        const InRows ir = in_rows(nx, R.n_obs, R.edge_dyn);
         float *base = fin + R.off_in;
         std::memset(base, 0, sizeof(float) * (size_t)ir.total * np);
+        if (R.edge_dyn)   /* per-edge matrices: entry (a, c) of the edge into node i at row a*nx+c, column i */
+            for (int i = 1; i < nn; ++i) {
+                for (int e = 0; e < nx * nx; ++e) base[(size_t)(ir.edge + e) * np + i] = P.Aedge[(size_t)i * nx * nx + e];
+                for (int e = 0; e < nx * NU; ++e)
+                    base[(size_t)(ir.edge + nx * nx + e) * np + i] = P.Bedge[(size_t)i * nx * NU + e];
+            }
         for (int i = 0; i < nn; ++i) {
             for (int j = 0; j < nx; ++j) base[(size_t)(ir.xref + j) * np + i] = P.xref[(size_t)i * nx + j];
             base[(size_t)ir.weight * np + i] = P.weight ? P.weight[i] : 1.f;
@@ -728,6 +740,7 @@ int bmpc_set_problems_flat(bmpc_batch *b, const bmpc_problem *probs, const float
         const bmpc_problem &P = probs[k];
         const ProbRec &R = b->recs[k];
         if (!P.x0 || (R.model == 2 && (!P.Alin || !P.Blin))) return BMPC_ERR_INVALID;
+        if (R.edge_dyn) return BMPC_ERR_INVALID;   /* per-edge matrices travel with bmpc_set_problems only */
         for (int j = 0; j < R.nx; ++j)
             if (!std::isfinite(P.x0[j])) return BMPC_ERR_INVALID;
         for (int j = 0; j < NU; ++j)
@@ -842,6 +855,8 @@ int bmpc_shift_warm_start(bmpc_batch *next, const bmpc_batch *prev, int32_t slot
     if (!next || !prev || slot < 0 || slot > 1 || next->n != prev->n) return BMPC_ERR_INVALID;
     if (next->parents != prev->parents) return BMPC_ERR_INVALID;
     for (int k = 0; k < next->n; ++k)
+        if (next->recs[k].edge_dyn) return BMPC_ERR_INVALID;   /* the shift rolls out per-node dynamics */
+    for (int k = 0; k < next->n; ++k)
         if (next->recs[k].model != prev->recs[k].model || next->recs[k].nc != prev->recs[k].nc ||
             next->recs[k].npad != prev->recs[k].npad)
             return BMPC_ERR_INVALID;
@@ -900,6 +915,8 @@ int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride) {
 int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, const float *mean, const float *std,
                    float *start, int64_t stride) {
     if (!b || !pred || !mean || !std || !start) return BMPC_ERR_INVALID;
+    for (const ProbRec &R : b->recs)
+        if (R.edge_dyn) return BMPC_ERR_INVALID;   /* the rollout of the start uses per-node dynamics */
     for (const ProbRec &R : b->recs) {
         const int64_t used = (int64_t)R.n * (2 * R.nx + NU + R.nc);
         if (used > stride || used > ld_pred) return BMPC_ERR_INVALID;
@@ -959,6 +976,7 @@ int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *
     for (int bt : kThreads)
         for (int v : kVariant)
             for (int ch : kChunk) {
+                if (v >= 3 && b->any_edge) continue;   /* per-edge dynamics: sweeps 1 and 2 */
                 bmpc_opts c = o;
                 c.block_threads = bt;
                 for (int m = 0; m < NUM_MODELS; ++m) c.block_threads_model[m] = 0;

@@ -547,6 +547,7 @@ struct View {
     float *A, *B, *f, *d, *q, *r, *hq, *hr, *K, *k, *P, *p, *dx, *du, *lq, *nv, *XL, *UL;
     float *CV0, *CV1, *JA0, *JA1;   /* scan buffers (two of each) */
     bool comp;   /* compensated iterate (Lo parts) in use */
+    bool edge;   /* per-edge linear dynamics: A, B point at the input rows, f and A, B are per edge */
 
     __device__ View(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout, float *fs) {
         n = R.n;
@@ -571,7 +572,7 @@ struct View {
         pdepth = ib + io.pdepth;
         ptop = ib + io.ptop;
         tab_off = io.sstart;
-        const InRows ir = in_rows(NX, nobs);
+        const InRows ir = in_rows(NX, nobs, R.edge_dyn);
         xref = fin + (size_t)ir.xref * np;
         w = fin + (size_t)ir.weight * np;
         obs = fin + (size_t)ir.obs * np;
@@ -601,6 +602,7 @@ struct View {
         nv = fs + (size_t)s.nv * np;
         XL = fs + (size_t)s.xl * np;
         UL = fs + (size_t)s.ul * np;
+        edge = false;   /* set by the solver for the linear model (per-edge dynamics) */
         CV0 = fs + (size_t)s.cv * np;
         CV1 = CV0 + (size_t)cvf_rows(NX) * np;
         JA0 = fs + (size_t)s.ja * np;
@@ -870,9 +872,12 @@ struct RicIn {
     float A[NX][NX], B[NX][NU], q[NX], r[NU], hq[3], hr[NU], w;
 };
 
+/* ja: the column of the Jacobians (node i's own for dynamics per node; the edge into its single
+ * child for per-edge dynamics) */
 template <int NX, int MODEL>
-__device__ __forceinline__ void ric_load(const View<NX> &V, int i, RicIn<NX> &in) {
+__device__ __forceinline__ void ric_load(const View<NX> &V, int i, RicIn<NX> &in, int ja = -1) {
     const int np = V.np;
+    if (ja < 0) ja = i;
     in.w = V.w[i];
     V.load_x(V.q, i, in.q);
 #pragma unroll
@@ -880,9 +885,9 @@ __device__ __forceinline__ void ric_load(const View<NX> &V, int i, RicIn<NX> &in
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
 #pragma unroll
-        for (int b = 0; b < NX; ++b) in.A[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
+        for (int b = 0; b < NX; ++b) in.A[a][b] = aload<NX, MODEL>(V.A, np, ja, a, b);
 #pragma unroll
-        for (int b = 0; b < NU; ++b) in.B[a][b] = V.B[(size_t)(a * NU + b) * np + i];
+        for (int b = 0; b < NU; ++b) in.B[a][b] = V.B[(size_t)(a * NU + b) * np + ja];
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
@@ -1019,6 +1024,201 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
     }
 }
 
+/* Per-edge linear dynamics: the increment f_m(x_p, u_p) - x_p = (A_m - I) xa + B_m u of the edge into
+ * node m at the parent's absolute state xa and input u. */
+template <int NX>
+__device__ __forceinline__ void edge_increment(const View<NX> &V, int m, const float (&xa)[NX], const float (&u)[NU],
+                                               float (&dl)[NX]) {
+    const int np = V.np;
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        float s = 0.f;
+#pragma unroll
+        for (int b = 0; b < NX; ++b) s += (V.A[(size_t)(a * NX + b) * np + m] - (a == b ? 1.f : 0.f)) * xa[b];
+#pragma unroll
+        for (int b = 0; b < NU; ++b) s += V.B[(size_t)(a * NU + b) * np + m] * u[b];
+        dl[a] = s;
+    }
+}
+
+/* Riccati step of a node with several children under per-edge dynamics (Eq. tree_Riccati with every
+ * child carried back through its own edge): Qxx = Q + sum A_m'P_m A_m, Qux = sum B_m'P_m A_m,
+ * H = R + sum B_m'P_m B_m, qx = q + sum A_m'(p_m + P_m d_m), qu = r + sum B_m'(p_m + P_m d_m); then
+ * the law and the value function as in riccati_node.  Stores K, k, P, p; returns P, p. */
+template <int NX>
+__device__ void riccati_edges(const ProbRec &R, const View<NX> &V, int i, float (&P)[nsym(NX)], float (&p)[NX],
+                              Shared &sh) {
+    constexpr int NS = nsym(NX);
+    const int np = V.np;
+    float Qxx[NX][NX], Qux[NU][NX], Quu[NU][NU], qx[NX], qu[NU];
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        qx[a] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NX; ++b) Qxx[a][b] = 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        qu[a] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NX; ++b) Qux[a][b] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NU; ++b) Quu[a][b] = 0.f;
+    }
+    const int fc = V.fchild[i], nch = V.nchild[i];
+    for (int m = fc; m < fc + nch; ++m) {
+        float Pm[NS], pbm[NX], Am[NX][NX], Bm[NX][NU], dm[NX];
+#pragma unroll
+        for (int e = 0; e < NS; ++e) Pm[e] = V.P[(size_t)e * np + m];
+        V.load_x(V.d, m, dm);
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+            float v = V.p[(size_t)a * np + m];
+#pragma unroll
+            for (int b = 0; b < NX; ++b) v += Pm[sidx<NX>(a, b)] * dm[b];
+            pbm[a] = v;
+#pragma unroll
+            for (int b = 0; b < NX; ++b) Am[a][b] = V.A[(size_t)(a * NX + b) * np + m];
+#pragma unroll
+            for (int b = 0; b < NU; ++b) Bm[a][b] = V.B[(size_t)(a * NU + b) * np + m];
+        }
+        float PA[NX][NX], PB[NX][NU];
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+#pragma unroll
+            for (int b = 0; b < NX; ++b) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += Pm[sidx<NX>(a, t)] * Am[t][b];
+                PA[a][b] = v;
+            }
+#pragma unroll
+            for (int b = 0; b < NU; ++b) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += Pm[sidx<NX>(a, t)] * Bm[t][b];
+                PB[a][b] = v;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NX; ++a) {
+#pragma unroll
+            for (int b = a; b < NX; ++b) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += Am[t][a] * PA[t][b];
+                Qxx[a][b] += v;
+            }
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += Am[t][a] * pbm[t];
+            qx[a] += v;
+        }
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+#pragma unroll
+            for (int b = 0; b < NX; ++b) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += Bm[t][j] * PA[t][b];
+                Qux[j][b] += v;
+            }
+#pragma unroll
+            for (int l = 0; l < NU; ++l) {
+                float v = 0.f;
+#pragma unroll
+                for (int t = 0; t < NX; ++t) v += Bm[t][j] * PB[t][l];
+                Quu[j][l] += v;
+            }
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v += Bm[t][j] * pbm[t];
+            qu[j] += v;
+        }
+    }
+    const float w = V.w[i];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+        Quu[a][a] += w * R.Rw[a] + V.hr[(size_t)a * np + i];
+        qu[a] += V.r[(size_t)a * np + i];
+    }
+#pragma unroll
+    for (int a = 0; a < NX; ++a) qx[a] += V.q[(size_t)a * np + i];
+    const float h00 = Quu[0][0], h01 = 0.5f * (Quu[0][1] + Quu[1][0]), h11 = Quu[1][1];
+    const float det = h00 * h11 - h01 * h01;
+    if (!(h00 > 0.f) || !(det > 0.f)) sh.flag = 1;
+    const float idet = 1.f / det;
+    const float g00 = h11 * idet, g01 = -h01 * idet, g11 = h00 * idet;
+    float Kn[NU][NX], kn[NU];
+#pragma unroll
+    for (int b = 0; b < NX + 1; ++b) {
+        const float rhs0 = (b < NX) ? Qux[0][b] : qu[0];
+        const float rhs1 = (b < NX) ? Qux[1][b] : qu[1];
+        const float s0 = g00 * rhs0 + g01 * rhs1;
+        const float s1 = g01 * rhs0 + g11 * rhs1;
+        if (b < NX) {
+            Kn[0][b] = -s0;
+            Kn[1][b] = -s1;
+        } else {
+            kn[0] = -s0;
+            kn[1] = -s1;
+        }
+    }
+    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+#pragma unroll
+    for (int a = 0; a < NX; ++a)
+#pragma unroll
+        for (int b = a; b < NX; ++b) {
+            float v = Qxx[a][b] + ((a == b) ? w * R.Qw[a] : 0.f);
+            if (a == 0 && b == 0) v += hxx;
+            if (a == 0 && b == 1) v += hxy;
+            if (a == 1 && b == 1) v += hyy;
+#pragma unroll
+            for (int t = 0; t < NU; ++t) v += Qux[t][a] * Kn[t][b];
+            P[sidx<NX>(a, b)] = v;
+            V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
+        }
+#pragma unroll
+    for (int a = 0; a < NX; ++a) {
+        float v = qx[a];
+#pragma unroll
+        for (int t = 0; t < NU; ++t) v += Qux[t][a] * kn[t];
+        p[a] = v;
+        V.p[(size_t)a * np + i] = v;
+    }
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+#pragma unroll
+        for (int b = 0; b < NX; ++b) V.K[(size_t)(a * NX + b) * np + i] = Kn[a][b];
+        V.k[(size_t)a * np + i] = kn[a];
+    }
+}
+
+/* Riccati step of non-leaf node i from its children's value functions in memory: the sum of Eq.
+ * (tree_Riccati) and one step (dynamics per node, or a single child's edge), or the per-edge sum at
+ * a node with several children. */
+template <int NX, int MODEL>
+__device__ __forceinline__ void riccati_from_children(const ProbRec &R, const View<NX> &V, int i, float (&P)[nsym(NX)],
+                                                      float (&p)[NX], Shared &sh) {
+    constexpr int NS = nsym(NX);
+    const int nch = V.nchild[i], fc = V.fchild[i];
+    if constexpr (MODEL == 2) {
+        if (V.edge && nch > 1) {
+            riccati_edges<NX>(R, V, i, P, p, sh);
+            return;
+        }
+    }
+    float Pb[NS], pb[NX];
+#pragma unroll
+    for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
+#pragma unroll
+    for (int a = 0; a < NX; ++a) pb[a] = 0.f;
+    for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
+    RicIn<NX> in;
+    ric_load<NX, MODEL>(V, i, in, (MODEL == 2 && V.edge) ? fc : i);
+    riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
+}
+
 /* Level-synchronous backward sweep: all nodes of a stage in parallel, one barrier per stage. */
 template <int NX, int MODEL>
 __device__ void backward_level(const ProbRec &R, const View<NX> &V, Shared &sh) {
@@ -1027,21 +1227,12 @@ __device__ void backward_level(const ProbRec &R, const View<NX> &V, Shared &sh) 
     for (int st = R.n_stage - 1; st >= 0; --st) {
         const int s0 = V.sstart[st], s1 = V.sstart[st + 1];
         for (int i = s0 + tid; i < s1; i += nt) {
-            const int nch = V.nchild[i], fc = V.fchild[i];
             float P[NS], p[NX];
-            if (nch == 0) {
+            if (V.nchild[i] == 0) {
                 leaf_value<NX>(R, V, i, P, p);
                 continue;
             }
-            float Pb[NS], pb[NX];
-#pragma unroll
-            for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
-#pragma unroll
-            for (int a = 0; a < NX; ++a) pb[a] = 0.f;
-            for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
-            RicIn<NX> in;
-            ric_load<NX, MODEL>(V, i, in);
-            riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
+            riccati_from_children<NX, MODEL>(R, V, i, P, p, sh);
         }
         __syncthreads();
     }
@@ -1069,27 +1260,15 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
             {
                 const int i = path[k];
                 const int nch = V.nchild[i];
-                if (nch == 0) {
-                    leaf_value<NX>(R, V, i, P, p);
-                } else {
-                    float Pb[NS], pb[NX];
-#pragma unroll
-                    for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
-#pragma unroll
-                    for (int a = 0; a < NX; ++a) pb[a] = 0.f;
-                    const int fc = V.fchild[i];
-                    for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
-                    RicIn<NX> in;
-                    ric_load<NX, MODEL>(V, i, in);
-                    riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
-                }
+                if (nch == 0) leaf_value<NX>(R, V, i, P, p);
+                else riccati_from_children<NX, MODEL>(R, V, i, P, p, sh);
             }
             for (k = khi - 1; k >= klo; --k) {
                 const int i = path[k];   /* single child path[k+1], its value function in P, p */
                 float dm[NX], Pb[NS], pb[NX];
                 RicIn<NX> in;
                 V.load_x(V.d, path[k + 1], dm);
-                ric_load<NX, MODEL>(V, i, in);
+                ric_load<NX, MODEL>(V, i, in, (MODEL == 2 && V.edge) ? path[k + 1] : i);
 #pragma unroll
                 for (int e = 0; e < NS; ++e) Pb[e] = 0.f + P[e];
 #pragma unroll
@@ -1280,7 +1459,8 @@ __device__ void forward_level(const ProbRec &R, const View<NX> &V) {
                 V.load_u(V.du, pa, dup);
             }
             FwdIn<NX> in;
-            fwd_load<NX, MODEL>(V, i, pa < 0 ? 0 : pa, in);
+            /* Jacobians of the edge into i: the parent's, or i's own with per-edge dynamics */
+            fwd_load<NX, MODEL>(V, i, (MODEL == 2 && V.edge) ? i : (pa < 0 ? 0 : pa), in);
             forward_node<NX, MODEL>(V, i, pa, V.nchild[i] != 0, in, dxp, dup, dxv, duv, true);
         }
         __syncthreads();
@@ -1307,7 +1487,9 @@ __device__ void forward_path(const ProbRec &R, const View<NX> &V, float *stg, in
         if (stg) {
 #pragma unroll
             for (int q = 0; q < SWEEP_DEPTH - 1; ++q) {
-                if (q < nst) fwd_issue<NX, MODEL>(V, path[q], q ? path[q - 1] : 0, slot + q * bs, ld);
+                if (q < nst)
+                    fwd_issue<NX, MODEL>(V, path[q], (MODEL == 2 && V.edge) ? path[q] : (q ? path[q - 1] : 0),
+                                         slot + q * bs, ld);
                 cp_commit();
             }
         }
@@ -1317,12 +1499,14 @@ __device__ void forward_path(const ProbRec &R, const View<NX> &V, float *stg, in
             FwdIn<NX> in;
             if (stg) {
                 const int q = k + SWEEP_DEPTH - 1;
-                if (q < nst) fwd_issue<NX, MODEL>(V, path[q], path[q - 1], slot + (q % SWEEP_DEPTH) * bs, ld);
+                if (q < nst)
+                    fwd_issue<NX, MODEL>(V, path[q], (MODEL == 2 && V.edge) ? path[q] : path[q - 1],
+                                         slot + (q % SWEEP_DEPTH) * bs, ld);
                 cp_commit();
                 cp_wait<SWEEP_DEPTH - 1>();
                 fwd_read<NX, MODEL>(slot + (k % SWEEP_DEPTH) * bs, ld, in);
             } else {
-                fwd_load<NX, MODEL>(V, i, pa < 0 ? 0 : pa, in);
+                fwd_load<NX, MODEL>(V, i, (MODEL == 2 && V.edge) ? i : (pa < 0 ? 0 : pa), in);
             }
             float dxv[NX], duv[NU];
             forward_node<NX, MODEL>(V, i, pa, k < depth, in, dxp, dup, dxv, duv, k >= top);
@@ -2137,8 +2321,12 @@ __device__ float start_merit(const ProbRec &R, const View<NX> &V, float rho, flo
             float xa[NX], ft[NX];
 #pragma unroll
             for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
-            dyn<NX, MODEL>(R, xa, u, ft);
+            const bool per_edge = MODEL == 2 && V.edge;
+            if (!per_edge) dyn<NX, MODEL>(R, xa, u, ft);
             for (int m = fc; m < fc + nch; ++m) {
+                if constexpr (MODEL == 2) {
+                    if (per_edge) edge_increment<NX>(V, m, xa, u, ft);
+                }
 #pragma unroll
                 for (int j = 0; j < NX; ++j) {
                     const float dref = V.xref[(size_t)j * np + i] - V.xref[(size_t)j * np + m];
@@ -2218,6 +2406,13 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
     constexpr bool HOIST_LOADS = hoist_loads<NX>();
     View<NX> V(R, ib, fin, fw, fout, fs);
     V.comp = O.compensated != 0;
+    if constexpr (MODEL == 2) {
+        if (R.edge_dyn) {   /* per-edge matrices: inputs at the edge's column, never written by the solver */
+            V.edge = true;
+            V.A = const_cast<float *>(fin) + (size_t)in_rows(NX, R.n_obs, 1).edge * R.npad;
+            V.B = V.A + (size_t)NX * NX * R.npad;
+        }
+    }
     /* stage and path tables into shared memory: the sweeps index through them at every stage */
     const int64_t tn = table_ints(R.npad, R.n_stage, R.n_paths);
     if (tn <= tab_cap) {
@@ -2303,13 +2498,26 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     V.store_u(V.hr, i, hr);
                     V.nv[i] = la;
                     if (!is_leaf) {
-                        float xn[NX];
-                        /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
-                        dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
-                            if (c < NX) V.A[(size_t)(a * NX + c) * np + i] = v;
-                            else V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
-                        });
-                        V.store_x(V.f, i, xn);
+                        bool done = false;
+                        if constexpr (MODEL == 2) {
+                            if (V.edge) {   /* per-edge dynamics: the increment of every child's edge */
+                                for (int m = V.fchild[i]; m < V.fchild[i] + V.nchild[i]; ++m) {
+                                    float dl[NX];
+                                    edge_increment<NX>(V, m, xa, u, dl);
+                                    V.store_x(V.f, m, dl);
+                                }
+                                done = true;
+                            }
+                        }
+                        if (!done) {
+                            float xn[NX];
+                            /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
+                            dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
+                                if (c < NX) V.A[(size_t)(a * NX + c) * np + i] = v;
+                                else V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                            });
+                            V.store_x(V.f, i, xn);
+                        }
                     }
                 } else {
                     const bool is_leaf = V.nchild[i] == 0;
@@ -2370,7 +2578,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                 V.load_x(V.q, i, qi);
                 V.load_x(V.X, pa, xp);
                 V.load_x(V.xref, pa, xrp);
-                V.load_x(V.f, pa, fp);
+                V.load_x(V.f, (MODEL == 2 && V.edge) ? i : pa, fp);   /* the increment of the edge into i */
                 float ld = 0.f, dd = 0.f, gx[NX];
                 if (i != 0) {
                     float dv[NX];
@@ -2389,7 +2597,30 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                 }
                 V.nv[(size_t)np + i] = ld;
                 V.nv[2 * (size_t)np + i] = dd;
-                if (nch) {
+                bool edge_done = false;
+                if constexpr (MODEL == 2) {
+                    if (nch && V.edge) {   /* per-edge: sum over children of A_m' lam_m and B_m' lam_m */
+                        float gu[NU];
+                        V.load_u(V.r, i, gu);
+                        for (int m = fc; m < fc + nch; ++m) {
+                            float lm[NX];
+                            V.load_x(V.L, m, lm);
+#pragma unroll
+                            for (int a = 0; a < NX; ++a) {
+                                if (i != 0) {
+#pragma unroll
+                                    for (int b = 0; b < NX; ++b) gx[b] += V.A[(size_t)(a * NX + b) * np + m] * lm[a];
+                                }
+#pragma unroll
+                                for (int b = 0; b < NU; ++b) gu[b] += V.B[(size_t)(a * NU + b) * np + m] * lm[a];
+                            }
+                        }
+#pragma unroll
+                        for (int b = 0; b < NU; ++b) rk = fmaxf(rk, fabsf(gu[b]));
+                        edge_done = true;
+                    }
+                }
+                if (nch && !edge_done) {
                     float Ai[NX][NX], Bi[NX][NU], ri[NU];
 #pragma unroll
                     for (int a = 0; a < NX; ++a) {
@@ -2514,8 +2745,12 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                             float xa[NX], ft[NX];
 #pragma unroll
                             for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + xt[j];
-                            dyn<NX, MODEL>(R, xa, ut, ft);
+                            const bool per_edge = MODEL == 2 && V.edge;
+                            if (!per_edge) dyn<NX, MODEL>(R, xa, ut, ft);
                             for (int m = fc; m < fc + nch; ++m) {
+                                if constexpr (MODEL == 2) {
+                                    if (per_edge) edge_increment<NX>(V, m, xa, ut, ft);
+                                }
 #pragma unroll
                                 for (int j = 0; j < NX; ++j) {
                                     const float lm = V.L[(size_t)j * np + m];

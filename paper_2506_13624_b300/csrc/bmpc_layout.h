@@ -25,8 +25,9 @@ __host__ __device__ constexpr int nsym(int nx) { return nx * (nx + 1) / 2; }
 /* One record per problem; 16-byte aligned, plain data. */
 struct alignas(16) ProbRec {
     int32_t n, npad, nx, nu, model, n_obs, nc, box_on, lane_on, n_stage, has_warm, n_paths;
-    int32_t n_bstage, n_waves, rsv1, rsv2;  /* n_bstage: distinct stages holding branch nodes;
-                                              n_waves: waves of the segment scans (variant 4) */
+    int32_t n_bstage, n_waves, edge_dyn, rsv2;  /* n_bstage: distinct stages holding branch nodes;
+                                                  n_waves: waves of the segment scans (variant 4);
+                                                  edge_dyn: linear dynamics per tree edge (model 2) */
     int64_t off_int;   /* int32 elements from the int region base      */
     int64_t off_in;    /* float elements from the input region base    */
     int64_t off_warm;  /* float elements from the warm-start region base */
@@ -90,19 +91,22 @@ __host__ __device__ inline int64_t table_ints(int npad, int n_stage, int n_paths
     return o.wave - o.sstart;
 }
 
-/* input region: xref[nx] weight[1] obs[6*n_obs] (rows of npad).  Per obstacle the rows hold the
- * ellipse centre cx, cy, the cosine and sine of its heading and 1/a^2, 1/b^2, converted once per
- * upload on the device from the caller's cx, cy, heading, a, b. */
+/* input region: xref[nx] weight[1] obs[6*n_obs] and, with per-edge dynamics, Ae[nx*nx] Be[nx*nu]
+ * (rows of npad).  Per obstacle the rows hold the ellipse centre cx, cy, the cosine and sine of its
+ * heading and 1/a^2, 1/b^2, converted once per upload on the device from the caller's cx, cy,
+ * heading, a, b.  Ae, Be: the matrices of the edge into node m at column m (row-major entries,
+ * one row each; column 0 unused), the layout of the scratch Jacobian rows A, B. */
 constexpr int OBS_ROWS = 6;
 struct InRows {
-    int xref, weight, obs, total;
+    int xref, weight, obs, edge, total;
 };
-__host__ __device__ inline InRows in_rows(int nx, int n_obs) {
+__host__ __device__ inline InRows in_rows(int nx, int n_obs, int edge_dyn = 0) {
     InRows r;
     r.xref = 0;
     r.weight = nx;
     r.obs = r.weight + 1;
-    r.total = r.obs + OBS_ROWS * n_obs;
+    r.edge = r.obs + OBS_ROWS * n_obs;
+    r.total = r.edge + (edge_dyn ? nx * nx + nx * NU : 0);
     return r;
 }
 

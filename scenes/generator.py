@@ -304,6 +304,8 @@ def chain_problem(seed: int, model: int, N: int, n_obs: int = 3):
     scene with horizon N."""
     if model == MODEL_UNICYCLE:
         return unicycle(seed, N=N)
+    if model == MODEL_LINEAR:
+        return mass_spring(seed, N=N, Nr=1, nd=1, constrained=True)
     rng = np.random.default_rng([8, seed, model, N])
     p = _base(model, N, {})
     vr = (0.0, 10.0) if model == MODEL_KINEMATIC else (2.0, 10.0)
@@ -362,6 +364,48 @@ def unicycle(seed: int, N: int = 50, splits=None):
              QNw=np.array([10.0, 10.0, 1.0, 1.0]), Rw=np.array([0.1, 0.1]),
              u_lo=np.array([-2.0, -1.5]), u_hi=np.array([2.0, 1.5]), box_on=1, lane_on=0,
              weight=branch_weights(parent), x0=x0, xref=xref, obs=obs)
+    return _finish(p)
+
+
+def _rk4_linear(Ac, Bc, h):
+    """Discrete matrices of one classical RK4 step of x' = Ac x + Bc u with u held: the RK4 map of a
+    linear system is x+ = (I + hA + (hA)^2/2 + (hA)^3/6 + (hA)^4/24) x + h (I + hA/2 + (hA)^2/6 +
+    (hA)^3/24) B u.  Problem data for the per-edge linear model (it is the plant, not the solver)."""
+    n = Ac.shape[0]
+    hA = h * Ac
+    I = np.eye(n)
+    A = I + hA + hA @ hA / 2 + hA @ hA @ hA / 6 + hA @ hA @ hA @ hA / 24
+    B = h * (I + hA / 2 + hA @ hA / 6 + hA @ hA @ hA / 24) @ Bc
+    return A, B
+
+
+def mass_spring(seed: int, N: int = 20, Nr: int = 2, nd: int = 2, constrained: bool = False):
+    """The tree setting of Sec. V-A: a chain of masses and springs between two walls whose spring
+    constant is uncertain, sampled n_d ways at every stage up to the robust horizon N_r (Z = n_d^N_r
+    scenario paths); each edge of the tree carries the dynamics of its branch's spring constant.
+    Two unit masses (n_x = 4: positions, then velocities) with a force on each (n_u = 2), springs
+    k ~ U[0.5, 1.5] per branch, dt = 0.1 s by RK4, tracking the origin with Q = I, R = 0.1 I,
+    x-bar random; with ``constrained`` the forces are bounded by 0.5."""
+    rng = np.random.default_rng([11, seed])
+    parent, stage = tree_parents(N, {s: nd for s in range(1, Nr + 1)})
+    n = parent.shape[0]
+    dt = 0.1
+    Ae, Be = np.zeros((n, 4, 4)), np.zeros((n, 4, 2))
+    for m in range(1, n):
+        k = rng.uniform(0.5, 1.5) if stage[m] <= Nr else None
+        if k is None:   # past the robust horizon the branch keeps its parent edge's model
+            Ae[m], Be[m] = Ae[parent[m]], Be[parent[m]]
+            continue
+        Kc = np.array([[-2.0 * k, k], [k, -2.0 * k]])
+        Ac = np.block([[np.zeros((2, 2)), np.eye(2)], [Kc, np.zeros((2, 2))]])
+        Bc = np.vstack([np.zeros((2, 2)), np.eye(2)])
+        Ae[m], Be[m] = _rk4_linear(Ac, Bc, dt)
+    p = dict(model=MODEL_LINEAR, nx=4, nu=2, dt=dt, parent=parent, stage=stage,
+             params=np.array(MODEL_PARAMS_LINEAR), Qw=np.ones(4), QNw=np.ones(4), Rw=np.full(2, 0.1),
+             u_lo=-np.ones(2) * (0.5 if constrained else 1e3), u_hi=np.ones(2) * (0.5 if constrained else 1e3),
+             box_on=1 if constrained else 0, lane_on=0, weight=branch_weights(parent),
+             x0=np.concatenate([rng.uniform(-1.0, 1.0, 2), np.zeros(2)]), xref=np.zeros((n, 4)),
+             obs=np.zeros((n, 0, 5)), Aedge=f32(Ae), Bedge=f32(Be))
     return _finish(p)
 
 

@@ -71,7 +71,7 @@ def test_batch_bytes_scale_with_nodes():
 
 
 @pytest.mark.parametrize("mutate", ["not_level_order", "parent_after", "bad_root", "bad_model", "too_many_obs",
-                                    "one_node", "bad_substeps"])
+                                    "one_node", "bad_substeps", "edge_on_vehicle"])
 def test_invalid_trees_rejected_on_host(mutate):
     p = dict(scenes.config1(0))
     par = p["parent"].copy()
@@ -92,6 +92,9 @@ def test_invalid_trees_rejected_on_host(mutate):
     elif mutate == "bad_substeps":
         p["params"] = p["params"].copy()
         p["params"][9] = 0.0
+    elif mutate == "edge_on_vehicle":               # per-edge dynamics exist for the linear model only
+        p["Aedge"] = np.zeros((p["n"], 4, 4))
+        p["Bedge"] = np.zeros((p["n"], 4, 2))
     p["parent"] = par
     rc, *_ = _sizes([p])
     assert rc == bmpc.ERR_INVALID

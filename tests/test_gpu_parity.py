@@ -644,3 +644,39 @@ def test_scan_variant_one_iteration_against_the_oracle_scan(cfg, k):
             if c.size:
                 d = float(np.abs(a - c).max()) / max(1.0, float(np.abs(c).max()))
                 assert d <= STEP_TOL[key], (cfg, seed, key, d)
+
+
+# ------------------------------------------------------------------ per-branch dynamics (Sec. V-A)
+@pytest.mark.parametrize("variant,bt", [(1, 64), (2, 64), (0, 256)])
+def test_per_edge_dynamics_one_iteration(variant, bt):
+    """Mass-spring trees whose spring constant differs per branch (every edge its own A_m, B_m): the
+    linear-quadratic problem is solved in one iteration, equal to the oracle's (which equals the dense
+    QP solution, pinned on the CPU)."""
+    ps = [scenes.mass_spring(0, N=20, Nr=2), scenes.mass_spring(1, N=12, Nr=3), scenes.mass_spring(2, N=30, Nr=5)]
+    gres = _gpu(ps, variant=variant, block_threads=bt)
+    for p, g in zip(ps, gres):
+        r = _orc(p)
+        assert g["status"] == oracle.OK and g["inner_iters"] == 1 == r["inner_iters"]
+        np.testing.assert_allclose(g["u"], r["u"], atol=1e-4 * max(1.0, np.abs(r["u"]).max()))
+        np.testing.assert_allclose(g["x"], r["x"], atol=1e-4 * max(1.0, np.abs(r["x"]).max()))
+
+
+def test_per_edge_dynamics_constrained_parity():
+    """The same trees with bounded forces (the AL method with active input bounds) against the oracle."""
+    ps = [scenes.mass_spring(s, N=20, Nr=3, constrained=True) for s in range(4)]
+    print(_run_config(ps, min_match=1.0))
+    print(_run_config(ps, min_match=1.0, variant=1))
+
+
+def test_per_edge_dynamics_refuses_sweeps_without_edges():
+    """The 8-lane, scan and jump sweeps read one model per node: a batch with per-edge dynamics is
+    refused for them, with nothing launched."""
+    from paper_2506_13624_b300 import bmpc
+    b = bmpc.Batch([scenes.mass_spring(0)])
+    b.set_problems()
+    for v in (3, 4, 5):
+        with pytest.raises(RuntimeError):
+            b.solve(bmpc.default_opts(variant=v))
+    b.solve(bmpc.default_opts(variant=2))
+    assert b.get_solutions()[0]["status"] == oracle.OK
+    b.close()

@@ -174,8 +174,9 @@ def _random_lqr(rng, parent, nx, nu):
     return leaf, Q, M, R, q, r, A, B, c
 
 
-def _dense_kkt(parent, leaf, Q, M, R, q, r, A, B, c):
-    """Dense KKT system of Eq. (lqr_tree_approx) with dx_0 = 0: returns dx, du, lam."""
+def _dense_kkt(parent, leaf, Q, M, R, q, r, A, B, c, edge=False):
+    """Dense KKT system of Eq. (lqr_tree_approx) with dx_0 = 0: returns dx, du, lam.  A, B per parent,
+    or per edge (row m: the edge into m) with edge=True."""
     n, nx, nu = len(parent), Q.shape[1], R.shape[1]
     uidx = {}
     off = n * nx
@@ -204,8 +205,8 @@ def _dense_kkt(parent, leaf, Q, M, R, q, r, A, B, c):
         pnt = parent[m]
         rows = slice(m * nx, (m + 1) * nx)
         E[rows, m * nx:(m + 1) * nx] = np.eye(nx)
-        E[rows, pnt * nx:(pnt + 1) * nx] -= A[pnt]
-        E[rows, uidx[pnt]:uidx[pnt] + nu] -= B[pnt]
+        E[rows, pnt * nx:(pnt + 1) * nx] -= A[m] if edge else A[pnt]
+        E[rows, uidx[pnt]:uidx[pnt] + nu] -= B[m] if edge else B[pnt]
         e[rows] = c[m]
     K = np.block([[H, E.T], [E, np.zeros((ncon, ncon))]])
     sol = np.linalg.solve(K, np.concatenate([-h, e]))
@@ -230,6 +231,111 @@ def test_tree_lqr_equals_dense_kkt(seed):
     np.testing.assert_allclose(dx, dx2, atol=1e-10 * scale)
     np.testing.assert_allclose(du, du2, atol=1e-10 * scale)
     np.testing.assert_allclose(lam[1:], lam2[1:], atol=1e-10 * scale)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_per_edge_tree_lqr_equals_dense_kkt(seed):
+    """Per-branch dynamics (Sec. V-A's trees: every edge its own A_m, B_m): the tree Riccati recursion
+    and the scan form both equal the dense KKT solution of the tree LQR with per-edge matrices."""
+    rng = np.random.default_rng(200 + seed)
+    nx, nu = (4, 2) if seed % 2 == 0 else (3, 1)
+    parent = _random_tree(rng) if seed < 4 else _scan_case_tree(seed)[1]
+    leaf, Q, M, R, q, r, A, B, c = _random_lqr(rng, parent, nx, nu)
+    n = len(parent)
+    Ae = np.eye(nx) + 0.3 * rng.standard_normal((n, nx, nx))     # a different matrix on every edge
+    Be = rng.standard_normal((n, nx, nu))
+    dx2, du2, lam2 = _dense_kkt(parent, leaf, Q, M, R, q, r, Ae, Be, c, edge=True)
+    scale = max(1.0, np.abs(dx2).max(), np.abs(lam2).max())
+    for fn in (oracle.tree_lqr, oracle.tree_lqr_scan):
+        K, k, P, pv, dx, du, lam = fn(parent, Q, M, R, q, r, Ae, Be, c, edge=True)
+        np.testing.assert_allclose(dx, dx2, atol=1e-9 * scale)
+        np.testing.assert_allclose(du, du2, atol=1e-9 * scale)
+        np.testing.assert_allclose(lam[1:], lam2[1:], atol=1e-9 * scale)
+    # with the parent's matrices copied to every edge the per-edge path is the per-parent one
+    Ap = np.array([A[parent[m]] if m else A[0] for m in range(n)])
+    Bp = np.array([B[parent[m]] if m else B[0] for m in range(n)])
+    got = oracle.tree_lqr(parent, Q, M, R, q, r, Ap, Bp, c, edge=True)
+    ref = oracle.tree_lqr(parent, Q, M, R, q, r, A, B, c)
+    for a, b in zip(got, ref):
+        np.testing.assert_allclose(a, b, atol=1e-12 * max(1.0, np.abs(b).max()))
+
+
+def _dense_lq_solution(p):
+    """The whole LQ problem of a per-edge linear tree (no constraints) as one equality-constrained QP:
+    min sum_i w_i [1/2 (x_i - xref_i)' Q (x_i - xref_i) + 1/2 u_i' R u_i] s.t. x_0 = x-bar,
+    x_m = A_m x_p(m) + B_m u_p(m); returns x, u."""
+    n, nx, nu, par = p["n"], p["nx"], p["nu"], p["parent"]
+    leaf = np.ones(n, bool)
+    leaf[par[1:]] = False
+    nz = n * (nx + nu)
+    H, h = np.zeros((nz, nz)), np.zeros(nz)
+    xs = lambda i: slice(i * nx, (i + 1) * nx)
+    us = lambda i: slice(n * nx + i * nu, n * nx + (i + 1) * nu)
+    for i in range(n):
+        Qd = np.diag(p["QNw"] if leaf[i] else p["Qw"]) * p["weight"][i]
+        H[xs(i), xs(i)] = Qd
+        h[xs(i)] = -Qd @ p["xref"][i]
+        H[us(i), us(i)] = np.diag(p["Rw"]) * p["weight"][i] if not leaf[i] else np.eye(nu)
+    rows = []
+    rhs = []
+    E0 = np.zeros((nx, nz))
+    E0[:, xs(0)] = np.eye(nx)
+    rows.append(E0)
+    rhs.append(p["x0"])
+    for m in range(1, n):
+        Em = np.zeros((nx, nz))
+        Em[:, xs(m)] = np.eye(nx)
+        Em[:, xs(par[m])] -= p["Aedge"][m]
+        Em[:, us(par[m])] -= p["Bedge"][m]
+        rows.append(Em)
+        rhs.append(np.zeros(nx))
+    for i in np.where(leaf)[0]:          # leaves have no input: pin it to zero
+        El = np.zeros((nu, nz))
+        El[:, us(i)] = np.eye(nu)
+        rows.append(El)
+        rhs.append(np.zeros(nu))
+    E, e = np.vstack(rows), np.concatenate(rhs)
+    Kk = np.block([[H, E.T], [E, np.zeros((E.shape[0], E.shape[0]))]])
+    z = np.linalg.solve(Kk, np.concatenate([-h, e]))[:nz]
+    return z[:n * nx].reshape(n, nx), z[n * nx:].reshape(n, nu)
+
+
+@pytest.mark.parametrize("seed,N,Nr", [(0, 20, 2), (1, 12, 3), (2, 30, 5)])
+def test_per_edge_lq_solve_is_the_qp_solution(seed, N, Nr):
+    """The mass-spring tree with a spring constant per branch (Sec. V-A): one iteration of the method
+    reaches the solution of the whole QP, solved here as one dense equality-constrained system."""
+    p = scenes.mass_spring(seed, N=N, Nr=Nr)
+    r = oracle.solve(p)
+    assert r["status"] == oracle.OK and r["inner_iters"] == 1
+    x, u = _dense_lq_solution(p)
+    leaf = np.ones(p["n"], bool)
+    leaf[p["parent"][1:]] = False
+    np.testing.assert_allclose(r["x"], x, atol=1e-9 * max(1.0, np.abs(x).max()))
+    np.testing.assert_allclose(r["u"][~leaf], u[~leaf], atol=1e-9 * max(1.0, np.abs(u).max()))
+
+
+def test_per_edge_model_changes_the_plan_only_after_the_split():
+    """Two trees that differ only in one branch's spring constant plan the same root input up to the
+    hedging the tree imposes, and the branches' states differ only below the split."""
+    p = scenes.mass_spring(4, N=15, Nr=1)
+    q = dict(p)
+    q["Aedge"] = p["Aedge"].copy()
+    first_child = int(np.where(p["parent"] == 0)[0][0])
+    chain = [first_child]
+    while True:
+        nxt = np.where(p["parent"] == chain[-1])[0]
+        if len(nxt) == 0:
+            break
+        chain.append(int(nxt[0]))
+    Kc = np.array([[-2.0 * 3.0, 3.0], [3.0, -2.0 * 3.0]])
+    Ac = np.block([[np.zeros((2, 2)), np.eye(2)], [Kc, np.zeros((2, 2))]])
+    A3, _ = scenes.generator._rk4_linear(Ac, np.vstack([np.zeros((2, 2)), np.eye(2)]), 0.1)
+    for m in chain:
+        q["Aedge"][m] = scenes.f32(A3)
+    rp, rq = oracle.solve(p), oracle.solve(q)
+    assert rp["status"] == rq["status"] == oracle.OK
+    assert np.abs(rp["u"][0] - rq["u"][0]).max() > 1e-6          # the root hedges over both models
+    assert np.abs(rp["x"][chain[0]] - rq["x"][chain[0]]).max() > 1e-6
 
 
 def test_single_path_riccati_reaches_dare():
