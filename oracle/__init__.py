@@ -46,7 +46,7 @@ class Opts(C.Structure):
                 ("eta0", C.c_double), ("a_omega", C.c_double), ("b_omega", C.c_double),
                 ("a_eta", C.c_double), ("b_eta", C.c_double), ("rho0", C.c_double),
                 ("rho_max", C.c_double), ("mu0", C.c_double), ("beta", C.c_double),
-                ("ls_rel_eps", C.c_double), ("lqr_scan", C.c_int), ("cap_rule", C.c_int),
+                ("ls_rel_eps", C.c_double), ("lqr_scan", C.c_int), ("hessian", C.c_int), ("cap_rule", C.c_int),
                 ("trace", C.c_void_p), ("trace_user", C.c_void_p)]
 
 
@@ -262,3 +262,34 @@ def aug_lagrangian(p, x, u, y, rho):
     m = _Marshal(p)
     yy = _d(y) if n_con(p) else np.zeros((p["n"], 1))
     return lib().orc_aug_lagrangian(C.byref(m.s), _ptr(_d(x)), _ptr(_d(u)), _ptr(yy), C.c_double(rho))
+
+
+def dyn_hessian(p, x, u, mu):
+    """sum_i mu_i d^2 f_i / dz dz of the discrete dynamics at (x, u), z = (x, u) (exact, hyper-dual)."""
+    m = _Marshal(p)
+    nz = p["nx"] + p["nu"]
+    H = np.zeros((nz, nz))
+    rc = lib().orc_dyn_hessian(C.byref(m.s), _ptr(_d(x)), _ptr(_d(u)), _ptr(_d(mu)), _ptr(H))
+    if rc != 0:
+        raise RuntimeError(f"orc_dyn_hessian failed: {rc}")
+    return H
+
+
+def obs_hessian(ob, X, Y):
+    out = np.zeros(3)
+    lib().orc_obs_hessian(_ptr(_d(ob)), C.c_double(X), C.c_double(Y), _ptr(out))
+    return out
+
+
+def jacobi_eig(S):
+    S = _d(S)
+    n = S.shape[0]
+    ev, V = np.zeros(n), np.zeros((n, n))
+    lib().orc_jacobi_eig(n, _ptr(S), _ptr(ev), _ptr(V))
+    return ev, V
+
+
+def eig_modify(S):
+    S = _d(S).copy()
+    lib().orc_eig_modify(S.shape[0], _ptr(S))
+    return S

@@ -90,6 +90,8 @@ typedef struct {
     double eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta;
     double rho0, rho_max, mu0, beta, ls_rel_eps;
     int lqr_scan;           /* 1: the search direction by the scans of Sec. III-B (orc_tree_lqr_scan) */
+    int hessian;            /* 0: Gauss-Newton; 1: exact Hessian of the Lagrangian with eigenvalue
+                               modification (Sec. IV-A), see exact_hessian */
     int cap_rule;           /* 0: Algorithm 1 (failure keeps y, rho <- min(tau rho, rho_max));
                                1: a failure at rho_max applies y <- max(0, y + rho g) */
     orc_trace_fn trace;     /* NULL: no trace */
@@ -895,6 +897,194 @@ int orc_tree_lqr_scan(int n, const int *parent, int nx, int nu, const double *Q,
     return st;
 }
 
+/* ------------------------------------------------------------ exact second derivatives */
+/* Hyper-dual numbers (Fike and Alonso, 2011): a + b e1 + c e2 + d e1 e2 with e1^2 = e2^2 = 0.
+ * Evaluating a function at z + e1 v + e2 w gives its value in a, the directional derivatives
+ * along v and w in b and c, and the second derivative v' H w in d, exactly (no truncation). */
+typedef struct { double a, b, c, d; } hd;
+
+static hd hd_c(double v) { hd r = {v, 0.0, 0.0, 0.0}; return r; }
+static hd hd_add(hd x, hd y) { hd r = {x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; return r; }
+static hd hd_sub(hd x, hd y) { hd r = {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; return r; }
+static hd hd_scale(hd x, double s) { hd r = {s * x.a, s * x.b, s * x.c, s * x.d}; return r; }
+static hd hd_mul(hd x, hd y) {
+    hd r = {x.a * y.a, x.a * y.b + x.b * y.a, x.a * y.c + x.c * y.a, x.a * y.d + x.b * y.c + x.c * y.b + x.d * y.a};
+    return r;
+}
+/* f(x) for a scalar function with value f0, first derivative f1 and second derivative f2 at x.a */
+static hd hd_fn(hd x, double f0, double f1, double f2) {
+    hd r = {f0, f1 * x.b, f1 * x.c, f1 * x.d + f2 * x.b * x.c};
+    return r;
+}
+static hd hd_inv(hd x) { return hd_fn(x, 1.0 / x.a, -1.0 / (x.a * x.a), 2.0 / (x.a * x.a * x.a)); }
+static hd hd_div(hd x, hd y) { return hd_mul(x, hd_inv(y)); }
+static hd hd_sin(hd x) { return hd_fn(x, sin(x.a), cos(x.a), -sin(x.a)); }
+static hd hd_cos(hd x) { return hd_fn(x, cos(x.a), -sin(x.a), -cos(x.a)); }
+static hd hd_tan(hd x) {
+    const double t = tan(x.a), s = 1.0 + t * t;
+    return hd_fn(x, t, s, 2.0 * t * s);
+}
+static hd hd_atan(hd x) {
+    const double s = 1.0 + x.a * x.a;
+    return hd_fn(x, atan(x.a), 1.0 / s, -2.0 * x.a / (s * s));
+}
+static hd hd_sqrt(hd x) {
+    const double r = sqrt(x.a);
+    return hd_fn(x, r, 0.5 / r, -0.25 / (r * x.a));
+}
+
+/* The continuous right-hand side of rhs() in hyper-dual arithmetic (the same formulas). */
+static void rhs_hd(const orc_problem *P, const hd *s, const hd *u, hd *f) {
+    const double *prm = P->params;
+    if (P->model == 0) {
+        const double L = prm[0];
+        f[0] = hd_mul(s[3], hd_cos(s[2]));
+        f[1] = hd_mul(s[3], hd_sin(s[2]));
+        f[2] = hd_scale(hd_mul(s[3], hd_tan(u[1])), 1.0 / L);
+        f[3] = u[0];
+        return;
+    }
+    if (P->model == 3) {
+        f[0] = hd_mul(s[3], hd_cos(s[2]));
+        f[1] = hd_mul(s[3], hd_sin(s[2]));
+        f[2] = u[1];
+        f[3] = u[0];
+        return;
+    }
+    /* dynamic bicycle */
+    const double m = prm[1], Iz = prm[2], lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6];
+    const double vmin = prm[7], veps = prm[8];
+    const hd psi = s[2], vx = s[3], vy = s[4], r = s[5], a = u[0], d = u[1];
+    const hd dv = hd_sub(vx, hd_c(vmin));
+    const hd w = hd_sqrt(hd_add(hd_mul(dv, dv), hd_c(veps * veps)));
+    const hd vb = hd_scale(hd_add(hd_add(vx, hd_c(vmin)), w), 0.5);
+    const hd tf = hd_div(hd_add(vy, hd_scale(r, lf)), vb), tr = hd_div(hd_sub(vy, hd_scale(r, lr)), vb);
+    const hd af = hd_sub(hd_atan(tf), d), ar = hd_atan(tr);
+    const hd Ff = hd_scale(af, -Cf), Fr = hd_scale(ar, -Cr);
+    const hd cp = hd_cos(psi), sp = hd_sin(psi);
+    f[0] = hd_sub(hd_mul(vx, cp), hd_mul(vy, sp));
+    f[1] = hd_add(hd_mul(vx, sp), hd_mul(vy, cp));
+    f[2] = r;
+    f[3] = hd_add(a, hd_mul(r, vy));
+    f[4] = hd_sub(hd_scale(hd_add(Ff, Fr), 1.0 / m), hd_mul(r, vx));
+    f[5] = hd_scale(hd_sub(hd_scale(Ff, lf), hd_scale(Fr, lr)), 1.0 / Iz);
+}
+
+/* Second derivatives of the discrete dynamics: H[j][k] = sum_i mu_i d^2 f_i / dz_j dz_k with z = (x, u),
+ * for the RK4 map of orc_dynamics (n_sub substeps) evaluated in hyper-dual arithmetic, one pair
+ * (j, k) at a time.  The linear model has none. */
+static void dyn_hessian(const orc_problem *P, const double *x, const double *u, const double *mu, double *H) {
+    const int nx = P->nx, nu = P->nu, nz = nx + nu;
+    memset(H, 0, sizeof(double) * nz * nz);
+    if (P->model == 2) return;
+    int n_sub = (int)P->params[9];
+    if (n_sub < 1) n_sub = 1;
+    const double h = P->dt / n_sub;
+    static const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+    static const double wts[4] = {1.0, 2.0, 2.0, 1.0};
+    for (int j = 0; j < nz; ++j)
+        for (int k = j; k < nz; ++k) {
+            hd z[MAXX], uu[MAXU];
+            for (int i = 0; i < nx; ++i) z[i] = hd_c(x[i]);
+            for (int i = 0; i < nu; ++i) uu[i] = hd_c(u[i]);
+            hd *vj = j < nx ? &z[j] : &uu[j - nx], *vk = k < nx ? &z[k] : &uu[k - nx];
+            vj->b = 1.0;
+            vk->c = 1.0;
+            for (int sub = 0; sub < n_sub; ++sub) {
+                hd kp[MAXX], ks[MAXX];
+                for (int i = 0; i < nx; ++i) { kp[i] = hd_c(0.0); ks[i] = hd_c(0.0); }
+                for (int st = 0; st < 4; ++st) {
+                    hd zs[MAXX], kk[MAXX];
+                    for (int i = 0; i < nx; ++i) zs[i] = hd_add(z[i], hd_scale(kp[i], cst[st] * h));
+                    rhs_hd(P, zs, uu, kk);
+                    for (int i = 0; i < nx; ++i) { ks[i] = hd_add(ks[i], hd_scale(kk[i], wts[st])); kp[i] = kk[i]; }
+                }
+                for (int i = 0; i < nx; ++i) z[i] = hd_add(z[i], hd_scale(ks[i], h / 6.0));
+            }
+            double v = 0.0;
+            for (int i = 0; i < nx; ++i) v += mu[i] * z[i].d;
+            H[j * nz + k] = v;
+            H[k * nz + j] = v;
+        }
+}
+
+/* Second derivatives of the keep-out value g = 1 - sqrt((d_par/a)^2 + (d_perp/b)^2 + eps) in (X, Y),
+ * hyper-dual like dyn_hessian: out = [gxx, gxy, gyy]. */
+static void obs_hessian(const double *ob, double X, double Y, double *out) {
+    const double ch = cos(ob[2]), sh = sin(ob[2]), a2 = ob[3] * ob[3], b2 = ob[4] * ob[4];
+    const int pairs[3][2] = {{0, 0}, {0, 1}, {1, 1}};
+    for (int t = 0; t < 3; ++t) {
+        hd px = hd_c(X), py = hd_c(Y);
+        hd *v1 = pairs[t][0] ? &py : &px, *v2 = pairs[t][1] ? &py : &px;
+        v1->b = 1.0;
+        v2->c = 1.0;
+        const hd dx = hd_sub(px, hd_c(ob[0])), dy = hd_sub(py, hd_c(ob[1]));
+        const hd dpar = hd_add(hd_scale(dx, ch), hd_scale(dy, sh)), dper = hd_sub(hd_scale(dy, ch), hd_scale(dx, sh));
+        const hd q = hd_add(hd_add(hd_scale(hd_mul(dpar, dpar), 1.0 / a2), hd_scale(hd_mul(dper, dper), 1.0 / b2)),
+                            hd_c(OBS_EPS));
+        out[t] = -hd_sqrt(q).d;
+    }
+}
+
+/* Eigen-decomposition of a symmetric n x n matrix by cyclic Jacobi rotations (Golub and Van Loan,
+ * Sec. 8.5): S = V diag(ev) V'.  Sweeps until the off-diagonal mass is below 1e-30 of the total. */
+static void jacobi_eig(int n, const double *S, double *ev, double *Vm) {
+    double Aw[MAXN * MAXN];
+    memcpy(Aw, S, sizeof(double) * n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Vm[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                tot += Aw[i * n + j] * Aw[i * n + j];
+                if (i != j) off += Aw[i * n + j] * Aw[i * n + j];
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = Aw[p * n + q];
+                if (apq == 0.0) continue;
+                const double theta = (Aw[q * n + q] - Aw[p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {   /* A <- J' A J with the rotation in the (p, q) plane */
+                    const double akp = Aw[k * n + p], akq = Aw[k * n + q];
+                    Aw[k * n + p] = c * akp - s * akq;
+                    Aw[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = Aw[p * n + k], aqk = Aw[q * n + k];
+                    Aw[p * n + k] = c * apk - s * aqk;
+                    Aw[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = Vm[k * n + p], vkq = Vm[k * n + q];
+                    Vm[k * n + p] = c * vkp - s * vkq;
+                    Vm[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) ev[i] = Aw[i * n + i];
+}
+
+/* Eigenvalue modification (Nocedal and Wright, Sec. 3.4): S <- V diag(max(ev, delta)) V' with
+ * delta = EIG_FLOOR max(1, max |ev|), so that the modified block is positive definite. */
+#define EIG_FLOOR 1e-6
+static void eig_modify(int n, double *S) {
+    double ev[MAXN], Vm[MAXN * MAXN], emax = 1.0;
+    jacobi_eig(n, S, ev, Vm);
+    for (int i = 0; i < n; ++i) if (fabs(ev[i]) > emax) emax = fabs(ev[i]);
+    const double delta = EIG_FLOOR * emax;
+    for (int i = 0; i < n; ++i) if (ev[i] < delta) ev[i] = delta;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) v += Vm[i * n + k] * ev[k] * Vm[j * n + k];
+            S[i * n + j] = v;
+        }
+}
+
 /* ------------------------------------------------------------ AL quadratisation (Sec. IV-A) */
 typedef struct {
     tree_t T;
@@ -1008,6 +1198,61 @@ static void linearise(const orc_problem *P, work_t *W, const double *x, const do
         for (int j = 0; j < nx; ++j) W->d[(size_t)m * nx + j] = W->f[(size_t)m * nx + j] - x[(size_t)m * nx + j];
     }
     W->La = La;
+}
+
+/* The exact Hessian option of Sec. IV-A: every node's block [[Q, M'], [M, R]] of the Hessian of the
+ * Lagrangian L_a + sum lam_m'(f_m - x_m) in (x_i, u_i), i.e. the Gauss-Newton block of linearise plus
+ * the curvature of the active keep-out rows (s_c grad^2 g_c with s_c = y_c + rho g_c > 0) and the
+ * dynamics' second derivatives weighted by the children's multipliers (sum_m lam_m' grad^2 f_m),
+ * followed by the eigenvalue modification that makes it positive definite. */
+static void exact_hessian(const orc_problem *P, work_t *W, const double *x, const double *u, const double *lam,
+                          const double *y, double rho) {
+    const int n = P->n, nx = P->nx, nu = P->nu, nc = W->nc;
+    const tree_t *T = &W->T;
+    for (int i = 0; i < n; ++i) {
+        const int leaf = T->n_child[i] == 0, nz = leaf ? nx : nx + nu;
+        double S[MAXN * MAXN];
+        const double *Qi = W->Q + (size_t)i * nx * nx, *Mi = W->M + (size_t)i * nu * nx, *Ri = W->R + (size_t)i * nu * nu;
+        for (int a = 0; a < nx; ++a)
+            for (int b = 0; b < nx; ++b) S[a * nz + b] = Qi[a * nx + b];
+        if (!leaf)
+            for (int a = 0; a < nu; ++a) {
+                for (int b = 0; b < nx; ++b) S[(nx + a) * nz + b] = S[b * nz + nx + a] = Mi[a * nx + b];
+                for (int b = 0; b < nu; ++b) S[(nx + a) * nz + nx + b] = Ri[a * nu + b];
+            }
+        /* keep-out curvature (box and lane rows are linear) */
+        const int row0 = 2 * nu * P->box_on;
+        for (int o = 0; o < P->n_obs && i != 0; ++o) {
+            const int c = row0 + o;
+            const double sc = y[(size_t)i * nc + c] + rho * W->g[(size_t)i * nc + c];
+            if (!(W->ex[(size_t)i * nc + c] && sc > 0.0)) continue;
+            double hxy[3];
+            obs_hessian(P->obs + ((size_t)i * P->n_obs + o) * 5, x[(size_t)i * nx], x[(size_t)i * nx + 1], hxy);
+            S[0] += sc * hxy[0];
+            S[1] += sc * hxy[1];
+            S[nz] += sc * hxy[1];
+            S[nz + 1] += sc * hxy[2];
+        }
+        /* the dynamics' curvature, weighted by the children's multipliers */
+        if (!leaf) {
+            double mu[MAXX] = {0}, H[MAXN * MAXN];
+            for (int t = 0; t < T->n_child[i]; ++t) {
+                const int m = T->child[T->first_child[i] + t];
+                for (int e = 0; e < nx; ++e) mu[e] += lam[(size_t)m * nx + e];
+            }
+            dyn_hessian(P, x + (size_t)i * nx, u + (size_t)i * nu, mu, H);
+            for (int e = 0; e < nz * nz; ++e) S[e] += H[e];
+        }
+        eig_modify(nz, S);
+        double *Qw = W->Q + (size_t)i * nx * nx, *Mw = W->M + (size_t)i * nu * nx, *Rw = W->R + (size_t)i * nu * nu;
+        for (int a = 0; a < nx; ++a)
+            for (int b = 0; b < nx; ++b) Qw[a * nx + b] = S[a * nz + b];
+        if (!leaf)
+            for (int a = 0; a < nu; ++a) {
+                for (int b = 0; b < nx; ++b) Mw[a * nx + b] = S[(nx + a) * nz + b];
+                for (int b = 0; b < nu; ++b) Rw[a * nu + b] = S[(nx + a) * nz + nx + b];
+            }
+    }
 }
 
 /* KKT residual of the relaxed problem Eq. (relax_bmpc) at the linearisation point:
@@ -1126,6 +1371,7 @@ void orc_default_opts(orc_opts *o) {
     o->beta = 1e-4;
     o->ls_rel_eps = 1e-6;
     o->lqr_scan = 0;
+    o->hessian = 0;
     o->cap_rule = 0;
     o->trace = NULL;
     o->trace_user = NULL;
@@ -1209,6 +1455,7 @@ int orc_solve(const orc_problem *P, const orc_opts *O_in, const double *wx, cons
         /* inner loop: iLQR steps on the relaxed problem until r_kkt <= omega */
         for (;;) {
             linearise(P, &W, x, u, y, rho);
+            if (O.hessian) exact_hessian(P, &W, x, u, lam, y, rho);
             r_kkt = kkt_relaxed(P, &W, lam);
             if (r_kkt <= omega) break;
             if (inner >= O.max_iters) goto done;
@@ -1441,4 +1688,24 @@ double orc_aug_lagrangian(const orc_problem *P, const double *x, const double *u
     double v = W.La;
     work_free(&W);
     return v;
+}
+
+/* Test entry points of the exact-Hessian option: the dynamics' second derivatives weighted by mu
+ * (H [nz][nz]), the keep-out curvature ([gxx, gxy, gyy] at X, Y of obstacle ob[5]), the Jacobi
+ * eigen-decomposition and the eigenvalue modification of a symmetric n x n matrix (in place). */
+int orc_dyn_hessian(const orc_problem *P, const double *x, const double *u, const double *mu, double *H) {
+    if (!check_problem(P)) return ORC_ERR_INVALID;
+    dyn_hessian(P, x, u, mu, H);
+    return ORC_OK;
+}
+void orc_obs_hessian(const double *ob, double X, double Y, double *out) { obs_hessian(ob, X, Y, out); }
+int orc_jacobi_eig(int n, const double *S, double *ev, double *Vm) {
+    if (n < 1 || n > MAXN) return ORC_ERR_INVALID;
+    jacobi_eig(n, S, ev, Vm);
+    return ORC_OK;
+}
+int orc_eig_modify(int n, double *S) {
+    if (n < 1 || n > MAXN) return ORC_ERR_INVALID;
+    eig_modify(n, S);
+    return ORC_OK;
 }

@@ -630,3 +630,91 @@ def test_full_solve_with_scan_lqr_equals_riccati(cfg, seed):
     for key in ("x", "u", "lam", "y"):
         scale = max(1.0, np.abs(a[key]).max())
         np.testing.assert_allclose(b[key], a[key], atol=1e-8 * scale, err_msg=key)
+
+
+# ------------------------------------------------------------------ exact Hessian option (Sec. IV-A)
+@pytest.mark.parametrize("cfg", [1, 3, "unicycle"])
+def test_dynamics_second_derivatives_match_differences_of_the_jacobian(cfg):
+    """sum_i mu_i d^2 f_i / dz dz of the RK4 map by hyper-dual numbers against central differences of
+    the analytic Jacobian (itself pinned by central differences of f)."""
+    p = scenes.unicycle(1) if cfg == "unicycle" else scenes.instances(cfg, 1)[0]
+    rng = np.random.default_rng(11)
+    nx, nu = p["nx"], p["nu"]
+    for _ in range(3):
+        x = p["x0"] + 0.5 * rng.standard_normal(nx)
+        u = 0.3 * rng.standard_normal(nu)
+        mu = rng.standard_normal(nx)
+        H = oracle.dyn_hessian(p, x, u, mu)
+        assert np.allclose(H, H.T)
+        h = 1e-5
+        cols = []
+        for j in range(nx + nu):
+            e = np.zeros(nx + nu)
+            e[j] = h
+            _, Ap, Bp = oracle.dynamics(p, x + e[:nx], u + e[nx:])
+            _, Am, Bm = oracle.dynamics(p, x - e[:nx], u - e[nx:])
+            Jp, Jm = np.hstack([Ap, Bp]), np.hstack([Am, Bm])
+            cols.append(mu @ (Jp - Jm) / (2 * h))
+        Hfd = np.array(cols).T
+        np.testing.assert_allclose(H, Hfd, rtol=0, atol=1e-6 * max(1.0, np.abs(H).max()))
+        assert np.abs(H[:2]).max() == 0.0 or p["model"] == 2   # positions do not enter the vehicle dynamics
+
+
+def test_keep_out_curvature_matches_differences_of_the_gradient():
+    p = scenes.config1(0)
+    ob = p["obs"][5, 0]
+    for X, Y in ((ob[0] + 2.0, ob[1] + 0.7), (ob[0] - 1.0, ob[1] - 1.6), (ob[0] + 3.5, ob[1])):
+        hxy = oracle.obs_hessian(ob, X, Y)
+        h = 1e-5
+        x = np.array([X, Y, 0.0, 1.0])
+        grads = []
+        for e in (np.array([h, 0, 0, 0]), np.array([0, h, 0, 0])):
+            q = dict(p)
+            _, Jp, _, _ = oracle.constraints(q, 5, False, x + e, np.zeros(2))
+            _, Jm, _, _ = oracle.constraints(q, 5, False, x - e, np.zeros(2))
+            grads.append((Jp[4, :2] - Jm[4, :2]) / (2 * h))
+        fd = np.array(grads)
+        np.testing.assert_allclose([hxy[0], hxy[1], hxy[2]], [fd[0, 0], fd[0, 1], fd[1, 1]], atol=1e-6)
+
+
+@pytest.mark.parametrize("n", [3, 6, 8])
+def test_jacobi_eigen_decomposition_and_modification(n):
+    """The cyclic Jacobi eigen-decomposition against numpy's symmetric eigensolver, and the eigenvalue
+    modification: positive definite afterwards, eigenvectors kept, eigenvalues above the floor kept."""
+    rng = np.random.default_rng(n)
+    F = rng.standard_normal((n, n))
+    S = F + F.T
+    ev, V = oracle.jacobi_eig(S)
+    np.testing.assert_allclose(np.sort(ev), np.linalg.eigvalsh(S), atol=1e-12 * np.abs(ev).max())
+    np.testing.assert_allclose(V @ np.diag(ev) @ V.T, S, atol=1e-12 * np.abs(S).max())
+    np.testing.assert_allclose(V.T @ V, np.eye(n), atol=1e-12)
+    Sm = oracle.eig_modify(S)
+    em = np.linalg.eigvalsh(Sm)
+    floor = 1e-6 * max(1.0, np.abs(ev).max())
+    assert em.min() >= floor * (1 - 1e-9)
+    keep = np.sort(ev[ev > floor])
+    np.testing.assert_allclose(em[-len(keep):], keep, atol=1e-10 * np.abs(ev).max())
+    Spd = F @ F.T + np.eye(n)
+    np.testing.assert_allclose(oracle.eig_modify(Spd), Spd, atol=1e-10 * np.abs(Spd).max())
+
+
+@pytest.mark.parametrize("cfg,seed", [(1, 0), (1, 3), (2, 1), ("unicycle", 2)])
+def test_exact_hessian_solves_reach_the_kkt_point(cfg, seed):
+    """With the exact Hessian (eigenvalue-modified) the method reaches a KKT point of Eq. (bmpc), the
+    same one as with Gauss-Newton."""
+    p = scenes.unicycle(seed) if cfg == "unicycle" else scenes.instances(cfg, 1, seed0=seed)[0]
+    a, b = oracle.solve(p), oracle.solve(p, hessian=1)
+    assert a["status"] == b["status"] == oracle.OK
+    k = oracle.kkt(p, b["x"], b["u"], b["lam"], b["y"])
+    assert k[:4].max() < 1e-5
+    inner = np.ones(p["n"], bool)
+    inner[[i for i in range(p["n"]) if i not in set(p["parent"][1:].tolist())]] = False
+    assert np.abs(a["u"][inner] - b["u"][inner]).max() <= 1e-4 * max(1.0, np.abs(a["u"]).max())
+
+
+def test_exact_hessian_equals_gauss_newton_on_linear_quadratic_trees():
+    """No curvature in the dynamics or the constraints: the two options take the same single step."""
+    p = scenes.linear_problem(3, N=12, splits={2: 2, 6: 3})
+    a, b = oracle.solve(p), oracle.solve(p, hessian=1)
+    assert a["inner_iters"] == b["inner_iters"] == 1
+    np.testing.assert_allclose(a["u"], b["u"], atol=1e-10)
