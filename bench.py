@@ -348,9 +348,13 @@ def run_gpu(args):
     b = bmpc.Batch(problems, stream=stream)
     b.set_problems()
     opts = bmpc.default_opts(block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm,
-                             ls_chunk=args.ls_chunk, variant=args.variant, queue_order=args.queue_order)
+                             ls_chunk=args.ls_chunk, variant=args.variant, queue_order=args.queue_order,
+                             hessian=args.hessian)
     if args.max_iters > 0:
         opts.max_iters = args.max_iters
+    if args.block_threads_model:
+        per_model = [int(v) for v in args.block_threads_model.split(",")]
+        opts.block_threads_model = (type(opts.block_threads_model))(*(per_model + [0] * 4)[:4])
     tuned = None
     if args.autotune:
         opts, us = b.autotune(opts)
@@ -462,9 +466,11 @@ def run_gpu(args):
                             "block_threads_model": list(opts.block_threads_model),
                             "variant": opts.variant, "ls_chunk": opts.ls_chunk,
                             "max_iters": opts.max_iters, "autotuned": tuned is not None,
+                            "hessian": "exact, eigenvalue-modified" if opts.hessian else "Gauss-Newton",
                             "queue_order": "longest predicted first (previous step's iterations)"
                             if opts.queue_order == 1 else "largest tree first"}},
         "converged_fraction": float(conv.mean()),
+        "node_iterations_per_step": node_iters,
         "tree_riccati_us_per_iter": ric_us_iter,
         "phase_us_per_iter": phases,
         "solve_latency_us": {"mean": float(tot_us.mean()), "max": float(tot_us.max())},
@@ -511,7 +517,7 @@ def run_single(args):
         s = torch.cuda.Stream()
         b = bmpc.Batch([p], stream=s)
         b.set_problems()
-        o = bmpc.default_opts(block_threads=args.block_threads or 512, variant=args.variant)
+        o = bmpc.default_opts(block_threads=args.block_threads or 512, variant=args.variant, hessian=args.hessian)
         for _ in range(args.warmup):
             b.solve(o, graph=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -532,7 +538,8 @@ def run_single(args):
                          status=r["status"], ms=ms, us_per_iter=1e3 * ms / it, phase_us_per_iter=phases,
                          latency_frac=crit_cycles_per_iter(p, fits) / per_cyc,
                          bwd_fwd_share=(c["backward"] + c["forward"]) / max(1, c["total"])))
-    out = {"workload": args.workload, "mode": "single problem per launch", "chain_fit_cycles": fits,
+    out = {"workload": args.workload, "mode": "single problem per launch", "hessian": args.hessian,
+           "chain_fit_cycles": fits,
            "mean_ms": float(np.mean([r["ms"] for r in rows])),
            "mean_us_per_iter": float(np.mean([r["us_per_iter"] for r in rows])),
            "mean_latency_frac": float(np.mean([r["latency_frac"] for r in rows])),
@@ -554,9 +561,13 @@ def main():
     ap.add_argument("--single", type=int, default=0, metavar="P",
                     help="single-problem latency of the first P problems of the workload (one per launch)")
     ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--block-threads-model", default="", metavar="K,D,L,U",
+                    help="threads per problem for the kinematic, dynamic, linear and unicycle launches")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--ls-chunk", type=int, default=2)
     ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--hessian", type=int, default=0, choices=[0, 1],
+                    help="1: exact Hessian of the Lagrangian with eigenvalue modification (Sec. IV-A)")
     ap.add_argument("--queue-order", type=int, default=1, choices=[0, 1])
     ap.add_argument("--max-iters", type=int, default=0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")

@@ -175,6 +175,13 @@ typedef struct {
                                With plain FP32 iterates, rho times the rounding of an input resting on
                                its bound (or of a position on a keep-out boundary) floors the relaxed
                                KKT residual near 1e-5.  0: plain FP32 iterate. */
+    int32_t hessian;        /* 0 (default): Gauss-Newton Hessian; 1: the exact Hessian of the
+                               Lagrangian with eigenvalue modification (Sec. IV-A): every node's block
+                               in (x, u) adds the RK4 map's second derivatives weighted by the
+                               children's multipliers (hyper-dual arithmetic) and the curvature of the
+                               active keep-out rows, and its eigenvalues are floored at 1e-6 max(1,
+                               max |ev|) (Jacobi rotations when a Cholesky test shows one below).
+                               Sweep variants 0-2 and 5 (3 and 4 assume the diagonal cost). */
 } bmpc_opts;
 
 typedef struct {

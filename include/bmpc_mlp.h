@@ -91,14 +91,18 @@ int bmpc_mlp_selftest_wait(int64_t cycles, void *stream);
  * dim must be at least nx - 1 + 5 n_scen n_obs_max. */
 int bmpc_mlp_features(const bmpc_batch *b, float *feat, int32_t dim, int32_t n_scen, int32_t n_obs_max);
 /* Targets of problem k from the batch's current solution (fp32, tgt + k*stride): the packed start
- * x | u | lam | y (node-major) with X0 subtracted from every state's X. */
-int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride);
+ * x | u | lam | y (node-major) with X0 subtracted from every state's X.  y_sqrt = 1 writes the AL
+ * multipliers as sqrt(y) (a variance-stabilising form: the heavy tail of the active keep-out rows'
+ * multipliers is compressed and zeros stay zero), 0 as y.  -1 on y_sqrt outside {0, 1} or a stride
+ * below a problem's packed size. */
+int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride, int32_t y_sqrt);
 /* Packed warm starts from network outputs: start[k] = mean + std * pred[k] with X0 added back to
- * every state's X (the inverse of bmpc_mlp_targets after standardisation), then the states
- * replaced by the rollout of the predicted controls from x0 through the tree, so that the start
- * satisfies the dynamics; feed to bmpc_set_warm_start_device. */
+ * every state's X (the inverse of bmpc_mlp_targets after standardisation), the AL multipliers
+ * clipped at 0 (and squared when y_sqrt = 1, the inverse of the targets' square-root form), then
+ * the states replaced by the rollout of the predicted controls from x0 through the tree, so that
+ * the start satisfies the dynamics; feed to bmpc_set_warm_start_device. */
 int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, const float *mean, const float *std,
-                   float *start, int64_t stride);
+                   float *start, int64_t stride, int32_t y_sqrt);
 /* out = bf16((raw - mean) / std) elementwise over rows x dim. */
 int bmpc_mlp_standardize(const float *raw, const float *mean, const float *std, uint16_t *out, int64_t rows,
                          int32_t dim, void *stream);

@@ -48,7 +48,7 @@ class Opts(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("variant", C.c_int32), ("warm_select", C.c_int32),
                 ("select_mu", C.c_float), ("select_rho", C.c_float), ("queue_order", C.c_int32),
                 ("block_threads_model", C.c_int32 * 4), ("cap_rule", C.c_int32),
-                ("kkt_margin", C.c_float), ("compensated", C.c_int32)]
+                ("kkt_margin", C.c_float), ("compensated", C.c_int32), ("hessian", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -30,20 +30,9 @@ cudaError_t launch_flat(int which, const FlatArgs &a, int n_problems, cudaStream
 cudaError_t launch_sincos(const float *a, float *sn, float *cs, int n, cudaStream_t stream);
 cudaError_t launch_fma(float *out, int blocks, int iters, cudaStream_t stream);
 int max_block_threads();
-cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm, bool scan);
+cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm, const KOpts &o);
 cudaError_t launch_scatter_warm(const WarmArgs &a, cudaStream_t stream);
 cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream);
-struct GlueArgs {
-    const ProbRec *recs;
-    const int32_t *ibase;
-    const float *inbase, *outbase;
-    float *out;
-    int64_t stride;
-    const float *pred, *mean, *std;
-    int64_t ld_pred;
-    int32_t n_scen, n_obs_max;
-    const int32_t *order_base;
-};
 cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream_t stream, int model);
 }  // namespace bmpc
 
@@ -277,6 +266,7 @@ KOpts to_kopts(const bmpc_opts &o) {
     k.warm_select = o.warm_select;
     k.cap_rule = o.cap_rule;
     k.compensated = o.compensated;
+    k.hessian = o.hessian;
     k.eps_tol = o.eps_tol * o.kkt_margin;   /* the kernel's own FP32 tests, with the margin */
     k.tau = o.tau;
     k.omega0 = o.omega0;
@@ -310,6 +300,7 @@ int check_opts(const bmpc_opts &o) {
     if (o.cap_rule < 0 || o.cap_rule > 1) return BMPC_ERR_INVALID;
     if (!(o.kkt_margin > 0.f && o.kkt_margin <= 1.f)) return BMPC_ERR_INVALID;
     if (o.compensated < 0 || o.compensated > 1) return BMPC_ERR_INVALID;
+    if (o.hessian < 0 || o.hessian > 1) return BMPC_ERR_INVALID;
     for (int m = 0; m < NUM_MODELS; ++m) {
         const int bt = o.block_threads_model[m];
         if (bt != 0 && (bt < 32 || bt > max_block_threads() || bt % 32)) return BMPC_ERR_INVALID;
@@ -386,7 +377,7 @@ void geometry(const bmpc_batch *b, const bmpc_opts &o, int model, int count, int
     if (per_sm == 0) {
         int occ = 1, ld;
         const size_t smem = solve_smem(model, b->tab_ints[model], b->max_paths[model], bt, &ld);
-        if (occupancy(model, bt, smem, &occ, o.variant == 4) != cudaSuccess || occ < 1) occ = 1;
+        if (occupancy(model, bt, smem, &occ, to_kopts(o)) != cudaSuccess || occ < 1) occ = 1;
         per_sm = occ;
     }
     *block = bt;
@@ -395,6 +386,7 @@ void geometry(const bmpc_batch *b, const bmpc_opts &o, int model, int count, int
 
 int launch(bmpc_batch *b, const bmpc_opts &o) {
     if (o.variant >= 3 && b->any_edge) return BMPC_ERR_INVALID;   /* per-edge dynamics: sweeps 1 and 2 */
+    if (o.hessian && (o.variant == 3 || o.variant == 4)) return BMPC_ERR_INVALID;   /* diagonal-cost sweeps */
     KernelArgs a;
     a.recs = at<const ProbRec>(b->data, b->L.recs);
     a.ibase = at<const int32_t>(b->data, b->L.ints);
@@ -474,6 +466,7 @@ void bmpc_default_opts(bmpc_opts *o) {
     o->cap_rule = 0;
     o->kkt_margin = 0.8f;
     o->compensated = 1;
+    o->hessian = 0;
 }
 
 int bmpc_batch_bytes(const bmpc_tree_desc *descs, int32_t n, size_t *data_bytes, size_t *scratch_bytes,
@@ -902,19 +895,20 @@ int bmpc_mlp_features(const bmpc_batch *b, float *feat, int32_t dim, int32_t n_s
     return cuda_status(launch_glue(0, g, b->n, b->stream, 0));
 }
 
-int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride) {
-    if (!b || !tgt) return BMPC_ERR_INVALID;
+int bmpc_mlp_targets(const bmpc_batch *b, float *tgt, int64_t stride, int32_t y_sqrt) {
+    if (!b || !tgt || y_sqrt < 0 || y_sqrt > 1) return BMPC_ERR_INVALID;
     for (const ProbRec &R : b->recs)
         if ((int64_t)R.n * (2 * R.nx + NU + R.nc) > stride) return BMPC_ERR_INVALID;
     GlueArgs g = glue_args(b);
     g.out = tgt;
     g.stride = stride;
+    g.y_sqrt = y_sqrt;
     return cuda_status(launch_glue(1, g, b->n, b->stream, 0));
 }
 
 int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, const float *mean, const float *std,
-                   float *start, int64_t stride) {
-    if (!b || !pred || !mean || !std || !start) return BMPC_ERR_INVALID;
+                   float *start, int64_t stride, int32_t y_sqrt) {
+    if (!b || !pred || !mean || !std || !start || y_sqrt < 0 || y_sqrt > 1) return BMPC_ERR_INVALID;
     for (const ProbRec &R : b->recs)
         if (R.edge_dyn) return BMPC_ERR_INVALID;   /* the rollout of the start uses per-node dynamics */
     for (const ProbRec &R : b->recs) {
@@ -928,6 +922,7 @@ int bmpc_mlp_start(const bmpc_batch *b, const float *pred, int64_t ld_pred, cons
     g.ld_pred = ld_pred;
     g.mean = mean;
     g.std = std;
+    g.y_sqrt = y_sqrt;
     for (int m = 0; m < NUM_MODELS; ++m) {
         const int cnt = b->model_begin[m + 1] - b->model_begin[m];
         g.order_base = reinterpret_cast<const int32_t *>(b->data + b->L.order) + b->model_begin[m];
@@ -977,6 +972,7 @@ int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *
         for (int v : kVariant)
             for (int ch : kChunk) {
                 if (v >= 3 && b->any_edge) continue;   /* per-edge dynamics: sweeps 1 and 2 */
+                if (o.hessian && (v == 3 || v == 4)) continue;
                 bmpc_opts c = o;
                 c.block_threads = bt;
                 for (int m = 0; m < NUM_MODELS; ++m) c.block_threads_model[m] = 0;

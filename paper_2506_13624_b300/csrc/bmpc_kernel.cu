@@ -521,13 +521,40 @@ __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], cons
     }
 }
 
-/* Entry (a, b) of a stored Jacobian A_n.  For the vehicle models the columns of the positions
- * X, Y are the unit vectors (positions do not enter the dynamics): they are compile-time
- * constants, never stored or loaded. */
+/* Entries of the Jacobians A_n = df/dx and B_n = df/du that the model's structure fixes exactly:
+ * 0 or 1 for a fixed entry, -1 for a computed one.  For the vehicle models the columns of the
+ * positions X, Y are the unit vectors (positions do not enter the dynamics).  In the kinematic
+ * bicycle and the unicycle (X, Y, heading, speed) the speed integrates the acceleration alone
+ * (its row of A is e_3, its steering entry of B is 0), and the heading rate does not depend on the
+ * heading (A[2][2] = 1); the unicycle's heading rate is its own input (A[2][3] = 0, B[2][0] = 0).
+ * The forward-mode RK4 tangents produce these entries exactly (sums of exact zeros onto 1 or 0),
+ * so reading them as constants changes no result; they are never loaded. */
+template <int MODEL>
+__host__ __device__ constexpr int a_fixed(int a, int b) {
+    if (MODEL == 2) return -1;
+    if (b < 2) return a == b ? 1 : 0;
+    if (MODEL == 1) return -1;
+    if (a == 2 && b == 2) return 1;
+    if (a == 3) return b == 3 ? 1 : 0;
+    if (MODEL == 3 && a == 2 && b == 3) return 0;
+    return -1;
+}
+template <int MODEL>
+__host__ __device__ constexpr int b_fixed(int a, int b) {
+    if (MODEL != 0 && MODEL != 3) return -1;
+    if (a == 3 && b == 1) return 0;
+    if (MODEL == 3 && a == 2 && b == 0) return 0;
+    return -1;
+}
 template <int NX, int MODEL>
 __device__ __forceinline__ float aload(const float *A, int np, int i, int a, int b) {
-    if (MODEL != 2 && b < 2) return a == b ? 1.f : 0.f;
+    if (a_fixed<MODEL>(a, b) >= 0) return (float)a_fixed<MODEL>(a, b);
     return A[(size_t)(a * NX + b) * np + i];
+}
+template <int NX, int MODEL>
+__device__ __forceinline__ float bload(const float *B, int np, int i, int a, int b) {
+    if (b_fixed<MODEL>(a, b) >= 0) return (float)b_fixed<MODEL>(a, b);
+    return B[(size_t)(a * NU + b) * np + i];
 }
 
 /* ------------------------------------------------------------------ problem view */
@@ -548,6 +575,8 @@ struct View {
     float *CV0, *CV1, *JA0, *JA1;   /* scan buffers (two of each) */
     bool comp;   /* compensated iterate (Lo parts) in use */
     bool edge;   /* per-edge linear dynamics: A, B point at the input rows, f and A, B are per edge */
+    bool hess;   /* exact-Hessian option: the node blocks Q, M, R are the dense rows HS */
+    float *HS;
 
     __device__ View(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout, float *fs) {
         n = R.n;
@@ -603,6 +632,8 @@ struct View {
         XL = fs + (size_t)s.xl * np;
         UL = fs + (size_t)s.ul * np;
         edge = false;   /* set by the solver for the linear model (per-edge dynamics) */
+        hess = false;
+        HS = fs + (size_t)s.hs * np;
         CV0 = fs + (size_t)s.cv * np;
         CV1 = CV0 + (size_t)cvf_rows(NX) * np;
         JA0 = fs + (size_t)s.ja * np;
@@ -832,6 +863,7 @@ __device__ __forceinline__ void leaf_value(const ProbRec &R, const View<NX> &V, 
             if (a == 0 && b == 0) v += hxx;
             if (a == 0 && b == 1) v += hxy;
             if (a == 1 && b == 1) v += hyy;
+            if (V.hess) v = V.HS[(size_t)sidx<NX>(a, b) * np + i];
             P[sidx<NX>(a, b)] = v;
         }
 #pragma unroll
@@ -887,7 +919,7 @@ __device__ __forceinline__ void ric_load(const View<NX> &V, int i, RicIn<NX> &in
 #pragma unroll
         for (int b = 0; b < NX; ++b) in.A[a][b] = aload<NX, MODEL>(V.A, np, ja, a, b);
 #pragma unroll
-        for (int b = 0; b < NU; ++b) in.B[a][b] = V.B[(size_t)(a * NU + b) * np + ja];
+        for (int b = 0; b < NU; ++b) in.B[a][b] = bload<NX, MODEL>(V.B, np, ja, a, b);
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
@@ -902,10 +934,17 @@ __device__ __forceinline__ void ric_load(const View<NX> &V, int i, RicIn<NX> &in
  * at stg[(buffer * rows + row) * ld + thread].  (The backward sweep loads directly: its Riccati
  * step is long enough that staging did not pay for its extra instructions.) */
 constexpr int SWEEP_DEPTH = 3;
-template <int MODEL>
-__host__ __device__ constexpr int a_first() { return MODEL == 2 ? 0 : 2; }   /* first stored column of A */
 template <int NX, int MODEL>
-__host__ __device__ constexpr int rows_stage() { return NX + NX * (NX - a_first<MODEL>()) + 2 * NX * NU + NU; }
+__host__ __device__ constexpr int jac_stored() {   /* entries of A and B that are not fixed */
+    int c = 0;
+    for (int a = 0; a < NX; ++a) {
+        for (int b = 0; b < NX; ++b) c += a_fixed<MODEL>(a, b) < 0;
+        for (int b = 0; b < NU; ++b) c += b_fixed<MODEL>(a, b) < 0;
+    }
+    return c;
+}
+template <int NX, int MODEL>
+__host__ __device__ constexpr int rows_stage() { return NX + jac_stored<NX, MODEL>() + NX * NU + NU; }
 
 /* Riccati step of a non-leaf node n from the summed child value functions (Pb, pb):
  * H_n = R_n + B'Pb B, K_n = -H^-1 (M_n + B'Pb A), k_n = -H^-1 (r_n + B'pb) of
@@ -940,20 +979,22 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
             PB[a][b] = v;
         }
     }
-    /* H blocks: Quu = R + B'PB, Qux = B'PA, qu = r + B'pbar, qx = q + A'pbar */
+    /* H blocks: Quu = R + B'PB, Qux = M + B'PA, qu = r + B'pbar, qx = q + A'pbar (M = 0 and R, Q
+     * diagonal plus penalty terms for Gauss-Newton; the dense modified blocks of the exact option) */
     float Quu[NU][NU], Qux[NU][NX], qu[NU], qx[NX];
+    const float *HSr = V.HS + nsym(NX) * (size_t)np + i;   /* M then R (packed) of the exact option */
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
 #pragma unroll
         for (int b = 0; b < NU; ++b) {
-            float v = (a == b) ? w * R.Rw[a] + in.hr[a] : 0.f;
+            float v = V.hess ? HSr[(size_t)(NU * NX + (a + b)) * np] : ((a == b) ? w * R.Rw[a] + in.hr[a] : 0.f);
 #pragma unroll
             for (int t = 0; t < NX; ++t) v += B[t][a] * PB[t][b];
             Quu[a][b] = v;
         }
 #pragma unroll
         for (int b = 0; b < NX; ++b) {
-            float v = 0.f;
+            float v = V.hess ? HSr[(size_t)(a * NX + b) * np] : 0.f;
 #pragma unroll
             for (int t = 0; t < NX; ++t) v += B[t][a] * PA[t][b];
             Qux[a][b] = v;
@@ -1001,6 +1042,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
             if (a == 0 && b == 0) v += hxx;
             if (a == 0 && b == 1) v += hxy;
             if (a == 1 && b == 1) v += hyy;
+            if (V.hess) v = V.HS[(size_t)sidx<NX>(a, b) * np + i];
 #pragma unroll
             for (int t = 0; t < NX; ++t) v += A[t][a] * PA[t][b];
 #pragma unroll
@@ -1137,9 +1179,19 @@ __device__ void riccati_edges(const ProbRec &R, const View<NX> &V, int i, float 
         }
     }
     const float w = V.w[i];
+    if (V.hess) {   /* the exact option's dense modified block: R and M here, Q below */
+        const float *HSr = V.HS + nsym(NX) * (size_t)np + i;
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+#pragma unroll
+            for (int b = 0; b < NU; ++b) Quu[a][b] += HSr[(size_t)(NU * NX + a + b) * np];
+#pragma unroll
+            for (int b = 0; b < NX; ++b) Qux[a][b] += HSr[(size_t)(a * NX + b) * np];
+        }
+    }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
-        Quu[a][a] += w * R.Rw[a] + V.hr[(size_t)a * np + i];
+        if (!V.hess) Quu[a][a] += w * R.Rw[a] + V.hr[(size_t)a * np + i];
         qu[a] += V.r[(size_t)a * np + i];
     }
 #pragma unroll
@@ -1173,6 +1225,7 @@ __device__ void riccati_edges(const ProbRec &R, const View<NX> &V, int i, float 
             if (a == 0 && b == 0) v += hxx;
             if (a == 0 && b == 1) v += hxy;
             if (a == 1 && b == 1) v += hyy;
+            if (V.hess) v = Qxx[a][b] + V.HS[(size_t)sidx<NX>(a, b) * np + i];
 #pragma unroll
             for (int t = 0; t < NU; ++t) v += Qux[t][a] * Kn[t][b];
             P[sidx<NX>(a, b)] = v;
@@ -1302,7 +1355,7 @@ __device__ __forceinline__ void fwd_load(const View<NX> &V, int i, int pa, FwdIn
 #pragma unroll
         for (int b = 0; b < NX; ++b) in.A[a][b] = aload<NX, MODEL>(V.A, np, pa, a, b);
 #pragma unroll
-        for (int b = 0; b < NU; ++b) in.B[a][b] = V.B[(size_t)(a * NU + b) * np + pa];
+        for (int b = 0; b < NU; ++b) in.B[a][b] = bload<NX, MODEL>(V.B, np, pa, a, b);
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
@@ -1320,9 +1373,11 @@ __device__ __forceinline__ void fwd_issue(const View<NX> &V, int i, int pa, floa
     for (int a = 0; a < NX; ++a) {
         cp4(slot + (j++) * ld, V.d + (size_t)a * np + i);
 #pragma unroll
-        for (int b = a_first<MODEL>(); b < NX; ++b) cp4(slot + (j++) * ld, V.A + (size_t)(a * NX + b) * np + pa);
+        for (int b = 0; b < NX; ++b)
+            if (a_fixed<MODEL>(a, b) < 0) cp4(slot + (j++) * ld, V.A + (size_t)(a * NX + b) * np + pa);
 #pragma unroll
-        for (int b = 0; b < NU; ++b) cp4(slot + (j++) * ld, V.B + (size_t)(a * NU + b) * np + pa);
+        for (int b = 0; b < NU; ++b)
+            if (b_fixed<MODEL>(a, b) < 0) cp4(slot + (j++) * ld, V.B + (size_t)(a * NU + b) * np + pa);
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
@@ -1339,11 +1394,9 @@ __device__ __forceinline__ void fwd_read(const float *slot, int ld, FwdIn<NX> &i
     for (int a = 0; a < NX; ++a) {
         in.d[a] = slot[(j++) * ld];
 #pragma unroll
-        for (int b = 0; b < a_first<MODEL>(); ++b) in.A[a][b] = a == b ? 1.f : 0.f;
+        for (int b = 0; b < NX; ++b) in.A[a][b] = a_fixed<MODEL>(a, b) >= 0 ? (float)a_fixed<MODEL>(a, b) : slot[(j++) * ld];
 #pragma unroll
-        for (int b = a_first<MODEL>(); b < NX; ++b) in.A[a][b] = slot[(j++) * ld];
-#pragma unroll
-        for (int b = 0; b < NU; ++b) in.B[a][b] = slot[(j++) * ld];
+        for (int b = 0; b < NU; ++b) in.B[a][b] = b_fixed<MODEL>(a, b) >= 0 ? (float)b_fixed<MODEL>(a, b) : slot[(j++) * ld];
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
@@ -1410,16 +1463,34 @@ __device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, con
             V.load_u(V.hr, i, hrv);
         }
 #pragma unroll
-        for (int a = 0; a < NX; ++a) {
-            dir[0] += qv[a] * dxv[a];
-            dir[1] += w * Qd[a] * dxv[a] * dxv[a];
-        }
-        dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
+        for (int a = 0; a < NX; ++a) dir[0] += qv[a] * dxv[a];
         if (nch) {
 #pragma unroll
-            for (int a = 0; a < NU; ++a) {
-                dir[0] += rv[a] * duv[a];
-                dir[1] += (w * R.Rw[a] + hrv[a]) * duv[a] * duv[a];
+            for (int a = 0; a < NU; ++a) dir[0] += rv[a] * duv[a];
+        }
+        if (!V.hess) {
+#pragma unroll
+            for (int a = 0; a < NX; ++a) dir[1] += w * Qd[a] * dxv[a] * dxv[a];
+            dir[1] += hxx * dxv[0] * dxv[0] + 2.f * hxy * dxv[0] * dxv[1] + hyy * dxv[1] * dxv[1];
+            if (nch) {
+#pragma unroll
+                for (int a = 0; a < NU; ++a) dir[1] += (w * R.Rw[a] + hrv[a]) * duv[a] * duv[a];
+            }
+        } else {   /* dz'W dz with the exact option's dense modified block */
+#pragma unroll
+            for (int a = 0; a < NX; ++a)
+#pragma unroll
+                for (int b = 0; b < NX; ++b) dir[1] += dxv[a] * V.HS[(size_t)sidx<NX>(a, b) * np + i] * dxv[b];
+            if (nch) {
+#pragma unroll
+                for (int a = 0; a < NU; ++a) {
+#pragma unroll
+                    for (int b = 0; b < NX; ++b)
+                        dir[1] += 2.f * duv[a] * V.HS[(size_t)(nsym(NX) + a * NX + b) * np + i] * dxv[b];
+#pragma unroll
+                    for (int b = 0; b < NU; ++b)
+                        dir[1] += duv[a] * V.HS[(size_t)(nsym(NX) + NU * NX + a + b) * np + i] * duv[b];
+                }
             }
         }
         if (i != 0) {
@@ -2013,7 +2084,7 @@ __device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V
 #pragma unroll
         for (int b = 0; b < NX; ++b) F[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
 #pragma unroll
-        for (int b = 0; b < NU; ++b) F[a][NX + b] = V.B[(size_t)(a * NU + b) * np + i];
+        for (int b = 0; b < NU; ++b) F[a][NX + b] = bload<NX, MODEL>(V.B, np, i, a, b);
     }
     /* row `lane` of Pbar F (Pbar symmetric: this lane's column is also its row) */
     if (lane < NX) {
@@ -2226,7 +2297,7 @@ __device__ void forward_coop(const ProbRec &R, const View<NX> &V) {
 #pragma unroll
                 for (int b = 0; b < NX; ++b) v += aload<NX, MODEL>(V.A, np, pa, la, b) * dx[b];
 #pragma unroll
-                for (int b = 0; b < NU; ++b) v += V.B[(size_t)(la * NU + b) * np + pa] * du[b];
+                for (int b = 0; b < NU; ++b) v += bload<NX, MODEL>(V.B, np, pa, la, b) * du[b];
 #pragma unroll
                 for (int a = 0; a < NX; ++a) dx[a] = gshfl(v, a, gmask);
             }
@@ -2397,8 +2468,309 @@ __device__ __forceinline__ void apply_step_serial(const View<NX> &V, int i, floa
     }
 }
 
+/* ------------------------------------------------------------------ exact Hessian option (Sec. IV-A) */
+/* Hyper-dual numbers (Fike and Alonso, 2011): a + b e1 + c e2 + d e1 e2 with e1^2 = e2^2 = 0; a
+ * function evaluated at z + e1 v + e2 w returns w'H v in d exactly, without truncation error. */
+struct Hd {
+    float a, b, c, d;
+};
+__device__ __forceinline__ Hd hd_c(float v) { return Hd{v, 0.f, 0.f, 0.f}; }
+__device__ __forceinline__ Hd operator+(Hd x, Hd y) { return Hd{x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
+__device__ __forceinline__ Hd operator-(Hd x, Hd y) { return Hd{x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
+__device__ __forceinline__ Hd operator*(Hd x, float s) { return Hd{x.a * s, x.b * s, x.c * s, x.d * s}; }
+__device__ __forceinline__ Hd operator*(Hd x, Hd y) {
+    return Hd{x.a * y.a, x.a * y.b + x.b * y.a, x.a * y.c + x.c * y.a, x.a * y.d + x.b * y.c + x.c * y.b + x.d * y.a};
+}
+/* f(x) from its value f0 and first and second derivatives f1, f2 at x.a */
+__device__ __forceinline__ Hd hd_fn(Hd x, float f0, float f1, float f2) {
+    return Hd{f0, f1 * x.b, f1 * x.c, f1 * x.d + f2 * x.b * x.c};
+}
+__device__ __forceinline__ void hd_sincos(Hd x, Hd &s, Hd &c) {
+    float sv, cv;
+    sincos_cw(x.a, &sv, &cv);
+    s = hd_fn(x, sv, cv, -sv);
+    c = hd_fn(x, cv, -sv, -cv);
+}
+__device__ __forceinline__ Hd hd_inv(Hd x) {
+    const float i = 1.f / x.a;
+    return hd_fn(x, i, -i * i, 2.f * i * i * i);
+}
+__device__ __forceinline__ Hd hd_atan(Hd x) {
+    const float s = 1.f / (1.f + x.a * x.a);
+    return hd_fn(x, atanf(x.a), s, -2.f * x.a * s * s);
+}
+__device__ __forceinline__ Hd hd_sqrt(Hd x) {
+    const float r = sqrtf(x.a);
+    return hd_fn(x, r, 0.5f / r, -0.25f / (r * x.a));
+}
+
+/* The vehicle right-hand sides of rhs() in hyper-dual arithmetic. */
+template <int NX, int MODEL>
+__device__ __forceinline__ void rhs_hd(const float *prm, const Hd (&s)[NX], const Hd (&u)[NU], Hd (&f)[NX]) {
+    if constexpr (MODEL == 0 || MODEL == 3) {
+        Hd sp, cp;
+        hd_sincos(s[2], sp, cp);
+        f[0] = s[3] * cp;
+        f[1] = s[3] * sp;
+        if constexpr (MODEL == 0) {
+            Hd sd, cd;
+            hd_sincos(u[1], sd, cd);
+            f[2] = s[3] * (sd * hd_inv(cd)) * (1.f / prm[0]);
+        } else {
+            f[2] = u[1];
+        }
+        f[3] = u[0];
+    } else if constexpr (MODEL == 1) {
+        const float lf = prm[3], lr = prm[4], Cf = prm[5], Cr = prm[6], vmin = prm[7], veps = prm[8];
+        const Hd vx = s[3], vy = s[4], r = s[5];
+        const Hd dv = vx - hd_c(vmin);
+        const Hd w = hd_sqrt(dv * dv + hd_c(veps * veps));
+        const Hd ivb = hd_inv((vx + hd_c(vmin) + w) * 0.5f);
+        const Hd Ff = (hd_atan((vy + r * lf) * ivb) - u[1]) * (-Cf);
+        const Hd Fr = hd_atan((vy - r * lr) * ivb) * (-Cr);
+        Hd sp, cp;
+        hd_sincos(s[2], sp, cp);
+        f[0] = vx * cp - vy * sp;
+        f[1] = vx * sp + vy * cp;
+        f[2] = r;
+        f[3] = u[0] + r * vy;
+        f[4] = (Ff + Fr) * (1.f / prm[1]) - r * vx;
+        f[5] = (Ff * lf - Fr * lr) * (1.f / prm[2]);
+    }
+}
+
+/* H = sum_i mu_i d^2 f_i / dz dz, z = (x, u), of the RK4 map (n_sub substeps) at absolute state xa,
+ * one hyper-dual evaluation per pair (j, k); the positions X, Y do not enter the vehicle dynamics,
+ * so their rows and columns are zero and skipped.  The linear model has none. */
+template <int NX, int MODEL>
+__device__ __forceinline__ void dyn_hessian(const ProbRec &R, const float (&xa)[NX], const float (&u)[NU],
+                                            const float (&mu)[NX], float (&H)[NX + NU][NX + NU]) {
+    constexpr int NZ = NX + NU;
+#pragma unroll
+    for (int j = 0; j < NZ; ++j)
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) H[j][k] = 0.f;
+    if constexpr (MODEL == 2) {
+        return;
+    } else {
+        const int nsub = max(1, (int)R.params[9]);
+        const float h = R.dt / (float)nsub;
+        for (int j = 2; j < NZ; ++j)
+            for (int k = j; k < NZ; ++k) {
+                Hd z[NX], uu[NU];
+#pragma unroll
+                for (int i = 0; i < NX; ++i) z[i] = Hd{xa[i], i == j ? 1.f : 0.f, i == k ? 1.f : 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < NU; ++i) uu[i] = Hd{u[i], NX + i == j ? 1.f : 0.f, NX + i == k ? 1.f : 0.f, 0.f};
+                for (int sub = 0; sub < nsub; ++sub) {
+                    Hd kp[NX], ks[NX];
+#pragma unroll
+                    for (int i = 0; i < NX; ++i) kp[i] = ks[i] = hd_c(0.f);
+#pragma unroll
+                    for (int st = 0; st < 4; ++st) {
+                        const float c = (st == 0) ? 0.f : (st == 3 ? 1.f : 0.5f);
+                        const float wg = (st == 0 || st == 3) ? 1.f : 2.f;
+                        Hd zs[NX], kk[NX];
+#pragma unroll
+                        for (int i = 0; i < NX; ++i) zs[i] = z[i] + kp[i] * (c * h);
+                        rhs_hd<NX, MODEL>(R.params, zs, uu, kk);
+#pragma unroll
+                        for (int i = 0; i < NX; ++i) {
+                            ks[i] = ks[i] + kk[i] * wg;
+                            kp[i] = kk[i];
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < NX; ++i) z[i] = z[i] + ks[i] * (h * (1.f / 6.f));
+                }
+                float v = 0.f;
+#pragma unroll
+                for (int i = 0; i < NX; ++i) v += mu[i] * z[i].d;
+                H[j][k] = v;
+                H[k][j] = v;
+            }
+    }
+}
+
+/* Eigenvalue modification of a symmetric n x n block (Nocedal and Wright, Sec. 3.4): eigenvalues
+ * floored at delta = EIG_FLOOR max(1, max |ev|).  When a Cholesky factorisation of S - dF I
+ * succeeds with dF = EIG_FLOOR max(1, |S|_F) >= delta, every eigenvalue already exceeds the floor
+ * and S is kept; otherwise cyclic Jacobi sweeps (Golub and Van Loan, Sec. 8.5) decompose it. */
+constexpr float EIG_FLOOR = 1e-6f;
+template <int N>
+__device__ __forceinline__ void eig_modify(float (&S)[N][N]) {
+    float fro = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) fro += S[i][j] * S[i][j];
+    const float dF = EIG_FLOOR * fmaxf(1.f, sqrtf(fro));
+    {
+        float L[N][N];
+        bool pd = true;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            float s = S[j][j] - dF;
+#pragma unroll
+            for (int t = 0; t < j; ++t) s -= L[j][t] * L[j][t];
+            pd = pd && s > 0.f;
+            const float ljj = sqrtf(fmaxf(s, 1e-30f)), il = 1.f / ljj;
+            L[j][j] = ljj;
+#pragma unroll
+            for (int i = j + 1; i < N; ++i) {
+                float v = S[i][j];
+#pragma unroll
+                for (int t = 0; t < j; ++t) v -= L[i][t] * L[j][t];
+                L[i][j] = v * il;
+            }
+        }
+        if (pd) return;
+    }
+    float Vm[N][N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) Vm[i][j] = i == j ? 1.f : 0.f;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        float off = 0.f;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+                if (i != j) off += S[i][j] * S[i][j];
+        if (!(off > 1e-14f * fro)) break;
+#pragma unroll
+        for (int p = 0; p < N - 1; ++p)
+#pragma unroll
+            for (int q = p + 1; q < N; ++q) {
+                const float apq = S[p][q];
+                if (apq == 0.f) continue;
+                const float theta = (S[q][q] - S[p][p]) / (2.f * apq);
+                const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+                const float c = rsqrtf(t * t + 1.f), s = t * c;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float akp = S[k][p], akq = S[k][q];
+                    S[k][p] = c * akp - s * akq;
+                    S[k][q] = s * akp + c * akq;
+                }
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float apk = S[p][k], aqk = S[q][k];
+                    S[p][k] = c * apk - s * aqk;
+                    S[q][k] = s * apk + c * aqk;
+                }
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float vkp = Vm[k][p], vkq = Vm[k][q];
+                    Vm[k][p] = c * vkp - s * vkq;
+                    Vm[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    float ev[N], emax = 1.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        ev[i] = S[i][i];
+        emax = fmaxf(emax, fabsf(ev[i]));
+    }
+    const float delta = EIG_FLOOR * emax;
+#pragma unroll
+    for (int i = 0; i < N; ++i) ev[i] = fmaxf(ev[i], delta);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < N; ++k) v += Vm[i][k] * ev[k] * Vm[j][k];
+            S[i][j] = v;
+        }
+}
+
+/* The exact-Hessian option at node i (called from the KKT pass, where mu, the sum of the children's
+ * multipliers, is at hand): the node's block of the Hessian of the Lagrangian in (x_i, u_i) - the
+ * Gauss-Newton block, the curvature of the active keep-out rows (s grad^2 g, s = y + rho g > 0) and
+ * mu' grad^2 f of the dynamics - eigenvalue-modified and stored in the HS rows (Q packed, M, R
+ * packed).  Not inlined: its registers stay out of the default path. */
+template <int NX, int MODEL>
+__device__ __noinline__ void node_exact_hessian(const ProbRec &R, const View<NX> &V, int i, const float (&mu)[NX],
+                                                float rho) {
+    constexpr int NZ = NX + NU;
+    const int np = V.np;
+    const bool leaf = V.nchild[i] == 0;
+    const float w = V.w[i];
+    const float *Qd = leaf ? R.QNw : R.Qw;
+    float S[NZ][NZ];
+#pragma unroll
+    for (int a = 0; a < NZ; ++a)
+#pragma unroll
+        for (int b = 0; b < NZ; ++b) S[a][b] = 0.f;
+#pragma unroll
+    for (int a = 0; a < NX; ++a) S[a][a] = w * Qd[a];
+    S[0][0] += V.hq[i];
+    S[0][1] += V.hq[(size_t)np + i];
+    S[1][0] += V.hq[(size_t)np + i];
+    S[1][1] += V.hq[2 * (size_t)np + i];
+#pragma unroll
+    for (int a = 0; a < NU; ++a) S[NX + a][NX + a] = leaf ? 1.f : w * R.Rw[a] + V.hr[(size_t)a * np + i];
+    float x[NX], u[NU];
+    Lo lo;
+    V.load_x(V.X, i, x);
+    V.load_u(V.U, i, u);
+    V.load_lo(i, lo);
+    if (i != 0) {
+        const int row0 = V.box ? 2 * NU : 0;
+        for (int o = 0; o < V.nobs; ++o) {
+            const float *ob = V.obs + (size_t)(OBS_ROWS * o) * np + i;
+            const float ch = ob[2 * (size_t)np], sh = ob[3 * (size_t)np];
+            const float ia2 = ob[4 * (size_t)np], ib2 = ob[5 * (size_t)np];
+            float dpar, dper, irr;
+            const float g = obs_g_comp(V.xref[i], V.xref[(size_t)np + i], ob[0], ob[(size_t)np], x[0], lo.x[0], x[1],
+                                       lo.x[1], ch, sh, ia2, ib2, dpar, dper, irr);
+            const float s = V.Y[(size_t)(row0 + o) * np + i] + rho * g;
+            if (!(s > 0.f)) continue;
+            /* grad^2 g = -(Mq / r - v v' / r^3), Mq = Rot' diag(1/a^2, 1/b^2) Rot, v = Rot' diag(.) (d_par, d_perp) */
+            const float m00 = ch * ch * ia2 + sh * sh * ib2, m01 = ch * sh * (ia2 - ib2), m11 = sh * sh * ia2 + ch * ch * ib2;
+            const float v0 = ch * ia2 * dpar - sh * ib2 * dper, v1 = sh * ia2 * dpar + ch * ib2 * dper;
+            const float i3 = irr * irr * irr;
+            S[0][0] += s * (v0 * v0 * i3 - m00 * irr);
+            S[0][1] += s * (v0 * v1 * i3 - m01 * irr);
+            S[1][0] += s * (v0 * v1 * i3 - m01 * irr);
+            S[1][1] += s * (v1 * v1 * i3 - m11 * irr);
+        }
+    }
+    if (!leaf) {
+        float xa[NX], H[NZ][NZ];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
+        dyn_hessian<NX, MODEL>(R, xa, u, mu, H);
+#pragma unroll
+        for (int a = 0; a < NZ; ++a)
+#pragma unroll
+            for (int b = 0; b < NZ; ++b) S[a][b] += H[a][b];
+    }
+    eig_modify<NZ>(S);
+#pragma unroll
+    for (int a = 0; a < NX; ++a)
+#pragma unroll
+        for (int b = a; b < NX; ++b) V.HS[(size_t)sidx<NX>(a, b) * np + i] = S[a][b];
+#pragma unroll
+    for (int a = 0; a < NU; ++a)
+#pragma unroll
+        for (int b = 0; b < NX; ++b) V.HS[(size_t)(nsym(NX) + a * NX + b) * np + i] = S[NX + a][b];
+    V.HS[(size_t)(nsym(NX) + NU * NX) * np + i] = S[NX][NX];
+    V.HS[(size_t)(nsym(NX) + NU * NX + 1) * np + i] = 0.5f * (S[NX][NX + 1] + S[NX + 1][NX]);
+    V.HS[(size_t)(nsym(NX) + NU * NX + 2) * np + i] = S[NX + 1][NX + 1];
+}
+
 /* ------------------------------------------------------------------ the per-problem solver */
-template <int NX, int MODEL, bool SCAN>
+/* Kernel flavours: the plain sweeps (variants 1, 2, 3, 5), the scan sweeps (variant 4) and the
+ * exact-Hessian option each have their own instances, so that the registers one needs leave the
+ * others' alone. */
+constexpr int FLAVOR_PLAIN = 0, FLAVOR_SCAN = 1, FLAVOR_HESS = 2;
+
+template <int NX, int MODEL, int FLAVOR>
 __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout,
                               float *fs, Stats *stat, const KOpts &O, Shared &sh, int32_t *tab, int tab_cap,
                               float *stg, int stg_ld) {
@@ -2406,6 +2778,8 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
     constexpr bool HOIST_LOADS = hoist_loads<NX>();
     View<NX> V(R, ib, fin, fw, fout, fs);
     V.comp = O.compensated != 0;
+    V.hess = FLAVOR == FLAVOR_HESS;
+    constexpr bool SCAN = FLAVOR == FLAVOR_SCAN;
     if constexpr (MODEL == 2) {
         if (R.edge_dyn) {   /* per-edge matrices: inputs at the edge's column, never written by the solver */
             V.edge = true;
@@ -2513,8 +2887,11 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                             float xn[NX];
                             /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
                             dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
-                                if (c < NX) V.A[(size_t)(a * NX + c) * np + i] = v;
-                                else V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                                if (c < NX) {
+                                    if (a_fixed<MODEL>(a, c) < 0) V.A[(size_t)(a * NX + c) * np + i] = v;
+                                } else if (b_fixed<MODEL>(a, c - NX) < 0) {
+                                    V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                                }
                             });
                             V.store_x(V.f, i, xn);
                         }
@@ -2546,8 +2923,11 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                         for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
                         /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
                         dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
-                            if (c < NX) V.A[(size_t)(a * NX + c) * np + i] = v;
-                            else V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                            if (c < NX) {
+                                if (a_fixed<MODEL>(a, c) < 0) V.A[(size_t)(a * NX + c) * np + i] = v;
+                            } else if (b_fixed<MODEL>(a, c - NX) < 0) {
+                                V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                            }
                         });
                         V.store_x(V.f, i, xn);
                     }
@@ -2612,7 +2992,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                                     for (int b = 0; b < NX; ++b) gx[b] += V.A[(size_t)(a * NX + b) * np + m] * lm[a];
                                 }
 #pragma unroll
-                                for (int b = 0; b < NU; ++b) gu[b] += V.B[(size_t)(a * NU + b) * np + m] * lm[a];
+                                for (int b = 0; b < NU; ++b) gu[b] += bload<NX, MODEL>(V.B, np, m, a, b) * lm[a];
                             }
                         }
 #pragma unroll
@@ -2627,7 +3007,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
 #pragma unroll
                         for (int b = 0; b < NX; ++b) Ai[a][b] = aload<NX, MODEL>(V.A, np, i, a, b);
 #pragma unroll
-                        for (int b = 0; b < NU; ++b) Bi[a][b] = V.B[(size_t)(a * NU + b) * np + i];
+                        for (int b = 0; b < NU; ++b) Bi[a][b] = bload<NX, MODEL>(V.B, np, i, a, b);
                     }
                     V.load_u(V.r, i, ri);
                     if (i != 0) {
@@ -2648,6 +3028,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
 #pragma unroll
                     for (int j = 0; j < NX; ++j) rk = fmaxf(rk, fabsf(gx[j]));
                 }
+                if constexpr (FLAVOR == FLAVOR_HESS) node_exact_hessian<NX, MODEL>(R, V, i, lsum, rho);
                 if (!(rk == rk)) rk = INFINITY;
                 sums[0] += la_i;
                 sums[1] += ld;
@@ -2893,7 +3274,7 @@ done:
 }
 
 /* One kernel per dynamics model, so that each carries only its own code and registers. */
-template <int MODEL, int BLOCK, bool SCAN = false>
+template <int MODEL, int BLOCK, int FLAVOR = FLAVOR_PLAIN>
 __global__ void __launch_bounds__(BLOCK, BLOCK <= BATCH_BLOCK ? 2 : 1) bmpc_solve_kernel(KernelArgs args) {
     constexpr int NX = MODEL == 1 ? 6 : 4;
     __shared__ Shared sh;
@@ -2917,7 +3298,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK <= BATCH_BLOCK ? 2 : 1) bmpc_solv
         }
         __syncthreads();
         const ProbRec &R = rec_s;
-        solve_problem<NX, MODEL, SCAN>(R, args.ibase + R.off_int, args.inbase + R.off_in, args.warmbase + R.off_warm,
+        solve_problem<NX, MODEL, FLAVOR>(R, args.ibase + R.off_int, args.inbase + R.off_in, args.warmbase + R.off_warm,
                                  args.outbase + R.off_out, args.scr + R.off_scr, args.stats + pid, args.opts, sh,
                                  tab_s, args.tab_ints, args.stg_ld ? stg : nullptr, args.stg_ld);
     }
@@ -3176,17 +3557,6 @@ cudaError_t launch_shift_warm(const WarmArgs &a, int model, cudaStream_t stream)
 
 
 /* ------------------------------------------------------------------ learned warm start: glue kernels */
-struct GlueArgs {
-    const ProbRec *recs;
-    const int32_t *ibase;
-    const float *inbase, *outbase;
-    float *out;                 /* features / targets / starts, problem k at out + k*stride */
-    int64_t stride;
-    const float *pred, *mean, *std;
-    int64_t ld_pred;
-    int32_t n_scen, n_obs_max;
-    const int32_t *order_base;  /* starts: problems of one model */
-};
 
 /* Features: x0 without X, then per scenario and obstacle (cx - X0, cy) at the path's middle node
  * and (cx - X0, cy, heading) at its leaf. */
@@ -3237,7 +3607,10 @@ __global__ void bmpc_targets_kernel(GlueArgs a) {
             tl[(size_t)i * nx + j] = o[(size_t)(orw.lam + j) * np + i];
         }
         for (int j = 0; j < NU; ++j) tu[(size_t)i * NU + j] = o[(size_t)(orw.u + j) * np + i];
-        for (int c = 0; c < nc; ++c) ty[(size_t)i * nc + c] = o[(size_t)(orw.y + c) * np + i];
+        for (int c = 0; c < nc; ++c) {
+            const float y = o[(size_t)(orw.y + c) * np + i];
+            ty[(size_t)i * nc + c] = a.y_sqrt ? sqrtf(fmaxf(y, 0.f)) : y;
+        }
     }
     const int64_t used = (int64_t)n * (2 * nx + NU + nc);
     for (int64_t j = used + threadIdx.x; j < a.stride; j += blockDim.x) t[j] = 0.f;
@@ -3258,7 +3631,10 @@ __global__ void bmpc_starts_kernel(GlueArgs a) {
     for (int64_t j = threadIdx.x; j < used; j += blockDim.x) {
         float v = a.mean[j] + a.std[j] * p[j];
         if (j < (int64_t)n * NX && j % NX == 0) v += R.x0[0];
-        if (j >= (int64_t)n * (2 * NX + NU)) v = fmaxf(v, 0.f);   /* AL multipliers are >= 0 */
+        if (j >= (int64_t)n * (2 * NX + NU)) {   /* AL multipliers are >= 0 */
+            v = fmaxf(v, 0.f);
+            if (a.y_sqrt) v *= v;
+        }
         s[j] = v;
     }
     __syncthreads();
@@ -3298,12 +3674,18 @@ cudaError_t launch_glue(int which, const GlueArgs &a, int n_problems, cudaStream
 /* Launch helper used by the host API: `args.order` lists problems of `model` only. */
 /* The kernel instance of a model for a block size. */
 using SolveFn = void (*)(KernelArgs);
-SolveFn solve_fn(int model, int block, bool scan = false) {
-    if (scan) {   /* sweep variant 4: one instance per model, up to 512 threads per problem */
-        if (model == 0) return bmpc_solve_kernel<0, MAX_BLOCK, true>;
-        if (model == 1) return bmpc_solve_kernel<1, MAX_BLOCK, true>;
-        if (model == 2) return bmpc_solve_kernel<2, MAX_BLOCK, true>;
-        return bmpc_solve_kernel<3, MAX_BLOCK, true>;
+SolveFn solve_fn(int model, int block, int flavor = FLAVOR_PLAIN) {
+    if (flavor == FLAVOR_SCAN) {   /* sweep variant 4: one instance per model, up to 512 threads per problem */
+        if (model == 0) return bmpc_solve_kernel<0, MAX_BLOCK, FLAVOR_SCAN>;
+        if (model == 1) return bmpc_solve_kernel<1, MAX_BLOCK, FLAVOR_SCAN>;
+        if (model == 2) return bmpc_solve_kernel<2, MAX_BLOCK, FLAVOR_SCAN>;
+        return bmpc_solve_kernel<3, MAX_BLOCK, FLAVOR_SCAN>;
+    }
+    if (flavor == FLAVOR_HESS) {   /* the exact-Hessian option: one instance per model */
+        if (model == 0) return bmpc_solve_kernel<0, MAX_BLOCK, FLAVOR_HESS>;
+        if (model == 1) return bmpc_solve_kernel<1, MAX_BLOCK, FLAVOR_HESS>;
+        if (model == 2) return bmpc_solve_kernel<2, MAX_BLOCK, FLAVOR_HESS>;
+        return bmpc_solve_kernel<3, MAX_BLOCK, FLAVOR_HESS>;
     }
     const bool big = block > BATCH_BLOCK;
     if (model == 0) return big ? bmpc_solve_kernel<0, MAX_BLOCK> : bmpc_solve_kernel<0, BATCH_BLOCK>;
@@ -3312,8 +3694,12 @@ SolveFn solve_fn(int model, int block, bool scan = false) {
     return big ? bmpc_solve_kernel<3, MAX_BLOCK> : bmpc_solve_kernel<3, BATCH_BLOCK>;
 }
 
+int solve_flavor(const KOpts &o) {
+    return o.variant == 4 ? FLAVOR_SCAN : o.hessian ? FLAVOR_HESS : FLAVOR_PLAIN;
+}
+
 cudaError_t launch_solve(const KernelArgs &args, int model, int grid, int block, size_t smem, cudaStream_t stream) {
-    solve_fn(model, block, args.opts.variant == 4)<<<grid, block, smem, stream>>>(args);
+    solve_fn(model, block, solve_flavor(args.opts))<<<grid, block, smem, stream>>>(args);
     return cudaGetLastError();
 }
 
@@ -3348,15 +3734,16 @@ cudaError_t prepare_solve(int model, size_t smem) {
                                          (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(solve_fn(model, MAX_BLOCK), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(solve_fn(model, MAX_BLOCK, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+    for (int f = FLAVOR_SCAN; f <= FLAVOR_HESS && e == cudaSuccess; ++f)
+        e = cudaFuncSetAttribute(solve_fn(model, MAX_BLOCK, f), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
     if (e == cudaSuccess) granted[model] = smem;
     return e;
 }
 
-cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm, bool scan) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_fn(model, block, scan), block, smem);
+cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm, const KOpts &o) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_fn(model, block, solve_flavor(o)), block,
+                                                         smem);
 }
 
 }  // namespace bmpc

@@ -144,13 +144,13 @@ __host__ __device__ inline OutRows out_rows(int nx, int nc) {
 __host__ __device__ constexpr int cvf_rows(int nx) { return nx * nx + 2 * nx + 2 * nsym(nx); }
 
 /* scratch: A[nx*nx] B[nx*nu] f[nx] d[nx] q[nx] r[nu] hq[3] hr[nu] K[nu*nx] k[nu] P[nsym] p[nx]
- *          dx[nx] du[nu] lq[nx] nv[3] xl[2] ul[nu] cv[2 * cvf_rows] ja[2]
+ *          dx[nx] du[nu] lq[nx] nv[3] xl[2] ul[nu] cv[2 * cvf_rows] ja[2] hs[nsym + nu*nx + 3]
  * xl, ul: low-order parts of the compensated iterate (positions X, Y of the state deviation and the
  * inputs): the iterate is xi + xl, u + ul, each pair a float and its rounding remainder.
  * cv: two buffers of scan elements, indexed by position in the segment order (backward) or by node
  * (forward: closed-loop maps in the A, c rows); ja: two rows of ancestor indices (forward). */
 struct ScrRows {
-    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, xl, ul, cv, ja, total;
+    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, xl, ul, cv, ja, hs, total;
 };
 __host__ __device__ inline ScrRows scr_rows(int nx) {
     ScrRows s;
@@ -174,13 +174,14 @@ __host__ __device__ inline ScrRows scr_rows(int nx) {
     s.ul = s.xl + 2;
     s.cv = s.ul + NU;
     s.ja = s.cv + 2 * cvf_rows(nx);
-    s.total = s.ja + 2;
+    s.hs = s.ja + 2;   /* exact-Hessian option: the node's modified block Q (packed), M, R (packed) */
+    s.total = s.hs + nsym(nx) + NU * nx + 3;
     return s;
 }
 
 /* Kernel-side copy of the solver options (Algorithm 1 constants). */
 struct KOpts {
-    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant, warm_select, cap_rule, compensated;
+    int32_t max_iters, max_outer, n_alpha, ls_chunk, variant, warm_select, cap_rule, compensated, hessian;
     float eps_tol, tau, omega0, eta0, a_omega, b_omega, a_eta, b_eta, rho0, rho_max, mu0, beta, ls_rel_eps, select_mu,
         select_rho;
 };
@@ -230,6 +231,20 @@ struct KernelArgs {
     KOpts opts;
     int32_t tab_ints;         /* dynamic shared memory for the stage/path tables, in ints (0: none) */
     int32_t stg_ld;           /* path threads with sweep staging slots after the tables (0: no staging) */
+};
+
+/* Arguments of the warm-start glue kernels (features, targets, starts). */
+struct GlueArgs {
+    const ProbRec *recs;
+    const int32_t *ibase;
+    const float *inbase, *outbase;
+    float *out;                 /* features / targets / starts, problem k at out + k*stride */
+    int64_t stride;
+    const float *pred, *mean, *std;
+    int64_t ld_pred;
+    int32_t n_scen, n_obs_max;
+    const int32_t *order_base;  /* starts: problems of one model */
+    int32_t y_sqrt;             /* targets / starts: AL multipliers in square-root form */
 };
 
 }  // namespace bmpc

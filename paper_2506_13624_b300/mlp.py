@@ -42,8 +42,9 @@ def _setup():
     L.bmpc_mlp_workspace_floats.argtypes = [C.POINTER(Layer), C.c_int32, C.c_int32]
     L.bmpc_mlp_workspace_floats.restype = C.c_int64
     L.bmpc_mlp_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32]
-    L.bmpc_mlp_targets.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
-    L.bmpc_mlp_start.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+    L.bmpc_mlp_targets.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32]
+    L.bmpc_mlp_start.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                 C.c_int32]
     L.bmpc_mlp_standardize.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                        C.c_void_p]
     L._mlp_ready = True
@@ -159,13 +160,13 @@ def features(batch, out, n_scen, n_obs):
     _check(_setup().bmpc_mlp_features(batch.handle, out.data_ptr(), out.shape[1], n_scen, n_obs), "bmpc_mlp_features")
 
 
-def targets(batch, out):
-    _check(_setup().bmpc_mlp_targets(batch.handle, out.data_ptr(), out.shape[1]), "bmpc_mlp_targets")
+def targets(batch, out, y_sqrt=1):
+    _check(_setup().bmpc_mlp_targets(batch.handle, out.data_ptr(), out.shape[1], int(y_sqrt)), "bmpc_mlp_targets")
 
 
-def starts(batch, pred, mean, std, out):
+def starts(batch, pred, mean, std, out, y_sqrt=1):
     _check(_setup().bmpc_mlp_start(batch.handle, pred.data_ptr(), pred.shape[1], mean.data_ptr(), std.data_ptr(),
-                                   out.data_ptr(), out.shape[1]), "bmpc_mlp_start")
+                                   out.data_ptr(), out.shape[1], int(y_sqrt)), "bmpc_mlp_start")
 
 
 def standardize(raw, mean, std, out):

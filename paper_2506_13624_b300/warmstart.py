@@ -4,9 +4,9 @@ network, and the receding-horizon comparison of cold, shifted and learned starts
 Features (per problem): the measured state without its X coordinate and, for every scenario
 and obstacle, the predicted obstacle position at the middle and the end of the scenario and
 its final heading, positions relative to the ego's X.  Targets: the converged solution
-(states with X relative to the ego, controls, dynamics multipliers, AL multipliers), both
-standardised with statistics of the training set.  At run time the network's start goes into
-warm-start slot 0 and the shifted previous solution (or nothing: the cold start) into slot 1; the
+(states with X relative to the ego, controls, dynamics multipliers, AL multipliers, the latter
+as sqrt(y) by default), both standardised with statistics of the training set.  At run time the
+network's start goes into warm-start slot 0 and the shifted previous solution (or nothing: the cold start) into slot 1; the
 solver starts from the network's start only when its merit, with a large constraint penalty, is
 not above the fallback's (bmpc_opts.warm_select, select_rho).
 
@@ -46,12 +46,13 @@ def solve_batch(problems, opts=None, prev=None, warm_from=None):
     return b
 
 
-def build_dataset(make, total, chunk, opts=None, device="cuda", log=print):
+def build_dataset(make, total, chunk, opts=None, device="cuda", log=print, y_sqrt=1, y_alt=False):
     """Solve `total` problems from make(chunk_index, count) in chunks; keep the converged ones.
 
-    Returns (X_raw, Y_raw) fp32 CUDA tensors [kept, feature_dim], [kept, target_dim] and timing."""
+    Returns (X_raw, Y_raw) fp32 CUDA tensors [kept, feature_dim], [kept, target_dim] and timing;
+    with y_alt the targets with the other multiplier form are in info["Y_alt"]."""
     import torch
-    X, Y = [], []
+    X, Y, Y2 = [], [], []
     t_gen = t_solve = 0.0
     kept = 0
     done = 0
@@ -68,7 +69,11 @@ def build_dataset(make, total, chunk, opts=None, device="cuda", log=print):
         fx = torch.empty((cnt, feature_dim(ps[0])), dtype=torch.float32, device=device)
         fy = torch.empty((cnt, target_dim(ps[0])), dtype=torch.float32, device=device)
         mlp.features(b, fx, N_SCEN, N_OBS)
-        mlp.targets(b, fy)
+        mlp.targets(b, fy, y_sqrt)
+        if y_alt:
+            fy2 = torch.empty_like(fy)
+            mlp.targets(b, fy2, 1 - y_sqrt)
+            Y2.append(fy2[ok])
         torch.cuda.synchronize()
         X.append(fx[ok])
         Y.append(fy[ok])
@@ -81,11 +86,15 @@ def build_dataset(make, total, chunk, opts=None, device="cuda", log=print):
             log(f"  dataset {done}/{total} solved, {kept} converged")
     X = torch.cat(X)
     Y = torch.cat(Y)
-    return X, Y, dict(generate_s=t_gen, solve_s=t_solve, kept=kept, total=total)
+    info = dict(generate_s=t_gen, solve_s=t_solve, kept=kept, total=total)
+    if y_alt:
+        info["Y_alt"] = torch.cat(Y2)
+    return X, Y, info
 
 
-def standardise(X_raw, Y_raw):
-    """Statistics of the training set and bf16 standardised copies (kernels do the conversion)."""
+def standardise(X_raw, Y_raw, y_sqrt=1):
+    """Statistics of the training set and bf16 standardised copies (kernels do the conversion).
+    y_sqrt records the multiplier form of the targets, which the starts invert."""
     import torch
     fm, fs = X_raw.mean(0), X_raw.std(0).clamp_min(1e-3)
     tm, ts = Y_raw.mean(0), Y_raw.std(0).clamp_min(1e-4)
@@ -93,7 +102,7 @@ def standardise(X_raw, Y_raw):
     Yb = torch.empty(Y_raw.shape, dtype=torch.bfloat16, device=Y_raw.device)
     mlp.standardize(X_raw, fm, fs, Xb)
     mlp.standardize(Y_raw, tm, ts, Yb)
-    return Xb, Yb, dict(fm=fm, fs=fs, tm=tm, ts=ts)
+    return Xb, Yb, dict(fm=fm, fs=fs, tm=tm, ts=ts, y_sqrt=y_sqrt)
 
 
 def train(net, Xb, Yb, epochs, batch=512, lr=1e-3, weight_decay=1e-4, seed=0, log=print):
@@ -134,8 +143,33 @@ def learned_starts(net, b, stats, batch_pad=128):
     mlp.standardize(fx, stats["fm"], stats["fs"], xb)
     pred = net.forward(xb)
     st = torch.empty((n, b.start_stride()), dtype=torch.float32, device=b.device)
-    mlp.starts(b, pred, stats["tm"], stats["ts"], st)
+    mlp.starts(b, pred, stats["tm"], stats["ts"], st, stats.get("y_sqrt", 1))
     b.set_warm_device(st, slot=0)
+    return st
+
+
+def start_errors(problems, starts, sols):
+    """Accuracy of packed starts against converged solutions (converged problems only): per block
+    (x, u, lam, y) the relative error sqrt(sum |start - sol|^2 / sum |sol|^2), and for y the
+    fraction of constraint rows whose activity (y > 1e-6) the start gets right."""
+    acc = {k: [0.0, 0.0] for k in ("x", "u", "lam", "y")}
+    agree = total = 0
+    for p, s, r in zip(problems, starts, sols):
+        if r["status"] != 0:
+            continue
+        n, nx = int(p["n"]), int(p["nx"])
+        nc = bmpc.n_con(p)
+        o = [0, n * nx, n * nx + 2 * n, 2 * n * nx + 2 * n, 2 * n * nx + 2 * n + n * nc]
+        for j, k in enumerate(("x", "u", "lam", "y")):
+            a, ref = np.asarray(s[o[j]:o[j + 1]], np.float64), np.asarray(r[k], np.float64).ravel()
+            acc[k][0] += float(np.sum((a - ref) ** 2))
+            acc[k][1] += float(np.sum(ref ** 2))
+        ys, yr = np.asarray(s[o[3]:o[4]]) > 1e-6, np.asarray(r["y"]).ravel() > 1e-6
+        agree += int(np.sum(ys == yr))
+        total += ys.size
+    out = {f"rel_{k}": math.sqrt(v[0] / max(v[1], 1e-30)) for k, v in acc.items()}
+    out["y_activity_agreement"] = agree / max(total, 1)
+    return out
 
 
 def timed_solve(b, opts):
@@ -189,9 +223,11 @@ def evaluate(net, stats, make_prev, count, opts=None, seed=0):
     timed_solve(prev, opts)                       # warm-up of the launch path
     prev.set_problems()
     first["cold"] = timed_solve(prev, opts)
+    cold_sols = prev.get_solutions()
     prev.set_problems()
     o1 = bmpc.Opts.from_buffer_copy(opts)
-    learned_starts(net, prev, stats)
+    st = learned_starts(net, prev, stats).cpu().numpy()
+    accuracy = start_errors(prev_ps, st, cold_sols)
     first["learned"] = timed_solve(prev, o1)
     prev.set_problems()
     first["learned_or_cold"] = learned(prev, None)
@@ -211,7 +247,7 @@ def evaluate(net, stats, make_prev, count, opts=None, seed=0):
     prev.close()
     b.close()
     return dict(first_solve={k: summarise(*v) for k, v in first.items()},
-                receding_horizon={k: summarise(*v) for k, v in nxt.items()})
+                receding_horizon={k: summarise(*v) for k, v in nxt.items()}, start_accuracy=accuracy)
 
 
 # ------------------------------------------------------------------ command line: the config-5 experiment
@@ -241,6 +277,8 @@ def main(argv=None):
     ap.add_argument("--eval-seed", type=int, default=6)
     ap.add_argument("--workers", type=int, default=12)
     ap.add_argument("--out", default="")
+    ap.add_argument("--y-form", choices=("sqrt", "linear", "both"), default="sqrt",
+                    help="form of the AL-multiplier targets; 'both' trains one network on each")
     a = ap.parse_args(argv)
     pool = mp.get_context("spawn").Pool(a.workers)          # started before the first CUDA call
     import torch
@@ -261,21 +299,30 @@ def main(argv=None):
     opts, _ = probe.autotune(opts)
     probe.close()
     t0 = time.perf_counter()
-    X, Y, info = build_dataset(make, a.train, a.chunk, opts)
+    y_sqrt = 0 if a.y_form == "linear" else 1
+    X, Y, info = build_dataset(make, a.train, a.chunk, opts, y_sqrt=y_sqrt, y_alt=a.y_form == "both")
     info["dataset_s"] = time.perf_counter() - t0
-    Xb, Yb, stats = standardise(X, Y)
-    del X, Y
-    torch.cuda.empty_cache()
-    dims = [Xb.shape[1], a.hidden, a.hidden, a.hidden, Yb.shape[1]]
-    net = mlp.MLP(dims, seed=1)
-    hist, t_train = train(net, Xb, Yb, a.epochs, a.batch, a.lr)
-    flops = 6.0 * a.batch * sum(x * y for x, y in zip(dims[:-1], dims[1:])) * a.epochs * (Xb.shape[0] // a.batch)
+    forms = [(y_sqrt, Y)] + ([(1 - y_sqrt, info.pop("Y_alt"))] if a.y_form == "both" else [])
+    del Y
     eval_make = lambda cnt: scenes.batch_problems(a.eval_seed * 1000003, cnt)
-    summary = evaluate(net, stats, eval_make, a.eval, opts)
+    res = dict(dataset=info, opts=dict(block_threads=opts.block_threads, variant=opts.variant,
+                                       ls_chunk=opts.ls_chunk), runs={})
+    while forms:
+        ys, Yf = forms.pop(0)
+        Xb, Yb, stats = standardise(X, Yf, y_sqrt=ys)
+        del Yf
+        torch.cuda.empty_cache()
+        dims = [Xb.shape[1], a.hidden, a.hidden, a.hidden, Yb.shape[1]]
+        net = mlp.MLP(dims, seed=1)
+        hist, t_train = train(net, Xb, Yb, a.epochs, a.batch, a.lr)
+        flops = 6.0 * a.batch * sum(x * y for x, y in zip(dims[:-1], dims[1:])) * a.epochs * (Xb.shape[0] // a.batch)
+        del Xb, Yb
+        torch.cuda.empty_cache()
+        res["runs"]["sqrt" if ys else "linear"] = dict(
+            dims=dims, train_loss=hist, train_s=t_train, train_tflops=flops / t_train / 1e12,
+            eval=evaluate(net, stats, eval_make, a.eval, opts))
+        del net
     pool.close()
-    res = dict(dataset=info, dims=dims, train_loss=hist, train_s=t_train, train_tflops=flops / t_train / 1e12,
-               eval=summary, opts=dict(block_threads=opts.block_threads, variant=opts.variant,
-                                       ls_chunk=opts.ls_chunk))
     print(json.dumps(res))
     if a.out:
         with open(a.out, "w") as f:

@@ -159,9 +159,9 @@ def test_default_options_match_their_documentation():
     assert (o.omega0, o.a_omega, o.b_omega, o.a_eta) == (1.0, 1.0, 1.0, np.float32(0.1))
     assert o.eta0 == np.float32(0.1) and o.b_eta == np.float32(0.9)
     assert (o.rho0, o.rho_max, o.mu0, o.cap_rule) == (10.0, 1e6, 1.0, 0)
-    assert o.kkt_margin == np.float32(0.8) and o.compensated == 1
+    assert o.kkt_margin == np.float32(0.8) and o.compensated == 1 and o.hessian == 0
     assert o.beta == np.float32(1e-4) and o.ls_rel_eps == np.float32(1e-6)
     assert (o.block_threads, o.blocks_per_sm, o.variant, o.warm_select, o.queue_order) == (0, 0, 0, 0, 1)
     assert list(o.block_threads_model) == [0, 0, 0, 0]
     assert o.select_mu == 100.0 and o.select_rho == 1e4
-    assert C.sizeof(bmpc.Opts) == 31 * 4   # 31 four-byte fields, as in bmpc_opts
+    assert C.sizeof(bmpc.Opts) == 32 * 4   # 32 four-byte fields, as in bmpc_opts

@@ -150,8 +150,9 @@ def _layerwise_backward(net, Ws, x, t):
     act = [_f64(keep[1]), _f64(keep[3])]
     # dy0, dy1 hold contiguous [B][width] gradients: g_0 in dy0, g_1 in dy1 after the step
     h0, h1 = Ws[0].shape[1], Ws[1].shape[1]
-    g0 = _f64(keep[-5]).reshape(-1)[:B * h0].reshape(B, h0)
-    g1 = _f64(keep[-4]).reshape(-1)[:B * h1].reshape(B, h1)
+    # only the first B * width entries are written: the rest of the buffer is never read
+    g0 = _f64(keep[-5].reshape(-1)[:B * h0]).reshape(B, h0)
+    g1 = _f64(keep[-4].reshape(-1)[:B * h1]).reshape(B, h1)
     P = _f64(pred)
     e = P - t
     g2_exact = 2.0 * e / e.size
@@ -212,18 +213,24 @@ def test_targets_and_starts_round_trip():
     sol = b.get_solutions()
     D = warmstart.target_dim(ps[0])
     tg = torch.empty((len(ps), D), dtype=torch.float32, device="cuda")
-    mlp.targets(b, tg)
-    mean = tg.mean(0)
-    std = tg.std(0).clamp_min(1e-3)
-    pred = ((tg - mean) / std).contiguous()
-    st = torch.empty((len(ps), b.start_stride()), dtype=torch.float32, device="cuda")
-    mlp.starts(b, pred, mean, std, st)
-    st = st.cpu().numpy()
-    for k, (p, s) in enumerate(zip(ps, sol)):
-        n, nx, nc = p["n"], p["nx"], bmpc.n_con(p)
-        # the start rolls the (converged, defect-free) controls out again: it reproduces the solution
-        packed = np.concatenate([s["x"].ravel(), s["u"].ravel(), s["lam"].ravel(), s["y"].ravel()])
-        np.testing.assert_allclose(st[k, :packed.size], packed, atol=2e-3 * max(1.0, np.abs(packed).max()))
+    for y_sqrt in (0, 1):
+        mlp.targets(b, tg, y_sqrt)
+        mean = tg.mean(0)
+        std = tg.std(0).clamp_min(1e-3)
+        pred = ((tg - mean) / std).contiguous()
+        st = torch.empty((len(ps), b.start_stride()), dtype=torch.float32, device="cuda")
+        mlp.starts(b, pred, mean, std, st, y_sqrt)
+        st = st.cpu().numpy()
+        tgh = tg.cpu().numpy()
+        for k, (p, s) in enumerate(zip(ps, sol)):
+            n, nx, nc = p["n"], p["nx"], bmpc.n_con(p)
+            # the start rolls the (converged, defect-free) controls out again: it reproduces the solution
+            packed = np.concatenate([s["x"].ravel(), s["u"].ravel(), s["lam"].ravel(), s["y"].ravel()])
+            np.testing.assert_allclose(st[k, :packed.size], packed, atol=2e-3 * max(1.0, np.abs(packed).max()))
+            # the multiplier targets in the requested form
+            yt = tgh[k, packed.size - s["y"].size:packed.size]
+            np.testing.assert_allclose(yt, np.sqrt(s["y"].ravel()) if y_sqrt else s["y"].ravel(), rtol=1e-6,
+                                       atol=1e-30)
     f = torch.zeros((len(ps), warmstart.feature_dim(ps[0])), dtype=torch.float32, device="cuda")
     mlp.features(b, f, warmstart.N_SCEN, warmstart.N_OBS)
     f = f.cpu().numpy()

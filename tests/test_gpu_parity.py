@@ -55,7 +55,7 @@ def _gpu(problems, **kw):
     return res
 
 
-def _check_pair(p, g, r):
+def _check_pair(p, g, r, orc_kw=None):
     """Returns 'match', 'distinct' or raises AssertionError with a reason."""
     assert g["status"] == oracle.OK, f"GPU status {g['status']} (oracle {r['status']}), r_kkt={g['r_kkt']:.2e}"
     nl = np.ones(p["n"], bool)
@@ -67,23 +67,23 @@ def _check_pair(p, g, r):
     du = np.abs(g["u"][inner] - r["u"][inner]).max()
     if du <= U_REL * max(np.abs(r["u"][inner]).max(), 1.0):
         return "match"
-    w = _orc(p, warm=(g["x"], g["u"], g["lam"], g["y"]))
+    w = _orc(p, warm=(g["x"], g["u"], g["lam"], g["y"]), **(orc_kw or {}))
     assert w["status"] == oracle.OK and w["inner_iters"] <= 2, "GPU point not confirmed by the oracle"
     assert np.abs(w["u"][inner] - g["u"][inner]).max() <= U_REL * max(np.abs(g["u"][inner]).max(), 1.0)
     return "distinct"
 
 
-def _run_config(problems, min_match=0.8, **kw):
+def _run_config(problems, min_match=0.8, orc_kw=None, **kw):
     gres = _gpu(problems, **kw)
     counts = {"match": 0, "distinct": 0, "oracle_fail": 0}
     dits = []
     for p, g in zip(problems, gres):
-        r = _orc(p)
+        r = _orc(p, **(orc_kw or {}))
         if r["status"] != oracle.OK:
             counts["oracle_fail"] += 1
             assert g["status"] in (oracle.OK, oracle.MAX_ITER, oracle.LS_FAIL)
             continue
-        kind = _check_pair(p, g, r)
+        kind = _check_pair(p, g, r, orc_kw)
         counts[kind] += 1
         if kind == "match":
             dits.append(g["inner_iters"] - r["inner_iters"])
@@ -474,23 +474,23 @@ def _fp32(a):
     return np.asarray(a, np.float32).astype(np.float64)
 
 
-def _one_iteration(p, k):
+def _one_iteration(p, k, hessian=0):
     """Both sides take one inner iteration from the same FP32 iterate: the cold start (k = 0, each
     side forms its own) or the oracle's iterate after k iterations, rounded to float32 (k is lowered
     below the oracle's own iteration count, so that the iterate is not already converged)."""
     if k == 0:
         warm = None
     else:
-        k = max(1, min(k, _orc(p)["inner_iters"] - 2))
-        it = _orc(p, max_iters=k)
+        k = max(1, min(k, _orc(p, hessian=hessian)["inner_iters"] - 2))
+        it = _orc(p, max_iters=k, hessian=hessian)
         warm = tuple(_fp32(it[key]) for key in ("x", "u", "lam", "y"))
     from paper_2506_13624_b300 import bmpc
     b = bmpc.Batch([p])
     b.set_problems(warm=None if warm is None else [warm])
-    b.solve(bmpc.default_opts(max_iters=1))
+    b.solve(bmpc.default_opts(max_iters=1, hessian=hessian))
     g = b.get_solutions()[0]
     b.close()
-    r = _orc(p, max_iters=1, warm=warm)
+    r = _orc(p, max_iters=1, warm=warm, hessian=hessian)
     return g, r
 
 
@@ -680,3 +680,55 @@ def test_per_edge_dynamics_refuses_sweeps_without_edges():
     b.solve(bmpc.default_opts(variant=2))
     assert b.get_solutions()[0]["status"] == oracle.OK
     b.close()
+
+
+# ------------------------------------------------------------------ exact Hessian (Sec. IV-A)
+def _exact_cases():
+    return (scenes.instances(1, 6) + scenes.instances(2, 3) + [scenes.unicycle(s) for s in range(6)]
+            + [scenes.unicycle(s, splits={1: 2, 10: 2}) for s in range(2)]
+            + [scenes.mass_spring(s, N=20, Nr=3, constrained=True) for s in range(2)])
+
+
+@pytest.mark.parametrize("variant", [0, 1, 5])
+def test_exact_hessian_parity(variant):
+    """The exact Hessian of the Lagrangian with eigenvalue modification on both sides (the GPU's
+    hyper-dual second derivatives and Jacobi eigen-decomposition in FP32 against the oracle's in
+    FP64), whole solves on every model and tree family, under the per-path, level and jump sweeps."""
+    ps = _exact_cases()
+    if variant == 5:   # the jump sweep reads one model per node: no per-edge dynamics
+        ps = [p for p in ps if p.get("Aedge") is None]
+    print(_run_config(ps, orc_kw={"hessian": 1}, variant=variant, hessian=1))
+
+
+@pytest.mark.parametrize("cfg,k", [(1, 0), (1, 3), (2, 0), (2, 4), ("unicycle", 5)])
+def test_exact_hessian_one_iteration(cfg, k):
+    """One exact-Hessian iteration from an identical FP32 iterate, element by element: the modified
+    blocks enter the Riccati recursion, the merit slope and the curvature test, so a wrong second
+    derivative or a wrong eigenvalue floor moves the step."""
+    for seed in range(2):
+        p = scenes.unicycle(seed) if cfg == "unicycle" else scenes.instances(cfg, 1, seed0=seed)[0]
+        g, r = _one_iteration(p, k, hessian=1)
+        assert g["inner_iters"] == r["inner_iters"] == 1 and g["status"] == r["status"]
+        for key in ("x", "u", "lam", "y"):
+            a, c = g[key], r[key]
+            if c.size:
+                d = float(np.abs(a - c).max()) / max(1.0, float(np.abs(c).max()))
+                assert d <= STEP_TOL[key], (cfg, k, seed, key, d)
+
+
+def test_exact_hessian_refuses_diagonal_cost_sweeps():
+    """The 8-lane and scan sweeps assume the diagonal cost blocks: with hessian = 1 they are refused
+    and nothing runs; the linear-quadratic problem (no curvature beyond the cost) is solved in one
+    iteration either way."""
+    from paper_2506_13624_b300 import bmpc
+    b = bmpc.Batch(scenes.instances(1, 2))
+    b.set_problems()
+    for v in (3, 4):
+        with pytest.raises(RuntimeError):
+            b.solve(bmpc.default_opts(variant=v, hessian=1))
+    b.close()
+    ps = [scenes.mass_spring(0, N=20, Nr=2), scenes.linear_problem(1, N=12, splits={2: 3})]
+    for g, p in zip(_gpu(ps, hessian=1), ps):
+        r = _orc(p)
+        assert g["status"] == oracle.OK and g["inner_iters"] == 1 == r["inner_iters"]
+        np.testing.assert_allclose(g["u"], r["u"], atol=1e-4 * max(1.0, np.abs(r["u"]).max()))

@@ -93,7 +93,7 @@ def test_trained_network_gains_over_cold_start_and_untrained_network():
     b.set_problems()
     b.set_warm_device(st, slot=0)
     b.solve(sel)
-    res = b.get_solutions(want_arrays=False)
+    res = b.get_solutions()
     checked = 0
     for k in range(0, len(ps), 16):
         x, u, lam, y = _unpack(ps[k], st_h[k], nc)
@@ -104,6 +104,25 @@ def test_trained_network_gains_over_cold_start_and_untrained_network():
             checked += 1
     assert checked >= 16
     it_sel, conv_sel = _summary(res)
+
+    # a solve from the learned start ends where the oracle's solve from the same start ends: the
+    # FP64 KKT conditions hold at the GPU's point, the controls agree, and so do the iteration counts
+    compared = 0
+    for k in range(0, len(ps), 16):
+        g = res[k]
+        if g["start_used"] != 1:
+            continue
+        warm = tuple(np.asarray(a, np.float64) for a in _unpack(ps[k], st_h[k], nc))
+        r = oracle.solve(ps[k], warm=warm, **oracle.PRODUCT_RULE)
+        if r["status"] != oracle.OK:
+            continue
+        assert g["status"] == oracle.OK, (k, g["status"], g["r_kkt"])
+        assert oracle.kkt(ps[k], g["x"], g["u"], g["lam"], g["y"])[:4].max() <= 1e-5, k
+        du = np.abs(g["u"] - r["u"]).max()
+        assert du <= 1e-4 * max(1.0, np.abs(r["u"]).max()), (k, du)
+        assert abs(g["inner_iters"] - r["inner_iters"]) <= 1, (k, g["inner_iters"], r["inner_iters"])
+        compared += 1
+    assert compared >= 8, compared
 
     # and the solves: fewer iterations on average and no fewer converged problems than the cold start
     print(f"\ncold: {it_cold:.2f} iterations, {conv_cold:.3f} converged; learned with cold fallback: "
