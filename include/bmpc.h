@@ -239,7 +239,9 @@ int bmpc_shift_warm_start(bmpc_batch *next, const bmpc_batch *prev, int32_t slot
  * 128 / 256 / 512, sweep variant 1 to 5, line-search chunk 1 / 2 / 4; the other fields from `base`,
  * NULL = defaults), timing each with CUDA events on the handle's stream, and returns in *best the
  * configuration with the most converged solves per second and in *best_us_per_solve its time per
- * problem.  Synchronises the stream; leaves the last candidate's solution in the outputs. */
+ * problem.  The scan sweeps (variant 4) are candidates for single-problem batches only: they trade
+ * work for depth, which only a problem solved alone can use.  Synchronises the stream; leaves the
+ * last candidate's solution in the outputs. */
 int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *best_us_per_solve);
 
 /* Copy solutions back (synchronises the stream).  Host arrays, concatenated over problems

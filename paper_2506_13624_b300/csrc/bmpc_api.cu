@@ -973,6 +973,7 @@ int bmpc_autotune(bmpc_batch *b, const bmpc_opts *base, bmpc_opts *best, float *
             for (int ch : kChunk) {
                 if (v >= 3 && b->any_edge) continue;   /* per-edge dynamics: sweeps 1 and 2 */
                 if (o.hessian && (v == 3 || v == 4)) continue;
+                if (v == 4 && b->n > 1) continue;   /* scan sweeps: single latency-critical solves */
                 bmpc_opts c = o;
                 c.block_threads = bt;
                 for (int m = 0; m < NUM_MODELS; ++m) c.block_threads_model[m] = 0;
