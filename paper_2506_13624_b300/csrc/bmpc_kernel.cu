@@ -245,6 +245,19 @@ __device__ __forceinline__ ModelK model_k(const float *prm, float dl) {
  * entries are folded away after unrolling).  MODEL 0: kinematic bicycle, 1: dynamic
  * bicycle with linear tyres and small steering angle, 3: unicycle (X' = v cos th,
  * Y' = v sin th, th' = omega, v' = a; the constraint benchmark of Sec. V-B). */
+/* Structural nonzeros of the right-hand side's state Jacobian J = dF/dx as rhs_jac sets them (every
+ * other entry stays 0).  The tangent propagation of dyn_lin skips the products with the structural
+ * zeros: IEEE arithmetic does not let the compiler drop 0 * t itself, and acc + 0 * t = acc for
+ * finite t, so the results are the same. */
+template <int MODEL>
+__host__ __device__ constexpr bool jac_nz(int i, int k) {
+    if (MODEL == 0) return (i < 2 && (k == 2 || k == 3)) || (i == 2 && k == 3);
+    if (MODEL == 3) return i < 2 && (k == 2 || k == 3);
+    if (MODEL == 1)
+        return (i < 2 && k >= 2 && k <= 4) || (i == 2 && k == 5) || (i == 3 && k >= 4) || (i >= 4 && k >= 3);
+    return true;
+}
+
 template <int NX, int MODEL>
 __device__ __forceinline__ void rhs_jac(const float *prm, const ModelK &mk, const float (&s)[NX], float a, float dl,
                                         float (&f)[NX], float (&J)[NX][NX], float (&Ju)[NX][NU]) {
@@ -445,7 +458,8 @@ __device__ __forceinline__ void dyn_lin(const ProbRec &R, const float (&x)[NX], 
                     for (int i = 0; i < NX; ++i) {
                         float acc = (jj >= NX) ? Ju[i][jj - NX] : 0.f;
 #pragma unroll
-                        for (int k = C0; k < NX; ++k) acc += J[i][k] * t[k];
+                        for (int k = C0; k < NX; ++k)
+                            if (jac_nz<MODEL>(i, k)) acc += J[i][k] * t[k];
                         Ds[i][j] += wg * acc;
                         Dp[i][j] = acc;
                     }
