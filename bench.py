@@ -549,6 +549,80 @@ def run_single(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------- general-size tree LQR (Sec. V-A)
+def lqr_work(parent, nx, nu, batch):
+    """Algorithmic FP32 flops and minimum DRAM bytes of one tree LQR solve (include/bmpc_lqr.h):
+    per edge T1 = PA, T2 = PB, A'T1, A'T2, B'T2, g and its products; per non-leaf node the Cholesky
+    of H, the n_x + 1 solves, P and p; the forward sweep.  Bytes: every input read once, every
+    output written once, and P, p, K, k read once more by the parent's step or the forward sweep."""
+    n = len(parent)
+    leaves = n - len(set(int(v) for v in parent[1:]))
+    edges, inner = n - 1, n - leaves
+    f_edge = 4 * nx ** 3 + 4 * nx * nx * nu + 2 * nx * nu * nu + 4 * nx * nx + 2 * nx * nu
+    f_node = nu ** 3 / 3 + 2 * nu * nu * (nx + 1) + 2 * nx * nx * nu + 2 * nx * nu
+    f_fwd = 2 * nx * nx + 2 * nx * nu
+    flops = batch * (edges * (f_edge + f_fwd) + inner * (f_node + 2 * nu * nx) + n * 2 * nx * nx)
+    words_in = n * (nx * nx + nx * nu + nx + nx * nx + nx) + inner * (nu * nu + nu)
+    words_out = n * (nx * nx + 2 * nx + nu * nx + nu + 2 * nx + nu)
+    words_reread = n * (nx * nx + nx) + inner * (nu * nx + nu)
+    return float(flops), 4.0 * batch * (words_in + words_out + words_reread)
+
+
+def run_lqr(args):
+    """Tree LQR timings at the sizes of Sec. V-A: tree LQR against the number of scenario paths
+    (n_x = 30, n_d = 2), batch LQR against the batch size (n_x = 10, N = 80) and single LQR against
+    the horizon (n_x = 30).  One JSON line per case; each solve is a CUDA graph of its launches,
+    timed with CUDA events over `steps` replays after `warmup`."""
+    import torch
+    from paper_2506_13624_b300 import bmpc, lqr
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        fp32_peak = bmpc.fp32_peak_tflops()
+    hbm_peak = None
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as fh:
+            hbm_peak = json.load(fh).get("hbm_gbs")
+    cases = ([("tree", 15, 40, nr, 1) for nr in (1, 3, 5, 7, 9)]
+             + [("batch", 5, 80, 0, b) for b in (1, 16, 64, 256, 1024)]
+             + [("single", 15, N, 0, 1) for N in (20, 40, 60, 80, 100)])
+    for kind, M, N, Nr, batch in cases:
+        d = scenes.mass_spring_chain(0, M=M, N=N, Nr=Nr, batch=batch)
+        dev = lambda a: torch.tensor(np.ascontiguousarray(a, np.float32), device="cuda")
+        ins = [dev(d[k]) for k in ("Q", "R", "q", "r", "A", "B", "c", "x0")]
+        h = lqr.TreeLQR(d["parent"], d["nx"], d["nu"], batch=batch, stream=s)
+        with torch.cuda.stream(s):
+            h.solve(*ins)                                  # eager run: checks H
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                h.solve(*ins, check=False)
+            for _ in range(args.warmup):
+                g.replay()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(s)
+            for _ in range(args.steps):
+                g.replay()
+            e1.record(s)
+        e1.synchronize()
+        h.status()
+        us = 1e3 * e0.elapsed_time(e1) / args.steps
+        flops, byts = lqr_work(d["parent"], d["nx"], d["nu"], batch)
+        tf, gbs = flops / (us * 1e-6) / 1e12, byts / (us * 1e-6) / 1e9
+        line = {"metric": "tree LQR solve time (Sec. V-A)", "value": us, "unit": "us/solve", "higher_is_better": False,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"case": kind, "masses": M, "nx": d["nx"], "nu": d["nu"], "N": N, "Nr": Nr, "nd": 2 if Nr else 1,
+                           "paths": 2 ** Nr, "nodes": int(len(d["parent"])), "batch": batch,
+                           "launches_per_solve": 2 * h.stages, "steps": args.steps, "warmup": args.warmup},
+                "roofline": {"alu": {"achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
+                                     "flops_per_solve": flops},
+                             "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": gbs / hbm_peak if hbm_peak else None, "bytes_per_solve": byts},
+                             "launch": {"us_per_launch": us / (2 * h.stages)}}}
+        print(json.dumps(line), flush=True)
+        h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -572,6 +646,8 @@ def main():
     ap.add_argument("--max-iters", type=int, default=0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--lqr", action="store_true",
+                    help="the general-size tree LQR at the sizes of Sec. V-A (one JSON line per case)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4, help="oracle problems per worker per reference step")
@@ -583,6 +659,8 @@ def main():
         run_reference(args)
     elif args.single:
         run_single(args)
+    elif args.lqr:
+        run_lqr(args)
     else:
         run_gpu(args)
 

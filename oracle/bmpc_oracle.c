@@ -49,8 +49,10 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define MAXX 16
-#define MAXU 8
+/* capacities of the fixed-size work arrays: state and input dimensions up to those of the
+ * mass-spring chains of Sec. V-A (n_x = 2M = 30, n_u = M - 1 = 14) and a little beyond */
+#define MAXX 32
+#define MAXU 16
 #define MAXN (MAXX + MAXU)
 #define OBS_EPS 1e-6   /* smoothing of the normalised distance at the ellipse centre */
 

@@ -8,9 +8,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbmpc.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("bmpc_kernel.cu", "bmpc_api.cu", "bmpc_static.cu", "mlp_kernels.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("bmpc_kernel.cu", "bmpc_api.cu", "bmpc_static.cu", "mlp_kernels.cu",
+                                          "tree_lqr.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "bmpc_layout.h"), os.path.join(ROOT, "include", "bmpc.h"),
-                  os.path.join(ROOT, "include", "bmpc_mlp.h")]
+                  os.path.join(ROOT, "include", "bmpc_mlp.h"), os.path.join(ROOT, "include", "bmpc_lqr.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]

@@ -409,6 +409,43 @@ def mass_spring(seed: int, N: int = 20, Nr: int = 2, nd: int = 2, constrained: b
     return _finish(p)
 
 
+def mass_spring_chain(seed: int, M: int = 15, N: int = 40, Nr: int = 3, nd: int = 2, batch: int = 1,
+                      dt: float = 0.1):
+    """Tree LQR data of Sec. V-A at the paper's sizes: a chain of M unit masses joined by springs,
+    with walls at both ends (n_x = 2M: positions, then velocities) and M - 1 actuators, actuator a
+    pushing masses a and a + 1 apart (n_u = M - 1).  The spring constant is uncertain: n_d values
+    k ~ U[0.5, 1.5] at every stage up to the robust horizon N_r (Z = n_d^N_r scenario paths), each
+    edge carrying the RK4 discretisation (step dt) of its branch's spring constant; past N_r a branch
+    keeps its parent edge's model.  Cost: Q = I at every node, R = 0.1 I, no linear terms; the batch
+    of `batch` problems shares the tree and differs in the spring samples and the initial positions
+    x0 ~ U[-1, 1] (velocities 0).  Returns float64 arrays in the layout of the general tree LQR
+    ([batch][n][...]), with parent and stage."""
+    rng = np.random.default_rng([12, seed, M, N, Nr, nd])
+    nx, nu = 2 * M, M - 1
+    parent, stage = tree_parents(N, {s: nd for s in range(1, Nr + 1)})
+    n = parent.shape[0]
+    E = np.zeros((M, nu))
+    for a in range(nu):
+        E[a, a], E[a + 1, a] = 1.0, -1.0
+    A = np.zeros((batch, n, nx, nx))
+    B = np.zeros((batch, n, nx, nu))
+    for t in range(batch):
+        for m in range(1, n):
+            if stage[m] > Nr:
+                A[t, m], B[t, m] = A[t, parent[m]], B[t, parent[m]]
+                continue
+            k = rng.uniform(0.5, 1.5)
+            Kc = k * (np.diag(np.full(M, -2.0)) + np.diag(np.ones(M - 1), 1) + np.diag(np.ones(M - 1), -1))
+            Ac = np.block([[np.zeros((M, M)), np.eye(M)], [Kc, np.zeros((M, M))]])
+            Bc = np.vstack([np.zeros((M, nu)), E])
+            A[t, m], B[t, m] = _rk4_linear(Ac, Bc, dt)
+    Q = np.broadcast_to(np.eye(nx), (batch, n, nx, nx)).copy()
+    R = np.broadcast_to(0.1 * np.eye(nu), (batch, n, nu, nu)).copy()
+    x0 = np.concatenate([rng.uniform(-1.0, 1.0, (batch, M)), np.zeros((batch, M))], axis=1)
+    return dict(parent=parent, stage=stage, nx=nx, nu=nu, Q=Q, R=R, q=np.zeros((batch, n, nx)),
+                r=np.zeros((batch, n, nu)), A=A, B=B, c=np.zeros((batch, n, nx)), x0=x0)
+
+
 def instances(config: int, count: int, seed0: int = 0):
     """Seeded instances of a configuration (1-3), seeds seed0 .. seed0+count-1."""
     gen = {1: config1, 2: config2, 3: config3}[config]

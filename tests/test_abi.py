@@ -39,6 +39,41 @@ def test_library_exports_every_mlp_symbol():
         assert hasattr(L, name), name
 
 
+def test_library_exports_every_tree_lqr_symbol():
+    src = open(os.path.join(ROOT, "include", "bmpc_lqr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(bmpc_lqr_[a-z_]+)\s*\(", src))
+    assert names == {"bmpc_lqr_create", "bmpc_lqr_solve", "bmpc_lqr_status", "bmpc_lqr_stages", "bmpc_lqr_destroy"}
+    L = bmpc.lib()
+    for name in names:
+        assert hasattr(L, name), name
+
+
+@pytest.mark.parametrize("case", ["nx", "nu", "batch", "root", "order", "levels", "empty"])
+def test_tree_lqr_rejects_bad_trees_and_sizes_on_the_host(case):
+    """bmpc_lqr_create validates before any device call: sizes beyond n_x = 32 or n_u = 16, a
+    root with a parent, a parent after its child, stages out of level order, an empty tree."""
+    from paper_2506_13624_b300 import lqr
+    parent, nx, nu, batch = np.array([-1, 0, 0, 1, 2], np.int32), 4, 2, 1
+    if case == "nx":
+        nx = 33
+    elif case == "nu":
+        nu = 17
+    elif case == "batch":
+        batch = 0
+    elif case == "root":
+        parent[0] = 0
+    elif case == "order":
+        parent = np.array([-1, 2, 0], np.int32)
+    elif case == "levels":
+        parent = np.array([-1, 0, 1, 0], np.int32)   # node 3 (stage 1) after node 2 (stage 2)
+    n = 0 if case == "empty" else len(parent)
+    h = C.c_void_p()
+    rc = lqr._lib().bmpc_lqr_create(n, parent.ctypes.data_as(C.POINTER(C.c_int32)), nx, nu, batch, None,
+                                    C.byref(h))
+    assert rc == bmpc.ERR_INVALID and not h.value
+
+
 def test_version_and_status_strings():
     assert b"sm_103a" in bmpc.lib().bmpc_version()
     for s in (0, 1, 2, -1, -2, -3, -4, -5):

@@ -260,6 +260,25 @@ def test_per_edge_tree_lqr_equals_dense_kkt(seed):
         np.testing.assert_allclose(a, b, atol=1e-12 * max(1.0, np.abs(b).max()))
 
 
+@pytest.mark.parametrize("nx,nu", [(10, 4), (30, 14), (32, 16)])
+def test_per_edge_tree_lqr_at_the_mass_spring_sizes(nx, nu):
+    """The tree Riccati recursion with per-edge matrices at the state and input dimensions of Sec.
+    V-A's mass-spring chains (n_x = 2M, n_u = M - 1) and the largest supported: equal to the dense
+    KKT solution."""
+    rng = np.random.default_rng(300 + nx)
+    parent = _random_tree(rng, n_max=14)
+    leaf, Q, M, R, q, r, A, B, c = _random_lqr(rng, parent, nx, nu)
+    n = len(parent)
+    Ae = np.eye(nx) + (0.3 / np.sqrt(nx)) * rng.standard_normal((n, nx, nx))
+    Be = rng.standard_normal((n, nx, nu)) / np.sqrt(nx)
+    dx2, du2, lam2 = _dense_kkt(parent, leaf, Q, M, R, q, r, Ae, Be, c, edge=True)
+    K, k, P, pv, dx, du, lam = oracle.tree_lqr(parent, Q, M, R, q, r, Ae, Be, c, edge=True)
+    scale = max(1.0, np.abs(dx2).max(), np.abs(lam2).max())
+    np.testing.assert_allclose(dx, dx2, atol=1e-9 * scale)
+    np.testing.assert_allclose(du, du2, atol=1e-9 * scale)
+    np.testing.assert_allclose(lam[1:], lam2[1:], atol=1e-9 * scale)
+
+
 def _dense_lq_solution(p):
     """The whole LQ problem of a per-edge linear tree (no constraints) as one equality-constrained QP:
     min sum_i w_i [1/2 (x_i - xref_i)' Q (x_i - xref_i) + 1/2 u_i' R u_i] s.t. x_0 = x-bar,
