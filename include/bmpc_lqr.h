@@ -52,8 +52,9 @@ int bmpc_lqr_create(int32_t n, const int32_t *parent, int32_t nx, int32_t nu, in
                     bmpc_lqr **out);
 
 /* One tree LQR solve of the whole batch, asynchronous on the handle's stream: the backward sweep
- * (one launch per stage, leaves to root; one warp per node, lane j owning row j of the node's
- * matrices) and the forward sweep (one launch per stage, root to leaves).  All pointers are device
+ * (one launch per stage, leaves to root; one block per node, each thread owning four entries of a
+ * row of the node's matrix products) and the forward sweep (one launch per stage, root to leaves;
+ * one warp per node).  All pointers are device
  * pointers in the layout above; inputs are only read, the outputs K, k, P, p, x, u, lam written in
  * full.  0 on success, BMPC_ERR_INVALID on a NULL required pointer, BMPC_ERR_CUDA on a launch error.
  * The call is capturable into a CUDA graph. */

@@ -2,18 +2,18 @@
  * recursion of Eq. (tree_Riccati) and the feedback laws of Eq. (tree_feedback_laws), then the
  * forward sweep of Sec. III-A.  The C ABI and the problem statement are in include/bmpc_lqr.h.
  *
- * Layout of the work: one launch per stage and sweep.  In a launch every warp owns one node of the
- * stage (of one problem of the batch); lane j owns row j of the node's n_x x n_x matrices (the
- * child value function P_m, the sums A'PA, and the new P), so a node step is a set of per-lane dot
- * products over shared-memory tiles:
- *   per child edge m:  T1 = P_m A_m, T2 = P_m B_m, g = p_m + P_m c_m           (lane j: row j)
- *                      S_xx += A_m' T1, S_xu += A_m' T2, S_uu += B_m' T2,
- *                      s_x += A_m' g, s_u += B_m' g                              (lane j: row j)
- *   node:              H = R + S_uu (Cholesky across the warp), [K k] = -H^-1 [M + S_xu' | r + s_u]
- *                      (lane c: right-hand side c), P = Q + S_xx + S_ux' K, p = q + s_x + S_ux' k
+ * Layout of the work: one launch per stage and sweep.  Backward, a block of NXP / 4 warps owns one
+ * node of the stage (of one problem of the batch): thread (lane l, warp w) owns entries
+ * (l, 4w .. 4w + 3) of the node's matrix products, so a node step is a set of short dot products
+ * over shared-memory tiles, with the tree's depth as the only sequential chain:
+ *   per child edge m:  T1 = P_m A_m, T2 = P_m B_m, g = p_m + P_m c_m
+ *                      S_xx += A_m' T1, S_xu += A_m' T2, S_uu += B_m' T2, s_x += A_m' g, s_u += B_m' g
+ *   node:              H = R + S_uu (Cholesky by one warp), [K k] = -H^-1 [M + S_xu' | r + s_u]
+ *                      (thread c: right-hand side c), P = Q + S_xx + S_ux' K, p = q + s_x + S_ux' k
+ * Forward, one warp per node (lane j: row j of x_m = A_m x_p + B_m u_p + c_m, then u and lam).
  * Tiles are zero-padded to NXP x NXP (NXP in {8, 16, 32}) and NUP (in {4, 8, 16}) so that every
- * loop is unrolled at compile time; the rows of the tiles that the lanes read in common are
- * fetched as 16-byte broadcasts.  FP32 throughout (the paper's batch experiments run FP32 too). */
+ * loop is unrolled at compile time; the tile rows that many threads read in common are fetched as
+ * 16-byte broadcasts.  FP32 throughout (the paper's batch experiments run FP32 too). */
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,7 +27,7 @@
 
 namespace {
 
-constexpr int LQR_WARPS = 4;   /* nodes per block */
+constexpr int LQR_WARPS = 4;   /* nodes per block of the forward sweep */
 constexpr unsigned FULL = 0xffffffffu;
 
 struct LqrArgs {
@@ -39,42 +39,75 @@ struct LqrArgs {
     int s0, cnt;   /* first node of the stage and its node count */
 };
 
-/* Per-warp shared tiles; row strides are multiples of 4 floats (16-byte rows for the broadcast
- * reads) and 4 more than the columns (stores of 16 bytes by 8 lanes at a time hit distinct banks). */
+/* Shared tiles of one node step; row strides are multiples of 4 floats (16-byte rows for the
+ * broadcast reads) and 4 more than the columns (16-byte stores or row reads by 8 lanes at a time
+ * hit distinct banks). */
 template <int NXP, int NUP>
 struct LqrTiles {
     static constexpr int SX = NXP + 4, SU = NUP + 4;
-    float A[NXP][SX];   /* the edge's A_m */
-    float B[NXP][SU];   /* the edge's B_m */
-    float T1[NXP][SX];  /* P_m A_m; later the node's P before symmetrisation */
-    float T2[NXP][SU];  /* P_m B_m */
-    float H[NUP][SU];   /* H, then its Cholesky factor (lower triangle) */
-    float X[NUP][SX];   /* [Q_ux | q_u] with q_u in column NXP, then [K | k] */
-    float g[NXP];       /* p_m + P_m c_m */
+    float A[NXP][SX];    /* the edge's A_m */
+    float B[NXP][SU];    /* the edge's B_m */
+    float PS[NXP][SX];   /* the child's P_m */
+    float T1[NXP][SX];   /* P_m A_m; later the node's P before symmetrisation */
+    float T2[NXP][SU];   /* P_m B_m */
+    float H[NUP][SU];    /* H, then its Cholesky factor (lower triangle) */
+    float X[NUP][SX];    /* [Q_ux | q_u] with q_u in column NXP, then [K | k] */
+    float QUX[NUP][SX];  /* Q_ux, kept for P and p */
+    float g[NXP];        /* p_m + P_m c_m */
+    float cv[NXP];       /* c_m */
+    float qx[NXP];       /* q + s_x */
+    float id[NUP];       /* 1 / L_bb (0 past n_u) */
 };
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d) {
-    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
-}
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-/* Stage a rows x cols row-major global matrix into a zero-padded tile of R x C (stride S). */
+/* Stage a rows x cols row-major global matrix into a zero-padded tile of R x C (stride S), the
+ * `nt` threads of the block striding over its entries. */
 template <int R, int C, int S>
-__device__ __forceinline__ void stage_tile(float (*T)[S], const float *g, int rows, int cols, int lane) {
-    for (int idx = lane; idx < R * C; idx += 32) {
+__device__ __forceinline__ void stage_tile(float (*T)[S], const float *g, int rows, int cols, int tid, int nt) {
+    for (int idx = tid; idx < R * C; idx += nt) {
         const int a = idx / C, b = idx % C;
         T[a][b] = (a < rows && b < cols) ? g[(size_t)a * cols + b] : 0.f;
     }
 }
 
-template <int NXP, int NUP>
-__global__ void __launch_bounds__(32 * LQR_WARPS) lqr_backward_kernel(LqrArgs a) {
+/* The same with the thread count NT known at compile time: every load is issued before the first
+ * store, so the tile costs one memory latency instead of one per round. */
+template <int R, int C, int S, int NT>
+__device__ __forceinline__ void stage_tile_nt(float (*T)[S], const float *g, int rows, int cols, int tid) {
+    constexpr int IT = (R * C + NT - 1) / NT;
+    float v[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int idx = tid + it * NT, a = idx / C, b = idx % C;
+        v[it] = (idx < R * C && a < rows && b < cols) ? g[(size_t)a * cols + b] : 0.f;
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int idx = tid + it * NT;
+        if (idx < R * C) T[idx / C][idx % C] = v[it];
+    }
+}
+
+__device__ __forceinline__ void fma4(float4 &acc, float s, const float4 v) {
+    acc.x += s * v.x;
+    acc.y += s * v.y;
+    acc.z += s * v.z;
+    acc.w += s * v.w;
+}
+
+/* Backward step of one node per block: NXP / 4 warps; thread (lane l, warp w) owns entries
+ * (l, 4w .. 4w + 3) of the n_x-column products and, for w < NUP / 4, of the n_u-column ones. */
+template <int NXP, int NUP, int MINB>
+__global__ void __launch_bounds__(8 * NXP, MINB) lqr_backward_kernel(LqrArgs a) {
+    constexpr int NW = NXP / 4, NWU = NUP / 4;
     extern __shared__ __align__(16) float lqr_smem[];
     using Tiles = LqrTiles<NXP, NUP>;
-    Tiles *ws = reinterpret_cast<Tiles *>(lqr_smem) + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
-    const long long item = (long long)blockIdx.x * LQR_WARPS + threadIdx.x / 32;
-    if (item >= (long long)a.cnt * a.batch) return;   /* the whole warp leaves together */
+    Tiles *ts = reinterpret_cast<Tiles *>(lqr_smem);
+    const int tid = threadIdx.x, nt = blockDim.x, l = tid & 31, w = tid >> 5;
+    const int j0 = 4 * w;   /* this thread's column group */
+    const long long item = blockIdx.x;
     const int t = (int)(item / a.cnt);
     const int i = a.s0 + (int)(item % a.cnt);
     const int nx = a.nx, nu = a.nu;
@@ -82,218 +115,179 @@ __global__ void __launch_bounds__(32 * LQR_WARPS) lqr_backward_kernel(LqrArgs a)
     const float *Qi = a.Q + node * nx * nx;
     float *Pi = a.P + node * nx * nx, *Ki = a.K + node * nu * nx;
     const int c0 = a.child_off[i], c1 = a.child_off[i + 1];
-    const bool row = lane < nx;
+    const bool row = l < nx && l < NXP;
 
     if (c0 == c1) {   /* leaf: P = sym(Q), p = q, no law */
-        if (row) {
-            for (int j = 0; j < nx; ++j) Pi[(size_t)j * nx + lane] = 0.5f * (Qi[(size_t)j * nx + lane] + Qi[(size_t)lane * nx + j]);
-            a.p[node * nx + lane] = a.q[node * nx + lane];
-        }
-        for (int e = lane; e < nu * nx; e += 32) Ki[e] = 0.f;
-        if (lane < nu) a.k[node * nu + lane] = 0.f;
+        if (row)
+            for (int j = j0; j < j0 + 4 && j < nx; ++j)
+                Pi[(size_t)j * nx + l] = 0.5f * (Qi[(size_t)j * nx + l] + Qi[(size_t)l * nx + j]);
+        if (w == 0 && row) a.p[node * nx + l] = a.q[node * nx + l];
+        for (int e = tid; e < nu * nx; e += nt) Ki[e] = 0.f;
+        if (tid < nu) a.k[node * nu + tid] = 0.f;
         return;
     }
 
-    /* the k loops of the A'T sums are unrolled by 2 at n_x = 32: fully unrolled they spill */
-    constexpr int KK_UNROLL = NXP > 16 ? 2 : NXP;
-    float sxx[NXP], sxu[NUP], suu[NUP], sx = 0.f, su = 0.f;
-#pragma unroll
-    for (int j = 0; j < NXP; ++j) sxx[j] = 0.f;
-#pragma unroll
-    for (int j = 0; j < NUP; ++j) sxu[j] = suu[j] = 0.f;
-
+    float4 sxx = make_float4(0.f, 0.f, 0.f, 0.f), sxu = sxx, suu = sxx;
+    float sx = 0.f, su = 0.f;
     for (int e = c0; e < c1; ++e) {
         const int m = a.child_idx[e];
         const size_t cm = (size_t)t * a.n + m;
-        __syncwarp();   /* the previous child's tiles are no longer read */
-        stage_tile<NXP, NXP, Tiles::SX>(ws->A, a.A + cm * nx * nx, nx, nx, lane);
-        stage_tile<NXP, NUP, Tiles::SU>(ws->B, a.B + cm * nx * nu, nx, nu, lane);
-        /* row `lane` of P_m (symmetric: its column, read coalesced), p_m and c_m */
-        const float *Pm = a.P + cm * nx * nx;
-        float prow[NXP];
+        __syncthreads();   /* the previous child's tiles are no longer read */
+        stage_tile_nt<NXP, NXP, Tiles::SX, 8 * NXP>(ts->A, a.A + cm * nx * nx, nx, nx, tid);
+        stage_tile_nt<NXP, NUP, Tiles::SU, 8 * NXP>(ts->B, a.B + cm * nx * nu, nx, nu, tid);
+        stage_tile_nt<NXP, NXP, Tiles::SX, 8 * NXP>(ts->PS, a.P + cm * nx * nx, nx, nx, tid);
+        if (tid < NXP) ts->cv[tid] = tid < nx ? a.c[cm * nx + tid] : 0.f;
+        __syncthreads();
+        /* T1 = P_m A_m (and T2 = P_m B_m for w < NUP / 4): entries (l, 4w .. 4w + 3) */
+        if (l < NXP) {
+            float4 t1 = make_float4(0.f, 0.f, 0.f, 0.f), t2 = t1;
+            float gl = 0.f;
 #pragma unroll
-        for (int kk = 0; kk < NXP; ++kk) prow[kk] = (row && kk < nx) ? Pm[(size_t)kk * nx + lane] : 0.f;
-        const float cl = row ? a.c[cm * nx + lane] : 0.f;
-        float gl = row ? a.p[cm * nx + lane] : 0.f;
+            for (int k4 = 0; k4 < NXP; k4 += 4) {
+                const float4 p4 = ld4(&ts->PS[l][k4]);
+                const float pk[4] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
-        for (int kk = 0; kk < NXP; ++kk) gl += prow[kk] * __shfl_sync(FULL, cl, kk);
-        if (lane < NXP) ws->g[lane] = gl;
-        __syncwarp();
-        /* T1 = P_m A_m, T2 = P_m B_m: row `lane` */
-        if (lane < NXP) {
-#pragma unroll
-            for (int j = 0; j < NXP; j += 4) {
-                float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-#pragma unroll
-                for (int kk = 0; kk < NXP; ++kk) {
-                    const float4 a4 = ld4(&ws->A[kk][j]);
-                    v0 += prow[kk] * a4.x;
-                    v1 += prow[kk] * a4.y;
-                    v2 += prow[kk] * a4.z;
-                    v3 += prow[kk] * a4.w;
+                for (int s = 0; s < 4; ++s) {
+                    fma4(t1, pk[s], ld4(&ts->A[k4 + s][j0]));
+                    if (w < NWU) fma4(t2, pk[s], ld4(&ts->B[k4 + s][j0]));
+                    if (w == NW - 1) gl += pk[s] * ts->cv[k4 + s];
                 }
-                st4(&ws->T1[lane][j], v0, v1, v2, v3);
             }
-#pragma unroll
-            for (int j = 0; j < NUP; j += 4) {
-                float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-#pragma unroll
-                for (int kk = 0; kk < NXP; ++kk) {
-                    const float4 b4 = ld4(&ws->B[kk][j]);
-                    v0 += prow[kk] * b4.x;
-                    v1 += prow[kk] * b4.y;
-                    v2 += prow[kk] * b4.z;
-                    v3 += prow[kk] * b4.w;
-                }
-                st4(&ws->T2[lane][j], v0, v1, v2, v3);
-            }
+            st4(&ts->T1[l][j0], t1);
+            if (w < NWU) st4(&ts->T2[l][j0], t2);
+            if (w == NW - 1) ts->g[l] = (l < nx ? a.p[cm * nx + l] : 0.f) + gl;
         }
-        __syncwarp();
-        /* S_xx += A' T1, S_xu += A' T2, s_x += A' g (row `lane`); S_uu += B' T2, s_u += B' g (rows < NUP) */
-        if (lane < NXP) {
-#pragma unroll(KK_UNROLL)
+        __syncthreads();
+        /* S_xx += A' T1, S_xu += A' T2, S_uu += B' T2 at (l, 4w ..); s_x += A' g, s_u += B' g (warp NW - 1) */
+        if (l < NXP) {
+#pragma unroll 8
             for (int kk = 0; kk < NXP; ++kk) {
-                const float akl = ws->A[kk][lane];
-#pragma unroll
-                for (int j = 0; j < NXP; j += 4) {
-                    const float4 t4 = ld4(&ws->T1[kk][j]);
-                    sxx[j] += akl * t4.x;
-                    sxx[j + 1] += akl * t4.y;
-                    sxx[j + 2] += akl * t4.z;
-                    sxx[j + 3] += akl * t4.w;
+                const float akl = ts->A[kk][l];
+                fma4(sxx, akl, ld4(&ts->T1[kk][j0]));
+                if (w < NWU) {
+                    const float4 t2 = ld4(&ts->T2[kk][j0]);
+                    fma4(sxu, akl, t2);
+                    if (l < NUP) fma4(suu, ts->B[kk][l], t2);
                 }
-#pragma unroll
-                for (int j = 0; j < NUP; j += 4) {
-                    const float4 t4 = ld4(&ws->T2[kk][j]);
-                    sxu[j] += akl * t4.x;
-                    sxu[j + 1] += akl * t4.y;
-                    sxu[j + 2] += akl * t4.z;
-                    sxu[j + 3] += akl * t4.w;
+                if (w == NW - 1) {
+                    sx += akl * ts->g[kk];
+                    if (l < NUP) su += ts->B[kk][l] * ts->g[kk];
                 }
-                sx += akl * ws->g[kk];
-            }
-        }
-        if (lane < NUP) {
-#pragma unroll(KK_UNROLL)
-            for (int kk = 0; kk < NXP; ++kk) {
-                const float bkl = ws->B[kk][lane];
-#pragma unroll
-                for (int j = 0; j < NUP; j += 4) {
-                    const float4 t4 = ld4(&ws->T2[kk][j]);
-                    suu[j] += bkl * t4.x;
-                    suu[j + 1] += bkl * t4.y;
-                    suu[j + 2] += bkl * t4.z;
-                    suu[j + 3] += bkl * t4.w;
-                }
-                su += bkl * ws->g[kk];
             }
         }
     }
-    __syncwarp();
+    __syncthreads();
 
-    /* the node's own terms: Q_xx (row `lane`), q_x; Q_ux column `lane` into X, H and q_u (rows < nu) */
-    float qux[NUP];
-#pragma unroll
-    for (int b = 0; b < NUP; ++b) {
-        const float mv = (a.M && row && b < nu) ? a.M[node * nu * nx + (size_t)b * nx + lane] : 0.f;
-        qux[b] = (row && b < nu) ? mv + sxu[b] : 0.f;
+    /* the node's own terms: Q_xx (l, 4w ..) in registers, Q_ux into X and QUX, H, q_u, q_x */
+    for (int idx = tid; idx < NUP * Tiles::SX; idx += nt) (&ts->X[0][0])[idx] = 0.f;
+    __syncthreads();
+    float4 qxx = sxx;
+    if (row) {
+        const float *qr = Qi + (size_t)l * nx;
+        qxx.x += j0 < nx ? qr[j0] : 0.f;
+        qxx.y += j0 + 1 < nx ? qr[j0 + 1] : 0.f;
+        qxx.z += j0 + 2 < nx ? qr[j0 + 2] : 0.f;
+        qxx.w += j0 + 3 < nx ? qr[j0 + 3] : 0.f;
     }
+    if (l < NXP && w < NWU) {
+        const float s4[4] = {sxu.x, sxu.y, sxu.z, sxu.w};
+        const float h4[4] = {suu.x, suu.y, suu.z, suu.w};
 #pragma unroll
-    for (int j = 0; j < NXP; ++j) sxx[j] = (row && j < nx) ? Qi[(size_t)lane * nx + j] + sxx[j] : 0.f;
-    const float qx = row ? a.q[node * nx + lane] + sx : 0.f;
-    for (int idx = lane; idx < NUP * Tiles::SX; idx += 32) (&ws->X[0][0])[idx] = 0.f;
-    __syncwarp();
-    if (lane < NXP) {
-#pragma unroll
-        for (int b = 0; b < NUP; ++b) ws->X[b][lane] = qux[b];
-    }
-    if (lane < nu) {
-        const float *Ri = a.R + node * nu * nu;
-#pragma unroll
-        for (int b = 0; b < NUP; ++b) ws->H[lane][b] = b < nu ? Ri[(size_t)lane * nu + b] + suu[b] : 0.f;
-        ws->X[lane][NXP] = a.r[node * nu + lane] + su;
-    }
-    __syncwarp();
-
-    /* Cholesky H = L L' in place (lower triangle), one column at a time across the warp */
-    bool bad = false;
-    for (int j = 0; j < nu; ++j) {
-        const float d = ws->H[j][j];
-        bad = bad || !(d > 0.f) || !isfinite(d);
-        const float ljj = sqrtf(d), il = 1.f / ljj;
-        __syncwarp();
-        if (lane > j && lane < nu) ws->H[lane][j] *= il;
-        if (lane == j) ws->H[j][j] = ljj;
-        __syncwarp();
-        if (lane > j && lane < nu) {
-            const float lij = ws->H[lane][j];
-            for (int b = j + 1; b <= lane; ++b) ws->H[lane][b] -= lij * ws->H[b][j];
+        for (int s = 0; s < 4; ++s) {
+            const int b = j0 + s;
+            const float mv = (a.M && row && b < nu) ? a.M[node * nu * nx + (size_t)b * nx + l] : 0.f;
+            const float v = (row && b < nu) ? mv + s4[s] : 0.f;
+            ts->X[b][l] = v;
+            ts->QUX[b][l] = v;
+            if (l < NUP) ts->H[l][b] = (l < nu && b < nu) ? a.R[node * nu * nu + (size_t)l * nu + b] + h4[s] : 0.f;
         }
-        __syncwarp();
     }
-    if (bad && lane == 0) atomicExch(a.flag, 1);
+    if (w == NW - 1 && l < NXP) {
+        ts->qx[l] = row ? a.q[node * nx + l] + sx : 0.f;
+        if (l < nu) ts->X[l][NXP] = a.r[node * nu + l] + su;
+    }
+    __syncthreads();
 
-    /* [K k] = -H^-1 [Q_ux | q_u]: lane c solves right-hand side c (c = nx is q_u, kept in column NXP) */
-    for (int cidx = lane; cidx <= nx; cidx += 32) {
-        const int col = cidx < nx ? cidx : NXP;
+    /* Cholesky H = L L' by warp 0 in registers: lane l holds row l, columns broadcast by shuffles
+     * (rows and columns past n_u are zero and stay zero) */
+    if (w == 0) {
+        float h[NUP];
+#pragma unroll
+        for (int b = 0; b < NUP; ++b) h[b] = l < NUP ? ts->H[l][b] : 0.f;
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < NUP; ++j) {
+            if (j < nu) {
+                const float d = __shfl_sync(FULL, h[j], j);
+                bad = bad || !(d > 0.f) || !isfinite(d);
+                const float ljj = sqrtf(d), il = 1.f / ljj;
+                if (l == j) h[j] = ljj;
+                else if (l > j) h[j] *= il;
+#pragma unroll
+                for (int b = j + 1; b < NUP; ++b) {
+                    const float lbj = __shfl_sync(FULL, h[j], b);
+                    if (l >= b) h[b] -= h[j] * lbj;
+                }
+            }
+        }
+        if (l < NUP) {
+#pragma unroll
+            for (int b = 0; b < NUP; ++b) ts->H[l][b] = b <= l ? h[b] : 0.f;
+            ts->id[l] = l < nu ? 1.f / h[l] : 0.f;
+        }
+        if (bad && l == 0) atomicExch(a.flag, 1);
+    }
+    __syncthreads();
+
+    /* [K k] = -H^-1 [Q_ux | q_u]: thread c solves right-hand side c (c = nx is q_u, in column NXP);
+     * the zero padding of L and 1/L_bb makes the unguarded substitutions exact past n_u */
+    if (tid <= nx) {
+        const int col = tid < nx ? tid : NXP;
         float y[NUP];
 #pragma unroll
-        for (int b = 0; b < NUP; ++b) y[b] = b < nu ? ws->X[b][col] : 0.f;
+        for (int b = 0; b < NUP; ++b) y[b] = ts->X[b][col];
 #pragma unroll
-        for (int b = 0; b < NUP; ++b)
-            if (b < nu) {
-                float s = y[b];
+        for (int b = 0; b < NUP; ++b) {
+            float s = y[b];
 #pragma unroll
-                for (int e = 0; e < b; ++e) s -= ws->H[b][e] * y[e];
-                y[b] = s / ws->H[b][b];
-            }
-#pragma unroll
-        for (int b = NUP - 1; b >= 0; --b)
-            if (b < nu) {
-                float s = y[b];
-#pragma unroll
-                for (int e = b + 1; e < NUP; ++e)
-                    if (e < nu) s -= ws->H[e][b] * y[e];
-                y[b] = s / ws->H[b][b];
-            }
-#pragma unroll
-        for (int b = 0; b < NUP; ++b)
-            if (b < nu) ws->X[b][col] = -y[b];
-    }
-    __syncwarp();
-
-    /* P = Q_xx + Q_ux' K (row `lane`), p = q_x + Q_ux' k; symmetrised through T1 */
-    float pl = qx;
-    if (lane < NXP) {
-#pragma unroll
-        for (int j = 0; j < NXP; j += 4) {
-            float v0 = sxx[j], v1 = sxx[j + 1], v2 = sxx[j + 2], v3 = sxx[j + 3];
-#pragma unroll
-            for (int b = 0; b < NUP; ++b) {
-                const float4 k4 = ld4(&ws->X[b][j]);
-                v0 += qux[b] * k4.x;
-                v1 += qux[b] * k4.y;
-                v2 += qux[b] * k4.z;
-                v3 += qux[b] * k4.w;
-            }
-            st4(&ws->T1[lane][j], v0, v1, v2, v3);
+            for (int e = 0; e < b; ++e) s -= ts->H[b][e] * y[e];
+            y[b] = s * ts->id[b];
         }
 #pragma unroll
-        for (int b = 0; b < NUP; ++b) pl += qux[b] * ws->X[b][NXP];
+        for (int b = NUP - 1; b >= 0; --b) {
+            float s = y[b];
+#pragma unroll
+            for (int e = b + 1; e < NUP; ++e) s -= ts->H[e][b] * y[e];
+            y[b] = s * ts->id[b];
+        }
+#pragma unroll
+        for (int b = 0; b < NUP; ++b) ts->X[b][col] = -y[b];
     }
-    __syncwarp();
-    if (row) {
-        for (int j = 0; j < nx; ++j) Pi[(size_t)j * nx + lane] = 0.5f * (ws->T1[lane][j] + ws->T1[j][lane]);
-        a.p[node * nx + lane] = pl;
-        for (int b = 0; b < nu; ++b) Ki[(size_t)b * nx + lane] = ws->X[b][lane];
+    __syncthreads();
+
+    /* P = Q_xx + Q_ux' K at (l, 4w ..) into T1; p = q_x + Q_ux' k (warp NW - 1) */
+    if (l < NXP) {
+        float4 pv = qxx;
+        float pl = ts->qx[l];
+#pragma unroll
+        for (int b = 0; b < NUP; ++b) {
+            const float qb = ts->QUX[b][l];
+            fma4(pv, qb, ld4(&ts->X[b][j0]));
+            if (w == NW - 1) pl += qb * ts->X[b][NXP];
+        }
+        st4(&ts->T1[l][j0], pv);
+        if (w == NW - 1 && row) a.p[node * nx + l] = pl;
     }
-    if (lane < nu) a.k[node * nu + lane] = ws->X[lane][NXP];
+    __syncthreads();
+    if (row)
+        for (int j = j0; j < j0 + 4 && j < nx; ++j) Pi[(size_t)j * nx + l] = 0.5f * (ts->T1[l][j] + ts->T1[j][l]);
+    if (row)
+        for (int b = w; b < nu; b += NW) Ki[(size_t)b * nx + l] = ts->X[b][l];
+    if (tid < nu) a.k[node * nu + tid] = ts->X[tid][NXP];
 }
 
 template <int NXP, int NUP>
 __global__ void __launch_bounds__(32 * LQR_WARPS) lqr_forward_kernel(LqrArgs a) {
-    __shared__ __align__(16) float sA[LQR_WARPS][NXP][NXP + 4];
-    __shared__ __align__(16) float sB[LQR_WARPS][NXP][NUP + 4];
     const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
     const long long item = (long long)blockIdx.x * LQR_WARPS + w;
     if (item >= (long long)a.cnt * a.batch) return;
@@ -302,42 +296,42 @@ __global__ void __launch_bounds__(32 * LQR_WARPS) lqr_forward_kernel(LqrArgs a) 
     const int nx = a.nx, nu = a.nu;
     const size_t node = (size_t)t * a.n + m;
     const bool row = lane < nx;
+    const bool leaf = a.child_off[m] == a.child_off[m + 1];
+    /* every row this lane needs, loaded at once: A_m, B_m (row `lane`), K_m (row `lane` < n_u) and
+     * P_m (column `lane` = row, coalesced) */
+    const float *Am = a.A + node * nx * nx + (size_t)lane * nx, *Bm = a.B + node * nx * nu + (size_t)lane * nu;
+    const float *Km = a.K + node * nu * nx + (size_t)lane * nx, *Pm = a.P + node * nx * nx;
+    float arow[NXP], brow[NUP], krow[NXP], prow[NXP];
+#pragma unroll
+    for (int k = 0; k < NXP; ++k) {
+        arow[k] = (m > 0 && row && k < nx) ? __ldg(Am + k) : 0.f;
+        krow[k] = (!leaf && lane < nu && k < nx) ? Km[k] : 0.f;
+        prow[k] = (row && k < nx) ? Pm[(size_t)k * nx + lane] : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < NUP; ++b) brow[b] = (m > 0 && row && b < nu) ? __ldg(Bm + b) : 0.f;
     float xl = 0.f;
     if (m == 0) {
         xl = row ? a.x0[(size_t)t * nx + lane] : 0.f;
     } else {
         const size_t pa = (size_t)t * a.n + a.parent[m];
-        stage_tile<NXP, NXP, NXP + 4>(sA[w], a.A + node * nx * nx, nx, nx, lane);
-        stage_tile<NXP, NUP, NUP + 4>(sB[w], a.B + node * nx * nu, nx, nu, lane);
         const float xp = row ? a.x[pa * nx + lane] : 0.f;
         const float up = lane < nu ? a.u[pa * nu + lane] : 0.f;
-        __syncwarp();
         float v = row ? a.c[node * nx + lane] : 0.f;
-        const int r = lane % NXP;
 #pragma unroll
-        for (int kk = 0; kk < NXP; kk += 4) {
-            const float4 a4 = ld4(&sA[w][r][kk]);
-            v += a4.x * __shfl_sync(FULL, xp, kk) + a4.y * __shfl_sync(FULL, xp, kk + 1) +
-                 a4.z * __shfl_sync(FULL, xp, kk + 2) + a4.w * __shfl_sync(FULL, xp, kk + 3);
-        }
+        for (int k = 0; k < NXP; ++k) v += arow[k] * __shfl_sync(FULL, xp, k);
 #pragma unroll
-        for (int b = 0; b < NUP; b += 4) {
-            const float4 b4 = ld4(&sB[w][r][b]);
-            v += b4.x * __shfl_sync(FULL, up, b) + b4.y * __shfl_sync(FULL, up, b + 1) +
-                 b4.z * __shfl_sync(FULL, up, b + 2) + b4.w * __shfl_sync(FULL, up, b + 3);
-        }
+        for (int b = 0; b < NUP; ++b) v += brow[b] * __shfl_sync(FULL, up, b);
         xl = row ? v : 0.f;
     }
-    /* u = K x + k (rows < nu; 0 at leaves), lam = P x + p */
-    const bool leaf = a.child_off[m] == a.child_off[m + 1];
-    float ul = 0.f;
-    const float *Km = a.K + node * nu * nx, *Pm = a.P + node * nx * nx;
-    if (!leaf && lane < nu) ul = a.k[node * nu + lane];
+    /* u = K x + k (rows < n_u; 0 at leaves), lam = P x + p */
+    float ul = (!leaf && lane < nu) ? a.k[node * nu + lane] : 0.f;
     float ll = row ? a.p[node * nx + lane] : 0.f;
-    for (int j = 0; j < nx; ++j) {
+#pragma unroll
+    for (int j = 0; j < NXP; ++j) {
         const float xj = __shfl_sync(FULL, xl, j);
-        if (!leaf && lane < nu) ul += Km[(size_t)lane * nx + j] * xj;
-        if (row) ll += Pm[(size_t)j * nx + lane] * xj;
+        ul += krow[j] * xj;
+        ll += prow[j] * xj;
     }
     if (row) {
         a.x[node * nx + lane] = xl;
@@ -347,18 +341,24 @@ __global__ void __launch_bounds__(32 * LQR_WARPS) lqr_forward_kernel(LqrArgs a) 
 }
 
 template <int NXP, int NUP>
-size_t backward_smem() { return LQR_WARPS * sizeof(LqrTiles<NXP, NUP>); }
+size_t backward_smem() { return sizeof(LqrTiles<NXP, NUP>); }
 
 using LqrKernel = void (*)(LqrArgs);
 struct Instance {
-    LqrKernel bwd, fwd;
+    LqrKernel bwd, bwd_wide, fwd;   /* bwd_wide: two blocks per SM, for stages wider than the GPU */
     size_t smem;
+    int bwd_threads;   /* one block per node: NXP / 4 warps */
 };
 
 Instance instance(int nx, int nu) {
-    if (nx <= 8 && nu <= 4) return {lqr_backward_kernel<8, 4>, lqr_forward_kernel<8, 4>, backward_smem<8, 4>()};
-    if (nx <= 16 && nu <= 8) return {lqr_backward_kernel<16, 8>, lqr_forward_kernel<16, 8>, backward_smem<16, 8>()};
-    return {lqr_backward_kernel<32, 16>, lqr_forward_kernel<32, 16>, backward_smem<32, 16>()};
+    if (nx <= 8 && nu <= 4)
+        return {lqr_backward_kernel<8, 4, 1>, lqr_backward_kernel<8, 4, 4>, lqr_forward_kernel<8, 4>,
+                backward_smem<8, 4>(), 64};
+    if (nx <= 16 && nu <= 8)
+        return {lqr_backward_kernel<16, 8, 1>, lqr_backward_kernel<16, 8, 3>, lqr_forward_kernel<16, 8>,
+                backward_smem<16, 8>(), 128};
+    return {lqr_backward_kernel<32, 16, 1>, lqr_backward_kernel<32, 16, 2>, lqr_forward_kernel<32, 16>,
+            backward_smem<32, 16>(), 256};
 }
 
 }  // namespace
@@ -367,6 +367,7 @@ struct bmpc_lqr {
     int n = 0, nx = 0, nu = 0, batch = 0;
     std::vector<int> sstart;   /* stage s holds nodes [sstart[s], sstart[s + 1]) */
     int32_t *d_parent = nullptr, *d_child_off = nullptr, *d_child_idx = nullptr, *d_flag = nullptr;
+    int sm_count = 148;
     cudaStream_t stream = nullptr;
     Instance inst{};
 };
@@ -409,8 +410,13 @@ int bmpc_lqr_create(int32_t n, const int32_t *parent, int32_t nx, int32_t nu, in
          cudaMemcpy(h->d_child_off, off.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(h->d_child_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(h->d_flag, 0, sizeof(int32_t)) == cudaSuccess;
+    int dev = 0;
+    ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(h->inst.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->inst.smem) ==
                    cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(h->inst.bwd_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)h->inst.smem) == cudaSuccess;
     if (!ok) {
         bmpc_lqr_destroy(h);
         return BMPC_ERR_CUDA;
@@ -431,7 +437,9 @@ int bmpc_lqr_solve(bmpc_lqr *h, const float *Q, const float *M, const float *R, 
     for (int s = S - 1; s >= 0; --s) {
         a.s0 = h->sstart[s];
         a.cnt = h->sstart[s + 1] - h->sstart[s];
-        h->inst.bwd<<<grid(a.cnt), 32 * LQR_WARPS, h->inst.smem, h->stream>>>(a);
+        const long long blocks = (long long)a.cnt * h->batch;
+        (blocks > h->sm_count ? h->inst.bwd_wide : h->inst.bwd)<<<(unsigned)blocks, h->inst.bwd_threads, h->inst.smem,
+                                                                  h->stream>>>(a);
     }
     for (int s = 0; s < S; ++s) {
         a.s0 = h->sstart[s];
