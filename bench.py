@@ -613,12 +613,14 @@ def run_lqr(args):
                 "dtype": "f32", "data": "synthetic",
                 "config": {"case": kind, "masses": M, "nx": d["nx"], "nu": d["nu"], "N": N, "Nr": Nr, "nd": 2 if Nr else 1,
                            "paths": 2 ** Nr, "nodes": int(len(d["parent"])), "batch": batch,
-                           "launches_per_solve": 2 * h.stages, "steps": args.steps, "warmup": args.warmup},
+                           "schedule": "one block per problem" if h.fused else "a launch per stage and sweep",
+                           "launches_per_solve": 1 if h.fused else 2 * h.stages, "steps": args.steps,
+                           "warmup": args.warmup},
                 "roofline": {"alu": {"achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
                                      "flops_per_solve": flops},
                              "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                      "frac": gbs / hbm_peak if hbm_peak else None, "bytes_per_solve": byts},
-                             "launch": {"us_per_launch": us / (2 * h.stages)}}}
+                             "launch": {"us_per_launch": us / (1 if h.fused else 2 * h.stages)}}}
         print(json.dumps(line), flush=True)
         h.close()
 

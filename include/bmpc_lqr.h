@@ -44,8 +44,8 @@ extern "C" {
 typedef struct bmpc_lqr bmpc_lqr;
 
 /* Validates the tree (n >= 1, parent[0] = -1, 0 <= parent[i] < i, stages nondecreasing in i) and
- * the sizes (1 <= nx <= 32, 1 <= nu <= 16, batch >= 1), copies the parent array, builds the stage
- * and child tables on the device and binds the handle to `stream` (a cudaStream_t, NULL = the
+ * the sizes (1 <= nx <= 32, 1 <= nu <= 16, batch >= 1), copies the tree into per-node tables on the
+ * device (child range, first child, parent) and binds the handle to `stream` (a cudaStream_t, NULL = the
  * default stream).  0 on success; BMPC_ERR_INVALID (-1) on a bad tree or size, BMPC_ERR_CUDA (-2)
  * if a device allocation or copy fails. */
 int bmpc_lqr_create(int32_t n, const int32_t *parent, int32_t nx, int32_t nu, int32_t batch, void *stream,
@@ -66,8 +66,17 @@ int bmpc_lqr_solve(bmpc_lqr *h, const float *Q, const float *M, const float *R, 
  * last call met a non-positive pivot (the record is cleared), or BMPC_ERR_CUDA. */
 int bmpc_lqr_status(bmpc_lqr *h);
 
-/* Launches per solve (two per stage) and the stage count, for timing and graph sizing. */
+/* The stage count S of the tree (a solve makes 2 S launches on the per-stage schedule, 1 fused). */
 int bmpc_lqr_stages(const bmpc_lqr *h);
+
+/* The launch schedule of later solves: 0 (default) chooses by a cost model of the tree's stage
+ * widths and the batch size; 1: one launch per stage and sweep, every node of a stage at once (wide
+ * trees); 2: one block per problem walking all of its stages, one launch per solve (narrow trees,
+ * batches of single paths).  Both compute the same arithmetic in the same order, so the results
+ * are bitwise equal.  BMPC_ERR_INVALID on a NULL handle or another value.  bmpc_lqr_fused returns 1
+ * when solves run fused, 0 when per stage. */
+int bmpc_lqr_set_schedule(bmpc_lqr *h, int32_t schedule);
+int bmpc_lqr_fused(const bmpc_lqr *h);
 
 void bmpc_lqr_destroy(bmpc_lqr *h);
 

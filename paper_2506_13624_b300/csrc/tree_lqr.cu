@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -33,7 +34,8 @@ constexpr unsigned FULL = 0xffffffffu;
 struct LqrArgs {
     const float *Q, *M, *R, *q, *r, *A, *B, *c, *x0;
     float *K, *k, *P, *p, *x, *u, *lam;
-    const int32_t *parent, *child_off, *child_idx;
+    const int32_t *child_idx;
+    const int4 *node4;   /* per node: first and end index into child_idx, first child (or -1), parent */
     int32_t *flag;
     int n, nx, nu, batch;
     int s0, cnt;   /* first node of the stage and its node count */
@@ -97,24 +99,23 @@ __device__ __forceinline__ void fma4(float4 &acc, float s, const float4 v) {
     acc.w += s * v.w;
 }
 
-/* Backward step of one node per block: NXP / 4 warps; thread (lane l, warp w) owns entries
- * (l, 4w .. 4w + 3) of the n_x-column products and, for w < NUP / 4, of the n_u-column ones. */
-template <int NXP, int NUP, int MINB>
-__global__ void __launch_bounds__(8 * NXP, MINB) lqr_backward_kernel(LqrArgs a) {
+/* Backward step of node i of problem t by the whole block: NXP / 4 warps; thread (lane l, warp w)
+ * owns entries (l, 4w .. 4w + 3) of the n_x-column products and, for w < NUP / 4, of the n_u-column
+ * ones.  Every thread of the block calls it with the same (t, i). */
+template <int NXP, int NUP>
+__device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i) {
     constexpr int NW = NXP / 4, NWU = NUP / 4;
     extern __shared__ __align__(16) float lqr_smem[];
     using Tiles = LqrTiles<NXP, NUP>;
     Tiles *ts = reinterpret_cast<Tiles *>(lqr_smem);
     const int tid = threadIdx.x, nt = blockDim.x, l = tid & 31, w = tid >> 5;
     const int j0 = 4 * w;   /* this thread's column group */
-    const long long item = blockIdx.x;
-    const int t = (int)(item / a.cnt);
-    const int i = a.s0 + (int)(item % a.cnt);
     const int nx = a.nx, nu = a.nu;
     const size_t node = (size_t)t * a.n + i;
     const float *Qi = a.Q + node * nx * nx;
     float *Pi = a.P + node * nx * nx, *Ki = a.K + node * nu * nx;
-    const int c0 = a.child_off[i], c1 = a.child_off[i + 1];
+    const int4 nd = a.node4[i];   /* one load gives the child range and the first child */
+    const int c0 = nd.x, c1 = nd.y;
     const bool row = l < nx && l < NXP;
 
     if (c0 == c1) {   /* leaf: P = sym(Q), p = q, no law */
@@ -127,10 +128,23 @@ __global__ void __launch_bounds__(8 * NXP, MINB) lqr_backward_kernel(LqrArgs a) 
         return;
     }
 
+    /* the node's own data, loaded now so that its latency hides behind the children's products:
+     * row l of Q at columns 4w .. 4w + 3, M and R at (4w .., l), q, r */
+    float qr4[4], mv4[4], rv4[4];
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) {
+        const int b = j0 + s2;
+        qr4[s2] = (row && b < nx) ? Qi[(size_t)l * nx + b] : 0.f;
+        mv4[s2] = (a.M && w < NWU && row && b < nu) ? a.M[node * nu * nx + (size_t)b * nx + l] : 0.f;
+        rv4[s2] = (w < NWU && l < nu && b < nu) ? a.R[node * nu * nu + (size_t)l * nu + b] : 0.f;
+    }
+    const float qv = (w == NW - 1 && row) ? a.q[node * nx + l] : 0.f;
+    const float rv = (w == NW - 1 && l < nu) ? a.r[node * nu + l] : 0.f;
+
     float4 sxx = make_float4(0.f, 0.f, 0.f, 0.f), sxu = sxx, suu = sxx;
     float sx = 0.f, su = 0.f;
     for (int e = c0; e < c1; ++e) {
-        const int m = a.child_idx[e];
+        const int m = e == c0 ? nd.z : a.child_idx[e];
         const size_t cm = (size_t)t * a.n + m;
         __syncthreads();   /* the previous child's tiles are no longer read */
         stage_tile_nt<NXP, NXP, Tiles::SX, 8 * NXP>(ts->A, a.A + cm * nx * nx, nx, nx, tid);
@@ -182,29 +196,25 @@ __global__ void __launch_bounds__(8 * NXP, MINB) lqr_backward_kernel(LqrArgs a) 
     for (int idx = tid; idx < NUP * Tiles::SX; idx += nt) (&ts->X[0][0])[idx] = 0.f;
     __syncthreads();
     float4 qxx = sxx;
-    if (row) {
-        const float *qr = Qi + (size_t)l * nx;
-        qxx.x += j0 < nx ? qr[j0] : 0.f;
-        qxx.y += j0 + 1 < nx ? qr[j0 + 1] : 0.f;
-        qxx.z += j0 + 2 < nx ? qr[j0 + 2] : 0.f;
-        qxx.w += j0 + 3 < nx ? qr[j0 + 3] : 0.f;
-    }
+    qxx.x += qr4[0];
+    qxx.y += qr4[1];
+    qxx.z += qr4[2];
+    qxx.w += qr4[3];
     if (l < NXP && w < NWU) {
         const float s4[4] = {sxu.x, sxu.y, sxu.z, sxu.w};
         const float h4[4] = {suu.x, suu.y, suu.z, suu.w};
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int b = j0 + s;
-            const float mv = (a.M && row && b < nu) ? a.M[node * nu * nx + (size_t)b * nx + l] : 0.f;
-            const float v = (row && b < nu) ? mv + s4[s] : 0.f;
+            const float v = (row && b < nu) ? mv4[s] + s4[s] : 0.f;
             ts->X[b][l] = v;
             ts->QUX[b][l] = v;
-            if (l < NUP) ts->H[l][b] = (l < nu && b < nu) ? a.R[node * nu * nu + (size_t)l * nu + b] + h4[s] : 0.f;
+            if (l < NUP) ts->H[l][b] = (l < nu && b < nu) ? rv4[s] + h4[s] : 0.f;
         }
     }
     if (w == NW - 1 && l < NXP) {
-        ts->qx[l] = row ? a.q[node * nx + l] + sx : 0.f;
-        if (l < nu) ts->X[l][NXP] = a.r[node * nu + l] + su;
+        ts->qx[l] = row ? qv + sx : 0.f;
+        if (l < nu) ts->X[l][NXP] = rv + su;
     }
     __syncthreads();
 
@@ -286,17 +296,21 @@ __global__ void __launch_bounds__(8 * NXP, MINB) lqr_backward_kernel(LqrArgs a) 
     if (tid < nu) a.k[node * nu + tid] = ts->X[tid][NXP];
 }
 
+/* One backward launch per stage: block b is node s0 + b % cnt of problem b / cnt. */
+template <int NXP, int NUP, int MINB>
+__global__ void __launch_bounds__(8 * NXP, MINB) lqr_backward_kernel(LqrArgs a) {
+    const long long item = blockIdx.x;
+    backward_node<NXP, NUP>(a, (int)(item / a.cnt), a.s0 + (int)(item % a.cnt));
+}
+
+/* Forward step of node m of problem t by one whole warp (lane j: row j). */
 template <int NXP, int NUP>
-__global__ void __launch_bounds__(32 * LQR_WARPS) lqr_forward_kernel(LqrArgs a) {
-    const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
-    const long long item = (long long)blockIdx.x * LQR_WARPS + w;
-    if (item >= (long long)a.cnt * a.batch) return;
-    const int t = (int)(item / a.cnt);
-    const int m = a.s0 + (int)(item % a.cnt);
+__device__ __forceinline__ void forward_node(const LqrArgs &a, int t, int m, int lane) {
     const int nx = a.nx, nu = a.nu;
     const size_t node = (size_t)t * a.n + m;
     const bool row = lane < nx;
-    const bool leaf = a.child_off[m] == a.child_off[m + 1];
+    const int4 nd = a.node4[m];
+    const bool leaf = nd.x == nd.y;
     /* every row this lane needs, loaded at once: A_m, B_m (row `lane`), K_m (row `lane` < n_u) and
      * P_m (column `lane` = row, coalesced) */
     const float *Am = a.A + node * nx * nx + (size_t)lane * nx, *Bm = a.B + node * nx * nu + (size_t)lane * nu;
@@ -314,7 +328,7 @@ __global__ void __launch_bounds__(32 * LQR_WARPS) lqr_forward_kernel(LqrArgs a) 
     if (m == 0) {
         xl = row ? a.x0[(size_t)t * nx + lane] : 0.f;
     } else {
-        const size_t pa = (size_t)t * a.n + a.parent[m];
+        const size_t pa = (size_t)t * a.n + nd.w;
         const float xp = row ? a.x[pa * nx + lane] : 0.f;
         const float up = lane < nu ? a.u[pa * nu + lane] : 0.f;
         float v = row ? a.c[node * nx + lane] : 0.f;
@@ -340,12 +354,43 @@ __global__ void __launch_bounds__(32 * LQR_WARPS) lqr_forward_kernel(LqrArgs a) 
     if (lane < nu) a.u[node * nu + lane] = ul;
 }
 
+/* One forward launch per stage: warp w of block b is node s0 + item % cnt of problem item / cnt,
+ * item = 4b + w. */
+template <int NXP, int NUP>
+__global__ void __launch_bounds__(32 * LQR_WARPS) lqr_forward_kernel(LqrArgs a) {
+    const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const long long item = (long long)blockIdx.x * LQR_WARPS + w;
+    if (item >= (long long)a.cnt * a.batch) return;
+    forward_node<NXP, NUP>(a, (int)(item / a.cnt), a.s0 + (int)(item % a.cnt), lane);
+}
+
+/* The whole solve of problem t = blockIdx.x in one block: the backward steps of all nodes, stage by
+ * stage from the leaves (one node at a time, the block on each), then the forward steps (the warps
+ * sharing each stage's nodes).  No block waits on another: problems are independent.  For trees
+ * whose stages are narrow, where the per-stage launches would leave the GPU idle between them. */
+template <int NXP, int NUP>
+__global__ void __launch_bounds__(8 * NXP) lqr_fused_kernel(LqrArgs a, const int32_t *sstart, int S) {
+    constexpr int NW = NXP / 4;
+    const int t = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int s = S - 1; s >= 0; --s)
+        for (int i = sstart[s]; i < sstart[s + 1]; ++i) {
+            backward_node<NXP, NUP>(a, t, i);
+            __syncthreads();   /* the node's P, p reach the parent's step; the tiles are free again */
+        }
+    for (int s = 0; s < S; ++s) {
+        for (int i = sstart[s] + w; i < sstart[s + 1]; i += NW) forward_node<NXP, NUP>(a, t, i, lane);
+        __syncthreads();
+    }
+}
+
 template <int NXP, int NUP>
 size_t backward_smem() { return sizeof(LqrTiles<NXP, NUP>); }
 
 using LqrKernel = void (*)(LqrArgs);
+using FusedKernel = void (*)(LqrArgs, const int32_t *, int);
 struct Instance {
     LqrKernel bwd, bwd_wide, fwd;   /* bwd_wide: two blocks per SM, for stages wider than the GPU */
+    FusedKernel fused;
     size_t smem;
     int bwd_threads;   /* one block per node: NXP / 4 warps */
 };
@@ -353,12 +398,12 @@ struct Instance {
 Instance instance(int nx, int nu) {
     if (nx <= 8 && nu <= 4)
         return {lqr_backward_kernel<8, 4, 1>, lqr_backward_kernel<8, 4, 4>, lqr_forward_kernel<8, 4>,
-                backward_smem<8, 4>(), 64};
+                lqr_fused_kernel<8, 4>, backward_smem<8, 4>(), 64};
     if (nx <= 16 && nu <= 8)
         return {lqr_backward_kernel<16, 8, 1>, lqr_backward_kernel<16, 8, 3>, lqr_forward_kernel<16, 8>,
-                backward_smem<16, 8>(), 128};
+                lqr_fused_kernel<16, 8>, backward_smem<16, 8>(), 128};
     return {lqr_backward_kernel<32, 16, 1>, lqr_backward_kernel<32, 16, 2>, lqr_forward_kernel<32, 16>,
-            backward_smem<32, 16>(), 256};
+            lqr_fused_kernel<32, 16>, backward_smem<32, 16>(), 256};
 }
 
 }  // namespace
@@ -366,11 +411,28 @@ Instance instance(int nx, int nu) {
 struct bmpc_lqr {
     int n = 0, nx = 0, nu = 0, batch = 0;
     std::vector<int> sstart;   /* stage s holds nodes [sstart[s], sstart[s + 1]) */
-    int32_t *d_parent = nullptr, *d_child_off = nullptr, *d_child_idx = nullptr, *d_flag = nullptr;
+    int32_t *d_child_idx = nullptr, *d_flag = nullptr, *d_sstart = nullptr;
+    int4 *d_node4 = nullptr;
+    int schedule = 0;   /* 0: by the cost model, 1: a launch per stage and sweep, 2: one block per problem */
     int sm_count = 148;
     cudaStream_t stream = nullptr;
     Instance inst{};
 };
+
+namespace {
+/* The schedule: per-stage launches expose every node of a stage at once; one block per problem saves
+ * the launches but walks each tree's nodes one after another.  Cost model in node-step units, two
+ * blocks resident per SM, a launch worth half a node step:
+ *   per stage:  sum_s (ceil(width_s * batch / (2 SMs)) + 1/2),   fused:  ceil(batch / (2 SMs)) * n. */
+bool fused_schedule(const bmpc_lqr *h) {
+    if (h->schedule) return h->schedule == 2;
+    const double slots = 2.0 * h->sm_count;
+    double staged = 0.0;
+    for (size_t s = 0; s + 1 < h->sstart.size(); ++s)
+        staged += std::ceil((double)(h->sstart[s + 1] - h->sstart[s]) * h->batch / slots) + 0.5;
+    return std::ceil(h->batch / slots) * h->n <= staged;
+}
+}  // namespace
 
 extern "C" {
 
@@ -402,12 +464,15 @@ int bmpc_lqr_create(int32_t n, const int32_t *parent, int32_t nx, int32_t nu, in
     for (int i = 0; i < n; ++i) off[i + 1] = off[i] + nchild[i];
     for (int i = 1; i < n; ++i) idx[off[parent[i]] + fill[parent[i]]++] = i;   /* ascending child ids */
     h->inst = instance(nx, nu);
-    bool ok = cudaMalloc(&h->d_parent, sizeof(int32_t) * n) == cudaSuccess &&
-              cudaMalloc(&h->d_child_off, sizeof(int32_t) * (n + 1)) == cudaSuccess &&
+    std::vector<int4> node4(n);
+    for (int i = 0; i < n; ++i) node4[i] = make_int4(off[i], off[i + 1], nchild[i] ? idx[off[i]] : -1, parent[i]);
+    bool ok = cudaMalloc(&h->d_node4, sizeof(int4) * n) == cudaSuccess &&
+              cudaMalloc(&h->d_sstart, sizeof(int32_t) * h->sstart.size()) == cudaSuccess &&
               cudaMalloc(&h->d_child_idx, sizeof(int32_t) * idx.size()) == cudaSuccess &&
               cudaMalloc(&h->d_flag, sizeof(int32_t)) == cudaSuccess;
-    ok = ok && cudaMemcpy(h->d_parent, parent, sizeof(int32_t) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(h->d_child_off, off.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+    ok = ok && cudaMemcpy(h->d_node4, node4.data(), sizeof(int4) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(h->d_sstart, h->sstart.data(), sizeof(int32_t) * h->sstart.size(), cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
          cudaMemcpy(h->d_child_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(h->d_flag, 0, sizeof(int32_t)) == cudaSuccess;
     int dev = 0;
@@ -417,6 +482,8 @@ int bmpc_lqr_create(int32_t n, const int32_t *parent, int32_t nx, int32_t nu, in
                    cudaSuccess;
     ok = ok && cudaFuncSetAttribute(h->inst.bwd_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)h->inst.smem) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(h->inst.fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->inst.smem) ==
+                   cudaSuccess;
     if (!ok) {
         bmpc_lqr_destroy(h);
         return BMPC_ERR_CUDA;
@@ -430,9 +497,13 @@ int bmpc_lqr_solve(bmpc_lqr *h, const float *Q, const float *M, const float *R, 
                    float *p, float *x, float *u, float *lam) {
     if (!h || !Q || !R || !q || !r || !A || !B || !c || !x0 || !K || !k || !P || !p || !x || !u || !lam)
         return BMPC_ERR_INVALID;
-    LqrArgs a{Q, M, R, q, r, A, B, c, x0, K, k, P, p, x, u, lam, h->d_parent, h->d_child_off, h->d_child_idx,
+    LqrArgs a{Q, M, R, q, r, A, B, c, x0, K, k, P, p, x, u, lam, h->d_child_idx, h->d_node4,
               h->d_flag, h->n, h->nx, h->nu, h->batch, 0, 0};
     const int S = (int)h->sstart.size() - 1;
+    if (fused_schedule(h)) {
+        h->inst.fused<<<(unsigned)h->batch, h->inst.bwd_threads, h->inst.smem, h->stream>>>(a, h->d_sstart, S);
+        return cudaGetLastError() == cudaSuccess ? BMPC_OK : BMPC_ERR_CUDA;
+    }
     auto grid = [&](int cnt) { return (unsigned)(((long long)cnt * h->batch + LQR_WARPS - 1) / LQR_WARPS); };
     for (int s = S - 1; s >= 0; --s) {
         a.s0 = h->sstart[s];
@@ -461,10 +532,18 @@ int bmpc_lqr_status(bmpc_lqr *h) {
 
 int bmpc_lqr_stages(const bmpc_lqr *h) { return h ? (int)h->sstart.size() - 1 : BMPC_ERR_INVALID; }
 
+int bmpc_lqr_set_schedule(bmpc_lqr *h, int32_t schedule) {
+    if (!h || schedule < 0 || schedule > 2) return BMPC_ERR_INVALID;
+    h->schedule = schedule;
+    return BMPC_OK;
+}
+
+int bmpc_lqr_fused(const bmpc_lqr *h) { return h ? (int)fused_schedule(h) : BMPC_ERR_INVALID; }
+
 void bmpc_lqr_destroy(bmpc_lqr *h) {
     if (!h) return;
-    cudaFree(h->d_parent);
-    cudaFree(h->d_child_off);
+    cudaFree(h->d_node4);
+    cudaFree(h->d_sstart);
     cudaFree(h->d_child_idx);
     cudaFree(h->d_flag);
     delete h;

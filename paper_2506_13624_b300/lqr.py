@@ -24,6 +24,8 @@ def _lib():
         L.bmpc_lqr_solve.argtypes = [C.c_void_p] + [C.c_void_p] * 16
         L.bmpc_lqr_status.argtypes = [C.c_void_p]
         L.bmpc_lqr_stages.argtypes = [C.c_void_p]
+        L.bmpc_lqr_set_schedule.argtypes = [C.c_void_p, C.c_int32]
+        L.bmpc_lqr_fused.argtypes = [C.c_void_p]
         L.bmpc_lqr_destroy.argtypes = [C.c_void_p]
         L.bmpc_lqr_destroy.restype = None
         _done = True
@@ -38,7 +40,7 @@ class TreeLQR:
     """A batch of `batch` tree LQR problems on one tree (parent array in level order), n_x <= 32,
     n_u <= 16, bound to a CUDA stream (default: torch's current stream)."""
 
-    def __init__(self, parent, nx: int, nu: int, batch: int = 1, stream=None):
+    def __init__(self, parent, nx: int, nu: int, batch: int = 1, stream=None, schedule: int = 0):
         import torch
         self.torch = torch
         self.parent = np.ascontiguousarray(parent, dtype=np.int32)
@@ -49,6 +51,7 @@ class TreeLQR:
                                            self.nu, self.batch, C.c_void_p(self.stream.cuda_stream), C.byref(h)),
                     "bmpc_lqr_create")
         self.handle = h
+        bmpc._check(_lib().bmpc_lqr_set_schedule(h, int(schedule)), "bmpc_lqr_set_schedule")
         dev = torch.device("cuda", torch.cuda.current_device())
         b, n, nx, nu = self.batch, self.n, self.nx, self.nu
         z = lambda *s: torch.zeros(s, dtype=torch.float32, device=dev)
@@ -58,6 +61,11 @@ class TreeLQR:
     @property
     def stages(self) -> int:
         return int(_lib().bmpc_lqr_stages(self.handle))
+
+    @property
+    def fused(self) -> bool:
+        """True when solves run as one block per problem (one launch), False when per stage."""
+        return bool(_lib().bmpc_lqr_fused(self.handle))
 
     def solve(self, Q, R, q, r, A, B, c, x0, M=None, check=True):
         """Queues one solve on the handle's stream; returns the output tensors (K, k, P, p, x, u, lam).

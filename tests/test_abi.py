@@ -43,7 +43,8 @@ def test_library_exports_every_tree_lqr_symbol():
     src = open(os.path.join(ROOT, "include", "bmpc_lqr.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = set(re.findall(r"\b(bmpc_lqr_[a-z_]+)\s*\(", src))
-    assert names == {"bmpc_lqr_create", "bmpc_lqr_solve", "bmpc_lqr_status", "bmpc_lqr_stages", "bmpc_lqr_destroy"}
+    assert names == {"bmpc_lqr_create", "bmpc_lqr_solve", "bmpc_lqr_status", "bmpc_lqr_stages", "bmpc_lqr_destroy",
+                     "bmpc_lqr_set_schedule", "bmpc_lqr_fused"}
     L = bmpc.lib()
     for name in names:
         assert hasattr(L, name), name

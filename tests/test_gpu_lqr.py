@@ -59,9 +59,9 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a, np.float32), device="cuda")
 
 
-def _solve(parent, nx, nu, Q, R, q, r, A, B, c, x0, M=None):
+def _solve(parent, nx, nu, Q, R, q, r, A, B, c, x0, M=None, schedule=0):
     from paper_2506_13624_b300 import lqr
-    h = lqr.TreeLQR(parent, nx, nu, batch=Q.shape[0])
+    h = lqr.TreeLQR(parent, nx, nu, batch=Q.shape[0], schedule=schedule)
     out = h.solve(_dev(Q), _dev(R), _dev(q), _dev(r), _dev(A), _dev(B), _dev(c), _dev(x0),
                   M=None if M is None else _dev(M))
     res = {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
@@ -76,15 +76,17 @@ def _close(got, want, what):
     return d
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
 @pytest.mark.parametrize("nx,nu", [(4, 2), (7, 3), (10, 4), (16, 8), (30, 14), (32, 16)])
-def test_matches_the_oracle_tree_recursion(nx, nu):
+def test_matches_the_oracle_tree_recursion(nx, nu, schedule):
     """Random ragged trees, per-edge A_m, B_m, c_m, cross terms M, a batch of three problems: every
-    block equal to the oracle's (dx_0 = 0 there, so x0 = 0 here)."""
+    block equal to the oracle's (dx_0 = 0 there, so x0 = 0 here), with a launch per stage and with
+    one block per problem."""
     rng = np.random.default_rng(500 + nx)
     parent = _tree(rng, 40)
     batch = 3
     leaf, Q, M, R, q, r, A, B, c = _random_data(rng, parent, nx, nu, batch)
-    got = _solve(parent, nx, nu, Q, R, q, r, A, B, c, np.zeros((batch, nx)), M=M)
+    got = _solve(parent, nx, nu, Q, R, q, r, A, B, c, np.zeros((batch, nx)), M=M, schedule=schedule)
     worst = 0.0
     for t in range(batch):
         K, k, P, pv, dx, du, lam = oracle.tree_lqr(parent, Q[t], M[t], R[t], q[t], r[t], A[t], B[t], c[t], edge=True)
@@ -198,3 +200,16 @@ def test_non_positive_definite_h_is_reported_and_cleared():
     h.solve(*args, check=False)
     assert int(lqr._lib().bmpc_lqr_status(h.handle)) == bmpc.OK
     h.close()
+
+
+@pytest.mark.parametrize("nx,nu", [(10, 4), (30, 14)])
+def test_schedules_agree_bitwise(nx, nu):
+    """The two launch schedules run the same node steps: identical bits."""
+    rng = np.random.default_rng(700 + nx)
+    parent = _tree(rng, 30)
+    leaf, Q, M, R, q, r, A, B, c = _random_data(rng, parent, nx, nu, 2)
+    x0 = rng.standard_normal((2, nx))
+    a = _solve(parent, nx, nu, Q, R, q, r, A, B, c, x0, M=M, schedule=1)
+    b = _solve(parent, nx, nu, Q, R, q, r, A, B, c, x0, M=M, schedule=2)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
