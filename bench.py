@@ -586,6 +586,10 @@ def run_lqr(args):
     cases = ([("tree", 15, 40, nr, 1) for nr in (1, 3, 5, 7, 9)]
              + [("batch", 5, 80, 0, b) for b in (1, 16, 64, 256, 1024)]
              + [("single", 15, N, 0, 1) for N in (20, 40, 60, 80, 100)])
+    if args.lqr_only:   # e.g. "single:100" (horizon), "tree:9" (N_r), "batch:1024" (batch size)
+        kind, val = args.lqr_only.split(":")
+        key = {"single": 2, "tree": 3, "batch": 4}[kind]
+        cases = [c for c in cases if c[0] == kind and c[key] == int(val)]
     for kind, M, N, Nr, batch in cases:
         d = scenes.mass_spring_chain(0, M=M, N=N, Nr=Nr, batch=batch)
         dev = lambda a: torch.tensor(np.ascontiguousarray(a, np.float32), device="cuda")
@@ -650,6 +654,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--lqr", action="store_true",
                     help="the general-size tree LQR at the sizes of Sec. V-A (one JSON line per case)")
+    ap.add_argument("--lqr-only", default="", metavar="CASE:VALUE",
+                    help="one tree LQR case: single:N, tree:N_r or batch:B")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4, help="oracle problems per worker per reference step")

@@ -256,19 +256,19 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i) {
         float y[NUP];
 #pragma unroll
         for (int b = 0; b < NUP; ++b) y[b] = ts->X[b][col];
+        /* column-oriented substitutions: each step scales one entry and updates the rest
+         * independently, so the dependent chain is n_u steps long, not n_u^2 / 2 */
 #pragma unroll
-        for (int b = 0; b < NUP; ++b) {
-            float s = y[b];
+        for (int b = 0; b < NUP; ++b) {   /* L y = x */
+            y[b] *= ts->id[b];
 #pragma unroll
-            for (int e = 0; e < b; ++e) s -= ts->H[b][e] * y[e];
-            y[b] = s * ts->id[b];
+            for (int e = b + 1; e < NUP; ++e) y[e] -= ts->H[e][b] * y[b];
         }
 #pragma unroll
-        for (int b = NUP - 1; b >= 0; --b) {
-            float s = y[b];
+        for (int b = NUP - 1; b >= 0; --b) {   /* L' z = y */
+            y[b] *= ts->id[b];
 #pragma unroll
-            for (int e = b + 1; e < NUP; ++e) s -= ts->H[e][b] * y[e];
-            y[b] = s * ts->id[b];
+            for (int e = 0; e < b; ++e) y[e] -= ts->H[b][e] * y[b];
         }
 #pragma unroll
         for (int b = 0; b < NUP; ++b) ts->X[b][col] = -y[b];
