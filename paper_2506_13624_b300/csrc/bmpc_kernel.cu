@@ -541,13 +541,15 @@ __device__ __forceinline__ void dyn(const ProbRec &R, const float (&x)[NX], cons
  * bicycle and the unicycle (X, Y, heading, speed) the speed integrates the acceleration alone
  * (its row of A is e_3, its steering entry of B is 0), and the heading rate does not depend on the
  * heading (A[2][2] = 1); the unicycle's heading rate is its own input (A[2][3] = 0, B[2][0] = 0).
+ * In the dynamic bicycle (X, Y, heading, v_x, v_y, r) only the positions' rates see the heading,
+ * so its heading column is (*, *, 1, 0, 0, 0).
  * The forward-mode RK4 tangents produce these entries exactly (sums of exact zeros onto 1 or 0),
  * so reading them as constants changes no result; they are never loaded. */
 template <int MODEL>
 __host__ __device__ constexpr int a_fixed(int a, int b) {
     if (MODEL == 2) return -1;
     if (b < 2) return a == b ? 1 : 0;
-    if (MODEL == 1) return -1;
+    if (MODEL == 1) return b == 2 ? (a == 2 ? 1 : (a >= 3 ? 0 : -1)) : -1;   /* only X, Y see the heading */
     if (a == 2 && b == 2) return 1;
     if (a == 3) return b == 3 ? 1 : 0;
     if (MODEL == 3 && a == 2 && b == 3) return 0;
