@@ -378,6 +378,13 @@ const char *bmpc_version(void);
  * arrays, BMPC_ERR_CUDA if the launch fails. */
 int bmpc_selftest_sincos(const float *a, float *s, float *c, int32_t n, void *stream);
 
+/* Test support: the eigenvalue modification of the exact-Hessian option (Sec. IV-A; hessian = 1)
+ * on `count` symmetric n x n matrices (n = 6 or 8, row-major, device array S of count n n floats,
+ * modified in place): every eigenvalue below 1e-6 max(1, max |ev|) is raised to it; a matrix whose
+ * Cholesky test shows none below is returned unchanged.  Asynchronous on `stream`.
+ * BMPC_ERR_INVALID on a null array, another n or count < 1; BMPC_ERR_CUDA if the launch fails. */
+int bmpc_selftest_eig_modify(float *S, int32_t n, int32_t count, void *stream);
+
 /* Measurement support (no counterpart in the paper): the FP32 FMA peak of the device, against which
  * the solver's arithmetic rate is reported.  Launches `blocks` blocks of 256 threads; every thread
  * runs eight independent FMA chains of `iters` rounds and writes one float to out[thread] (out: a

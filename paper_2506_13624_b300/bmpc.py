@@ -97,6 +97,7 @@ def lib() -> C.CDLL:
         L.bmpc_get_solutions_flat.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.POINTER(Stats)]
         L.bmpc_selftest_sincos.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+        L.bmpc_selftest_eig_modify.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
         L.bmpc_get_solutions_flat_async.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.bmpc_wait_solutions.argtypes = [C.c_void_p, C.POINTER(Stats)]
         L.bmpc_set_stream.argtypes = [C.c_void_p, C.c_void_p]
@@ -111,7 +112,8 @@ EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_
             "bmpc_destroy_tree", "bmpc_status_str", "bmpc_version", "bmpc_create_batch_static", "bmpc_autotune",
             "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order", "bmpc_transfer_bytes",
             "bmpc_set_problems_flat", "bmpc_get_solutions_flat", "bmpc_transfer_bytes_flat", "bmpc_selftest_sincos",
-            "bmpc_get_solutions_flat_async", "bmpc_wait_solutions", "bmpc_set_stream", "bmpc_selftest_fma"]
+            "bmpc_get_solutions_flat_async", "bmpc_wait_solutions", "bmpc_set_stream", "bmpc_selftest_fma",
+            "bmpc_selftest_eig_modify"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -125,6 +127,19 @@ def selftest_sincos(a):
         _check(lib().bmpc_selftest_sincos(a.data_ptr(), s.data_ptr(), c.data_ptr(), a.numel(),
                                           torch.cuda.current_stream(a.device).cuda_stream), "bmpc_selftest_sincos")
     return s, c
+
+
+def selftest_eig_modify(S):
+    """The exact-Hessian option's eigenvalue modification on a float32 CUDA tensor [count, n, n]
+    (n = 6 or 8); returns the modified copy."""
+    import torch
+    assert S.is_cuda and S.dtype == torch.float32 and S.dim() == 3 and S.shape[1] == S.shape[2]
+    out = S.contiguous().clone()
+    with torch.cuda.device(S.device):
+        _check(lib().bmpc_selftest_eig_modify(out.data_ptr(), S.shape[1], S.shape[0],
+                                              torch.cuda.current_stream(S.device).cuda_stream),
+               "bmpc_selftest_eig_modify")
+    return out
 
 
 def fp32_peak_tflops(reps: int = 5) -> float:

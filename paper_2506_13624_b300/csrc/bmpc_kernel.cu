@@ -3402,6 +3402,32 @@ cudaError_t launch_sincos(const float *a, float *sn, float *cs, int n, cudaStrea
     return cudaGetLastError();
 }
 
+/* Eigenvalue-modification self-test: eig_modify (the exact-Hessian option) on `count` symmetric
+ * N x N matrices in place, one matrix per thread (N = 6 and 8: the stacked (x, u) blocks of the
+ * n_x = 4 and n_x = 6 models). */
+template <int N>
+__global__ void bmpc_eig_kernel(float *S, int count) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    float M[N][N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) M[i][j] = S[(size_t)k * N * N + i * N + j];
+    eig_modify<N>(M);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) S[(size_t)k * N * N + i * N + j] = M[i][j];
+}
+
+cudaError_t launch_eig(float *S, int n, int count, cudaStream_t stream) {
+    const int blocks = (count + 127) / 128;
+    if (n == 6) bmpc_eig_kernel<6><<<blocks, 128, 0, stream>>>(S, count);
+    else bmpc_eig_kernel<8><<<blocks, 128, 0, stream>>>(S, count);
+    return cudaGetLastError();
+}
+
 /* ------------------------------------------------------------------ input transfers */
 /* Obstacle row values from the caller's heading and semi-axes: cos and sin of the heading and
  * 1/a^2, 1/b^2, each in double precision rounded once (one definition for both upload paths). */
