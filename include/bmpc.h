@@ -385,6 +385,16 @@ int bmpc_selftest_sincos(const float *a, float *s, float *c, int32_t n, void *st
  * BMPC_ERR_INVALID on a null array, another n or count < 1; BMPC_ERR_CUDA if the launch fails. */
 int bmpc_selftest_eig_modify(float *S, int32_t n, int32_t count, void *stream);
 
+/* Test support: the second derivatives of the exact-Hessian option (Sec. IV-A; hessian = 1):
+ * H_k = sum_i mu_k,i d^2 f_i / dz dz of the discrete dynamics (RK4 with params[9] substeps of
+ * dt / params[9], the model's right-hand side) at z = (x_k, u_k), by hyper-dual arithmetic, for
+ * k < count.  params: host array of the 10 model constants (as bmpc_tree_desc.params); x, mu: device
+ * [count][nx] (absolute states, nx = 6 for model 1 else 4); u: device [count][2]; H: device
+ * [count][nx + 2][nx + 2], row-major in (x, u) order (zero for the linear model).  Asynchronous on
+ * `stream`.  BMPC_ERR_INVALID on a model outside 0..3, null arrays, count < 1 or dt <= 0. */
+int bmpc_selftest_dyn_hessian(int32_t model, const float *params, float dt, const float *x, const float *u,
+                              const float *mu, float *H, int32_t count, void *stream);
+
 /* Measurement support (no counterpart in the paper): the FP32 FMA peak of the device, against which
  * the solver's arithmetic rate is reported.  Launches `blocks` blocks of 256 threads; every thread
  * runs eight independent FMA chains of `iters` rounds and writes one float to out[thread] (out: a

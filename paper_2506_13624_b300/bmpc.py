@@ -98,6 +98,8 @@ def lib() -> C.CDLL:
                                               C.POINTER(Stats)]
         L.bmpc_selftest_sincos.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
         L.bmpc_selftest_eig_modify.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
+        L.bmpc_selftest_dyn_hessian.argtypes = [C.c_int32, C.POINTER(C.c_float), C.c_float, C.c_void_p, C.c_void_p,
+                                                C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
         L.bmpc_get_solutions_flat_async.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.bmpc_wait_solutions.argtypes = [C.c_void_p, C.POINTER(Stats)]
         L.bmpc_set_stream.argtypes = [C.c_void_p, C.c_void_p]
@@ -113,7 +115,7 @@ EXPORTED = ["bmpc_default_opts", "bmpc_batch_bytes", "bmpc_create_batch", "bmpc_
             "bmpc_set_warm_start_device", "bmpc_shift_warm_start", "bmpc_get_queue_order", "bmpc_transfer_bytes",
             "bmpc_set_problems_flat", "bmpc_get_solutions_flat", "bmpc_transfer_bytes_flat", "bmpc_selftest_sincos",
             "bmpc_get_solutions_flat_async", "bmpc_wait_solutions", "bmpc_set_stream", "bmpc_selftest_fma",
-            "bmpc_selftest_eig_modify"]
+            "bmpc_selftest_eig_modify", "bmpc_selftest_dyn_hessian"]
 
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -140,6 +142,22 @@ def selftest_eig_modify(S):
                                               torch.cuda.current_stream(S.device).cuda_stream),
                "bmpc_selftest_eig_modify")
     return out
+
+
+def selftest_dyn_hessian(model, params, dt, x, u, mu):
+    """The exact-Hessian option's second derivatives of the dynamics on the device: float32 CUDA
+    tensors x, mu [count, nx], u [count, 2]; returns H [count, nx + 2, nx + 2]."""
+    import torch
+    x, u, mu = x.contiguous(), u.contiguous(), mu.contiguous()
+    count, nx = x.shape
+    H = torch.empty((count, nx + 2, nx + 2), dtype=torch.float32, device=x.device)
+    prm = (C.c_float * 10)(*[float(v) for v in params])
+    with torch.cuda.device(x.device):
+        _check(lib().bmpc_selftest_dyn_hessian(int(model), prm, float(dt), x.data_ptr(), u.data_ptr(), mu.data_ptr(),
+                                               H.data_ptr(), count, torch.cuda.current_stream(x.device).cuda_stream),
+               "bmpc_selftest_dyn_hessian")
+        torch.cuda.current_stream(x.device).synchronize()
+    return H
 
 
 def fp32_peak_tflops(reps: int = 5) -> float:

@@ -29,6 +29,8 @@ cudaError_t launch_order(const ProbRec *recs, const Stats *stats, int32_t *order
 cudaError_t launch_flat(int which, const FlatArgs &a, int n_problems, cudaStream_t stream);
 cudaError_t launch_sincos(const float *a, float *sn, float *cs, int n, cudaStream_t stream);
 cudaError_t launch_eig(float *S, int n, int count, cudaStream_t stream);
+cudaError_t launch_dynhess(int model, const float *params, float dt, const float *x, const float *u, const float *mu,
+                           float *H, int count, cudaStream_t stream);
 cudaError_t launch_fma(float *out, int blocks, int iters, cudaStream_t stream);
 int max_block_threads();
 cudaError_t occupancy(int model, int block, size_t smem, int *blocks_per_sm, const KOpts &o);
@@ -1239,6 +1241,16 @@ int bmpc_selftest_sincos(const float *a, float *s, float *c, int32_t n, void *st
 int bmpc_selftest_eig_modify(float *S, int32_t n, int32_t count, void *stream) {
     if (!S || (n != 6 && n != 8) || count < 1) return BMPC_ERR_INVALID;
     return bmpc::launch_eig(S, n, count, static_cast<cudaStream_t>(stream)) == cudaSuccess ? BMPC_OK : BMPC_ERR_CUDA;
+}
+
+int bmpc_selftest_dyn_hessian(int32_t model, const float *params, float dt, const float *x, const float *u,
+                              const float *mu, float *H, int32_t count, void *stream) {
+    if (model < 0 || model >= NUM_MODELS || !params || !x || !u || !mu || !H || count < 1 || !(dt > 0.f))
+        return BMPC_ERR_INVALID;
+    return bmpc::launch_dynhess(model, params, dt, x, u, mu, H, count, static_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? BMPC_OK
+               : BMPC_ERR_CUDA;
 }
 
 int bmpc_selftest_fma(float *out, int32_t blocks, int32_t iters, void *stream) {

@@ -3421,6 +3421,49 @@ __global__ void bmpc_eig_kernel(float *S, int count) {
         for (int j = 0; j < N; ++j) S[(size_t)k * N * N + i * N + j] = M[i][j];
 }
 
+/* Second-derivative self-test: dyn_hessian (the exact-Hessian option's sum_i mu_i d^2 f_i / dz dz
+ * of the RK4 map, z = (x, u)) at `count` points, one per thread; rows and columns in (x, u) order. */
+struct Params10 {
+    float v[10];
+};
+
+template <int MODEL>
+__global__ void bmpc_dynhess_kernel(Params10 prm, float dt, const float *x, const float *u, const float *mu, float *H,
+                                    int count) {
+    constexpr int NX = MODEL == 1 ? 6 : 4, NZ = NX + NU;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    ProbRec R = {};
+    R.dt = dt;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) R.params[i] = prm.v[i];
+    float xa[NX], uu[NU], m[NX], Hm[NZ][NZ];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+        xa[i] = x[(size_t)k * NX + i];
+        m[i] = mu[(size_t)k * NX + i];
+    }
+#pragma unroll
+    for (int i = 0; i < NU; ++i) uu[i] = u[(size_t)k * NU + i];
+    dyn_hessian<NX, MODEL>(R, xa, uu, m, Hm);
+#pragma unroll
+    for (int i = 0; i < NZ; ++i)
+#pragma unroll
+        for (int j = 0; j < NZ; ++j) H[(size_t)k * NZ * NZ + i * NZ + j] = Hm[i][j];
+}
+
+cudaError_t launch_dynhess(int model, const float *params, float dt, const float *x, const float *u, const float *mu,
+                           float *H, int count, cudaStream_t stream) {
+    Params10 p;
+    for (int i = 0; i < 10; ++i) p.v[i] = params[i];
+    const int blocks = (count + 127) / 128;
+    if (model == 0) bmpc_dynhess_kernel<0><<<blocks, 128, 0, stream>>>(p, dt, x, u, mu, H, count);
+    else if (model == 1) bmpc_dynhess_kernel<1><<<blocks, 128, 0, stream>>>(p, dt, x, u, mu, H, count);
+    else if (model == 2) bmpc_dynhess_kernel<2><<<blocks, 128, 0, stream>>>(p, dt, x, u, mu, H, count);
+    else bmpc_dynhess_kernel<3><<<blocks, 128, 0, stream>>>(p, dt, x, u, mu, H, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eig(float *S, int n, int count, cudaStream_t stream) {
     const int blocks = (count + 127) / 128;
     if (n == 6) bmpc_eig_kernel<6><<<blocks, 128, 0, stream>>>(S, count);
