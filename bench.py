@@ -594,7 +594,7 @@ def run_lqr(args):
         d = scenes.mass_spring_chain(0, M=M, N=N, Nr=Nr, batch=batch)
         dev = lambda a: torch.tensor(np.ascontiguousarray(a, np.float32), device="cuda")
         ins = [dev(d[k]) for k in ("Q", "R", "q", "r", "A", "B", "c", "x0")]
-        h = lqr.TreeLQR(d["parent"], d["nx"], d["nu"], batch=batch, stream=s)
+        h = lqr.TreeLQR(d["parent"], d["nx"], d["nu"], batch=batch, stream=s, schedule=args.lqr_schedule)
         with torch.cuda.stream(s):
             h.solve(*ins)                                  # eager run: checks H
             g = torch.cuda.CUDAGraph()
@@ -656,6 +656,8 @@ def main():
                     help="the general-size tree LQR at the sizes of Sec. V-A (one JSON line per case)")
     ap.add_argument("--lqr-only", default="", metavar="CASE:VALUE",
                     help="one tree LQR case: single:N, tree:N_r or batch:B")
+    ap.add_argument("--lqr-schedule", type=int, default=0, choices=[0, 1, 2],
+                    help="tree LQR launch schedule: 0 cost model, 1 per stage, 2 one block per problem")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4, help="oracle problems per worker per reference step")
