@@ -700,7 +700,7 @@ def test_exact_hessian_parity(variant):
     print(_run_config(ps, orc_kw={"hessian": 1}, variant=variant, hessian=1))
 
 
-@pytest.mark.parametrize("cfg,k", [(1, 0), (1, 3), (2, 0), (2, 4), ("unicycle", 5)])
+@pytest.mark.parametrize("cfg,k", [(1, 0), (1, 3), (2, 0), (2, 4), (3, 0), (3, 6), ("unicycle", 5)])
 def test_exact_hessian_one_iteration(cfg, k):
     """One exact-Hessian iteration from an identical FP32 iterate, element by element: the modified
     blocks enter the Riccati recursion, the merit slope and the curvature test, so a wrong second
@@ -732,3 +732,10 @@ def test_exact_hessian_refuses_diagonal_cost_sweeps():
         r = _orc(p)
         assert g["status"] == oracle.OK and g["inner_iters"] == 1 == r["inner_iters"]
         np.testing.assert_allclose(g["u"], r["u"], atol=1e-4 * max(1.0, np.abs(r["u"]).max()))
+
+
+def test_exact_hessian_dynamic_bicycle_parity():
+    """The exact option on the dynamic bicycle (config 3: n_x = 6, four RK4 substeps, tyre slip
+    angles): whole solves against the oracle's exact option, the same bar as Gauss-Newton."""
+    ps = scenes.instances(3, 2, seed0=1)
+    print(_run_config(ps, min_match=0.5, orc_kw={"hessian": 1}, hessian=1))
