@@ -51,10 +51,10 @@ typedef struct bmpc_lqr bmpc_lqr;
 int bmpc_lqr_create(int32_t n, const int32_t *parent, int32_t nx, int32_t nu, int32_t batch, void *stream,
                     bmpc_lqr **out);
 
-/* One tree LQR solve of the whole batch, asynchronous on the handle's stream: the backward sweep
- * (one launch per stage, leaves to root; one block per node, each thread owning four entries of a
- * row of the node's matrix products) and the forward sweep (one launch per stage, root to leaves;
- * one warp per node).  All pointers are device
+/* One tree LQR solve of the whole batch, asynchronous on the handle's stream: the backward sweep,
+ * leaves to root (one block per node step, each thread owning four entries of a row of the node's
+ * matrix products), and the forward sweep, root to leaves (lane j of a warp on row j), on the
+ * schedule of bmpc_lqr_set_schedule.  All pointers are device
  * pointers in the layout above; inputs are only read, the outputs K, k, P, p, x, u, lam written in
  * full.  0 on success, BMPC_ERR_INVALID on a NULL required pointer, BMPC_ERR_CUDA on a launch error.
  * The call is capturable into a CUDA graph. */
@@ -71,9 +71,9 @@ int bmpc_lqr_stages(const bmpc_lqr *h);
 
 /* The launch schedule of later solves: 0 (default) chooses by a cost model of the tree's stage
  * widths and the batch size; 1: one launch per stage and sweep, every node of a stage at once (wide
- * trees); 2: one block per problem walking all of its stages, one launch per solve (narrow trees,
- * batches of single paths).  Both compute the same arithmetic in the same order, so the results
- * are bitwise equal.  BMPC_ERR_INVALID on a NULL handle or another value.  bmpc_lqr_fused returns 1
+ * trees); 2: one block per problem walking its nodes in post-order backward and its stages forward,
+ * one launch per solve (narrow trees, batches of single paths).  Both compute the same arithmetic in
+ * the same order, so the results are bitwise equal.  BMPC_ERR_INVALID on a NULL handle or another value.  bmpc_lqr_fused returns 1
  * when solves run fused, 0 when per stage. */
 int bmpc_lqr_set_schedule(bmpc_lqr *h, int32_t schedule);
 int bmpc_lqr_fused(const bmpc_lqr *h);

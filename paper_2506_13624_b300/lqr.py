@@ -1,8 +1,9 @@
 """Binding of the general-size tree LQR (include/bmpc_lqr.h): argument marshalling only.
 
-The solve runs in ``libbmpc.so``: one warp per node, a launch per stage and sweep (backward Riccati
-recursion with per-edge dynamics, then the forward sweep).  Inputs and outputs are float32 CUDA
-tensors in the header's layout; there is no CPU path.
+The solve runs in ``libbmpc.so``: the backward Riccati recursion with per-edge dynamics, then the
+forward sweep, either as a launch per stage and sweep or as one block per problem (the header's
+schedules).  Inputs and outputs are float32 CUDA tensors in the header's layout; there is no CPU
+path.
 """
 from __future__ import annotations
 

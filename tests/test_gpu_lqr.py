@@ -213,3 +213,33 @@ def test_schedules_agree_bitwise(nx, nu):
     b = _solve(parent, nx, nu, Q, R, q, r, A, B, c, x0, M=M, schedule=2)
     for key in a:
         assert np.array_equal(a[key], b[key]), key
+
+
+def test_wide_stages_agree_bitwise_and_match_the_oracle():
+    """Sec. V-A's chain with 32 scenario paths and a batch of six: the last stages hold 192 node steps,
+    more than the GPU has SMs, so the launch-per-stage schedule runs them with the two-blocks-per-SM
+    instance (whose Cholesky is lane-parallel), and the one-block-per-problem schedule runs every
+    node in post-order with the register Cholesky.  Both factorisations do the same operations in the
+    same order, so the two schedules agree bit for bit; problem 5 is checked against the oracle."""
+    d = scenes.mass_spring_chain(11, M=15, N=10, Nr=5, batch=6)
+    parent, nx, nu = d["parent"], d["nx"], d["nu"]
+    args = (d["Q"], d["R"], d["q"], d["r"], d["A"], d["B"], d["c"], d["x0"])
+    a = _solve(parent, nx, nu, *args, schedule=1)
+    b = _solve(parent, nx, nu, *args, schedule=2)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+    n, t = len(parent), 5
+    leaf = np.ones(n, bool)
+    leaf[parent[1:]] = False
+    xh = np.zeros((n, nx))
+    xh[0] = d["x0"][t]
+    for m in range(1, n):
+        xh[m] = d["A"][t, m] @ xh[parent[m]]
+    qd = np.einsum("nij,nj->ni", d["Q"][t], xh) + d["q"][t]
+    K, k, P, pv, dx, du, lam = oracle.tree_lqr(parent, d["Q"][t], np.zeros((n, nu, nx)), d["R"][t], qd, d["r"][t],
+                                               d["A"][t], d["B"][t], np.zeros((n, nx)), edge=True)
+    _close(a["x"][t], xh + dx, "x")
+    _close(a["u"][t][~leaf], du[~leaf], "u")
+    _close(a["K"][t][~leaf], K[~leaf], "K")
+    _close(a["P"][t], P, "P")
+    _close(a["lam"][t], lam, "lam")
