@@ -2,8 +2,8 @@
  * recursion of Eq. (tree_Riccati) and the feedback laws of Eq. (tree_feedback_laws), then the
  * forward sweep of Sec. III-A.  The C ABI and the problem statement are in include/bmpc_lqr.h.
  *
- * Layout of the work.  Backward, a block of NXP / 4 warps owns one node (of one problem of the
- * batch): thread (lane l, warp w) owns entries (l, 4w .. 4w + 3) of the node's matrix products, so a
+ * Layout of the work.  Backward, a block of NXP^2 / 4 threads (at least a warp) owns one node (of one
+ * problem of the batch): thread l + NXP w owns entries (l, 4w .. 4w + 3) of the node's matrix products, so a
  * node step is a set of short dot products over shared-memory tiles, with the tree's depth as the
  * only sequential chain:
  *   per child edge m:  T1 = P_m A_m, T2 = P_m B_m, g = p_m + P_m c_m
@@ -33,6 +33,11 @@
 namespace {
 
 constexpr int LQR_WARPS = 4;   /* nodes per block of the forward sweep */
+
+/* Threads of a node step's block: one per (row, group of four columns) of an NXP x NXP product
+ * (NXP^2 / 4), at least one warp. */
+template <int NXP>
+__host__ __device__ constexpr int lqr_nt() { return NXP * NXP / 4 > 32 ? NXP * NXP / 4 : 32; }
 constexpr unsigned FULL = 0xffffffffu;
 
 struct LqrArgs {
@@ -77,12 +82,12 @@ __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<floa
  * staging is issued before its first store, so a staging costs one memory latency. */
 template <int NXP, int NUP>
 struct EdgeRegs {
-    static constexpr int NT = 8 * NXP, IA = (NXP * NXP + NT - 1) / NT, IB = (NXP * NUP + NT - 1) / NT;
+    static constexpr int NT = lqr_nt<NXP>(), IA = (NXP * NXP + NT - 1) / NT, IB = (NXP * NUP + NT - 1) / NT;
     float va[IA], vb[IB], vc;
 };
 template <int NXP, int NUP>
 struct ValueRegs {
-    static constexpr int NT = 8 * NXP, IA = (NXP * NXP + NT - 1) / NT;
+    static constexpr int NT = lqr_nt<NXP>(), IA = (NXP * NXP + NT - 1) / NT;
     float vp[IA], vq;
 };
 
@@ -161,7 +166,7 @@ __device__ __forceinline__ void fma_row(float &acc, const float4 a, const float4
     acc += a.w * b.w;
 }
 
-/* Backward step of node i of problem t by the whole block: NXP / 4 warps; thread (lane l, warp w)
+/* Backward step of node i of problem t by the whole block of lqr_nt<NXP>() threads; thread l + NXP w
  * owns entries (l, 4w .. 4w + 3) of the n_x-column products and, for w < NUP / 4, of the n_u-column
  * ones.  Every thread of the block calls it with the same arguments; nd = (first and end index into
  * child_idx, last child).  The children are taken from the last to the first.
@@ -174,8 +179,10 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
     extern __shared__ __align__(16) float lqr_smem[];
     using Tiles = LqrTiles<NXP, NUP>;
     Tiles *ts = reinterpret_cast<Tiles *>(lqr_smem);
-    const int tid = threadIdx.x, nt = blockDim.x, l = tid & 31, w = tid >> 5;
-    const int j0 = 4 * w;   /* this thread's column group */
+    const int tid = threadIdx.x, nt = blockDim.x, l = tid % NXP, w = tid / NXP;
+    const int j0 = 4 * w;     /* this thread's column group */
+    /* threads past the NXP^2 / 4 product threads (a block of one warp at NXP = 8) idle in the products */
+    const bool act = lqr_nt<NXP>() == NXP * NXP / 4 || w < NW;
     const int nx = a.nx, nu = a.nu;
     const size_t base = (size_t)t * a.n, node = base + i;
     const float *Qi = a.Q + node * nx * nx;
@@ -199,7 +206,7 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
         for (int e = tid; e < nu * nx; e += nt) Ki[e] = 0.f;
         if (tid < nu) a.k[node * nu + tid] = 0.f;
         if constexpr (FUSED) {
-            if (l < NXP) {
+            if (act) {
 #pragma unroll
                 for (int s = 0; s < 4; ++s) ts->PS[j0 + s][l] = ps[s];
                 if (w == 0) ts->pv[l] = qv;
@@ -239,7 +246,7 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
             __syncthreads();
         }
         /* T1 = P_m A_m (and T2 = P_m B_m for w < NUP / 4): entries (l, 4w .. 4w + 3); g = p_m + P_m c_m */
-        if (l < NXP) {
+        if (act) {
             float4 t1 = make_float4(0.f, 0.f, 0.f, 0.f), t2 = t1;
             float gl = 0.f;
 #pragma unroll
@@ -268,7 +275,7 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
         __syncthreads();
         /* S_xx += A' T1, S_xu += A' T2, S_uu += B' T2 at (l, 4w ..); s_x += A' g, s_u += B' g (warp
          * NW - 1); the operands of four k at a time are loaded before their products */
-        if (l < NXP) {
+        if (act) {
 #pragma unroll
             for (int k4 = 0; k4 < NXP; k4 += 4) {
                 float a_[4], b_[4], g_[4];
@@ -304,7 +311,7 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
     qxx.y += qr4[1];
     qxx.z += qr4[2];
     qxx.w += qr4[3];
-    if (l < NXP && w < NWU) {
+    if (w < NWU) {
         const float s4[4] = {sxu.x, sxu.y, sxu.z, sxu.w};
         const float h4[4] = {suu.x, suu.y, suu.z, suu.w};
 #pragma unroll
@@ -316,7 +323,7 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
             if (l < NUP) ts->H[l][b] = (l < nu && b < nu) ? rv4[s] + h4[s] : (l == b ? 1.f : 0.f);
         }
     }
-    if (w == NW - 1 && l < NXP) {
+    if (w == NW - 1) {
         ts->qx[l] = row ? qv + sx : 0.f;
         if (l < NUP) ts->X[l][NXP] = l < nu ? rv + su : 0.f;
     }
@@ -375,7 +382,8 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
     } else {
     /* Cholesky H = L L' by warp 0 in registers: lane l holds row l, columns broadcast by shuffles
      * (H is the identity past n_u; pivots past n_u are skipped and 1 / L_bb is 0 there) */
-    if (w == 0) {
+    static_assert(NXP == 32, "the lane-parallel factorisation takes l as the lane");
+    if (tid < 32) {
         float h[NUP], idl = 0.f;
 #pragma unroll
         for (int b = 0; b < NUP; ++b) h[b] = l < NUP ? ts->H[l][b] : 0.f;
@@ -436,7 +444,7 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
     }
 
     /* P = Q_xx + Q_ux' K at (l, 4w ..) into T1; p = q_x + Q_ux' k (warp NW - 1) */
-    if (l < NXP) {
+    if (act) {
         float4 pv4 = qxx;
         float pl = ts->qx[l];
 #pragma unroll
@@ -452,7 +460,7 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
         }
     }
     __syncthreads();
-    if (l < NXP) {
+    if (act) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int j = j0 + s;
@@ -461,14 +469,14 @@ __device__ __forceinline__ void backward_node(const LqrArgs &a, int t, int i, in
             if (FUSED) ts->PS[j][l] = v;
         }
     }
-    if (row)
+    if (row && act)
         for (int b = w; b < nu; b += NW) Ki[(size_t)b * nx + l] = ts->X[b][l];
     if (tid < nu) a.k[node * nu + tid] = ts->X[tid][NXP];
 }
 
 /* One backward launch per stage: block b is node s0 + b % cnt of problem b / cnt. */
 template <int NXP, int NUP, int MINB>
-__global__ void __launch_bounds__(8 * NXP, MINB) lqr_backward_kernel(LqrArgs a) {
+__global__ void __launch_bounds__(lqr_nt<NXP>(), MINB) lqr_backward_kernel(LqrArgs a) {
     const long long item = blockIdx.x;
     const int i = a.s0 + (int)(item % a.cnt);
     const int4 nd = a.node4[i];
@@ -547,7 +555,7 @@ __device__ __forceinline__ void forward_single(const LqrArgs &a, int t, int m, b
     extern __shared__ __align__(16) float lqr_smem[];
     using Tiles = LqrTiles<NXP, NUP>;
     Tiles *ts = reinterpret_cast<Tiles *>(lqr_smem);
-    constexpr int NT = 8 * NXP, IA = (NXP * NXP + NT - 1) / NT, IB = (NXP * NUP + NT - 1) / NT;
+    constexpr int NT = lqr_nt<NXP>(), IA = (NXP * NXP + NT - 1) / NT, IB = (NXP * NUP + NT - 1) / NT;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nx = a.nx, nu = a.nu;
     const size_t node = (size_t)t * a.n + m;
@@ -644,8 +652,8 @@ __device__ __forceinline__ void forward_single(const LqrArgs &a, int t, int m, b
  * block (forward_single), wider ones a warp per node.  For trees whose stages are narrow, where the
  * per-stage launches would leave the GPU idle between them. */
 template <int NXP, int NUP>
-__global__ void __launch_bounds__(8 * NXP) lqr_fused_kernel(LqrArgs a, const int4 *plan, const int32_t *sstart, int S) {
-    constexpr int NW = NXP / 4;
+__global__ void __launch_bounds__(lqr_nt<NXP>()) lqr_fused_kernel(LqrArgs a, const int4 *plan, const int32_t *sstart, int S) {
+    constexpr int WARPS = lqr_nt<NXP>() / 32;
     const int t = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31, n = a.n;
     const int4 none = make_int4(-1, 0, 0, -1);
     int4 cur = plan[0], nxt = n > 1 ? plan[1] : none;
@@ -667,7 +675,7 @@ __global__ void __launch_bounds__(8 * NXP) lqr_fused_kernel(LqrArgs a, const int
             forward_single<NXP, NUP>(a, t, b0, single_prev);
             single_prev = true;
         } else {
-            for (int i = b0 + w; i < b1; i += NW) forward_node<NXP, NUP>(a, t, i, lane);
+            for (int i = b0 + w; i < b1; i += WARPS) forward_node<NXP, NUP>(a, t, i, lane);
             single_prev = false;
         }
         __syncthreads();
@@ -685,18 +693,18 @@ struct Instance {
     LqrKernel bwd, bwd_wide, fwd;   /* bwd_wide: two blocks per SM, for stages wider than the GPU */
     FusedKernel fused;
     size_t smem;
-    int bwd_threads;   /* one block per node: NXP / 4 warps */
+    int bwd_threads;   /* one block per node step: lqr_nt<NXP>() */
 };
 
 Instance instance(int nx, int nu) {
     if (nx <= 8 && nu <= 4)
-        return {lqr_backward_kernel<8, 4, 1>, lqr_backward_kernel<8, 4, 4>, lqr_forward_kernel<8, 4>,
-                lqr_fused_kernel<8, 4>, backward_smem<8, 4>(), 64};
+        return {lqr_backward_kernel<8, 4, 1>, lqr_backward_kernel<8, 4, 8>, lqr_forward_kernel<8, 4>,
+                lqr_fused_kernel<8, 4>, backward_smem<8, 4>(), lqr_nt<8>()};
     if (nx <= 16 && nu <= 8)
-        return {lqr_backward_kernel<16, 8, 1>, lqr_backward_kernel<16, 8, 3>, lqr_forward_kernel<16, 8>,
-                lqr_fused_kernel<16, 8>, backward_smem<16, 8>(), 128};
+        return {lqr_backward_kernel<16, 8, 1>, lqr_backward_kernel<16, 8, 6>, lqr_forward_kernel<16, 8>,
+                lqr_fused_kernel<16, 8>, backward_smem<16, 8>(), lqr_nt<16>()};
     return {lqr_backward_kernel<32, 16, 1>, lqr_backward_kernel<32, 16, 2>, lqr_forward_kernel<32, 16>,
-            lqr_fused_kernel<32, 16>, backward_smem<32, 16>(), 256};
+            lqr_fused_kernel<32, 16>, backward_smem<32, 16>(), lqr_nt<32>()};
 }
 
 }  // namespace
@@ -708,22 +716,24 @@ struct bmpc_lqr {
     int4 *d_node4 = nullptr, *d_plan = nullptr;   /* d_plan: the post-order of the one-block-per-problem schedule */
     int schedule = 0;   /* 0: by the cost model, 1: a launch per stage and sweep, 2: one block per problem */
     int sm_count = 148;
+    int occ_fused = 1, occ_wide = 1;   /* resident blocks per SM of the fused and the wide-stage kernels */
     cudaStream_t stream = nullptr;
     Instance inst{};
 };
 
 namespace {
 /* The schedule: per-stage launches expose every node of a stage at once; one block per problem saves
- * the launches but walks each tree's nodes one after another.  Cost model in node-step units, two
- * blocks resident per SM, a launch worth half a node step:
- *   per stage:  sum_s (ceil(width_s * batch / (2 SMs)) + 1/2),   fused:  ceil(batch / (2 SMs)) * n. */
+ * the launches but walks each tree's nodes one after another.  Cost model in node-step units, a
+ * launch worth half a node step, with the blocks each kernel keeps resident per SM (o_w for the
+ * wide-stage backward kernel, o_f for the fused one):
+ *   per stage:  sum_s (ceil(width_s * batch / (o_w SMs)) + 1/2),   fused:  ceil(batch / (o_f SMs)) * n. */
 bool fused_schedule(const bmpc_lqr *h) {
     if (h->schedule) return h->schedule == 2;
-    const double slots = 2.0 * h->sm_count;
+    const double slots_w = (double)h->occ_wide * h->sm_count, slots_f = (double)h->occ_fused * h->sm_count;
     double staged = 0.0;
     for (size_t s = 0; s + 1 < h->sstart.size(); ++s)
-        staged += std::ceil((double)(h->sstart[s + 1] - h->sstart[s]) * h->batch / slots) + 0.5;
-    return std::ceil(h->batch / slots) * h->n <= staged;
+        staged += std::ceil((double)(h->sstart[s + 1] - h->sstart[s]) * h->batch / slots_w) + 0.5;
+    return std::ceil(h->batch / slots_f) * h->n <= staged;
 }
 }  // namespace
 
@@ -793,6 +803,12 @@ int bmpc_lqr_create(int32_t n, const int32_t *parent, int32_t nx, int32_t nu, in
                                     (int)h->inst.smem) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(h->inst.fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->inst.smem) ==
                    cudaSuccess;
+    ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_fused, h->inst.fused, h->inst.bwd_threads,
+                                                             h->inst.smem) == cudaSuccess &&
+         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occ_wide, h->inst.bwd_wide, h->inst.bwd_threads,
+                                                       h->inst.smem) == cudaSuccess;
+    h->occ_fused = std::max(1, h->occ_fused);
+    h->occ_wide = std::max(1, h->occ_wide);
     if (!ok) {
         bmpc_lqr_destroy(h);
         return BMPC_ERR_CUDA;
