@@ -2,12 +2,12 @@
  * Learned warm start: a multilayer perceptron with BF16 weights and activations, FP32
  * accumulation, trained and evaluated by the kernels in this file.
  *
- *   gemm_tc<TA, TB, EPI>     C[M x N] = op(A)[M x K] op(B)[K x N] on the 5th-generation tensor
+ *   gemm_tc<TA, TB, EPI, WN> C[M x N] = op(A)[M x K] op(B)[K x N] on the 5th-generation tensor
  *                            cores: tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) issued by one
- *                            thread from shared-memory descriptors, the 128 x 128 accumulator in
- *                            tensor memory (TMEM), operand tiles loaded by TMA
- *                            (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage ring of
- *                            full/empty mbarriers; the epilogue reads TMEM with tcgen05.ld.
+ *                            thread from shared-memory descriptors, the 128 x WN accumulator
+ *                            (WN = 128, or 256 when N allows) in tensor memory (TMEM), operand tiles
+ *                            loaded by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage
+ *                            ring of full/empty mbarriers; the epilogue reads TMEM with tcgen05.ld.
  *                            op(X) is X or X^T: K-major and MN-major operands use the matching
  *                            swizzled descriptor layouts.
  *                            Epilogues: plain f32 (weight gradients), + bias in f32 (output
@@ -31,14 +31,22 @@
 
 namespace bmpc_mlp {
 
-constexpr int BM = 128, BN = 128, BK = 64, NSTAGE = 4;
+constexpr int BM = 128, BN = 128, BK = 64, NSTAGE = 4;   /* BN: the narrow tile (N a multiple of 128) */
 constexpr int THREADS = 192;                                   /* warp 0 TMA, warp 1 MMA, warps 2-5 epilogue */
 constexpr int TILE_BYTES = 128 * BK * 2;                       /* one 128 x 64 bf16 operand tile (16 KB) */
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;                    /* A and B tiles of one k-step */
 constexpr int OUT_BUF = 32 * 32 * 4;                           /* one 32 x 32 FP32 chunk of C for a TMA store */
 constexpr int OUT_BYTES = 4 * 2 * OUT_BUF;                     /* two buffers per epilogue warp */
-constexpr int GEMM_SMEM = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024;   /* 160 KB + alignment slack */
-constexpr int TMEM_COLS = 2 * BN;                              /* two FP32 accumulators of 128 lanes x 128 */
+constexpr int GROUP_M = 16;                                    /* m-tiles per group of the tile order */
+
+/* Output tiles of 128 x WN, WN = 128 or 256 (N a multiple of 256): the wide tile reads 3/4 of the
+ * operand bytes per product of the narrow one.  Per k-step the A slice is 16 KB and the B slice
+ * WN x 64 bf16; two FP32 accumulators of 128 lanes x WN columns fill 256 or all 512 TMEM columns. */
+template <int WN>
+struct GemmCfg {
+    static constexpr int STAGE = TILE_BYTES + WN * BK * 2;                  /* A and B slices of one k-step */
+    static constexpr int SMEM = NSTAGE * STAGE + OUT_BYTES + 1024;           /* 161 or 225 KB with the slack */
+    static constexpr int TMEM = 2 * WN;
+};
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_DGELU = 3 };
 
@@ -70,10 +78,11 @@ __device__ __forceinline__ uint32_t slice_offset(int j, bool mn_major) { return 
 
 /* Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5), BF16 A and B
  * (bits 7-9, 10-12), A and B majors (bit 15, 16: 0 K-major, 1 M/N-major), N/8 (bits 17-22),
- * M/16 (bits 24-28). */
+ * M/16 (bits 24-28); M = 128, N = WN. */
+template <int WN>
 __host__ __device__ constexpr uint32_t mma_idesc(bool a_mn, bool b_mn) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+           ((uint32_t)(WN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 /* One 2-D TMA load (one thread) with 128-byte swizzle into `dst` (1024-byte aligned), completing
@@ -96,15 +105,15 @@ __device__ __forceinline__ void tma_store_chunk(const CUtensorMap *map, const vo
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-/* The operand slice of k-step t: K-major, one box of 64 k x 128 rows; M/N-major, two boxes of 64 mn x
- * 64 k (the two halves of the tile's 128 rows). */
-template <bool KMAJ>
+/* The operand slice of k-step t for a tile of ROWS rows (128 or 256): K-major, one box of 64 k x ROWS
+ * rows (the map's box); M/N-major, ROWS / 64 boxes of 64 mn x 64 k, 8 KB apart. */
+template <bool KMAJ, int ROWS>
 __device__ __forceinline__ void load_slice(unsigned char *dst, const CUtensorMap *map, int k0, int r0, uint64_t *bar) {
     if (KMAJ) {
         tma_box(dst, map, k0, r0, bar);
     } else {
-        tma_box(dst, map, r0, k0, bar);
-        tma_box(dst + 8192, map, r0 + 64, k0, bar);
+#pragma unroll
+        for (int h = 0; h < ROWS / 64; ++h) tma_box(dst + 8192 * h, map, r0 + 64 * h, k0, bar);
     }
 }
 
@@ -164,10 +173,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 /* C = op(A) op(B), persistent and warp-specialised.  TA: A is given transposed (stored K x M);
  * TB: B is given transposed (stored N x K); amap/bmap are their TMA views and ldc the row length of
- * C.  The grid's blocks take the 128 x 128 output tiles t = blockIdx.x, + gridDim.x, ... of the
- * S x MT x NT tile space (split z, m-tile fastest, so the blocks that run together share each B
- * tile in L2); split z covers k-steps [z kps, min(K/BK, (z+1) kps)) and, for EPI_F32, writes its
- * partial product to C + z c_split.
+ * C.  The grid's blocks take the 128 x WN output tiles t = blockIdx.x, + gridDim.x, ... of the
+ * S x MT x NT tile space: split z slowest, then groups of GROUP_M m-tiles, inside a group the m-tile
+ * fastest, so that the blocks that run together share each B tile and a panel of GROUP_M A tiles
+ * in L2; split z covers k-steps [z kps, min(K/BK, (z+1) kps)) and, for EPI_F32, writes its partial
+ * product to C + z c_split.
  *   warp 0, one thread: TMA producer over an NSTAGE ring of operand stages (full/empty mbarriers);
  *   warp 1, one thread: issues the MMAs of each k-step once its stage has landed, commits them to
  *     the stage's empty barrier, and after a tile's last k-step to tmem_full of its accumulator;
@@ -177,7 +187,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
  *     the epilogue, and releases the accumulator on tmem_empty.
  * Every wait is bounded; on a timeout the block records it in g_gemm_timeout, every role stops,
  * the producer waits for its loads in flight, the MMA thread for its MMAs, and TMEM is freed. */
-template <bool TA, bool TB, int EPI>
+template <bool TA, bool TB, int EPI, int WN>
 __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUtensorMap amap,
                                                     const __grid_constant__ CUtensorMap bmap,
                                                     const __grid_constant__ CUtensorMap cmap, void *C, int ldc, int K,
@@ -191,7 +201,7 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
-                     "r"(TMEM_COLS));
+                     "r"(GemmCfg<WN>::TMEM));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -213,10 +223,11 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
     const uint32_t tmem = tmem_slot;
     const int KT_all = K / BK;
     auto tile_of = [&](int t, int &m0, int &n0, int &kbeg, int &KT, int &z) {
-        const int mt = t % MT, r = t / MT;
-        n0 = (r % NT) * BN;
-        z = r / NT;
-        m0 = mt * BM;
+        const int per = MT * NT, r = t % per, g = r / (GROUP_M * NT), first = g * GROUP_M;
+        const int gm = min(MT - first, GROUP_M), w = r - g * GROUP_M * NT;
+        z = t / per;
+        m0 = (first + w % gm) * BM;
+        n0 = (w / gm) * WN;
         kbeg = z * kps;
         KT = min(KT_all - kbeg, kps);
     };
@@ -229,12 +240,12 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
                 for (int kt = 0; kt < KT; ++kt, ++g) {
                     const int s = g % NSTAGE;
                     if (!mbar_wait_or_abort(&empty[s], ((g / NSTAGE) & 1) ^ 1, &abort_flag)) break;
-                    unsigned char *sa = smem + s * STAGE_BYTES;
+                    unsigned char *sa = smem + s * GemmCfg<WN>::STAGE;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[s])),
-                                 "r"(STAGE_BYTES)
+                                 "r"(GemmCfg<WN>::STAGE)
                                  : "memory");
-                    load_slice<!TA>(sa, &amap, (kbeg + kt) * BK, m0, &full[s]);
-                    load_slice<TB>(sa + TILE_BYTES, &bmap, (kbeg + kt) * BK, n0, &full[s]);
+                    load_slice<!TA, BM>(sa, &amap, (kbeg + kt) * BK, m0, &full[s]);
+                    load_slice<TB, WN>(sa + TILE_BYTES, &bmap, (kbeg + kt) * BK, n0, &full[s]);
                 }
             }
             if (abort_flag) {   /* the last loads of every stage land before the block frees its memory */
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = mma_idesc(TA, !TB);
+            constexpr uint32_t idesc = mma_idesc<WN>(TA, !TB);
             uint32_t g = 0;
             int i = 0;
             for (int t = blockIdx.x; t < T && !abort_flag; t += gridDim.x, ++i) {
@@ -253,7 +264,7 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
                 const int acc = i & 1;
                 if (!mbar_wait_or_abort(&tmem_empty[acc], ((i >> 1) & 1) ^ 1, &abort_flag)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t d = tmem + (uint32_t)(acc * BN);
+                const uint32_t d = tmem + (uint32_t)(acc * WN);
                 bool fail = false;
                 for (int kt = 0; kt < KT; ++kt, ++g) {
                     const int s = g % NSTAGE;
@@ -262,7 +273,7 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa = smem_addr(smem + s * STAGE_BYTES), sb = sa + TILE_BYTES;
+                    const uint32_t sa = smem_addr(smem + s * GemmCfg<WN>::STAGE), sb = sa + TILE_BYTES;
 #pragma unroll
                     for (int j = 0; j < BK / 16; ++j) {
                         const uint64_t da = tile_desc(sa + slice_offset(j, TA), TA);
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
         }
     } else {
         const int q = warp & 3;   /* TMEM lane quarter this warp may access */
-        unsigned char *obuf = smem + NSTAGE * STAGE_BYTES;   /* 1024-byte aligned output chunk buffers */
+        unsigned char *obuf = smem + NSTAGE * GemmCfg<WN>::STAGE;   /* 1024-byte aligned output chunk buffers */
         int nst = 0;                                          /* TMA stores issued by this warp */
         int i = 0;
         for (int t = blockIdx.x; t < T; t += gridDim.x, ++i) {
@@ -303,9 +314,9 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
             void *Cz = EPI == EPI_F32 ? static_cast<void *>(static_cast<float *>(C) + z * c_split) : C;
             const int r = m0 + q * 32 + lane;
 #pragma unroll 1
-            for (int cc = 0; cc < BN / 32; ++cc) {
+            for (int cc = 0; cc < WN / 32; ++cc) {
                 uint32_t v[32];
-                tmem_ld32(v, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + cc * 32));
+                tmem_ld32(v, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * WN + cc * 32));
                 const int c0 = n0 + cc * 32;
                 const size_t o = (size_t)r * ldc + c0;
                 if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
@@ -379,7 +390,8 @@ __global__ void __launch_bounds__(THREADS) gemm_tc(const __grid_constant__ CUten
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (abort_flag && tid == 0) atomicExch(&g_gemm_timeout, 1);
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GemmCfg<WN>::TMEM));
 }
 
 /* Self-test of the bounded wait: one thread waits for the first phase of an mbarrier that nothing
@@ -513,10 +525,13 @@ using namespace bmpc_mlp;
 
 bool dims_ok(int M, int N, int K) { return M > 0 && N > 0 && K > 0 && M % BM == 0 && N % BN == 0 && K % BK == 0; }
 
+/* The output tile width for N columns: 256 when N is a multiple of 256, else 128. */
+int gemm_wn(int N) { return N % 256 == 0 ? 256 : BN; }
+
 /* K-steps per split for a GEMM with few output tiles: enough splits to give every SM about two
  * blocks, at least 8 k-steps each; returns K/BK (one split) when splitting does not pay. */
 int split_kps(int M, int N, int K) {
-    const int tiles = (M / BM) * (N / BN), KT = K / BK;
+    const int tiles = (M / BM) * (N / gemm_wn(N)), KT = K / BK;
     if (tiles >= 148) return KT;
     int S = std::min((2 * 148 + tiles - 1) / tiles, KT / 8);
     if (S < 2) return KT;
@@ -547,10 +562,11 @@ EncodeTiled encoder() {
 }
 
 /* TMA view of a GEMM operand for gemm_tc (see load_slice): a 2-D map of the stored matrix with
- * 128-byte swizzle.  kmajor: stored [mn][ld] with K along a row, boxes of 64 k x 128 rows; else
- * stored [k][ld] with MN along a row, boxes of 64 mn x 64 k.  mn and k are the operand's extents
- * (multiples of 128 and BK), ld the stored row length in elements (a multiple of 8: 16-byte rows). */
-bool make_operand_map(CUtensorMap *m, const void *ptr, int mn, int k, int ld, bool kmajor) {
+ * 128-byte swizzle.  kmajor: stored [mn][ld] with K along a row, boxes of 64 k x `rows` rows (the
+ * operand tile's 128 or 256); else stored [k][ld] with MN along a row, boxes of 64 mn x 64 k.  mn and
+ * k are the operand's extents (multiples of the tile and of BK), ld the stored row length in
+ * elements (a multiple of 8: 16-byte rows). */
+bool make_operand_map(CUtensorMap *m, const void *ptr, int mn, int k, int ld, bool kmajor, int rows) {
     const EncodeTiled enc = encoder();
     if (!enc) return false;
     cuuint64_t dim[2], str[1] = {(cuuint64_t)ld * 2};
@@ -559,7 +575,7 @@ bool make_operand_map(CUtensorMap *m, const void *ptr, int mn, int k, int ld, bo
         dim[0] = (cuuint64_t)k;
         dim[1] = (cuuint64_t)mn;
         box[0] = 64;
-        box[1] = 128;
+        box[1] = (cuuint32_t)rows;
     } else {
         dim[0] = (cuuint64_t)mn;
         dim[1] = (cuuint64_t)k;
@@ -584,12 +600,12 @@ bool make_output_map(CUtensorMap *m, void *C, int M, int N, int ldc, int S, int6
            CUDA_SUCCESS;
 }
 
-template <bool TA, bool TB, int EPI>
+template <bool TA, bool TB, int EPI, int WN>
 cudaError_t set_smem() {
-    static bool done = false;   /* 161 KB of dynamic shared memory needs the opt-in, once per instance */
+    static bool done = false;   /* 161 or 225 KB of dynamic shared memory need the opt-in, once per instance */
     if (done) return cudaSuccess;
-    const cudaError_t e =
-        cudaFuncSetAttribute(gemm_tc<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    const cudaError_t e = cudaFuncSetAttribute(gemm_tc<TA, TB, EPI, WN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               GemmCfg<WN>::SMEM);
     done = e == cudaSuccess;
     return e;
 }
@@ -607,23 +623,25 @@ int gemm_grid(int T) {
     return std::max(1, std::min(T, sms));
 }
 
-/* C = epilogue(op(A) op(B)); GEMMs with few output tiles and a long K are split along K into the
- * workspace ws (ws_floats floats, may be 0) and reduced in split order by splitk_reduce. */
-template <bool TA, bool TB, int EPI>
-cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ldc, int M, int N, int K, const float *bias,
-                 void *pre, cudaStream_t s, float *ws = nullptr, int64_t ws_floats = 0) {
+/* C = epilogue(op(A) op(B)) with output tiles of 128 x WN; GEMMs with few output tiles and a long K
+ * are split along K into the workspace ws (ws_floats floats, may be 0) and reduced in split order by
+ * splitk_reduce. */
+template <bool TA, bool TB, int EPI, int WN>
+cudaError_t gemm_w(const void *A, int lda, const void *B, int ldb, void *C, int ldc, int M, int N, int K,
+                   const float *bias, void *pre, cudaStream_t s, float *ws, int64_t ws_floats) {
+    constexpr int SMEM = GemmCfg<WN>::SMEM;
     const int KT = K / BK, kps = split_kps(M, N, K), S = (KT + kps - 1) / kps;
-    const int MT = M / BM, NT = N / BN;
+    const int MT = M / BM, NT = N / WN;
     CUtensorMap am, bm;
-    if (!make_operand_map(&am, A, M, K, lda, !TA) || !make_operand_map(&bm, B, N, K, ldb, TB))
+    if (!make_operand_map(&am, A, M, K, lda, !TA, BM) || !make_operand_map(&bm, B, N, K, ldb, TB, WN))
         return cudaErrorInvalidValue;
     if (S > 1 && ws && (int64_t)S * M * N <= ws_floats) {
-        cudaError_t e = set_smem<TA, TB, EPI_F32>();
+        cudaError_t e = set_smem<TA, TB, EPI_F32, WN>();
         if (e != cudaSuccess) return e;
         const int T = S * MT * NT;
         CUtensorMap cm;
         if (!make_output_map(&cm, ws, M, N, N, S, (int64_t)M * N)) return cudaErrorInvalidValue;
-        gemm_tc<TA, TB, EPI_F32><<<gemm_grid(T), THREADS, GEMM_SMEM, s>>>(am, bm, cm, ws, N, K, nullptr, nullptr, kps,
+        gemm_tc<TA, TB, EPI_F32, WN><<<gemm_grid(T), THREADS, SMEM, s>>>(am, bm, cm, ws, N, K, nullptr, nullptr, kps,
                                                                          (int64_t)M * N, MT, NT, T);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -632,7 +650,7 @@ cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ld
         splitk_reduce<EPI><<<grid, 256, 0, s>>>(ws, S, M, N, C, ldc, bias, static_cast<__nv_bfloat16 *>(pre));
         return cudaGetLastError();
     }
-    const cudaError_t e = set_smem<TA, TB, EPI>();
+    const cudaError_t e = set_smem<TA, TB, EPI, WN>();
     if (e != cudaSuccess) return e;
     CUtensorMap cm;
     if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
@@ -640,10 +658,17 @@ cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ld
     } else {
         cm = am;   /* unused by the bf16 epilogues */
     }
-    gemm_tc<TA, TB, EPI><<<gemm_grid(MT * NT), THREADS, GEMM_SMEM, s>>>(am, bm, cm, C, ldc, K, bias,
-                                                                       static_cast<__nv_bfloat16 *>(pre), KT, 0, MT,
-                                                                       NT, MT * NT);
+    gemm_tc<TA, TB, EPI, WN><<<gemm_grid(MT * NT), THREADS, SMEM, s>>>(am, bm, cm, C, ldc, K, bias,
+                                                                      static_cast<__nv_bfloat16 *>(pre), KT, 0, MT,
+                                                                      NT, MT * NT);
     return cudaGetLastError();
+}
+
+template <bool TA, bool TB, int EPI>
+cudaError_t gemm(const void *A, int lda, const void *B, int ldb, void *C, int ldc, int M, int N, int K, const float *bias,
+                 void *pre, cudaStream_t s, float *ws = nullptr, int64_t ws_floats = 0) {
+    return gemm_wn(N) == 256 ? gemm_w<TA, TB, EPI, 256>(A, lda, B, ldb, C, ldc, M, N, K, bias, pre, s, ws, ws_floats)
+                             : gemm_w<TA, TB, EPI, BN>(A, lda, B, ldb, C, ldc, M, N, K, bias, pre, s, ws, ws_floats);
 }
 
 int check_layers(const bmpc_mlp_layer *L, int n) {

@@ -34,7 +34,9 @@ def feature_dim(p) -> int:
 
 
 def target_dim(p) -> int:
-    return round128(int(p["n"]) * (2 * int(p["nx"]) + 2 + bmpc.n_con(p)))
+    """Targets per problem, padded to a multiple of 256: the output layer's GEMMs then run on the
+    128 x 256 output tiles."""
+    return (int(p["n"]) * (2 * int(p["nx"]) + 2 + bmpc.n_con(p)) + 255) // 256 * 256
 
 
 def solve_batch(problems, opts=None, prev=None, warm_from=None):

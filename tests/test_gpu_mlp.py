@@ -59,13 +59,15 @@ def _assert_bf16_matches(got, ref_exact, name, max_flip_frac=2e-3):
     assert flips <= max(2, max_flip_frac * got.size), (name, flips, got.size)
 
 
+@pytest.mark.parametrize("N", [384, 512])
 @pytest.mark.parametrize("K", [192, 1024])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
-def test_gemm_variants_match_fp64(ta, tb, K):
-    """Every operand major on the tcgen05 path; K = 1024 cycles the 3-stage ring five times."""
+def test_gemm_variants_match_fp64(ta, tb, K, N):
+    """Every operand major on the tcgen05 path, with 128 x 128 output tiles (N = 384) and 128 x 256
+    ones (N = 512); K = 1024 cycles the 4-stage ring four times."""
     from paper_2506_13624_b300 import mlp
-    rng = np.random.default_rng(int(ta) * 2 + int(tb) + K)
-    M, N = 256, 384
+    rng = np.random.default_rng(int(ta) * 2 + int(tb) + K + N)
+    M = 256
     A = mlp_ref.bf16(rng.standard_normal((K, M) if ta else (M, K)))
     B = mlp_ref.bf16(rng.standard_normal((N, K) if tb else (K, N)))
     C = mlp.gemm(_bf(A), _bf(B), ta, tb).cpu().numpy()
