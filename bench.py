@@ -86,7 +86,8 @@ def flops_model(p) -> dict:
         ls_dyn = nsub * 4 * (rhs + 6 * nx)
     con = 8 * nx + 30 * n_obs + 20
     return dict(
-        linearise=lin_dyn + con + 2 * nx * nx + 8 * nx,
+        lin_dyn=lin_dyn,                         # f, A, B: only where the point has moved
+        linearise=con + 2 * nx * nx + 8 * nx,    # cost, penalty terms, defects, KKT: at every check
         riccati=(2 * nx ** 3 + 4 * nx * nx + 2 * ns * nx + 4 * nx * nx + 2 * nx * nx + ns * (2 * nx + 4)
                  + 12 * nx + 60 + ns + 2 * nx * nx),
         forward=4 * nx * nx + 8 * nx + 8 * nx,
@@ -111,7 +112,8 @@ def algorithmic_flops(problems, results) -> float:
         n = int(p["n"])
         it = r["inner_iters"]
         checks = it + r["outer_iters"]            # linearisation + KKT check per inner step and per outer exit
-        tot += n * (checks * m["linearise"] + it * (m["riccati"] + m["forward"] + m["update"])
+        moved = it + 1                            # dynamics linearised at the start and after every step
+        tot += n * (moved * m["lin_dyn"] + checks * m["linearise"] + it * (m["riccati"] + m["forward"] + m["update"])
                     + r["ls_evals"] * m["ls_eval"] + r["outer_iters"] * m["outer"])
     return tot
 
@@ -474,7 +476,9 @@ def run_gpu(args):
         "tree_riccati_us_per_iter": ric_us_iter,
         "phase_us_per_iter": phases,
         "solve_latency_us": {"mean": float(tot_us.mean()), "max": float(tot_us.max())},
-        "inner_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
+        "inner_iters": {"mean": float(iters.mean()), "max": int(iters.max()),
+                        "outer_mean": float(np.mean([r["outer_iters"] for r in res])),
+                        "ls_evals_per_iter": float(sum(r["ls_evals"] for r in res) / max(1, iters.sum()))},
         "gpu_launches": args.steps * n_models * (2 if opts.queue_order == 1 else 1),
         "roofline": {"bound": "latency", "achieved": lat_achieved, "peak": lat_peak,
                      "unit": "inner iterations/s per problem in flight", "frac": lat_frac,

@@ -2838,6 +2838,9 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
 
     float rho = O.rho0, mu = O.mu0, omega = O.omega0, eta = O.eta0;
     float pending = 0.f;   /* step of the last line search, not yet applied to (x, u, lam) */
+    /* f, A and B depend on (x, u) alone: after an outer update the point has not moved, so the
+     * next linearisation keeps them and recomputes only the terms that see y and rho */
+    bool lin_done = false;
     float r_kkt = INFINITY, cviol = INFINITY;
     int inner = 0, outer = 0, ls_fail = 0, ls_fail_total = 0, ls_evals = 0, status = 1 /* MAX_ITER */;
     const int G = (O.ls_chunk <= 0 || O.ls_chunk > MAX_CHUNK) ? min(O.n_alpha, MAX_CHUNK) : O.ls_chunk;
@@ -2856,6 +2859,8 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
             /* ===== linearise + quadratise at the current point (first applying the step of the
              * previous line search, node by node: x += a dx, u += a du, lam += a (lam_QP - lam)) */
             long long t0 = clock64();
+            const bool relin = !lin_done || pending > 0.f;
+            lin_done = true;
             for (int i = tid; i < n; i += nt) {
                 if constexpr (HOIST_LOADS) {
                     /* loads first (the node's rows, the step, the constraint data), stores last: a
@@ -2870,7 +2875,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     if (step) apply_step<NX>(V, i, pending, x, u, lam, lo);
                     const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, lo, rho, q, r, hq, hr);
                     float xa[NX];
-                    if (!is_leaf) {
+                    if (!is_leaf && relin) {
     #pragma unroll
                         for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
                     }
@@ -2887,7 +2892,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     V.hq[2 * (size_t)np + i] = hq[2];
                     V.store_u(V.hr, i, hr);
                     V.nv[i] = la;
-                    if (!is_leaf) {
+                    if (!is_leaf && relin) {
                         bool done = false;
                         if constexpr (MODEL == 2) {
                             if (V.edge) {   /* per-edge dynamics: the increment of every child's edge */
@@ -2933,7 +2938,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     V.hq[2 * (size_t)np + i] = hq[2];
                     V.store_u(V.hr, i, hr);
                     V.nv[i] = la;
-                    if (!is_leaf) {
+                    if (!is_leaf && relin) {
                         float xa[NX], xn[NX];
     #pragma unroll
                         for (int j = 0; j < NX; ++j) xa[j] = V.xref[(size_t)j * np + i] + x[j];
