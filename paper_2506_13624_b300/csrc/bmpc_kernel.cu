@@ -593,6 +593,7 @@ struct View {
     bool edge;   /* per-edge linear dynamics: A, B point at the input rows, f and A, B are per edge */
     bool hess;   /* exact-Hessian option: the node blocks Q, M, R are the dense rows HS */
     float *HS;
+    float *FR;   /* node-major forward records (fr_stride(NX) floats per node) */
 
     __device__ View(const ProbRec &R, const int32_t *ib, const float *fin, const float *fw, float *fout, float *fs) {
         n = R.n;
@@ -650,6 +651,7 @@ struct View {
         edge = false;   /* set by the solver for the linear model (per-edge dynamics) */
         hess = false;
         HS = fs + (size_t)s.hs * np;
+        FR = fs + (size_t)s.fr * np;
         CV0 = fs + (size_t)s.cv * np;
         CV1 = CV0 + (size_t)cvf_rows(NX) * np;
         JA0 = fs + (size_t)s.ja * np;
@@ -891,10 +893,18 @@ __device__ __forceinline__ void leaf_value(const ProbRec &R, const View<NX> &V, 
     }
 }
 
+/* Stores an NX-vector as float2 pairs (dst 8-byte aligned). */
+template <int NX>
+__device__ __forceinline__ void put_pairs(float *dst, const float (&v)[NX]) {
+#pragma unroll
+    for (int j = 0; j < NX / 2; ++j) reinterpret_cast<float2 *>(dst)[j] = make_float2(v[2 * j], v[2 * j + 1]);
+}
+
 /* Adds the value function of child m to (Pb, pb): Pb += P_m, pb += p_m + P_m d_m, with
  * P_m, p_m, d_m read from memory (Eq. tree_Riccati, sum over ch(n)). */
 template <int NX>
-__device__ __forceinline__ void add_child_mem(const View<NX> &V, int m, float (&Pb)[nsym(NX)], float (&pb)[NX]) {
+__device__ __forceinline__ void add_child_mem(const View<NX> &V, int m, float (&Pb)[nsym(NX)], float (&pb)[NX],
+                                              float *dst = nullptr) {
     constexpr int NS = nsym(NX);
     const int np = V.np;
     float Pm[NS], dm[NX];
@@ -904,6 +914,7 @@ __device__ __forceinline__ void add_child_mem(const View<NX> &V, int m, float (&
         Pb[e] += Pm[e];
     }
     V.load_x(V.d, m, dm);
+    if (dst) put_pairs<NX>(dst, dm);   /* the child's defect into its forward record */
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
         float v = V.p[(size_t)a * np + m];
@@ -962,6 +973,40 @@ __host__ __device__ constexpr int jac_stored() {   /* entries of A and B that ar
 template <int NX, int MODEL>
 __host__ __device__ constexpr int rows_stage() { return NX + jac_stored<NX, MODEL>() + NX * NU + NU; }
 
+/* Position of the stored Jacobian entry (a, c) (column c < NX: A, else B) among the entries that
+ * are not structurally fixed, in row-major order over [A B]. */
+template <int NX, int MODEL>
+__host__ __device__ constexpr int jac_slot(int a, int c) {
+    int k = 0;
+    for (int i = 0; i < NX; ++i)
+        for (int j = 0; j < NX + NU; ++j) {
+            if (i == a && j == c) return k;
+            k += (j < NX ? a_fixed<MODEL>(i, j) : b_fixed<MODEL>(i, j - NX)) < 0;
+        }
+    return -1;
+}
+
+/* Models whose per-path forward sweep reads node-major records (not the linear model, whose A, B
+ * may be per edge and live in the input rows). */
+template <int MODEL>
+__host__ __device__ constexpr bool frec_model() { return MODEL != 2; }
+
+/* Node-major forward record of node i (the vehicle models; per-edge linear dynamics keep the rows):
+ * K_i, the stored entries of A_i and B_i, k_i and d_i (the defect of the edge into i), written by the
+ * tree Riccati step, the linearisation and the defect phase.  A per-path forward stage moves the
+ * node's record with used/4 16-byte copies from one base address instead of one 4-byte copy per
+ * row; the parent's A, B come from the record the stage before read. */
+template <int NX, int MODEL>
+struct Frec {
+    static constexpr int K = 0, J = NU * NX, k = NU * NX + jac_stored<NX, MODEL>(), d = k + NU;
+    static constexpr int used = (d + NX + 3) & ~3;
+    static constexpr int stride = fr_stride(NX);
+    static constexpr int ring = 4;                       /* records in flight per path thread */
+    static constexpr int tstride = ring * used + 4;      /* floats per thread (spreads the banks) */
+    static_assert(!frec_model<MODEL>() || used <= stride, "forward record larger than its allocation");
+    static_assert(J % 4 == 0, "the Jacobian block must start on 16 bytes");
+};
+
 /* Riccati step of a non-leaf node n from the summed child value functions (Pb, pb):
  * H_n = R_n + B'Pb B, K_n = -H^-1 (M_n + B'Pb A), k_n = -H^-1 (r_n + B'pb) of
  * Eq. (tree_feedback_laws) (M_n = 0 here: no constraint couples x and u), then
@@ -969,7 +1014,8 @@ __host__ __device__ constexpr int rows_stage() { return NX + jac_stored<NX, MODE
 template <int NX, int MODEL, bool STORE_PV = true>
 __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V, int i, const RicIn<NX> &in,
                                              const float (&Pb)[nsym(NX)], const float (&pb)[NX],
-                                             float (&P)[nsym(NX)], float (&p)[NX], Shared &sh) {
+                                             float (&P)[nsym(NX)], float (&p)[NX], Shared &sh,
+                                             float *rec = nullptr) {
     const int np = V.np;
     const float w = in.w;
     const float(&q)[NX] = in.q;
@@ -1073,6 +1119,36 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
         for (int t = 0; t < NU; ++t) v += Qux[t][a] * kn[t];
         p[a] = v;
         if (STORE_PV) V.p[(size_t)a * np + i] = v;
+    }
+    if constexpr (frec_model<MODEL>()) {
+        if (rec) {   /* the node's forward record instead of the K, k rows: K, the stored A, B entries, k */
+            using F = Frec<NX, MODEL>;
+            constexpr int JS = F::k - F::J;
+            float jv[JS];
+#pragma unroll
+            for (int a = 0; a < NX; ++a) {
+#pragma unroll
+                for (int b = 0; b < NX; ++b)
+                    if (a_fixed<MODEL>(a, b) < 0) jv[jac_slot<NX, MODEL>(a, b)] = A[a][b];
+#pragma unroll
+                for (int b = 0; b < NU; ++b)
+                    if (b_fixed<MODEL>(a, b) < 0) jv[jac_slot<NX, MODEL>(a, NX + b)] = B[a][b];
+            }
+            float4 *rK = reinterpret_cast<float4 *>(rec + F::K);
+#pragma unroll
+            for (int q = 0; q < NU * NX / 4; ++q) {
+                const int e = 4 * q;
+                rK[q] = make_float4(Kn[e / NX][e % NX], Kn[(e + 1) / NX][(e + 1) % NX], Kn[(e + 2) / NX][(e + 2) % NX],
+                                    Kn[(e + 3) / NX][(e + 3) % NX]);
+            }
+            float4 *rJ = reinterpret_cast<float4 *>(rec + F::J);
+#pragma unroll
+            for (int q = 0; q < JS / 4; ++q) rJ[q] = make_float4(jv[4 * q], jv[4 * q + 1], jv[4 * q + 2], jv[4 * q + 3]);
+            if constexpr (JS % 4 == 2)
+                *reinterpret_cast<float2 *>(rec + F::k - 2) = make_float2(jv[JS - 2], jv[JS - 1]);
+            *reinterpret_cast<float2 *>(rec + F::k) = make_float2(kn[0], kn[1]);
+            return;
+        }
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
@@ -1268,7 +1344,7 @@ __device__ void riccati_edges(const ProbRec &R, const View<NX> &V, int i, float 
  * a node with several children. */
 template <int NX, int MODEL>
 __device__ __forceinline__ void riccati_from_children(const ProbRec &R, const View<NX> &V, int i, float (&P)[nsym(NX)],
-                                                      float (&p)[NX], Shared &sh) {
+                                                      float (&p)[NX], Shared &sh, bool rec = false) {
     constexpr int NS = nsym(NX);
     const int nch = V.nchild[i], fc = V.fchild[i];
     if constexpr (MODEL == 2) {
@@ -1282,10 +1358,12 @@ __device__ __forceinline__ void riccati_from_children(const ProbRec &R, const Vi
     for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
 #pragma unroll
     for (int a = 0; a < NX; ++a) pb[a] = 0.f;
-    for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
+    using F = Frec<NX, MODEL>;
+    for (int m = fc; m < fc + nch; ++m)
+        add_child_mem<NX>(V, m, Pb, pb, rec ? V.FR + (size_t)m * F::stride + F::d : nullptr);
     RicIn<NX> in;
     ric_load<NX, MODEL>(V, i, in, (MODEL == 2 && V.edge) ? fc : i);
-    riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
+    riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh, rec ? V.FR + (size_t)i * F::stride : nullptr);
 }
 
 /* Level-synchronous backward sweep: all nodes of a stage in parallel, one barrier per stage. */
@@ -1312,7 +1390,8 @@ __device__ void backward_level(const ProbRec &R, const View<NX> &V, Shared &sh) 
  * child in registers; the block synchronises only before the stages that hold branch nodes,
  * where the children's value functions are summed from memory. */
 template <int NX, int MODEL>
-__device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
+__device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh, bool rec = false) {
+    using F = Frec<NX, MODEL>;
     constexpr int NS = nsym(NX);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int S = R.n_paths, ns = R.n_stage, nb = R.n_bstage;
@@ -1330,7 +1409,7 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
                 const int i = path[k];
                 const int nch = V.nchild[i];
                 if (nch == 0) leaf_value<NX>(R, V, i, P, p);
-                else riccati_from_children<NX, MODEL>(R, V, i, P, p, sh);
+                else riccati_from_children<NX, MODEL>(R, V, i, P, p, sh, rec);
             }
             for (k = khi - 1; k >= klo; --k) {
                 const int i = path[k];   /* single child path[k+1], its value function in P, p */
@@ -1338,6 +1417,7 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
                 RicIn<NX> in;
                 V.load_x(V.d, path[k + 1], dm);
                 ric_load<NX, MODEL>(V, i, in, (MODEL == 2 && V.edge) ? path[k + 1] : i);
+                if (rec) put_pairs<NX>(V.FR + (size_t)path[k + 1] * F::stride + F::d, dm);
 #pragma unroll
                 for (int e = 0; e < NS; ++e) Pb[e] = 0.f + P[e];
 #pragma unroll
@@ -1347,7 +1427,7 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh) {
                     for (int b = 0; b < NX; ++b) v += P[sidx<NX>(a, b)] * dm[b];
                     pb[a] = 0.f + v;
                 }
-                riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
+                riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh, rec ? V.FR + (size_t)i * F::stride : nullptr);
             }
 
         }
@@ -1608,6 +1688,132 @@ __device__ void forward_path(const ProbRec &R, const View<NX> &V, float *stg, in
     __syncthreads();
 }
 
+
+__device__ __forceinline__ void cp16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+/* The per-path forward sweep on node-major records: stage k of path s copies node path[k + 2]'s
+ * record into the thread's ring (four records, 16-byte copies), then takes node i = path[k] from
+ * its own record (d_i, K_i, k_i) and its parent's (A, B, read the stage before):
+ * dx_i = A_p dx_p + B_p du_p + d_i, du_i = K_i dx_i + k_i.  Thread t's ring lives at
+ * stg[t * tstride], 16-byte aligned. */
+template <int NX, int MODEL>
+__device__ void forward_path_rec(const ProbRec &R, const View<NX> &V, float *stg) {
+    using F = Frec<NX, MODEL>;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int S = R.n_paths, ns = R.n_stage;
+    float *ring = stg + (size_t)tid * F::tstride;
+    for (int s = tid; s < S; s += nt) {
+        const int32_t *path = V.ptab + (size_t)s * ns;
+        const int depth = V.pdepth[s], top = V.ptop[s];
+        const int nst = depth + 1;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (q < nst) {
+                const float *src = V.FR + (size_t)path[q] * F::stride;
+#pragma unroll
+                for (int c = 0; c < F::used / 4; ++c) cp16(ring + q * F::used + 4 * c, src + 4 * c);
+            }
+            cp_commit();
+        }
+        float dxp[NX], dup[NU] = {0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < NX; ++j) dxp[j] = 0.f;
+        for (int k = 0; k <= depth; ++k) {
+            const int i = path[k];
+            {
+                const int q = k + 2;
+                if (q < nst) {
+                    const float *src = V.FR + (size_t)path[q] * F::stride;
+                    float *dst = ring + (q % F::ring) * F::used;
+#pragma unroll
+                    for (int c = 0; c < F::used / 4; ++c) cp16(dst + 4 * c, src + 4 * c);
+                }
+                cp_commit();
+                cp_wait<2>();
+            }
+            const float *cur = ring + (k % F::ring) * F::used;
+            const float *prv = ring + ((k + F::ring - 1) % F::ring) * F::used;
+            float dxv[NX], duv[NU];
+            if (k == 0) {
+#pragma unroll
+                for (int j = 0; j < NX; ++j) dxv[j] = 0.f;
+            } else {
+                float dv[NX];
+#pragma unroll
+                for (int j = 0; j < NX / 2; ++j) {
+                    const float2 t2 = reinterpret_cast<const float2 *>(cur + F::d)[j];
+                    dv[2 * j] = t2.x;
+                    dv[2 * j + 1] = t2.y;
+                }
+                float jv[F::k - F::J];
+#pragma unroll
+                for (int c = 0; c < (F::k - F::J) / 4; ++c) {
+                    const float4 t4 = reinterpret_cast<const float4 *>(prv + F::J)[c];
+                    jv[4 * c] = t4.x;
+                    jv[4 * c + 1] = t4.y;
+                    jv[4 * c + 2] = t4.z;
+                    jv[4 * c + 3] = t4.w;
+                }
+                if constexpr ((F::k - F::J) % 4 == 2) {
+                    const float2 t2 = *reinterpret_cast<const float2 *>(prv + F::k - 2);
+                    jv[F::k - F::J - 2] = t2.x;
+                    jv[F::k - F::J - 1] = t2.y;
+                }
+#pragma unroll
+                for (int a = 0; a < NX; ++a) {
+                    float v = dv[a];
+#pragma unroll
+                    for (int b = 0; b < NX; ++b) {
+                        const float ab = a_fixed<MODEL>(a, b) >= 0 ? (float)a_fixed<MODEL>(a, b)
+                                                                   : jv[jac_slot<NX, MODEL>(a, b)];
+                        v += ab * dxp[b];
+                    }
+#pragma unroll
+                    for (int b = 0; b < NU; ++b) {
+                        const float bb = b_fixed<MODEL>(a, b) >= 0 ? (float)b_fixed<MODEL>(a, b)
+                                                                   : jv[jac_slot<NX, MODEL>(a, NX + b)];
+                        v += bb * dup[b];
+                    }
+                    dxv[a] = v;
+                }
+            }
+            duv[0] = duv[1] = 0.f;
+            if (k < depth) {
+                float kv[NU * NX + NU];
+#pragma unroll
+                for (int c = 0; c < NU * NX / 4; ++c) {
+                    const float4 t4 = reinterpret_cast<const float4 *>(cur + F::K)[c];
+                    kv[4 * c] = t4.x;
+                    kv[4 * c + 1] = t4.y;
+                    kv[4 * c + 2] = t4.z;
+                    kv[4 * c + 3] = t4.w;
+                }
+                const float2 t2 = *reinterpret_cast<const float2 *>(cur + F::k);
+                kv[NU * NX] = t2.x;
+                kv[NU * NX + 1] = t2.y;
+#pragma unroll
+                for (int a = 0; a < NU; ++a) {
+                    float v = kv[NU * NX + a];
+#pragma unroll
+                    for (int b = 0; b < NX; ++b) v += kv[a * NX + b] * dxv[b];
+                    duv[a] = v;
+                }
+            }
+            if (k >= top) {
+                V.store_x(V.dx, i, dxv);
+                V.store_u(V.du, i, duv);
+            }
+#pragma unroll
+            for (int j = 0; j < NX; ++j) dxp[j] = dxv[j];
+            dup[0] = duv[0];
+            dup[1] = duv[1];
+        }
+    }
+    __syncthreads();
+}
 
 /* ------------------------------------------------------------------ scan sweeps (Sec. III-B) */
 /* The tree LQR of Sec. III-B with the sweeps' depth cut from N + 1 dependent steps to a logarithm
@@ -3071,7 +3277,8 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
             __syncthreads();
             if constexpr (SCAN) backward_scan<NX, MODEL>(R, V, sh);
             else if (variant == 3) backward_coop<NX, MODEL>(R, V, sh);
-            else if (variant == 2 || variant == 5) backward_path<NX, MODEL>(R, V, sh);
+            else if (variant == 2 || variant == 5)   /* variant 2 with staging: forward records, no K, k rows */
+                backward_path<NX, MODEL>(R, V, sh, frec_model<MODEL>() && variant == 2 && stg != nullptr);
             else backward_level<NX, MODEL>(R, V, sh);
             __syncthreads();
             c_bwd += clock64() - t0;
@@ -3085,7 +3292,14 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
             float dir[3] = {0.f, 0.f, 0.f};   /* grad'dz, dz'W dz, (dlam - lam)'d */
             if (SCAN || variant == 5) forward_jump<NX, MODEL>(R, V);
             else if (variant == 3) forward_coop<NX, MODEL>(R, V);
-            else if (variant == 2) forward_path<NX, MODEL>(R, V, stg, stg_ld);
+            else if (variant == 2) {
+                if constexpr (frec_model<MODEL>()) {
+                    if (stg) forward_path_rec<NX, MODEL>(R, V, stg);
+                    else forward_path<NX, MODEL>(R, V, nullptr, 0);
+                } else {
+                    forward_path<NX, MODEL>(R, V, stg, stg_ld);
+                }
+            }
             else forward_level<NX, MODEL>(R, V);
             multipliers_and_directions<NX, MODEL>(R, V, dir);
             block_sum<3>(dir, sh);
@@ -3301,7 +3515,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK <= BATCH_BLOCK ? 2 : 1) bmpc_solv
     __shared__ Shared sh;
     __shared__ int pid_s;
     __shared__ ProbRec rec_s;
-    extern __shared__ int32_t tab_s[];
+    extern __shared__ __align__(16) int32_t tab_s[];   /* 16-byte aligned: the forward records are copied in 16-byte units */
     float *stg = reinterpret_cast<float *>(tab_s + ((args.tab_ints + 3) & ~3));
     for (;;) {
         if (threadIdx.x == 0) pid_s = atomicAdd(args.queue, 1);
@@ -3798,13 +4012,14 @@ int max_block_threads() { return MAX_BLOCK; }
 /* Dynamic shared memory of a solve launch: the stage/path tables (tab_ints) and, when it fits in
  * 96 KB, the sweep staging of min(max_paths, block) path threads (*stg_ld, else 0). */
 size_t solve_smem(int model, int tab_ints, int max_paths, int block, int *stg_ld) {
-    const int rows = model == 0   ? rows_stage<4, 0>()
-                     : model == 1 ? rows_stage<6, 1>()
-                     : model == 2 ? rows_stage<4, 2>()
-                                  : rows_stage<4, 3>();
+    /* floats per path thread: the ring of node-major records, or (per-edge dynamics) the row slots */
+    const int per_thread = model == 0   ? Frec<4, 0>::tstride
+                           : model == 1 ? Frec<6, 1>::tstride
+                           : model == 2 ? SWEEP_DEPTH * rows_stage<4, 2>()
+                                        : Frec<4, 3>::tstride;
     const int ld = std::min(max_paths, block);
     const size_t tab = sizeof(int32_t) * (size_t)((tab_ints + 3) & ~3);
-    const size_t stg = sizeof(float) * (size_t)SWEEP_DEPTH * rows * ld;
+    const size_t stg = sizeof(float) * (size_t)per_thread * ld;
     if (ld > 0 && tab + stg <= 96u * 1024u) {
         *stg_ld = ld;
         return tab + stg;

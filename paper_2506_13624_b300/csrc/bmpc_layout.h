@@ -143,14 +143,22 @@ __host__ __device__ inline OutRows out_rows(int nx, int nc) {
  * c[nx] C[nsym] P[nsym] p[nx] (C and P symmetric, packed). */
 __host__ __device__ constexpr int cvf_rows(int nx) { return nx * nx + 2 * nx + 2 * nsym(nx); }
 
+/* Floats per node of the node-major forward records (scratch region fr): K[nu*nx], the entries of
+ * A and B that are not structurally fixed, k[nu], d[nx], padded to a multiple of 4 so that every
+ * record starts on a 16-byte boundary.  The models with n_x = 6 (dynamic bicycle) store 32 entries of
+ * [A B], those with n_x = 4 at most 12 (kinematic bicycle; the unicycle 10; the linear model keeps
+ * no records): 52 and 28 floats, checked against each model's record at compile time. */
+__host__ __device__ constexpr int fr_stride(int nx) { return nx == 6 ? 52 : 28; }
+
 /* scratch: A[nx*nx] B[nx*nu] f[nx] d[nx] q[nx] r[nu] hq[3] hr[nu] K[nu*nx] k[nu] P[nsym] p[nx]
  *          dx[nx] du[nu] lq[nx] nv[3] xl[2] ul[nu] cv[2 * cvf_rows] ja[2] hs[nsym + nu*nx + 3]
+ *          fr[fr_stride rows, node-major: fr_stride floats per node]
  * xl, ul: low-order parts of the compensated iterate (positions X, Y of the state deviation and the
  * inputs): the iterate is xi + xl, u + ul, each pair a float and its rounding remainder.
  * cv: two buffers of scan elements, indexed by position in the segment order (backward) or by node
  * (forward: closed-loop maps in the A, c rows); ja: two rows of ancestor indices (forward). */
 struct ScrRows {
-    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, xl, ul, cv, ja, hs, total;
+    int A, B, f, d, q, r, hq, hr, K, k, P, p, dx, du, lq, nv, xl, ul, cv, ja, hs, fr, total;
 };
 __host__ __device__ inline ScrRows scr_rows(int nx) {
     ScrRows s;
@@ -175,7 +183,8 @@ __host__ __device__ inline ScrRows scr_rows(int nx) {
     s.cv = s.ul + NU;
     s.ja = s.cv + 2 * cvf_rows(nx);
     s.hs = s.ja + 2;   /* exact-Hessian option: the node's modified block Q (packed), M, R (packed) */
-    s.total = s.hs + nsym(nx) + NU * nx + 3;
+    s.fr = s.hs + nsym(nx) + NU * nx + 3;
+    s.total = s.fr + fr_stride(nx);
     return s;
 }
 
