@@ -739,3 +739,26 @@ def test_exact_hessian_dynamic_bicycle_parity():
     angles): whole solves against the oracle's exact option, the same bar as Gauss-Newton."""
     ps = scenes.instances(3, 2, seed0=1)
     print(_run_config(ps, min_match=0.5, orc_kw={"hessian": 1}, hessian=1))
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_sweep_records_match_the_component_rows(model):
+    """The per-path sweeps on node-major records and on the component-major rows give the same
+    solution bit for bit: the records carry exactly the rows' values and the forward step does the
+    same arithmetic.  A problem solved alone uses the records (its threads' staging fits in shared
+    memory); next to a tree with 128 (dynamic) or 256 (kinematic) scenario paths in the same launch
+    the staging no longer fits and every problem of the launch sweeps on the rows."""
+    if model == 1:
+        small = [scenes.config3(0)]
+        wide = scenes.batch_problems(7, 1, model=1, N=50, splits={1: 2, 4: 2, 8: 2, 12: 2, 16: 2, 20: 2, 30: 2})
+    else:
+        small = [scenes.config2(1)]
+        wide = scenes.batch_problems(7, 1, model=0, N=24, splits={1: 2, 3: 2, 5: 2, 7: 2, 9: 2, 11: 2, 13: 2, 15: 2})
+    assert int(wide[0]["n"]) > 1000
+    alone = _gpu(small, block_threads=512, variant=2)[0]
+    mixed = _gpu(small + wide, block_threads=512, variant=2)[0]
+    assert alone["status"] == oracle.OK
+    for key in ("x", "u", "lam", "y"):
+        assert np.array_equal(alone[key], mixed[key]), key
+    for key in ("status", "inner_iters", "outer_iters", "ls_evals"):
+        assert alone[key] == mixed[key], key
