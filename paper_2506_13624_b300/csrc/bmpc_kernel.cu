@@ -562,15 +562,25 @@ __host__ __device__ constexpr int b_fixed(int a, int b) {
     if (MODEL == 3 && a == 2 && b == 0) return 0;
     return -1;
 }
+/* Index of row r of node i in a block of ROWS scratch rows.  The vehicle models' Jacobian rows are
+ * tiled by 32 nodes, a tile's rows contiguous: ((i / 32) ROWS + r) 32 + i % 32.  Consecutive nodes
+ * stay consecutive (coalesced node-parallel phases) and one node's rows sit at fixed offsets from
+ * one address (the per-path sweeps).  The linear model keeps component-major rows: with per-edge
+ * dynamics its A, B are input rows. */
+template <int ROWS, int MODEL>
+__device__ __forceinline__ size_t jrow(int np, int i, int r) {
+    if constexpr (MODEL == 2) return (size_t)r * np + i;
+    else return ((size_t)(i >> 5) * ROWS + r) * 32 + (i & 31);
+}
 template <int NX, int MODEL>
 __device__ __forceinline__ float aload(const float *A, int np, int i, int a, int b) {
     if (a_fixed<MODEL>(a, b) >= 0) return (float)a_fixed<MODEL>(a, b);
-    return A[(size_t)(a * NX + b) * np + i];
+    return A[jrow<NX * NX, MODEL>(np, i, a * NX + b)];
 }
 template <int NX, int MODEL>
 __device__ __forceinline__ float bload(const float *B, int np, int i, int a, int b) {
     if (b_fixed<MODEL>(a, b) >= 0) return (float)b_fixed<MODEL>(a, b);
-    return B[(size_t)(a * NU + b) * np + i];
+    return B[jrow<NX * NU, MODEL>(np, i, a * NU + b)];
 }
 
 /* ------------------------------------------------------------------ problem view */
@@ -1470,10 +1480,10 @@ __device__ __forceinline__ void fwd_issue(const View<NX> &V, int i, int pa, floa
         cp4(slot + (j++) * ld, V.d + (size_t)a * np + i);
 #pragma unroll
         for (int b = 0; b < NX; ++b)
-            if (a_fixed<MODEL>(a, b) < 0) cp4(slot + (j++) * ld, V.A + (size_t)(a * NX + b) * np + pa);
+            if (a_fixed<MODEL>(a, b) < 0) cp4(slot + (j++) * ld, V.A + jrow<NX * NX, MODEL>(np, pa, a * NX + b));
 #pragma unroll
         for (int b = 0; b < NU; ++b)
-            if (b_fixed<MODEL>(a, b) < 0) cp4(slot + (j++) * ld, V.B + (size_t)(a * NU + b) * np + pa);
+            if (b_fixed<MODEL>(a, b) < 0) cp4(slot + (j++) * ld, V.B + jrow<NX * NU, MODEL>(np, pa, a * NU + b));
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
@@ -3115,9 +3125,9 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                             /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
                             dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
                                 if (c < NX) {
-                                    if (a_fixed<MODEL>(a, c) < 0) V.A[(size_t)(a * NX + c) * np + i] = v;
+                                    if (a_fixed<MODEL>(a, c) < 0) V.A[jrow<NX * NX, MODEL>(np, i, a * NX + c)] = v;
                                 } else if (b_fixed<MODEL>(a, c - NX) < 0) {
-                                    V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                                    V.B[jrow<NX * NU, MODEL>(np, i, a * NU + (c - NX))] = v;
                                 }
                             });
                             V.store_x(V.f, i, xn);
@@ -3151,9 +3161,9 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                         /* Jacobian entries go straight to the scratch rows (column c < nx: A, else B) */
                         dyn_lin<NX, MODEL>(R, xa, u, xn, [&](int a, int c, float v) {
                             if (c < NX) {
-                                if (a_fixed<MODEL>(a, c) < 0) V.A[(size_t)(a * NX + c) * np + i] = v;
+                                if (a_fixed<MODEL>(a, c) < 0) V.A[jrow<NX * NX, MODEL>(np, i, a * NX + c)] = v;
                             } else if (b_fixed<MODEL>(a, c - NX) < 0) {
-                                V.B[(size_t)(a * NU + (c - NX)) * np + i] = v;
+                                V.B[jrow<NX * NU, MODEL>(np, i, a * NU + (c - NX))] = v;
                             }
                         });
                         V.store_x(V.f, i, xn);
