@@ -876,7 +876,7 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 
 /* ------------------------------------------------------------------ tree Riccati step */
 /* Terminal value function of a leaf: P = Q_N + penalty Hessian, p = q (stored and returned). */
-template <int NX>
+template <int NX, int MODEL>
 __device__ __forceinline__ void leaf_value(const ProbRec &R, const View<NX> &V, int i, float (&P)[nsym(NX)],
                                            float (&p)[NX]) {
     constexpr int NS = nsym(NX);
@@ -895,11 +895,11 @@ __device__ __forceinline__ void leaf_value(const ProbRec &R, const View<NX> &V, 
             P[sidx<NX>(a, b)] = v;
         }
 #pragma unroll
-    for (int e = 0; e < NS; ++e) V.P[(size_t)e * np + i] = P[e];
+    for (int e = 0; e < NS; ++e) V.P[jrow<NS, MODEL>(np, i, e)] = P[e];
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
         p[a] = V.q[(size_t)a * np + i];
-        V.p[(size_t)a * np + i] = p[a];
+        V.p[jrow<NX, MODEL>(np, i, a)] = p[a];
     }
 }
 
@@ -912,7 +912,7 @@ __device__ __forceinline__ void put_pairs(float *dst, const float (&v)[NX]) {
 
 /* Adds the value function of child m to (Pb, pb): Pb += P_m, pb += p_m + P_m d_m, with
  * P_m, p_m, d_m read from memory (Eq. tree_Riccati, sum over ch(n)). */
-template <int NX>
+template <int NX, int MODEL>
 __device__ __forceinline__ void add_child_mem(const View<NX> &V, int m, float (&Pb)[nsym(NX)], float (&pb)[NX],
                                               float *dst = nullptr) {
     constexpr int NS = nsym(NX);
@@ -920,14 +920,14 @@ __device__ __forceinline__ void add_child_mem(const View<NX> &V, int m, float (&
     float Pm[NS], dm[NX];
 #pragma unroll
     for (int e = 0; e < NS; ++e) {
-        Pm[e] = V.P[(size_t)e * np + m];
+        Pm[e] = V.P[jrow<NS, MODEL>(np, m, e)];
         Pb[e] += Pm[e];
     }
     V.load_x(V.d, m, dm);
     if (dst) put_pairs<NX>(dst, dm);   /* the child's defect into its forward record */
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
-        float v = V.p[(size_t)a * np + m];
+        float v = V.p[jrow<NX, MODEL>(np, m, a)];
 #pragma unroll
         for (int b = 0; b < NX; ++b) v += Pm[sidx<NX>(a, b)] * dm[b];
         pb[a] += v;
@@ -1120,7 +1120,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
 #pragma unroll
             for (int t = 0; t < NU; ++t) v += Qux[t][a] * Kn[t][b];
             P[sidx<NX>(a, b)] = v;
-            if (STORE_PV) V.P[(size_t)sidx<NX>(a, b) * np + i] = v;
+            if (STORE_PV) V.P[jrow<nsym(NX), MODEL>(np, i, sidx<NX>(a, b))] = v;
         }
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
@@ -1128,7 +1128,7 @@ __device__ __forceinline__ void riccati_node(const ProbRec &R, const View<NX> &V
 #pragma unroll
         for (int t = 0; t < NU; ++t) v += Qux[t][a] * kn[t];
         p[a] = v;
-        if (STORE_PV) V.p[(size_t)a * np + i] = v;
+        if (STORE_PV) V.p[jrow<NX, MODEL>(np, i, a)] = v;
     }
     if constexpr (frec_model<MODEL>()) {
         if (rec) {   /* the node's forward record instead of the K, k rows: K, the stored A, B entries, k */
@@ -1370,7 +1370,7 @@ __device__ __forceinline__ void riccati_from_children(const ProbRec &R, const Vi
     for (int a = 0; a < NX; ++a) pb[a] = 0.f;
     using F = Frec<NX, MODEL>;
     for (int m = fc; m < fc + nch; ++m)
-        add_child_mem<NX>(V, m, Pb, pb, rec ? V.FR + (size_t)m * F::stride + F::d : nullptr);
+        add_child_mem<NX, MODEL>(V, m, Pb, pb, rec ? V.FR + (size_t)m * F::stride + F::d : nullptr);
     RicIn<NX> in;
     ric_load<NX, MODEL>(V, i, in, (MODEL == 2 && V.edge) ? fc : i);
     riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh, rec ? V.FR + (size_t)i * F::stride : nullptr);
@@ -1386,7 +1386,7 @@ __device__ void backward_level(const ProbRec &R, const View<NX> &V, Shared &sh) 
         for (int i = s0 + tid; i < s1; i += nt) {
             float P[NS], p[NX];
             if (V.nchild[i] == 0) {
-                leaf_value<NX>(R, V, i, P, p);
+                leaf_value<NX, MODEL>(R, V, i, P, p);
                 continue;
             }
             riccati_from_children<NX, MODEL>(R, V, i, P, p, sh);
@@ -1418,7 +1418,7 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh, b
             {
                 const int i = path[k];
                 const int nch = V.nchild[i];
-                if (nch == 0) leaf_value<NX>(R, V, i, P, p);
+                if (nch == 0) leaf_value<NX, MODEL>(R, V, i, P, p);
                 else riccati_from_children<NX, MODEL>(R, V, i, P, p, sh, rec);
             }
             for (k = khi - 1; k >= klo; --k) {
@@ -1601,9 +1601,10 @@ __device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, con
         }
         if (i != 0) {
             float pv[NX], Pv[nsym(NX)], lv[NX], dv[NX], lqv[NX];
-            V.load_x(V.p, i, pv);
 #pragma unroll
-            for (int e = 0; e < nsym(NX); ++e) Pv[e] = V.P[(size_t)e * np + i];
+            for (int a = 0; a < NX; ++a) pv[a] = V.p[jrow<NX, MODEL>(np, i, a)];
+#pragma unroll
+            for (int e = 0; e < nsym(NX); ++e) Pv[e] = V.P[jrow<nsym(NX), MODEL>(np, i, e)];
             V.load_x(V.L, i, lv);
             V.load_x(V.d, i, dv);
 #pragma unroll
@@ -2141,7 +2142,7 @@ __device__ void backward_scan(const ProbRec &R, const View<NX> &V, Shared &sh) {
                 float P[NS], p[NX];
                 const int nch = V.nchild[i];
                 if (nch == 0) {
-                    leaf_value<NX>(R, V, i, P, p);
+                    leaf_value<NX, MODEL>(R, V, i, P, p);
                 } else {
                     float Pb[NS], pb[NX];
 #pragma unroll
@@ -2149,7 +2150,7 @@ __device__ void backward_scan(const ProbRec &R, const View<NX> &V, Shared &sh) {
 #pragma unroll
                     for (int a = 0; a < NX; ++a) pb[a] = 0.f;
                     const int fc = V.fchild[i];
-                    for (int m = fc; m < fc + nch; ++m) add_child_mem<NX>(V, m, Pb, pb);
+                    for (int m = fc; m < fc + nch; ++m) add_child_mem<NX, MODEL>(V, m, Pb, pb);
                     RicIn<NX> in;
                     ric_load<NX, MODEL>(V, i, in);
                     riccati_node<NX, MODEL>(R, V, i, in, Pb, pb, P, p, sh);
@@ -2175,9 +2176,9 @@ __device__ void backward_scan(const ProbRec &R, const View<NX> &V, Shared &sh) {
             if (V.fend[f] == f) continue;
             const int i = V.fnode[f];
 #pragma unroll
-            for (int e = 0; e < NS; ++e) V.P[(size_t)e * np + i] = cur[(size_t)(Cvf<NX>::P + e) * np + f];
+            for (int e = 0; e < NS; ++e) V.P[jrow<NS, MODEL>(np, i, e)] = cur[(size_t)(Cvf<NX>::P + e) * np + f];
 #pragma unroll
-            for (int a = 0; a < NX; ++a) V.p[(size_t)a * np + i] = cur[(size_t)(Cvf<NX>::p + a) * np + f];
+            for (int a = 0; a < NX; ++a) V.p[jrow<NX, MODEL>(np, i, a)] = cur[(size_t)(Cvf<NX>::p + a) * np + f];
         }
         __syncthreads();
     }
@@ -2188,7 +2189,7 @@ __device__ void backward_scan(const ProbRec &R, const View<NX> &V, Shared &sh) {
         for (int e = 0; e < NS; ++e) Pb[e] = 0.f;
 #pragma unroll
         for (int a = 0; a < NX; ++a) pb[a] = 0.f;
-        add_child_mem<NX>(V, V.fchild[i], Pb, pb);
+        add_child_mem<NX, MODEL>(V, V.fchild[i], Pb, pb);
         RicIn<NX> in;
         ric_load<NX, MODEL>(V, i, in);
         riccati_node<NX, MODEL, false>(R, V, i, in, Pb, pb, P, p, sh);
@@ -2398,12 +2399,12 @@ __device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V
     if (lane < NX) {
 #pragma unroll
         for (int a = 0; a < NX; ++a)
-            if (a <= lane) V.P[(size_t)sidx<NX>(a, lane) * np + i] = Pc[a];
+            if (a <= lane) V.P[jrow<nsym(NX), MODEL>(np, i, sidx<NX>(a, lane))] = Pc[a];
         V.K[(size_t)lane * np + i] = K0;
         V.K[(size_t)(NX + lane) * np + i] = K1;
     } else if (lane == NX) {
 #pragma unroll
-        for (int a = 0; a < NX; ++a) V.p[(size_t)a * np + i] = p[a];
+        for (int a = 0; a < NX; ++a) V.p[jrow<NX, MODEL>(np, i, a)] = p[a];
         V.k[i] = k0;
         V.k[(size_t)np + i] = k1;
     }
@@ -2460,9 +2461,10 @@ __device__ void backward_coop(const ProbRec &R, const View<NX> &V, Shared &sh) {
                     if (lane < NX) {
 #pragma unroll
                         for (int a = 0; a < NX; ++a)
-                            if (a <= lane) V.P[(size_t)sidx<NX>(a, lane) * np + i] = Pc[a];
+                            if (a <= lane) V.P[jrow<nsym(NX), MODEL>(np, i, sidx<NX>(a, lane))] = Pc[a];
                     } else if (lane == NX) {
-                        V.store_x(V.p, i, p);
+#pragma unroll
+                        for (int a = 0; a < NX; ++a) V.p[jrow<NX, MODEL>(np, i, a)] = p[a];
                     }
                 } else {
                     /* children summed from memory: column `lane` of Pbar, pbar replicated */
@@ -2477,10 +2479,10 @@ __device__ void backward_coop(const ProbRec &R, const View<NX> &V, Shared &sh) {
                     for (int m = fc; m < fc + nch; ++m) {
                         float dm[NX];
                         V.load_x(V.d, m, dm);
-                        float vm = V.p[(size_t)lc * np + m];
+                        float vm = V.p[jrow<NX, MODEL>(np, m, lc)];
 #pragma unroll
                         for (int a = 0; a < NX; ++a) {
-                            const float Pa = V.P[(size_t)sidx<NX>(a, lc) * np + m];
+                            const float Pa = V.P[jrow<nsym(NX), MODEL>(np, m, sidx<NX>(a, lc))];
                             Pbc[a] += Pa;
                             vm += Pa * dm[a];
                         }
