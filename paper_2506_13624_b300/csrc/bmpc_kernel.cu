@@ -582,6 +582,17 @@ __device__ __forceinline__ float bload(const float *B, int np, int i, int a, int
     if (b_fixed<MODEL>(a, b) >= 0) return (float)b_fixed<MODEL>(a, b);
     return B[jrow<NX * NU, MODEL>(np, i, a * NU + b)];
 }
+/* ROWS consecutive scratch rows of node i (tiled like the Jacobian rows for the vehicle models). */
+template <int ROWS, int MODEL>
+__device__ __forceinline__ void ld_rows(const float *base, int np, int i, float (&v)[ROWS]) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) v[r] = base[jrow<ROWS, MODEL>(np, i, r)];
+}
+template <int ROWS, int MODEL>
+__device__ __forceinline__ void st_rows(float *base, int np, int i, const float (&v)[ROWS]) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) base[jrow<ROWS, MODEL>(np, i, r)] = v[r];
+}
 
 /* ------------------------------------------------------------------ problem view */
 template <int NX>
@@ -882,7 +893,7 @@ __device__ __forceinline__ void leaf_value(const ProbRec &R, const View<NX> &V, 
     constexpr int NS = nsym(NX);
     const int np = V.np;
     const float w = V.w[i];
-    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+    const float hxx = V.hq[jrow<3, MODEL>(np, i, 0)], hxy = V.hq[jrow<3, MODEL>(np, i, 1)], hyy = V.hq[jrow<3, MODEL>(np, i, 2)];
 #pragma unroll
     for (int a = 0; a < NX; ++a)
 #pragma unroll
@@ -898,7 +909,7 @@ __device__ __forceinline__ void leaf_value(const ProbRec &R, const View<NX> &V, 
     for (int e = 0; e < NS; ++e) V.P[jrow<NS, MODEL>(np, i, e)] = P[e];
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
-        p[a] = V.q[(size_t)a * np + i];
+        p[a] = V.q[jrow<NX, MODEL>(np, i, a)];
         V.p[jrow<NX, MODEL>(np, i, a)] = p[a];
     }
 }
@@ -923,7 +934,7 @@ __device__ __forceinline__ void add_child_mem(const View<NX> &V, int m, float (&
         Pm[e] = V.P[jrow<NS, MODEL>(np, m, e)];
         Pb[e] += Pm[e];
     }
-    V.load_x(V.d, m, dm);
+    ld_rows<NX, MODEL>(V.d, V.np, m, dm);
     if (dst) put_pairs<NX>(dst, dm);   /* the child's defect into its forward record */
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
@@ -948,9 +959,9 @@ __device__ __forceinline__ void ric_load(const View<NX> &V, int i, RicIn<NX> &in
     const int np = V.np;
     if (ja < 0) ja = i;
     in.w = V.w[i];
-    V.load_x(V.q, i, in.q);
+    ld_rows<NX, MODEL>(V.q, V.np, i, in.q);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) in.hq[a] = V.hq[(size_t)a * np + i];
+    for (int a = 0; a < 3; ++a) in.hq[a] = V.hq[jrow<3, MODEL>(np, i, a)];
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
 #pragma unroll
@@ -960,8 +971,8 @@ __device__ __forceinline__ void ric_load(const View<NX> &V, int i, RicIn<NX> &in
     }
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
-        in.r[a] = V.r[(size_t)a * np + i];
-        in.hr[a] = V.hr[(size_t)a * np + i];
+        in.r[a] = V.r[jrow<NU, MODEL>(np, i, a)];
+        in.hr[a] = V.hr[jrow<NU, MODEL>(np, i, a)];
     }
 }
 
@@ -1425,7 +1436,7 @@ __device__ void backward_path(const ProbRec &R, const View<NX> &V, Shared &sh, b
                 const int i = path[k];   /* single child path[k+1], its value function in P, p */
                 float dm[NX], Pb[NS], pb[NX];
                 RicIn<NX> in;
-                V.load_x(V.d, path[k + 1], dm);
+                ld_rows<NX, MODEL>(V.d, V.np, path[k + 1], dm);
                 ric_load<NX, MODEL>(V, i, in, (MODEL == 2 && V.edge) ? path[k + 1] : i);
                 if (rec) put_pairs<NX>(V.FR + (size_t)path[k + 1] * F::stride + F::d, dm);
 #pragma unroll
@@ -1457,7 +1468,7 @@ __device__ __forceinline__ void fwd_load(const View<NX> &V, int i, int pa, FwdIn
     const int np = V.np;
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
-        in.d[a] = V.d[(size_t)a * np + i];
+        in.d[a] = V.d[jrow<NX, MODEL>(np, i, a)];
 #pragma unroll
         for (int b = 0; b < NX; ++b) in.A[a][b] = aload<NX, MODEL>(V.A, np, pa, a, b);
 #pragma unroll
@@ -1477,7 +1488,7 @@ __device__ __forceinline__ void fwd_issue(const View<NX> &V, int i, int pa, floa
     int j = 0;
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
-        cp4(slot + (j++) * ld, V.d + (size_t)a * np + i);
+        cp4(slot + (j++) * ld, V.d + jrow<NX, MODEL>(np, i, a));
 #pragma unroll
         for (int b = 0; b < NX; ++b)
             if (a_fixed<MODEL>(a, b) < 0) cp4(slot + (j++) * ld, V.A + jrow<NX * NX, MODEL>(np, pa, a * NX + b));
@@ -1562,11 +1573,11 @@ __device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, con
         V.load_u(V.du, i, duv);
         const float w = V.w[i];
         const float *Qd = nch ? R.Qw : R.QNw;
-        const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
-        V.load_x(V.q, i, qv);
+        const float hxx = V.hq[jrow<3, MODEL>(np, i, 0)], hxy = V.hq[jrow<3, MODEL>(np, i, 1)], hyy = V.hq[jrow<3, MODEL>(np, i, 2)];
+        ld_rows<NX, MODEL>(V.q, V.np, i, qv);
         if (nch) {
-            V.load_u(V.r, i, rv);
-            V.load_u(V.hr, i, hrv);
+            ld_rows<NU, MODEL>(V.r, V.np, i, rv);
+            ld_rows<NU, MODEL>(V.hr, V.np, i, hrv);
         }
 #pragma unroll
         for (int a = 0; a < NX; ++a) dir[0] += qv[a] * dxv[a];
@@ -1606,7 +1617,7 @@ __device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, con
 #pragma unroll
             for (int e = 0; e < nsym(NX); ++e) Pv[e] = V.P[jrow<nsym(NX), MODEL>(np, i, e)];
             V.load_x(V.L, i, lv);
-            V.load_x(V.d, i, dv);
+            ld_rows<NX, MODEL>(V.d, V.np, i, dv);
 #pragma unroll
             for (int a = 0; a < NX; ++a) {
                 float v = pv[a];
@@ -1861,7 +1872,7 @@ __device__ __forceinline__ void cvf_step(const ProbRec &R, const View<NX> &V, in
         ir[a] = 1.f / h;
     }
     float dm[NX];
-    V.load_x(V.d, m, dm);
+    ld_rows<NX, MODEL>(V.d, V.np, m, dm);
 #pragma unroll
     for (int a = 0; a < NX; ++a) {
 #pragma unroll
@@ -2351,12 +2362,12 @@ __device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V
             for (int t = 0; t < NX; ++t) v += F[t][a] * PFc[t];
             Hc[a] = v;
         }
-        const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+        const float hxx = V.hq[jrow<3, MODEL>(np, i, 0)], hxy = V.hq[jrow<3, MODEL>(np, i, 1)], hyy = V.hq[jrow<3, MODEL>(np, i, 2)];
 #pragma unroll
         for (int a = 0; a < NZ; ++a) {
             if (a != lane) continue;
             if (a < NX) Hc[a] += w * R.Qw[a];
-            else Hc[a] += w * R.Rw[a - NX] + V.hr[(size_t)(a - NX) * np + i];
+            else Hc[a] += w * R.Rw[a - NX] + V.hr[jrow<NU, MODEL>(np, i, a - NX)];
         }
         if (lane == 0) {
             Hc[0] += hxx;
@@ -2365,7 +2376,7 @@ __device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V
             Hc[0] += hxy;
             Hc[1] += hyy;
         }
-        g = lane < NX ? V.q[(size_t)lane * np + i] : V.r[(size_t)(lane - NX) * np + i];
+        g = lane < NX ? V.q[jrow<NX, MODEL>(np, i, lane)] : V.r[jrow<NU, MODEL>(np, i, lane - NX)];
 #pragma unroll
         for (int t = 0; t < NX; ++t) g += Fc[t] * pb[t];
     }
@@ -2411,11 +2422,11 @@ __device__ __forceinline__ void coop_riccati(const ProbRec &R, const View<NX> &V
 }
 
 /* pbar = p + P d (P distributed by columns over the lanes, p replicated): returns pbar replicated. */
-template <int NX>
+template <int NX, int MODEL>
 __device__ __forceinline__ void coop_pbar(const View<NX> &V, int c, const float (&Pc)[NX], const float (&p)[NX],
                                           float (&pb)[NX], int lane, unsigned gmask) {
     float dm[NX];
-    V.load_x(V.d, c, dm);
+    ld_rows<NX, MODEL>(V.d, V.np, c, dm);
     float v = 0.f;
 #pragma unroll
     for (int t = 0; t < NX; ++t) v += Pc[t] * dm[t];
@@ -2449,7 +2460,7 @@ __device__ void backward_coop(const ProbRec &R, const View<NX> &V, Shared &sh) {
                     const float w = V.w[i];
 #pragma unroll
                     for (int a = 0; a < NX; ++a) Pc[a] = (a == lc) ? w * R.QNw[a] : 0.f;
-                    const float hxx = V.hq[i], hxy = V.hq[(size_t)np + i], hyy = V.hq[2 * (size_t)np + i];
+                    const float hxx = V.hq[jrow<3, MODEL>(np, i, 0)], hxy = V.hq[jrow<3, MODEL>(np, i, 1)], hyy = V.hq[jrow<3, MODEL>(np, i, 2)];
                     if (lc == 0) {
                         Pc[0] += hxx;
                         Pc[1] += hxy;
@@ -2457,7 +2468,7 @@ __device__ void backward_coop(const ProbRec &R, const View<NX> &V, Shared &sh) {
                         Pc[0] += hxy;
                         Pc[1] += hyy;
                     }
-                    V.load_x(V.q, i, p);
+                    ld_rows<NX, MODEL>(V.q, V.np, i, p);
                     if (lane < NX) {
 #pragma unroll
                         for (int a = 0; a < NX; ++a)
@@ -2478,7 +2489,7 @@ __device__ void backward_coop(const ProbRec &R, const View<NX> &V, Shared &sh) {
                     const int fc = V.fchild[i];
                     for (int m = fc; m < fc + nch; ++m) {
                         float dm[NX];
-                        V.load_x(V.d, m, dm);
+                        ld_rows<NX, MODEL>(V.d, V.np, m, dm);
                         float vm = V.p[jrow<NX, MODEL>(np, m, lc)];
 #pragma unroll
                         for (int a = 0; a < NX; ++a) {
@@ -2496,7 +2507,7 @@ __device__ void backward_coop(const ProbRec &R, const View<NX> &V, Shared &sh) {
             for (int k = khi - 1; k >= klo; --k) {
                 const int i = path[k], c = path[k + 1];
                 float pb[NX];
-                coop_pbar<NX>(V, c, Pc, p, pb, lane, gmask);
+                coop_pbar<NX, MODEL>(V, c, Pc, p, pb, lane, gmask);
                 float Pbc[NX];
 #pragma unroll
                 for (int a = 0; a < NX; ++a) Pbc[a] = Pc[a];
@@ -2527,7 +2538,7 @@ __device__ void forward_coop(const ProbRec &R, const View<NX> &V) {
             const int i = path[k];
             if (i != 0) {
                 const int pa = path[k - 1];
-                float v = V.d[(size_t)la * np + i];
+                float v = V.d[jrow<NX, MODEL>(np, i, la)];
 #pragma unroll
                 for (int b = 0; b < NX; ++b) v += aload<NX, MODEL>(V.A, np, pa, la, b) * dx[b];
 #pragma unroll
@@ -2942,12 +2953,12 @@ __device__ __noinline__ void node_exact_hessian(const ProbRec &R, const View<NX>
         for (int b = 0; b < NZ; ++b) S[a][b] = 0.f;
 #pragma unroll
     for (int a = 0; a < NX; ++a) S[a][a] = w * Qd[a];
-    S[0][0] += V.hq[i];
-    S[0][1] += V.hq[(size_t)np + i];
-    S[1][0] += V.hq[(size_t)np + i];
-    S[1][1] += V.hq[2 * (size_t)np + i];
+    S[0][0] += V.hq[jrow<3, MODEL>(np, i, 0)];
+    S[0][1] += V.hq[jrow<3, MODEL>(np, i, 1)];
+    S[1][0] += V.hq[jrow<3, MODEL>(np, i, 1)];
+    S[1][1] += V.hq[jrow<3, MODEL>(np, i, 2)];
 #pragma unroll
-    for (int a = 0; a < NU; ++a) S[NX + a][NX + a] = leaf ? 1.f : w * R.Rw[a] + V.hr[(size_t)a * np + i];
+    for (int a = 0; a < NU; ++a) S[NX + a][NX + a] = leaf ? 1.f : w * R.Rw[a] + V.hr[jrow<NU, MODEL>(np, i, a)];
     float x[NX], u[NU];
     Lo lo;
     V.load_x(V.X, i, x);
@@ -3103,12 +3114,12 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                         V.store_lo(i, lo);
                         if (i != 0) V.store_x(V.L, i, lam);
                     }
-                    V.store_x(V.q, i, q);
-                    V.store_u(V.r, i, r);
-                    V.hq[i] = hq[0];
-                    V.hq[(size_t)np + i] = hq[1];
-                    V.hq[2 * (size_t)np + i] = hq[2];
-                    V.store_u(V.hr, i, hr);
+                    st_rows<NX, MODEL>(V.q, V.np, i, q);
+                    st_rows<NU, MODEL>(V.r, V.np, i, r);
+                    V.hq[jrow<3, MODEL>(np, i, 0)] = hq[0];
+                    V.hq[jrow<3, MODEL>(np, i, 1)] = hq[1];
+                    V.hq[jrow<3, MODEL>(np, i, 2)] = hq[2];
+                    st_rows<NU, MODEL>(V.hr, V.np, i, hr);
                     V.nv[i] = la;
                     if (!is_leaf && relin) {
                         bool done = false;
@@ -3149,12 +3160,12 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                         V.store_lo(i, lo);
                     }
                     const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, lo, rho, q, r, hq, hr);
-                    V.store_x(V.q, i, q);
-                    V.store_u(V.r, i, r);
-                    V.hq[i] = hq[0];
-                    V.hq[(size_t)np + i] = hq[1];
-                    V.hq[2 * (size_t)np + i] = hq[2];
-                    V.store_u(V.hr, i, hr);
+                    st_rows<NX, MODEL>(V.q, V.np, i, q);
+                    st_rows<NU, MODEL>(V.r, V.np, i, r);
+                    V.hq[jrow<3, MODEL>(np, i, 0)] = hq[0];
+                    V.hq[jrow<3, MODEL>(np, i, 1)] = hq[1];
+                    V.hq[jrow<3, MODEL>(np, i, 2)] = hq[2];
+                    st_rows<NU, MODEL>(V.hr, V.np, i, hr);
                     V.nv[i] = la;
                     if (!is_leaf && relin) {
                         float xa[NX], xn[NX];
@@ -3194,7 +3205,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                 V.load_x(V.X, i, xi);
                 V.load_x(V.xref, i, xri);
                 V.load_x(V.L, i, li);
-                V.load_x(V.q, i, qi);
+                ld_rows<NX, MODEL>(V.q, V.np, i, qi);
                 V.load_x(V.X, pa, xp);
                 V.load_x(V.xref, pa, xrp);
                 V.load_x(V.f, (MODEL == 2 && V.edge) ? i : pa, fp);   /* the increment of the edge into i */
@@ -3212,7 +3223,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                         rk = fmaxf(rk, fabsf(dj));
                         gx[j] = qi[j] - lj;
                     }
-                    V.store_x(V.d, i, dv);
+                    st_rows<NX, MODEL>(V.d, V.np, i, dv);
                 }
                 V.nv[(size_t)np + i] = ld;
                 V.nv[2 * (size_t)np + i] = dd;
@@ -3220,7 +3231,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                 if constexpr (MODEL == 2) {
                     if (nch && V.edge) {   /* per-edge: sum over children of A_m' lam_m and B_m' lam_m */
                         float gu[NU];
-                        V.load_u(V.r, i, gu);
+                        ld_rows<NU, MODEL>(V.r, V.np, i, gu);
                         for (int m = fc; m < fc + nch; ++m) {
                             float lm[NX];
                             V.load_x(V.L, m, lm);
@@ -3248,7 +3259,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
 #pragma unroll
                         for (int b = 0; b < NU; ++b) Bi[a][b] = bload<NX, MODEL>(V.B, np, i, a, b);
                     }
-                    V.load_u(V.r, i, ri);
+                    ld_rows<NU, MODEL>(V.r, V.np, i, ri);
                     if (i != 0) {
 #pragma unroll
                         for (int a = 0; a < NX; ++a)
