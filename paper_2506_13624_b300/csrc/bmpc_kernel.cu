@@ -1554,8 +1554,8 @@ __device__ __forceinline__ void forward_node(const View<NX> &V, int i, int pa, b
         }
     }
     if (own) {
-        V.store_x(V.dx, i, dxv);
-        V.store_u(V.du, i, duv);
+        st_rows<NX, MODEL>(V.dx, V.np, i, dxv);
+        st_rows<NU, MODEL>(V.du, V.np, i, duv);
     }
 }
 
@@ -1569,8 +1569,8 @@ __device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, con
          * first merit terms) the value function, multipliers and defect for lam_QP */
         const int nch = V.nchild[i];
         float dxv[NX], duv[NU], qv[NX], rv[NU], hrv[NU];
-        V.load_x(V.dx, i, dxv);
-        V.load_u(V.du, i, duv);
+        ld_rows<NX, MODEL>(V.dx, V.np, i, dxv);
+        ld_rows<NU, MODEL>(V.du, V.np, i, duv);
         const float w = V.w[i];
         const float *Qd = nch ? R.Qw : R.QNw;
         const float hxx = V.hq[jrow<3, MODEL>(np, i, 0)], hxy = V.hq[jrow<3, MODEL>(np, i, 1)], hyy = V.hq[jrow<3, MODEL>(np, i, 2)];
@@ -1627,7 +1627,7 @@ __device__ __forceinline__ void multipliers_and_directions(const ProbRec &R, con
                 const float lam = lv[a];
                 dir[2] += ((v - lam) - lam) * dv[a];
             }
-            V.store_x(V.lq, i, lqv);
+            st_rows<NX, MODEL>(V.lq, V.np, i, lqv);
         }
     }
 }
@@ -1644,8 +1644,8 @@ __device__ void forward_level(const ProbRec &R, const View<NX> &V) {
             for (int j = 0; j < NX; ++j) dxp[j] = 0.f;
             const int pa = i ? V.parent[i] : -1;
             if (pa >= 0) {
-                V.load_x(V.dx, pa, dxp);
-                V.load_u(V.du, pa, dup);
+                ld_rows<NX, MODEL>(V.dx, V.np, pa, dxp);
+                ld_rows<NU, MODEL>(V.du, V.np, pa, dup);
             }
             FwdIn<NX> in;
             /* Jacobians of the edge into i: the parent's, or i's own with per-edge dynamics */
@@ -1825,8 +1825,8 @@ __device__ void forward_path_rec(const ProbRec &R, const View<NX> &V, float *stg
                 }
             }
             if (k >= top) {
-                V.store_x(V.dx, i, dxv);
-                V.store_u(V.du, i, duv);
+                st_rows<NX, MODEL>(V.dx, V.np, i, dxv);
+                st_rows<NU, MODEL>(V.du, V.np, i, duv);
             }
 #pragma unroll
             for (int j = 0; j < NX; ++j) dxp[j] = dxv[j];
@@ -2292,7 +2292,7 @@ __device__ void forward_jump(const ProbRec &R, const View<NX> &V) {
         float dxv[NX], du0 = 0.f, du1 = 0.f;
 #pragma unroll
         for (int r = 0; r < NX; ++r) dxv[r] = i ? cur[(size_t)(F::c + r) * np + i] : 0.f;
-        V.store_x(V.dx, i, dxv);
+        st_rows<NX, MODEL>(V.dx, V.np, i, dxv);
         if (V.nchild[i]) {
             du0 = V.k[i];
             du1 = V.k[(size_t)np + i];
@@ -2302,8 +2302,8 @@ __device__ void forward_jump(const ProbRec &R, const View<NX> &V) {
                 du1 += V.K[(size_t)(NX + b) * np + i] * dxv[b];
             }
         }
-        V.du[i] = du0;
-        V.du[(size_t)np + i] = du1;
+        V.du[jrow<NU, MODEL>(np, i, 0)] = du0;
+        V.du[jrow<NU, MODEL>(np, i, 1)] = du1;
     }
 }
 
@@ -2559,11 +2559,11 @@ __device__ void forward_coop(const ProbRec &R, const View<NX> &V) {
                 if (lane < NX) {
 #pragma unroll
                     for (int a = 0; a < NX; ++a)
-                        if (a == lane) V.dx[(size_t)a * np + i] = dx[a];
+                        if (a == lane) V.dx[jrow<NX, MODEL>(np, i, a)] = dx[a];
                 } else if (lane < NX + NU) {
 #pragma unroll
                     for (int a = 0; a < NU; ++a)
-                        if (a == lane - NX) V.du[(size_t)a * np + i] = du[a];
+                        if (a == lane - NX) V.du[jrow<NU, MODEL>(np, i, a)] = du[a];
                 }
             }
         }
@@ -2659,17 +2659,17 @@ __device__ float start_merit(const ProbRec &R, const View<NX> &V, float rho, flo
 
 /* The accepted step at node i: x += a dx, u += a du (in registers, caller stores) and, except at
  * the root, lam += a (lam_QP - lam) in memory (Algorithm 1, update after the line search). */
-template <int NX>
+template <int NX, int MODEL>
 __device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU],
                                            float (&lam)[NX], Lo &lo) {
     /* every row is loaded before anything is computed or stored, so the loads go out together;
      * the caller stores x, u and (for i != 0) lam after the rest of its node work */
     float dxv[NX], duv[NU], lmv[NX], lqv[NX];
-    V.load_x(V.dx, i, dxv);
-    V.load_u(V.du, i, duv);
+    ld_rows<NX, MODEL>(V.dx, V.np, i, dxv);
+    ld_rows<NU, MODEL>(V.du, V.np, i, duv);
     if (i != 0) {
         V.load_x(V.L, i, lmv);
-        V.load_x(V.lq, i, lqv);
+        ld_rows<NX, MODEL>(V.lq, V.np, i, lqv);
     }
     if (V.comp) {
         comp_add(x[0], lo.x[0], a * dxv[0]);
@@ -2691,23 +2691,23 @@ __device__ __forceinline__ void apply_step(const View<NX> &V, int i, float a, fl
 }
 
 /* The same step row by row, storing lam_i as it goes (the register-lean form; see hoist_loads). */
-template <int NX>
+template <int NX, int MODEL>
 __device__ __forceinline__ void apply_step_serial(const View<NX> &V, int i, float a, float (&x)[NX], float (&u)[NU],
                                                   Lo &lo) {
     const int np = V.np;
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
-        const float t = a * V.dx[(size_t)j * np + i];
+        const float t = a * V.dx[jrow<NX, MODEL>(np, i, j)];
         if (j < 2 && V.comp) comp_add(x[j], lo.x[j], t);
         else x[j] += t;
         if (i != 0) {
             const float lm = V.L[(size_t)j * np + i];
-            V.L[(size_t)j * np + i] = lm + a * (V.lq[(size_t)j * np + i] - lm);
+            V.L[(size_t)j * np + i] = lm + a * (V.lq[jrow<NX, MODEL>(np, i, j)] - lm);
         }
     }
 #pragma unroll
     for (int j = 0; j < NU; ++j) {
-        const float t = a * V.du[(size_t)j * np + i];
+        const float t = a * V.du[jrow<NU, MODEL>(np, i, j)];
         if (V.comp) comp_add(u[j], lo.u[j], t);
         else u[j] += t;
     }
@@ -3101,7 +3101,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     V.load_u(V.U, i, u);
                     V.load_lo(i, lo);
                     const bool step = pending > 0.f;
-                    if (step) apply_step<NX>(V, i, pending, x, u, lam, lo);
+                    if (step) apply_step<NX, MODEL>(V, i, pending, x, u, lam, lo);
                     const float la = node_la<NX, true>(R, V, i, is_leaf, x, u, lo, rho, q, r, hq, hr);
                     float xa[NX];
                     if (!is_leaf && relin) {
@@ -3120,7 +3120,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     V.hq[jrow<3, MODEL>(np, i, 1)] = hq[1];
                     V.hq[jrow<3, MODEL>(np, i, 2)] = hq[2];
                     st_rows<NU, MODEL>(V.hr, V.np, i, hr);
-                    V.nv[i] = la;
+                    V.nv[jrow<3, MODEL>(np, i, 0)] = la;
                     if (!is_leaf && relin) {
                         bool done = false;
                         if constexpr (MODEL == 2) {
@@ -3154,7 +3154,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     V.load_u(V.U, i, u);
                     V.load_lo(i, lo);
                     if (pending > 0.f) {
-                        apply_step_serial<NX>(V, i, pending, x, u, lo);
+                        apply_step_serial<NX, MODEL>(V, i, pending, x, u, lo);
                         V.store_x(V.X, i, x);
                         V.store_u(V.U, i, u);
                         V.store_lo(i, lo);
@@ -3166,7 +3166,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     V.hq[jrow<3, MODEL>(np, i, 1)] = hq[1];
                     V.hq[jrow<3, MODEL>(np, i, 2)] = hq[2];
                     st_rows<NU, MODEL>(V.hr, V.np, i, hr);
-                    V.nv[i] = la;
+                    V.nv[jrow<3, MODEL>(np, i, 0)] = la;
                     if (!is_leaf && relin) {
                         float xa[NX], xn[NX];
     #pragma unroll
@@ -3194,7 +3194,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                  * merit terms), then the Jacobians A_i, B_i and r_i for the coupling terms */
                 const int nch = V.nchild[i], fc = V.fchild[i];
                 const int pa = i ? V.parent[i] : 0;
-                const float la_i = V.nv[i];
+                const float la_i = V.nv[jrow<3, MODEL>(np, i, 0)];
                 float lsum[NX];
 #pragma unroll
                 for (int j = 0; j < NX; ++j) lsum[j] = 0.f;
@@ -3225,8 +3225,8 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     }
                     st_rows<NX, MODEL>(V.d, V.np, i, dv);
                 }
-                V.nv[(size_t)np + i] = ld;
-                V.nv[2 * (size_t)np + i] = dd;
+                V.nv[jrow<3, MODEL>(np, i, 1)] = ld;
+                V.nv[jrow<3, MODEL>(np, i, 2)] = dd;
                 bool edge_done = false;
                 if constexpr (MODEL == 2) {
                     if (nch && V.edge) {   /* per-edge: sum over children of A_m' lam_m and B_m' lam_m */
@@ -3354,11 +3354,11 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                         float x[NX], u[NU], dxv[NX], duv[NU];
                         V.load_x(V.X, i, x);
                         V.load_u(V.U, i, u);
-                        V.load_x(V.dx, i, dxv);
-                        V.load_u(V.du, i, duv);
-                        float base = V.nv[i];
+                        ld_rows<NX, MODEL>(V.dx, V.np, i, dxv);
+                        ld_rows<NU, MODEL>(V.du, V.np, i, duv);
+                        float base = V.nv[jrow<3, MODEL>(np, i, 0)];
                         for (int m = fc; m < fc + nch; ++m)
-                            base += V.nv[(size_t)np + m] + 0.5f * mu * V.nv[2 * (size_t)np + m];
+                            base += V.nv[jrow<3, MODEL>(np, m, 1)] + 0.5f * mu * V.nv[jrow<3, MODEL>(np, m, 2)];
                         float xt[NX], ut[NU], qd[NX], rd[NU], hqd[3], hrd[NU];
                         Lo lt;
                         V.load_lo(i, lt);
@@ -3393,10 +3393,10 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
 #pragma unroll
                                 for (int j = 0; j < NX; ++j) {
                                     const float lm = V.L[(size_t)j * np + m];
-                                    const float ltj = lm + al * (V.lq[(size_t)j * np + m] - lm);
+                                    const float ltj = lm + al * (V.lq[jrow<NX, MODEL>(np, m, j)] - lm);
                                     const float dref = V.xref[(size_t)j * np + i] - V.xref[(size_t)j * np + m];
                                     const float dm = (dref + ((x[j] - V.X[(size_t)j * np + m]) +
-                                                              al * (dxv[j] - V.dx[(size_t)j * np + m]))) + ft[j];
+                                                              al * (dxv[j] - V.dx[jrow<NX, MODEL>(np, m, j)]))) + ft[j];
                                     v += ltj * dm + 0.5f * mu * dm * dm;
                                 }
                             }
@@ -3437,7 +3437,7 @@ __device__ __forceinline__ void solve_problem(const ProbRec &R, const int32_t *i
                     V.load_x(V.X, i, x);
                     V.load_u(V.U, i, u);
                     V.load_lo(i, lo);
-                    apply_step_serial<NX>(V, i, pending, x, u, lo);
+                    apply_step_serial<NX, MODEL>(V, i, pending, x, u, lo);
                     V.store_x(V.X, i, x);
                     V.store_u(V.U, i, u);
                     V.store_lo(i, lo);
