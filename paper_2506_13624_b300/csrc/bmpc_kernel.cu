@@ -562,10 +562,11 @@ __host__ __device__ constexpr int b_fixed(int a, int b) {
     if (MODEL == 3 && a == 2 && b == 0) return 0;
     return -1;
 }
-/* Index of row r of node i in a block of ROWS scratch rows.  The vehicle models' Jacobian rows are
- * tiled by 32 nodes, a tile's rows contiguous: ((i / 32) ROWS + r) 32 + i % 32.  Consecutive nodes
- * stay consecutive (coalesced node-parallel phases) and one node's rows sit at fixed offsets from
- * one address (the per-path sweeps).  The linear model keeps component-major rows: with per-edge
+/* Index of row r of node i in a block of ROWS scratch rows.  The vehicle models' solver rows (A, B,
+ * P, p, q, r, the penalty terms, the defects, dx, du, lam_QP, the merit terms) are tiled by 32
+ * nodes, a tile's rows contiguous: ((i / 32) ROWS + r) 32 + i % 32.  Consecutive nodes stay
+ * consecutive (coalesced node-parallel phases) and one node's rows sit at fixed offsets from one
+ * address (the per-path sweeps).  The linear model keeps component-major rows: with per-edge
  * dynamics its A, B are input rows. */
 template <int ROWS, int MODEL>
 __device__ __forceinline__ size_t jrow(int np, int i, int r) {
